@@ -1,0 +1,232 @@
+/*
+ * cg.h -- C ABI of the GB300 (sm_103a) particle <-> dual-grid coupling
+ * library: the per-step exchange between Lagrangian particles and the two
+ * Eulerian grids of the dual-grid multiscale CFD-DEM coupling of
+ * Pozzetti, Jasak, Besseron, Rousset, Peters, "A parallel dual-grid
+ * multiscale approach to CFD-DEM couplings" (arXiv 1807.11834).
+ *
+ * Sec. 2.1 and Fig. 1 of the paper: a coarse uniform "bulk" grid maps the
+ * Lagrangian particle fields to Eulerian ones and solves the fluid-particle
+ * interaction; a fine grid carries the fluid.  Particle-related fields go
+ * bulk -> fine, the fluid solution goes fine -> bulk.  One step is
+ *   (a0) bin particles by bulk cell          cg_bin_particles
+ *   (a1) deposit particle volume -> porosity cg_deposit(CG_DEP_VOLUME)
+ *   (a2) average fine velocity onto bulk     cg_average_fine_to_bulk
+ *   (a3) drag at the particles (+ reaction)  cg_drag / cg_deposit(CG_DEP_MOMENTUM)
+ *   (a4) project the bulk source onto fine   cg_project_bulk_to_fine
+ *   all fused in                              cg_step
+ *
+ * Conventions
+ *   - Grids: origin x0[3], extent L[3], fine cells fine_n[3], integer
+ *     coarsening ratio r, bulk cells n_b = fine_n / r, bulk spacing
+ *     H = L / n_b.  Linear cell index i + n_x (j + n_y k), x fastest.
+ *   - "T" below is float for CG_FP32 and double for CG_FP64.
+ *   - Particle arrays are AoS of 4: pos_d[n] = (x, y, z, diameter),
+ *     vel[n] = (u, v, w, unused).  Field arrays are SoA: [ncomp][cells].
+ *     Per-particle outputs are in the caller's particle order.
+ *   - Every pointer passed to a compute call is DEVICE memory owned by the
+ *     caller (cg_step_host excepted), 16-byte aligned for T = float and
+ *     32-byte aligned for T = double.  The library never frees them.
+ *   - Every compute call is enqueued on the handle's CUDA stream and
+ *     returns without synchronising.  Argument errors are reported
+ *     synchronously by the return code and nothing is enqueued.
+ *     Conditions found on the device (points outside the domain,
+ *     non-finite inputs, porosity clamped for the drag law) are counted in
+ *     a device status word read by cg_sync_status.
+ *   - No call throws or aborts; no call allocates device memory once the
+ *     handle's buffers fit the particle count (cg_step can then be captured
+ *     in a CUDA graph).
+ */
+#ifndef CG_H
+#define CG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CG_OK = 0,
+    CG_ERR_INVALID_ARG = 1,   /* bad argument; nothing was enqueued          */
+    CG_ERR_CUDA = 2,          /* a CUDA runtime call failed                  */
+    CG_ERR_OOM = 3,           /* device allocation failed                    */
+    CG_ERR_NOT_BINNED = 4,    /* needs cg_bin_particles with the same n first */
+    CG_ERR_OUT_OF_RANGE = 5,  /* size beyond a documented limit              */
+    CG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up          */
+    CG_ERR_NONFINITE = 7      /* non-finite input seen on the device         */
+} cg_status;
+
+typedef enum { CG_FP32 = 0, CG_FP64 = 1 } cg_precision;
+typedef enum { CG_DRAG_DI_FELICE = 0, CG_DRAG_ERGUN_WEN_YU = 1 } cg_drag_law;
+typedef enum { CG_INTERP_TRILINEAR = 0, CG_INTERP_CELL = 1 } cg_interp;
+typedef enum { CG_DEP_VOLUME = 0, CG_DEP_MOMENTUM = 1 } cg_deposit_kind;
+
+/* Status-word bits (cg_sync_status). */
+enum {
+    CG_FLAG_OUTSIDE = 1u,      /* a particle outside the domain was clamped  */
+    CG_FLAG_NONFINITE = 2u,    /* a NaN/Inf position was seen                */
+    CG_FLAG_EPS_CLAMPED = 4u,  /* porosity < eps_min was raised for the drag */
+    CG_FLAG_TIMEOUT = 8u       /* a bounded device wait gave up              */
+};
+
+/* Number of entries of the conservation-sum vector written by cg_step. */
+#define CG_NSUMS 16
+
+/* Problem description.  Sec. 2.1 (two grids, the bulk one coarse and
+ * uniform), Eq. (DragLaw) (beta depends on slip, rho_f, rho_p, d_p, A_p,
+ * mu_f and porosity), Eq. (DEM_EQUATIONS) (gravity).
+ *   eps_switch  Ergun -> Wen-Yu switch porosity (eps >= eps_switch is Wen-Yu), in (0, 1]
+ *   eps_min     porosity seen by the drag law is max(eps, eps_min), in [0, 1)
+ * Limits: fine_n[a] % ratio == 0, bulk cells >= 2 per axis, at most 2^22
+ * bulk cells and 2^31 - 1 fine cells. */
+typedef struct {
+    double origin[3];
+    double extent[3];
+    int32_t fine_n[3];
+    int32_t ratio;
+    int32_t prec;        /* cg_precision */
+    int32_t law;         /* cg_drag_law  */
+    int32_t interp;      /* cg_interp    */
+    int32_t reserved0;
+    double rho_f, mu_f, rho_p;
+    double eps_switch;
+    double eps_min;
+    double gravity[3];
+} cg_grid_desc;
+
+typedef struct cg_grids cg_grids;   /* opaque handle: bins, scratch, status */
+typedef struct cg_mlp cg_mlp;       /* opaque learned drag closure          */
+
+typedef struct {
+    int64_t n;       /* number of particles, 0 <= n <= 2^31 - 1 */
+    void* pos_d;     /* [n] T4: x, y, z, d (advanced in place when dt > 0) */
+    void* vel;       /* [n] T4: u, v, w, -  (advanced in place when dt > 0) */
+} cg_particles;
+
+typedef struct {
+    double* eps_bulk;      /* [n_b] porosity (always double)          required */
+    void* u_bulk;          /* [3][n_b] T averaged fluid velocity        required */
+    void* var_bulk;        /* [n_b] T sub-bulk velocity variance        nullable */
+    void* S_bulk;          /* [3][n_b] T bulk momentum source           required */
+    void* force;           /* [3][n] T drag force per particle          required */
+    void* S_fine;          /* [3][n_f] T projected source               required */
+    void* eps_fine;        /* [n_f] T projected porosity                nullable */
+    double* sums;          /* [CG_NSUMS] device, conservation sums      nullable */
+    int32_t* cell;         /* [n] bulk cell per particle                nullable */
+    int32_t* perm;         /* [n] particles in cell order               nullable */
+    int32_t* cell_start;   /* [n_b + 1] segment starts                  nullable */
+} cg_step_out;
+
+/* Human-readable name of a status code (static storage). */
+const char* cg_status_string(cg_status s);
+
+/* Create the coupling handle for one pair of nested grids (Sec. 2.1,
+ * Fig. 1).  cuda_stream is a cudaStream_t (NULL = legacy default stream);
+ * the handle allocates its bulk-sized buffers on the current device.
+ * On error *out is set to NULL. */
+cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids** out);
+
+/* Free the handle and everything it owns (synchronises its stream). NULL is OK. */
+cg_status cg_destroy_grids(cg_grids* g);
+
+/* Change the stream later calls are enqueued on. */
+cg_status cg_set_stream(cg_grids* g, void* cuda_stream);
+
+/* Bulk cells per axis and total bulk / fine cell counts (host values). */
+cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, int64_t* n_fine);
+
+/* (a0) Bin particles by bulk cell: the per-step particle-cell connectivity
+ * of Sec. 2.2.  Cell of a point, per axis: clamp(floor((x - x0) / H), 0,
+ * n_b - 1) with the quotient taken in IEEE double (subtraction, then
+ * correctly rounded division); half-open cells, x = x0 + L in the last
+ * cell; points with quotient outside [0, n_b] are clamped and counted.
+ * Particles are sorted stably by cell: perm lists the particles of cell c
+ * at perm[cell_start[c] .. cell_start[c+1]) in increasing index order.
+ * pos_d: [n] T4.  Outputs (all nullable): cell_out[n], perm_out[n],
+ * cell_start_out[n_b + 1].  The handle keeps the binning for later
+ * cg_deposit / cg_drag calls with the same n. */
+cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
+                           int32_t* cell_out, int32_t* perm_out, int32_t* cell_start_out);
+
+/* (a1)/(a3) Deposit onto the bulk grid over the particles of each cell,
+ * summed in the stable order of the last cg_bin_particles.
+ *   CG_DEP_VOLUME:   per_particle = pos_d [n] T4 (diameter used);
+ *                    bulk_out = eps double [n_b], eps = 1 - sum(pi d^3/6) / V_B
+ *                    (Table 1 porosity field; Sec. 2.3 porosity definition).
+ *   CG_DEP_MOMENTUM: per_particle = force [3][n] T;
+ *                    bulk_out = S [3][n_b] T, S = -(1/V_B) sum F
+ *                    (Eq. UFP: F_fpi is the counterpart of F_drag).
+ * Returns CG_ERR_NOT_BINNED without a binning of this n. */
+cg_status cg_deposit(cg_grids* g, int32_t kind, int64_t n, const void* per_particle, void* bulk_out);
+
+/* (a2) Fine -> bulk transfer of the fluid solution (Fig. 1): mean of the
+ * r^3 nested fine cells per bulk cell for each velocity component, and
+ * optionally the variance of the velocity about that mean summed over the
+ * three components.  u_fine [3][n_f] T -> u_bulk [3][n_b] T,
+ * var_bulk [n_b] T (nullable). */
+cg_status cg_average_fine_to_bulk(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk);
+
+/* (a3) Drag on every particle, Eq. (DragLaw): F = beta (u_f - u_p), with
+ * porosity and fluid velocity interpolated at the particle from the bulk
+ * cell centres (trilinear, constant extrapolation in the outer half cell;
+ * or the cell value) and beta from the Di Felice or Ergun / Wen-Yu
+ * correlation.  pos_d, vel: [n] T4; eps_bulk: double [n_b]; u_bulk: [3][n_b] T;
+ * force_out: [3][n] T.  When S_bulk_out ([3][n_b] T) is not NULL the
+ * reaction S = -(1/V_B) sum F is deposited in the same pass (needs the
+ * binning of this n).  mlp must be NULL (plain correlation). */
+cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel,
+                  const double* eps_bulk, const void* u_bulk,
+                  void* force_out, void* S_bulk_out, const cg_mlp* mlp);
+
+/* (a4) Bulk -> fine transfer of particle-related fields (Fig. 1): each
+ * fine cell centre takes the interpolant of the bulk field with the
+ * particle stencil.  bulk [ncomp][n_b] T -> fine_out [ncomp][n_f] T,
+ * 1 <= ncomp <= 4.  Conserves sum S V exactly in real arithmetic. */
+cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, void* fine_out);
+
+/* One coupling step (a0..a4) on device memory: bin, porosity, fluid
+ * average, drag with fused reaction deposit, projection of the source
+ * (and of the porosity when out->eps_fine is set), conservation sums.
+ * With dt > 0 the particles are then advanced by semi-implicit Euler
+ * under drag and gravity, Eq. (DEM_EQUATIONS) without contacts:
+ * u += dt (F/m + g), x += dt u, m = rho_p pi d^3 / 6, specular walls.
+ * u_fine: [3][n_f] T.  sums (CG_NSUMS doubles): 0 sum V_p,
+ * 1 sum (1 - eps_B) V_B, 2..4 sum F_p, 5..7 sum S_B V_B, 8..10 sum S_f V_f,
+ * 11 sum |F_p|, 12..14 sum m_p u_p after the advance, 15 particles whose
+ * porosity was clamped. */
+cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
+                  const cg_step_out* out, double dt);
+
+/* cg_step on HOST buffers: copies the inputs to handle-owned device
+ * buffers, runs cg_step, copies every requested output back and waits for
+ * the stream.  Same layouts as cg_step with host pointers everywhere
+ * (page-locked memory recommended); p->pos_d / p->vel are advanced in
+ * place when dt > 0.  Allocates the device buffers on first use or growth. */
+cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine,
+                       const cg_step_out* out, double dt);
+
+/* Wait for the handle's stream and read-and-clear the device status word.
+ * flags (nullable) gets CG_FLAG_* bits; counts (nullable, 4 entries) gets
+ * particles outside, non-finite positions, clamped porosities, timeouts.
+ * Returns CG_ERR_NONFINITE / CG_ERR_TIMEOUT when those bits are set,
+ * CG_ERR_CUDA if the stream holds an error, else CG_OK. */
+cg_status cg_sync_status(cg_grids* g, uint32_t* flags, int64_t* counts);
+
+/* Number of CUDA kernels this handle has launched so far. */
+int64_t cg_launch_count(const cg_grids* g);
+
+/* Per-kernel device timing.  When enabled, every kernel launch of the
+ * handle is bracketed by CUDA events on its stream; cg_profile_read waits
+ * for the stream and returns, for kernel slot k (0 <= k < count), its name,
+ * launches and total milliseconds since the last reset.  Returns the
+ * number of slots in *count. */
+cg_status cg_profile_enable(cg_grids* g, int32_t on);
+cg_status cg_profile_reset(cg_grids* g);
+cg_status cg_profile_read(cg_grids* g, int32_t k, const char** name,
+                          int64_t* launches, double* total_ms, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
