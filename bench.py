@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the particle <-> dual-grid coupling step on GB300.
+
+Workload: the packed bed (1 x 1 x 2 m, fine 256 x 256 x 512, ratio 4 ->
+bulk 64 x 64 x 128, 4,000,000 spheres d = 4 mm, Ergun / Wen-Yu drag,
+FP32), seeded synthetic inputs resident in HBM.  One step is one call of
+cg_step: bin, porosity, fluid average, drag with the fused reaction
+deposit, projection of the source and of the porosity onto the fine grid,
+and the conservation sums.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the path does not shard): value is the
+total particle-steps of all ranks over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the same workload (rank 0
+only, a bounded number of full steps on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled particle-steps/s"
+UNIT = "particle-steps/s"
+
+# DRAM traffic per launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
+# source file is byte-identical to the one profiled (sha256 prefix).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="packed_bed", choices=["packed_bed", "small_packed_bed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples, kept with their timestamps."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self._t is not None:
+            self._t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.samples:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            rows.append((ts, parts))
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or \
+            sorted(rows, key=lambda r: abs(r[0] - (t0 + t1) / 2))[:3]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for _, p in inside if num(p[0]) is not None]
+        smax = [num(p[1]) for _, p in inside if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in inside for i in range(4) if p[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside),
+                "power_w_max": max((num(p[2]) or 0.0) for _, p in inside)}
+
+
+def algorithmic_bytes(g, n, eps_fine=True):
+    """Algorithmic bytes of one step and of the kernels, FP32 path.
+    Particles: read x, y, z, d (16), u_p (12), write F (12), bin key and
+    permutation written and read once (8).  Fine cells: read u_f (12), write
+    S_f (12) and eps_f (4).  Bulk cells: eps (8 w + 8 r), u_B (12 w + 12 r),
+    var (4), S_B (12 w + 12 r) rounded to 40 for the step."""
+    nf, nb = g.n_fine, g.n_bulk
+    per = {
+        "project": nf * (12 + (4 if eps_fine else 0)) + nb * (12 + (4 if eps_fine else 0)),
+        "average": nf * 12 + nb * 16,
+    }
+    step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
+    return step, per
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1807_11834_gb300 as cg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = getattr(synth, args.workload)(seed=rank)
+    g = cg.Grids(w.desc)
+    n = w.n
+    dev = torch.device("cuda", local)
+    pos = torch.from_numpy(w.pos_d).to(dev)
+    vel = torch.from_numpy(w.vel).to(dev)
+    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).to(dev)
+    out = g.alloc_outputs(n, var=True, eps_fine=True, device=dev)
+    input_bytes = pos.numel() * 4 + vel.numel() * 4 + uf.numel() * 4
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        g.cg_step(pos, vel, uf, out)
+    rc, flags, counts = g.cg_sync_status()
+    if rc != 0:
+        raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.35)
+    barrier()
+    l0 = g.cg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record()
+    for _ in range(args.steps):
+        g.cg_step(pos, vel, uf, out)
+    e1.record()
+    e1.synchronize()
+    t1 = time.time()
+    barrier()
+    launches = g.cg_launch_count() - l0
+    time.sleep(0.25)
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rc, flags, counts = g.cg_sync_status()
+    if rc != 0:
+        raise RuntimeError(f"timed status {rc}")
+
+    # per-kernel device time: a second pass of the same steps with the
+    # library's CUDA events around every launch (kept out of the timed pass)
+    prof_steps = min(args.steps, 200)
+    g.cg_profile_reset()
+    g.cg_profile_enable(True)
+    for _ in range(prof_steps):
+        g.cg_step(pos, vel, uf, out)
+    prof = g.cg_profile_read()
+    g.cg_profile_enable(False)
+
+    step_bytes, kern_bytes = algorithmic_bytes(g, n)
+    peak, peak_src = load_peaks()
+    kern_ms = {k: v[1] / v[0] for k, v in prof.items() if v[0]}
+    kern_total = {k: v[1] for k, v in prof.items()}
+    tot = sum(kern_total.values())
+    dominant = max(kern_total, key=kern_total.get)
+    launches_per_step = {k: v[0] / prof_steps for k, v in prof.items()}
+    dom_bytes = kern_bytes.get(dominant)
+    roofline = None
+    if dom_bytes is not None:
+        ach = dom_bytes / (kern_ms[dominant] * 1e-3) / 1e9
+        src = os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", "fine.cu")
+        tr = NCU_TRAFFIC.get(dominant)
+        traffic = tr["bytes"] if tr and tr["sha"] == file_sha(src) else None
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(ach, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
+                    "algorithmic_bytes": dom_bytes, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    ms_step = ms / args.steps
+    step_gbs = step_bytes / (ms_step * 1e-3) / 1e9
+    value = world * n * args.steps / (ms * 1e-3)
+    clocks = sampler.summary(t0, t1)
+
+    # end-to-end: host buffers through cg_step_host (H2D of the inputs and
+    # D2H of every output inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hpos = torch.from_numpy(w.pos_d.copy()).pin_memory()
+        hvel = torch.from_numpy(w.vel.copy()).pin_memory()
+        huf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).pin_memory()
+        hout = {k: (torch.empty(v.shape, dtype=v.dtype).pin_memory() if v is not None else None)
+                for k, v in out.items()}
+        for _ in range(2):
+            g.cg_step_host(hpos, hvel, huf, hout)
+        ke = max(3, min(args.steps, 30))
+        barrier()
+        ta = time.perf_counter()
+        for _ in range(ke):
+            g.cg_step_host(hpos, hvel, huf, hout)
+        tb = time.perf_counter()
+        te = tb - ta
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None)
+        e2e = {"value": world * n * ke / te, "unit": UNIT, "h2d_bytes_per_step": int(input_bytes),
+               "d2h_bytes_per_step": int(d2h), "steps": ke, "ms_per_step": 1e3 * te / ke,
+               "entry": "cg_step_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ks = max(1, args.cpu_steps)
+        ta = time.perf_counter()
+        for _ in range(ks):
+            oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+        tc = time.perf_counter() - ta
+        cpu = {"value": n * ks / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ks} full oracle steps of the same packed bed (FP64 C, single thread), {tc:.1f} s"}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: 1x1x2 box, fine {'x'.join(map(str, w.desc['fine_n']))}, "
+                                   f"ratio {w.desc['ratio']}, {n} spheres, Ergun/Wen-Yu, FP32",
+                       "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs {input_bytes / 1e6:.0f} MB > L2 (126 MB) per step, no flush",
+                       "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
+                       "step_frac_of_hbm": round(step_gbs / peak, 4)},
+            "roofline": roofline,
+            "kernels": {k: {"ms_per_launch": round(kern_ms[k], 5), "share": round(kern_total[k] / tot, 4),
+                            "launches_per_step": launches_per_step[k]} for k in sorted(kern_total)},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    oracle.build()
+    w = getattr(synth, args.workload)(seed=0)
+    n = w.n
+    wu = min(max(0, args.warmup), 1)
+    ks = max(1, min(args.steps, 8))
+    for _ in range(wu):
+        oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    ta = time.perf_counter()
+    for _ in range(ks):
+        oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    tc = time.perf_counter() - ta
+    value = n * ks / tc
+    sample = f"{ks} full oracle steps (warm-up {wu}) of the packed bed, FP64 C, single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": ks, "warmup": wu, "ms_per_step": 1e3 * tc / ks, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: 1x1x2 box, fine {'x'.join(map(str, w.desc['fine_n']))}, "
+                                   f"ratio {w.desc['ratio']}, {n} spheres, Ergun/Wen-Yu",
+                       "particles": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,7 @@ def _load():
                 "or_drag_beta": (d, [pg, d, d, pd, P(C.c_int)]),
                 "or_drag": (i64, [pg, i64, pd, pd, pd, pd, pd]),
                 "or_deposit_momentum": (None, [pg, i64, pd, pi, pi, pd]),
+                "or_particle_state": (None, [pg, i64, pd, pd, pd, pd, pd, pd]),
                 "or_project": (None, [pg, C.c_int, pd, pd]),
                 "or_euler": (None, [pg, i64, pd, pd, pd, d]),
                 "or_step": (i64, [pg, i64, pd, pd, pd, d, pi, pi, pi, pd, pd, pd, pd, pd, pd, pd, pd]),
@@ -222,6 +223,18 @@ def drag(desc, pos_d, vel, eps_bulk, u_bulk):
     u = _f64(u_bulk)
     ncl = lib.or_drag(C.byref(g), n, _pd(pos), _pd(v), _pd(e), _pd(u), _pd(F))
     return F, int(ncl)
+
+
+def particle_state(desc, pos_d, vel, eps_bulk, u_bulk):
+    """(eps_p[n], |slip|[n]) as seen by each particle's drag law."""
+    lib = _load()
+    g = grid(desc)
+    pos = _f64(pos_d).reshape(-1, 4)
+    v = _f64(vel).reshape(-1, 4)
+    n = pos.shape[0]
+    e, s = np.zeros(n), np.zeros(n)
+    lib.or_particle_state(C.byref(g), n, _pd(pos), _pd(v), _pd(_f64(eps_bulk)), _pd(_f64(u_bulk)), _pd(e), _pd(s))
+    return e, s
 
 
 def deposit_momentum(desc, force, cell_start, perm):

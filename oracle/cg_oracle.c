@@ -324,6 +324,23 @@ int64_t or_drag(const or_grid* G, int64_t n, const double* pos_d, const double* 
     return nclamped;
 }
 
+void or_particle_state(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                       const double* eps_bulk, const double* u_bulk, double* eps_p, double* slip)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        const double* x = &pos_d[4 * p];
+        double uf[3];
+        or_gather(G, eps_bulk, 1, x, &eps_p[p]);
+        or_gather(G, u_bulk, 3, x, uf);
+        double s2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double s = uf[a] - vel[4 * p + a];
+            s2 += s * s;
+        }
+        slip[p] = sqrt(s2);
+    }
+}
+
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk)
 {

@@ -79,6 +79,11 @@ double or_drag_beta(const or_grid* G, double eps, double d, const double s[3], i
 int64_t or_drag(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
                 const double* eps_bulk, const double* u_bulk, double* force);
 
+/* Porosity and slip magnitude seen by each particle's drag law, before
+ * the eps_min clamp (used by tests to locate correlation branch points). */
+void or_particle_state(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                       const double* eps_bulk, const double* u_bulk, double* eps_p, double* slip);
+
 /* S_B = -(1/V_B) sum_{p in B} F_p  (per component). */
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk);

@@ -1,0 +1,305 @@
+"""Python binding of the GB300 particle <-> dual-grid coupling library.
+
+A thin ctypes layer over the C ABI of ``include/cg.h``.  It marshals torch
+CUDA tensors (``data_ptr()``) and the current CUDA stream, and checks
+shapes and dtypes; every step of the coupling runs in the library's own
+CUDA kernels.  There is no CPU fallback: if the shared library has not
+been built, importing the binding succeeds but the first call raises.
+
+The step follows Fig. 1 and Sec. 2 of Pozzetti et al., "A parallel
+dual-grid multiscale approach to CFD-DEM couplings" (arXiv 1807.11834):
+particles are binned on the coarse bulk grid, porosity and the reaction
+source are deposited there, the fluid velocity is averaged from the fine
+grid, drag is computed at the particles (Eq. DragLaw), and the source is
+projected back to the fine grid.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcg.so")
+
+CG_OK = 0
+STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_INVALID_ARG", 2: "CG_ERR_CUDA", 3: "CG_ERR_OOM",
+                4: "CG_ERR_NOT_BINNED", 5: "CG_ERR_OUT_OF_RANGE", 6: "CG_ERR_TIMEOUT",
+                7: "CG_ERR_NONFINITE"}
+CG_FP32, CG_FP64 = 0, 1
+CG_DRAG_DI_FELICE, CG_DRAG_ERGUN_WEN_YU = 0, 1
+CG_INTERP_TRILINEAR, CG_INTERP_CELL = 0, 1
+CG_DEP_VOLUME, CG_DEP_MOMENTUM = 0, 1
+CG_FLAG_OUTSIDE, CG_FLAG_NONFINITE, CG_FLAG_EPS_CLAMPED, CG_FLAG_TIMEOUT = 1, 2, 4, 8
+CG_NSUMS = 16
+SUM_NAMES = ["vol_particles", "vol_deposited", "F_x", "F_y", "F_z", "SbVb_x", "SbVb_y", "SbVb_z",
+             "SfVf_x", "SfVf_y", "SfVf_z", "F_abs", "mom_x", "mom_y", "mom_z", "n_clamped"]
+
+
+class CgError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}")
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("extent", C.c_double * 3), ("fine_n", C.c_int32 * 3),
+                ("ratio", C.c_int32), ("prec", C.c_int32), ("law", C.c_int32), ("interp", C.c_int32),
+                ("reserved0", C.c_int32), ("rho_f", C.c_double), ("mu_f", C.c_double),
+                ("rho_p", C.c_double), ("eps_switch", C.c_double), ("eps_min", C.c_double),
+                ("gravity", C.c_double * 3)]
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("pos_d", C.c_void_p), ("vel", C.c_void_p)]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("eps_bulk", C.c_void_p), ("u_bulk", C.c_void_p), ("var_bulk", C.c_void_p),
+                ("S_bulk", C.c_void_p), ("force", C.c_void_p), ("S_fine", C.c_void_p),
+                ("eps_fine", C.c_void_p), ("sums", C.c_void_p), ("cell", C.c_void_p),
+                ("perm", C.c_void_p), ("cell_start", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "cg_status_string": (C.c_char_p, [C.c_int]),
+    "cg_create_grids": (C.c_int, [C.POINTER(GridDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cg_destroy_grids": (C.c_int, [C.c_void_p]),
+    "cg_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "cg_grid_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "cg_bin_particles": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_deposit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]),
+    "cg_average_fine_to_bulk": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_drag": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_project_bulk_to_fine": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "cg_step": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
+    "cg_step_host": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
+    "cg_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int64)]),
+    "cg_launch_count": (C.c_int64, [C.c_void_p]),
+    "cg_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cg_profile_reset": (C.c_int, [C.c_void_p]),
+    "cg_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+}
+
+
+def lib():
+    """The loaded shared library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA coupling library not built ({LIB_PATH}); "
+                                   "run __graft_entry__.build() first")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != CG_OK:
+        raise CgError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_desc(d: dict) -> GridDesc:
+    g = GridDesc()
+    g.origin[:] = d["origin"]
+    g.extent[:] = d["extent"]
+    g.fine_n[:] = d["fine_n"]
+    g.ratio = d["ratio"]
+    g.prec = CG_FP64 if d.get("fp64", False) else CG_FP32
+    g.law = d["law"]
+    g.interp = d.get("interp", CG_INTERP_TRILINEAR)
+    g.rho_f, g.mu_f, g.rho_p = d["rho_f"], d["mu_f"], d["rho_p"]
+    g.eps_switch, g.eps_min = d["eps_switch"], d["eps_min"]
+    g.gravity[:] = d.get("gravity", (0.0, 0.0, 0.0))
+    return g
+
+
+class Grids:
+    """Owner of a ``cg_grids`` handle (one coupling instance on cuda:0).
+
+    All tensors passed in must be contiguous CUDA tensors of the path
+    dtype (float32 or float64; the bulk porosity is always float64)."""
+
+    def __init__(self, desc: dict, stream=None):
+        import torch
+        self.desc = dict(desc)
+        self.dtype = torch.float64 if desc.get("fp64", False) else torch.float32
+        self._d = make_desc(desc)
+        h = C.c_void_p()
+        _check(lib().cg_create_grids(C.byref(self._d), _stream_handle(stream), C.byref(h)), "cg_create_grids")
+        self.h = h
+        nb = (C.c_int32 * 3)()
+        nbulk, nfine = C.c_int64(), C.c_int64()
+        _check(lib().cg_grid_dims(self.h, nb, C.byref(nbulk), C.byref(nfine)), "cg_grid_dims")
+        self.bulk_n = tuple(nb)
+        self.n_bulk = nbulk.value
+        self.n_fine = nfine.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cg_destroy_grids(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- argument checks (marshalling only) ---------------------------------
+    def _t(self, t, shape, dtype=None, name="tensor"):
+        if t is None:
+            return None
+        dtype = dtype or self.dtype
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+            raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor")
+        if shape is not None and t.numel() != int(shape):
+            raise ValueError(f"{name}: need {shape} elements, got {t.numel()}")
+        return t
+
+    def set_stream(self, stream=None):
+        _check(lib().cg_set_stream(self.h, _stream_handle(stream)), "cg_set_stream")
+
+    # -- the C ABI, one method per entry -----------------------------------
+    def cg_bin_particles(self, pos_d, cell=None, perm=None, cell_start=None):
+        import torch
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(cell, n, torch.int32, "cell")
+        self._t(perm, n, torch.int32, "perm")
+        self._t(cell_start, self.n_bulk + 1, torch.int32, "cell_start")
+        _check(lib().cg_bin_particles(self.h, n, _ptr(pos_d), _ptr(cell), _ptr(perm), _ptr(cell_start)),
+               "cg_bin_particles")
+
+    def cg_deposit(self, kind, n, per_particle, bulk_out):
+        import torch
+        if kind == CG_DEP_VOLUME:
+            self._t(per_particle, 4 * n, name="pos_d")
+            self._t(bulk_out, self.n_bulk, torch.float64, "eps_bulk")
+        else:
+            self._t(per_particle, 3 * n, name="force")
+            self._t(bulk_out, 3 * self.n_bulk, name="S_bulk")
+        _check(lib().cg_deposit(self.h, kind, n, _ptr(per_particle), _ptr(bulk_out)), "cg_deposit")
+
+    def cg_average_fine_to_bulk(self, u_fine, u_bulk, var_bulk=None):
+        self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        self._t(u_bulk, 3 * self.n_bulk, name="u_bulk")
+        self._t(var_bulk, self.n_bulk, name="var_bulk")
+        _check(lib().cg_average_fine_to_bulk(self.h, _ptr(u_fine), _ptr(u_bulk), _ptr(var_bulk)),
+               "cg_average_fine_to_bulk")
+
+    def cg_drag(self, pos_d, vel, eps_bulk, u_bulk, force, S_bulk=None):
+        import torch
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(vel, 4 * n, name="vel")
+        self._t(eps_bulk, self.n_bulk, torch.float64, "eps_bulk")
+        self._t(u_bulk, 3 * self.n_bulk, name="u_bulk")
+        self._t(force, 3 * n, name="force")
+        self._t(S_bulk, 3 * self.n_bulk, name="S_bulk")
+        _check(lib().cg_drag(self.h, n, _ptr(pos_d), _ptr(vel), _ptr(eps_bulk), _ptr(u_bulk), _ptr(force),
+                             _ptr(S_bulk), None), "cg_drag")
+
+    def cg_project_bulk_to_fine(self, bulk, fine_out):
+        ncomp = bulk.numel() // self.n_bulk
+        self._t(bulk, ncomp * self.n_bulk, name="bulk")
+        self._t(fine_out, ncomp * self.n_fine, name="fine_out")
+        _check(lib().cg_project_bulk_to_fine(self.h, ncomp, _ptr(bulk), _ptr(fine_out)),
+               "cg_project_bulk_to_fine")
+
+    def alloc_outputs(self, n, var=True, eps_fine=False, bins=False, device="cuda"):
+        """Output tensors of one step (device), by cg_step_out field name."""
+        import torch
+        kw = dict(device=device, dtype=self.dtype)
+        o = dict(eps_bulk=torch.empty(self.n_bulk, device=device, dtype=torch.float64),
+                 u_bulk=torch.empty(3, self.n_bulk, **kw),
+                 var_bulk=torch.empty(self.n_bulk, **kw) if var else None,
+                 S_bulk=torch.empty(3, self.n_bulk, **kw),
+                 force=torch.empty(3, n, **kw),
+                 S_fine=torch.empty(3, self.n_fine, **kw),
+                 eps_fine=torch.empty(self.n_fine, **kw) if eps_fine else None,
+                 sums=torch.empty(CG_NSUMS, device=device, dtype=torch.float64))
+        if bins:
+            o["cell"] = torch.empty(n, device=device, dtype=torch.int32)
+            o["perm"] = torch.empty(n, device=device, dtype=torch.int32)
+            o["cell_start"] = torch.empty(self.n_bulk + 1, device=device, dtype=torch.int32)
+        return o
+
+    @staticmethod
+    def _out_struct(out):
+        so = StepOut()
+        for name, _ in StepOut._fields_:
+            t = out.get(name)
+            setattr(so, name, None if t is None else t.data_ptr())
+        return so
+
+    def cg_step(self, pos_d, vel, u_fine, out, dt=0.0):
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(vel, 4 * n, name="vel")
+        self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
+        so = self._out_struct(out)
+        _check(lib().cg_step(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step")
+
+    def cg_step_host(self, pos_d, vel, u_fine, out, dt=0.0):
+        """Same as cg_step on host (CPU, ideally pinned) tensors; blocks."""
+        n = pos_d.shape[0]
+        for t in [pos_d, vel, u_fine] + [v for v in out.values() if v is not None]:
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("cg_step_host needs contiguous host tensors")
+        p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
+        so = self._out_struct(out)
+        _check(lib().cg_step_host(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step_host")
+
+    def cg_sync_status(self):
+        """(return code, flags, [outside, nonfinite, clamped, timeouts])."""
+        flags = C.c_uint32()
+        counts = (C.c_int64 * 4)()
+        rc = lib().cg_sync_status(self.h, C.byref(flags), counts)
+        return rc, flags.value, list(counts)
+
+    def cg_launch_count(self):
+        return int(lib().cg_launch_count(self.h))
+
+    def cg_profile_enable(self, on=True):
+        _check(lib().cg_profile_enable(self.h, 1 if on else 0), "cg_profile_enable")
+
+    def cg_profile_reset(self):
+        _check(lib().cg_profile_reset(self.h), "cg_profile_reset")
+
+    def cg_profile_read(self):
+        """{kernel name: (launches, total ms)} since the last reset."""
+        count = C.c_int32()
+        _check(lib().cg_profile_read(self.h, -1, None, None, None, C.byref(count)), "cg_profile_read")
+        res = {}
+        for k in range(count.value):
+            name, launches, ms = C.c_char_p(), C.c_int64(), C.c_double()
+            _check(lib().cg_profile_read(self.h, k, C.byref(name), C.byref(launches), C.byref(ms), None),
+                   "cg_profile_read")
+            res[name.value.decode()] = (launches.value, ms.value)
+        return res
+
+
+def status_string(code: int) -> str:
+    return lib().cg_status_string(code).decode()

@@ -1,0 +1,568 @@
+// api.cu -- the C ABI of include/cg.h: argument checks, handle and buffer
+// management, and the orchestration of the coupling step on one stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "cg_internal.cuh"
+
+using namespace cg;
+
+namespace {
+
+bool finite3(const double* v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename P>
+cg_status dalloc(P** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA;
+    }
+    *p = (P*)q;
+    return CG_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+cg_status ensure_buf(DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return CG_OK;
+    dfree(b.p);
+    b.bytes = 0;
+    CG_TRY(dalloc(&b.p, bytes));
+    b.bytes = bytes;
+    return CG_OK;
+}
+
+void split_ff(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+int ceil_log2(long long v) {
+    int b = 0;
+    while ((1LL << b) < v) ++b;
+    return b;
+}
+
+cg_status check_handle(const cg_grids* g) { return g ? CG_OK : CG_ERR_INVALID_ARG; }
+
+}  // namespace
+
+namespace cg {
+
+// ---------------------------------------------------------------------------
+// Profiling plumbing
+// ---------------------------------------------------------------------------
+int prof_slot(cg_grids* g, const char* name) {
+    for (size_t i = 0; i < g->slots.size(); ++i)
+        if (g->slots[i].name == name) return (int)i;
+    ProfSlot s;
+    s.name = name;
+    g->slots.push_back(s);
+    return (int)g->slots.size() - 1;
+}
+
+static void prof_drain(cg_grids* g) {
+    if (g->pending.empty()) return;
+    cudaStreamSynchronize(g->stream);
+    for (const PendingEv& pe : g->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->ev_pool[2 * pe.ev], g->ev_pool[2 * pe.ev + 1]) == cudaSuccess) {
+            g->slots[pe.slot].total_ms += ms;
+            g->slots[pe.slot].launches += 1;
+        }
+    }
+    cudaGetLastError();
+    g->pending.clear();
+    g->ev_used = 0;
+}
+
+void prof_begin(cg_grids* g, int slot, int* ev) {
+    (void)slot;
+    if (g->ev_used >= 4096) prof_drain(g);
+    if (2 * (size_t)g->ev_used + 1 >= g->ev_pool.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            cudaGetLastError();
+            *ev = -1;
+            return;
+        }
+        g->ev_pool.push_back(a);
+        g->ev_pool.push_back(b);
+    }
+    *ev = g->ev_used++;
+    cudaEventRecord(g->ev_pool[2 * *ev], g->stream);
+}
+
+void prof_end(cg_grids* g, int slot, int ev) {
+    if (ev < 0) return;
+    cudaEventRecord(g->ev_pool[2 * ev + 1], g->stream);
+    g->pending.push_back({slot, ev});
+}
+
+// ---------------------------------------------------------------------------
+// Buffers that grow with the particle count
+// ---------------------------------------------------------------------------
+cg_status ensure_partials(cg_grids* g, long long n) {
+    const long long bulk_blk = (g->gd.nbulk + 255) / 256;
+    const long long fine_blk = (g->gd.nfine + 255) / 256;
+    const long long drag_blk = std::max(1LL, (n + 255) / 256);
+    const long long proj_blk = (g->gd.r == 2 || g->gd.r == 4 || g->gd.r == 8) ? bulk_blk : fine_blk;
+    const long long need = bulk_blk * 1 + drag_blk * kDragSums + bulk_blk * 3 + proj_blk * 3;
+    if (need > g->part_cap) {
+        dfree(g->partials);
+        CG_TRY(dalloc(&g->partials, sizeof(double) * need));
+        g->part_cap = need;
+    }
+    g->part_off[PS_VOL] = 0;
+    g->part_off[PS_MOM] = bulk_blk;
+    g->part_off[PS_PROJ] = bulk_blk * 4;
+    g->part_off[PS_DRAG] = bulk_blk * 4 + proj_blk * 3;
+    return CG_OK;
+}
+
+cg_status ensure_particle_capacity(cg_grids* g, long long n) {
+    CG_TRY(ensure_partials(g, n));
+    if (n <= g->cap) return CG_OK;
+    const long long cap = ((n + kSortTile - 1) / kSortTile) * kSortTile;
+    dfree(g->key);
+    dfree(g->key1);
+    dfree(g->val1);
+    dfree(g->perm);
+    dfree(g->inv_perm);
+    dfree(g->Fs);
+    dfree(g->hist);
+    dfree(g->scan_part);
+    g->cap = -1;
+    g->n_binned = -1;
+    CG_TRY(dalloc(&g->key, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->key1, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->val1, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->perm, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->inv_perm, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->Fs, 4 * g->tsize * cap));
+    const long long ntiles = cap / kSortTile;
+    const int maxbits = std::max(g->pass_bits[0], g->pass_bits[1]);
+    g->hist_cap = ntiles << maxbits;
+    CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
+    const long long scan_m = std::max(g->hist_cap, g->gd.nbulk + 1);
+    g->scan_cap = (scan_m + kScanItems - 1) / kScanItems;
+    CG_TRY(dalloc(&g->scan_part, sizeof(int32_t) * g->scan_cap));
+    g->cap = cap;
+    return CG_OK;
+}
+
+}  // namespace cg
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* cg_status_string(cg_status s) {
+    switch (s) {
+        case CG_OK: return "ok";
+        case CG_ERR_INVALID_ARG: return "invalid argument";
+        case CG_ERR_CUDA: return "CUDA runtime error";
+        case CG_ERR_OOM: return "device out of memory";
+        case CG_ERR_NOT_BINNED: return "particles not binned for this count";
+        case CG_ERR_OUT_OF_RANGE: return "size beyond a documented limit";
+        case CG_ERR_TIMEOUT: return "bounded device wait gave up";
+        case CG_ERR_NONFINITE: return "non-finite input";
+    }
+    return "unknown status";
+}
+
+static void free_all(cg_grids* g) {
+    dfree(g->key);
+    dfree(g->key1);
+    dfree(g->val1);
+    dfree(g->perm);
+    dfree(g->inv_perm);
+    dfree(g->Fs);
+    dfree(g->hist);
+    dfree(g->scan_part);
+    dfree(g->cell_start);
+    dfree(g->bulk4);
+    dfree(g->eps_t);
+    dfree(g->partials);
+    dfree(g->sums_scratch);
+    dfree(g->status);
+    DevBuf* st[] = {&g->st_pos, &g->st_vel, &g->st_ufine, &g->st_eps, &g->st_ub, &g->st_var, &g->st_Sb,
+                    &g->st_F,   &g->st_Sf,  &g->st_epsf,  &g->st_sums, &g->st_cell, &g->st_perm, &g->st_cs};
+    for (DevBuf* b : st) {
+        dfree(b->p);
+        b->bytes = 0;
+    }
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    g->ev_pool.clear();
+}
+
+cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids** out) {
+    if (!out) return CG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc) return CG_ERR_INVALID_ARG;
+    const cg_grid_desc& d = *desc;
+    if (!finite3(d.origin) || !finite3(d.extent) || !finite3(d.gravity)) return CG_ERR_INVALID_ARG;
+    if (d.ratio < 1) return CG_ERR_INVALID_ARG;
+    long long nbulk = 1, nfine = 1;
+    int nb[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(d.extent[a] > 0.0) || d.fine_n[a] < 1 || d.fine_n[a] % d.ratio != 0) return CG_ERR_INVALID_ARG;
+        nb[a] = d.fine_n[a] / d.ratio;
+        if (nb[a] < 2) return CG_ERR_INVALID_ARG;
+        nbulk *= nb[a];
+        nfine *= d.fine_n[a];
+    }
+    if (d.prec != CG_FP32 && d.prec != CG_FP64) return CG_ERR_INVALID_ARG;
+    if (d.law != CG_DRAG_DI_FELICE && d.law != CG_DRAG_ERGUN_WEN_YU) return CG_ERR_INVALID_ARG;
+    if (d.interp != CG_INTERP_TRILINEAR && d.interp != CG_INTERP_CELL) return CG_ERR_INVALID_ARG;
+    if (!(d.rho_f > 0.0) || !(d.mu_f > 0.0) || !(d.rho_p > 0.0) || !isfinite(d.rho_f) || !isfinite(d.mu_f) ||
+        !isfinite(d.rho_p))
+        return CG_ERR_INVALID_ARG;
+    if (!(d.eps_switch > 0.0 && d.eps_switch <= 1.0)) return CG_ERR_INVALID_ARG;
+    if (!(d.eps_min >= 0.0 && d.eps_min < 1.0)) return CG_ERR_INVALID_ARG;
+    if (nbulk > (1LL << kMaxBulkBits) || nfine > 2147483647LL) return CG_ERR_OUT_OF_RANGE;
+
+    cg_grids* g = new (std::nothrow) cg_grids();
+    if (!g) return CG_ERR_OOM;
+    g->desc = d;
+    g->fp64 = d.prec == CG_FP64;
+    g->tsize = g->fp64 ? 8 : 4;
+    g->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return CG_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+
+    GridDev& gd = g->gd;
+    memset(&gd, 0, sizeof gd);
+    gd.r = d.ratio;
+    gd.nbulk = nbulk;
+    gd.nfine = nfine;
+    double h[3];
+    for (int a = 0; a < 3; ++a) {
+        gd.nb[a] = nb[a];
+        gd.nf[a] = d.fine_n[a];
+        gd.x0[a] = d.origin[a];
+        gd.xhi[a] = d.origin[a] + d.extent[a];
+        gd.H[a] = d.extent[a] / (double)nb[a];
+        h[a] = d.extent[a] / (double)d.fine_n[a];
+        gd.invH[a] = 1.0 / gd.H[a];
+        gd.x0f[a] = (float)d.origin[a];
+        gd.invHf[a] = (float)gd.invH[a];
+        gd.ax0f[a] = (float)fabs(d.origin[a] * gd.invH[a]);
+        split_ff(d.origin[a], gd.x0h[a], gd.x0l[a]);
+        split_ff(gd.invH[a], gd.ihh[a], gd.ihl[a]);
+    }
+    gd.VB = gd.H[0] * gd.H[1] * gd.H[2];
+    gd.invVB = 1.0 / gd.VB;
+    gd.Vf = h[0] * h[1] * h[2];
+    gd.invVBf = (float)gd.invVB;
+    gd.VBf = (float)gd.VB;
+    gd.Vff = (float)gd.Vf;
+    split_ff(gd.VB, gd.VBh, gd.VBl);
+    split_ff(gd.Vf, gd.Vfh, gd.Vfl);
+    gd.law = d.law;
+    gd.interp = d.interp;
+    gd.rho_f = d.rho_f;
+    gd.mu_f = d.mu_f;
+    gd.rho_p = d.rho_p;
+    gd.eps_switch = d.eps_switch;
+    gd.eps_min = d.eps_min;
+    for (int a = 0; a < 3; ++a) gd.g[a] = d.gravity[a];
+
+    g->bulk_bits = std::max(1, ceil_log2(nbulk));
+    if (g->bulk_bits <= kMaxDigitBits) {
+        g->npasses = 1;
+        g->pass_bits[0] = g->bulk_bits;
+        g->pass_bits[1] = 0;
+    } else {
+        g->npasses = 2;
+        g->pass_bits[0] = (g->bulk_bits + 1) / 2;
+        g->pass_bits[1] = g->bulk_bits - g->pass_bits[0];
+    }
+
+    cg_status st = CG_OK;
+    if (st == CG_OK) st = dalloc(&g->cell_start, sizeof(int32_t) * (nbulk + 1));
+    if (st == CG_OK) st = dalloc(&g->bulk4, 4 * g->tsize * nbulk);
+    if (st == CG_OK) st = dalloc(&g->eps_t, g->tsize * nbulk);
+    if (st == CG_OK) st = dalloc(&g->sums_scratch, sizeof(double) * CG_NSUMS);
+    if (st == CG_OK) st = dalloc(&g->status, sizeof(unsigned long long) * kNumSlots);
+    if (st == CG_OK && cudaMemset(g->status, 0, sizeof(unsigned long long) * kNumSlots) != cudaSuccess)
+        st = CG_ERR_CUDA;
+    if (st == CG_OK) st = ensure_particle_capacity(g, 1);
+    if (st != CG_OK) {
+        free_all(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return CG_OK;
+}
+
+cg_status cg_destroy_grids(cg_grids* g) {
+    if (!g) return CG_OK;
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    free_all(g);
+    delete g;
+    return CG_OK;
+}
+
+cg_status cg_set_stream(cg_grids* g, void* cuda_stream) {
+    CG_TRY(check_handle(g));
+    g->stream = (cudaStream_t)cuda_stream;
+    return CG_OK;
+}
+
+cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, int64_t* n_fine) {
+    CG_TRY(check_handle(g));
+    if (bulk_n)
+        for (int a = 0; a < 3; ++a) bulk_n[a] = g->gd.nb[a];
+    if (n_bulk) *n_bulk = g->gd.nbulk;
+    if (n_fine) *n_fine = g->gd.nfine;
+    return CG_OK;
+}
+
+static cg_status check_n(long long n) { return (n < 0 || n > 2147483647LL) ? CG_ERR_OUT_OF_RANGE : CG_OK; }
+
+static cg_status copy_bins(cg_grids* g, long long n, int32_t* cell_out, int32_t* perm_out, int32_t* cs_out) {
+    if (cell_out && n)
+        CG_CUDA(cudaMemcpyAsync(cell_out, g->key, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, g->stream));
+    if (perm_out && n)
+        CG_CUDA(cudaMemcpyAsync(perm_out, g->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, g->stream));
+    if (cs_out)
+        CG_CUDA(cudaMemcpyAsync(cs_out, g->cell_start, sizeof(int32_t) * (g->gd.nbulk + 1),
+                                cudaMemcpyDeviceToDevice, g->stream));
+    return CG_OK;
+}
+
+cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d, int32_t* cell_out, int32_t* perm_out,
+                           int32_t* cell_start_out) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_n(n));
+    if (n > 0 && (!pos_d || !aligned16(pos_d))) return CG_ERR_INVALID_ARG;
+    CG_TRY(ensure_particle_capacity(g, n));
+    CG_TRY(launch_bin(g, n, pos_d));
+    return copy_bins(g, n, cell_out, perm_out, cell_start_out);
+}
+
+cg_status cg_deposit(cg_grids* g, int32_t kind, int64_t n, const void* per_particle, void* bulk_out) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_n(n));
+    if (kind != CG_DEP_VOLUME && kind != CG_DEP_MOMENTUM) return CG_ERR_INVALID_ARG;
+    if (!bulk_out || (n > 0 && !per_particle)) return CG_ERR_INVALID_ARG;
+    if (kind == CG_DEP_VOLUME && n > 0 && !aligned16(per_particle)) return CG_ERR_INVALID_ARG;
+    if (g->n_binned != n) return CG_ERR_NOT_BINNED;
+    if (kind == CG_DEP_VOLUME) return launch_deposit_volume(g, n, per_particle, (double*)bulk_out, false);
+    return launch_deposit_momentum(g, n, per_particle, false, bulk_out, false);
+}
+
+cg_status cg_average_fine_to_bulk(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk) {
+    CG_TRY(check_handle(g));
+    if (!u_fine || !u_bulk || !aligned16(u_fine)) return CG_ERR_INVALID_ARG;
+    return launch_average(g, u_fine, u_bulk, var_bulk);
+}
+
+cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel, const double* eps_bulk,
+                  const void* u_bulk, void* force_out, void* S_bulk_out, const cg_mlp* mlp) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_n(n));
+    if (mlp) return CG_ERR_INVALID_ARG;
+    if (!eps_bulk || !u_bulk) return CG_ERR_INVALID_ARG;
+    if (n > 0 && (!pos_d || !vel || !force_out || !aligned16(pos_d) || !aligned16(vel))) return CG_ERR_INVALID_ARG;
+    if (S_bulk_out && g->n_binned != n) return CG_ERR_NOT_BINNED;
+    CG_TRY(ensure_particle_capacity(g, n));
+    CG_TRY(launch_pack(g, eps_bulk, u_bulk, false));
+    CG_TRY(launch_drag(g, n, pos_d, vel, force_out, S_bulk_out != nullptr, false, 0.0));
+    if (S_bulk_out) CG_TRY(launch_deposit_momentum(g, n, nullptr, true, S_bulk_out, false));
+    return CG_OK;
+}
+
+cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, void* fine_out) {
+    CG_TRY(check_handle(g));
+    if (ncomp < 1 || ncomp > 4 || !bulk || !fine_out || !aligned16(fine_out)) return CG_ERR_INVALID_ARG;
+    const void* in[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* out[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int c = 0; c < ncomp; ++c) {
+        in[c] = (const char*)bulk + (size_t)c * g->gd.nbulk * g->tsize;
+        out[c] = (char*)fine_out + (size_t)c * g->gd.nfine * g->tsize;
+    }
+    return launch_project(g, ncomp, in, out, false);
+}
+
+static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* o,
+                           double dt) {
+    const long long n = p->n;
+    CG_TRY(ensure_particle_capacity(g, n));
+    for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
+    CG_TRY(launch_bin(g, n, p->pos_d));
+    CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
+    CG_TRY(launch_deposit_volume(g, n, p->pos_d, o->eps_bulk, true));
+    CG_TRY(launch_average(g, u_fine, o->u_bulk, o->var_bulk));
+    CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
+    CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, true, true, dt));
+    if (n == 0) g->part_blocks[PS_DRAG] = 0;
+    CG_TRY(launch_deposit_momentum(g, n, nullptr, true, o->S_bulk, true));
+    const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
+    const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, g->eps_t};
+    void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, o->eps_fine};
+    CG_TRY(launch_project(g, o->eps_fine ? 4 : 3, in, out, true));
+    CG_TRY(launch_sums(g, o->sums ? o->sums : g->sums_scratch));
+    return CG_OK;
+}
+
+static cg_status check_step_args(const cg_particles* p, const void* u_fine, const cg_step_out* o, double dt,
+                                 bool device) {
+    if (!p || !o || !u_fine) return CG_ERR_INVALID_ARG;
+    CG_TRY(check_n(p->n));
+    if (!(dt >= 0.0) || !isfinite(dt)) return CG_ERR_INVALID_ARG;
+    if (p->n > 0 && (!p->pos_d || !p->vel || !o->force)) return CG_ERR_INVALID_ARG;
+    if (!o->eps_bulk || !o->u_bulk || !o->S_bulk || !o->S_fine) return CG_ERR_INVALID_ARG;
+    if (device) {
+        if (p->n > 0 && (!aligned16(p->pos_d) || !aligned16(p->vel))) return CG_ERR_INVALID_ARG;
+        if (!aligned16(u_fine) || !aligned16(o->S_fine) || (o->eps_fine && !aligned16(o->eps_fine)))
+            return CG_ERR_INVALID_ARG;
+    }
+    return CG_OK;
+}
+
+cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out, double dt) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, true));
+    return step_impl(g, p, u_fine, out, dt);
+}
+
+cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
+                       double dt) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, false));
+    const long long n = p->n;
+    const size_t ts = g->tsize, nb = (size_t)g->gd.nbulk, nf = (size_t)g->gd.nfine;
+    const size_t pbytes = 4 * ts * (size_t)std::max(1LL, n);
+    CG_TRY(ensure_buf(g->st_pos, pbytes));
+    CG_TRY(ensure_buf(g->st_vel, pbytes));
+    CG_TRY(ensure_buf(g->st_ufine, 3 * ts * nf));
+    CG_TRY(ensure_buf(g->st_eps, sizeof(double) * nb));
+    CG_TRY(ensure_buf(g->st_ub, 3 * ts * nb));
+    CG_TRY(ensure_buf(g->st_Sb, 3 * ts * nb));
+    CG_TRY(ensure_buf(g->st_F, 3 * ts * (size_t)std::max(1LL, n)));
+    CG_TRY(ensure_buf(g->st_Sf, 3 * ts * nf));
+    if (out->var_bulk) CG_TRY(ensure_buf(g->st_var, ts * nb));
+    if (out->eps_fine) CG_TRY(ensure_buf(g->st_epsf, ts * nf));
+    if (out->sums) CG_TRY(ensure_buf(g->st_sums, sizeof(double) * CG_NSUMS));
+    if (out->cell) CG_TRY(ensure_buf(g->st_cell, sizeof(int32_t) * (size_t)std::max(1LL, n)));
+    if (out->perm) CG_TRY(ensure_buf(g->st_perm, sizeof(int32_t) * (size_t)std::max(1LL, n)));
+    if (out->cell_start) CG_TRY(ensure_buf(g->st_cs, sizeof(int32_t) * (nb + 1)));
+
+    cudaStream_t s = g->stream;
+    if (n > 0) {
+        CG_CUDA(cudaMemcpyAsync(g->st_pos.p, p->pos_d, 4 * ts * n, cudaMemcpyHostToDevice, s));
+        CG_CUDA(cudaMemcpyAsync(g->st_vel.p, p->vel, 4 * ts * n, cudaMemcpyHostToDevice, s));
+    }
+    CG_CUDA(cudaMemcpyAsync(g->st_ufine.p, u_fine, 3 * ts * nf, cudaMemcpyHostToDevice, s));
+    cg_particles dp = {n, g->st_pos.p, g->st_vel.p};
+    cg_step_out d;
+    d.eps_bulk = (double*)g->st_eps.p;
+    d.u_bulk = g->st_ub.p;
+    d.var_bulk = out->var_bulk ? g->st_var.p : nullptr;
+    d.S_bulk = g->st_Sb.p;
+    d.force = g->st_F.p;
+    d.S_fine = g->st_Sf.p;
+    d.eps_fine = out->eps_fine ? g->st_epsf.p : nullptr;
+    d.sums = out->sums ? (double*)g->st_sums.p : nullptr;
+    d.cell = out->cell ? (int32_t*)g->st_cell.p : nullptr;
+    d.perm = out->perm ? (int32_t*)g->st_perm.p : nullptr;
+    d.cell_start = out->cell_start ? (int32_t*)g->st_cs.p : nullptr;
+    CG_TRY(step_impl(g, &dp, g->st_ufine.p, &d, dt));
+    auto d2h = [&](void* dst, const void* src, size_t bytes) -> cg_status {
+        if (dst && bytes) CG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        return CG_OK;
+    };
+    CG_TRY(d2h(out->eps_bulk, d.eps_bulk, sizeof(double) * nb));
+    CG_TRY(d2h(out->u_bulk, d.u_bulk, 3 * ts * nb));
+    CG_TRY(d2h(out->var_bulk, d.var_bulk, ts * nb));
+    CG_TRY(d2h(out->S_bulk, d.S_bulk, 3 * ts * nb));
+    CG_TRY(d2h(out->force, d.force, 3 * ts * n));
+    CG_TRY(d2h(out->S_fine, d.S_fine, 3 * ts * nf));
+    CG_TRY(d2h(out->eps_fine, d.eps_fine, ts * nf));
+    CG_TRY(d2h(out->sums, d.sums, sizeof(double) * CG_NSUMS));
+    CG_TRY(d2h(out->cell, d.cell, sizeof(int32_t) * n));
+    CG_TRY(d2h(out->perm, d.perm, sizeof(int32_t) * n));
+    CG_TRY(d2h(out->cell_start, d.cell_start, sizeof(int32_t) * (nb + 1)));
+    if (dt > 0.0 && n > 0) {
+        CG_TRY(d2h(p->pos_d, g->st_pos.p, 4 * ts * n));
+        CG_TRY(d2h(p->vel, g->st_vel.p, 4 * ts * n));
+    }
+    CG_CUDA(cudaStreamSynchronize(s));
+    return CG_OK;
+}
+
+cg_status cg_sync_status(cg_grids* g, uint32_t* flags, int64_t* counts) {
+    CG_TRY(check_handle(g));
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CG_ERR_CUDA;
+    }
+    unsigned long long h[kNumSlots];
+    CG_CUDA(cudaMemcpy(h, g->status, sizeof h, cudaMemcpyDeviceToHost));
+    CG_CUDA(cudaMemset(g->status, 0, sizeof h));
+    if (flags) *flags = (uint32_t)h[ST_FLAGS];
+    if (counts) {
+        counts[0] = (int64_t)h[ST_OUTSIDE];
+        counts[1] = (int64_t)h[ST_NONFINITE];
+        counts[2] = (int64_t)h[ST_CLAMPED];
+        counts[3] = (int64_t)h[ST_TIMEOUT];
+    }
+    if (h[ST_FLAGS] & CG_FLAG_TIMEOUT) return CG_ERR_TIMEOUT;
+    if (h[ST_FLAGS] & CG_FLAG_NONFINITE) return CG_ERR_NONFINITE;
+    return CG_OK;
+}
+
+int64_t cg_launch_count(const cg_grids* g) { return g ? g->launches : -1; }
+
+cg_status cg_profile_enable(cg_grids* g, int32_t on) {
+    CG_TRY(check_handle(g));
+    if (!on) prof_drain(g);
+    g->prof = on != 0;
+    return CG_OK;
+}
+
+cg_status cg_profile_reset(cg_grids* g) {
+    CG_TRY(check_handle(g));
+    prof_drain(g);
+    for (ProfSlot& s : g->slots) {
+        s.launches = 0;
+        s.total_ms = 0.0;
+    }
+    return CG_OK;
+}
+
+cg_status cg_profile_read(cg_grids* g, int32_t k, const char** name, int64_t* launches, double* total_ms,
+                          int32_t* count) {
+    CG_TRY(check_handle(g));
+    prof_drain(g);
+    if (count) *count = (int32_t)g->slots.size();
+    if (k < 0 || k >= (int32_t)g->slots.size()) return name || launches || total_ms ? CG_ERR_INVALID_ARG : CG_OK;
+    if (name) *name = g->slots[k].name.c_str();
+    if (launches) *launches = g->slots[k].launches;
+    if (total_ms) *total_ms = g->slots[k].total_ms;
+    return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// bin.cu -- (a0) particle binning by bulk cell: the per-step particle to
+// cell connectivity of Sec. 2.2 of arXiv 1807.11834.
+//
+// Cell rule (per axis): clamp(floor((x - x0) / H), 0, n_b - 1) with the
+// quotient in IEEE double (subtract, then correctly rounded divide).  The
+// FP32 path evaluates the quotient in float with a proven error bound and
+// falls back to the exact double evaluation only when the float quotient
+// lies within that bound of an integer, so the cell is bit-identical to the
+// double rule at FP32 cost.
+//
+// Sort: least-significant-digit counting sort, one or two passes of at most
+// 11 bits.  Each 4096-particle tile ranks its keys stably with warp-level
+// match: warp w owns a contiguous 512-particle slice, walks it 32 at a time
+// in index order and keeps per-digit counters in shared memory, so the
+// rank of a particle within its digit group follows its index.  Tile
+// histograms are scanned digit-major across tiles, which makes the whole
+// pass stable and fully deterministic (no atomics decide any position).
+// Per-cell counts use integer atomics (order-independent), then a scan.
+#include "cg_internal.cuh"
+
+namespace cg {
+
+__device__ __forceinline__ void add_status(unsigned long long* st, int outside, int nonfin) {
+    // block-level aggregation by the caller; one atomic per non-zero counter
+    if (outside) {
+        atomicAdd(&st[ST_OUTSIDE], (unsigned long long)outside);
+        atomicOr(&st[ST_FLAGS], (unsigned long long)CG_FLAG_OUTSIDE);
+    }
+    if (nonfin) {
+        atomicAdd(&st[ST_NONFINITE], (unsigned long long)nonfin);
+        atomicOr(&st[ST_FLAGS], (unsigned long long)CG_FLAG_NONFINITE);
+    }
+}
+
+// ----------------------------------------------------------------------
+// Key kernel: cell per particle, per-cell counts, tile histogram of digit 0
+// ----------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads)
+k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
+          int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
+          unsigned long long* __restrict__ status) {
+    extern __shared__ int sh[];
+    __shared__ int s_cnt[2];
+    const int R = 1 << bits0;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    int n_out = 0, n_nf = 0;
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + (long long)k * kSortThreads + threadIdx.x;
+        bool valid = p < n;
+        int c = -1;
+        if (valid) {
+            V4<T> v = ld4(pos, p);
+            int outside = 0;
+            if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
+            c = cell_of(v, g, outside);
+            n_out += outside;
+            key[p] = c;
+        }
+        // warp-aggregated per-cell count (integer: order-independent)
+        unsigned peers = __match_any_sync(0xffffffffu, c);
+        int before = __popc(peers & lt);
+        if (valid && before == 0) atomicAdd(&count[c], __popc(peers));
+        int d = valid ? (c & (R - 1)) : -1;
+        unsigned dpeers = __match_any_sync(0xffffffffu, d);
+        if (valid && __popc(dpeers & lt) == 0) atomicAdd(&sh[d], __popc(dpeers));
+    }
+    (void)lane;
+    if (n_out) atomicAdd(&s_cnt[0], n_out);
+    if (n_nf) atomicAdd(&s_cnt[1], n_nf);
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blockIdx.x] = sh[i];
+    if (threadIdx.x == 0) add_status(status, s_cnt[0], s_cnt[1]);
+}
+
+// Tile histogram of a digit of already-computed keys (second pass).
+__global__ void __launch_bounds__(kSortThreads)
+k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift, int bits,
+           int32_t* __restrict__ hist) {
+    extern __shared__ int sh[];
+    const int R = 1 << bits;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + (long long)k * kSortThreads + threadIdx.x;
+        bool valid = p < n;
+        int d = valid ? ((__ldg(keys + p) >> shift) & (R - 1)) : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && __popc(peers & lt) == 0) atomicAdd(&sh[d], __popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blockIdx.x] = sh[i];
+}
+
+// Stable scatter of one digit pass.  offs = exclusive scan of the tile
+// histograms, digit-major ([digit][tile]).
+template <bool FIRST, bool FINAL>
+__global__ void __launch_bounds__(kSortThreads)
+k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
+              int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
+              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
+              int32_t* __restrict__ perm, int32_t* __restrict__ inv_perm) {
+    extern __shared__ int cnt[];  // [kSortWarps][R]
+    const int R = 1 << bits;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    int* wc = cnt + warp * R;
+    const unsigned lt = lanemask_lt();
+    const long long base = (long long)blockIdx.x * kSortTile + (long long)warp * (kSortTile / kSortWarps);
+    int kv[kSortItems], vv[kSortItems], rk[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        bool valid = p < n;
+        int kk = valid ? __ldg(keys_in + p) : 0;
+        int v = 0;
+        if (valid) v = FIRST ? (int)p : __ldg(vals_in + p);
+        int d = valid ? ((kk >> shift) & (R - 1)) : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & lt);
+        int c0 = valid ? wc[d] : 0;
+        __syncwarp();
+        if (valid && before == 0) wc[d] = c0 + __popc(peers);
+        __syncwarp();
+        kv[k] = kk;
+        vv[k] = v;
+        rk[k] = c0 + before;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < R; d += blockDim.x) {
+        int run = __ldg(offs + (long long)d * ntiles + blockIdx.x);
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            int t = cnt[w * R + d];
+            cnt[w * R + d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        if (p < n) {
+            int d = (kv[k] >> shift) & (R - 1);
+            int dst = wc[d] + rk[k];
+            if (FINAL) {
+                perm[dst] = vv[k];
+                inv_perm[vv[k]] = dst;
+            } else {
+                keys_out[dst] = kv[k];
+                vals_out[dst] = vv[k];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------
+// Exclusive scan of int32 (totals fit in int32: at most 2^31 - 1 particles)
+// ----------------------------------------------------------------------
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) sh_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        sh_warp[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    int wbase = warp ? sh_warp[warp - 1] : 0;
+    total = sh_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return wbase + x - v;
+}
+
+// Load the 16 consecutive elements of a thread (zero past m).
+__device__ __forceinline__ void load16(const int32_t* __restrict__ in, long long start, long long m, int v[16]) {
+    if (start + 16 <= m) {
+        const int4* q = reinterpret_cast<const int4*>(in + start);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int4 t = q[j];
+            v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = (start + j < m) ? in[start + j] : 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const int32_t* __restrict__ in, long long m,
+                                                     int32_t* __restrict__ part) {
+    __shared__ int shw[32];
+    long long start = (long long)blockIdx.x * kScanItems + threadIdx.x * 16;
+    int v[16];
+    load16(in, start, m, v);
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s += v[j];
+    int total;
+    block_exclusive_scan(s, shw, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Single-block exclusive scan of part[0..nb) in place (any length).
+__global__ void __launch_bounds__(1024) k_scan_top(int32_t* __restrict__ part, long long nb) {
+    __shared__ int shw[32];
+    int carry = 0;
+    for (long long s0 = 0; s0 < nb; s0 += 1024) {
+        long long i = s0 + threadIdx.x;
+        int v = i < nb ? part[i] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, shw, total);
+        if (i < nb) part[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const int32_t* in, long long m,
+                                                   const int32_t* __restrict__ part, int32_t* out) {
+    __shared__ int shw[32];
+    long long start = (long long)blockIdx.x * kScanItems + threadIdx.x * 16;
+    int v[16];
+    load16(in, start, m, v);
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s += v[j];
+    int total;
+    int ex = block_exclusive_scan(s, shw, total) + part[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (start + j < m) out[start + j] = ex;
+        ex += v[j];
+    }
+}
+
+// out may alias in.
+static cg_status scan_exclusive(cg_grids* g, const int32_t* in, int32_t* out, long long m) {
+    if (m <= 0) return CG_OK;
+    long long nblk = (m + kScanItems - 1) / kScanItems;
+    if (nblk > g->scan_cap) return CG_ERR_OUT_OF_RANGE;
+    CG_LAUNCH(g, "bin_scan", k_scan_reduce, (unsigned)nblk, 256, 0, in, m, g->scan_part);
+    CG_LAUNCH(g, "bin_scan", k_scan_top, 1, 1024, 0, g->scan_part, nblk);
+    CG_LAUNCH(g, "bin_scan", k_scan_down, (unsigned)nblk, 256, 0, in, m, g->scan_part, out);
+    return CG_OK;
+}
+
+static bool g_attr_done = false;
+
+static cg_status set_attrs() {
+    if (g_attr_done) return CG_OK;
+    const int smem = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);
+    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    g_attr_done = true;
+    return CG_OK;
+}
+
+cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
+    CG_TRY(set_attrs());
+    const long long nbulk = g->gd.nbulk;
+    // count[] lives in cell_start; the exclusive scan turns it into starts
+    CG_CUDA(cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (nbulk + 1), g->stream));
+    g->n_binned = -1;
+    if (n == 0) {
+        g->n_binned = 0;
+        return CG_OK;
+    }
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const int b0 = g->pass_bits[0], b1 = g->pass_bits[1];
+    const bool two = g->npasses == 2;
+    const long long m0 = (long long)ntiles << b0;
+    if (m0 > g->hist_cap || (two && ((long long)ntiles << b1) > g->hist_cap)) return CG_ERR_OUT_OF_RANGE;
+
+    if (g->fp64)
+        CG_LAUNCH(g, "bin_key", k_bin_key<double>, ntiles, kSortThreads, sizeof(int) << b0,
+                  (const double*)pos_d, n, g->gd, g->key, g->cell_start, g->hist, ntiles, b0, g->status);
+    else
+        CG_LAUNCH(g, "bin_key", k_bin_key<float>, ntiles, kSortThreads, sizeof(int) << b0,
+                  (const float*)pos_d, n, g->gd, g->key, g->cell_start, g->hist, ntiles, b0, g->status);
+    CG_TRY(scan_exclusive(g, g->cell_start, g->cell_start, nbulk + 1));
+    CG_TRY(scan_exclusive(g, g->hist, g->hist, m0));
+    const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
+    if (!two) {
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true>), ntiles, kSortThreads, smem0,
+                  g->key, nullptr, n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm, g->inv_perm);
+    } else {
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false>), ntiles, kSortThreads, smem0,
+                  g->key, nullptr, n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr, nullptr);
+        const long long m1 = (long long)ntiles << b1;
+        CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1,
+                  g->key1, n, ntiles, b0, b1, g->hist);
+        CG_TRY(scan_exclusive(g, g->hist, g->hist, m1));
+        const size_t smem1 = (size_t)kSortWarps * sizeof(int) << b1;
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true>), ntiles, kSortThreads, smem1,
+                  g->key1, g->val1, n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm, g->inv_perm);
+    }
+    g->n_binned = n;
+    return CG_OK;
+}
+
+}  // namespace cg

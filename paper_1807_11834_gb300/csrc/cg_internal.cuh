@@ -1,0 +1,346 @@
+// cg_internal.cuh -- internal declarations of the GB300 coupling library.
+//
+// Shared by the .cu files of the library only (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cg.h"
+
+namespace cg {
+
+// ----------------------------------------------------------------------
+// Sizes
+// ----------------------------------------------------------------------
+constexpr int kSortThreads = 256;                   // threads of a sort tile
+constexpr int kSortItems = 16;                      // items per thread
+constexpr int kSortTile = kSortThreads * kSortItems; // 4096 particles per tile
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kMaxDigitBits = 11;                   // radix digit of one pass
+constexpr int kMaxBulkBits = 2 * kMaxDigitBits;     // two passes -> 2^22 cells
+constexpr int kScanItems = 4096;                    // elements per scan block
+constexpr int kNumSlots = 16;                       // status counters
+
+// Status word slots (unsigned long long each).
+enum { ST_FLAGS = 0, ST_OUTSIDE = 1, ST_NONFINITE = 2, ST_CLAMPED = 3, ST_TIMEOUT = 4 };
+
+// Partial-sum regions of the conservation sums.
+enum { PS_VOL = 0, PS_DRAG = 1, PS_MOM = 2, PS_PROJ = 3, PS_NREG = 4 };
+constexpr int kDragSums = 9;   // V_p, F(3), |F|, m u (3), clamped count
+
+// ----------------------------------------------------------------------
+// Device-side view of the grid geometry (passed by value to kernels)
+// ----------------------------------------------------------------------
+struct GridDev {
+    int nb[3];          // bulk cells per axis
+    int nf[3];          // fine cells per axis
+    int r;              // coarsening ratio
+    long long nbulk, nfine;
+    double x0[3];       // origin
+    double xhi[3];      // origin + extent
+    double H[3];        // bulk spacing (L / nb, rounded to double)
+    double invH[3];     // 1 / H (double)
+    double VB, invVB, Vf;
+    // float versions for the FP32 path
+    float x0f[3];       // (float)x0
+    float invHf[3];     // (float)(1/H)
+    float ax0f[3];      // |x0 / H| (filter margin term)
+    float x0h[3], x0l[3];   // x0 as float-float
+    float ihh[3], ihl[3];   // 1/H as float-float
+    float invVBf, VBf, Vff;
+    float VBh, VBl, Vfh, Vfl;   // V_B, V_f as float-float
+    // physics
+    int law, interp;
+    double rho_f, mu_f, rho_p, eps_switch, eps_min, g[3];
+};
+
+// ----------------------------------------------------------------------
+// Handle
+// ----------------------------------------------------------------------
+struct ProfSlot {
+    std::string name;
+    long long launches = 0;
+    double total_ms = 0.0;
+};
+
+struct PendingEv {
+    int slot;
+    int ev;   // index into the event pool (start = 2 ev, stop = 2 ev + 1)
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace cg
+
+struct cg_grids {
+    cg_grid_desc desc;
+    cg::GridDev gd;
+    int fp64 = 0;
+    size_t tsize = 4;          // bytes of T
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    int bulk_bits = 0, pass_bits[2] = {0, 0}, npasses = 1;
+
+    // binning state
+    long long n_binned = -1;
+    long long cap = -1;        // particle capacity of the particle buffers
+
+    // particle-sized buffers
+    int32_t* key = nullptr;        // [cap] cell per particle (caller order)
+    int32_t* key1 = nullptr;       // [cap] keys after pass 1
+    int32_t* val1 = nullptr;       // [cap] particle ids after pass 1
+    int32_t* perm = nullptr;       // [cap] particle ids in cell order
+    int32_t* inv_perm = nullptr;   // [cap] sorted position of each particle
+    int32_t* key_sorted = nullptr; // [cap] cell of each sorted slot
+    void* Fs = nullptr;            // [cap] T4 drag force in cell order
+    int32_t* hist = nullptr;       // [2^digit * ntiles]
+    int32_t* scan_part = nullptr;  // scan block partials
+    long long hist_cap = 0, scan_cap = 0;
+
+    // bulk-sized buffers
+    int32_t* cell_start = nullptr; // [nbulk + 1]
+    void* bulk4 = nullptr;         // [nbulk] T4: phi, u_x, u_y, u_z
+    void* eps_t = nullptr;         // [nbulk] T: porosity in the path precision
+    double* partials = nullptr;    // conservation-sum block partials
+    long long part_off[cg::PS_NREG] = {0, 0, 0, 0};
+    long long part_blocks[cg::PS_NREG] = {0, 0, 0, 0};
+    long long part_cap = 0;
+    double* sums_scratch = nullptr;   // [CG_NSUMS] when the caller gives none
+    unsigned long long* status = nullptr;   // [kNumSlots]
+
+    // host-buffer entry: device staging
+    cg::DevBuf st_pos, st_vel, st_ufine, st_eps, st_ub, st_var, st_Sb, st_F, st_Sf, st_epsf,
+        st_sums, st_cell, st_perm, st_cs;
+
+    // launch accounting / profiling
+    long long launches = 0;
+    bool prof = false;
+    std::vector<cg::ProfSlot> slots;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cg::PendingEv> pending;
+    int ev_used = 0;
+};
+
+namespace cg {
+
+// ----------------------------------------------------------------------
+// Launch plumbing (api.cu)
+// ----------------------------------------------------------------------
+int prof_slot(cg_grids* g, const char* name);
+void prof_begin(cg_grids* g, int slot, int* ev);
+void prof_end(cg_grids* g, int slot, int ev);
+
+// Launch a kernel on the handle's stream, count it, time it when profiling,
+// and turn a launch error into CG_ERR_CUDA.
+#define CG_LAUNCH(g, name, kernel, grid, block, smem, ...)                        \
+    do {                                                                         \
+        int slot_ = -1, ev_ = -1;                                                \
+        if ((g)->prof) {                                                         \
+            slot_ = cg::prof_slot((g), (name));                                  \
+            cg::prof_begin((g), slot_, &ev_);                                    \
+        }                                                                        \
+        kernel<<<(grid), (block), (smem), (g)->stream>>>(__VA_ARGS__);           \
+        (g)->launches++;                                                         \
+        cudaError_t e_ = cudaGetLastError();                                     \
+        if ((g)->prof) cg::prof_end((g), slot_, ev_);                            \
+        if (e_ != cudaSuccess) return CG_ERR_CUDA;                               \
+    } while (0)
+
+#define CG_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return CG_ERR_CUDA;      \
+    } while (0)
+
+#define CG_TRY(call)                                    \
+    do {                                                \
+        cg_status s_ = (call);                          \
+        if (s_ != CG_OK) return s_;                     \
+    } while (0)
+
+// ----------------------------------------------------------------------
+// Step launchers (one .cu each)
+// ----------------------------------------------------------------------
+cg_status ensure_particle_capacity(cg_grids* g, long long n);
+cg_status ensure_partials(cg_grids* g, long long n);
+
+cg_status launch_bin(cg_grids* g, long long n, const void* pos_d);
+cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums);
+cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, bool sorted,
+                                  void* S_bulk, bool sums);
+cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk);
+cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
+cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force,
+                      bool fused, bool sums, double dt);
+cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);
+cg_status launch_sums(cg_grids* g, double* sums);
+
+}  // namespace cg
+
+// ----------------------------------------------------------------------
+// Device helpers
+// ----------------------------------------------------------------------
+namespace cg {
+
+template <typename T> struct V4;
+template <> struct V4<float> {
+    float x, y, z, w;
+};
+template <> struct V4<double> {
+    double x, y, z, w;
+};
+
+__device__ __forceinline__ V4<float> ld4(const float* __restrict__ p, long long i) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* __restrict__ p, long long i) {
+    const double2* q = reinterpret_cast<const double2*>(p) + 2 * i;
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(float* p, long long i, float x, float y, float z, float w) {
+    reinterpret_cast<float4*>(p)[i] = make_float4(x, y, z, w);
+}
+__device__ __forceinline__ void st4(double* p, long long i, double x, double y, double z, double w) {
+    double2* q = reinterpret_cast<double2*>(p) + 2 * i;
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, w);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    T z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// Compensated accumulator (TwoSum cascade, Neumaier-equivalent).
+template <typename T>
+struct CSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        T t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c += e;
+    }
+    __device__ __forceinline__ void merge(const CSum& o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ __forceinline__ T get() const { return s + c; }
+};
+
+// Warp-level fixed-tree reduction of a compensated sum (deterministic).
+template <typename T>
+__device__ __forceinline__ CSum<T> warp_reduce(CSum<T> v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        CSum<T> o;
+        o.s = __shfl_xor_sync(0xffffffffu, v.s, off);
+        o.c = __shfl_xor_sync(0xffffffffu, v.c, off);
+        v.merge(o);
+    }
+    return v;
+}
+
+// Block-level deterministic reduction of K compensated sums; thread 0
+// writes part[k * stride + blockIdx.x] as double (each block one column).
+template <typename T, int K>
+__device__ __forceinline__ void block_sums(CSum<T> (&v)[K], double* __restrict__ part, long long stride) {
+    __shared__ T sh_s[K][32];
+    __shared__ T sh_c[K][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        CSum<T> r = warp_reduce(v[k]);
+        if (lane == 0) {
+            sh_s[k][warp] = r.s;
+            sh_c[k][warp] = r.c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const int k = threadIdx.x;
+        CSum<T> a;
+        a.s = sh_s[k][0];
+        a.c = sh_c[k][0];
+        for (int w = 1; w < nw; ++w) {
+            CSum<T> o;
+            o.s = sh_s[k][w];
+            o.c = sh_c[k][w];
+            a.merge(o);
+        }
+        part[(long long)k * stride + blockIdx.x] = (double)a.s + (double)a.c;
+    }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ----------------------------------------------------------------------
+// (a0) bin index, shared by the binning and the cell-value gather.
+// ----------------------------------------------------------------------
+// ----------------------------------------------------------------------
+__device__ __forceinline__ int bin_axis_exact(double x, double x0, double H, int nb, int& outside) {
+    double q = __ddiv_rn(__dsub_rn(x, x0), H);
+    int i;
+    if (!(q >= 0.0)) i = 0;
+    else if (q >= (double)nb) i = nb - 1;
+    else i = (int)floor(q);
+    if (!(q >= 0.0 && q <= (double)nb)) outside = 1;
+    return i;
+}
+
+// |q32 - q64| <= 4 u (|q| + |x0/H|), u = 2^-24, for
+// q32 = (x - fl(x0)) * fl(1/H) in round-to-nearest float; the margin below
+// is twice that bound.  Outside the margin floor(q32) == floor(q64).
+__device__ __forceinline__ int bin_axis_f32(float x, const GridDev& g, int a, int& outside) {
+    float q = __fmul_rn(__fsub_rn(x, g.x0f[a]), g.invHf[a]);
+    float fl = floorf(q);
+    float m = (fabsf(q) + g.ax0f[a]) * 4.76837158203125e-7f + 1e-30f;
+    if ((q - fl > m) && (fl + 1.0f - q > m)) {
+        int i = (int)fl;
+        if (i < 0) { outside = 1; return 0; }
+        if (i >= g.nb[a]) { outside = 1; return g.nb[a] - 1; }
+        return i;
+    }
+    return bin_axis_exact((double)x, g.x0[a], g.H[a], g.nb[a], outside);
+}
+
+__device__ __forceinline__ int cell_of(const V4<float>& v, const GridDev& g, int& outside) {
+    int i = bin_axis_f32(v.x, g, 0, outside);
+    int j = bin_axis_f32(v.y, g, 1, outside);
+    int k = bin_axis_f32(v.z, g, 2, outside);
+    return i + g.nb[0] * (j + g.nb[1] * k);
+}
+__device__ __forceinline__ int cell_of(const V4<double>& v, const GridDev& g, int& outside) {
+    int i = bin_axis_exact(v.x, g.x0[0], g.H[0], g.nb[0], outside);
+    int j = bin_axis_exact(v.y, g.x0[1], g.H[1], g.nb[1], outside);
+    int k = bin_axis_exact(v.z, g.x0[2], g.H[2], g.nb[2], outside);
+    return i + g.nb[0] * (j + g.nb[1] * k);
+}
+
+__device__ __forceinline__ int cell_of_f(float x, float y, float z, const GridDev& g) {
+    int o = 0;
+    return cell_of(V4<float>{x, y, z, 0.f}, g, o);
+}
+__device__ __forceinline__ int cell_of_d(double x, double y, double z, const GridDev& g) {
+    int o = 0;
+    return cell_of(V4<double>{x, y, z, 0.0}, g, o);
+}
+
+}  // namespace cg

@@ -1,0 +1,360 @@
+// fine.cu -- the two fine-grid sweeps of the coupling step (Fig. 1 of
+// arXiv 1807.11834): (a2) the fluid solution goes fine -> bulk, (a4) the
+// particle-related fields go bulk -> fine.
+//
+// Both kernels run one thread per bulk cell.  Thread (I, J, K) owns the
+// r^3 nested fine cells of its bulk cell: it reads (or writes) r^2 rows of
+// r consecutive fine values per component, as one 16-byte vector per row
+// for r = 4 (8 bytes for r = 2, two 16-byte vectors for r = 8).  Adjacent
+// threads own adjacent bulk cells along x, so a warp touches 32 * r
+// consecutive fine values per row: fully coalesced, every fine value read
+// or written exactly once.  These two sweeps carry most of the bytes of a
+// step, so they are written to stream at HBM speed.
+#include "cg_internal.cuh"
+
+namespace cg {
+
+template <typename T, int R> struct Row;
+template <> struct Row<float, 4> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+template <> struct Row<float, 2> {
+    static __device__ __forceinline__ void load(const float* p, float v[2]) {
+        float2 q = __ldcs(reinterpret_cast<const float2*>(p));
+        v[0] = q.x; v[1] = q.y;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[2]) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    }
+};
+template <> struct Row<float, 8> {
+    static __device__ __forceinline__ void load(const float* p, float v[8]) {
+        float4 a = __ldcs(reinterpret_cast<const float4*>(p)), b = __ldcs(reinterpret_cast<const float4*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[8]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+        __stcs(reinterpret_cast<float4*>(p) + 1, make_float4(v[4], v[5], v[6], v[7]));
+    }
+};
+template <int R> struct Row<double, R> {
+    static __device__ __forceinline__ void load(const double* p, double v[R]) {
+#pragma unroll
+        for (int i = 0; i < R; i += 2) {
+            double2 q = __ldcs(reinterpret_cast<const double2*>(p + i));
+            v[i] = q.x;
+            v[i + 1] = q.y;
+        }
+    }
+    static __device__ __forceinline__ void store(double* p, const double v[R]) {
+#pragma unroll
+        for (int i = 0; i < R; i += 2) __stcs(reinterpret_cast<double2*>(p + i), make_double2(v[i], v[i + 1]));
+    }
+};
+
+__device__ __forceinline__ void bulk_ijk(long long cb, const GridDev& g, int& I, int& J, int& K) {
+    I = (int)(cb % g.nb[0]);
+    long long t = cb / g.nb[0];
+    J = (int)(t % g.nb[1]);
+    K = (int)(t / g.nb[1]);
+}
+
+// ----------------------------------------------------------------------
+// (a2) mean and variance of the r^3 fine cells of a bulk cell.
+// The variance uses a shift by the first fine value of the cell:
+// var = (Q - sum_c D_c^2 / n) / n with Q = sum (u - ref)^2 and
+// D_c = sum_f u_c - n ref_c, both compensated, which equals the two-pass
+// population variance without a second read of the fine data.
+// ----------------------------------------------------------------------
+template <typename T, int RC>
+__global__ void __launch_bounds__(256)
+k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var) {
+    const long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb >= g.nbulk) return;
+    int I, J, K;
+    bulk_ijk(cb, g, I, J, K);
+    const int r = RC ? RC : g.r;
+    const long long nx = g.nf[0], nxy = (long long)g.nf[0] * g.nf[1];
+    const long long f0 = (long long)I * r + nx * ((long long)J * r) + nxy * ((long long)K * r);
+    CSum<T> s[3], q;
+    T ref[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ref[c] = __ldg(u + c * g.nfine + f0);
+    if constexpr (RC > 0) {
+#pragma unroll
+        for (int dk = 0; dk < RC; ++dk) {
+#pragma unroll
+            for (int dj = 0; dj < RC; ++dj) {
+                const long long f = f0 + nx * dj + nxy * dk;
+                T v[3][RC];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Row<T, RC>::load(u + c * g.nfine + f, v[c]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int i = 0; i < RC; ++i) {
+                        s[c].add(v[c][i]);
+                        T dv = v[c][i] - ref[c];
+                        q.add(dv * dv);
+                    }
+            }
+        }
+    } else {
+        for (int dk = 0; dk < r; ++dk)
+            for (int dj = 0; dj < r; ++dj) {
+                const long long f = f0 + nx * dj + nxy * dk;
+                for (int i = 0; i < r; ++i)
+                    for (int c = 0; c < 3; ++c) {
+                        T v = __ldg(u + c * g.nfine + f + i);
+                        s[c].add(v);
+                        T dv = v - ref[c];
+                        q.add(dv * dv);
+                    }
+            }
+    }
+    const T n = (T)r * (T)r * (T)r;
+    const T invn = (T)1 / n;
+    T corr = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ub[c * g.nbulk + cb] = s[c].get() * invn;
+        if (var) {
+            // D_c = (s_hi - n ref) + s_lo, the n ref product split exactly
+            T p = n * ref[c];
+            T pe = fma(n, ref[c], -p);
+            T d1, e1;
+            two_sum(s[c].s, -p, d1, e1);
+            T D = d1 + (e1 + (s[c].c - pe));
+            corr += D * D;
+        }
+    }
+    if (var) {
+        T a, e;
+        two_sum(q.s, -corr * invn, a, e);
+        T v = (a + (e + q.c)) * invn;
+        var[cb] = v > T(0) ? v : T(0);
+    }
+}
+
+// ----------------------------------------------------------------------
+// (a4) interpolate ncomp bulk fields at the fine cell centres of a bulk
+// cell.  Along one axis, fine offset a in [0, r) of bulk cell I sits at
+// lattice coordinate xi = I + (2a + 1 - r) / (2r): for 2a + 1 < r it lies
+// between bulk centres I-1 and I with t = (2a + 1 + r) / (2r), otherwise
+// between I and I+1 with t = (2a + 1 - r) / (2r).  At the domain edges the
+// neighbour index is clamped to I, which reproduces constant extrapolation
+// in the outer half cell exactly because lerp(a, a, t) == a.  The weights
+// are exact dyadic rationals for power-of-two r.
+// ----------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T lerp(T a, T b, T t) { return fma(t, b - a, a); }
+
+template <int R> struct Stencil {
+    // neighbour slot (0: I-1, 1: I, 2: I+1) of the lower/upper support and t
+    static __device__ __forceinline__ void at(int a, int& lo, int& hi, float& t) {
+        const int num = 2 * a + 1 - R;
+        if (num < 0) { lo = 0; hi = 1; t = (float)(num + 2 * R) / (float)(2 * R); }
+        else { lo = 1; hi = 2; t = (float)num / (float)(2 * R); }
+    }
+};
+
+// Multiply a compensated sum by V_f, keeping the product's rounding error.
+__device__ __forceinline__ void scale_sum(CSum<float>& a, const GridDev& g) {
+    float hi = a.s * g.Vfh;
+    float lo = fmaf(a.s, g.Vfh, -hi);
+    lo = fmaf(a.s, g.Vfl, lo);
+    lo = fmaf(a.c, g.Vfh, lo);
+    a.s = hi;
+    a.c = lo;
+}
+__device__ __forceinline__ void scale_sum(CSum<double>& a, const GridDev& g) {
+    a.s *= g.Vf;
+    a.c *= g.Vf;
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(256)
+k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
+          const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0, T* __restrict__ out1,
+          T* __restrict__ out2, T* __restrict__ out3, double* __restrict__ part, long long pstride,
+          int do_sums) {
+    const long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CSum<T> sacc[3];
+    if (cb < g.nbulk) {
+        int I, J, K;
+        bulk_ijk(cb, g, I, J, K);
+        const int nbx = g.nb[0], nby = g.nb[1], nbz = g.nb[2];
+        const int xs[3] = {max(I - 1, 0), I, min(I + 1, nbx - 1)};
+        const int ys[3] = {max(J - 1, 0), J, min(J + 1, nby - 1)};
+        const int zs[3] = {max(K - 1, 0), K, min(K + 1, nbz - 1)};
+        const long long nx = g.nf[0], nxy = (long long)g.nf[0] * g.nf[1];
+        const long long f0 = (long long)I * RC + nx * ((long long)J * RC) + nxy * ((long long)K * RC);
+#pragma unroll 1
+        for (int c = 0; c < ncomp; ++c) {
+            const T* __restrict__ B = c == 0 ? in0 : c == 1 ? in1 : c == 2 ? in2 : in3;
+            T* __restrict__ O = c == 0 ? out0 : c == 1 ? out1 : c == 2 ? out2 : out3;
+            T f[3][3][3];   // [z][y][x]
+#pragma unroll
+            for (int z = 0; z < 3; ++z)
+#pragma unroll
+                for (int y = 0; y < 3; ++y)
+#pragma unroll
+                    for (int x = 0; x < 3; ++x)
+                        f[z][y][x] = __ldg(B + xs[x] + (long long)nbx * (ys[y] + (long long)nby * zs[z]));
+            CSum<T> rowsum;
+#pragma unroll
+            for (int az = 0; az < RC; ++az) {
+                int zlo, zhi;
+                float tzf;
+                Stencil<RC>::at(az, zlo, zhi, tzf);
+                const T tz = (T)tzf;
+                T fz[3][3];   // [y][x] after the z lerp
+#pragma unroll
+                for (int y = 0; y < 3; ++y)
+#pragma unroll
+                    for (int x = 0; x < 3; ++x) fz[y][x] = lerp(f[zlo][y][x], f[zhi][y][x], tz);
+#pragma unroll
+                for (int ay = 0; ay < RC; ++ay) {
+                    int ylo, yhi;
+                    float tyf;
+                    Stencil<RC>::at(ay, ylo, yhi, tyf);
+                    const T ty = (T)tyf;
+                    T gx[3];
+#pragma unroll
+                    for (int x = 0; x < 3; ++x) gx[x] = lerp(fz[ylo][x], fz[yhi][x], ty);
+                    T v[RC];
+                    T rs = 0;
+#pragma unroll
+                    for (int ax = 0; ax < RC; ++ax) {
+                        int xlo, xhi;
+                        float txf;
+                        Stencil<RC>::at(ax, xlo, xhi, txf);
+                        v[ax] = lerp(gx[xlo], gx[xhi], (T)txf);
+                        rs += v[ax];
+                    }
+                    Row<T, RC>::store(O + f0 + nx * ay + nxy * az, v);
+                    rowsum.add(rs);
+                }
+            }
+            if (c < 3) sacc[c] = rowsum;
+        }
+    }
+    if (do_sums) {
+        // sum_f S_f V_f = V_f sum_f S_f; V_f applied as a float-float product
+#pragma unroll
+        for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
+        block_sums<T, 3>(sacc, part, pstride);
+    }
+}
+
+// Generic ratio: one thread per fine cell, the same clamped stencil with
+// integer-derived weights.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
+                  const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0,
+                  T* __restrict__ out1, T* __restrict__ out2, T* __restrict__ out3,
+                  double* __restrict__ part, long long pstride, int do_sums) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CSum<T> sacc[3];
+    if (f < g.nfine) {
+        const int r = g.r;
+        long long t = f;
+        const int fi[3] = {(int)(t % g.nf[0]), (int)((t / g.nf[0]) % g.nf[1]),
+                           (int)(t / ((long long)g.nf[0] * g.nf[1]))};
+        int lo[3], hi[3];
+        T w[3];
+        for (int a = 0; a < 3; ++a) {
+            const int I = fi[a] / r, off = fi[a] - I * r;
+            const int num = 2 * off + 1 - r;
+            if (num < 0) { lo[a] = max(I - 1, 0); hi[a] = I; w[a] = (T)(num + 2 * r) / (T)(2 * r); }
+            else { lo[a] = I; hi[a] = min(I + 1, g.nb[a] - 1); w[a] = (T)num / (T)(2 * r); }
+        }
+        const long long nbx = g.nb[0], nbxy = (long long)g.nb[0] * g.nb[1];
+        for (int c = 0; c < ncomp; ++c) {
+            const T* __restrict__ B = c == 0 ? in0 : c == 1 ? in1 : c == 2 ? in2 : in3;
+            T* __restrict__ O = c == 0 ? out0 : c == 1 ? out1 : c == 2 ? out2 : out3;
+            T zv[2];
+            for (int dz = 0; dz < 2; ++dz) {
+                const long long kz = (dz ? hi[2] : lo[2]) * nbxy;
+                T yv[2];
+                for (int dy = 0; dy < 2; ++dy) {
+                    const long long jy = (dy ? hi[1] : lo[1]) * nbx;
+                    yv[dy] = lerp(__ldg(B + kz + jy + lo[0]), __ldg(B + kz + jy + hi[0]), w[0]);
+                }
+                zv[dz] = lerp(yv[0], yv[1], w[1]);
+            }
+            const T v = lerp(zv[0], zv[1], w[2]);
+            O[f] = v;
+            if (c < 3) sacc[c].add(v);
+        }
+    }
+    if (do_sums) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
+        block_sums<T, 3>(sacc, part, pstride);
+    }
+}
+
+static inline unsigned blocks_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+
+cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk) {
+    const unsigned nblk = blocks_of(g->gd.nbulk, 256);
+#define CG_AVG(T, RC)                                                                                   \
+    CG_LAUNCH(g, "average", (k_average<T, RC>), nblk, 256, 0, (const T*)u_fine, g->gd, (T*)u_bulk, \
+              (T*)var_bulk)
+    if (g->fp64) {
+        switch (g->gd.r) {
+            case 2: CG_AVG(double, 2); break;
+            case 4: CG_AVG(double, 4); break;
+            case 8: CG_AVG(double, 8); break;
+            default: CG_AVG(double, 0); break;
+        }
+    } else {
+        switch (g->gd.r) {
+            case 2: CG_AVG(float, 2); break;
+            case 4: CG_AVG(float, 4); break;
+            case 8: CG_AVG(float, 8); break;
+            default: CG_AVG(float, 0); break;
+        }
+    }
+#undef CG_AVG
+    return CG_OK;
+}
+
+cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums) {
+    double* part = g->partials + g->part_off[PS_PROJ];
+    const int r = g->gd.r;
+    const bool fast = (r == 2 || r == 4 || r == 8);
+    const unsigned nblk = fast ? blocks_of(g->gd.nbulk, 256) : blocks_of(g->gd.nfine, 256);
+    g->part_blocks[PS_PROJ] = sums ? (long long)nblk : -1;
+#define CG_PRJ(T, KER)                                                                                   \
+    CG_LAUNCH(g, "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2],        \
+              (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], part,       \
+              (long long)nblk, (int)sums)
+    if (g->fp64) {
+        switch (r) {
+            case 2: CG_PRJ(double, (k_project<double, 2>)); break;
+            case 4: CG_PRJ(double, (k_project<double, 4>)); break;
+            case 8: CG_PRJ(double, (k_project<double, 8>)); break;
+            default: CG_PRJ(double, k_project_generic<double>); break;
+        }
+    } else {
+        switch (r) {
+            case 2: CG_PRJ(float, (k_project<float, 2>)); break;
+            case 4: CG_PRJ(float, (k_project<float, 4>)); break;
+            case 8: CG_PRJ(float, (k_project<float, 8>)); break;
+            default: CG_PRJ(float, k_project_generic<float>); break;
+        }
+    }
+#undef CG_PRJ
+    return CG_OK;
+}
+
+}  // namespace cg

@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bins and permutations must match bit for bit; FP64 fields within 1e-12 and
+FP32 fields within 2e-6 relative (per cell / per particle, denominator
+max(|ref|, 1e-3 max|ref|), vectors by Euclidean norm).  Sizes span several
+4096-particle sort tiles with ragged tails, one- and two-pass sorts, and
+the benchmark's full packed-bed workload."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import (TOL_FP32, TOL_FP64, assert_close, inputs, to_dev, to_np, switch_mask)
+
+pytestmark = pytest.mark.gpu
+
+
+def run_step(cg, w, dt=0.0, eps_fine=True):
+    import torch
+    g = cg.Grids(w.desc)
+    pos, vel, uf = inputs(w)
+    out = g.alloc_outputs(w.n, eps_fine=eps_fine, bins=True)
+    g.cg_step(pos, vel, uf, out, dt=dt)
+    rc, flags, counts = g.cg_sync_status()
+    torch.cuda.synchronize()
+    host = {k: to_np(v) for k, v in out.items()}
+    host["pos_d"], host["vel"] = to_np(pos), to_np(vel)
+    host["rc"], host["flags"], host["counts"] = rc, flags, counts
+    g.close()
+    return host
+
+
+def compare_step(w, got, ref, tol, mask=None):
+    assert np.array_equal(got["cell"], ref["cell"]), "cells differ"
+    assert np.array_equal(got["cell_start"], ref["cell_start"]), "cell starts differ"
+    assert np.array_equal(got["perm"], ref["perm"]), "permutation differs"
+    errs = {}
+    errs["eps_bulk"] = assert_close("eps_bulk", got["eps_bulk"], ref["eps_bulk"], tol)
+    errs["u_bulk"] = assert_close("u_bulk", got["u_bulk"], ref["u_bulk"], tol, vec=True)
+    errs["var_bulk"] = assert_close("var_bulk", got["var_bulk"], ref["var_bulk"], tol)
+    errs["force"] = assert_close("force", got["force"], ref["force"], tol, vec=True, mask=mask)
+    if mask is None or mask.all():
+        errs["S_bulk"] = assert_close("S_bulk", got["S_bulk"], ref["S_bulk"], tol, vec=True)
+        errs["S_fine"] = assert_close("S_fine", got["S_fine"], ref["S_fine"], tol, vec=True)
+    if got.get("eps_fine") is not None and ref.get("eps_fine") is not None:
+        errs["eps_fine"] = assert_close("eps_fine", got["eps_fine"], ref["eps_fine"], tol)
+    return errs
+
+
+def compare_sums(got, ref, tol):
+    s, r = got["sums"], ref["sums"]
+    vol = abs(r[0])
+    fs = r[11]
+    assert abs(s[0] - r[0]) <= tol * vol and abs(s[1] - r[1]) <= tol * vol
+    for k in list(range(2, 11)) + [11]:
+        assert abs(s[k] - r[k]) <= tol * fs + 1e-300, (k, s[k], r[k])
+    # conservation on the device sums themselves
+    assert np.all(np.abs(s[2:5] + s[5:8]) <= 10 * tol * fs)
+    assert np.all(np.abs(s[5:8] - s[8:11]) <= 10 * tol * fs)
+    assert s[15] == r[15]
+
+
+# ------------------------------------------------------------------ FP64
+def test_tiny_fp64_step(cuda_lib):
+    w = synth.tiny(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    assert got["rc"] == 0 and got["counts"] == [0, 0, 0, 0]
+    compare_step(w, got, ref, TOL_FP64)
+    compare_sums(got, ref, 1e-12)
+
+
+def test_tiny_fp64_individual_entry_points(cuda_lib):
+    import torch
+    w = synth.tiny(seed=3, n=25_000)
+    d = w.desc
+    g = cuda_lib.Grids(d)
+    pos, vel, uf = inputs(w)
+    n = w.n
+    cell = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = torch.empty_like(cell)
+    cs = torch.empty(g.n_bulk + 1, dtype=torch.int32, device="cuda")
+    g.cg_bin_particles(pos, cell, perm, cs)
+    rc_cell, rc_perm, rc_cs, _ = oracle.bin(d, w.pos_d)
+    assert np.array_equal(to_np(cell), rc_cell)
+    assert np.array_equal(to_np(perm), rc_perm)
+    assert np.array_equal(to_np(cs), rc_cs)
+    eps = torch.empty(g.n_bulk, dtype=torch.float64, device="cuda")
+    g.cg_deposit(cuda_lib.CG_DEP_VOLUME, n, pos, eps)
+    r_eps, _ = oracle.deposit_volume(d, w.pos_d, rc_cs, rc_perm)
+    assert_close("eps", to_np(eps), r_eps, TOL_FP64)
+    ub = torch.empty(3, g.n_bulk, dtype=torch.float64, device="cuda")
+    var = torch.empty(g.n_bulk, dtype=torch.float64, device="cuda")
+    g.cg_average_fine_to_bulk(uf, ub, var)
+    r_ub, r_var = oracle.average(d, w.u_fine)
+    assert_close("u_bulk", to_np(ub), r_ub, TOL_FP64, vec=True)
+    assert_close("var", to_np(var), r_var, TOL_FP64)
+    # drag from the oracle's own bulk fields (isolates the drag step)
+    F = torch.empty(3, n, dtype=torch.float64, device="cuda")
+    S = torch.empty(3, g.n_bulk, dtype=torch.float64, device="cuda")
+    g.cg_drag(pos, vel, to_dev(r_eps), to_dev(r_ub), F, S)
+    r_F, _ = oracle.drag(d, w.pos_d, w.vel, r_eps, r_ub)
+    assert_close("force", to_np(F), r_F, TOL_FP64, vec=True)
+    r_S = oracle.deposit_momentum(d, r_F, rc_cs, rc_perm)
+    assert_close("S_bulk(fused)", to_np(S), r_S, TOL_FP64, vec=True)
+    # momentum deposit from caller-order forces
+    S2 = torch.empty_like(S)
+    g.cg_deposit(cuda_lib.CG_DEP_MOMENTUM, n, to_dev(r_F), S2)
+    assert_close("S_bulk(deposit)", to_np(S2), r_S, TOL_FP64, vec=True)
+    # projection of the oracle's bulk source
+    Sf = torch.empty(3, g.n_fine, dtype=torch.float64, device="cuda")
+    g.cg_project_bulk_to_fine(to_dev(r_S), Sf)
+    assert_close("S_fine", to_np(Sf), oracle.project(d, r_S), TOL_FP64, vec=True)
+    rc, flags, counts = g.cg_sync_status()
+    assert rc == 0
+    g.close()
+
+
+@pytest.mark.parametrize("r", [2, 3, 8])
+def test_ratios_fp64(cuda_lib, r):
+    nb = 6 if r != 8 else 4
+    w = synth.tiny(seed=r, n=7_777, fine=nb * r, ratio=r)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    compare_step(w, got, ref, TOL_FP64)
+    compare_sums(got, ref, 1e-12)
+
+
+def test_cell_value_interp_fp64(cuda_lib):
+    w = synth.tiny(seed=5, n=9_000)
+    w.desc["interp"] = synth.INTERP_CELL
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    compare_step(w, got, ref, TOL_FP64)
+
+
+# ------------------------------------------------------------------ FP32
+def test_tiny_fp32_step(cuda_lib):
+    w = synth.tiny(seed=1, n=50_000, fp64=False)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    compare_step(w, got, ref, TOL_FP32)
+    compare_sums(got, ref, TOL_FP32)
+
+
+def test_small_packed_bed_fp32(cuda_lib):
+    w = synth.small_packed_bed(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    mask = switch_mask(w, ref)
+    compare_step(w, got, ref, TOL_FP32, mask=mask)
+    if mask.all():
+        compare_sums(got, ref, TOL_FP32)
+
+
+def test_small_clustered_bed_fp32_with_euler(cuda_lib):
+    """One step with the Euler advance; parity of the advanced state is
+    checked from the shared initial state (trajectories are not compared
+    over many steps)."""
+    w = synth.small_clustered_bed(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, dt=w.dt, want_eps_fine=True)
+    got = run_step(cuda_lib, w, dt=w.dt)
+    compare_step(w, got, ref, TOL_FP32)
+    compare_sums(got, ref, 5 * TOL_FP32)
+    assert_close("vel", got["vel"][:, :3].T, ref["vel"][:, :3].T, TOL_FP32, vec=True)
+    assert_close("pos", got["pos_d"][:, :3].T, ref["pos_d"][:, :3].T, TOL_FP32, vec=True)
+    assert np.array_equal(got["pos_d"][:, 3], w.pos_d[:, 3])
+
+
+def test_packed_bed_full_size_fp32(cuda_lib):
+    """The benchmark's workload (4M particles, fine 256x256x512) at full size,
+    in the launch configuration the benchmark times."""
+    w = synth.packed_bed(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    mask = switch_mask(w, ref)
+    errs = compare_step(w, got, ref, TOL_FP32, mask=mask)
+    print("packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()},
+          "excluded at switch:", int((~mask).sum()))
+
+
+def test_repeat_is_bit_identical(cuda_lib):
+    w = synth.small_clustered_bed(seed=1)
+    a = run_step(cuda_lib, w)
+    b = run_step(cuda_lib, w)
+    for k in ["cell", "perm", "cell_start", "eps_bulk", "u_bulk", "var_bulk", "force", "S_bulk", "S_fine",
+              "sums"]:
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_host_entry_matches_device_entry(cuda_lib):
+    import torch
+    w = synth.small_packed_bed(seed=2)
+    dev = run_step(cuda_lib, w, eps_fine=False)
+    g = cuda_lib.Grids(w.desc)
+    out = {k: (v.cpu().pin_memory() if v is not None else None)
+           for k, v in g.alloc_outputs(w.n, bins=True).items()}
+    pos = torch.from_numpy(w.pos_d.copy()).pin_memory()
+    vel = torch.from_numpy(w.vel.copy()).pin_memory()
+    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).pin_memory()
+    g.cg_step_host(pos, vel, uf, out)
+    for k in ["cell", "perm", "cell_start", "eps_bulk", "u_bulk", "force", "S_bulk", "S_fine", "sums"]:
+        assert np.array_equal(out[k].numpy(), dev[k]), k
+    g.close()
+
+
+# ------------------------------------------------------------- edge cases
+def test_edge_empty_particle_set(cuda_lib):
+    w = synth.tiny(seed=0, n=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    assert np.all(got["cell_start"] == 0)
+    assert np.all(got["eps_bulk"] == 1.0)
+    assert np.all(got["S_bulk"] == 0.0) and np.all(got["S_fine"] == 0.0)
+    assert_close("u_bulk", got["u_bulk"], ref["u_bulk"], TOL_FP64, vec=True)
+    assert got["sums"][0] == 0.0 and got["sums"][2] == 0.0
+
+
+def test_edge_faces_outside_and_one_crowded_cell(cuda_lib):
+    """Particles exactly on bulk faces and on the upper domain faces, some
+    outside (clamped and counted), and 30,000 in a single cell (one long
+    segment across many sort tiles)."""
+    w = synth.tiny(seed=9, n=40_000, fine=32, ratio=4, fp64=False)
+    rng = np.random.default_rng(0)
+    pos = w.pos_d
+    H = 1.0 / 8
+    k = 5000
+    pos[:k, :3] = rng.integers(0, 9, (k, 3)) * H             # exactly on faces, incl. x = 1
+    pos[k:k + 100, 0] = -0.01                                 # outside below
+    pos[k + 100:k + 200, 2] = 1.02                            # outside above
+    pos[10_000:40_000, :3] = 0.3 + 0.01 * rng.random((30_000, 3))
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    assert got["counts"][0] == ref["outside"] == 200
+    assert got["flags"] & 1
+    # the crowded cell is over-packed: porosity < eps_min, clamped for the drag
+    compare_step(w, got, ref, TOL_FP32)
+    assert got["counts"][2] == int(ref["sums"][15])
+
+
+def test_edge_nonfinite_positions_are_reported(cuda_lib):
+    import torch
+    w = synth.tiny(seed=2, n=5_000, fp64=False)
+    w.pos_d[17, 0] = np.nan
+    w.pos_d[99, 2] = np.inf
+    g = cuda_lib.Grids(w.desc)
+    pos, vel, uf = inputs(w)
+    cell = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    g.cg_bin_particles(pos, cell)
+    rc, flags, counts = g.cg_sync_status()
+    assert rc == 7 and flags & 2 and counts[1] == 2
+    ref_cell, _, _, _ = oracle.bin(w.desc, w.pos_d)
+    assert np.array_equal(to_np(cell), ref_cell)
+    rc, flags, counts = g.cg_sync_status()    # read-and-clear
+    assert rc == 0 and flags == 0
+    g.close()
+
+
+def test_edge_minimal_grid_and_two_particles(cuda_lib):
+    desc = synth.make_desc((0.25, -1.0, 3.0), (0.5, 2.0, 1.0), (2, 4, 6), 1, fp64=True, law=1)
+    pos = np.array([[0.3, -0.5, 3.2, 0.01], [0.74, 0.99, 3.99, 0.02]])
+    vel = np.array([[0.1, 0.0, -0.1, 0.0], [0.0, 0.2, 0.0, 0.0]])
+    u = np.random.default_rng(1).normal(size=(3, 6, 4, 2))
+    w = synth.Workload("minimal", desc, pos, vel, u)
+    ref = oracle.step(desc, pos, vel, u, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    compare_step(w, got, ref, TOL_FP64)
+
+
+def test_not_binned_and_bad_args(cuda_lib):
+    import torch
+    w = synth.tiny(seed=0, n=100)
+    g = cuda_lib.Grids(w.desc)
+    pos, vel, uf = inputs(w)
+    eps = torch.empty(g.n_bulk, dtype=torch.float64, device="cuda")
+    with pytest.raises(cuda_lib.CgError) as e:
+        g.cg_deposit(cuda_lib.CG_DEP_VOLUME, w.n, pos, eps)
+    assert e.value.code == 4
+    L = cuda_lib.lib()
+    # misaligned particle array
+    assert L.cg_bin_particles(g.h, 10, pos.data_ptr() + 4, None, None, None) == 1
+    g.close()
