@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
+    ap.add_argument("--no-graph", action="store_true", help="time eager cg_step calls instead of a CUDA graph")
     return ap.parse_args()
 
 
@@ -188,24 +189,53 @@ def run_gb300(args):
     if rc != 0:
         raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
 
+    # launches of one step (counted eagerly; graph replays run the same kernels)
+    l0 = g.cg_launch_count()
+    g.cg_step(pos, vel, uf, out)
+    launches_per_step = g.cg_launch_count() - l0
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0 = time.time()
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        t1 = time.time()
+        barrier()
+        return e0.elapsed_time(e1), t0, t1
+
+    eager_ms, _, _ = timed(lambda: g.cg_step(pos, vel, uf, out), min(args.steps, 200))
+    eager_ms_step = eager_ms / min(args.steps, 200)
+    step_fn = lambda: g.cg_step(pos, vel, uf, out)
+    graph = None
+    if not args.no_graph:
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        g.set_stream(cs)
+        with torch.cuda.stream(cs):
+            g.cg_step(pos, vel, uf, out)
+        cs.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cs):
+            g.cg_step(pos, vel, uf, out)
+        g.set_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        step_fn = graph.replay
+        for _ in range(max(3, args.warmup)):
+            step_fn()
+        torch.cuda.synchronize()
+
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.35)
-    barrier()
-    l0 = g.cg_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.time()
-    e0.record()
-    for _ in range(args.steps):
-        g.cg_step(pos, vel, uf, out)
-    e1.record()
-    e1.synchronize()
-    t1 = time.time()
-    barrier()
-    launches = g.cg_launch_count() - l0
+    ms, t0, t1 = timed(step_fn, args.steps)
+    launches = launches_per_step * args.steps
     time.sleep(0.25)
     sampler.stop()
-    ms = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -230,7 +260,7 @@ def run_gb300(args):
     kern_total = {k: v[1] for k, v in prof.items()}
     tot = sum(kern_total.values())
     dominant = max(kern_total, key=kern_total.get)
-    launches_per_step = {k: v[0] / prof_steps for k, v in prof.items()}
+    kern_launches = {k: v[0] / prof_steps for k, v in prof.items()}
     dom_bytes = kern_bytes.get(dominant)
     roofline = None
     if dom_bytes is not None:
@@ -297,11 +327,15 @@ def run_gb300(args):
                        "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs {input_bytes / 1e6:.0f} MB > L2 (126 MB) per step, no flush",
+                       "timing": ("CUDA graph of one cg_step, replayed K times" if graph is not None
+                                  else "eager cg_step calls"),
+                       "eager_ms_per_step": round(eager_ms_step, 5),
+                       "launches_per_step": launches_per_step,
                        "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
                        "step_frac_of_hbm": round(step_gbs / peak, 4)},
             "roofline": roofline,
             "kernels": {k: {"ms_per_launch": round(kern_ms[k], 5), "share": round(kern_total[k] / tot, 4),
-                            "launches_per_step": launches_per_step[k]} for k in sorted(kern_total)},
+                            "launches_per_step": kern_launches[k]} for k in sorted(kern_total)},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),

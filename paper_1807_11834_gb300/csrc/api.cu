@@ -116,14 +116,14 @@ void prof_end(cg_grids* g, int slot, int ev) {
 // Buffers that grow with the particle count
 // ---------------------------------------------------------------------------
 cg_status ensure_partials(cg_grids* g, long long n) {
-    const long long bulk_blk = (g->gd.nbulk + 255) / 256;
+    const long long bulk_blk = (g->gd.nbulk + 7) / 8;   // cell kernels run 8 cells (warps) per block
     const long long fine_blk = (g->gd.nfine + 255) / 256;
-    const long long drag_blk = std::max(1LL, (n + 255) / 256);
+    (void)n;
     const long long proj_blk = (g->gd.r == 2 || g->gd.r == 4 || g->gd.r == 8) ? bulk_blk : fine_blk;
-    const long long need = bulk_blk * 1 + drag_blk * kDragSums + bulk_blk * 3 + proj_blk * 3;
+    const long long need = bulk_blk * 1 + bulk_blk * kDragCellSums + bulk_blk * 3 + proj_blk * 3;
     if (need > g->part_cap) {
         dfree(g->partials);
-        CG_TRY(dalloc(&g->partials, sizeof(double) * need));
+        CG_TRY(dalloc(&g->partials, 2 * g->tsize * need));
         g->part_cap = need;
     }
     g->part_off[PS_VOL] = 0;
@@ -141,8 +141,6 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     dfree(g->key1);
     dfree(g->val1);
     dfree(g->perm);
-    dfree(g->inv_perm);
-    dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
     g->cap = -1;
@@ -151,14 +149,11 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     CG_TRY(dalloc(&g->key1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->val1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->perm, sizeof(int32_t) * cap));
-    CG_TRY(dalloc(&g->inv_perm, sizeof(int32_t) * cap));
-    CG_TRY(dalloc(&g->Fs, 4 * g->tsize * cap));
     const long long ntiles = cap / kSortTile;
     const int maxbits = std::max(g->pass_bits[0], g->pass_bits[1]);
     g->hist_cap = ntiles << maxbits;
     CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
-    const long long scan_m = std::max(g->hist_cap, g->gd.nbulk + 1);
-    g->scan_cap = (scan_m + kScanItems - 1) / kScanItems;
+    g->scan_cap = (g->hist_cap + kScanItems - 1) / kScanItems + (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
     CG_TRY(dalloc(&g->scan_part, sizeof(int32_t) * g->scan_cap));
     g->cap = cap;
     return CG_OK;
@@ -190,8 +185,6 @@ static void free_all(cg_grids* g) {
     dfree(g->key1);
     dfree(g->val1);
     dfree(g->perm);
-    dfree(g->inv_perm);
-    dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
     dfree(g->cell_start);
@@ -370,7 +363,7 @@ cg_status cg_deposit(cg_grids* g, int32_t kind, int64_t n, const void* per_parti
     if (kind == CG_DEP_VOLUME && n > 0 && !aligned16(per_particle)) return CG_ERR_INVALID_ARG;
     if (g->n_binned != n) return CG_ERR_NOT_BINNED;
     if (kind == CG_DEP_VOLUME) return launch_deposit_volume(g, n, per_particle, (double*)bulk_out, false);
-    return launch_deposit_momentum(g, n, per_particle, false, bulk_out, false);
+    return launch_deposit_momentum(g, n, per_particle, bulk_out);
 }
 
 cg_status cg_average_fine_to_bulk(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk) {
@@ -389,9 +382,7 @@ cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel, co
     if (S_bulk_out && g->n_binned != n) return CG_ERR_NOT_BINNED;
     CG_TRY(ensure_particle_capacity(g, n));
     CG_TRY(launch_pack(g, eps_bulk, u_bulk, false));
-    CG_TRY(launch_drag(g, n, pos_d, vel, force_out, S_bulk_out != nullptr, false, 0.0));
-    if (S_bulk_out) CG_TRY(launch_deposit_momentum(g, n, nullptr, true, S_bulk_out, false));
-    return CG_OK;
+    return launch_drag(g, n, pos_d, vel, force_out, S_bulk_out, false, 0.0);
 }
 
 cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, void* fine_out) {
@@ -416,9 +407,7 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     CG_TRY(launch_deposit_volume(g, n, p->pos_d, o->eps_bulk, true));
     CG_TRY(launch_average(g, u_fine, o->u_bulk, o->var_bulk));
     CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
-    CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, true, true, dt));
-    if (n == 0) g->part_blocks[PS_DRAG] = 0;
-    CG_TRY(launch_deposit_momentum(g, n, nullptr, true, o->S_bulk, true));
+    CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
     const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, g->eps_t};
     void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, o->eps_fine};

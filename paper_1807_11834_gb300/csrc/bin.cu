@@ -46,8 +46,6 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
     for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
     int n_out = 0, n_nf = 0;
     const long long base = (long long)blockIdx.x * kSortTile;
 #pragma unroll 4
@@ -63,15 +61,10 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
             n_out += outside;
             key[p] = c;
         }
-        // warp-aggregated per-cell count (integer: order-independent)
-        unsigned peers = __match_any_sync(0xffffffffu, c);
-        int before = __popc(peers & lt);
-        if (valid && before == 0) atomicAdd(&count[c], __popc(peers));
-        int d = valid ? (c & (R - 1)) : -1;
-        unsigned dpeers = __match_any_sync(0xffffffffu, d);
-        if (valid && __popc(dpeers & lt) == 0) atomicAdd(&sh[d], __popc(dpeers));
+        // per-cell count: integer atomics, order-independent
+        if (valid) atomicAdd(&count[c], 1);
+        if (valid) atomicAdd(&sh[c & (R - 1)], 1);
     }
-    (void)lane;
     if (n_out) atomicAdd(&s_cnt[0], n_out);
     if (n_nf) atomicAdd(&s_cnt[1], n_nf);
     __syncthreads();
@@ -87,15 +80,12 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
     const int R = 1 << bits;
     for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    const unsigned lt = lanemask_lt();
     const long long base = (long long)blockIdx.x * kSortTile;
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
         bool valid = p < n;
-        int d = valid ? ((__ldg(keys + p) >> shift) & (R - 1)) : -1;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && __popc(peers & lt) == 0) atomicAdd(&sh[d], __popc(peers));
+        if (valid) atomicAdd(&sh[(__ldg(keys + p) >> shift) & (R - 1)], 1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blockIdx.x] = sh[i];
@@ -107,8 +97,7 @@ template <bool FIRST, bool FINAL>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
               int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
-              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
-              int32_t* __restrict__ perm, int32_t* __restrict__ inv_perm) {
+              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm) {
     extern __shared__ int cnt[];  // [kSortWarps][R]
     const int R = 1 << bits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -118,13 +107,19 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
     const unsigned lt = lanemask_lt();
     const long long base = (long long)blockIdx.x * kSortTile + (long long)warp * (kSortTile / kSortWarps);
     int kv[kSortItems], vv[kSortItems], rk[kSortItems];
+    // all loads of the slice first, so they are in flight together
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + k * 32 + lane;
         bool valid = p < n;
-        int kk = valid ? __ldg(keys_in + p) : 0;
-        int v = 0;
-        if (valid) v = FIRST ? (int)p : __ldg(vals_in + p);
+        kv[k] = valid ? __ldg(keys_in + p) : 0;
+        vv[k] = valid ? (FIRST ? (int)p : __ldg(vals_in + p)) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        bool valid = p < n;
+        int kk = kv[k];
         int d = valid ? ((kk >> shift) & (R - 1)) : -1;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = __popc(peers & lt);
@@ -132,8 +127,6 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
         __syncwarp();
         if (valid && before == 0) wc[d] = c0 + __popc(peers);
         __syncwarp();
-        kv[k] = kk;
-        vv[k] = v;
         rk[k] = c0 + before;
     }
     __syncthreads();
@@ -155,7 +148,6 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
             int dst = wc[d] + rk[k];
             if (FINAL) {
                 perm[dst] = vv[k];
-                inv_perm[vv[k]] = dst;
             } else {
                 keys_out[dst] = kv[k];
                 vals_out[dst] = vv[k];
@@ -208,60 +200,90 @@ __device__ __forceinline__ void load16(const int32_t* __restrict__ in, long long
     }
 }
 
-__global__ void __launch_bounds__(256) k_scan_reduce(const int32_t* __restrict__ in, long long m,
-                                                     int32_t* __restrict__ part) {
+// Up to two independent arrays are scanned by one pair of launches: blocks
+// [0, nA) cover array A, blocks [nA, nA + nB) array B.
+struct ScanJob {
+    const int32_t* in[2];
+    int32_t* out[2];
+    long long m[2];
+    long long nblk[2];
+};
+
+__device__ __forceinline__ void scan_locate(const ScanJob& j, int& which, long long& blk) {
+    blk = blockIdx.x;
+    which = 0;
+    if (blk >= j.nblk[0]) {
+        blk -= j.nblk[0];
+        which = 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restrict__ part) {
     __shared__ int shw[32];
-    long long start = (long long)blockIdx.x * kScanItems + threadIdx.x * 16;
+    int which;
+    long long blk;
+    scan_locate(j, which, blk);
+    long long start = blk * kScanItems + threadIdx.x * 16;
     int v[16];
-    load16(in, start, m, v);
+    load16(j.in[which], start, j.m[which], v);
     int s = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s += v[j];
+    for (int k = 0; k < 16; ++k) s += v[k];
     int total;
     block_exclusive_scan(s, shw, total);
     if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-// Single-block exclusive scan of part[0..nb) in place (any length).
-__global__ void __launch_bounds__(1024) k_scan_top(int32_t* __restrict__ part, long long nb) {
+// Each block sums the partials of the blocks before it in its array (a few
+// thousand at most), then scans its own chunk: no third launch.
+__global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __restrict__ part) {
     __shared__ int shw[32];
-    int carry = 0;
-    for (long long s0 = 0; s0 < nb; s0 += 1024) {
-        long long i = s0 + threadIdx.x;
-        int v = i < nb ? part[i] : 0;
-        int total;
-        int ex = block_exclusive_scan(v, shw, total);
-        if (i < nb) part[i] = carry + ex;
-        carry += total;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_scan_down(const int32_t* in, long long m,
-                                                   const int32_t* __restrict__ part, int32_t* out) {
-    __shared__ int shw[32];
-    long long start = (long long)blockIdx.x * kScanItems + threadIdx.x * 16;
+    __shared__ int s_base;
+    int which;
+    long long blk;
+    scan_locate(j, which, blk);
+    const long long first = which ? j.nblk[0] : 0;
+    int acc = 0;
+    for (long long i = threadIdx.x; i < blk; i += blockDim.x) acc += part[first + i];
+    int tot;
+    block_exclusive_scan(acc, shw, tot);
+    if (threadIdx.x == 0) s_base = tot;
+    __syncthreads();
+    const int base = s_base;
+    long long start = blk * kScanItems + threadIdx.x * 16;
     int v[16];
-    load16(in, start, m, v);
+    load16(j.in[which], start, j.m[which], v);
     int s = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) s += v[j];
+    for (int k = 0; k < 16; ++k) s += v[k];
     int total;
-    int ex = block_exclusive_scan(s, shw, total) + part[blockIdx.x];
+    int ex = block_exclusive_scan(s, shw, total) + base;
+    int32_t* out = j.out[which];
+    const long long m = j.m[which];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (start + j < m) out[start + j] = ex;
-        ex += v[j];
+    for (int k = 0; k < 16; ++k) {
+        if (start + k < m) out[start + k] = ex;
+        ex += v[k];
     }
 }
 
-// out may alias in.
-static cg_status scan_exclusive(cg_grids* g, const int32_t* in, int32_t* out, long long m) {
-    if (m <= 0) return CG_OK;
-    long long nblk = (m + kScanItems - 1) / kScanItems;
+// Exclusive scans of one or two arrays (out may alias in).
+static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA, long long mA,
+                                 const int32_t* inB, int32_t* outB, long long mB) {
+    ScanJob j;
+    j.in[0] = inA;
+    j.out[0] = outA;
+    j.m[0] = mA;
+    j.in[1] = inB;
+    j.out[1] = outB;
+    j.m[1] = inB ? mB : 0;
+    j.nblk[0] = (mA + kScanItems - 1) / kScanItems;
+    j.nblk[1] = (j.m[1] + kScanItems - 1) / kScanItems;
+    const long long nblk = j.nblk[0] + j.nblk[1];
+    if (nblk == 0) return CG_OK;
     if (nblk > g->scan_cap) return CG_ERR_OUT_OF_RANGE;
-    CG_LAUNCH(g, "bin_scan", k_scan_reduce, (unsigned)nblk, 256, 0, in, m, g->scan_part);
-    CG_LAUNCH(g, "bin_scan", k_scan_top, 1, 1024, 0, g->scan_part, nblk);
-    CG_LAUNCH(g, "bin_scan", k_scan_down, (unsigned)nblk, 256, 0, in, m, g->scan_part, out);
+    CG_LAUNCH(g, "bin_scan", k_scan_reduce, (unsigned)nblk, 256, 0, j, g->scan_part);
+    CG_LAUNCH(g, "bin_scan", k_scan_down, (unsigned)nblk, 256, 0, j, g->scan_part);
     return CG_OK;
 }
 
@@ -269,7 +291,7 @@ static bool g_attr_done = false;
 
 static cg_status set_attrs() {
     if (g_attr_done) return CG_OK;
-    const int smem = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);
+    const int smem = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);   // 128 KB at 16 warps x 2^11
     CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -300,22 +322,21 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
     else
         CG_LAUNCH(g, "bin_key", k_bin_key<float>, ntiles, kSortThreads, sizeof(int) << b0,
                   (const float*)pos_d, n, g->gd, g->key, g->cell_start, g->hist, ntiles, b0, g->status);
-    CG_TRY(scan_exclusive(g, g->cell_start, g->cell_start, nbulk + 1));
-    CG_TRY(scan_exclusive(g, g->hist, g->hist, m0));
+    CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
     const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
     if (!two) {
         CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true>), ntiles, kSortThreads, smem0,
-                  g->key, nullptr, n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm, g->inv_perm);
+                  g->key, nullptr, n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm);
     } else {
         CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false>), ntiles, kSortThreads, smem0,
-                  g->key, nullptr, n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr, nullptr);
+                  g->key, nullptr, n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr);
         const long long m1 = (long long)ntiles << b1;
         CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1,
                   g->key1, n, ntiles, b0, b1, g->hist);
-        CG_TRY(scan_exclusive(g, g->hist, g->hist, m1));
+        CG_TRY(scan_exclusive2(g, g->hist, g->hist, m1, nullptr, nullptr, 0));
         const size_t smem1 = (size_t)kSortWarps * sizeof(int) << b1;
         CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true>), ntiles, kSortThreads, smem1,
-                  g->key1, g->val1, n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm, g->inv_perm);
+                  g->key1, g->val1, n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm);
     }
     g->n_binned = n;
     return CG_OK;

@@ -16,8 +16,8 @@ namespace cg {
 // ----------------------------------------------------------------------
 // Sizes
 // ----------------------------------------------------------------------
-constexpr int kSortThreads = 256;                   // threads of a sort tile
-constexpr int kSortItems = 16;                      // items per thread
+constexpr int kSortThreads = 512;                   // threads of a sort tile
+constexpr int kSortItems = 8;                       // items per thread
 constexpr int kSortTile = kSortThreads * kSortItems; // 4096 particles per tile
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxDigitBits = 11;                   // radix digit of one pass
@@ -31,6 +31,7 @@ enum { ST_FLAGS = 0, ST_OUTSIDE = 1, ST_NONFINITE = 2, ST_CLAMPED = 3, ST_TIMEOU
 // Partial-sum regions of the conservation sums.
 enum { PS_VOL = 0, PS_DRAG = 1, PS_MOM = 2, PS_PROJ = 3, PS_NREG = 4 };
 constexpr int kDragSums = 9;   // V_p, F(3), |F|, m u (3), clamped count
+constexpr int kDragCellSums = kDragSums + 3;   // + S_B V_B (3) in the cell-order drag
 
 // ----------------------------------------------------------------------
 // Device-side view of the grid geometry (passed by value to kernels)
@@ -98,9 +99,6 @@ struct cg_grids {
     int32_t* key1 = nullptr;       // [cap] keys after pass 1
     int32_t* val1 = nullptr;       // [cap] particle ids after pass 1
     int32_t* perm = nullptr;       // [cap] particle ids in cell order
-    int32_t* inv_perm = nullptr;   // [cap] sorted position of each particle
-    int32_t* key_sorted = nullptr; // [cap] cell of each sorted slot
-    void* Fs = nullptr;            // [cap] T4 drag force in cell order
     int32_t* hist = nullptr;       // [2^digit * ntiles]
     int32_t* scan_part = nullptr;  // scan block partials
     long long hist_cap = 0, scan_cap = 0;
@@ -109,7 +107,7 @@ struct cg_grids {
     int32_t* cell_start = nullptr; // [nbulk + 1]
     void* bulk4 = nullptr;         // [nbulk] T4: phi, u_x, u_y, u_z
     void* eps_t = nullptr;         // [nbulk] T: porosity in the path precision
-    double* partials = nullptr;    // conservation-sum block partials
+    void* partials = nullptr;      // conservation-sum block partials: (s, c) pairs of T
     long long part_off[cg::PS_NREG] = {0, 0, 0, 0};
     long long part_blocks[cg::PS_NREG] = {0, 0, 0, 0};
     long long part_cap = 0;
@@ -174,14 +172,15 @@ cg_status ensure_partials(cg_grids* g, long long n);
 
 cg_status launch_bin(cg_grids* g, long long n, const void* pos_d);
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums);
-cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, bool sorted,
-                                  void* S_bulk, bool sums);
+cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk);
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk);
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
-cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force,
-                      bool fused, bool sums, double dt);
+cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
+                      bool sums, double dt);
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);
 cg_status launch_sums(cg_grids* g, double* sums);
+// First element (in units of T) of the partial region r.
+inline void* part_ptr(cg_grids* g, int r) { return (char*)g->partials + 2 * g->tsize * g->part_off[r]; }
 
 }  // namespace cg
 
@@ -254,10 +253,12 @@ __device__ __forceinline__ CSum<T> warp_reduce(CSum<T> v) {
     return v;
 }
 
-// Block-level deterministic reduction of K compensated sums; thread 0
-// writes part[k * stride + blockIdx.x] as double (each block one column).
+// Block-level deterministic reduction of K compensated sums.  Thread 0..K-1
+// writes the pair (s, c) of sum k to part[2 * (k * stride + blockIdx.x)]:
+// partials stay in the path precision as compensated pairs, so no FP64
+// arithmetic runs per block (GB300's FP64 rate is a small fraction of FP32).
 template <typename T, int K>
-__device__ __forceinline__ void block_sums(CSum<T> (&v)[K], double* __restrict__ part, long long stride) {
+__device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part, long long stride) {
     __shared__ T sh_s[K][32];
     __shared__ T sh_c[K][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -281,7 +282,9 @@ __device__ __forceinline__ void block_sums(CSum<T> (&v)[K], double* __restrict__
             o.c = sh_c[k][w];
             a.merge(o);
         }
-        part[(long long)k * stride + blockIdx.x] = (double)a.s + (double)a.c;
+        T* dst = part + 2 * ((long long)k * stride + blockIdx.x);
+        dst[0] = a.s;
+        dst[1] = a.c;
     }
 }
 

@@ -22,88 +22,64 @@ template <> __device__ __forceinline__ float pi_over_6<float>() { return 0.52359
 template <> __device__ __forceinline__ double pi_over_6<double>() { return 0.52359877559829887308; }
 
 // ----------------------------------------------------------------------
-// Porosity
+// Porosity: one warp per bulk cell, lanes strided over the cell's stable
+// segment, compensated per-lane sums combined by a fixed xor tree.
 // ----------------------------------------------------------------------
+constexpr int kDepWarps = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kDepWarps)
 k_deposit_volume(const T* __restrict__ pos, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps,
-                 double* __restrict__ part, long long pstride, int do_sums) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                 T* __restrict__ part, long long pstride, int do_sums) {
+    const int lane = threadIdx.x & 31;
+    const long long c = (long long)blockIdx.x * kDepWarps + (threadIdx.x >> 5);
     CSum<T> cell_sum;
     if (c < g.nbulk) {
         const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
-        int i = b;
-        // 4-way unrolled gather to keep several loads in flight
-        for (; i + 4 <= e; i += 4) {
-            int p0 = __ldg(perm + i), p1 = __ldg(perm + i + 1), p2 = __ldg(perm + i + 2), p3 = __ldg(perm + i + 3);
-            T d0 = __ldg(pos + 4 * (long long)p0 + 3), d1 = __ldg(pos + 4 * (long long)p1 + 3);
-            T d2 = __ldg(pos + 4 * (long long)p2 + 3), d3 = __ldg(pos + 4 * (long long)p3 + 3);
-            cell_sum.add(pi_over_6<T>() * d0 * d0 * d0);
-            cell_sum.add(pi_over_6<T>() * d1 * d1 * d1);
-            cell_sum.add(pi_over_6<T>() * d2 * d2 * d2);
-            cell_sum.add(pi_over_6<T>() * d3 * d3 * d3);
-        }
-        for (; i < e; ++i) {
-            T d = __ldg(pos + 4 * (long long)__ldg(perm + i) + 3);
+        for (int i = b + lane; i < e; i += 32) {
+            const T d = __ldg(pos + 4 * (long long)__ldg(perm + i) + 3);
             cell_sum.add(pi_over_6<T>() * d * d * d);
         }
-        const double vol = (double)cell_sum.s + (double)cell_sum.c;
-        eps[c] = 1.0 - vol * g.invVB;
+        if (b != e) cell_sum = warp_reduce(cell_sum);
+        if (lane == 0) eps[c] = 1.0 - ((double)cell_sum.s + (double)cell_sum.c) * g.invVB;
     }
     if (do_sums) {
-        CSum<T> v[1] = {cell_sum};
+        CSum<T> v[1];
+        if (lane == 0) v[0] = cell_sum;
         block_sums<T, 1>(v, part, pstride);
     }
 }
 
 // ----------------------------------------------------------------------
-// Reaction source from the drag forces
-//   SORTED: forces already in bin order as T4 (the fused drag output)
-//   else  : caller-order SoA forces gathered through perm
+// Reaction source from caller-order SoA forces, gathered through perm (one
+// warp per cell as above).  Inside the coupling step the reaction is fused
+// into the cell-order drag instead.
 // ----------------------------------------------------------------------
-template <typename T, bool SORTED>
-__global__ void __launch_bounds__(256)
-k_deposit_momentum(const T* __restrict__ Fs, const T* __restrict__ F, long long n,
-                   const int32_t* __restrict__ perm, const int32_t* __restrict__ cs, GridDev g,
-                   T* __restrict__ S, double* __restrict__ part, long long pstride, int do_sums) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T>
+__global__ void __launch_bounds__(32 * kDepWarps)
+k_deposit_momentum(const T* __restrict__ F, long long n, const int32_t* __restrict__ perm,
+                   const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const long long c = (long long)blockIdx.x * kDepWarps + (threadIdx.x >> 5);
+    if (c >= g.nbulk) return;
     CSum<T> a[3];
-    CSum<T> sv[3];
-    if (c < g.nbulk) {
-        const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
-        for (int i = b; i < e; ++i) {
-            if (SORTED) {
-                V4<T> f = ld4(Fs, i);
-                a[0].add(f.x);
-                a[1].add(f.y);
-                a[2].add(f.z);
-            } else {
-                const long long p = __ldg(perm + i);
-                a[0].add(__ldg(F + p));
-                a[1].add(__ldg(F + n + p));
-                a[2].add(__ldg(F + 2 * n + p));
-            }
-        }
+    const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
+    for (int i = b + lane; i < e; i += 32) {
+        const long long p = __ldg(perm + i);
+        a[0].add(__ldg(F + p));
+        a[1].add(__ldg(F + n + p));
+        a[2].add(__ldg(F + 2 * n + p));
+    }
+    if (b != e)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] = warp_reduce(a[k]);
+    if (lane == 0)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            T s;
-            if (sizeof(T) == 4) s = -(a[k].get()) * (T)g.invVBf;
-            else s = -(a[k].get()) * (T)g.invVB;
-            S[k * g.nbulk + c] = s;
-            // S_B V_B as an exact float-float product, V_B split in two
-            if (sizeof(T) == 4) {
-                T hi = s * (T)g.VBh;
-                T lo = fma(s, (T)g.VBh, -hi);
-                lo = fma(s, (T)g.VBl, lo);
-                sv[k].add(hi);
-                sv[k].c += lo;
-            } else {
-                sv[k].add(s * (T)g.VB);
-            }
+            if (sizeof(T) == 4) S[k * g.nbulk + c] = -(a[k].get()) * (T)g.invVBf;
+            else S[k * g.nbulk + c] = -(a[k].get()) * (T)g.invVB;
         }
-    }
-    if (do_sums) block_sums<T, 3>(sv, part, pstride);
 }
 
 // ----------------------------------------------------------------------
@@ -125,37 +101,42 @@ k_pack(const double* __restrict__ eps, const T* __restrict__ u, GridDev g, T* __
 // Final FP64 reduction of the block partials (one block, fixed order)
 // ----------------------------------------------------------------------
 struct SumsMap {
-    long long off[CG_NSUMS];     // offset of the partial column, -1 = not computed
+    long long off[CG_NSUMS];     // first pair of the partial column, -1 = not computed
     long long cnt[CG_NSUMS];     // number of partials
 };
 
-__global__ void __launch_bounds__(256) k_sums(const double* __restrict__ part, SumsMap map,
-                                              double* __restrict__ sums) {
-    __shared__ double sh_s[8], sh_c[8];
+// One block per sum: merge the compensated pairs in a fixed order (strided
+// per thread, then a fixed tree), convert the final pair to double.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMap map, double* __restrict__ sums) {
+    __shared__ T sh_s[8], sh_c[8];
+    const int k = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 0; k < CG_NSUMS; ++k) {
-        CSum<double> a;
-        if (map.off[k] >= 0)
-            for (long long i = threadIdx.x; i < map.cnt[k]; i += blockDim.x) a.add(part[map.off[k] + i]);
-        a = warp_reduce(a);
-        if (lane == 0) {
-            sh_s[warp] = a.s;
-            sh_c[warp] = a.c;
+    CSum<T> a;
+    if (map.off[k] >= 0)
+        for (long long i = threadIdx.x; i < map.cnt[k]; i += blockDim.x) {
+            CSum<T> o;
+            o.s = part[2 * (map.off[k] + i)];
+            o.c = part[2 * (map.off[k] + i) + 1];
+            a.merge(o);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            CSum<double> t;
-            t.s = sh_s[0];
-            t.c = sh_c[0];
-            for (int w = 1; w < 8; ++w) {
-                CSum<double> o;
-                o.s = sh_s[w];
-                o.c = sh_c[w];
-                t.merge(o);
-            }
-            sums[k] = map.off[k] >= 0 ? t.get() : __longlong_as_double(0x7ff8000000000000LL);
+    a = warp_reduce(a);
+    if (lane == 0) {
+        sh_s[warp] = a.s;
+        sh_c[warp] = a.c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CSum<T> t;
+        t.s = sh_s[0];
+        t.c = sh_c[0];
+        for (int w = 1; w < 8; ++w) {
+            CSum<T> o;
+            o.s = sh_s[w];
+            o.c = sh_c[w];
+            t.merge(o);
         }
-        __syncthreads();
+        sums[k] = map.off[k] >= 0 ? (double)t.s + (double)t.c : __longlong_as_double(0x7ff8000000000000LL);
     }
 }
 
@@ -166,42 +147,26 @@ static inline unsigned blocks_for(long long n, int per) { return (unsigned)((n +
 
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums) {
     (void)n;
-    const unsigned nblk = blocks_for(g->gd.nbulk, 256);
-    double* part = g->partials + g->part_off[PS_VOL];
+    const unsigned nblk = blocks_for(g->gd.nbulk, kDepWarps);
+    void* part = part_ptr(g, PS_VOL);
     g->part_blocks[PS_VOL] = sums ? (long long)nblk : -1;
     if (g->fp64)
-        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<double>, nblk, 256, 0, (const double*)pos_d, g->perm,
-                  g->cell_start, g->gd, eps, part, (long long)nblk, (int)sums);
+        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<double>, nblk, 32 * kDepWarps, 0, (const double*)pos_d, g->perm,
+                  g->cell_start, g->gd, eps, (double*)part, (long long)nblk, (int)sums);
     else
-        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<float>, nblk, 256, 0, (const float*)pos_d, g->perm,
-                  g->cell_start, g->gd, eps, part, (long long)nblk, (int)sums);
+        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<float>, nblk, 32 * kDepWarps, 0, (const float*)pos_d, g->perm,
+                  g->cell_start, g->gd, eps, (float*)part, (long long)nblk, (int)sums);
     return CG_OK;
 }
 
-cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, bool sorted, void* S_bulk,
-                                  bool sums) {
-    const unsigned nblk = blocks_for(g->gd.nbulk, 256);
-    double* part = g->partials + g->part_off[PS_MOM];
-    g->part_blocks[PS_MOM] = sums ? (long long)nblk : -1;
-    if (g->fp64) {
-        if (sorted)
-            CG_LAUNCH(g, "deposit_momentum", (k_deposit_momentum<double, true>), nblk, 256, 0,
-                      (const double*)g->Fs, nullptr, n, g->perm, g->cell_start, g->gd, (double*)S_bulk, part,
-                      (long long)nblk, (int)sums);
-        else
-            CG_LAUNCH(g, "deposit_momentum", (k_deposit_momentum<double, false>), nblk, 256, 0, nullptr,
-                      (const double*)force_soa, n, g->perm, g->cell_start, g->gd, (double*)S_bulk, part,
-                      (long long)nblk, (int)sums);
-    } else {
-        if (sorted)
-            CG_LAUNCH(g, "deposit_momentum", (k_deposit_momentum<float, true>), nblk, 256, 0,
-                      (const float*)g->Fs, nullptr, n, g->perm, g->cell_start, g->gd, (float*)S_bulk, part,
-                      (long long)nblk, (int)sums);
-        else
-            CG_LAUNCH(g, "deposit_momentum", (k_deposit_momentum<float, false>), nblk, 256, 0, nullptr,
-                      (const float*)force_soa, n, g->perm, g->cell_start, g->gd, (float*)S_bulk, part,
-                      (long long)nblk, (int)sums);
-    }
+cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk) {
+    const unsigned nblk = blocks_for(g->gd.nbulk, kDepWarps);
+    if (g->fp64)
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<double>, nblk, 32 * kDepWarps, 0, (const double*)force_soa, n,
+                  g->perm, g->cell_start, g->gd, (double*)S_bulk);
+    else
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<float>, nblk, 32 * kDepWarps, 0, (const float*)force_soa, n,
+                  g->perm, g->cell_start, g->gd, (float*)S_bulk);
     return CG_OK;
 }
 
@@ -232,13 +197,16 @@ cg_status launch_sums(cg_grids* g, double* sums) {
     col(1, PS_VOL, 0);
     for (int a = 0; a < 3; ++a) {
         col(2 + a, PS_DRAG, 1 + a);
-        col(5 + a, PS_MOM, a);
+        col(5 + a, PS_DRAG, kDragSums + a);
         col(8 + a, PS_PROJ, a);
         col(12 + a, PS_DRAG, 5 + a);
     }
     col(11, PS_DRAG, 4);
     col(15, PS_DRAG, 8);
-    CG_LAUNCH(g, "sums", k_sums, 1, 256, 0, g->partials, m, sums);
+    if (g->fp64)
+        CG_LAUNCH(g, "sums", k_sums<double>, CG_NSUMS, 256, 0, (const double*)g->partials, m, sums);
+    else
+        CG_LAUNCH(g, "sums", k_sums<float>, CG_NSUMS, 256, 0, (const float*)g->partials, m, sums);
     return CG_OK;
 }
 

@@ -182,7 +182,7 @@ template <typename T, int RC>
 __global__ void __launch_bounds__(256)
 k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
           const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0, T* __restrict__ out1,
-          T* __restrict__ out2, T* __restrict__ out3, double* __restrict__ part, long long pstride,
+          T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part, long long pstride,
           int do_sums) {
     const long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     CSum<T> sacc[3];
@@ -200,13 +200,24 @@ k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restr
             const T* __restrict__ B = c == 0 ? in0 : c == 1 ? in1 : c == 2 ? in2 : in3;
             T* __restrict__ O = c == 0 ? out0 : c == 1 ? out1 : c == 2 ? out2 : out3;
             T f[3][3][3];   // [z][y][x]
+            if (g.interp == CG_INTERP_CELL) {
+                // cell values: every nested fine cell takes its bulk cell's value
+                const T v0 = __ldg(B + cb);
 #pragma unroll
-            for (int z = 0; z < 3; ++z)
+                for (int z = 0; z < 3; ++z)
 #pragma unroll
-                for (int y = 0; y < 3; ++y)
+                    for (int y = 0; y < 3; ++y)
 #pragma unroll
-                    for (int x = 0; x < 3; ++x)
-                        f[z][y][x] = __ldg(B + xs[x] + (long long)nbx * (ys[y] + (long long)nby * zs[z]));
+                        for (int x = 0; x < 3; ++x) f[z][y][x] = v0;
+            } else {
+#pragma unroll
+                for (int z = 0; z < 3; ++z)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y)
+#pragma unroll
+                        for (int x = 0; x < 3; ++x)
+                            f[z][y][x] = __ldg(B + xs[x] + (long long)nbx * (ys[y] + (long long)nby * zs[z]));
+            }
             CSum<T> rowsum;
 #pragma unroll
             for (int az = 0; az < RC; ++az) {
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(256)
 k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
                   const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0,
                   T* __restrict__ out1, T* __restrict__ out2, T* __restrict__ out3,
-                  double* __restrict__ part, long long pstride, int do_sums) {
+                  T* __restrict__ part, long long pstride, int do_sums) {
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     CSum<T> sacc[3];
     if (f < g.nfine) {
@@ -273,7 +284,8 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
         for (int a = 0; a < 3; ++a) {
             const int I = fi[a] / r, off = fi[a] - I * r;
             const int num = 2 * off + 1 - r;
-            if (num < 0) { lo[a] = max(I - 1, 0); hi[a] = I; w[a] = (T)(num + 2 * r) / (T)(2 * r); }
+            if (g.interp == CG_INTERP_CELL) { lo[a] = hi[a] = I; w[a] = T(0); }
+            else if (num < 0) { lo[a] = max(I - 1, 0); hi[a] = I; w[a] = (T)(num + 2 * r) / (T)(2 * r); }
             else { lo[a] = I; hi[a] = min(I + 1, g.nb[a] - 1); w[a] = (T)num / (T)(2 * r); }
         }
         const long long nbx = g.nb[0], nbxy = (long long)g.nb[0] * g.nb[1];
@@ -329,14 +341,14 @@ cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* va
 }
 
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums) {
-    double* part = g->partials + g->part_off[PS_PROJ];
+    void* part = part_ptr(g, PS_PROJ);
     const int r = g->gd.r;
     const bool fast = (r == 2 || r == 4 || r == 8);
     const unsigned nblk = fast ? blocks_of(g->gd.nbulk, 256) : blocks_of(g->gd.nfine, 256);
     g->part_blocks[PS_PROJ] = sums ? (long long)nblk : -1;
 #define CG_PRJ(T, KER)                                                                                   \
     CG_LAUNCH(g, "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2],        \
-              (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], part,       \
+              (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], (T*)part,   \
               (long long)nblk, (int)sums)
     if (g->fp64) {
         switch (r) {

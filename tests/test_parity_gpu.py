@@ -162,8 +162,16 @@ def test_small_clustered_bed_fp32_with_euler(cuda_lib):
     got = run_step(cuda_lib, w, dt=w.dt)
     compare_step(w, got, ref, TOL_FP32)
     compare_sums(got, ref, 5 * TOL_FP32)
-    assert_close("vel", got["vel"][:, :3].T, ref["vel"][:, :3].T, TOL_FP32, vec=True)
-    assert_close("pos", got["pos_d"][:, :3].T, ref["pos_d"][:, :3].T, TOL_FP32, vec=True)
+    # u_new = u + dt (F/m + g): drag and gravity cancel for some particles, so
+    # the bound is relative to the magnitude of the terms, not of the result
+    d = w.pos_d[:, 3].astype(np.float64)
+    m = w.desc["rho_p"] * np.pi * d ** 3 / 6.0
+    scale_u = np.abs(w.vel[:, :3]).sum(axis=1) + w.dt * (np.linalg.norm(ref["force"], axis=0) / m + 9.81)
+    du = np.linalg.norm(got["vel"][:, :3].astype(np.float64) - ref["vel"][:, :3], axis=1)
+    assert np.max(du / scale_u) <= TOL_FP32, np.max(du / scale_u)
+    scale_x = np.abs(w.pos_d[:, :3].astype(np.float64)).max(axis=1) + w.dt * np.linalg.norm(ref["vel"][:, :3], axis=1)
+    dx = np.abs(got["pos_d"][:, :3].astype(np.float64) - ref["pos_d"][:, :3]).max(axis=1)
+    assert np.max(dx / scale_x) <= TOL_FP32, np.max(dx / scale_x)
     assert np.array_equal(got["pos_d"][:, 3], w.pos_d[:, 3])
 
 
@@ -233,8 +241,13 @@ def test_edge_faces_outside_and_one_crowded_cell(cuda_lib):
     got = run_step(cuda_lib, w)
     assert got["counts"][0] == ref["outside"] == 200
     assert got["flags"] & 1
-    # the crowded cell is over-packed: porosity < eps_min, clamped for the drag
+    # the crowded cell is over-packed: porosity ~ -7 there, clamped for the
+    # drag.  The projected porosity then crosses zero next to it, where the
+    # float rounding of |eps| ~ 7 exceeds a relative bound; it is checked
+    # against the field's magnitude instead.
+    eps_f_got, eps_f_ref = got.pop("eps_fine"), ref.pop("eps_fine")
     compare_step(w, got, ref, TOL_FP32)
+    assert np.max(np.abs(eps_f_got - eps_f_ref)) <= TOL_FP32 * np.max(np.abs(eps_f_ref))
     assert got["counts"][2] == int(ref["sums"][15])
 
 
