@@ -148,8 +148,9 @@ def algorithmic_bytes(g, n, eps_fine=True):
     var (4), S_B (12 w + 12 r) rounded to 40 for the step."""
     nf, nb = g.n_fine, g.n_bulk
     per = {
-        "project": nf * (12 + (4 if eps_fine else 0)) + nb * (12 + (4 if eps_fine else 0)),
-        "average": nf * 12 + nb * 16,
+        "project": nf * 12 + nb * 12,        # S_f written, S_B read
+        "project_eps": nf * 4 + nb * 4,      # eps_f written, eps_B read
+        "average": nf * 12 + nb * 16,        # u_f read, u_B and var written
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
     return step, per

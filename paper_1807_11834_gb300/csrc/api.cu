@@ -120,16 +120,17 @@ cg_status ensure_partials(cg_grids* g, long long n) {
     const long long fine_blk = (g->gd.nfine + 255) / 256;
     (void)n;
     const long long proj_blk = (g->gd.r == 2 || g->gd.r == 4 || g->gd.r == 8) ? bulk_blk : fine_blk;
-    const long long need = bulk_blk * 1 + bulk_blk * kDragCellSums + bulk_blk * 3 + proj_blk * 3;
+    const long long part_blk = std::max(bulk_blk, (long long)g->num_sms * 8);
+    const long long need = part_blk * (1 + kDragCellSums + 3) + proj_blk * 3;
     if (need > g->part_cap) {
         dfree(g->partials);
         CG_TRY(dalloc(&g->partials, 2 * g->tsize * need));
         g->part_cap = need;
     }
     g->part_off[PS_VOL] = 0;
-    g->part_off[PS_MOM] = bulk_blk;
-    g->part_off[PS_PROJ] = bulk_blk * 4;
-    g->part_off[PS_DRAG] = bulk_blk * 4 + proj_blk * 3;
+    g->part_off[PS_MOM] = part_blk;
+    g->part_off[PS_PROJ] = part_blk * 4;
+    g->part_off[PS_DRAG] = part_blk * 4 + proj_blk * 3;
     return CG_OK;
 }
 
@@ -141,6 +142,11 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     dfree(g->key1);
     dfree(g->val1);
     dfree(g->perm);
+    dfree(g->key_sorted);
+    dfree(g->inv_perm);
+    dfree(g->vol);
+    dfree(g->vol_sorted);
+    dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
     g->cap = -1;
@@ -149,6 +155,11 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     CG_TRY(dalloc(&g->key1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->val1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->perm, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->key_sorted, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->inv_perm, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->vol, g->tsize * cap));
+    CG_TRY(dalloc(&g->vol_sorted, g->tsize * cap));
+    CG_TRY(dalloc(&g->Fs, 4 * g->tsize * cap));
     const long long ntiles = cap / kSortTile;
     const int maxbits = std::max(g->pass_bits[0], g->pass_bits[1]);
     g->hist_cap = ntiles << maxbits;
@@ -185,6 +196,11 @@ static void free_all(cg_grids* g) {
     dfree(g->key1);
     dfree(g->val1);
     dfree(g->perm);
+    dfree(g->key_sorted);
+    dfree(g->inv_perm);
+    dfree(g->vol);
+    dfree(g->vol_sorted);
+    dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
     dfree(g->cell_start);
@@ -201,6 +217,11 @@ static void free_all(cg_grids* g) {
     }
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     g->ev_pool.clear();
+    cudaEvent_t evs[] = {g->ev_fork, g->ev_avg, g->ev_pack, g->ev_epsf};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (g->aux) cudaStreamDestroy(g->aux);
+    g->aux = nullptr;
 }
 
 cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids** out) {
@@ -298,6 +319,10 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     if (st == CG_OK) st = dalloc(&g->status, sizeof(unsigned long long) * kNumSlots);
     if (st == CG_OK && cudaMemset(g->status, 0, sizeof(unsigned long long) * kNumSlots) != cudaSuccess)
         st = CG_ERR_CUDA;
+    if (st == CG_OK && cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking) != cudaSuccess) st = CG_ERR_CUDA;
+    cudaEvent_t* evs[] = {&g->ev_fork, &g->ev_avg, &g->ev_pack, &g->ev_epsf};
+    for (cudaEvent_t* e : evs)
+        if (st == CG_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) st = CG_ERR_CUDA;
     if (st == CG_OK) st = ensure_particle_capacity(g, 1);
     if (st != CG_OK) {
         free_all(g);
@@ -397,21 +422,51 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
     return launch_project(g, ncomp, in, out, false);
 }
 
+// Launch f on the auxiliary stream (the handle's launch macros use g->stream).
+extern "C++" {
+template <typename Fn>
+static cg_status on_aux(cg_grids* g, Fn f) {
+    cudaStream_t main = g->stream;
+    g->stream = g->aux;
+    cg_status s = f();
+    g->stream = main;
+    return s;
+}
+}
+
+// One coupling step.  Fork / join on the auxiliary stream:
+//   main: bin -> porosity --(avg)--> pack -> drag -> reaction -> project S --(eps_f)--> sums
+//   aux :  average fine -> bulk      \-> project eps
+// The averaging reads only the fine field and the porosity projection only
+// the packed porosity, so both overlap the latency-bound particle kernels.
 static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* o,
                            double dt) {
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
     for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
+    CG_CUDA(cudaEventRecord(g->ev_fork, g->stream));
+    CG_CUDA(cudaStreamWaitEvent(g->aux, g->ev_fork, 0));
+    CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk); }));
+    CG_CUDA(cudaEventRecord(g->ev_avg, g->aux));
     CG_TRY(launch_bin(g, n, p->pos_d));
     CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
-    CG_TRY(launch_deposit_volume(g, n, p->pos_d, o->eps_bulk, true));
-    CG_TRY(launch_average(g, u_fine, o->u_bulk, o->var_bulk));
+    CG_TRY(launch_deposit_volume(g, n, nullptr, o->eps_bulk, true));   // sorted volumes of this binning
+    CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_avg, 0));
     CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
+    if (o->eps_fine) {
+        CG_CUDA(cudaEventRecord(g->ev_pack, g->stream));
+        CG_CUDA(cudaStreamWaitEvent(g->aux, g->ev_pack, 0));
+        const void* ein[4] = {g->eps_t, nullptr, nullptr, nullptr};
+        void* eout[4] = {o->eps_fine, nullptr, nullptr, nullptr};
+        CG_TRY(on_aux(g, [&] { return launch_project(g, 1, ein, eout, false); }));
+    }
+    CG_CUDA(cudaEventRecord(g->ev_epsf, g->aux));
     CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
-    const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, g->eps_t};
-    void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, o->eps_fine};
-    CG_TRY(launch_project(g, o->eps_fine ? 4 : 3, in, out, true));
+    const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, nullptr};
+    void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, nullptr};
+    CG_TRY(launch_project(g, 3, in, out, true));
+    CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_epsf, 0));
     CG_TRY(launch_sums(g, o->sums ? o->sums : g->sums_scratch));
     return CG_OK;
 }

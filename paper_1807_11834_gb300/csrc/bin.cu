@@ -35,11 +35,15 @@ __device__ __forceinline__ void add_status(unsigned long long* st, int outside, 
 // ----------------------------------------------------------------------
 // Key kernel: cell per particle, per-cell counts, tile histogram of digit 0
 // ----------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T pi6_b();
+template <> __device__ __forceinline__ float pi6_b<float>() { return 0.52359877559829887f; }
+template <> __device__ __forceinline__ double pi6_b<double>() { return 0.52359877559829887308; }
+
 template <typename T>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
           int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
-          unsigned long long* __restrict__ status) {
+          T* __restrict__ vol, unsigned long long* __restrict__ status) {
     extern __shared__ int sh[];
     __shared__ int s_cnt[2];
     const int R = 1 << bits0;
@@ -60,10 +64,15 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
             c = cell_of(v, g, outside);
             n_out += outside;
             key[p] = c;
+            vol[p] = pi6_b<T>() * v.w * v.w * v.w;
         }
-        // per-cell count: integer atomics, order-independent
-        if (valid) atomicAdd(&count[c], 1);
-        if (valid) atomicAdd(&sh[c & (R - 1)], 1);
+        // counts: one integer atomic per run of equal cells in the warp
+        // (spatially ordered input has runs of several particles)
+        const int len = run_head_length(c, valid);
+        if (len) {
+            atomicAdd(&count[c], len);
+            atomicAdd(&sh[c & (R - 1)], len);
+        }
     }
     if (n_out) atomicAdd(&s_cnt[0], n_out);
     if (n_nf) atomicAdd(&s_cnt[1], n_nf);
@@ -93,11 +102,13 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
 
 // Stable scatter of one digit pass.  offs = exclusive scan of the tile
 // histograms, digit-major ([digit][tile]).
-template <bool FIRST, bool FINAL>
+template <bool FIRST, bool FINAL, typename T>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
               int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
-              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm) {
+              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
+              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+              T* __restrict__ vol_sorted) {
     extern __shared__ int cnt[];  // [kSortWarps][R]
     const int R = 1 << bits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,6 +159,9 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
             int dst = wc[d] + rk[k];
             if (FINAL) {
                 perm[dst] = vv[k];
+                key_sorted[dst] = kv[k];
+                inv_perm[vv[k]] = dst;
+                vol_sorted[dst] = __ldg(vol + vv[k]);
             } else {
                 keys_out[dst] = kv[k];
                 vals_out[dst] = vv[k];
@@ -292,11 +306,44 @@ static bool g_attr_done = false;
 static cg_status set_attrs() {
     if (g_attr_done) return CG_OK;
     const int smem = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);   // 128 KB at 16 warps x 2^11
-    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+#define CG_ATTR(F, L, T) \
+    CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<F, L, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
+    CG_ATTR(true, true, float);
+    CG_ATTR(true, false, float);
+    CG_ATTR(false, true, float);
+    CG_ATTR(true, true, double);
+    CG_ATTR(true, false, double);
+    CG_ATTR(false, true, double);
+#undef CG_ATTR
     g_attr_done = true;
+    return CG_OK;
+}
+
+template <typename T>
+static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, long long m0) {
+    const long long nbulk = g->gd.nbulk;
+    const int b0 = g->pass_bits[0], b1 = g->pass_bits[1];
+    CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
+              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status);
+    CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
+    const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
+    if (g->npasses == 1) {
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true, T>), ntiles, kSortThreads, smem0, g->key, nullptr,
+                  n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
+                  (const T*)g->vol, (T*)g->vol_sorted);
+    } else {
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false, T>), ntiles, kSortThreads, smem0, g->key, nullptr,
+                  n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr, nullptr, nullptr, (const T*)nullptr,
+                  (T*)nullptr);
+        const long long m1 = (long long)ntiles << b1;
+        CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1, g->key1, n, ntiles, b0, b1,
+                  g->hist);
+        CG_TRY(scan_exclusive2(g, g->hist, g->hist, m1, nullptr, nullptr, 0));
+        const size_t smem1 = (size_t)kSortWarps * sizeof(int) << b1;
+        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true, T>), ntiles, kSortThreads, smem1, g->key1, g->val1,
+                  n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
+                  (const T*)g->vol, (T*)g->vol_sorted);
+    }
     return CG_OK;
 }
 
@@ -306,8 +353,10 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
     // count[] lives in cell_start; the exclusive scan turns it into starts
     CG_CUDA(cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (nbulk + 1), g->stream));
     g->n_binned = -1;
+    g->vol_valid = false;
     if (n == 0) {
         g->n_binned = 0;
+        g->vol_valid = true;
         return CG_OK;
     }
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
@@ -316,29 +365,10 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
     const long long m0 = (long long)ntiles << b0;
     if (m0 > g->hist_cap || (two && ((long long)ntiles << b1) > g->hist_cap)) return CG_ERR_OUT_OF_RANGE;
 
-    if (g->fp64)
-        CG_LAUNCH(g, "bin_key", k_bin_key<double>, ntiles, kSortThreads, sizeof(int) << b0,
-                  (const double*)pos_d, n, g->gd, g->key, g->cell_start, g->hist, ntiles, b0, g->status);
-    else
-        CG_LAUNCH(g, "bin_key", k_bin_key<float>, ntiles, kSortThreads, sizeof(int) << b0,
-                  (const float*)pos_d, n, g->gd, g->key, g->cell_start, g->hist, ntiles, b0, g->status);
-    CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
-    const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
-    if (!two) {
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true>), ntiles, kSortThreads, smem0,
-                  g->key, nullptr, n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm);
-    } else {
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false>), ntiles, kSortThreads, smem0,
-                  g->key, nullptr, n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr);
-        const long long m1 = (long long)ntiles << b1;
-        CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1,
-                  g->key1, n, ntiles, b0, b1, g->hist);
-        CG_TRY(scan_exclusive2(g, g->hist, g->hist, m1, nullptr, nullptr, 0));
-        const size_t smem1 = (size_t)kSortWarps * sizeof(int) << b1;
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true>), ntiles, kSortThreads, smem1,
-                  g->key1, g->val1, n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm);
-    }
+    if (g->fp64) CG_TRY(bin_passes<double>(g, n, (const double*)pos_d, ntiles, m0));
+    else CG_TRY(bin_passes<float>(g, n, (const float*)pos_d, ntiles, m0));
     g->n_binned = n;
+    g->vol_valid = true;
     return CG_OK;
 }
 

@@ -99,6 +99,12 @@ struct cg_grids {
     int32_t* key1 = nullptr;       // [cap] keys after pass 1
     int32_t* val1 = nullptr;       // [cap] particle ids after pass 1
     int32_t* perm = nullptr;       // [cap] particle ids in cell order
+    int32_t* key_sorted = nullptr; // [cap] cell of each slot of the sorted order
+    int32_t* inv_perm = nullptr;   // [cap] sorted slot of each particle
+    void* vol = nullptr;           // [cap] T particle volume, caller order
+    void* vol_sorted = nullptr;    // [cap] T particle volume, sorted order
+    void* Fs = nullptr;            // [cap] T4 drag force, sorted order
+    bool vol_valid = false;        // vol_sorted matches the binned positions
     int32_t* hist = nullptr;       // [2^digit * ntiles]
     int32_t* scan_part = nullptr;  // scan block partials
     long long hist_cap = 0, scan_cap = 0;
@@ -117,6 +123,11 @@ struct cg_grids {
     // host-buffer entry: device staging
     cg::DevBuf st_pos, st_vel, st_ufine, st_eps, st_ub, st_var, st_Sb, st_F, st_Sf, st_epsf,
         st_sums, st_cell, st_perm, st_cs;
+
+    // second stream of the step: fine-grid work that does not depend on the
+    // particle path runs beside it (fork / join through events)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_avg = nullptr, ev_pack = nullptr, ev_epsf = nullptr;
 
     // launch accounting / profiling
     long long launches = 0;
@@ -172,6 +183,7 @@ cg_status ensure_partials(cg_grids* g, long long n);
 
 cg_status launch_bin(cg_grids* g, long long n, const void* pos_d);
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums);
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
 cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk);
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk);
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
@@ -288,6 +300,19 @@ __device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part
     }
 }
 
+// Length of the run of equal values starting at this lane, or 0 if the lane
+// is not the first of its run (runs of consecutive lanes with equal v).
+__device__ __forceinline__ int run_head_length(int v, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, v, 1);
+    const bool head = valid && (lane == 0 || prev != v);
+    const unsigned heads = __ballot_sync(0xffffffffu, head) | __ballot_sync(0xffffffffu, !valid);
+    if (!head) return 0;
+    const unsigned later = heads & ~((2u << lane) - 1u);
+    const int next = lane == 31 ? 32 : (later ? __ffs(later) - 1 : 32);
+    return next - lane;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -344,6 +369,58 @@ __device__ __forceinline__ int cell_of_f(float x, float y, float z, const GridDe
 __device__ __forceinline__ int cell_of_d(double x, double y, double z, const GridDev& g) {
     int o = 0;
     return cell_of(V4<double>{x, y, z, 0.0}, g, o);
+}
+
+// ----------------------------------------------------------------------
+// Segmented reductions over the sorted particle order.
+//
+// The sorted order is cut into chunks of kSegChunk slots; warp w owns the
+// segments (cells) that START in its chunks and runs past a chunk's end to
+// finish its last segment, so every segment is reduced by exactly one warp
+// and the work follows the particles, not the cells (a dense bed occupying
+// a few percent of the cells still spreads over every SM).  Within a warp
+// the slots are taken 32 at a time; a compensated segmented inclusive scan
+// over the lanes (fixed shuffle tree) plus a carry between rounds gives, at
+// the last slot of each segment, the segment's sum.  The order of the sum
+// is fixed by the input, so results are deterministic.
+// ----------------------------------------------------------------------
+constexpr int kSegChunk = 256;
+
+// Range [s, t) of sorted slots owned by the chunk starting at `base`.
+__device__ __forceinline__ void seg_chunk_range(long long base, long long n, const int32_t* __restrict__ key_sorted,
+                                                const int32_t* __restrict__ cs, long long& s, long long& t) {
+    const long long last = (base + kSegChunk < n ? base + kSegChunk : n) - 1;
+    s = base;
+    if (base > 0) {
+        const int k0 = __ldg(key_sorted + base);
+        if (__ldg(key_sorted + base - 1) == k0) s = __ldg(cs + k0 + 1);
+    }
+    t = __ldg(cs + __ldg(key_sorted + last) + 1);
+    if (s > last) t = s;   // the whole chunk lies inside a segment owned earlier
+}
+
+// Inclusive segmented scan of K compensated sums over the lanes, keyed by
+// `key`; lane i ends with the sum of its segment's lanes <= i.
+template <typename T, int K>
+__device__ __forceinline__ void warp_seg_scan(CSum<T> (&v)[K], int key) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int ko = __shfl_up_sync(0xffffffffu, key, off);
+        const bool take = lane >= off && ko == key;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            CSum<T> o;
+            o.s = __shfl_up_sync(0xffffffffu, v[k].s, off);
+            o.c = __shfl_up_sync(0xffffffffu, v[k].c, off);
+            if (take) {
+                // earlier lanes first: result = o (+) v
+                CSum<T> r = o;
+                r.merge(v[k]);
+                v[k] = r;
+            }
+        }
+    }
 }
 
 }  // namespace cg

@@ -13,6 +13,8 @@
 // compensated accumulator, so the result depends only on the particle set
 // of the cell, never on the launch shape, and needs no atomics.  The
 // porosity is formed in double from the compensated pair.
+#include <algorithm>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -22,64 +24,226 @@ template <> __device__ __forceinline__ float pi_over_6<float>() { return 0.52359
 template <> __device__ __forceinline__ double pi_over_6<double>() { return 0.52359877559829887308; }
 
 // ----------------------------------------------------------------------
-// Porosity: one warp per bulk cell, lanes strided over the cell's stable
-// segment, compensated per-lane sums combined by a fixed xor tree.
+// Porosity over the sorted order (see seg_chunk_range): the segmented
+// compensated sum of V_p leaves each cell's volume at its last slot, where
+// eps = 1 - sum / V_B is formed in double.  Cells without particles are
+// set to 1 beforehand by k_fill.
 // ----------------------------------------------------------------------
-constexpr int kDepWarps = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) k_fill(T* __restrict__ a, long long m, T v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kDepWarps)
-k_deposit_volume(const T* __restrict__ pos, const int32_t* __restrict__ perm,
-                 const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps,
-                 T* __restrict__ part, long long pstride, int do_sums) {
+__global__ void __launch_bounds__(256)
+k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restrict__ perm,
+                 const int32_t* __restrict__ key_sorted, const int32_t* __restrict__ cs, GridDev g,
+                 double* __restrict__ eps, T* __restrict__ part, long long pstride, int do_sums) {
     const int lane = threadIdx.x & 31;
-    const long long c = (long long)blockIdx.x * kDepWarps + (threadIdx.x >> 5);
-    CSum<T> cell_sum;
-    if (c < g.nbulk) {
-        const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
-        for (int i = b + lane; i < e; i += 32) {
-            const T d = __ldg(pos + 4 * (long long)__ldg(perm + i) + 3);
-            cell_sum.add(pi_over_6<T>() * d * d * d);
+    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    CSum<T> tot[1];
+    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
+        long long s, t;
+        seg_chunk_range(base, n, key_sorted, cs, s, t);
+        CSum<T> carry;
+        int carry_key = -1;
+        for (long long r = s; r < t; r += 32) {
+            const long long i = r + lane;
+            const bool valid = i < t;
+            int key = -1;
+            CSum<T> v[1];
+            if (valid) {
+                key = __ldg(key_sorted + i);
+                const T d = __ldg(pos + 4 * (long long)__ldg(perm + i) + 3);
+                v[0].s = pi_over_6<T>() * d * d * d;
+            }
+            if (lane == 0 && key == carry_key) {
+                CSum<T> c0 = carry;
+                c0.merge(v[0]);
+                v[0] = c0;
+            }
+            warp_seg_scan<T, 1>(v, key);
+            int next = __shfl_down_sync(0xffffffffu, key, 1);
+            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
+            if (valid && next != key) {
+                eps[key] = 1.0 - ((double)v[0].s + (double)v[0].c) * g.invVB;
+                tot[0].merge(v[0]);
+            }
+            carry.s = __shfl_sync(0xffffffffu, v[0].s, 31);
+            carry.c = __shfl_sync(0xffffffffu, v[0].c, 31);
+            carry_key = __shfl_sync(0xffffffffu, key, 31);
         }
-        if (b != e) cell_sum = warp_reduce(cell_sum);
-        if (lane == 0) eps[c] = 1.0 - ((double)cell_sum.s + (double)cell_sum.c) * g.invVB;
     }
-    if (do_sums) {
-        CSum<T> v[1];
-        if (lane == 0) v[0] = cell_sum;
-        block_sums<T, 1>(v, part, pstride);
+    if (do_sums) block_sums<T, 1>(tot, part, pstride);
+}
+
+// Porosity from the volumes already in sorted order (written by the final
+// binning pass): the same segmented sum without any gather.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __restrict__ key_sorted,
+                        const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
+                        long long pstride, int do_sums) {
+    const int lane = threadIdx.x & 31;
+    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    CSum<T> tot[1];
+    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
+        long long s, t;
+        seg_chunk_range(base, n, key_sorted, cs, s, t);
+        CSum<T> carry;
+        int carry_key = -1;
+        for (long long r = s; r < t; r += 32) {
+            const long long i = r + lane;
+            const bool valid = i < t;
+            int key = -1;
+            CSum<T> v[1];
+            if (valid) {
+                key = __ldg(key_sorted + i);
+                v[0].s = __ldg(vs + i);
+            }
+            if (lane == 0 && key == carry_key) {
+                CSum<T> c0 = carry;
+                c0.merge(v[0]);
+                v[0] = c0;
+            }
+            warp_seg_scan<T, 1>(v, key);
+            int next = __shfl_down_sync(0xffffffffu, key, 1);
+            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
+            if (valid && next != key) {
+                eps[key] = 1.0 - ((double)v[0].s + (double)v[0].c) * g.invVB;
+                tot[0].merge(v[0]);
+            }
+            carry.s = __shfl_sync(0xffffffffu, v[0].s, 31);
+            carry.c = __shfl_sync(0xffffffffu, v[0].c, 31);
+            carry_key = __shfl_sync(0xffffffffu, key, 31);
+        }
     }
+    if (do_sums) block_sums<T, 1>(tot, part, pstride);
+}
+
+// Reaction from the forces the drag wrote in sorted order (T4 per slot);
+// S_B V_B accumulated as an exact float-float product for the diagnostics.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
+                       const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
+                       long long pstride, int do_sums) {
+    const int lane = threadIdx.x & 31;
+    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    CSum<T> sv[3];
+    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
+        long long s, t;
+        seg_chunk_range(base, n, key_sorted, cs, s, t);
+        CSum<T> carry[3];
+        int carry_key = -1;
+        for (long long r = s; r < t; r += 32) {
+            const long long i = r + lane;
+            const bool valid = i < t;
+            int key = -1;
+            CSum<T> v[3];
+            if (valid) {
+                key = __ldg(key_sorted + i);
+                const V4<T> f = ld4(Fs, i);
+                v[0].s = f.x;
+                v[1].s = f.y;
+                v[2].s = f.z;
+            }
+            if (lane == 0 && key == carry_key)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    CSum<T> c0 = carry[k];
+                    c0.merge(v[k]);
+                    v[k] = c0;
+                }
+            warp_seg_scan<T, 3>(v, key);
+            int next = __shfl_down_sync(0xffffffffu, key, 1);
+            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
+            if (valid && next != key)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    T s_;
+                    if (sizeof(T) == 4) s_ = -(v[k].get()) * (T)g.invVBf;
+                    else s_ = -(v[k].get()) * (T)g.invVB;
+                    S[k * g.nbulk + key] = s_;
+                    if (sizeof(T) == 4) {
+                        T hi = s_ * (T)g.VBh;
+                        T lo = fma(s_, (T)g.VBh, -hi);
+                        lo = fma(s_, (T)g.VBl, lo);
+                        sv[k].add(hi);
+                        sv[k].c += lo;
+                    } else {
+                        sv[k].add(s_ * (T)g.VB);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                carry[k].s = __shfl_sync(0xffffffffu, v[k].s, 31);
+                carry[k].c = __shfl_sync(0xffffffffu, v[k].c, 31);
+            }
+            carry_key = __shfl_sync(0xffffffffu, key, 31);
+        }
+    }
+    if (do_sums) block_sums<T, 3>(sv, part, pstride);
 }
 
 // ----------------------------------------------------------------------
-// Reaction source from caller-order SoA forces, gathered through perm (one
-// warp per cell as above).  Inside the coupling step the reaction is fused
-// into the cell-order drag instead.
+// Reaction source from caller-order SoA forces, over the sorted order as
+// above (inside the coupling step the reaction is fused into the drag).
+// S_B must be zero beforehand for cells without particles.
 // ----------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(32 * kDepWarps)
+__global__ void __launch_bounds__(256)
 k_deposit_momentum(const T* __restrict__ F, long long n, const int32_t* __restrict__ perm,
-                   const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S) {
+                   const int32_t* __restrict__ key_sorted, const int32_t* __restrict__ cs, GridDev g,
+                   T* __restrict__ S) {
     const int lane = threadIdx.x & 31;
-    const long long c = (long long)blockIdx.x * kDepWarps + (threadIdx.x >> 5);
-    if (c >= g.nbulk) return;
-    CSum<T> a[3];
-    const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
-    for (int i = b + lane; i < e; i += 32) {
-        const long long p = __ldg(perm + i);
-        a[0].add(__ldg(F + p));
-        a[1].add(__ldg(F + n + p));
-        a[2].add(__ldg(F + 2 * n + p));
-    }
-    if (b != e)
+    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
+        long long s, t;
+        seg_chunk_range(base, n, key_sorted, cs, s, t);
+        CSum<T> carry[3];
+        int carry_key = -1;
+        for (long long r = s; r < t; r += 32) {
+            const long long i = r + lane;
+            const bool valid = i < t;
+            int key = -1;
+            CSum<T> v[3];
+            if (valid) {
+                key = __ldg(key_sorted + i);
+                const long long p = __ldg(perm + i);
+                v[0].s = __ldg(F + p);
+                v[1].s = __ldg(F + n + p);
+                v[2].s = __ldg(F + 2 * n + p);
+            }
+            if (lane == 0 && key == carry_key)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a[k] = warp_reduce(a[k]);
-    if (lane == 0)
+                for (int k = 0; k < 3; ++k) {
+                    CSum<T> c0 = carry[k];
+                    c0.merge(v[k]);
+                    v[k] = c0;
+                }
+            warp_seg_scan<T, 3>(v, key);
+            int next = __shfl_down_sync(0xffffffffu, key, 1);
+            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
+            if (valid && next != key)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (sizeof(T) == 4) S[k * g.nbulk + c] = -(a[k].get()) * (T)g.invVBf;
-            else S[k * g.nbulk + c] = -(a[k].get()) * (T)g.invVB;
+                for (int k = 0; k < 3; ++k) {
+                    if (sizeof(T) == 4) S[k * g.nbulk + key] = -(v[k].get()) * (T)g.invVBf;
+                    else S[k * g.nbulk + key] = -(v[k].get()) * (T)g.invVB;
+                }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                carry[k].s = __shfl_sync(0xffffffffu, v[k].s, 31);
+                carry[k].c = __shfl_sync(0xffffffffu, v[k].c, 31);
+            }
+            carry_key = __shfl_sync(0xffffffffu, key, 31);
         }
+    }
 }
 
 // ----------------------------------------------------------------------
@@ -145,28 +309,74 @@ __global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMa
 // ----------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
+static unsigned seg_blocks(cg_grids* g, long long n) {
+    const long long chunks = (n + kSegChunk - 1) / kSegChunk;
+    return (unsigned)std::max(1LL, std::min((chunks + 7) / 8, (long long)g->num_sms * 8));
+}
+
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums) {
-    (void)n;
-    const unsigned nblk = blocks_for(g->gd.nbulk, kDepWarps);
+    const unsigned fblk = (unsigned)std::min((g->gd.nbulk + 255) / 256, (long long)g->num_sms * 8);
+    CG_LAUNCH(g, "deposit_volume", k_fill<double>, fblk, 256, 0, eps, g->gd.nbulk, 1.0);
+    const unsigned nblk = seg_blocks(g, n);
     void* part = part_ptr(g, PS_VOL);
     g->part_blocks[PS_VOL] = sums ? (long long)nblk : -1;
+    if (sums && n == 0) {
+        // no slots: the diagnostics partial is a single zero pair
+        CG_CUDA(cudaMemsetAsync(part, 0, 2 * g->tsize, g->stream));
+        g->part_blocks[PS_VOL] = 1;
+        return CG_OK;
+    }
+    if (n == 0) return CG_OK;
+    if (pos_d == nullptr) {
+        // volumes already in sorted order from the binning of these positions
+        if (g->fp64)
+            CG_LAUNCH(g, "deposit_volume", k_deposit_volume_sorted<double>, nblk, 256, 0,
+                      (const double*)g->vol_sorted, n, g->key_sorted, g->cell_start, g->gd, eps, (double*)part,
+                      (long long)nblk, (int)sums);
+        else
+            CG_LAUNCH(g, "deposit_volume", k_deposit_volume_sorted<float>, nblk, 256, 0,
+                      (const float*)g->vol_sorted, n, g->key_sorted, g->cell_start, g->gd, eps, (float*)part,
+                      (long long)nblk, (int)sums);
+        return CG_OK;
+    }
     if (g->fp64)
-        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<double>, nblk, 32 * kDepWarps, 0, (const double*)pos_d, g->perm,
-                  g->cell_start, g->gd, eps, (double*)part, (long long)nblk, (int)sums);
+        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<double>, nblk, 256, 0, (const double*)pos_d, n, g->perm,
+                  g->key_sorted, g->cell_start, g->gd, eps, (double*)part, (long long)nblk, (int)sums);
     else
-        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<float>, nblk, 32 * kDepWarps, 0, (const float*)pos_d, g->perm,
-                  g->cell_start, g->gd, eps, (float*)part, (long long)nblk, (int)sums);
+        CG_LAUNCH(g, "deposit_volume", k_deposit_volume<float>, nblk, 256, 0, (const float*)pos_d, n, g->perm,
+                  g->key_sorted, g->cell_start, g->gd, eps, (float*)part, (long long)nblk, (int)sums);
+    return CG_OK;
+}
+
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums) {
+    CG_CUDA(cudaMemsetAsync(S_bulk, 0, 3 * g->tsize * (size_t)g->gd.nbulk, g->stream));
+    void* part = part_ptr(g, PS_MOM);
+    if (n == 0) {
+        g->part_blocks[PS_MOM] = sums ? 1 : -1;
+        if (sums) CG_CUDA(cudaMemsetAsync(part, 0, 2 * g->tsize * 3, g->stream));
+        return CG_OK;
+    }
+    const unsigned nblk = seg_blocks(g, n);
+    g->part_blocks[PS_MOM] = sums ? (long long)nblk : -1;
+    if (g->fp64)
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<double>, nblk, 256, 0, (const double*)g->Fs, n,
+                  g->key_sorted, g->cell_start, g->gd, (double*)S_bulk, (double*)part, (long long)nblk, (int)sums);
+    else
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<float>, nblk, 256, 0, (const float*)g->Fs, n,
+                  g->key_sorted, g->cell_start, g->gd, (float*)S_bulk, (float*)part, (long long)nblk, (int)sums);
     return CG_OK;
 }
 
 cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk) {
-    const unsigned nblk = blocks_for(g->gd.nbulk, kDepWarps);
+    CG_CUDA(cudaMemsetAsync(S_bulk, 0, 3 * g->tsize * (size_t)g->gd.nbulk, g->stream));
+    if (n == 0) return CG_OK;
+    const unsigned nblk = seg_blocks(g, n);
     if (g->fp64)
-        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<double>, nblk, 32 * kDepWarps, 0, (const double*)force_soa, n,
-                  g->perm, g->cell_start, g->gd, (double*)S_bulk);
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<double>, nblk, 256, 0, (const double*)force_soa, n,
+                  g->perm, g->key_sorted, g->cell_start, g->gd, (double*)S_bulk);
     else
-        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<float>, nblk, 32 * kDepWarps, 0, (const float*)force_soa, n,
-                  g->perm, g->cell_start, g->gd, (float*)S_bulk);
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_momentum<float>, nblk, 256, 0, (const float*)force_soa, n,
+                  g->perm, g->key_sorted, g->cell_start, g->gd, (float*)S_bulk);
     return CG_OK;
 }
 
@@ -197,7 +407,7 @@ cg_status launch_sums(cg_grids* g, double* sums) {
     col(1, PS_VOL, 0);
     for (int a = 0; a < 3; ++a) {
         col(2 + a, PS_DRAG, 1 + a);
-        col(5 + a, PS_DRAG, kDragSums + a);
+        col(5 + a, PS_MOM, a);
         col(8 + a, PS_PROJ, a);
         col(12 + a, PS_DRAG, 5 + a);
     }

@@ -166,7 +166,11 @@ __device__ __forceinline__ V4<T> ld4_plain(const T* p, long long i) {
 template <typename T, bool EULER>
 __global__ void __launch_bounds__(256)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
-       T* __restrict__ F, T dt, unsigned long long* __restrict__ status) {
+       T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
+       T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
+    T lane_sums[kDragSums];
+#pragma unroll
+    for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
     int clamped_total = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -175,11 +179,13 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
         const V4<T> b = gather(bulk4, x.x, x.y, x.z, g);
         T phi = b.x;
         T eps = T(1) - phi;
+        int cl = 0;
         if (eps < P.eps_min) {
             eps = P.eps_min;
             phi = T(1) - P.eps_min;
-            clamped_total += 1;
+            cl = 1;
         }
+        clamped_total += cl;
         const T sx = b.y - v.x, sy = b.z - v.y, sz = b.w - v.z;
         const T smag = M<T>::sqrt_(sx * sx + sy * sy + sz * sz);
         const T d = x.w;
@@ -188,8 +194,11 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
         F[p] = fx;
         F[n + p] = fy;
         F[2 * n + p] = fz;
+        if (Fs) st4(Fs, __ldg(inv_perm + p), fx, fy, fz, T(0));
+        T ux = v.x, uy = v.y, uz = v.z;
+        const T vp = M<T>::pi6() * d * d * d;
+        const T m = P.rho_p * vp;
         if (EULER) {
-            const T m = P.rho_p * M<T>::pi6() * d * d * d;
             T xn[3] = {x.x, x.y, x.z};
             T un[3] = {v.x + dt * (fx / m + P.g[0]), v.y + dt * (fy / m + P.g[1]), v.z + dt * (fz / m + P.g[2])};
 #pragma unroll
@@ -202,7 +211,19 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
             }
             st4(pos, p, xn[0], xn[1], xn[2], d);
             st4(vel, p, un[0], un[1], un[2], v.w);
+            ux = un[0];
+            uy = un[1];
+            uz = un[2];
         }
+        lane_sums[0] += vp;
+        lane_sums[1] += fx;
+        lane_sums[2] += fy;
+        lane_sums[3] += fz;
+        lane_sums[4] += beta * smag;
+        lane_sums[5] += m * ux;
+        lane_sums[6] += m * uy;
+        lane_sums[7] += m * uz;
+        lane_sums[8] += (T)cl;
     }
     int wsum = clamped_total;
 #pragma unroll
@@ -211,132 +232,11 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
         atomicAdd(&status[ST_CLAMPED], (unsigned long long)wsum);
         atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
     }
-}
-
-// ----------------------------------------------------------------------
-// Cell-order drag with the fused reaction deposit (needs the binning).
-// One warp per bulk cell: lane l takes particles l, l + 32, ... of the
-// cell's stable segment (coalesced reads of the permutation, 32 particle
-// gathers in flight), writes each force in the caller's order and keeps a
-// TwoSum-compensated partial of the cell's force; a fixed xor tree then
-// combines the 32 partials.  The summation order depends only on the
-// cell's own particles, never on the launch shape: the reaction
-// S_B = -(1/V_B) sum F is deterministic, needs no atomics and no second
-// pass over the forces.  Empty cells cost one read of cell_start.
-// Partial sums (per block): V_p, F (3), |F|, m u (3), clamped, S_B V_B (3).
-// ----------------------------------------------------------------------
-constexpr int kCellSums = kDragCellSums;
-constexpr int kCellWarps = 8;   // cells (warps) per block
-
-template <typename T, bool EULER>
-__global__ void __launch_bounds__(32 * kCellWarps)
-k_drag_cells(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
-             const int32_t* __restrict__ perm, const int32_t* __restrict__ cs, T* __restrict__ F,
-             T* __restrict__ S, T dt, T* __restrict__ part, long long pstride, int do_sums,
-             unsigned long long* __restrict__ status) {
-    const int lane = threadIdx.x & 31;
-    const long long c = (long long)blockIdx.x * kCellWarps + (threadIdx.x >> 5);
-    T sum_v = 0, sum_f[3] = {0, 0, 0}, sum_fa = 0, sum_mu[3] = {0, 0, 0};
-    int clamped_total = 0;
-    CSum<T> acc[kCellSums];
-    if (c < g.nbulk) {
-        const int b = __ldg(cs + c), e = __ldg(cs + c + 1);
-        CSum<T> sb[3];
-        for (int i = b + lane; i < e; i += 32) {
-            const long long p = __ldg(perm + i);
-            const V4<T> x = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
-            const V4<T> v = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
-            const V4<T> bb = gather(bulk4, x.x, x.y, x.z, g);
-            T phi = bb.x;
-            T eps = T(1) - phi;
-            if (eps < P.eps_min) {
-                eps = P.eps_min;
-                phi = T(1) - P.eps_min;
-                clamped_total += 1;
-            }
-            const T sx = bb.y - v.x, sy = bb.z - v.y, sz = bb.w - v.z;
-            const T smag = M<T>::sqrt_(sx * sx + sy * sy + sz * sz);
-            const T d = x.w;
-            const T beta = drag_beta(g.law, eps, phi, d, smag, P);
-            const T fx = beta * sx, fy = beta * sy, fz = beta * sz;
-            F[p] = fx;
-            F[n + p] = fy;
-            F[2 * n + p] = fz;
-            sb[0].add(fx);
-            sb[1].add(fy);
-            sb[2].add(fz);
-            T ux = v.x, uy = v.y, uz = v.z;
-            const T vp = M<T>::pi6() * d * d * d;
-            const T m = P.rho_p * vp;
-            if (EULER) {
-                T xn[3] = {x.x, x.y, x.z};
-                T un[3] = {v.x + dt * (fx / m + P.g[0]), v.y + dt * (fy / m + P.g[1]),
-                           v.z + dt * (fz / m + P.g[2])};
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    T xa = xn[a] + dt * un[a];
-                    const T lo = (T)g.x0[a], hi = (T)g.xhi[a];
-                    if (xa < lo) { xa = T(2) * lo - xa; un[a] = -un[a]; }
-                    else if (xa > hi) { xa = T(2) * hi - xa; un[a] = -un[a]; }
-                    xn[a] = xa;
-                }
-                st4(pos, p, xn[0], xn[1], xn[2], d);
-                st4(vel, p, un[0], un[1], un[2], v.w);
-                ux = un[0];
-                uy = un[1];
-                uz = un[2];
-            }
-            sum_v += vp;
-            sum_f[0] += fx;
-            sum_f[1] += fy;
-            sum_f[2] += fz;
-            sum_fa += beta * smag;
-            sum_mu[0] += m * ux;
-            sum_mu[1] += m * uy;
-            sum_mu[2] += m * uz;
-        }
-        if (b != e) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) sb[k] = warp_reduce(sb[k]);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                T s;
-                if (sizeof(T) == 4) s = -(sb[k].get()) * (T)g.invVBf;
-                else s = -(sb[k].get()) * (T)g.invVB;
-                S[k * g.nbulk + c] = s;
-                if (sizeof(T) == 4) {
-                    // S_B V_B as an exact float-float product, V_B split in two
-                    T hi = s * (T)g.VBh;
-                    T lo = fma(s, (T)g.VBh, -hi);
-                    lo = fma(s, (T)g.VBl, lo);
-                    acc[kDragSums + k].add(hi);
-                    acc[kDragSums + k].c += lo;
-                } else {
-                    acc[kDragSums + k].add(s * (T)g.VB);
-                }
-            }
-        }
-    }
-    int wsum = clamped_total;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
-    if (lane == 0 && wsum) {
-        atomicAdd(&status[ST_CLAMPED], (unsigned long long)wsum);
-        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
-    }
     if (do_sums) {
-        acc[0].add(sum_v);
-        acc[1].add(sum_f[0]);
-        acc[2].add(sum_f[1]);
-        acc[3].add(sum_f[2]);
-        acc[4].add(sum_fa);
-        acc[5].add(sum_mu[0]);
-        acc[6].add(sum_mu[1]);
-        acc[7].add(sum_mu[2]);
-        acc[8].add((T)clamped_total);
-        block_sums<T, kCellSums>(acc, part, pstride);
+        CSum<T> acc[kDragSums];
+#pragma unroll
+        for (int k = 0; k < kDragSums; ++k) acc[k].add(lane_sums[k]);
+        block_sums<T, kDragSums>(acc, part, pstride);
     }
 }
 
@@ -356,39 +256,25 @@ static Phys<T> phys_of(const GridDev& g) {
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
                       bool sums, double dt) {
     const bool euler = dt > 0.0;
-    if (S_bulk) {
-        // cell order, reaction fused; every bulk cell writes its S_B
-        const unsigned nblk = (unsigned)((g->gd.nbulk + kCellWarps - 1) / kCellWarps);
-        void* part = part_ptr(g, PS_DRAG);
-        g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
-#define CG_DRAGC(T, E)                                                                                  \
-    CG_LAUNCH(g, "drag", (k_drag_cells<T, E>), nblk, 32 * kCellWarps, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd), \
-              (const T*)g->bulk4, g->perm, g->cell_start, (T*)force, (T*)S_bulk, (T)dt, (T*)part,            \
-              (long long)nblk, (int)sums, g->status)
-        if (g->fp64) {
-            if (euler) CG_DRAGC(double, true);
-            else CG_DRAGC(double, false);
-        } else {
-            if (euler) CG_DRAGC(float, true);
-            else CG_DRAGC(float, false);
-        }
-#undef CG_DRAGC
-        return CG_OK;
-    }
-    g->part_blocks[PS_DRAG] = -1;
-    if (n == 0) return CG_OK;
+    void* part = part_ptr(g, PS_DRAG);
     const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * 8));
-#define CG_DRAGP(T, E)                                                                                  \
-    CG_LAUNCH(g, "drag", (k_drag<T, E>), nblk, 256, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd),      \
-              (const T*)g->bulk4, (T*)force, (T)dt, g->status)
-    if (g->fp64) {
-        if (euler) CG_DRAGP(double, true);
-        else CG_DRAGP(double, false);
-    } else {
-        if (euler) CG_DRAGP(float, true);
-        else CG_DRAGP(float, false);
-    }
+    g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
+    void* Fs = S_bulk ? g->Fs : nullptr;
+    if (n > 0 || sums) {
+#define CG_DRAGP(T, E)                                                                                      \
+    CG_LAUNCH(g, "drag", (k_drag<T, E>), nblk, 256, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd),          \
+              (const T*)g->bulk4, (T*)force, (T*)Fs, g->inv_perm, (T)dt, (T*)part, (long long)nblk, (int)sums,   \
+              g->status)
+        if (g->fp64) {
+            if (euler) CG_DRAGP(double, true);
+            else CG_DRAGP(double, false);
+        } else {
+            if (euler) CG_DRAGP(float, true);
+            else CG_DRAGP(float, false);
+        }
 #undef CG_DRAGP
+    }
+    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, sums));
     return CG_OK;
 }
 

@@ -10,6 +10,8 @@
 // consecutive fine values per row: fully coalesced, every fine value read
 // or written exactly once.  These two sweeps carry most of the bytes of a
 // step, so they are written to stream at HBM speed.
+#include <algorithm>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -73,10 +75,20 @@ __device__ __forceinline__ void bulk_ijk(long long cb, const GridDev& g, int& I,
 // population variance without a second read of the fine data.
 // ----------------------------------------------------------------------
 template <typename T, int RC>
+__device__ __forceinline__ void average_cell(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
+                                             T* __restrict__ var, long long cb);
+
+template <typename T, int RC>
 __global__ void __launch_bounds__(256)
 k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var) {
-    const long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb >= g.nbulk) return;
+    for (long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x; cb < g.nbulk;
+         cb += (long long)gridDim.x * blockDim.x)
+        average_cell<T, RC>(u, g, ub, var, cb);
+}
+
+template <typename T, int RC>
+__device__ __forceinline__ void average_cell(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
+                                             T* __restrict__ var, long long cb) {
     int I, J, K;
     bulk_ijk(cb, g, I, J, K);
     const int r = RC ? RC : g.r;
@@ -317,7 +329,10 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
 static inline unsigned blocks_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk) {
-    const unsigned nblk = blocks_of(g->gd.nbulk, 256);
+    // grid-stride over two blocks per SM: each thread keeps r^2 x 3 row loads
+    // in flight, enough to stream at HBM speed while leaving most warp slots
+    // to the particle kernels running beside it
+    const unsigned nblk = (unsigned)std::min((long long)blocks_of(g->gd.nbulk, 256), (long long)g->num_sms * 2);
 #define CG_AVG(T, RC)                                                                                   \
     CG_LAUNCH(g, "average", (k_average<T, RC>), nblk, 256, 0, (const T*)u_fine, g->gd, (T*)u_bulk, \
               (T*)var_bulk)
@@ -347,7 +362,7 @@ cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* co
     const unsigned nblk = fast ? blocks_of(g->gd.nbulk, 256) : blocks_of(g->gd.nfine, 256);
     g->part_blocks[PS_PROJ] = sums ? (long long)nblk : -1;
 #define CG_PRJ(T, KER)                                                                                   \
-    CG_LAUNCH(g, "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2],        \
+    CG_LAUNCH(g, ncomp == 1 ? "project_eps" : "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2], \
               (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], (T*)part,   \
               (long long)nblk, (int)sums)
     if (g->fp64) {
