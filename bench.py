@@ -141,16 +141,27 @@ class ClockSampler:
 
 
 def algorithmic_bytes(g, n, eps_fine=True):
-    """Algorithmic bytes of one step and of the kernels, FP32 path.
-    Particles: read x, y, z, d (16), u_p (12), write F (12), bin key and
-    permutation written and read once (8).  Fine cells: read u_f (12), write
-    S_f (12) and eps_f (4).  Bulk cells: eps (8 w + 8 r), u_B (12 w + 12 r),
-    var (4), S_B (12 w + 12 r) rounded to 40 for the step."""
+    """Algorithmic bytes of one step (the minimal traffic of the path) and,
+    per launch, of each kernel of this implementation (bytes it must move
+    to do its part, FP32; L2-resident gathers of the bulk fields and
+    histogram / scan scratch are not counted).
+
+    Step: particles read x, y, z, d (16) and u_p (12), write F (12), plus
+    the bin key and permutation written and read once (8); fine cells read
+    u_f (12) and write S_f (12) and eps_f (4); bulk cells ~40 B."""
     nf, nb = g.n_fine, g.n_bulk
+    nbx = nb  # bulk cells
     per = {
-        "project": nf * 12 + nb * 12,        # S_f written, S_B read
-        "project_eps": nf * 4 + nb * 4,      # eps_f written, eps_B read
-        "average": nf * 12 + nb * 16,        # u_f read, u_B and var written
+        "bin_key": n * (16 + 4 + 4),                      # pos read; key, volume written
+        "bin_scatter": n * (12 + 28) // 2,                # pass 1: 4 r + 8 w; pass 2: 12 r + 16 w (mean)
+        "bin_hist": n * 4,
+        "deposit_volume": (nbx * 8 + n * 8 + nbx * 8) // 2,   # fill eps; read sorted volume + key; write eps
+        "pack": nbx * (8 + 12 + 16 + 4),
+        "drag": n * (16 + 16 + 4 + 12 + 16),              # pos, vel, slot read; F and sorted F written
+        "deposit_momentum": n * (16 + 4) + nbx * 12,
+        "project": nf * 12 + nbx * 12,                    # S_f written, S_B read
+        "project_eps": nf * 4 + nbx * 4,                  # eps_f written, eps_B read
+        "average": nf * 12 + nbx * 16,                    # u_f read, u_B and var written
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
     return step, per
@@ -246,7 +257,9 @@ def run_gb300(args):
         raise RuntimeError(f"timed status {rc}")
 
     # per-kernel device time: a second pass of the same steps with the
-    # library's CUDA events around every launch (kept out of the timed pass)
+    # library's CUDA events around every launch (kept out of the timed pass;
+    # the library runs the step on one stream while timing kernels, so each
+    # event pair measures one kernel alone)
     prof_steps = min(args.steps, 200)
     g.cg_profile_reset()
     g.cg_profile_enable(True)
@@ -260,18 +273,21 @@ def run_gb300(args):
     kern_ms = {k: v[1] / v[0] for k, v in prof.items() if v[0]}
     kern_total = {k: v[1] for k, v in prof.items()}
     tot = sum(kern_total.values())
-    dominant = max(kern_total, key=kern_total.get)
+    dominant = max((k for k in kern_total if k in kern_bytes), key=kern_total.get)
     kern_launches = {k: v[0] / prof_steps for k, v in prof.items()}
     dom_bytes = kern_bytes.get(dominant)
     roofline = None
     if dom_bytes is not None:
         ach = dom_bytes / (kern_ms[dominant] * 1e-3) / 1e9
-        src = os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", "fine.cu")
         tr = NCU_TRAFFIC.get(dominant)
-        traffic = tr["bytes"] if tr and tr["sha"] == file_sha(src) else None
+        traffic = None
+        if tr and tr["sha"] == file_sha(os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", tr["file"])):
+            traffic = tr["bytes"]
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(ach, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
-                    "algorithmic_bytes": dom_bytes, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+                    "algorithmic_bytes": dom_bytes, "ms_per_launch": round(kern_ms[dominant], 5),
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "timing": "serialized per-kernel CUDA events over a profiled pass of the same steps"}
     ms_step = ms / args.steps
     step_gbs = step_bytes / (ms_step * 1e-3) / 1e9
     value = world * n * args.steps / (ms * 1e-3)

@@ -423,9 +423,12 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
 }
 
 // Launch f on the auxiliary stream (the handle's launch macros use g->stream).
+// While per-kernel timing is on, everything stays on the main stream so that
+// each kernel's event pair measures that kernel alone.
 extern "C++" {
 template <typename Fn>
 static cg_status on_aux(cg_grids* g, Fn f) {
+    if (g->prof) return f();
     cudaStream_t main = g->stream;
     g->stream = g->aux;
     cg_status s = f();
@@ -444,10 +447,11 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
     for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
+    cudaStream_t side = g->prof ? g->stream : g->aux;
     CG_CUDA(cudaEventRecord(g->ev_fork, g->stream));
-    CG_CUDA(cudaStreamWaitEvent(g->aux, g->ev_fork, 0));
+    CG_CUDA(cudaStreamWaitEvent(side, g->ev_fork, 0));
     CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk); }));
-    CG_CUDA(cudaEventRecord(g->ev_avg, g->aux));
+    CG_CUDA(cudaEventRecord(g->ev_avg, side));
     CG_TRY(launch_bin(g, n, p->pos_d));
     CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
     CG_TRY(launch_deposit_volume(g, n, nullptr, o->eps_bulk, true));   // sorted volumes of this binning
@@ -455,12 +459,12 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
     if (o->eps_fine) {
         CG_CUDA(cudaEventRecord(g->ev_pack, g->stream));
-        CG_CUDA(cudaStreamWaitEvent(g->aux, g->ev_pack, 0));
+        CG_CUDA(cudaStreamWaitEvent(side, g->ev_pack, 0));
         const void* ein[4] = {g->eps_t, nullptr, nullptr, nullptr};
         void* eout[4] = {o->eps_fine, nullptr, nullptr, nullptr};
         CG_TRY(on_aux(g, [&] { return launch_project(g, 1, ein, eout, false); }));
     }
-    CG_CUDA(cudaEventRecord(g->ev_epsf, g->aux));
+    CG_CUDA(cudaEventRecord(g->ev_epsf, side));
     CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
     const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, nullptr};

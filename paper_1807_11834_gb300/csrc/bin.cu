@@ -52,13 +52,20 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
     __syncthreads();
     int n_out = 0, n_nf = 0;
     const long long base = (long long)blockIdx.x * kSortTile;
-#pragma unroll 4
+    V4<T> pv[kSortItems];
+    // all position loads of the thread first, so they are in flight together
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + (long long)k * kSortThreads + threadIdx.x;
+        if (p < n) pv[k] = ld4(pos, p);
+    }
+#pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
         bool valid = p < n;
         int c = -1;
         if (valid) {
-            V4<T> v = ld4(pos, p);
+            const V4<T>& v = pv[k];
             int outside = 0;
             if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
             c = cell_of(v, g, outside);
@@ -103,7 +110,7 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
 // Stable scatter of one digit pass.  offs = exclusive scan of the tile
 // histograms, digit-major ([digit][tile]).
 template <bool FIRST, bool FINAL, typename T>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
 k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
               int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
               int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
@@ -118,6 +125,7 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
     const unsigned lt = lanemask_lt();
     const long long base = (long long)blockIdx.x * kSortTile + (long long)warp * (kSortTile / kSortWarps);
     int kv[kSortItems], vv[kSortItems], rk[kSortItems];
+    T vol_k[kSortItems];
     // all loads of the slice first, so they are in flight together
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
@@ -126,6 +134,10 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
         kv[k] = valid ? __ldg(keys_in + p) : 0;
         vv[k] = valid ? (FIRST ? (int)p : __ldg(vals_in + p)) : 0;
     }
+    if (FINAL)
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k)
+            if (base + k * 32 + lane < n) vol_k[k] = __ldg(vol + vv[k]);
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + k * 32 + lane;
@@ -161,7 +173,7 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
                 perm[dst] = vv[k];
                 key_sorted[dst] = kv[k];
                 inv_perm[vv[k]] = dst;
-                vol_sorted[dst] = __ldg(vol + vv[k]);
+                vol_sorted[dst] = vol_k[k];
             } else {
                 keys_out[dst] = kv[k];
                 vals_out[dst] = vv[k];

@@ -378,11 +378,10 @@ __device__ __forceinline__ int cell_of_d(double x, double y, double z, const Gri
 // segments (cells) that START in its chunks and runs past a chunk's end to
 // finish its last segment, so every segment is reduced by exactly one warp
 // and the work follows the particles, not the cells (a dense bed occupying
-// a few percent of the cells still spreads over every SM).  Within a warp
-// the slots are taken 32 at a time; a compensated segmented inclusive scan
-// over the lanes (fixed shuffle tree) plus a carry between rounds gives, at
-// the last slot of each segment, the segment's sum.  The order of the sum
-// is fixed by the input, so results are deterministic.
+// a few percent of the cells still spreads over every SM).  The warp walks
+// its segments one by one: lane l accumulates slots b + l, b + l + 32, ...
+// of segment [b, e) in a compensated sum, and a fixed xor tree combines the
+// lanes.  The summation order depends only on the segment's own slots.
 // ----------------------------------------------------------------------
 constexpr int kSegChunk = 256;
 
@@ -397,6 +396,97 @@ __device__ __forceinline__ void seg_chunk_range(long long base, long long n, con
     }
     t = __ldg(cs + __ldg(key_sorted + last) + 1);
     if (s > last) t = s;   // the whole chunk lies inside a segment owned earlier
+}
+
+// Segmented sum of K values per slot over the slots [s, t) of one chunk,
+// 32 slots per round: a plain shuffle scan inside the round (at most five
+// roundings), compensated sums for the carry between rounds and for each
+// segment's total.  load(i, v) fills the K values of slot i; emit(key, tot)
+// receives each segment's compensated total on the lane of its last slot.
+// The next round's slots are loaded before the current one is reduced.
+template <typename T, int K, typename Load, typename Emit>
+__device__ __forceinline__ void seg_rounds(long long s, long long t, const int32_t* __restrict__ key_sorted,
+                                           Load load, Emit emit) {
+    constexpr int B = 4;   // rounds loaded ahead of the reduction
+    const int lane = threadIdx.x & 31;
+    CSum<T> carry[K];
+    int carry_key = -1;
+    for (long long r0 = s; r0 < t; r0 += 32 * B) {
+        int key[B + 1];
+        T v[B][K];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const long long i = r0 + 32 * j + lane;
+            key[j] = -1;
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[j][k] = T(0);
+            if (i < t) {
+                key[j] = __ldg(key_sorted + i);
+                load(i, v[j]);
+            }
+        }
+        {
+            const long long i = r0 + 32 * B + lane;
+            key[B] = (lane == 0 && i < t) ? __ldg(key_sorted + i) : -1;   // first key after the batch
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if (r0 + 32 * j >= t) break;   // warp-uniform
+            const long long i = r0 + 32 * j + lane;
+            const bool valid = i < t;
+            const int kj = key[j];
+            T* vj = v[j];
+            // plain inclusive segmented scan over the lanes
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ko = __shfl_up_sync(0xffffffffu, kj, off);
+                const bool take = lane >= off && ko == kj;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const T vo = __shfl_up_sync(0xffffffffu, vj[k], off);
+                    if (take) vj[k] += vo;
+                }
+            }
+            // every lane takes part in both shuffles; lane 31 looks at the next round
+            int next = __shfl_down_sync(0xffffffffu, kj, 1);
+            const int next31 = __shfl_sync(0xffffffffu, j + 1 < B ? key[j + 1] : key[B], 0);
+            if (lane == 31) next = next31;
+            const bool ends = valid && next != kj;
+            const bool cont = kj == carry_key;
+            if (ends) {
+                CSum<T> tot[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (cont) tot[k] = carry[k];
+                    tot[k].add(vj[k]);
+                }
+                emit(kj, tot);
+            }
+            // carry: the segment of lane 31 if it goes on into the next round
+            const int k31 = __shfl_sync(0xffffffffu, kj, 31);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const T v31 = __shfl_sync(0xffffffffu, vj[k], 31);
+                if (k31 != carry_key) carry[k] = CSum<T>();
+                carry[k].add(v31);
+            }
+            carry_key = k31;
+        }
+    }
+}
+
+// Walk the segments owned by the chunk at `base`: fn(key, b, e) for each.
+template <typename Fn>
+__device__ __forceinline__ void seg_walk(long long base, long long n, const int32_t* __restrict__ key_sorted,
+                                         const int32_t* __restrict__ cs, Fn fn) {
+    long long s, t;
+    seg_chunk_range(base, n, key_sorted, cs, s, t);
+    while (s < t) {
+        const int key = __ldg(key_sorted + s);
+        const long long e = __ldg(cs + key + 1);
+        fn(key, s, e);
+        s = e;
+    }
 }
 
 // Inclusive segmented scan of K compensated sums over the lanes, keyed by

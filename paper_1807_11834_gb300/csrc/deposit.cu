@@ -80,46 +80,24 @@ k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restri
 }
 
 // Porosity from the volumes already in sorted order (written by the final
-// binning pass): the same segmented sum without any gather.
+// binning pass): rounds of 32 slots, no gather.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __restrict__ key_sorted,
                         const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
                         long long pstride, int do_sums) {
-    const int lane = threadIdx.x & 31;
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     CSum<T> tot[1];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
         seg_chunk_range(base, n, key_sorted, cs, s, t);
-        CSum<T> carry;
-        int carry_key = -1;
-        for (long long r = s; r < t; r += 32) {
-            const long long i = r + lane;
-            const bool valid = i < t;
-            int key = -1;
-            CSum<T> v[1];
-            if (valid) {
-                key = __ldg(key_sorted + i);
-                v[0].s = __ldg(vs + i);
-            }
-            if (lane == 0 && key == carry_key) {
-                CSum<T> c0 = carry;
-                c0.merge(v[0]);
-                v[0] = c0;
-            }
-            warp_seg_scan<T, 1>(v, key);
-            int next = __shfl_down_sync(0xffffffffu, key, 1);
-            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
-            if (valid && next != key) {
-                eps[key] = 1.0 - ((double)v[0].s + (double)v[0].c) * g.invVB;
-                tot[0].merge(v[0]);
-            }
-            carry.s = __shfl_sync(0xffffffffu, v[0].s, 31);
-            carry.c = __shfl_sync(0xffffffffu, v[0].c, 31);
-            carry_key = __shfl_sync(0xffffffffu, key, 31);
-        }
+        seg_rounds<T, 1>(
+            s, t, key_sorted, [&](long long i, T (&v)[1]) { v[0] = __ldg(vs + i); },
+            [&](int key, CSum<T> (&a)[1]) {
+                eps[key] = 1.0 - ((double)a[0].s + (double)a[0].c) * g.invVB;
+                tot[0].merge(a[0]);
+            });
     }
     if (do_sums) block_sums<T, 1>(tot, part, pstride);
 }
@@ -131,43 +109,26 @@ __global__ void __launch_bounds__(256)
 k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
                        const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
                        long long pstride, int do_sums) {
-    const int lane = threadIdx.x & 31;
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     CSum<T> sv[3];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
         seg_chunk_range(base, n, key_sorted, cs, s, t);
-        CSum<T> carry[3];
-        int carry_key = -1;
-        for (long long r = s; r < t; r += 32) {
-            const long long i = r + lane;
-            const bool valid = i < t;
-            int key = -1;
-            CSum<T> v[3];
-            if (valid) {
-                key = __ldg(key_sorted + i);
+        seg_rounds<T, 3>(
+            s, t, key_sorted,
+            [&](long long i, T (&v)[3]) {
                 const V4<T> f = ld4(Fs, i);
-                v[0].s = f.x;
-                v[1].s = f.y;
-                v[2].s = f.z;
-            }
-            if (lane == 0 && key == carry_key)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    CSum<T> c0 = carry[k];
-                    c0.merge(v[k]);
-                    v[k] = c0;
-                }
-            warp_seg_scan<T, 3>(v, key);
-            int next = __shfl_down_sync(0xffffffffu, key, 1);
-            if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
-            if (valid && next != key)
+                v[0] = f.x;
+                v[1] = f.y;
+                v[2] = f.z;
+            },
+            [&](int key, CSum<T> (&a)[3]) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     T s_;
-                    if (sizeof(T) == 4) s_ = -(v[k].get()) * (T)g.invVBf;
-                    else s_ = -(v[k].get()) * (T)g.invVB;
+                    if (sizeof(T) == 4) s_ = -(a[k].get()) * (T)g.invVBf;
+                    else s_ = -(a[k].get()) * (T)g.invVB;
                     S[k * g.nbulk + key] = s_;
                     if (sizeof(T) == 4) {
                         T hi = s_ * (T)g.VBh;
@@ -179,13 +140,7 @@ k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __r
                         sv[k].add(s_ * (T)g.VB);
                     }
                 }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                carry[k].s = __shfl_sync(0xffffffffu, v[k].s, 31);
-                carry[k].c = __shfl_sync(0xffffffffu, v[k].c, 31);
-            }
-            carry_key = __shfl_sync(0xffffffffu, key, 31);
-        }
+            });
     }
     if (do_sums) block_sums<T, 3>(sv, part, pstride);
 }
