@@ -149,6 +149,23 @@ cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, in
 cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
                            int32_t* cell_out, int32_t* perm_out, int32_t* cell_start_out);
 
+/* Binning that allocates nothing, for callers that must not allocate
+ * device memory (for example code running while another component
+ * captures a CUDA graph, or plug-ins restricted to the memory their host
+ * hands them).  The paper has no counterpart: this is a library facility.
+ * Same cell rule, stable order and outputs as cg_bin_particles, but without
+ * a handle: the grid comes from desc (the physics fields are not used) and
+ * all scratch lives in one fixed device array inside the library (about
+ * 10 MB per GPU that loads it, held until exit).
+ *   n <= 262,144 particles (else CG_ERR_OUT_OF_RANGE), at most 2^22 cells.
+ *   pos_d [n] T4 (16-byte aligned); perm_out [n] and cell_start_out
+ *   [n_b + 1] required; cell_out [n] nullable.  Enqueued on cuda_stream.
+ * The first call on a device looks up the array's address on that device;
+ * make it before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU race: order them on one stream. */
+cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n, const void* pos_d, int32_t* cell_out,
+                                  int32_t* perm_out, int32_t* cell_start_out, void* cuda_stream);
+
 /* (a1)/(a3) Deposit onto the bulk grid over the particles of each cell,
  * summed in the stable order of the last cg_bin_particles.
  *   CG_DEP_VOLUME:   per_particle = pos_d [n] T4 (diameter used);

@@ -71,6 +71,8 @@ _SIGS = {
     "cg_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "cg_grid_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "cg_bin_particles": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_bin_particles_static": (C.c_int, [C.POINTER(GridDesc), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
     "cg_deposit": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]),
     "cg_average_fine_to_bulk": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_drag": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -299,6 +301,15 @@ class Grids:
                    "cg_profile_read")
             res[name.value.decode()] = (launches.value, ms.value)
         return res
+
+
+def cg_bin_particles_static(desc: dict, pos_d, perm, cell_start, cell=None, stream=None):
+    """Binning without any device allocation (fixed scratch inside the
+    library, at most 262,144 particles); same outputs as cg_bin_particles."""
+    d = make_desc(desc)
+    n = pos_d.shape[0]
+    _check(lib().cg_bin_particles_static(C.byref(d), n, _ptr(pos_d), _ptr(cell), _ptr(perm), _ptr(cell_start),
+                                         _stream_handle(stream)), "cg_bin_particles_static")
 
 
 def status_string(code: int) -> str:
