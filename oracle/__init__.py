@@ -87,6 +87,7 @@ def _load():
                 "or_drag": (i64, [pg, i64, pd, pd, pd, pd, pd]),
                 "or_deposit_momentum": (None, [pg, i64, pd, pi, pi, pd]),
                 "or_particle_state": (None, [pg, i64, pd, pd, pd, pd, pd, pd]),
+                "or_mlp_features": (None, [pg, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd]),
                 "or_project": (None, [pg, C.c_int, pd, pd]),
                 "or_euler": (None, [pg, i64, pd, pd, pd, d]),
                 "or_step": (i64, [pg, i64, pd, pd, pd, d, pi, pi, pi, pd, pd, pd, pd, pd, pd, pd, pd]),
@@ -235,6 +236,21 @@ def particle_state(desc, pos_d, vel, eps_bulk, u_bulk):
     e, s = np.zeros(n), np.zeros(n)
     lib.or_particle_state(C.byref(g), n, _pd(pos), _pd(v), _pd(_f64(eps_bulk)), _pd(_f64(u_bulk)), _pd(e), _pd(s))
     return e, s
+
+
+def mlp_features(desc, pos_d, vel, eps_bulk, u_stale, var_stale, u_fresh):
+    """(features[n, 7], target[n], F_stale[3, n]) of the learned closure."""
+    lib = _load()
+    g = grid(desc)
+    pos = _f64(pos_d).reshape(-1, 4)
+    v = _f64(vel).reshape(-1, 4)
+    n = pos.shape[0]
+    feat = np.zeros((n, 7))
+    target = np.zeros(n)
+    Fs = np.zeros((3, n))
+    lib.or_mlp_features(C.byref(g), n, _pd(pos), _pd(v), _pd(_f64(eps_bulk)), _pd(_f64(u_stale)),
+                        _pd(_f64(var_stale)), _pd(_f64(u_fresh)), _pd(feat), _pd(target), _pd(Fs))
+    return feat, target, Fs
 
 
 def deposit_momentum(desc, force, cell_start, perm):

@@ -341,6 +341,47 @@ void or_particle_state(const or_grid* G, int64_t n, const double* pos_d, const d
     }
 }
 
+void or_mlp_features(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                     const double* eps_bulk, const double* u_stale, const double* var_stale,
+                     const double* u_fresh, double* feat, double* target, double* F_stale)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        const double* x = &pos_d[4 * p];
+        const double d = x[3];
+        double eps, us[3], uf[3], var, grad[3], ss[3], sf[3];
+        or_gather(G, eps_bulk, 1, x, &eps);
+        or_gather(G, u_stale, 3, x, us);
+        or_gather(G, u_fresh, 3, x, uf);
+        or_gather(G, var_stale, 1, x, &var);
+        or_gather_grad(G, eps_bulk, x, grad);
+        for (int a = 0; a < 3; ++a) {
+            ss[a] = us[a] - vel[4 * p + a];
+            sf[a] = uf[a] - vel[4 * p + a];
+        }
+        const double epsc = eps < G->eps_min ? G->eps_min : eps;
+        const double smag = sqrt(ss[0] * ss[0] + ss[1] * ss[1] + ss[2] * ss[2]);
+        const double Re = G->rho_f * epsc * d * smag / G->mu_f;
+        double* f = &feat[7 * p];
+        f[0] = epsc;
+        f[1] = log10(1.0 + Re);
+        f[2] = smag;
+        f[3] = grad[0];
+        f[4] = grad[1];
+        f[5] = grad[2];
+        f[6] = var;
+        const double bs = or_drag_beta(G, eps, d, ss, NULL);
+        const double bf = or_drag_beta(G, eps, d, sf, NULL);
+        double dot = 0.0, nn = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double Fs = bs * ss[a], Ff = bf * sf[a];
+            F_stale[a * n + p] = Fs;
+            dot += Ff * Fs;
+            nn += Fs * Fs;
+        }
+        target[p] = nn > 0.0 ? dot / nn : 1.0;
+    }
+}
+
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk)
 {

@@ -84,6 +84,17 @@ int64_t or_drag(const or_grid* G, int64_t n, const double* pos_d, const double* 
 void or_particle_state(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
                        const double* eps_bulk, const double* u_bulk, double* eps_p, double* slip);
 
+/* Learned-closure inputs (not in the paper).  At each particle, with the
+ * porosity of this step and the fluid velocity / variance of the last
+ * refresh (stale) and of this step (fresh):
+ *   feat[7p + 0..6] = eps_c, log10(1 + Re), |s|, d eps/dx, d eps/dy, d eps/dz, sigma^2
+ *   with eps_c = max(eps, eps_min), s = u_stale - u_p, Re = rho_f eps_c d |s| / mu_f,
+ *   target[p] = (F_fresh . F_stale) / |F_stale|^2  (1 when F_stale = 0),
+ *   F_stale[3][n] the drag from the stale fields. */
+void or_mlp_features(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                     const double* eps_bulk, const double* u_stale, const double* var_stale,
+                     const double* u_fresh, double* feat, double* target, double* F_stale);
+
 /* S_B = -(1/V_B) sum_{p in B} F_p  (per component). */
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk);
