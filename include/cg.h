@@ -223,6 +223,49 @@ cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
 cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine,
                        const cg_step_out* out, double dt);
 
+/* ------------------------------------------------------------------------
+ * Learned drag closure (not in the paper; the paper's drag law is the plain
+ * correlation of Eq. DragLaw).  A multilayer perceptron c = f(features),
+ * 16 (7 used) -> 64 -> 64 -> 1 with exact-erf GELU, scales the drag computed
+ * from stale bulk fields, F = c F_stale, in place of a fresh fine-to-bulk
+ * average.  BF16 operands, FP32 accumulation on the tensor cores; FP32
+ * master weights; Adam.  Parameters (FP32, CG_MLP_NPARAM floats, in order):
+ * W1 [16][64] (input, hidden), b1 [64], W2 [64][64] (in, out), b2 [64],
+ * w3 [64], b3 [1].  Feature rows are 8 floats: eps, log10(1 + Re), |s|,
+ * d eps/dx, d eps/dy, d eps/dz, sigma^2, unused; the network sees
+ * (f - lo) / (hi - lo) per feature, and a row is in range when every
+ * scaled feature lies in [0, 1].
+ * ------------------------------------------------------------------------ */
+#define CG_MLP_NPARAM 5313
+#define CG_MLP_NFEAT 7
+
+/* Create a closure from host parameters and the feature box [lo, hi]
+ * (host, CG_MLP_NFEAT each, hi > lo).  Allocates its device state. */
+cg_status cg_mlp_create(const float* params, const float* feat_lo, const float* feat_hi, void* cuda_stream,
+                        cg_mlp** out);
+cg_status cg_mlp_destroy(cg_mlp* m);
+
+/* Copy the current parameters and / or the last reduced gradient to the
+ * host (either nullable; waits for the stream). */
+cg_status cg_mlp_get_params(cg_mlp* m, float* params, float* grads);
+cg_status cg_mlp_set_params(cg_mlp* m, const float* params);
+
+/* c for n feature rows: features [n][8] device (16-byte aligned),
+ * c_out [n], in_range_out [n] (nullable, 1 when in range). */
+cg_status cg_mlp_forward(cg_mlp* m, int64_t n, const float* features, float* c_out, int32_t* in_range_out);
+
+/* Mean-square loss against targets [n] and its gradient (kept in the
+ * handle, readable with cg_mlp_get_params); loss_out: device float, nullable. */
+cg_status cg_mlp_grads(cg_mlp* m, int64_t n, const float* features, const float* targets, float* loss_out);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch. */
+cg_status cg_mlp_train_step(cg_mlp* m, int64_t n, const float* features, const float* targets, float lr,
+                            float* loss_out);
+
+/* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
+ * kernels expired (flags: CG_FLAG_*). */
+cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags);
+
 /* Wait for the handle's stream and read-and-clear the device status word.
  * flags (nullable) gets CG_FLAG_* bits; counts (nullable, 4 entries) gets
  * particles outside, non-finite positions, clamped porosities, timeouts.

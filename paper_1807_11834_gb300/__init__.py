@@ -86,7 +86,18 @@ _SIGS = {
     "cg_profile_reset": (C.c_int, [C.c_void_p]),
     "cg_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "cg_mlp_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cg_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "cg_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "cg_mlp_forward": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_grads": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p]),
+    "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
 }
+
+MLP_NPARAM = 5313
+MLP_NFEAT = 7
 
 
 def lib():
@@ -310,6 +321,84 @@ def cg_bin_particles_static(desc: dict, pos_d, perm, cell_start, cell=None, stre
     n = pos_d.shape[0]
     _check(lib().cg_bin_particles_static(C.byref(d), n, _ptr(pos_d), _ptr(cell), _ptr(perm), _ptr(cell_start),
                                          _stream_handle(stream)), "cg_bin_particles_static")
+
+
+class Mlp:
+    """Owner of a ``cg_mlp`` closure handle (learned drag correction).
+    Parameters are a flat float32 array of MLP_NPARAM (W1, b1, W2, b2, w3, b3)."""
+
+    def __init__(self, params, feat_lo, feat_hi, stream=None):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        lo = np.ascontiguousarray(feat_lo, dtype=np.float32)
+        hi = np.ascontiguousarray(feat_hi, dtype=np.float32)
+        if p.size != MLP_NPARAM or lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
+            raise ValueError("bad closure parameter or feature-box sizes")
+        h = C.c_void_p()
+        _check(lib().cg_mlp_create(p.ctypes.data, lo.ctypes.data, hi.ctypes.data, _stream_handle(stream),
+                                   C.byref(h)), "cg_mlp_create")
+        self.h = h
+        self.lo, self.hi = lo, hi
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, grads=False):
+        import numpy as np
+        p = np.zeros(MLP_NPARAM, np.float32)
+        g = np.zeros(MLP_NPARAM, np.float32) if grads else None
+        _check(lib().cg_mlp_get_params(self.h, p.ctypes.data, None if g is None else g.ctypes.data),
+               "cg_mlp_get_params")
+        return (p, g) if grads else p
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().cg_mlp_set_params(self.h, p.ctypes.data), "cg_mlp_set_params")
+
+    def forward(self, features, c_out, in_range=None):
+        n = features.shape[0]
+        _check(lib().cg_mlp_forward(self.h, n, _ptr(features), _ptr(c_out), _ptr(in_range)), "cg_mlp_forward")
+
+    def grads(self, features, targets, loss=None):
+        _check(lib().cg_mlp_grads(self.h, features.shape[0], _ptr(features), _ptr(targets), _ptr(loss)),
+               "cg_mlp_grads")
+
+    def train_step(self, features, targets, lr, loss=None):
+        _check(lib().cg_mlp_train_step(self.h, features.shape[0], _ptr(features), _ptr(targets), float(lr),
+                                       _ptr(loss)), "cg_mlp_train_step")
+
+    def sync_status(self):
+        flags = C.c_uint32()
+        rc = lib().cg_mlp_sync_status(self.h, C.byref(flags))
+        return rc, flags.value
+
+
+def mlp_pack(p: dict):
+    """Flatten a parameter dict (W1, b1, W2, b2, w3, b3) in the ABI order."""
+    import numpy as np
+    return np.concatenate([np.asarray(p[k], np.float64).reshape(-1) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]
+                          ).astype(np.float32)
+
+
+def mlp_unpack(flat, hidden=64, k0=16):
+    import numpy as np
+    f = np.asarray(flat, np.float64)
+    out, o = {}, 0
+    for k, shape in (("W1", (k0, hidden)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+                     ("w3", (hidden,)), ("b3", (1,))):
+        sz = int(np.prod(shape))
+        out[k] = f[o:o + sz].reshape(shape)
+        o += sz
+    return out
 
 
 def status_string(code: int) -> str:

@@ -1,0 +1,650 @@
+// mlp.cu -- the learned drag closure (not in the paper): a small multilayer
+// perceptron c = f(features) that scales the drag computed from stale bulk
+// fields, trained and evaluated by this library's own tensor-core kernels.
+//
+// Network (features padded to 16 inputs, hidden width 64):
+//   Z1 = X W1 + b1, A1 = GELU(Z1); Z2 = A1 W2 + b2, A2 = GELU(Z2); c = A2 w3 + b3
+// GELU is the exact erf form.  Weights are kept as FP32 master copies; the
+// matrix products take BF16 operands with FP32 accumulation on the 5th
+// generation tensor cores: a CTA of 128 threads owns a tile of 128 rows,
+// stages BF16 operands in shared memory in the no-swizzle K-major
+// core-matrix layout, one thread issues tcgen05.mma into tensor memory
+// (TMEM), completion is tracked by an mbarrier (bounded wait), and each
+// thread reads back its row with tcgen05.ld.  The small weight-gradient
+// products (A^T dZ) run in FP32 on the CUDA cores in a fixed order, so
+// training is deterministic.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include <cuda_bf16.h>
+
+#include "cg_internal.cuh"
+
+namespace cg {
+namespace mlp {
+
+constexpr int K0 = 16;                 // padded input width
+constexpr int H = 64;                  // hidden width
+constexpr int NFEAT = 7;               // used inputs
+constexpr int FEAT_STRIDE = 8;         // floats per feature row in memory
+constexpr int OFF_W1 = 0;              // [K0][H]
+constexpr int OFF_B1 = OFF_W1 + K0 * H;
+constexpr int OFF_W2 = OFF_B1 + H;     // [H][H] (in, out)
+constexpr int OFF_B2 = OFF_W2 + H * H;
+constexpr int OFF_W3 = OFF_B2 + H;
+constexpr int OFF_B3 = OFF_W3 + H;
+constexpr int NPARAM = OFF_B3 + 1;     // 5313
+constexpr int TILE = 128;              // rows per CTA tile
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMEM / mbarrier primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bounded wait for the given phase parity; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(saddr(bar)), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between 8-row groups along M (or N).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulate, both
+// operands K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) in a K-major core-matrix tile with K columns.
+__host__ __device__ constexpr uint32_t koff(int row, int k, int K) {
+    return (uint32_t)((row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// Store 8 consecutive K values of one row (one 16-byte core-matrix row).
+__device__ __forceinline__ void st_row8(unsigned char* tile, int row, int k0, int K, const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = (uint32_t)bf16_bits(v[2 * i]) | ((uint32_t)bf16_bits(v[2 * i + 1]) << 16);
+    *reinterpret_cast<uint4*>(tile + koff(row, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of a CTA
+// ---------------------------------------------------------------------------
+struct Smem {
+    alignas(128) unsigned char W1t[H * K0 * 2];    // B of GEMM 1: (n = hidden, k = input)
+    alignas(128) unsigned char W2t[H * H * 2];     // B of GEMM 2: (n = out, k = in)
+    alignas(128) unsigned char W2b[H * H * 2];     // B of the dA1 product: (n = in, k = out)
+    alignas(128) unsigned char X[TILE * K0 * 2];   // A of GEMM 1
+    alignas(128) unsigned char A1[TILE * H * 2];   // A of GEMM 2 (BF16 GELU(Z1))
+    alignas(128) unsigned char dZ2b[TILE * H * 2]; // A of the dA1 product (BF16 dZ2)
+    float b1[H], b2[H], w3[H];
+    float lo[FEAT_STRIDE], inv[FEAT_STRIDE];
+    float b3;
+    uint64_t bar;
+    uint32_t tmem;
+    int fail;
+};
+struct SmemTrain {
+    Smem s;
+    float dZ2[TILE][H + 1];   // FP32 dZ2 (padded against bank conflicts)
+    float dZ1[TILE][H + 1];   // FP32 dZ1
+    float A2dc[TILE][H + 1];  // A2 * dc, for the w3 gradient
+    float dc[TILE];
+    float r2[TILE];
+};
+
+// Load the BF16 operand copies of the weights and the FP32 vectors.
+__device__ void load_weights(Smem& s, const float* __restrict__ P, const float* __restrict__ scale) {
+    for (int e = threadIdx.x; e < H * K0; e += blockDim.x) {
+        const int n = e / K0, k = e % K0;   // W1t(n, k) = W1[k][n]
+        *reinterpret_cast<uint16_t*>(s.W1t + koff(n, k, K0)) = bf16_bits(P[OFF_W1 + k * H + n]);
+    }
+    for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+        const int i = e / H, o = e % H;     // W2[i][o]
+        const uint16_t b = bf16_bits(P[OFF_W2 + i * H + o]);
+        *reinterpret_cast<uint16_t*>(s.W2t + koff(o, i, H)) = b;   // (n = out, k = in)
+        *reinterpret_cast<uint16_t*>(s.W2b + koff(i, o, H)) = b;   // (n = in, k = out)
+    }
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+        s.b1[j] = P[OFF_B1 + j];
+        s.b2[j] = P[OFF_B2 + j];
+        s.w3[j] = P[OFF_W3 + j];
+    }
+    if (threadIdx.x < FEAT_STRIDE) {
+        s.lo[threadIdx.x] = scale[threadIdx.x];
+        s.inv[threadIdx.x] = scale[FEAT_STRIDE + threadIdx.x];
+    }
+    if (threadIdx.x == 0) s.b3 = P[OFF_B3];
+}
+
+// Scaled network input of one row from raw features; returns in-range.
+__device__ __forceinline__ bool scale_row(const Smem& s, const float* f, float (&x)[K0]) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < K0; ++k) x[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < NFEAT; ++k) {
+        const float v = (f[k] - s.lo[k]) * s.inv[k];
+        ok = ok && (v >= 0.f && v <= 1.f);
+        x[k] = v;
+    }
+    return ok;
+}
+
+// CTA set-up: TMEM columns and the mbarrier.
+__device__ void cta_setup(Smem& s, uint32_t ncols) {
+    if (threadIdx.x < 32) tmem_alloc(&s.tmem, ncols);
+    if (threadIdx.x == 0) {
+        mbar_init(&s.bar, 1);
+        s.fail = 0;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+__device__ void cta_teardown(Smem& s, uint32_t ncols) {
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (s.fail && threadIdx.x == 0) {
+        // a wait expired: give the tensor core one more bounded wait for the
+        // product still in flight before its TMEM columns are released
+        mbar_wait(&s.bar, 0);
+        mbar_wait(&s.bar, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(s.tmem, ncols);
+}
+
+// Dynamic shared memory rounded up to a 1 KB boundary (the launch adds slack).
+template <typename S>
+__device__ __forceinline__ S& smem_as(unsigned char* raw) {
+    const uintptr_t a = ((uintptr_t)raw + 1023) & ~(uintptr_t)1023;
+    return *reinterpret_cast<S*>(a);
+}
+
+// Issue the GEMM(s) of one stage from thread 0 and wait for completion.
+// Returns false (and marks the CTA failed) if the bounded wait expires.
+__device__ bool run_stage(Smem& s, int stage, uint32_t& phase, unsigned long long* status) {
+    fence_async_smem();   // make this thread's shared-memory stores visible to the tensor core
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t tm = s.tmem;
+        if (stage == 0) {   // Z1 (cols 0..63) = X[128x16] W1
+            umma(tm, sdesc(saddr(s.X), 128, 256), sdesc(saddr(s.W1t), 128, 256), idesc_bf16(TILE, H), 0);
+        } else if (stage == 1) {   // Z2 (cols 64..127) = A1[128x64] W2
+#pragma unroll
+            for (int kk = 0; kk < H / 16; ++kk)
+                umma(tm + 64, sdesc(saddr(s.A1) + kk * 256, 128, 1024), sdesc(saddr(s.W2t) + kk * 256, 128, 1024),
+                     idesc_bf16(TILE, H), kk > 0);
+        } else {   // dA1 (cols 128..191) = dZ2[128x64] W2^T
+#pragma unroll
+            for (int kk = 0; kk < H / 16; ++kk)
+                umma(tm + 128, sdesc(saddr(s.dZ2b) + kk * 256, 128, 1024),
+                     sdesc(saddr(s.W2b) + kk * 256, 128, 1024), idesc_bf16(TILE, H), kk > 0);
+        }
+        umma_commit(&s.bar);
+    }
+    const bool mine = mbar_wait(&s.bar, phase);
+    phase ^= 1u;
+    // the whole CTA agrees on the outcome, so no thread leaves a loop alone
+    const bool failed = __syncthreads_or(!mine) != 0;
+    if (failed && threadIdx.x == 0) {
+        s.fail = 1;
+        atomicAdd(&status[ST_TIMEOUT], 1ull);
+        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_TIMEOUT);
+    }
+    fence_after();
+    return !failed;
+}
+
+// TMEM address of this thread's lane at a column.
+__device__ __forceinline__ uint32_t lane_addr(const Smem& s, int col) {
+    return s.tmem + ((uint32_t)((threadIdx.x & ~31) & 127) << 16) + (uint32_t)col;
+}
+
+// Forward of the tile: rows' X already in s.X.  Leaves Z1 / Z2 (without
+// bias) in TMEM and returns this thread's output c.
+__device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c) {
+    if (!run_stage(s, 0, phase, status)) return false;
+    const int row = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < H / 16; ++q) {
+        float z[16];
+        tmem_ld16(lane_addr(s, 16 * q), z);
+        float a[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[i] = gelu(z[i] + s.b1[16 * q + i]);
+        st_row8(s.A1, row, 16 * q, H, a);
+        st_row8(s.A1, row, 16 * q + 8, H, a + 8);
+    }
+    if (!run_stage(s, 1, phase, status)) return false;
+    float acc = s.b3;
+#pragma unroll
+    for (int q = 0; q < H / 16; ++q) {
+        float z[16];
+        tmem_ld16(lane_addr(s, 64 + 16 * q), z);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc = fmaf(gelu(z[i] + s.b2[16 * q + i]), s.w3[16 * q + i], acc);
+    }
+    c = acc;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+// c for every feature row (rows outside the training box still get c; the
+// in-range flag tells the caller).
+__global__ void __launch_bounds__(TILE, 1)
+k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
+              long long n, float* __restrict__ c_out, int32_t* __restrict__ in_range,
+              unsigned long long* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& s = smem_as<Smem>(smem_raw);
+    load_weights(s, P, scale);
+    cta_setup(s, 256);
+    uint32_t phase = 0;
+    const long long ntiles = (n + TILE - 1) / TILE;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long r = t * TILE + threadIdx.x;
+        float f[FEAT_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (r < n) {
+            const float4 a = reinterpret_cast<const float4*>(feat)[2 * r];
+            const float4 b = reinterpret_cast<const float4*>(feat)[2 * r + 1];
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+        }
+        float x[K0];
+        const bool ok = scale_row(s, f, x);
+        st_row8(s.X, threadIdx.x, 0, K0, x);
+        st_row8(s.X, threadIdx.x, 8, K0, x + 8);
+        float c = 0.f;
+        if (!tile_forward(s, phase, status, c)) break;
+        if (r < n) {
+            c_out[r] = c;
+            if (in_range) in_range[r] = ok ? 1 : 0;
+        }
+    }
+    cta_teardown(s, 256);
+}
+
+// Loss and gradient partials of a batch: each CTA accumulates its tiles'
+// contributions in a fixed order and writes one partial per parameter.
+// Layout of part: [gridDim.x][NPARAM + 1] (the last entry: sum of residual^2).
+__global__ void __launch_bounds__(TILE, 1)
+k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
+           const float* __restrict__ target, long long n, float* __restrict__ part,
+           unsigned long long* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SmemTrain& st = smem_as<SmemTrain>(smem_raw);
+    Smem& s = st.s;
+    load_weights(s, P, scale);
+    cta_setup(s, 256);
+    uint32_t phase = 0;
+    const int tid = threadIdx.x;
+    const float inv_n = 1.0f / (float)n;
+    // this thread's gradient accumulators: W2 entries tid*32 .. +32 (flattened
+    // (in, out)), W1 entries tid*8 .. +8, bias / w3 entries for tid < 64
+    float gW2[32], gW1[8];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) gW2[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gW1[i] = 0.f;
+    float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f, loss = 0.f;
+    const long long ntiles = (n + TILE - 1) / TILE;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long r = t * TILE + tid;
+        float f[FEAT_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float tg = 0.f;
+        if (r < n) {
+            const float4 a = reinterpret_cast<const float4*>(feat)[2 * r];
+            const float4 b = reinterpret_cast<const float4*>(feat)[2 * r + 1];
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+            tg = target[r];
+        }
+        float x[K0];
+        scale_row(s, f, x);
+        st_row8(s.X, tid, 0, K0, x);
+        st_row8(s.X, tid, 8, K0, x + 8);
+        float c = 0.f;
+        if (!tile_forward(s, phase, status, c)) break;
+        const float res = (r < n) ? (c - tg) : 0.f;
+        const float dc = 2.0f * res * inv_n;
+        st.dc[tid] = dc;
+        st.r2[tid] = res * res;
+        // dZ2 = dc w3 * GELU'(Z2); A2 dc for the w3 gradient
+#pragma unroll
+        for (int q = 0; q < H / 16; ++q) {
+            float z[16], d[16];
+            tmem_ld16(lane_addr(s, 64 + 16 * q), z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = 16 * q + i;
+                const float zz = z[i] + s.b2[j];
+                d[i] = dc * s.w3[j] * gelu_grad(zz);
+                st.dZ2[tid][j] = d[i];
+                st.A2dc[tid][j] = gelu(zz) * dc;
+            }
+            st_row8(s.dZ2b, tid, 16 * q, H, d);
+            st_row8(s.dZ2b, tid, 16 * q + 8, H, d + 8);
+        }
+        // dA1 = dZ2 W2^T on the tensor cores
+        if (!run_stage(s, 2, phase, status)) break;
+#pragma unroll
+        for (int q = 0; q < H / 16; ++q) {
+            float da[16], z1[16];
+            tmem_ld16(lane_addr(s, 128 + 16 * q), da);
+            tmem_ld16(lane_addr(s, 16 * q), z1);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) st.dZ1[tid][16 * q + i] = da[i] * gelu_grad(z1[i] + s.b1[16 * q + i]);
+        }
+        __syncthreads();
+        // weight gradients, rows summed in increasing order
+#pragma unroll 1
+        for (int row = 0; row < TILE; ++row) {
+            // W2 (in, out): entries tid*32 + e -> in = (tid*32+e) / 64, out = (tid*32+e) % 64
+            const int in = (tid * 32) / H, out0 = (tid * 32) % H;
+            const float a1 = bf16_val(*reinterpret_cast<const uint16_t*>(s.A1 + koff(row, in, H)));
+#pragma unroll
+            for (int e = 0; e < 32; ++e) gW2[e] = fmaf(a1, st.dZ2[row][out0 + e], gW2[e]);
+            // W1 (k, j): entries tid*8 + e -> k = (tid*8+e) / 64, j = (tid*8+e) % 64
+            const int k = (tid * 8) / H, j0 = (tid * 8) % H;
+            const float xk = bf16_val(*reinterpret_cast<const uint16_t*>(s.X + koff(row, k, K0)));
+#pragma unroll
+            for (int e = 0; e < 8; ++e) gW1[e] = fmaf(xk, st.dZ1[row][j0 + e], gW1[e]);
+            if (tid < H) {
+                gb1 += st.dZ1[row][tid];
+                gb2 += st.dZ2[row][tid];
+                gw3 += st.A2dc[row][tid];
+            } else if (tid == H) {
+                gb3 += st.dc[row];
+                loss += st.r2[row];
+            }
+        }
+        __syncthreads();
+    }
+    float* out = part + (long long)blockIdx.x * (NPARAM + 1);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) out[OFF_W2 + tid * 32 + e] = gW2[e];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) out[OFF_W1 + tid * 8 + e] = gW1[e];
+    if (tid < H) {
+        out[OFF_B1 + tid] = gb1;
+        out[OFF_B2 + tid] = gb2;
+        out[OFF_W3 + tid] = gw3;
+    } else if (tid == H) {
+        out[OFF_B3] = gb3;
+        out[NPARAM] = loss;
+    }
+    cta_teardown(s, 256);
+}
+
+// Sum the CTA partials (fixed order), optionally apply one Adam step.
+__global__ void __launch_bounds__(256)
+k_mlp_reduce_adam(const float* __restrict__ part, int nparts, float* __restrict__ grads, float* __restrict__ P,
+                  float* __restrict__ m, float* __restrict__ v, int t, float lr, int do_update,
+                  float* __restrict__ loss_out, long long n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > NPARAM) return;
+    float g = 0.f;
+    for (int b = 0; b < nparts; ++b) g += part[(long long)b * (NPARAM + 1) + i];
+    if (i == NPARAM) {
+        if (loss_out) loss_out[0] = g / (float)n;
+        return;
+    }
+    grads[i] = g;
+    if (do_update) {
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / (1.f - powf(b1, (float)t));
+        const float vh = vi / (1.f - powf(b2, (float)t));
+        P[i] -= lr * mh / (sqrtf(vh) + eps);
+    }
+}
+
+}  // namespace mlp
+}  // namespace cg
+
+// ---------------------------------------------------------------------------
+// Handle and C ABI
+// ---------------------------------------------------------------------------
+struct cg_mlp {
+    cudaStream_t stream = nullptr;
+    int num_sms = 148;
+    float* P = nullptr;        // FP32 master parameters
+    float* m = nullptr;        // Adam first moments
+    float* v = nullptr;        // Adam second moments
+    float* grads = nullptr;    // last reduced gradient
+    float* scale = nullptr;    // lo[8], 1/(hi - lo)[8]
+    float* part = nullptr;     // CTA partials
+    unsigned long long* status = nullptr;
+    float lo[8] = {0}, hi[8] = {0};
+    int t = 0;
+    const void* var_bulk = nullptr;   // bound inputs of the fused learned drag
+    const void* u_fine = nullptr;
+};
+
+namespace {
+using namespace cg::mlp;
+
+size_t smem_forward() { return sizeof(Smem) + 1024; }
+size_t smem_train() { return sizeof(SmemTrain) + 1024; }
+bool g_mlp_attr = false;
+
+cg_status mlp_attrs() {
+    if (g_mlp_attr) return CG_OK;
+    // at least ~76 KB of shared memory per CTA, so at most two CTAs share an
+    // SM and their 256 TMEM columns each always fit in the SM's 512
+    const int fwd = (int)std::max<size_t>(smem_forward(), 80 * 1024);
+    CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+    CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
+    g_mlp_attr = true;
+    return CG_OK;
+}
+
+void host_scale(const float* lo, const float* hi, float out[16]) {
+    for (int k = 0; k < 8; ++k) {
+        out[k] = lo[k];
+        const float r = hi[k] - lo[k];
+        out[8 + k] = r > 0.f ? 1.0f / r : 0.f;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_mlp_create(const float* params, const float* feat_lo, const float* feat_hi, void* cuda_stream,
+                        cg_mlp** out) {
+    if (!out) return CG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || !feat_lo || !feat_hi) return CG_ERR_INVALID_ARG;
+    for (int k = 0; k < NFEAT; ++k)
+        if (!(feat_hi[k] > feat_lo[k]) || !isfinite(feat_lo[k]) || !isfinite(feat_hi[k])) return CG_ERR_INVALID_ARG;
+    cg_mlp* m = new (std::nothrow) cg_mlp();
+    if (!m) return CG_ERR_OOM;
+    m->stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < 8; ++k) {
+        m->lo[k] = k < NFEAT ? feat_lo[k] : 0.f;
+        m->hi[k] = k < NFEAT ? feat_hi[k] : 1.f;
+    }
+    float sc[16];
+    host_scale(m->lo, m->hi, sc);
+    const size_t pb = sizeof(float) * NPARAM;
+    const size_t partb = sizeof(float) * (size_t)(NPARAM + 1) * (size_t)(2 * m->num_sms);
+    bool ok = cudaMalloc(&m->P, pb) == cudaSuccess && cudaMalloc(&m->m, pb) == cudaSuccess &&
+              cudaMalloc(&m->v, pb) == cudaSuccess && cudaMalloc(&m->grads, pb) == cudaSuccess &&
+              cudaMalloc(&m->scale, sizeof sc) == cudaSuccess && cudaMalloc(&m->part, partb) == cudaSuccess &&
+              cudaMalloc(&m->status, sizeof(unsigned long long) * cg::kNumSlots) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->P, params, pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(m->m, 0, pb) == cudaSuccess && cudaMemset(m->v, 0, pb) == cudaSuccess &&
+         cudaMemcpy(m->scale, sc, sizeof sc, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(m->status, 0, sizeof(unsigned long long) * cg::kNumSlots) == cudaSuccess;
+    if (!ok || mlp_attrs() != CG_OK) {
+        cudaGetLastError();
+        cudaFree(m->P); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grads); cudaFree(m->scale);
+        cudaFree(m->part); cudaFree(m->status);
+        delete m;
+        return CG_ERR_OOM;
+    }
+    *out = m;
+    return CG_OK;
+}
+
+cg_status cg_mlp_destroy(cg_mlp* m) {
+    if (!m) return CG_OK;
+    cudaStreamSynchronize(m->stream);
+    cudaFree(m->P); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grads); cudaFree(m->scale);
+    cudaFree(m->part); cudaFree(m->status);
+    cudaGetLastError();
+    delete m;
+    return CG_OK;
+}
+
+cg_status cg_mlp_get_params(cg_mlp* m, float* params, float* grads) {
+    if (!m) return CG_ERR_INVALID_ARG;
+    CG_CUDA(cudaStreamSynchronize(m->stream));
+    if (params) CG_CUDA(cudaMemcpy(params, m->P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    if (grads) CG_CUDA(cudaMemcpy(grads, m->grads, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    return CG_OK;
+}
+
+cg_status cg_mlp_set_params(cg_mlp* m, const float* params) {
+    if (!m || !params) return CG_ERR_INVALID_ARG;
+    CG_CUDA(cudaMemcpyAsync(m->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, m->stream));
+    CG_CUDA(cudaStreamSynchronize(m->stream));
+    return CG_OK;
+}
+
+cg_status cg_mlp_forward(cg_mlp* m, int64_t n, const float* features, float* c_out, int32_t* in_range_out) {
+    if (!m || n < 0 || (n > 0 && (!features || !c_out || ((uintptr_t)features & 15u)))) return CG_ERR_INVALID_ARG;
+    if (n == 0) return CG_OK;
+    CG_TRY(mlp_attrs());
+    const long long ntiles = (n + TILE - 1) / TILE;
+    const unsigned grid = (unsigned)std::min(ntiles, (long long)2 * m->num_sms);
+    const size_t sm = std::max<size_t>(smem_forward(), 80 * 1024);
+    k_mlp_forward<<<grid, TILE, sm, m->stream>>>(m->P, m->scale, features, n, c_out, in_range_out, m->status);
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+static cg_status grad_impl(cg_mlp* m, int64_t n, const float* features, const float* targets, float lr,
+                           int do_update, float* loss_out) {
+    if (!m || n <= 0 || !features || !targets || ((uintptr_t)features & 15u)) return CG_ERR_INVALID_ARG;
+    CG_TRY(mlp_attrs());
+    const long long ntiles = (n + TILE - 1) / TILE;
+    const int grid = (int)std::min(ntiles, (long long)m->num_sms);
+    k_mlp_grad<<<grid, TILE, smem_train(), m->stream>>>(m->P, m->scale, features, targets, n, m->part, m->status);
+    CG_CUDA(cudaGetLastError());
+    if (do_update) m->t += 1;
+    k_mlp_reduce_adam<<<(NPARAM + 1 + 255) / 256, 256, 0, m->stream>>>(m->part, grid, m->grads, m->P, m->m, m->v,
+                                                                        m->t, lr, do_update, loss_out, n);
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+cg_status cg_mlp_grads(cg_mlp* m, int64_t n, const float* features, const float* targets, float* loss_out) {
+    return grad_impl(m, n, features, targets, 0.f, 0, loss_out);
+}
+
+cg_status cg_mlp_train_step(cg_mlp* m, int64_t n, const float* features, const float* targets, float lr,
+                            float* loss_out) {
+    if (!(lr > 0.f) || !isfinite(lr)) return CG_ERR_INVALID_ARG;
+    return grad_impl(m, n, features, targets, lr, 1, loss_out);
+}
+
+cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags) {
+    if (!m) return CG_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CG_ERR_CUDA;
+    }
+    unsigned long long h[cg::kNumSlots];
+    CG_CUDA(cudaMemcpy(h, m->status, sizeof h, cudaMemcpyDeviceToHost));
+    CG_CUDA(cudaMemset(m->status, 0, sizeof h));
+    if (flags) *flags = (uint32_t)h[cg::ST_FLAGS];
+    return (h[cg::ST_FLAGS] & CG_FLAG_TIMEOUT) ? CG_ERR_TIMEOUT : CG_OK;
+}
+
+}  // extern "C"

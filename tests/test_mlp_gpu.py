@@ -1,0 +1,123 @@
+"""The learned closure's tensor-core kernels against the FP64 oracle.
+
+The oracle runs in its bf16 mode: the operands of the matrix products are
+rounded to bfloat16 where the kernels round them, and everything else is
+float64.  The remaining differences are FP32 accumulation and FP32 GELU in
+the kernels, plus rare one-ulp differences in re-rounding a hidden
+activation to bfloat16 when it sits on a rounding boundary (each moves c by
+at most ~2^-8 of one term).  Tolerances below are set from that: c within
+5e-3 absolute (c ~ 1), gradients within 1e-2 relative per parameter block
+(norm-wise), Adam within 1e-5 of the oracle's update of the same gradient.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as om
+
+pytestmark = pytest.mark.gpu
+
+LO = np.array([0.1, 0.0, 0.0, -20.0, -20.0, -20.0, 0.0], np.float32)
+HI = np.array([1.0, 4.0, 1.0, 20.0, 20.0, 20.0, 0.05], np.float32)
+
+
+def scaled(feat):
+    """Network input exactly as the kernel forms it (float32 ops)."""
+    f = feat[:, :7].astype(np.float32)
+    inv = (np.float32(1.0) / (HI - LO)).astype(np.float32)
+    x = np.zeros((feat.shape[0], om.K0))
+    x[:, :7] = ((f - LO) * inv).astype(np.float32)
+    return x
+
+
+def random_features(n, seed):
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n, 8), np.float32)
+    f[:, :7] = LO + (HI - LO) * rng.random((n, 7)).astype(np.float32)
+    return f
+
+
+def make(cg, seed=0):
+    p = om.init_params(hidden=64, seed=seed)
+    rng = np.random.default_rng(seed + 10)
+    p["b1"] = rng.normal(size=64) * 0.1
+    p["b2"] = rng.normal(size=64) * 0.1
+    m = cg.Mlp(cg.mlp_pack(p), LO, HI)
+    return m, cg.mlp_unpack(cg.mlp_pack(p))
+
+
+def test_forward_matches_oracle(cuda_lib):
+    import torch
+    m, p = make(cuda_lib, 0)
+    n = 1000                      # 8 tiles of 128, ragged tail
+    feat = random_features(n, 1)
+    f_d = torch.from_numpy(feat).cuda()
+    c = torch.empty(n, device="cuda")
+    ok = torch.empty(n, dtype=torch.int32, device="cuda")
+    m.forward(f_d, c, ok)
+    assert m.sync_status()[0] == 0
+    want, _ = om.forward(p, scaled(feat), bf16_inputs=True)
+    got = c.cpu().numpy()
+    err = np.abs(got - want)
+    print("forward max abs err", err.max(), "median", np.median(err))
+    assert err.max() < 5e-3 and np.median(err) < 1e-4
+    assert ok.cpu().numpy().all()
+    feat[5, 0] = HI[0] * 1.5      # out of the training box
+    m.forward(torch.from_numpy(feat).cuda(), c, ok)
+    assert ok.cpu().numpy()[5] == 0 and ok.cpu().numpy()[4] == 1
+    m.close()
+
+
+def test_gradients_match_oracle(cuda_lib):
+    import torch
+    m, p = make(cuda_lib, 1)
+    n = 777
+    feat = random_features(n, 2)
+    rng = np.random.default_rng(3)
+    target = (1.0 + 0.3 * rng.normal(size=n)).astype(np.float32)
+    loss = torch.zeros(1, device="cuda")
+    m.grads(torch.from_numpy(feat).cuda(), torch.from_numpy(target).cuda(), loss)
+    _, g_flat = m.params(grads=True)
+    g = cuda_lib.mlp_unpack(g_flat)
+    want_loss, want = om.loss_and_grads(p, scaled(feat), target.astype(np.float64), bf16_inputs=True)
+    assert loss.item() == pytest.approx(want_loss, rel=1e-3)
+    for k in want:
+        num = np.linalg.norm(g[k] - want[k])
+        den = np.linalg.norm(want[k])
+        print(k, num / den)
+        assert num <= 1e-2 * den, (k, num / den)
+    m.close()
+
+
+def test_adam_step_matches_oracle_update(cuda_lib):
+    import torch
+    m, p = make(cuda_lib, 2)
+    n = 512
+    feat = torch.from_numpy(random_features(n, 4)).cuda()
+    target = torch.full((n,), 1.2, device="cuda")
+    p0 = m.params().astype(np.float64)
+    m.train_step(feat, target, 1e-3)
+    p1, g = m.params(grads=True)
+    z = {"w": np.zeros_like(p0)}
+    P, _, _ = om.adam_step({"w": p0}, {"w": g.astype(np.float64)}, z, z, 1, 1e-3)
+    assert np.max(np.abs(p1 - P["w"])) < 1e-5
+    m.close()
+
+
+def test_training_fits_a_smooth_target(cuda_lib):
+    import torch
+    m, _ = make(cuda_lib, 3)
+    n = 8192
+    feat_np = random_features(n, 5)
+    x = scaled(feat_np)
+    target_np = (1.0 + 0.3 * x[:, 0] - 0.2 * x[:, 2] ** 2 + 0.1 * x[:, 6]).astype(np.float32)
+    feat = torch.from_numpy(feat_np).cuda()
+    target = torch.from_numpy(target_np).cuda()
+    loss = torch.zeros(1, device="cuda")
+    m.grads(feat, target, loss)
+    l0 = loss.item()
+    for _ in range(400):
+        m.train_step(feat, target, 2e-3, loss)
+    assert m.sync_status()[0] == 0
+    print("loss", l0, "->", loss.item())
+    assert loss.item() < 0.02 * l0
+    m.close()
