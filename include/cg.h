@@ -70,6 +70,9 @@ enum {
     CG_FLAG_TIMEOUT = 8u       /* a bounded device wait gave up              */
 };
 
+/* Number of counters returned by cg_sync_status. */
+#define CG_NCOUNTS 5
+
 /* Number of entries of the conservation-sum vector written by cg_step. */
 #define CG_NSUMS 16
 
@@ -191,7 +194,11 @@ cg_status cg_average_fine_to_bulk(cg_grids* g, const void* u_fine, void* u_bulk,
  * correlation.  pos_d, vel: [n] T4; eps_bulk: double [n_b]; u_bulk: [3][n_b] T;
  * force_out: [3][n] T.  When S_bulk_out ([3][n_b] T) is not NULL the
  * reaction S = -(1/V_B) sum F is deposited in the same pass (needs the
- * binning of this n).  mlp must be NULL (plain correlation). */
+ * binning of this n).  mlp NULL: the plain correlation.  mlp set (FP32
+ * grids only; cg_mlp_bind first): u_bulk is the stale fluid record and the
+ * learned closure of cg_drag_learned below is applied (its fallback reads
+ * the bound fine field); the closure's parameters must be ready on this
+ * handle's stream (same stream, or synchronised). */
 cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel,
                   const double* eps_bulk, const void* u_bulk,
                   void* force_out, void* S_bulk_out, const cg_mlp* mlp);
@@ -214,6 +221,19 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
  * porosity was clamped. */
 cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
                   const cg_step_out* out, double dt);
+
+/* Learned coupling step (closure below; not in the paper).  refresh != 0:
+ * exactly cg_step, which also writes the fresh u_bulk and var_bulk that
+ * later steps use as their stale record.  refresh == 0: the fine -> bulk
+ * average is skipped; out->u_bulk and out->var_bulk are then INPUTS (the
+ * record of the last refresh, left unchanged) and the drag is the learned
+ * closure F = c F_stale, falling back per particle to the plain drag with
+ * the fluid velocity averaged afresh from u_fine when its features lie
+ * outside the closure's box (counted: cg_sync_status counts[4]).  The drag
+ * diagnostics of sums (0, 2..4, 11..15) are NaN on such steps.  FP32 grids
+ * only; out->var_bulk required. */
+cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine,
+                          const cg_step_out* out, double dt, const cg_mlp* mlp, int32_t refresh);
 
 /* cg_step on HOST buffers: copies the inputs to handle-owned device
  * buffers, runs cg_step, copies every requested output back and waits for
@@ -262,13 +282,32 @@ cg_status cg_mlp_grads(cg_mlp* m, int64_t n, const float* features, const float*
 cg_status cg_mlp_train_step(cg_mlp* m, int64_t n, const float* features, const float* targets, float lr,
                             float* loss_out);
 
+/* Closure inputs and training targets at every particle, in either
+ * precision: features [n][8] float (layout above) from the porosity of
+ * this step (eps_bulk, double [n_b]) and the stale record (u_stale [3][n_b]
+ * T, var_stale [n_b] T), with the porosity gradient that of the trilinear
+ * interpolant (zero along an axis where the particle is in the outer half
+ * cell, and everywhere in cell-value mode); target [n] float
+ * c* = (F_fresh . F_stale) / |F_stale|^2 (1 where F_stale = 0), F_fresh
+ * the drag with u_fresh [3][n_b] T.  pos_d, vel, features 16-byte aligned.
+ * Enqueued on the grids' stream. */
+cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void* vel, const double* eps_bulk,
+                          const void* u_stale, const void* var_stale, const void* u_fresh,
+                          float* features_out, float* target_out);
+
+/* Bind the stale variance field (var [n_b] float) and the fine velocity
+ * (u_fine [3][n_f] float, 16-byte aligned) read by cg_drag with this
+ * closure; both NULL unbinds.  The pointers are kept, not copied. */
+cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine);
+
 /* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
  * kernels expired (flags: CG_FLAG_*). */
 cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags);
 
 /* Wait for the handle's stream and read-and-clear the device status word.
- * flags (nullable) gets CG_FLAG_* bits; counts (nullable, 4 entries) gets
- * particles outside, non-finite positions, clamped porosities, timeouts.
+ * flags (nullable) gets CG_FLAG_* bits; counts (nullable, CG_NCOUNTS
+ * entries) gets particles outside, non-finite positions, clamped
+ * porosities, timeouts, learned-drag fallbacks.
  * Returns CG_ERR_NONFINITE / CG_ERR_TIMEOUT when those bits are set,
  * CG_ERR_CUDA if the stream holds an error, else CG_OK. */
 cg_status cg_sync_status(cg_grids* g, uint32_t* flags, int64_t* counts);

@@ -32,6 +32,7 @@ CG_INTERP_TRILINEAR, CG_INTERP_CELL = 0, 1
 CG_DEP_VOLUME, CG_DEP_MOMENTUM = 0, 1
 CG_FLAG_OUTSIDE, CG_FLAG_NONFINITE, CG_FLAG_EPS_CLAMPED, CG_FLAG_TIMEOUT = 1, 2, 4, 8
 CG_NSUMS = 16
+CG_NCOUNTS = 5
 SUM_NAMES = ["vol_particles", "vol_deposited", "F_x", "F_y", "F_z", "SbVb_x", "SbVb_y", "SbVb_z",
              "SfVf_x", "SfVf_y", "SfVf_z", "F_abs", "mom_x", "mom_y", "mom_z", "n_clamped"]
 
@@ -94,6 +95,11 @@ _SIGS = {
     "cg_mlp_grads": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p]),
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_step_learned": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double,
+                                  C.c_void_p, C.c_int32]),
 }
 
 MLP_NPARAM = 5313
@@ -221,7 +227,7 @@ class Grids:
         _check(lib().cg_average_fine_to_bulk(self.h, _ptr(u_fine), _ptr(u_bulk), _ptr(var_bulk)),
                "cg_average_fine_to_bulk")
 
-    def cg_drag(self, pos_d, vel, eps_bulk, u_bulk, force, S_bulk=None):
+    def cg_drag(self, pos_d, vel, eps_bulk, u_bulk, force, S_bulk=None, mlp=None):
         import torch
         n = pos_d.shape[0]
         self._t(pos_d, 4 * n, name="pos_d")
@@ -231,7 +237,7 @@ class Grids:
         self._t(force, 3 * n, name="force")
         self._t(S_bulk, 3 * self.n_bulk, name="S_bulk")
         _check(lib().cg_drag(self.h, n, _ptr(pos_d), _ptr(vel), _ptr(eps_bulk), _ptr(u_bulk), _ptr(force),
-                             _ptr(S_bulk), None), "cg_drag")
+                             _ptr(S_bulk), None if mlp is None else mlp.h), "cg_drag")
 
     def cg_project_bulk_to_fine(self, bulk, fine_out):
         ncomp = bulk.numel() // self.n_bulk
@@ -275,6 +281,34 @@ class Grids:
         so = self._out_struct(out)
         _check(lib().cg_step(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step")
 
+    def cg_step_learned(self, pos_d, vel, u_fine, out, mlp, refresh, dt=0.0):
+        """cg_step with the learned closure; without refresh out["u_bulk"] and
+        out["var_bulk"] are the stale record (inputs)."""
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(vel, 4 * n, name="vel")
+        self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
+        so = self._out_struct(out)
+        _check(lib().cg_step_learned(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt), mlp.h,
+                                     1 if refresh else 0), "cg_step_learned")
+
+    def cg_mlp_features(self, pos_d, vel, eps_bulk, u_stale, var_stale, u_fresh, features, target):
+        """Closure features [n][8] float32 and targets [n] float32 at every particle."""
+        import torch
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(vel, 4 * n, name="vel")
+        self._t(eps_bulk, self.n_bulk, torch.float64, "eps_bulk")
+        self._t(u_stale, 3 * self.n_bulk, name="u_stale")
+        self._t(var_stale, self.n_bulk, name="var_stale")
+        self._t(u_fresh, 3 * self.n_bulk, name="u_fresh")
+        self._t(features, 8 * n, torch.float32, "features")
+        self._t(target, n, torch.float32, "target")
+        _check(lib().cg_mlp_features(self.h, n, _ptr(pos_d), _ptr(vel), _ptr(eps_bulk), _ptr(u_stale),
+                                     _ptr(var_stale), _ptr(u_fresh), _ptr(features), _ptr(target)),
+               "cg_mlp_features")
+
     def cg_step_host(self, pos_d, vel, u_fine, out, dt=0.0):
         """Same as cg_step on host (CPU, ideally pinned) tensors; blocks."""
         n = pos_d.shape[0]
@@ -286,9 +320,9 @@ class Grids:
         _check(lib().cg_step_host(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step_host")
 
     def cg_sync_status(self):
-        """(return code, flags, [outside, nonfinite, clamped, timeouts])."""
+        """(return code, flags, [outside, nonfinite, clamped, timeouts, fallbacks])."""
         flags = C.c_uint32()
-        counts = (C.c_int64 * 4)()
+        counts = (C.c_int64 * CG_NCOUNTS)()
         rc = lib().cg_sync_status(self.h, C.byref(flags), counts)
         return rc, flags.value, list(counts)
 
@@ -380,6 +414,12 @@ class Mlp:
         flags = C.c_uint32()
         rc = lib().cg_mlp_sync_status(self.h, C.byref(flags))
         return rc, flags.value
+
+    def bind(self, var_stale, u_fine):
+        """Stale variance field and fine velocity read by Grids.cg_drag(mlp=self)
+        (float32 device tensors, kept alive by this object)."""
+        self._bound = (var_stale, u_fine)
+        _check(lib().cg_mlp_bind(self.h, _ptr(var_stale), _ptr(u_fine)), "cg_mlp_bind")
 
 
 def mlp_pack(p: dict):

@@ -62,6 +62,8 @@ cg_status check_handle(const cg_grids* g) { return g ? CG_OK : CG_ERR_INVALID_AR
 
 namespace cg {
 
+cg_status grow_buf(DevBuf& b, size_t bytes) { return ensure_buf(b, bytes); }
+
 // ---------------------------------------------------------------------------
 // Profiling plumbing
 // ---------------------------------------------------------------------------
@@ -210,7 +212,8 @@ static void free_all(cg_grids* g) {
     dfree(g->sums_scratch);
     dfree(g->status);
     DevBuf* st[] = {&g->st_pos, &g->st_vel, &g->st_ufine, &g->st_eps, &g->st_ub, &g->st_var, &g->st_Sb,
-                    &g->st_F,   &g->st_Sf,  &g->st_epsf,  &g->st_sums, &g->st_cell, &g->st_perm, &g->st_cs};
+                    &g->st_F,   &g->st_Sf,  &g->st_epsf,  &g->st_sums, &g->st_cell, &g->st_perm, &g->st_cs,
+                    &g->fresh4};
     for (DevBuf* b : st) {
         dfree(b->p);
         b->bytes = 0;
@@ -401,12 +404,20 @@ cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel, co
                   const void* u_bulk, void* force_out, void* S_bulk_out, const cg_mlp* mlp) {
     CG_TRY(check_handle(g));
     CG_TRY(check_n(n));
-    if (mlp) return CG_ERR_INVALID_ARG;
     if (!eps_bulk || !u_bulk) return CG_ERR_INVALID_ARG;
     if (n > 0 && (!pos_d || !vel || !force_out || !aligned16(pos_d) || !aligned16(vel))) return CG_ERR_INVALID_ARG;
     if (S_bulk_out && g->n_binned != n) return CG_ERR_NOT_BINNED;
+    const void* var_stale = nullptr;
+    const void* u_fine = nullptr;
+    if (mlp) {
+        if (g->fp64) return CG_ERR_INVALID_ARG;
+        CG_TRY(mlp_bound_inputs(mlp, &var_stale, &u_fine));
+    }
     CG_TRY(ensure_particle_capacity(g, n));
     CG_TRY(launch_pack(g, eps_bulk, u_bulk, false));
+    if (mlp)
+        return launch_drag_learned(g, mlp, n, const_cast<void*>(pos_d), const_cast<void*>(vel), var_stale, u_fine,
+                                   force_out, S_bulk_out, 0.0);
     return launch_drag(g, n, pos_d, vel, force_out, S_bulk_out, false, 0.0);
 }
 
@@ -442,15 +453,19 @@ static cg_status on_aux(cg_grids* g, Fn f) {
 //   aux :  average fine -> bulk      \-> project eps
 // The averaging reads only the fine field and the porosity projection only
 // the packed porosity, so both overlap the latency-bound particle kernels.
+//
+// With a learned closure and no refresh the averaging is skipped: u_bulk and
+// var_bulk are inputs (the record of the last refresh) and the drag is the
+// learned kernel, which reads the fine field only for its fallback rows.
 static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* o,
-                           double dt) {
+                           double dt, const cg_mlp* mlp = nullptr) {
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
     for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
     cudaStream_t side = g->prof ? g->stream : g->aux;
     CG_CUDA(cudaEventRecord(g->ev_fork, g->stream));
     CG_CUDA(cudaStreamWaitEvent(side, g->ev_fork, 0));
-    CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk); }));
+    if (!mlp) CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk); }));
     CG_CUDA(cudaEventRecord(g->ev_avg, side));
     CG_TRY(launch_bin(g, n, p->pos_d));
     CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
@@ -465,7 +480,10 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
         CG_TRY(on_aux(g, [&] { return launch_project(g, 1, ein, eout, false); }));
     }
     CG_CUDA(cudaEventRecord(g->ev_epsf, side));
-    CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
+    if (mlp)
+        CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, o->force, o->S_bulk, dt));
+    else
+        CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
     const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, nullptr};
     void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, nullptr};
@@ -494,6 +512,14 @@ cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine, const 
     CG_TRY(check_handle(g));
     CG_TRY(check_step_args(p, u_fine, out, dt, true));
     return step_impl(g, p, u_fine, out, dt);
+}
+
+cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out, double dt,
+                          const cg_mlp* mlp, int32_t refresh) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, true));
+    if (!mlp || g->fp64 || !out->var_bulk) return CG_ERR_INVALID_ARG;
+    return step_impl(g, p, u_fine, out, dt, refresh ? nullptr : mlp);
 }
 
 cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
@@ -576,6 +602,7 @@ cg_status cg_sync_status(cg_grids* g, uint32_t* flags, int64_t* counts) {
         counts[1] = (int64_t)h[ST_NONFINITE];
         counts[2] = (int64_t)h[ST_CLAMPED];
         counts[3] = (int64_t)h[ST_TIMEOUT];
+        counts[4] = (int64_t)h[ST_FALLBACK];
     }
     if (h[ST_FLAGS] & CG_FLAG_TIMEOUT) return CG_ERR_TIMEOUT;
     if (h[ST_FLAGS] & CG_FLAG_NONFINITE) return CG_ERR_NONFINITE;

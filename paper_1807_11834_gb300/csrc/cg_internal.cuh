@@ -26,7 +26,7 @@ constexpr int kScanItems = 4096;                    // elements per scan block
 constexpr int kNumSlots = 16;                       // status counters
 
 // Status word slots (unsigned long long each).
-enum { ST_FLAGS = 0, ST_OUTSIDE = 1, ST_NONFINITE = 2, ST_CLAMPED = 3, ST_TIMEOUT = 4 };
+enum { ST_FLAGS = 0, ST_OUTSIDE = 1, ST_NONFINITE = 2, ST_CLAMPED = 3, ST_TIMEOUT = 4, ST_FALLBACK = 5 };
 
 // Partial-sum regions of the conservation sums.
 enum { PS_VOL = 0, PS_DRAG = 1, PS_MOM = 2, PS_PROJ = 3, PS_NREG = 4 };
@@ -123,6 +123,7 @@ struct cg_grids {
     // host-buffer entry: device staging
     cg::DevBuf st_pos, st_vel, st_ufine, st_eps, st_ub, st_var, st_Sb, st_F, st_Sf, st_epsf,
         st_sums, st_cell, st_perm, st_cs;
+    cg::DevBuf fresh4;   // [nbulk] T4: (phi, u) of the fresh field of cg_mlp_features
 
     // second stream of the step: fine-grid work that does not depend on the
     // particle path runs beside it (fork / join through events)
@@ -189,6 +190,12 @@ cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* va
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
                       bool sums, double dt);
+// Learned drag (FP32 only): bulk4 must hold (phi of this step, stale u).
+cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
+                              const void* var_stale, const void* u_fine, void* force, void* S_bulk, double dt);
+cg_status grow_buf(DevBuf& b, size_t bytes);
+// The stale variance field and fine velocity bound to a closure by cg_mlp_bind.
+cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine);
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);
 cg_status launch_sums(cg_grids* g, double* sums);
 // First element (in units of T) of the partial region r.

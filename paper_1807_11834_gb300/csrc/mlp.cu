@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include "cg_internal.cuh"
+#include "drag_law.cuh"
 
 namespace cg {
 namespace mlp {
@@ -40,6 +41,7 @@ constexpr int OFF_B3 = OFF_W3 + H;
 constexpr int NPARAM = OFF_B3 + 1;     // 5313
 constexpr int TILE = 128;              // rows per CTA tile
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kLearnedCols = 128;  // TMEM columns of the learned drag (Z1 and Z2)
 
 // ---------------------------------------------------------------------------
 // tcgen05 / TMEM / mbarrier primitives (inline PTX)
@@ -480,6 +482,201 @@ k_mlp_reduce_adam(const float* __restrict__ part, int nparts, float* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Closure inputs and training targets at every particle (any precision):
+// features from the stale bulk record (porosity of this step, velocity and
+// variance of the last refresh), target c* = (F_fresh . F_stale) / |F_stale|^2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void closure_features(const Probe<T>& st, const V4<T>& x, const V4<T>& v,
+                                                 const GridDev& g, const Phys<T>& P, float (&f)[FEAT_STRIDE],
+                                                 T& epsc, T& phic, T (&s)[3], T& smag) {
+    T eps = T(1) - st.phi;
+    epsc = eps;
+    phic = st.phi;
+    if (eps < P.eps_min) {
+        epsc = P.eps_min;
+        phic = T(1) - P.eps_min;
+    }
+    s[0] = st.ux - v.x;
+    s[1] = st.uy - v.y;
+    s[2] = st.uz - v.z;
+    smag = M<T>::sqrt_(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    const T Re = P.rho_mu * epsc * x.w * smag;
+    f[0] = (float)epsc;
+    f[1] = (float)(sizeof(T) == 4 ? log10f((float)(T(1) + Re)) : log10((double)(T(1) + Re)));
+    f[2] = (float)smag;
+    f[3] = (float)(-st.gphi[0]);
+    f[4] = (float)(-st.gphi[1]);
+    f[5] = (float)(-st.gphi[2]);
+    f[6] = (float)st.sc;
+    f[7] = 0.f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_mlp_features(const T* __restrict__ pos, const T* __restrict__ vel, long long n, GridDev g, Phys<T> P,
+               const T* __restrict__ bulk_stale, const T* __restrict__ var_stale, const T* __restrict__ bulk_fresh,
+               float* __restrict__ feat, float* __restrict__ target) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const V4<T> x = ld4(pos, p), v = ld4(vel, p);
+        const Probe<T> st = probe(bulk_stale, var_stale, x.x, x.y, x.z, g);
+        const V4<T> fr = gather(bulk_fresh, x.x, x.y, x.z, g);
+        float f[FEAT_STRIDE];
+        T epsc, phic, s[3], smag;
+        closure_features(st, x, v, g, P, f, epsc, phic, s, smag);
+        const T bs = drag_beta(g.law, epsc, phic, x.w, smag, P);
+        const T sf[3] = {fr.y - v.x, fr.z - v.y, fr.w - v.z};
+        const T sfm = M<T>::sqrt_(sf[0] * sf[0] + sf[1] * sf[1] + sf[2] * sf[2]);
+        const T bf = drag_beta(g.law, epsc, phic, x.w, sfm, P);
+        T dot = 0, nn = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T Fs = bs * s[a], Ff = bf * sf[a];
+            dot += Ff * Fs;
+            nn += Fs * Fs;
+        }
+        reinterpret_cast<float4*>(feat)[2 * p] = make_float4(f[0], f[1], f[2], f[3]);
+        reinterpret_cast<float4*>(feat)[2 * p + 1] = make_float4(f[4], f[5], f[6], 0.f);
+        target[p] = nn > T(0) ? (float)(dot / nn) : 1.0f;
+    }
+}
+
+// Fresh fluid velocity at a point averaged on demand from the fine grid
+// (the fallback of the learned drag): mean of the r^3 fine cells of each
+// bulk cell the stencil touches, then the same interpolation as the gather.
+__device__ V4<float> fresh_velocity(const float* __restrict__ u_fine, float x, float y, float z, const GridDev& g) {
+    int i0[3] = {0, 0, 0};
+    float t[3] = {0.f, 0.f, 0.f};
+    const bool cell = g.interp == CG_INTERP_CELL;
+    if (cell) {
+        const int c = cell_of_f(x, y, z, g);
+        i0[0] = c % g.nb[0];
+        i0[1] = (c / g.nb[0]) % g.nb[1];
+        i0[2] = c / (g.nb[0] * g.nb[1]);
+    } else {
+        axis_weight(x, g, 0, i0[0], t[0]);
+        axis_weight(y, g, 1, i0[1], t[1]);
+        axis_weight(z, g, 2, i0[2], t[2]);
+    }
+    const int r = g.r;
+    const long long nx = g.nf[0], nxy = (long long)g.nf[0] * g.nf[1];
+    const float inv = 1.0f / (float)(r * r * r);
+    // per-axis pair of bulk values, interpolated x, then y, then z as the gather does
+    float corner[8][3];
+    for (int q = 0; q < (cell ? 1 : 8); ++q) {
+        const int I = i0[0] + (q & 1), J = i0[1] + ((q >> 1) & 1), K = i0[2] + (q >> 2);
+        float sum[3] = {0.f, 0.f, 0.f};
+        for (int dk = 0; dk < r; ++dk)
+            for (int dj = 0; dj < r; ++dj) {
+                const long long row = nx * (J * r + dj) + nxy * (K * r + dk) + (long long)I * r;
+                for (int di = 0; di < r; ++di)
+                    for (int c = 0; c < 3; ++c) sum[c] += __ldg(u_fine + c * g.nfine + row + di);
+            }
+        for (int c = 0; c < 3; ++c) corner[q][c] = sum[c] * inv;
+    }
+    if (cell) return {0.f, corner[0][0], corner[0][1], corner[0][2]};
+    float u[3];
+    for (int c = 0; c < 3; ++c) {
+        const float a00 = lerp_(corner[0][c], corner[1][c], t[0]), a10 = lerp_(corner[2][c], corner[3][c], t[0]);
+        const float a01 = lerp_(corner[4][c], corner[5][c], t[0]), a11 = lerp_(corner[6][c], corner[7][c], t[0]);
+        u[c] = lerp_(lerp_(a00, a10, t[1]), lerp_(a01, a11, t[1]), t[2]);
+    }
+    return {0.f, u[0], u[1], u[2]};
+}
+
+// Learned drag: per tile of 128 particles (caller order) each thread forms
+// its particle's closure inputs and the drag F_stale from the stale bulk
+// record (porosity of this step, fluid velocity and variance of the last
+// refresh); the tile goes through the network on the tensor cores; in
+// range F = c F_stale, otherwise F is the plain drag with the fluid
+// velocity averaged afresh from the fine grid.  The force is also written
+// to its sorted slot for the fused reaction deposit when Fs is given, and
+// with dt > 0 the particle is advanced as the plain drag kernel does.
+__global__ void __launch_bounds__(TILE, 1)
+k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, const float* __restrict__ bulk_stale,
+               const float* __restrict__ var_stale, const float* __restrict__ u_fine, const float* __restrict__ Pm,
+               const float* __restrict__ scale, float* __restrict__ F, float* __restrict__ Fs,
+               const int32_t* __restrict__ inv_perm, float dt, unsigned long long* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& s = smem_as<Smem>(smem_raw);
+    load_weights(s, Pm, scale);
+    cta_setup(s, kLearnedCols);
+    uint32_t phase = 0;
+    unsigned fallbacks = 0, clamped = 0;
+    const long long ntiles = (n + TILE - 1) / TILE;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long p = t * TILE + threadIdx.x;
+        float f[FEAT_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float Fst[3] = {0.f, 0.f, 0.f};
+        V4<float> x = {0, 0, 0, 0}, v = {0, 0, 0, 0};
+        float epsc = 1.f, phic = 0.f;
+        if (p < n) {
+            const float4 xa = reinterpret_cast<const float4*>(pos)[p];
+            const float4 va = reinterpret_cast<const float4*>(vel)[p];
+            x = {xa.x, xa.y, xa.z, xa.w};
+            v = {va.x, va.y, va.z, va.w};
+            const Probe<float> st = probe(bulk_stale, var_stale, x.x, x.y, x.z, g);
+            float sv[3], smag;
+            closure_features(st, x, v, g, P, f, epsc, phic, sv, smag);
+            clamped += (1.f - st.phi) < P.eps_min;
+            const float b = drag_beta(g.law, epsc, phic, x.w, smag, P);
+            Fst[0] = b * sv[0];
+            Fst[1] = b * sv[1];
+            Fst[2] = b * sv[2];
+        }
+        float xin[K0];
+        const bool ok = scale_row(s, f, xin);
+        st_row8(s.X, threadIdx.x, 0, K0, xin);
+        st_row8(s.X, threadIdx.x, 8, K0, xin + 8);
+        float c = 1.f;
+        if (!tile_forward(s, phase, status, c)) break;
+        if (p < n) {
+            float Fo[3];
+            if (ok) {
+                Fo[0] = c * Fst[0];
+                Fo[1] = c * Fst[1];
+                Fo[2] = c * Fst[2];
+            } else {
+                ++fallbacks;
+                const V4<float> uf = fresh_velocity(u_fine, x.x, x.y, x.z, g);
+                const float sf[3] = {uf.y - v.x, uf.z - v.y, uf.w - v.z};
+                const float sm = sqrtf(sf[0] * sf[0] + sf[1] * sf[1] + sf[2] * sf[2]);
+                const float b = drag_beta(g.law, epsc, phic, x.w, sm, P);
+                Fo[0] = b * sf[0];
+                Fo[1] = b * sf[1];
+                Fo[2] = b * sf[2];
+            }
+            F[p] = Fo[0];
+            F[n + p] = Fo[1];
+            F[2 * n + p] = Fo[2];
+            if (Fs) st4(Fs, __ldg(inv_perm + p), Fo[0], Fo[1], Fo[2], 0.f);
+            if (dt > 0.f) {
+                const float m = P.rho_p * M<float>::pi6() * x.w * x.w * x.w;
+                float xn[3] = {x.x, x.y, x.z};
+                float un[3] = {v.x + dt * (Fo[0] / m + P.g[0]), v.y + dt * (Fo[1] / m + P.g[1]),
+                               v.z + dt * (Fo[2] / m + P.g[2])};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float xa = xn[a] + dt * un[a];
+                    const float lo = (float)g.x0[a], hi = (float)g.xhi[a];
+                    if (xa < lo) { xa = 2.f * lo - xa; un[a] = -un[a]; }
+                    else if (xa > hi) { xa = 2.f * hi - xa; un[a] = -un[a]; }
+                    xn[a] = xa;
+                }
+                st4(pos, p, xn[0], xn[1], xn[2], x.w);
+                st4(vel, p, un[0], un[1], un[2], v.w);
+            }
+        }
+    }
+    if (fallbacks) atomicAdd(&status[ST_FALLBACK], (unsigned long long)fallbacks);
+    if (clamped) {
+        atomicAdd(&status[ST_CLAMPED], (unsigned long long)clamped);
+        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
+    }
+    cta_teardown(s, kLearnedCols);
+}
+
 }  // namespace mlp
 }  // namespace cg
 
@@ -506,6 +703,9 @@ namespace {
 using namespace cg::mlp;
 
 size_t smem_forward() { return sizeof(Smem) + 1024; }
+// at least 72 KB per CTA: at most three learned-drag CTAs share an SM, so
+// their 128 TMEM columns each always fit in the SM's 512
+size_t smem_learned() { return std::max<size_t>(sizeof(Smem) + 1024, 72 * 1024); }
 size_t smem_train() { return sizeof(SmemTrain) + 1024; }
 bool g_mlp_attr = false;
 
@@ -516,6 +716,7 @@ cg_status mlp_attrs() {
     const int fwd = (int)std::max<size_t>(smem_forward(), 80 * 1024);
     CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
     CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
+    CG_CUDA(cudaFuncSetAttribute(k_drag_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_learned()));
     g_mlp_attr = true;
     return CG_OK;
 }
@@ -530,7 +731,74 @@ void host_scale(const float* lo, const float* hi, float out[16]) {
 
 }  // namespace
 
+namespace cg {
+
+cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine) {
+    if (!m->var_bulk || !m->u_fine) return CG_ERR_INVALID_ARG;
+    *var_stale = m->var_bulk;
+    *u_fine = m->u_fine;
+    return CG_OK;
+}
+
+cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
+                              const void* var_stale, const void* u_fine, void* force, void* S_bulk, double dt) {
+    if (g->fp64 || !var_stale || !u_fine) return CG_ERR_INVALID_ARG;
+    if (n > 0 && ((uintptr_t)u_fine & 15u)) return CG_ERR_INVALID_ARG;
+    CG_TRY(mlp_attrs());
+    g->part_blocks[PS_DRAG] = -1;   // the drag diagnostics are not formed on this path
+    void* Fs = S_bulk ? g->Fs : nullptr;
+    if (n > 0) {
+        const long long ntiles = (n + TILE - 1) / TILE;
+        const unsigned grid = (unsigned)std::min(ntiles, (long long)3 * g->num_sms);
+        CG_LAUNCH(g, "drag_learned", k_drag_learned, grid, TILE, smem_learned(), (float*)pos_d, (float*)vel, n,
+                  g->gd, cg::phys_of<float>(g->gd), (const float*)g->bulk4, (const float*)var_stale,
+                  (const float*)u_fine, m->P, m->scale, (float*)force, (float*)Fs, g->inv_perm, (float)dt,
+                  g->status);
+    }
+    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, true));
+    return CG_OK;
+}
+
+}  // namespace cg
+
 extern "C" {
+
+cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void* vel, const double* eps_bulk,
+                          const void* u_stale, const void* var_stale, const void* u_fresh, float* feat_out,
+                          float* target_out) {
+    if (!g) return CG_ERR_INVALID_ARG;
+    if (n < 0 || n > INT32_MAX) return CG_ERR_INVALID_ARG;
+    if (!eps_bulk || !u_stale || !var_stale || !u_fresh) return CG_ERR_INVALID_ARG;
+    if (n > 0 && (!pos_d || !vel || !feat_out || !target_out)) return CG_ERR_INVALID_ARG;
+    if (n > 0 && (((uintptr_t)pos_d | (uintptr_t)vel | (uintptr_t)feat_out) & 15u)) return CG_ERR_INVALID_ARG;
+    // pack (phi, u_fresh) into the fresh record, then (phi, u_stale) into the drag's record
+    void* const keep = g->bulk4;
+    CG_TRY(grow_buf(g->fresh4, 4 * g->tsize * (size_t)g->gd.nbulk));
+    g->bulk4 = g->fresh4.p;
+    const cg_status s1 = cg::launch_pack(g, eps_bulk, u_fresh, false);
+    g->bulk4 = keep;
+    CG_TRY(s1);
+    CG_TRY(cg::launch_pack(g, eps_bulk, u_stale, false));
+    if (n == 0) return CG_OK;
+    const unsigned grid = (unsigned)std::min((n + 255) / 256, (int64_t)g->num_sms * 8);
+    if (g->fp64)
+        CG_LAUNCH(g, "mlp_features", k_mlp_features<double>, grid, 256, 0, (const double*)pos_d, (const double*)vel,
+                  (long long)n, g->gd, cg::phys_of<double>(g->gd), (const double*)g->bulk4, (const double*)var_stale,
+                  (const double*)g->fresh4.p, feat_out, target_out);
+    else
+        CG_LAUNCH(g, "mlp_features", k_mlp_features<float>, grid, 256, 0, (const float*)pos_d, (const float*)vel,
+                  (long long)n, g->gd, cg::phys_of<float>(g->gd), (const float*)g->bulk4, (const float*)var_stale,
+                  (const float*)g->fresh4.p, feat_out, target_out);
+    return CG_OK;
+}
+
+cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine) {
+    if (!m) return CG_ERR_INVALID_ARG;
+    if ((var_stale == nullptr) != (u_fine == nullptr) || ((uintptr_t)u_fine & 15u)) return CG_ERR_INVALID_ARG;
+    m->var_bulk = var_stale;
+    m->u_fine = u_fine;
+    return CG_OK;
+}
 
 cg_status cg_mlp_create(const float* params, const float* feat_lo, const float* feat_hi, void* cuda_stream,
                         cg_mlp** out) {

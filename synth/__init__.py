@@ -209,6 +209,23 @@ def small_clustered_bed(seed: int = 0, fp64: bool = False) -> Workload:
     return clustered_bed(seed, fine_n=(128, 128, 64), ratio=4, n=500_000, fp64=fp64)
 
 
+def evolved_field(w: Workload, seed: int = 0, amp: float = 0.05) -> np.ndarray:
+    """A later fine velocity field for the stale / fresh closure cases:
+    the workload's field plus a smooth large-scale swirl of amplitude
+    ``amp`` and white noise of amplitude ``amp / 4`` per fine cell."""
+    rng = rng_for(seed, 9)
+    d = w.desc
+    cx, cy, cz = fine_centres(d["origin"], d["extent"], d["fine_n"])
+    Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
+    kx, ky, kz = (2 * np.pi / d["extent"][a] for a in range(3))
+    u = w.u_fine.astype(np.float64, copy=True)
+    u[0] += amp * np.sin(ky * Y) * np.cos(kz * Z)
+    u[1] += amp * np.sin(kz * Z) * np.cos(kx * X)
+    u[2] += amp * np.sin(kx * X) * np.cos(ky * Y)
+    u += (amp / 4) * rng.normal(size=u.shape)
+    return u.astype(w.dtype)
+
+
 WORKLOADS = {
     "tiny": tiny,
     "packed_bed": packed_bed,

@@ -65,7 +65,7 @@ def test_tiny_fp64_step(cuda_lib):
     w = synth.tiny(seed=0)
     ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
     got = run_step(cuda_lib, w)
-    assert got["rc"] == 0 and got["counts"] == [0, 0, 0, 0]
+    assert got["rc"] == 0 and got["counts"] == [0, 0, 0, 0, 0]
     compare_step(w, got, ref, TOL_FP64)
     compare_sums(got, ref, 1e-12)
 
