@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", default="packed_bed", choices=["packed_bed", "small_packed_bed"])
+    ap.add_argument("--workload", default="packed_bed",
+                    choices=["packed_bed", "small_packed_bed", "clustered_bed", "small_clustered_bed"])
+    ap.add_argument("--learned", action="store_true",
+                    help="train the drag closure on the workload family, then compare learned and plain steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
@@ -394,10 +397,146 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_learned(args):
+    """Learned closure against the plain path on one workload family:
+    train on seeds 0 and 1 (stale records refreshed every 2, 5, 10 steps,
+    fluid relaxed by the coupling source), judge the drag error on seed 2
+    at several refresh intervals K, then time the plain step and the
+    learned stale step (CUDA graphs) and report the amortised throughput of
+    one refresh plus K - 1 learned steps at the largest K whose learned
+    drag error is <= 1%."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1807_11834_gb300 as cg
+    from paper_1807_11834_gb300 import closure
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    make = getattr(synth, args.workload)
+    dt = 1e-4                      # the clustered bed's step; the packed bed is advanced with the same
+    t0 = time.time()
+    F, T = closure.generate_pairs(make, seeds=(0, 1), refreshes=(2, 5, 10), steps=12,
+                                  n_pairs=2_000_000, dt=dt)
+    t_gen = time.time() - t0
+    m, hist = closure.train(F, T, epochs=20, batch=65536, lr=2e-3)
+    t_train = time.time() - t0 - t_gen
+    n_pairs = int(F.shape[0])
+    del F, T
+    Ks = (5, 10, 20, 50)
+    w = make(seed=2)
+    evals = {K: closure.evaluate(m, lambda seed: w, seed=2, refresh=K, steps=K + 2, dt=dt) for K in Ks}
+    ok = [K for K in Ks if evals[K]["err_learned"] <= 0.01]
+    K_star = max(ok) if ok else None
+
+    g = cg.Grids(w.desc)
+    n = w.n
+    pos = torch.from_numpy(w.pos_d).cuda()
+    vel = torch.from_numpy(w.vel).cuda()
+    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).cuda()
+    out = g.alloc_outputs(n, var=True, eps_fine=True)
+    g.cg_step(pos, vel, uf, out)            # the refresh that makes the stale record
+    torch.cuda.synchronize()
+
+    def graph_of(fn):
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        g.set_stream(cs)
+        with torch.cuda.stream(cs):
+            fn()
+        cs.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=cs):
+            fn()
+        g.set_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        return gr
+
+    plain = graph_of(lambda: g.cg_step(pos, vel, uf, out))
+    age = 3
+    learned = graph_of(lambda: g.cg_step_learned(pos, vel, uf, out, m, age))
+
+    def time_graph(gr, steps):
+        for _ in range(max(3, args.warmup)):
+            gr.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            gr.replay()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(20, min(args.steps, 500))
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ta = time.time()
+    ms_plain = time_graph(plain, steps)
+    ms_learned = time_graph(learned, steps)
+    tb = time.time()
+    time.sleep(0.2)
+    sampler.stop()
+    rc, flags, counts = g.cg_sync_status()
+    if rc != 0:
+        raise RuntimeError(f"timed status {rc}")
+
+    # per-kernel times of the learned step (serialised events)
+    g.cg_profile_reset()
+    g.cg_profile_enable(True)
+    for _ in range(20):
+        g.cg_step_learned(pos, vel, uf, out, m, age)
+    prof = g.cg_profile_read()
+    g.cg_profile_enable(False)
+    kern = {k: {"ms_per_launch": round(v[1] / v[0], 5)} for k, v in prof.items() if v[0]}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    roof = None
+    if "drag_learned" in kern:
+        # network: 2 (16 x 64 + 64 x 64) flops per row on the tensor cores
+        flops = 2.0 * (16 * 64 + 64 * 64) * n
+        ach = flops / (kern["drag_learned"]["ms_per_launch"] * 1e-3) / 1e12
+        pk = float(peaks.get("bf16_tflops", 1900.0))
+        roof = {"kernel": "drag_learned", "bound": "tensor", "achieved": round(ach, 2), "peak": pk,
+                "unit": "TFLOP/s", "frac": round(ach / pk, 5),
+                "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"}
+    amort = None
+    if K_star:
+        ms_amort = (ms_plain + (K_star - 1) * ms_learned) / K_star
+        amort = n / (ms_amort * 1e-3)
+    line = {"metric": "learned coupled particle-steps/s at <=1% relative drag error",
+            "value": amort, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+            "higher_is_better": True, "dtype": "f32 (closure bf16 x bf16 -> f32)", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
+                       "dt": dt, "training_pairs": n_pairs, "train_seeds": [0, 1], "eval_seed": 2,
+                       "generate_s": round(t_gen, 1), "train_s": round(t_train, 1)},
+            "refresh_K": K_star,
+            "plain": {"ms_per_step": round(ms_plain, 5), "value": n / (ms_plain * 1e-3)},
+            "learned_step": {"ms_per_step": round(ms_learned, 5), "value": n / (ms_learned * 1e-3),
+                             "age": age},
+            "drag_error": {str(K): evals[K] for K in Ks},
+            "loss_standardised": [round(h, 5) for h in (hist[0], hist[-1])],
+            "kernels_learned_step": kern, "roofline_closure": roof,
+            "clocks": sampler.summary(ta, tb)}
+    print(json.dumps(line))
+    m.close()
+    g.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.learned:
+        run_learned(args)
     else:
         run_gb300(args)
 

@@ -196,9 +196,9 @@ cg_status cg_average_fine_to_bulk(cg_grids* g, const void* u_fine, void* u_bulk,
  * reaction S = -(1/V_B) sum F is deposited in the same pass (needs the
  * binning of this n).  mlp NULL: the plain correlation.  mlp set (FP32
  * grids only; cg_mlp_bind first): u_bulk is the stale fluid record and the
- * learned closure of cg_drag_learned below is applied (its fallback reads
- * the bound fine field); the closure's parameters must be ready on this
- * handle's stream (same stream, or synchronised). */
+ * learned closure of cg_step_learned below is applied with the bound age
+ * (its fallback reads the bound fine field); the closure's parameters must
+ * be ready on this handle's stream (same stream, or synchronised). */
 cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel,
                   const double* eps_bulk, const void* u_bulk,
                   void* force_out, void* S_bulk_out, const cg_mlp* mlp);
@@ -222,18 +222,19 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
 cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
                   const cg_step_out* out, double dt);
 
-/* Learned coupling step (closure below; not in the paper).  refresh != 0:
- * exactly cg_step, which also writes the fresh u_bulk and var_bulk that
- * later steps use as their stale record.  refresh == 0: the fine -> bulk
- * average is skipped; out->u_bulk and out->var_bulk are then INPUTS (the
- * record of the last refresh, left unchanged) and the drag is the learned
- * closure F = c F_stale, falling back per particle to the plain drag with
- * the fluid velocity averaged afresh from u_fine when its features lie
- * outside the closure's box (counted: cg_sync_status counts[4]).  The drag
- * diagnostics of sums (0, 2..4, 11..15) are NaN on such steps.  FP32 grids
- * only; out->var_bulk required. */
+/* Learned coupling step (closure below; not in the paper).  age == 0: a
+ * refresh, exactly cg_step, which also writes the fresh u_bulk and var_bulk
+ * that later steps use as their stale record.  age >= 1 (steps since that
+ * refresh): the fine -> bulk average is skipped; out->u_bulk and
+ * out->var_bulk are then INPUTS (the record of the last refresh, left
+ * unchanged) and the drag is the learned closure F = (1 + age r) F_stale,
+ * falling back per particle to the plain drag with the fluid velocity
+ * averaged afresh from u_fine when its features lie outside the closure's
+ * box (counted: cg_sync_status counts[4]).  The drag diagnostics of sums
+ * (0, 2..4, 11..15) are NaN on such steps.  FP32 grids only;
+ * out->var_bulk required. */
 cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine,
-                          const cg_step_out* out, double dt, const cg_mlp* mlp, int32_t refresh);
+                          const cg_step_out* out, double dt, const cg_mlp* mlp, int32_t age);
 
 /* cg_step on HOST buffers: copies the inputs to handle-owned device
  * buffers, runs cg_step, copies every requested output back and waits for
@@ -254,7 +255,9 @@ cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine,
  * w3 [64], b3 [1].  Feature rows are 8 floats: eps, log10(1 + Re), |s|,
  * d eps/dx, d eps/dy, d eps/dz, sigma^2, unused; the network sees
  * (f - lo) / (hi - lo) per feature, and a row is in range when every
- * scaled feature lies in [0, 1].
+ * scaled feature lies in [0, 1].  The network output r is the drag
+ * correction per step of record age: the learned drag is
+ * F = (1 + age r) F_stale, age = steps since the record was refreshed.
  * ------------------------------------------------------------------------ */
 #define CG_MLP_NPARAM 5313
 #define CG_MLP_NFEAT 7
@@ -295,10 +298,11 @@ cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void*
                           const void* u_stale, const void* var_stale, const void* u_fresh,
                           float* features_out, float* target_out);
 
-/* Bind the stale variance field (var [n_b] float) and the fine velocity
- * (u_fine [3][n_f] float, 16-byte aligned) read by cg_drag with this
- * closure; both NULL unbinds.  The pointers are kept, not copied. */
-cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine);
+/* Bind the stale variance field (var [n_b] float), the fine velocity
+ * (u_fine [3][n_f] float, 16-byte aligned) and the record age (>= 1) used
+ * by cg_drag with this closure; both pointers NULL unbinds.  The pointers
+ * are kept, not copied. */
+cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int32_t age);
 
 /* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
  * kernels expired (flags: CG_FLAG_*). */

@@ -97,7 +97,7 @@ _SIGS = {
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "cg_step_learned": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double,
                                   C.c_void_p, C.c_int32]),
 }
@@ -281,9 +281,10 @@ class Grids:
         so = self._out_struct(out)
         _check(lib().cg_step(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step")
 
-    def cg_step_learned(self, pos_d, vel, u_fine, out, mlp, refresh, dt=0.0):
-        """cg_step with the learned closure; without refresh out["u_bulk"] and
-        out["var_bulk"] are the stale record (inputs)."""
+    def cg_step_learned(self, pos_d, vel, u_fine, out, mlp, age, dt=0.0):
+        """cg_step with the learned closure: age 0 refreshes (cg_step);
+        age >= 1 uses out["u_bulk"] and out["var_bulk"] as the stale record
+        (inputs) of that age."""
         n = pos_d.shape[0]
         self._t(pos_d, 4 * n, name="pos_d")
         self._t(vel, 4 * n, name="vel")
@@ -291,7 +292,7 @@ class Grids:
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step_learned(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt), mlp.h,
-                                     1 if refresh else 0), "cg_step_learned")
+                                     int(age)), "cg_step_learned")
 
     def cg_mlp_features(self, pos_d, vel, eps_bulk, u_stale, var_stale, u_fresh, features, target):
         """Closure features [n][8] float32 and targets [n] float32 at every particle."""
@@ -415,11 +416,12 @@ class Mlp:
         rc = lib().cg_mlp_sync_status(self.h, C.byref(flags))
         return rc, flags.value
 
-    def bind(self, var_stale, u_fine):
-        """Stale variance field and fine velocity read by Grids.cg_drag(mlp=self)
-        (float32 device tensors, kept alive by this object)."""
+    def bind(self, var_stale, u_fine, age=1):
+        """Stale variance field, fine velocity and record age used by
+        Grids.cg_drag(mlp=self) (float32 device tensors, kept alive by this
+        object)."""
         self._bound = (var_stale, u_fine)
-        _check(lib().cg_mlp_bind(self.h, _ptr(var_stale), _ptr(u_fine)), "cg_mlp_bind")
+        _check(lib().cg_mlp_bind(self.h, _ptr(var_stale), _ptr(u_fine), int(age)), "cg_mlp_bind")
 
 
 def mlp_pack(p: dict):

@@ -409,15 +409,16 @@ cg_status cg_drag(cg_grids* g, int64_t n, const void* pos_d, const void* vel, co
     if (S_bulk_out && g->n_binned != n) return CG_ERR_NOT_BINNED;
     const void* var_stale = nullptr;
     const void* u_fine = nullptr;
+    int32_t age = 1;
     if (mlp) {
         if (g->fp64) return CG_ERR_INVALID_ARG;
-        CG_TRY(mlp_bound_inputs(mlp, &var_stale, &u_fine));
+        CG_TRY(mlp_bound_inputs(mlp, &var_stale, &u_fine, &age));
     }
     CG_TRY(ensure_particle_capacity(g, n));
     CG_TRY(launch_pack(g, eps_bulk, u_bulk, false));
     if (mlp)
         return launch_drag_learned(g, mlp, n, const_cast<void*>(pos_d), const_cast<void*>(vel), var_stale, u_fine,
-                                   force_out, S_bulk_out, 0.0);
+                                   age, force_out, S_bulk_out, 0.0);
     return launch_drag(g, n, pos_d, vel, force_out, S_bulk_out, false, 0.0);
 }
 
@@ -458,7 +459,7 @@ static cg_status on_aux(cg_grids* g, Fn f) {
 // var_bulk are inputs (the record of the last refresh) and the drag is the
 // learned kernel, which reads the fine field only for its fallback rows.
 static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* o,
-                           double dt, const cg_mlp* mlp = nullptr) {
+                           double dt, const cg_mlp* mlp = nullptr, int32_t age = 0) {
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
     for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
@@ -481,7 +482,8 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     }
     CG_CUDA(cudaEventRecord(g->ev_epsf, side));
     if (mlp)
-        CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, o->force, o->S_bulk, dt));
+        CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, age, o->force, o->S_bulk,
+                                   dt));
     else
         CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
@@ -515,11 +517,11 @@ cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine, const 
 }
 
 cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out, double dt,
-                          const cg_mlp* mlp, int32_t refresh) {
+                          const cg_mlp* mlp, int32_t age) {
     CG_TRY(check_handle(g));
     CG_TRY(check_step_args(p, u_fine, out, dt, true));
-    if (!mlp || g->fp64 || !out->var_bulk) return CG_ERR_INVALID_ARG;
-    return step_impl(g, p, u_fine, out, dt, refresh ? nullptr : mlp);
+    if (!mlp || g->fp64 || !out->var_bulk || age < 0) return CG_ERR_INVALID_ARG;
+    return step_impl(g, p, u_fine, out, dt, age == 0 ? nullptr : mlp, age);
 }
 
 cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,

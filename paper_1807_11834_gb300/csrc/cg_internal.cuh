@@ -192,10 +192,11 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
                       bool sums, double dt);
 // Learned drag (FP32 only): bulk4 must hold (phi of this step, stale u).
 cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
-                              const void* var_stale, const void* u_fine, void* force, void* S_bulk, double dt);
+                              const void* var_stale, const void* u_fine, int32_t age, void* force, void* S_bulk,
+                              double dt);
 cg_status grow_buf(DevBuf& b, size_t bytes);
-// The stale variance field and fine velocity bound to a closure by cg_mlp_bind.
-cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine);
+// The stale variance field, fine velocity and record age bound to a closure by cg_mlp_bind.
+cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine, int32_t* age);
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);
 cg_status launch_sums(cg_grids* g, double* sums);
 // First element (in units of T) of the partial region r.

@@ -41,7 +41,8 @@ constexpr int OFF_B3 = OFF_W3 + H;
 constexpr int NPARAM = OFF_B3 + 1;     // 5313
 constexpr int TILE = 128;              // rows per CTA tile
 constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr uint32_t kLearnedCols = 128;  // TMEM columns of the learned drag (Z1 and Z2)
+constexpr uint32_t kInferCols = 64;     // TMEM columns of a forward-only CTA (Z1, then Z2 in the same columns)
+constexpr uint32_t kTrainCols = 256;    // Z1 (0..63), Z2 (64..127), dA1 (128..191)
 
 // ---------------------------------------------------------------------------
 // tcgen05 / TMEM / mbarrier primitives (inline PTX)
@@ -136,21 +137,35 @@ __device__ __forceinline__ void st_row8(unsigned char* tile, int row, int k0, in
     *reinterpret_cast<uint4*>(tile + koff(row, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU x Phi(x) of the forward pass, with the complementary error function
+// from formula 7.1.26 of Abramowitz & Stegun (Handbook of Mathematical
+// Functions): erfc(z) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2),
+// t = 1 / (1 + p z), z >= 0, absolute error below 1.5e-7.  With
+// q = erfc(|x| / sqrt 2) / 2: GELU(x) = x (1 - q) for x >= 0, x q otherwise.
+__device__ __forceinline__ float gelu(float x) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    float p = fmaf(t, 1.061405429f, -1.453152027f);
+    p = fmaf(t, p, 1.421413741f);
+    p = fmaf(t, p, -0.284496736f);
+    p = fmaf(t, p, 0.254829592f);
+    const float q = 0.5f * t * p * __expf(-z * z);
+    return x >= 0.f ? x - x * q : x * q;
+}
+// Its derivative Phi(x) + x phi(x) (training only), from CUDA's erff / expf.
 __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout of a CTA
+// Shared-memory layout of a CTA: the forward part, and the extra operands of
+// the training kernel
 // ---------------------------------------------------------------------------
 struct Smem {
     alignas(128) unsigned char W1t[H * K0 * 2];    // B of GEMM 1: (n = hidden, k = input)
     alignas(128) unsigned char W2t[H * H * 2];     // B of GEMM 2: (n = out, k = in)
-    alignas(128) unsigned char W2b[H * H * 2];     // B of the dA1 product: (n = in, k = out)
     alignas(128) unsigned char X[TILE * K0 * 2];   // A of GEMM 1
     alignas(128) unsigned char A1[TILE * H * 2];   // A of GEMM 2 (BF16 GELU(Z1))
-    alignas(128) unsigned char dZ2b[TILE * H * 2]; // A of the dA1 product (BF16 dZ2)
     float b1[H], b2[H], w3[H];
     float lo[FEAT_STRIDE], inv[FEAT_STRIDE];
     float b3;
@@ -160,6 +175,8 @@ struct Smem {
 };
 struct SmemTrain {
     Smem s;
+    alignas(128) unsigned char W2b[H * H * 2];     // B of the dA1 product: (n = in, k = out)
+    alignas(128) unsigned char dZ2b[TILE * H * 2]; // A of the dA1 product (BF16 dZ2)
     float dZ2[TILE][H + 1];   // FP32 dZ2 (padded against bank conflicts)
     float dZ1[TILE][H + 1];   // FP32 dZ1
     float A2dc[TILE][H + 1];  // A2 * dc, for the w3 gradient
@@ -175,9 +192,7 @@ __device__ void load_weights(Smem& s, const float* __restrict__ P, const float* 
     }
     for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
         const int i = e / H, o = e % H;     // W2[i][o]
-        const uint16_t b = bf16_bits(P[OFF_W2 + i * H + o]);
-        *reinterpret_cast<uint16_t*>(s.W2t + koff(o, i, H)) = b;   // (n = out, k = in)
-        *reinterpret_cast<uint16_t*>(s.W2b + koff(i, o, H)) = b;   // (n = in, k = out)
+        *reinterpret_cast<uint16_t*>(s.W2t + koff(o, i, H)) = bf16_bits(P[OFF_W2 + i * H + o]);   // (n = out, k = in)
     }
     for (int j = threadIdx.x; j < H; j += blockDim.x) {
         s.b1[j] = P[OFF_B1 + j];
@@ -189,6 +204,14 @@ __device__ void load_weights(Smem& s, const float* __restrict__ P, const float* 
         s.inv[threadIdx.x] = scale[FEAT_STRIDE + threadIdx.x];
     }
     if (threadIdx.x == 0) s.b3 = P[OFF_B3];
+}
+
+// W2 as the B operand of dA1 = dZ2 W2^T (training).
+__device__ void load_w2b(SmemTrain& st, const float* __restrict__ P) {
+    for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+        const int i = e / H, o = e % H;     // W2[i][o]
+        *reinterpret_cast<uint16_t*>(st.W2b + koff(i, o, H)) = bf16_bits(P[OFF_W2 + i * H + o]);   // (n = in, k = out)
+    }
 }
 
 // Scaled network input of one row from raw features; returns in-range.
@@ -238,33 +261,25 @@ __device__ __forceinline__ S& smem_as(unsigned char* raw) {
     return *reinterpret_cast<S*>(a);
 }
 
-// Issue the GEMM(s) of one stage from thread 0 and wait for completion.
-// Returns false (and marks the CTA failed) if the bounded wait expires.
-__device__ bool run_stage(Smem& s, int stage, uint32_t& phase, unsigned long long* status) {
+// D[128 x 64] (TMEM columns dcol..dcol+63) = A[128 x 16 nk] B^T with A and
+// B K-major core-matrix tiles of K = 16 nk: issued from thread 0 after the
+// CTA's operand stores, then a bounded wait for completion.  Returns false
+// (and marks the CTA failed) if the wait expires; the whole CTA agrees.
+__device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const unsigned char* B, int nk,
+                         uint32_t& phase, unsigned long long* status) {
     fence_async_smem();   // make this thread's shared-memory stores visible to the tensor core
     fence_before();
     __syncthreads();
     fence_after();
     if (threadIdx.x == 0) {
-        const uint32_t tm = s.tmem;
-        if (stage == 0) {   // Z1 (cols 0..63) = X[128x16] W1
-            umma(tm, sdesc(saddr(s.X), 128, 256), sdesc(saddr(s.W1t), 128, 256), idesc_bf16(TILE, H), 0);
-        } else if (stage == 1) {   // Z2 (cols 64..127) = A1[128x64] W2
-#pragma unroll
-            for (int kk = 0; kk < H / 16; ++kk)
-                umma(tm + 64, sdesc(saddr(s.A1) + kk * 256, 128, 1024), sdesc(saddr(s.W2t) + kk * 256, 128, 1024),
-                     idesc_bf16(TILE, H), kk > 0);
-        } else {   // dA1 (cols 128..191) = dZ2[128x64] W2^T
-#pragma unroll
-            for (int kk = 0; kk < H / 16; ++kk)
-                umma(tm + 128, sdesc(saddr(s.dZ2b) + kk * 256, 128, 1024),
-                     sdesc(saddr(s.W2b) + kk * 256, 128, 1024), idesc_bf16(TILE, H), kk > 0);
-        }
+        const uint32_t sbo = (uint32_t)nk * 256;   // (K / 8) core matrices of 128 bytes per 8-row group
+        for (int kk = 0; kk < nk; ++kk)
+            umma(s.tmem + dcol, sdesc(saddr(A) + kk * 256, 128, sbo), sdesc(saddr(B) + kk * 256, 128, sbo),
+                 idesc_bf16(TILE, H), kk > 0);
         umma_commit(&s.bar);
     }
     const bool mine = mbar_wait(&s.bar, phase);
     phase ^= 1u;
-    // the whole CTA agrees on the outcome, so no thread leaves a loop alone
     const bool failed = __syncthreads_or(!mine) != 0;
     if (failed && threadIdx.x == 0) {
         s.fail = 1;
@@ -280,10 +295,11 @@ __device__ __forceinline__ uint32_t lane_addr(const Smem& s, int col) {
     return s.tmem + ((uint32_t)((threadIdx.x & ~31) & 127) << 16) + (uint32_t)col;
 }
 
-// Forward of the tile: rows' X already in s.X.  Leaves Z1 / Z2 (without
-// bias) in TMEM and returns this thread's output c.
-__device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c) {
-    if (!run_stage(s, 0, phase, status)) return false;
+// Forward of the tile: rows' X already in s.X.  Z1 goes to TMEM columns
+// 0..63 and Z2 (without bias) to z2col..z2col+63 (0 reuses Z1's columns,
+// which are read out before GEMM 2 is issued); returns this thread's c.
+__device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c, uint32_t z2col) {
+    if (!run_gemm(s, 0, s.X, s.W1t, K0 / 16, phase, status)) return false;
     const int row = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < H / 16; ++q) {
@@ -295,12 +311,12 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
         st_row8(s.A1, row, 16 * q, H, a);
         st_row8(s.A1, row, 16 * q + 8, H, a + 8);
     }
-    if (!run_stage(s, 1, phase, status)) return false;
+    if (!run_gemm(s, z2col, s.A1, s.W2t, H / 16, phase, status)) return false;
     float acc = s.b3;
 #pragma unroll
     for (int q = 0; q < H / 16; ++q) {
         float z[16];
-        tmem_ld16(lane_addr(s, 64 + 16 * q), z);
+        tmem_ld16(lane_addr(s, z2col + 16 * q), z);
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc = fmaf(gelu(z[i] + s.b2[16 * q + i]), s.w3[16 * q + i], acc);
     }
@@ -313,14 +329,14 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
 // ---------------------------------------------------------------------------
 // c for every feature row (rows outside the training box still get c; the
 // in-range flag tells the caller).
-__global__ void __launch_bounds__(TILE, 1)
+__global__ void __launch_bounds__(TILE, 4)
 k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
               long long n, float* __restrict__ c_out, int32_t* __restrict__ in_range,
               unsigned long long* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& s = smem_as<Smem>(smem_raw);
     load_weights(s, P, scale);
-    cta_setup(s, 256);
+    cta_setup(s, kInferCols);
     uint32_t phase = 0;
     const long long ntiles = (n + TILE - 1) / TILE;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -336,13 +352,13 @@ k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, cons
         st_row8(s.X, threadIdx.x, 0, K0, x);
         st_row8(s.X, threadIdx.x, 8, K0, x + 8);
         float c = 0.f;
-        if (!tile_forward(s, phase, status, c)) break;
+        if (!tile_forward(s, phase, status, c, 0)) break;
         if (r < n) {
             c_out[r] = c;
             if (in_range) in_range[r] = ok ? 1 : 0;
         }
     }
-    cta_teardown(s, 256);
+    cta_teardown(s, kInferCols);
 }
 
 // Loss and gradient partials of a batch: each CTA accumulates its tiles'
@@ -356,7 +372,8 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
     SmemTrain& st = smem_as<SmemTrain>(smem_raw);
     Smem& s = st.s;
     load_weights(s, P, scale);
-    cta_setup(s, 256);
+    load_w2b(st, P);
+    cta_setup(s, kTrainCols);
     uint32_t phase = 0;
     const int tid = threadIdx.x;
     const float inv_n = 1.0f / (float)n;
@@ -384,7 +401,7 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
         st_row8(s.X, tid, 0, K0, x);
         st_row8(s.X, tid, 8, K0, x + 8);
         float c = 0.f;
-        if (!tile_forward(s, phase, status, c)) break;
+        if (!tile_forward(s, phase, status, c, 64)) break;
         const float res = (r < n) ? (c - tg) : 0.f;
         const float dc = 2.0f * res * inv_n;
         st.dc[tid] = dc;
@@ -402,11 +419,11 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
                 st.dZ2[tid][j] = d[i];
                 st.A2dc[tid][j] = gelu(zz) * dc;
             }
-            st_row8(s.dZ2b, tid, 16 * q, H, d);
-            st_row8(s.dZ2b, tid, 16 * q + 8, H, d + 8);
+            st_row8(st.dZ2b, tid, 16 * q, H, d);
+            st_row8(st.dZ2b, tid, 16 * q + 8, H, d + 8);
         }
         // dA1 = dZ2 W2^T on the tensor cores
-        if (!run_stage(s, 2, phase, status)) break;
+        if (!run_gemm(s, 128, st.dZ2b, st.W2b, H / 16, phase, status)) break;
 #pragma unroll
         for (int q = 0; q < H / 16; ++q) {
             float da[16], z1[16];
@@ -453,7 +470,7 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
         out[OFF_B3] = gb3;
         out[NPARAM] = loss;
     }
-    cta_teardown(s, 256);
+    cta_teardown(s, kTrainCols);
 }
 
 // Sum the CTA partials (fixed order), optionally apply one Adam step.
@@ -588,20 +605,21 @@ __device__ V4<float> fresh_velocity(const float* __restrict__ u_fine, float x, f
 // Learned drag: per tile of 128 particles (caller order) each thread forms
 // its particle's closure inputs and the drag F_stale from the stale bulk
 // record (porosity of this step, fluid velocity and variance of the last
-// refresh); the tile goes through the network on the tensor cores; in
-// range F = c F_stale, otherwise F is the plain drag with the fluid
+// refresh, `age` steps ago); the tile goes through the network on the
+// tensor cores, whose output r is the correction per step; in range
+// F = (1 + age r) F_stale, otherwise F is the plain drag with the fluid
 // velocity averaged afresh from the fine grid.  The force is also written
 // to its sorted slot for the fused reaction deposit when Fs is given, and
 // with dt > 0 the particle is advanced as the plain drag kernel does.
-__global__ void __launch_bounds__(TILE, 1)
+__global__ void __launch_bounds__(TILE, 4)
 k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, const float* __restrict__ bulk_stale,
                const float* __restrict__ var_stale, const float* __restrict__ u_fine, const float* __restrict__ Pm,
                const float* __restrict__ scale, float* __restrict__ F, float* __restrict__ Fs,
-               const int32_t* __restrict__ inv_perm, float dt, unsigned long long* __restrict__ status) {
+               const int32_t* __restrict__ inv_perm, float dt, float age, unsigned long long* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& s = smem_as<Smem>(smem_raw);
     load_weights(s, Pm, scale);
-    cta_setup(s, kLearnedCols);
+    cta_setup(s, kInferCols);
     uint32_t phase = 0;
     unsigned fallbacks = 0, clamped = 0;
     const long long ntiles = (n + TILE - 1) / TILE;
@@ -629,14 +647,15 @@ k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, co
         const bool ok = scale_row(s, f, xin);
         st_row8(s.X, threadIdx.x, 0, K0, xin);
         st_row8(s.X, threadIdx.x, 8, K0, xin + 8);
-        float c = 1.f;
-        if (!tile_forward(s, phase, status, c)) break;
+        float c = 0.f;
+        if (!tile_forward(s, phase, status, c, 0)) break;
         if (p < n) {
             float Fo[3];
             if (ok) {
-                Fo[0] = c * Fst[0];
-                Fo[1] = c * Fst[1];
-                Fo[2] = c * Fst[2];
+                const float cc = fmaf(age, c, 1.0f);   // correction after `age` steps
+                Fo[0] = cc * Fst[0];
+                Fo[1] = cc * Fst[1];
+                Fo[2] = cc * Fst[2];
             } else {
                 ++fallbacks;
                 const V4<float> uf = fresh_velocity(u_fine, x.x, x.y, x.z, g);
@@ -674,7 +693,7 @@ k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, co
         atomicAdd(&status[ST_CLAMPED], (unsigned long long)clamped);
         atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
     }
-    cta_teardown(s, kLearnedCols);
+    cta_teardown(s, kInferCols);
 }
 
 }  // namespace mlp
@@ -697,24 +716,24 @@ struct cg_mlp {
     int t = 0;
     const void* var_bulk = nullptr;   // bound inputs of the fused learned drag
     const void* u_fine = nullptr;
+    int32_t age = 1;
 };
 
 namespace {
 using namespace cg::mlp;
 
-size_t smem_forward() { return sizeof(Smem) + 1024; }
-// at least 72 KB per CTA: at most three learned-drag CTAs share an SM, so
-// their 128 TMEM columns each always fit in the SM's 512
-size_t smem_learned() { return std::max<size_t>(sizeof(Smem) + 1024, 72 * 1024); }
+// Forward-only CTAs hold 64 TMEM columns each and at least 28 KB of shared
+// memory, so at most eight share an SM and their columns always fit in the
+// SM's 512 (a training CTA, 256 columns and over 150 KB, leaves room for at
+// most two of them beside it).
+size_t smem_forward() { return std::max<size_t>(sizeof(Smem) + 1024, 28 * 1024); }
+size_t smem_learned() { return smem_forward(); }
 size_t smem_train() { return sizeof(SmemTrain) + 1024; }
 bool g_mlp_attr = false;
 
 cg_status mlp_attrs() {
     if (g_mlp_attr) return CG_OK;
-    // at least ~76 KB of shared memory per CTA, so at most two CTAs share an
-    // SM and their 256 TMEM columns each always fit in the SM's 512
-    const int fwd = (int)std::max<size_t>(smem_forward(), 80 * 1024);
-    CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd));
+    CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forward()));
     CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
     CG_CUDA(cudaFuncSetAttribute(k_drag_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_learned()));
     g_mlp_attr = true;
@@ -733,27 +752,29 @@ void host_scale(const float* lo, const float* hi, float out[16]) {
 
 namespace cg {
 
-cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine) {
+cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine, int32_t* age) {
     if (!m->var_bulk || !m->u_fine) return CG_ERR_INVALID_ARG;
     *var_stale = m->var_bulk;
     *u_fine = m->u_fine;
+    *age = m->age;
     return CG_OK;
 }
 
 cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
-                              const void* var_stale, const void* u_fine, void* force, void* S_bulk, double dt) {
-    if (g->fp64 || !var_stale || !u_fine) return CG_ERR_INVALID_ARG;
+                              const void* var_stale, const void* u_fine, int32_t age, void* force, void* S_bulk,
+                              double dt) {
+    if (g->fp64 || !var_stale || !u_fine || age < 1) return CG_ERR_INVALID_ARG;
     if (n > 0 && ((uintptr_t)u_fine & 15u)) return CG_ERR_INVALID_ARG;
     CG_TRY(mlp_attrs());
     g->part_blocks[PS_DRAG] = -1;   // the drag diagnostics are not formed on this path
     void* Fs = S_bulk ? g->Fs : nullptr;
     if (n > 0) {
         const long long ntiles = (n + TILE - 1) / TILE;
-        const unsigned grid = (unsigned)std::min(ntiles, (long long)3 * g->num_sms);
+        const unsigned grid = (unsigned)std::min(ntiles, (long long)4 * g->num_sms);
         CG_LAUNCH(g, "drag_learned", k_drag_learned, grid, TILE, smem_learned(), (float*)pos_d, (float*)vel, n,
                   g->gd, cg::phys_of<float>(g->gd), (const float*)g->bulk4, (const float*)var_stale,
                   (const float*)u_fine, m->P, m->scale, (float*)force, (float*)Fs, g->inv_perm, (float)dt,
-                  g->status);
+                  (float)age, g->status);
     }
     if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, true));
     return CG_OK;
@@ -792,11 +813,13 @@ cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void*
     return CG_OK;
 }
 
-cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine) {
+cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int32_t age) {
     if (!m) return CG_ERR_INVALID_ARG;
     if ((var_stale == nullptr) != (u_fine == nullptr) || ((uintptr_t)u_fine & 15u)) return CG_ERR_INVALID_ARG;
+    if (var_stale && age < 1) return CG_ERR_INVALID_ARG;
     m->var_bulk = var_stale;
     m->u_fine = u_fine;
+    m->age = var_stale ? age : 1;
     return CG_OK;
 }
 
@@ -870,9 +893,8 @@ cg_status cg_mlp_forward(cg_mlp* m, int64_t n, const float* features, float* c_o
     if (n == 0) return CG_OK;
     CG_TRY(mlp_attrs());
     const long long ntiles = (n + TILE - 1) / TILE;
-    const unsigned grid = (unsigned)std::min(ntiles, (long long)2 * m->num_sms);
-    const size_t sm = std::max<size_t>(smem_forward(), 80 * 1024);
-    k_mlp_forward<<<grid, TILE, sm, m->stream>>>(m->P, m->scale, features, n, c_out, in_range_out, m->status);
+    const unsigned grid = (unsigned)std::min(ntiles, (long long)4 * m->num_sms);
+    k_mlp_forward<<<grid, TILE, smem_forward(), m->stream>>>(m->P, m->scale, features, n, c_out, in_range_out, m->status);
     CG_CUDA(cudaGetLastError());
     return CG_OK;
 }
