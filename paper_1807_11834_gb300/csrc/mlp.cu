@@ -301,7 +301,10 @@ __device__ __forceinline__ uint32_t lane_addr(const Smem& s, int col) {
 __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c, uint32_t z2col) {
     if (!run_gemm(s, 0, s.X, s.W1t, K0 / 16, phase, status)) return false;
     const int row = threadIdx.x;
-#pragma unroll
+    // the column loops stay rolled: 16 activations per pass give enough
+    // independent work, and the unrolled body would not fit the
+    // instruction cache beside the rest of the fused drag kernel
+#pragma unroll 1
     for (int q = 0; q < H / 16; ++q) {
         float z[16];
         tmem_ld16(lane_addr(s, 16 * q), z);
@@ -313,7 +316,7 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
     }
     if (!run_gemm(s, z2col, s.A1, s.W2t, H / 16, phase, status)) return false;
     float acc = s.b3;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < H / 16; ++q) {
         float z[16];
         tmem_ld16(lane_addr(s, z2col + 16 * q), z);
