@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", default="packed_bed",
                     choices=["packed_bed", "small_packed_bed", "clustered_bed", "small_clustered_bed"])
+    ap.add_argument("--batch", action="store_true",
+                    help="64 uneven instances: batched persistent launches vs one by one")
     ap.add_argument("--learned", action="store_true",
                     help="train the drag closure on the workload family, then compare learned and plain steps")
     ap.add_argument("--no-e2e", action="store_true")
@@ -531,10 +533,92 @@ def run_learned(args):
     g.close()
 
 
+def run_batch(args):
+    """64 independent uneven instances (fine edge 32..128, ratio 2/4/8, 10^4
+    to 2 10^6 particles each, Taylor-Green fluid, Di Felice, FP32): one by
+    one (eager, and as one CUDA graph of the 64 cg_step calls) against the
+    batched step (default decomposition, then autotuned, eager and as a
+    replayed graph).  Value: batched, tuned, graph particle-steps/s."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1807_11834_gb300 as cg
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    ws = synth.uneven_batch(seed=0, count=64)
+    n_tot = sum(w.n for w in ws)
+    inst = []
+    for w in ws:
+        g = cg.Grids(w.desc)
+        out = g.alloc_outputs(w.n, var=True, eps_fine=True)
+        g.close()
+        inst.append((w.desc, torch.from_numpy(w.pos_d).cuda(), torch.from_numpy(w.vel).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).cuda(), out))
+    b = cg.Batch(inst)
+    steps = max(10, min(args.steps, 200))
+
+    def timed(fn, k):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    l0 = sum(b.instance_launch_count(i) for i in range(len(ws)))
+    b.step_each()
+    launches_each = sum(b.instance_launch_count(i) for i in range(len(ws))) - l0
+    res = {}
+    res["one_by_one_eager"] = timed(lambda: b.step_each(), max(3, steps // 4))
+    b.use_graph(True)
+    res["one_by_one_graph"] = timed(lambda: b.step_each(), max(3, steps // 4))
+    b.use_graph(False)
+    res["batched_default_eager"] = timed(lambda: b.step(), steps)
+    cfg, tune_ms = b.tune(reps=5)
+    res["batched_tuned_eager"] = timed(lambda: b.step(), steps)
+    b.use_graph(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ta = time.time()
+    res["batched_tuned_graph"] = timed(lambda: b.step(), steps)
+    tb = time.time()
+    time.sleep(0.2)
+    sampler.stop()
+    rc, flags, counts = b.sync_status()
+    if rc != 0:
+        raise RuntimeError(f"batched status {rc} {counts}")
+    ms = res["batched_tuned_graph"]
+    fine = sum(w.u_fine[0].size for w in ws)
+    line = {"metric": "batched coupled particle-steps/s (64 uneven instances)", "value": n_tot / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 uneven instances, seed 0", "particles": n_tot, "fine_cells": fine,
+                       "tuned": cfg, "tune_median_ms": tune_ms,
+                       "launches_per_batched_step": b.launches_per_step(),
+                       "launches_one_by_one_per_step": launches_each},
+            "ms_per_step_variants": {k: round(v, 4) for k, v in res.items()},
+            "speedup_vs_one_by_one_eager": res["one_by_one_eager"] / ms,
+            "speedup_vs_one_by_one_graph": res["one_by_one_graph"] / ms,
+            "clocks": sampler.summary(ta, tb)}
+    print(json.dumps(line))
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch:
+        run_batch(args)
     elif args.learned:
         run_learned(args)
     else:

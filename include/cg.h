@@ -308,6 +308,70 @@ cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int3
  * kernels expired (flags: CG_FLAG_*). */
 cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags);
 
+/* ------------------------------------------------------------------------
+ * Batched coupling (not in the paper): many independent FP32 instances of
+ * uneven grids and particle counts stepped together.  Each phase of the
+ * step (zeroing, binning passes, porosity, fine -> bulk average, pack, drag,
+ * reaction, projections, sums) is one persistent launch over every
+ * instance, so a batched step is about 16 launches whatever the number of
+ * instances; cg_batch_use_graph replays them as one CUDA graph.  Every
+ * field of an instance is bit-identical to cg_step of that instance (and
+ * across configurations); the FP64 sums may differ in their last bits.
+ * ------------------------------------------------------------------------ */
+typedef struct cg_batch cg_batch;
+
+/* One instance: grids (prec CG_FP32, ratio 2, 4 or 8), device particles
+ * (n >= 1, 16-byte aligned), device u_fine [3][n_f], device outputs as for
+ * cg_step (var_bulk, eps_fine, sums nullable; cell, perm, cell_start must
+ * be NULL).  The pointers are kept for the life of the batch. */
+typedef struct {
+    cg_grid_desc desc;
+    cg_particles particles;
+    const void* u_fine;
+    cg_step_out out;
+} cg_batch_item;
+
+/* Work decomposition (results do not depend on it). */
+typedef struct {
+    int32_t digit_bits;  /* widest radix digit of a binning pass, 8..11      */
+    int32_t drag_items;  /* particles per thread of a drag block, 1..64      */
+    int32_t avg_items;   /* bulk cells per thread of an average block, 1..64 */
+    int32_t seg_chunks;  /* 256-slot chunks per warp of the deposits, 1..64  */
+    int32_t grid_mult;   /* persistent CTAs = grid_mult x resident per SM x SMs, 1..8 */
+} cg_batch_config;
+
+cg_status cg_batch_default_config(cg_batch_config* c);
+/* Creates one grids handle per instance (its scratch) plus the batch's own
+ * stream and buffers; cuda_stream is the caller's stream, joined before
+ * and after every step.  CG_ERR_INVALID_ARG for a bad item. */
+cg_status cg_batch_create(const cg_batch_item* items, int32_t count, void* cuda_stream, cg_batch** out);
+cg_status cg_batch_destroy(cg_batch* b);
+/* Re-plan under a configuration (waits for the batch stream; CG_ERR_OUT_OF_RANGE
+ * when digit_bits cannot bin an instance in two passes). */
+cg_status cg_batch_set_config(cg_batch* b, const cg_batch_config* c);
+cg_status cg_batch_get_config(const cg_batch* b, cg_batch_config* c);
+/* on != 0: cg_batch_step captures its launches once per dt and replays the graph. */
+cg_status cg_batch_use_graph(cg_batch* b, int32_t on);
+/* One coupling step of every instance (dt as for cg_step, same for all). */
+cg_status cg_batch_step(cg_batch* b, double dt);
+/* The same step as cg_step of each instance in turn (each on its own
+ * handle with its own launch shapes): the one-by-one reference; replayed
+ * as one graph when graphs are on. */
+cg_status cg_batch_step_each(cg_batch* b, double dt);
+/* Autotune the configuration: coordinate search over the knobs, each
+ * candidate timed as the median of reps batched steps with dt = 0.
+ * cache_path (nullable) maps the batch's signature to its choice and is
+ * read before / appended after a search.  chosen, best_ms nullable
+ * (best_ms = -1 on a cache hit). */
+cg_status cg_batch_tune(cg_batch* b, int32_t reps, const char* cache_path, cg_batch_config* chosen,
+                        double* best_ms);
+/* Status over all instances, as cg_sync_status (counts summed). */
+cg_status cg_batch_sync_status(cg_batch* b, uint32_t* flags, int64_t* counts);
+/* The grids handle of instance i (for stepping it alone), NULL if out of range. */
+cg_grids* cg_batch_instance(cg_batch* b, int32_t i);
+int64_t cg_batch_launch_count(const cg_batch* b);
+int64_t cg_batch_launches_per_step(const cg_batch* b);
+
 /* Wait for the handle's stream and read-and-clear the device status word.
  * flags (nullable) gets CG_FLAG_* bits; counts (nullable, CG_NCOUNTS
  * entries) gets particles outside, non-finite positions, clamped

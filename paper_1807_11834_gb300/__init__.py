@@ -62,6 +62,18 @@ class StepOut(C.Structure):
                 ("perm", C.c_void_p), ("cell_start", C.c_void_p)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("desc", GridDesc), ("particles", Particles), ("u_fine", C.c_void_p), ("out", StepOut)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("digit_bits", C.c_int32), ("drag_items", C.c_int32), ("avg_items", C.c_int32),
+                ("seg_chunks", C.c_int32), ("grid_mult", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +112,20 @@ _SIGS = {
     "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "cg_step_learned": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double,
                                   C.c_void_p, C.c_int32]),
+    "cg_batch_default_config": (C.c_int, [C.POINTER(BatchConfig)]),
+    "cg_batch_create": (C.c_int, [C.POINTER(BatchItem), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cg_batch_destroy": (C.c_int, [C.c_void_p]),
+    "cg_batch_set_config": (C.c_int, [C.c_void_p, C.POINTER(BatchConfig)]),
+    "cg_batch_get_config": (C.c_int, [C.c_void_p, C.POINTER(BatchConfig)]),
+    "cg_batch_use_graph": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cg_batch_step": (C.c_int, [C.c_void_p, C.c_double]),
+    "cg_batch_step_each": (C.c_int, [C.c_void_p, C.c_double]),
+    "cg_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p, C.POINTER(BatchConfig),
+                                C.POINTER(C.c_double)]),
+    "cg_batch_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int64)]),
+    "cg_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int32]),
+    "cg_batch_launch_count": (C.c_int64, [C.c_void_p]),
+    "cg_batch_launches_per_step": (C.c_int64, [C.c_void_p]),
 }
 
 MLP_NPARAM = 5313
@@ -422,6 +448,94 @@ class Mlp:
         object)."""
         self._bound = (var_stale, u_fine)
         _check(lib().cg_mlp_bind(self.h, _ptr(var_stale), _ptr(u_fine), int(age)), "cg_mlp_bind")
+
+
+class Batch:
+    """Owner of a ``cg_batch``: many FP32 coupling instances stepped by one
+    persistent launch per phase.  ``instances`` is a list of
+    (desc dict, pos_d, vel, u_fine, out dict) with contiguous CUDA float32
+    tensors (out as from Grids.alloc_outputs, bins=False); the tensors are
+    kept alive by this object."""
+
+    def __init__(self, instances, stream=None):
+        items = (BatchItem * len(instances))()
+        self._keep = []
+        for k, (desc, pos, vel, uf, out) in enumerate(instances):
+            it = items[k]
+            it.desc = make_desc(desc)
+            it.particles = Particles(pos.shape[0], pos.data_ptr(), vel.data_ptr())
+            it.u_fine = uf.data_ptr()
+            it.out = Grids._out_struct(out)
+            self._keep.append((pos, vel, uf, out))
+        self._items = items
+        h = C.c_void_p()
+        _check(lib().cg_batch_create(items, len(instances), _stream_handle(stream), C.byref(h)), "cg_batch_create")
+        self.h = h
+        self.count = len(instances)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, dt=0.0):
+        _check(lib().cg_batch_step(self.h, float(dt)), "cg_batch_step")
+
+    def step_each(self, dt=0.0):
+        """cg_step of every instance in turn (the one-by-one reference)."""
+        _check(lib().cg_batch_step_each(self.h, float(dt)), "cg_batch_step_each")
+
+    def step_one(self, i, dt=0.0):
+        """cg_step of instance i alone, on its own grids handle (same buffers)."""
+        it = self._items[i]
+        g = lib().cg_batch_instance(self.h, i)
+        if not g:
+            raise IndexError(i)
+        _check(lib().cg_step(C.c_void_p(g), C.byref(it.particles), it.u_fine, C.byref(it.out), float(dt)),
+               "cg_step")
+
+    def use_graph(self, on=True):
+        _check(lib().cg_batch_use_graph(self.h, 1 if on else 0), "cg_batch_use_graph")
+
+    def config(self):
+        c = BatchConfig()
+        _check(lib().cg_batch_get_config(self.h, C.byref(c)), "cg_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, **kw):
+        c = BatchConfig()
+        _check(lib().cg_batch_get_config(self.h, C.byref(c)), "cg_batch_get_config")
+        for k, v in kw.items():
+            setattr(c, k, int(v))
+        _check(lib().cg_batch_set_config(self.h, C.byref(c)), "cg_batch_set_config")
+
+    def tune(self, reps=5, cache_path=None):
+        c = BatchConfig()
+        ms = C.c_double()
+        _check(lib().cg_batch_tune(self.h, int(reps), None if cache_path is None else str(cache_path).encode(),
+                                   C.byref(c), C.byref(ms)), "cg_batch_tune")
+        return c.as_dict(), ms.value
+
+    def sync_status(self):
+        flags = C.c_uint32()
+        counts = (C.c_int64 * CG_NCOUNTS)()
+        rc = lib().cg_batch_sync_status(self.h, C.byref(flags), counts)
+        return rc, flags.value, list(counts)
+
+    def launch_count(self):
+        return int(lib().cg_batch_launch_count(self.h))
+
+    def launches_per_step(self):
+        return int(lib().cg_batch_launches_per_step(self.h))
+
+    def instance_launch_count(self, i):
+        return int(lib().cg_launch_count(C.c_void_p(lib().cg_batch_instance(self.h, i))))
 
 
 def mlp_pack(p: dict):

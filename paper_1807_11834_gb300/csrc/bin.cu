@@ -17,6 +17,7 @@
 // pass stable and fully deterministic (no atomics decide any position).
 // Per-cell counts use integer atomics (order-independent), then a scan.
 #include "cg_internal.cuh"
+#include "batch.cuh"
 
 namespace cg {
 
@@ -40,18 +41,17 @@ template <> __device__ __forceinline__ float pi6_b<float>() { return 0.523598775
 template <> __device__ __forceinline__ double pi6_b<double>() { return 0.52359877559829887308; }
 
 template <typename T>
-__global__ void __launch_bounds__(kSortThreads)
-k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
-          int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
-          T* __restrict__ vol, unsigned long long* __restrict__ status) {
-    extern __shared__ int sh[];
+__device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long long n, const GridDev& g,
+                                             int32_t* __restrict__ key, int32_t* __restrict__ count,
+                                             int32_t* __restrict__ hist, int ntiles, int bits0, T* __restrict__ vol,
+                                             unsigned long long* __restrict__ status, int* sh, Blk blk) {
     __shared__ int s_cnt[2];
     const int R = 1 << bits0;
     for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     int n_out = 0, n_nf = 0;
-    const long long base = (long long)blockIdx.x * kSortTile;
+    const long long base = blk.id * kSortTile;
     V4<T> pv[kSortItems];
     // all position loads of the thread first, so they are in flight together
 #pragma unroll
@@ -84,19 +84,26 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
     if (n_out) atomicAdd(&s_cnt[0], n_out);
     if (n_nf) atomicAdd(&s_cnt[1], n_nf);
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blockIdx.x] = sh[i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
     if (threadIdx.x == 0) add_status(status, s_cnt[0], s_cnt[1]);
 }
 
-// Tile histogram of a digit of already-computed keys (second pass).
+template <typename T>
 __global__ void __launch_bounds__(kSortThreads)
-k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift, int bits,
-           int32_t* __restrict__ hist) {
+k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
+          int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
+          T* __restrict__ vol, unsigned long long* __restrict__ status) {
     extern __shared__ int sh[];
+    bin_key_body(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk());
+}
+
+// Tile histogram of a digit of already-computed keys (second pass).
+__device__ __forceinline__ void bin_hist_body(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
+                                              int bits, int32_t* __restrict__ hist, int* sh, Blk blk) {
     const int R = 1 << bits;
     for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * kSortTile;
+    const long long base = blk.id * kSortTile;
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
@@ -104,26 +111,34 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
         if (valid) atomicAdd(&sh[(__ldg(keys + p) >> shift) & (R - 1)], 1);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blockIdx.x] = sh[i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift, int bits,
+           int32_t* __restrict__ hist) {
+    extern __shared__ int sh[];
+    bin_hist_body(keys, n, ntiles, shift, bits, hist, sh, launch_blk());
 }
 
 // Stable scatter of one digit pass.  offs = exclusive scan of the tile
 // histograms, digit-major ([digit][tile]).
 template <bool FIRST, bool FINAL, typename T>
-__global__ void __launch_bounds__(kSortThreads, 2)
-k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
-              int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
-              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
-              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
-              T* __restrict__ vol_sorted) {
-    extern __shared__ int cnt[];  // [kSortWarps][R]
+__device__ __forceinline__ void bin_scatter_body(const int32_t* __restrict__ keys_in,
+                                                 const int32_t* __restrict__ vals_in, long long n, int ntiles,
+                                                 int shift, int bits, const int32_t* __restrict__ offs,
+                                                 int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
+                                                 int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
+                                                 int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+                                                 T* __restrict__ vol_sorted, int* cnt /* [kSortWarps][R] */,
+                                                 Blk blk) {
     const int R = 1 << bits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     int* wc = cnt + warp * R;
     const unsigned lt = lanemask_lt();
-    const long long base = (long long)blockIdx.x * kSortTile + (long long)warp * (kSortTile / kSortWarps);
+    const long long base = blk.id * kSortTile + (long long)warp * (kSortTile / kSortWarps);
     int kv[kSortItems], vv[kSortItems], rk[kSortItems];
     T vol_k[kSortItems];
     // all loads of the slice first, so they are in flight together
@@ -154,7 +169,7 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
     }
     __syncthreads();
     for (int d = threadIdx.x; d < R; d += blockDim.x) {
-        int run = __ldg(offs + (long long)d * ntiles + blockIdx.x);
+        int run = __ldg(offs + (long long)d * ntiles + blk.id);
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
             int t = cnt[w * R + d];
@@ -180,6 +195,18 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
             }
         }
     }
+}
+
+template <bool FIRST, bool FINAL, typename T>
+__global__ void __launch_bounds__(kSortThreads, 2)
+k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
+              int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
+              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
+              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+              T* __restrict__ vol_sorted) {
+    extern __shared__ int cnt[];
+    bin_scatter_body<FIRST, FINAL, T>(keys_in, vals_in, n, ntiles, shift, bits, offs, keys_out, vals_out, perm,
+                                      key_sorted, inv_perm, vol, vol_sorted, cnt, launch_blk());
 }
 
 // ----------------------------------------------------------------------
@@ -226,17 +253,8 @@ __device__ __forceinline__ void load16(const int32_t* __restrict__ in, long long
     }
 }
 
-// Up to two independent arrays are scanned by one pair of launches: blocks
-// [0, nA) cover array A, blocks [nA, nA + nB) array B.
-struct ScanJob {
-    const int32_t* in[2];
-    int32_t* out[2];
-    long long m[2];
-    long long nblk[2];
-};
-
-__device__ __forceinline__ void scan_locate(const ScanJob& j, int& which, long long& blk) {
-    blk = blockIdx.x;
+__device__ __forceinline__ void scan_locate(const ScanJob& j, long long id, int& which, long long& blk) {
+    blk = id;
     which = 0;
     if (blk >= j.nblk[0]) {
         blk -= j.nblk[0];
@@ -244,11 +262,13 @@ __device__ __forceinline__ void scan_locate(const ScanJob& j, int& which, long l
     }
 }
 
-__global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restrict__ part) {
+// Blocks of a job: [0, nblk[0]) over array A, then nblk[1] over array B;
+// part holds one total per block of the job.
+__device__ __forceinline__ void scan_reduce_body(const ScanJob& j, int32_t* __restrict__ part, Blk b) {
     __shared__ int shw[32];
     int which;
     long long blk;
-    scan_locate(j, which, blk);
+    scan_locate(j, b.id, which, blk);
     long long start = blk * kScanItems + threadIdx.x * 16;
     int v[16];
     load16(j.in[which], start, j.m[which], v);
@@ -257,17 +277,21 @@ __global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restr
     for (int k = 0; k < 16; ++k) s += v[k];
     int total;
     block_exclusive_scan(s, shw, total);
-    if (threadIdx.x == 0) part[blockIdx.x] = total;
+    if (threadIdx.x == 0) part[b.id] = total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restrict__ part) {
+    scan_reduce_body(j, part, launch_blk());
 }
 
 // Each block sums the partials of the blocks before it in its array (a few
 // thousand at most), then scans its own chunk: no third launch.
-__global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __restrict__ part) {
+__device__ __forceinline__ void scan_down_body(const ScanJob& j, const int32_t* __restrict__ part, Blk b) {
     __shared__ int shw[32];
     __shared__ int s_base;
     int which;
     long long blk;
-    scan_locate(j, which, blk);
+    scan_locate(j, b.id, which, blk);
     const long long first = which ? j.nblk[0] : 0;
     int acc = 0;
     for (long long i = threadIdx.x; i < blk; i += blockDim.x) acc += part[first + i];
@@ -291,6 +315,10 @@ __global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __r
         if (start + k < m) out[start + k] = ex;
         ex += v[k];
     }
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __restrict__ part) {
+    scan_down_body(j, part, launch_blk());
 }
 
 // Exclusive scans of one or two arrays (out may alias in).
@@ -357,6 +385,97 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
                   (const T*)g->vol, (T*)g->vol_sorted);
     }
     return CG_OK;
+}
+
+// ----------------------------------------------------------------------
+// Batched binning phases (FP32 instances)
+// ----------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) kb_bin_key(BLaunch L) {
+    extern __shared__ int sh[];
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        bin_key_body<float>(I.pos, I.n, I.gd, I.key, I.count, I.hist, I.ntiles, I.b0, I.vol, I.status, sh, b);
+    });
+}
+
+__global__ void __launch_bounds__(kSortThreads) kb_bin_hist1(BLaunch L) {
+    extern __shared__ int sh[];
+    batch_loop(L, [&](const BInst& I, Blk b) { bin_hist_body(I.key1, I.n, I.ntiles, I.b0, I.b1, I.hist, sh, b); });
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) kb_bin_scatter(BLaunch L, int pass) {
+    extern __shared__ int cnt[];
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        if (pass == 1)
+            bin_scatter_body<false, true, float>(I.key1, I.val1, I.n, I.ntiles, I.b0, I.b1, I.hist, nullptr, nullptr,
+                                                 I.perm, I.key_sorted, I.inv_perm, I.vol, I.vol_sorted, cnt, b);
+        else if (I.npasses == 1)
+            bin_scatter_body<true, true, float>(I.key, nullptr, I.n, I.ntiles, 0, I.b0, I.hist, nullptr, nullptr,
+                                                I.perm, I.key_sorted, I.inv_perm, I.vol, I.vol_sorted, cnt, b);
+        else
+            bin_scatter_body<true, false, float>(I.key, nullptr, I.n, I.ntiles, 0, I.b0, I.hist, I.key1, I.val1,
+                                                 nullptr, nullptr, nullptr, (const float*)nullptr, (float*)nullptr,
+                                                 cnt, b);
+    });
+}
+
+__global__ void __launch_bounds__(256) kb_scan_reduce(BLaunch L, int pass) {
+    batch_loop(L, [&](const BInst& I, Blk b) { scan_reduce_body(pass ? I.scan1 : I.scan0, I.scan_part, b); });
+}
+
+__global__ void __launch_bounds__(256) kb_scan_down(BLaunch L, int pass) {
+    batch_loop(L, [&](const BInst& I, Blk b) { scan_down_body(pass ? I.scan1 : I.scan0, I.scan_part, b); });
+}
+
+static bool g_batch_attr = false;
+
+static cg_status batch_bin_attrs() {
+    if (g_batch_attr) return CG_OK;
+    const int mx = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);
+    CG_CUDA(cudaFuncSetAttribute(kb_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    CG_CUDA(cudaFuncSetAttribute(kb_bin_key, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (1 << kMaxDigitBits) * (int)sizeof(int)));
+    CG_CUDA(cudaFuncSetAttribute(kb_bin_hist1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (1 << kMaxDigitBits) * (int)sizeof(int)));
+    g_batch_attr = true;
+    return CG_OK;
+}
+
+cg_status launch_batch_bin(int phase, const BLaunch& L, unsigned grid, size_t smem, cudaStream_t s) {
+    CG_TRY(batch_bin_attrs());
+    if (L.total == 0 || grid == 0) return CG_OK;
+    switch (phase) {
+        case BP_KEY: kb_bin_key<<<grid, kSortThreads, smem, s>>>(L); break;
+        case BP_SCAN0_R: kb_scan_reduce<<<grid, 256, 0, s>>>(L, 0); break;
+        case BP_SCAN0_D: kb_scan_down<<<grid, 256, 0, s>>>(L, 0); break;
+        case BP_SCAT0: kb_bin_scatter<<<grid, kSortThreads, smem, s>>>(L, 0); break;
+        case BP_HIST1: kb_bin_hist1<<<grid, kSortThreads, smem, s>>>(L); break;
+        case BP_SCAN1_R: kb_scan_reduce<<<grid, 256, 0, s>>>(L, 1); break;
+        case BP_SCAN1_D: kb_scan_down<<<grid, 256, 0, s>>>(L, 1); break;
+        case BP_SCAT1: kb_bin_scatter<<<grid, kSortThreads, smem, s>>>(L, 1); break;
+        default: return CG_ERR_INVALID_ARG;
+    }
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+int batch_bin_occupancy(int phase, size_t smem) {
+    if (batch_bin_attrs() != CG_OK) return 1;
+    int occ = 0;
+    cudaError_t e = cudaSuccess;
+    switch (phase) {
+        case BP_KEY: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_bin_key, kSortThreads, smem); break;
+        case BP_HIST1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_bin_hist1, kSortThreads, smem); break;
+        case BP_SCAT0:
+        case BP_SCAT1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_bin_scatter, kSortThreads, smem); break;
+        case BP_SCAN0_R:
+        case BP_SCAN1_R: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_scan_reduce, 256, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_scan_down, 256, 0); break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return occ > 0 ? occ : 1;
 }
 
 cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {

@@ -179,6 +179,22 @@ void prof_end(cg_grids* g, int slot, int ev);
 // ----------------------------------------------------------------------
 // Step launchers (one .cu each)
 // ----------------------------------------------------------------------
+// Up to two independent arrays are scanned by one pair of launches: blocks
+// [0, nA) cover array A, blocks [nA, nA + nB) array B.
+struct ScanJob {
+    const int32_t* in[2];
+    int32_t* out[2];
+    long long m[2];
+    long long nblk[2];
+};
+
+// Column map of the conservation-sum reduction: sum k merges cnt[k]
+// compensated pairs starting at pair off[k] of the partials.
+struct SumsMap {
+    long long off[CG_NSUMS];     // first pair of the partial column, -1 = not computed
+    long long cnt[CG_NSUMS];     // number of partials
+};
+
 cg_status ensure_particle_capacity(cg_grids* g, long long n);
 cg_status ensure_partials(cg_grids* g, long long n);
 
@@ -199,6 +215,8 @@ cg_status grow_buf(DevBuf& b, size_t bytes);
 cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine, int32_t* age);
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);
 cg_status launch_sums(cg_grids* g, double* sums);
+// Sum columns of the partial regions (offsets in pairs; blocks < 0: region not formed).
+SumsMap sums_map(const long long* part_off, const long long* part_blocks);
 // First element (in units of T) of the partial region r.
 inline void* part_ptr(cg_grids* g, int r) { return (char*)g->partials + 2 * g->tsize * g->part_off[r]; }
 
@@ -273,12 +291,21 @@ __device__ __forceinline__ CSum<T> warp_reduce(CSum<T> v) {
     return v;
 }
 
+// Block coordinates of a kernel body: the launch's own (blockIdx.x,
+// gridDim.x) for one instance, or a virtual block of one instance inside a
+// batched launch over many instances.
+struct Blk {
+    long long id;   // block index within the instance's work
+    long long n;    // number of blocks of the instance's work
+};
+__device__ __forceinline__ Blk launch_blk() { return {(long long)blockIdx.x, (long long)gridDim.x}; }
+
 // Block-level deterministic reduction of K compensated sums.  Thread 0..K-1
-// writes the pair (s, c) of sum k to part[2 * (k * stride + blockIdx.x)]:
+// writes the pair (s, c) of sum k to part[2 * (k * stride + bid)]:
 // partials stay in the path precision as compensated pairs, so no FP64
 // arithmetic runs per block (GB300's FP64 rate is a small fraction of FP32).
 template <typename T, int K>
-__device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part, long long stride) {
+__device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part, long long stride, long long bid) {
     __shared__ T sh_s[K][32];
     __shared__ T sh_c[K][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -302,7 +329,7 @@ __device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part
             o.c = sh_c[k][w];
             a.merge(o);
         }
-        T* dst = part + 2 * ((long long)k * stride + blockIdx.x);
+        T* dst = part + 2 * ((long long)k * stride + bid);
         dst[0] = a.s;
         dst[1] = a.c;
     }

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "cg_internal.cuh"
+#include "batch.cuh"
 
 namespace cg {
 
@@ -30,9 +31,13 @@ template <> __device__ __forceinline__ double pi_over_6<double>() { return 0.523
 // set to 1 beforehand by k_fill.
 // ----------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ void fill_body(T* __restrict__ a, long long m, T v, Blk b) {
+    for (long long i = b.id * blockDim.x + threadIdx.x; i < m; i += b.n * blockDim.x) a[i] = v;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_fill(T* __restrict__ a, long long m, T v) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
-        a[i] = v;
+    fill_body(a, m, v, launch_blk());
 }
 
 template <typename T>
@@ -76,18 +81,19 @@ k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restri
             carry_key = __shfl_sync(0xffffffffu, key, 31);
         }
     }
-    if (do_sums) block_sums<T, 1>(tot, part, pstride);
+    if (do_sums) block_sums<T, 1>(tot, part, pstride, blockIdx.x);
 }
 
 // Porosity from the volumes already in sorted order (written by the final
 // binning pass): rounds of 32 slots, no gather.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __restrict__ key_sorted,
-                        const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
-                        long long pstride, int do_sums) {
-    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+__device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__ vs, long long n,
+                                                           const int32_t* __restrict__ key_sorted,
+                                                           const int32_t* __restrict__ cs, const GridDev& g,
+                                                           double* __restrict__ eps, T* __restrict__ part,
+                                                           long long pstride, int do_sums, Blk b) {
+    const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = b.n * (blockDim.x >> 5);
     CSum<T> tot[1];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
@@ -99,18 +105,27 @@ k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __
                 tot[0].merge(a[0]);
             });
     }
-    if (do_sums) block_sums<T, 1>(tot, part, pstride);
+    if (do_sums) block_sums<T, 1>(tot, part, pstride, b.id);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __restrict__ key_sorted,
+                        const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
+                        long long pstride, int do_sums) {
+    deposit_volume_sorted_body(vs, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk());
 }
 
 // Reaction from the forces the drag wrote in sorted order (T4 per slot);
 // S_B V_B accumulated as an exact float-float product for the diagnostics.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
-                       const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
-                       long long pstride, int do_sums) {
-    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+__device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ Fs, long long n,
+                                                          const int32_t* __restrict__ key_sorted,
+                                                          const int32_t* __restrict__ cs, const GridDev& g,
+                                                          T* __restrict__ S, T* __restrict__ part, long long pstride,
+                                                          int do_sums, Blk b) {
+    const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = b.n * (blockDim.x >> 5);
     CSum<T> sv[3];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
@@ -142,7 +157,15 @@ k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __r
                 }
             });
     }
-    if (do_sums) block_sums<T, 3>(sv, part, pstride);
+    if (do_sums) block_sums<T, 3>(sv, part, pstride, b.id);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
+                       const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
+                       long long pstride, int do_sums) {
+    deposit_sorted_force_body(Fs, n, key_sorted, cs, g, S, part, pstride, do_sums, launch_blk());
 }
 
 // ----------------------------------------------------------------------
@@ -206,30 +229,33 @@ k_deposit_momentum(const T* __restrict__ F, long long n, const int32_t* __restri
 // cell in the path precision, phi = 1 - eps formed in double.
 // ----------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ void pack_body(const double* __restrict__ eps, const T* __restrict__ u, const GridDev& g,
+                                          T* __restrict__ bulk4, T* __restrict__ eps_t, Blk b) {
+    for (long long c = b.id * blockDim.x + threadIdx.x; c < g.nbulk; c += b.n * blockDim.x) {
+        const double e = __ldg(eps + c);
+        st4(bulk4, c, (T)(1.0 - e), __ldg(u + c), __ldg(u + g.nbulk + c), __ldg(u + 2 * g.nbulk + c));
+        if (eps_t) eps_t[c] = (T)e;
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256)
 k_pack(const double* __restrict__ eps, const T* __restrict__ u, GridDev g, T* __restrict__ bulk4,
        T* __restrict__ eps_t) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.nbulk) return;
-    const double e = __ldg(eps + c);
-    st4(bulk4, c, (T)(1.0 - e), __ldg(u + c), __ldg(u + g.nbulk + c), __ldg(u + 2 * g.nbulk + c));
-    if (eps_t) eps_t[c] = (T)e;
+    pack_body(eps, u, g, bulk4, eps_t, launch_blk());
 }
 
 // ----------------------------------------------------------------------
 // Final FP64 reduction of the block partials (one block, fixed order)
 // ----------------------------------------------------------------------
-struct SumsMap {
-    long long off[CG_NSUMS];     // first pair of the partial column, -1 = not computed
-    long long cnt[CG_NSUMS];     // number of partials
-};
 
 // One block per sum: merge the compensated pairs in a fixed order (strided
 // per thread, then a fixed tree), convert the final pair to double.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMap map, double* __restrict__ sums) {
+__device__ __forceinline__ void sums_body(const T* __restrict__ part, const SumsMap& map, double* __restrict__ sums,
+                                          Blk b) {
     __shared__ T sh_s[8], sh_c[8];
-    const int k = blockIdx.x;
+    const int k = (int)b.id;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     CSum<T> a;
     if (map.off[k] >= 0)
@@ -257,6 +283,79 @@ __global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMa
         }
         sums[k] = map.off[k] >= 0 ? (double)t.s + (double)t.c : __longlong_as_double(0x7ff8000000000000LL);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMap map, double* __restrict__ sums) {
+    sums_body(part, map, sums, launch_blk());
+}
+
+// ----------------------------------------------------------------------
+// Batched phases (FP32 instances): zeroing, porosity, pack, reaction, sums
+// ----------------------------------------------------------------------
+// Cell counts to 0, porosity to 1 (cells without particles keep it), the
+// reaction to 0 (cells without particles keep it).
+__global__ void __launch_bounds__(256) kb_zero(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        fill_body<int32_t>(I.count, I.gd.nbulk + 1, 0, b);
+        fill_body<double>(I.eps, I.gd.nbulk, 1.0, b);
+        fill_body<float>(I.S_bulk, 3 * I.gd.nbulk, 0.f, b);
+    });
+}
+
+__global__ void __launch_bounds__(256) kb_deposit_volume(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        deposit_volume_sorted_body<float>(I.vol_sorted, I.n, I.key_sorted, I.count, I.gd, I.eps,
+                                          I.part + 2 * I.part_off[PS_VOL], I.part_blocks[PS_VOL], 1, b);
+    });
+}
+
+__global__ void __launch_bounds__(256) kb_pack(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        pack_body<float>(I.eps, I.u_bulk, I.gd, I.bulk4, I.eps_fine ? I.eps_t : nullptr, b);
+    });
+}
+
+__global__ void __launch_bounds__(256) kb_deposit_momentum(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        deposit_sorted_force_body<float>(I.Fs, I.n, I.key_sorted, I.count, I.gd, I.S_bulk,
+                                         I.part + 2 * I.part_off[PS_MOM], I.part_blocks[PS_MOM], 1, b);
+    });
+}
+
+__global__ void __launch_bounds__(256) kb_sums(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) { sums_body<float>(I.part, I.smap, I.sums, b); });
+}
+
+cg_status launch_batch_deposit(int phase, const BLaunch& L, unsigned grid, cudaStream_t s) {
+    if (L.total == 0 || grid == 0) return CG_OK;
+    switch (phase) {
+        case BP_ZERO: kb_zero<<<grid, 256, 0, s>>>(L); break;
+        case BP_DEPV: kb_deposit_volume<<<grid, 256, 0, s>>>(L); break;
+        case BP_PACK: kb_pack<<<grid, 256, 0, s>>>(L); break;
+        case BP_DEPM: kb_deposit_momentum<<<grid, 256, 0, s>>>(L); break;
+        case BP_SUMS: kb_sums<<<grid, 256, 0, s>>>(L); break;
+        default: return CG_ERR_INVALID_ARG;
+    }
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+int batch_deposit_occupancy(int phase) {
+    int occ = 0;
+    cudaError_t e = cudaSuccess;
+    switch (phase) {
+        case BP_ZERO: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_zero, 256, 0); break;
+        case BP_DEPV: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_deposit_volume, 256, 0); break;
+        case BP_PACK: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_pack, 256, 0); break;
+        case BP_DEPM: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_deposit_momentum, 256, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_sums, 256, 0); break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return occ > 0 ? occ : 1;
 }
 
 // ----------------------------------------------------------------------
@@ -346,16 +445,16 @@ cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool w
     return CG_OK;
 }
 
-cg_status launch_sums(cg_grids* g, double* sums) {
+SumsMap sums_map(const long long* part_off, const long long* part_blocks) {
     SumsMap m;
     for (int k = 0; k < CG_NSUMS; ++k) {
         m.off[k] = -1;
         m.cnt[k] = 0;
     }
     auto col = [&](int dst, int region, int k) {
-        if (g->part_blocks[region] >= 0) {
-            m.off[dst] = g->part_off[region] + (long long)k * g->part_blocks[region];
-            m.cnt[dst] = g->part_blocks[region];
+        if (part_blocks[region] >= 0) {
+            m.off[dst] = part_off[region] + (long long)k * part_blocks[region];
+            m.cnt[dst] = part_blocks[region];
         }
     };
     col(0, PS_DRAG, 0);
@@ -368,6 +467,11 @@ cg_status launch_sums(cg_grids* g, double* sums) {
     }
     col(11, PS_DRAG, 4);
     col(15, PS_DRAG, 8);
+    return m;
+}
+
+cg_status launch_sums(cg_grids* g, double* sums) {
+    const SumsMap m = sums_map(g->part_off, g->part_blocks);
     if (g->fp64)
         CG_LAUNCH(g, "sums", k_sums<double>, CG_NSUMS, 256, 0, (const double*)g->partials, m, sums);
     else

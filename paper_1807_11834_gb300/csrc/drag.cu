@@ -21,6 +21,7 @@
 
 #include "cg_internal.cuh"
 #include "drag_law.cuh"
+#include "batch.cuh"
 
 namespace cg {
 
@@ -42,16 +43,17 @@ __device__ __forceinline__ V4<T> ld4_plain(const T* p, long long i) {
 // u += dt (F/m + g), x += dt u, specular reflection at the domain faces.
 // ----------------------------------------------------------------------
 template <typename T, bool EULER>
-__global__ void __launch_bounds__(256)
-k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
-       T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
-       T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
+__device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
+                                          const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
+                                          const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part,
+                                          long long pstride, int do_sums, unsigned long long* __restrict__ status,
+                                          Blk b) {
     T lane_sums[kDragSums];
 #pragma unroll
     for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
     int clamped_total = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const long long stride = b.n * blockDim.x;
+    for (long long p = b.id * blockDim.x + threadIdx.x; p < n; p += stride) {
         const V4<T> x = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
         const V4<T> v = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
         const V4<T> b = gather(bulk4, x.x, x.y, x.z, g);
@@ -114,8 +116,43 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
         CSum<T> acc[kDragSums];
 #pragma unroll
         for (int k = 0; k < kDragSums; ++k) acc[k].add(lane_sums[k]);
-        block_sums<T, kDragSums>(acc, part, pstride);
+        block_sums<T, kDragSums>(acc, part, pstride, b.id);
     }
+}
+
+template <typename T, bool EULER>
+__global__ void __launch_bounds__(256)
+k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
+       T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
+       T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
+    drag_body<T, EULER>(pos, vel, n, g, P, bulk4, F, Fs, inv_perm, dt, part, pstride, do_sums, status,
+                        launch_blk());
+}
+
+// Batched drag with the fused sorted-order force record (FP32 instances).
+template <bool EULER>
+__global__ void __launch_bounds__(256) kb_drag(BLaunch L, float dt) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        drag_body<float, EULER>(I.pos, I.vel, I.n, I.gd, I.P, I.bulk4, I.force, I.Fs, I.inv_perm, dt,
+                                I.part + 2 * I.part_off[PS_DRAG], I.part_blocks[PS_DRAG], 1, I.status, b);
+    });
+}
+
+cg_status launch_batch_drag(const BLaunch& L, unsigned grid, float dt, cudaStream_t s) {
+    if (L.total == 0 || grid == 0) return CG_OK;
+    if (dt > 0.f) kb_drag<true><<<grid, 256, 0, s>>>(L, dt);
+    else kb_drag<false><<<grid, 256, 0, s>>>(L, 0.f);
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+int batch_drag_occupancy() {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_drag<true>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return occ > 0 ? occ : 1;
 }
 
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,

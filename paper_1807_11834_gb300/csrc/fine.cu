@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "cg_internal.cuh"
+#include "batch.cuh"
 
 namespace cg {
 
@@ -79,11 +80,16 @@ __device__ __forceinline__ void average_cell(const T* __restrict__ u, const Grid
                                              T* __restrict__ var, long long cb);
 
 template <typename T, int RC>
+__device__ __forceinline__ void average_body(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
+                                             T* __restrict__ var, Blk b) {
+    for (long long cb = b.id * blockDim.x + threadIdx.x; cb < g.nbulk; cb += b.n * blockDim.x)
+        average_cell<T, RC>(u, g, ub, var, cb);
+}
+
+template <typename T, int RC>
 __global__ void __launch_bounds__(256)
 k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var) {
-    for (long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x; cb < g.nbulk;
-         cb += (long long)gridDim.x * blockDim.x)
-        average_cell<T, RC>(u, g, ub, var, cb);
+    average_body<T, RC>(u, g, ub, var, launch_blk());
 }
 
 template <typename T, int RC>
@@ -190,13 +196,14 @@ __device__ __forceinline__ void scale_sum(CSum<double>& a, const GridDev& g) {
     a.c *= g.Vf;
 }
 
+// One thread per bulk cell (block b covers cells [b.id blockDim, (b.id + 1) blockDim)).
 template <typename T, int RC>
-__global__ void __launch_bounds__(256)
-k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
-          const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0, T* __restrict__ out1,
-          T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part, long long pstride,
-          int do_sums) {
-    const long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void project_body(const T* __restrict__ in0, const T* __restrict__ in1,
+                                             const T* __restrict__ in2, const T* __restrict__ in3, int ncomp,
+                                             const GridDev& g, T* __restrict__ out0, T* __restrict__ out1,
+                                             T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part,
+                                             long long pstride, int do_sums, Blk b) {
+    const long long cb = b.id * blockDim.x + threadIdx.x;
     CSum<T> sacc[3];
     if (cb < g.nbulk) {
         int I, J, K;
@@ -272,8 +279,18 @@ k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restr
         // sum_f S_f V_f = V_f sum_f S_f; V_f applied as a float-float product
 #pragma unroll
         for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
-        block_sums<T, 3>(sacc, part, pstride);
+        block_sums<T, 3>(sacc, part, pstride, b.id);
     }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(256)
+k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
+          const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0, T* __restrict__ out1,
+          T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part, long long pstride,
+          int do_sums) {
+    project_body<T, RC>(in0, in1, in2, in3, ncomp, g, out0, out1, out2, out3, part, pstride, do_sums,
+                        launch_blk());
 }
 
 // Generic ratio: one thread per fine cell, the same clamped stencil with
@@ -322,8 +339,65 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
     if (do_sums) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
-        block_sums<T, 3>(sacc, part, pstride);
+        block_sums<T, 3>(sacc, part, pstride, blockIdx.x);
     }
+}
+
+// ----------------------------------------------------------------------
+// Batched fine-grid phases (FP32 instances, ratio 2, 4 or 8)
+// ----------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kb_average(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        switch (I.gd.r) {
+            case 2: average_body<float, 2>(I.u_fine, I.gd, I.u_bulk, I.var, b); break;
+            case 4: average_body<float, 4>(I.u_fine, I.gd, I.u_bulk, I.var, b); break;
+            default: average_body<float, 8>(I.u_fine, I.gd, I.u_bulk, I.var, b); break;
+        }
+    });
+}
+
+// eps: project the porosity (one component, no sums) instead of the source
+__global__ void __launch_bounds__(256) kb_project(BLaunch L, int eps) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        const long long nb = I.gd.nbulk, nf = I.gd.nfine;
+        const float* in0 = eps ? I.eps_t : I.S_bulk;
+        const float* in1 = eps ? nullptr : I.S_bulk + nb;
+        const float* in2 = eps ? nullptr : I.S_bulk + 2 * nb;
+        float* o0 = eps ? I.eps_fine : I.S_fine;
+        float* o1 = eps ? nullptr : I.S_fine + nf;
+        float* o2 = eps ? nullptr : I.S_fine + 2 * nf;
+        const int nc = eps ? 1 : 3;
+        float* part = I.part + 2 * I.part_off[PS_PROJ];
+        const long long ps = I.part_blocks[PS_PROJ];
+        switch (I.gd.r) {
+            case 2: project_body<float, 2>(in0, in1, in2, nullptr, nc, I.gd, o0, o1, o2, nullptr, part, ps, !eps, b); break;
+            case 4: project_body<float, 4>(in0, in1, in2, nullptr, nc, I.gd, o0, o1, o2, nullptr, part, ps, !eps, b); break;
+            default: project_body<float, 8>(in0, in1, in2, nullptr, nc, I.gd, o0, o1, o2, nullptr, part, ps, !eps, b); break;
+        }
+    });
+}
+
+cg_status launch_batch_fine(int phase, const BLaunch& L, unsigned grid, cudaStream_t s) {
+    if (L.total == 0 || grid == 0) return CG_OK;
+    switch (phase) {
+        case BP_AVG: kb_average<<<grid, 256, 0, s>>>(L); break;
+        case BP_PROJ: kb_project<<<grid, 256, 0, s>>>(L, 0); break;
+        case BP_PROJE: kb_project<<<grid, 256, 0, s>>>(L, 1); break;
+        default: return CG_ERR_INVALID_ARG;
+    }
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+int batch_fine_occupancy(int phase) {
+    int occ = 0;
+    cudaError_t e = phase == BP_AVG ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_average, 256, 0)
+                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_project, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return occ > 0 ? occ : 1;
 }
 
 static inline unsigned blocks_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }

@@ -209,6 +209,38 @@ def small_clustered_bed(seed: int = 0, fp64: bool = False) -> Workload:
     return clustered_bed(seed, fine_n=(128, 128, 64), ratio=4, n=500_000, fp64=fp64)
 
 
+def batch_instance(seed: int, k: int, edge: int, ratio: int, n: int, d: float) -> Workload:
+    """Instance k of a batch: unit cube, fine edge^3, the given ratio, n
+    spheres of diameter d uniform in the domain, N(0, 0.05) velocities,
+    the Taylor-Green field of ``tiny``, Di Felice drag, FP32."""
+    rng = rng_for(seed, 100 + k)
+    desc = make_desc((0, 0, 0), (1, 1, 1), (edge,) * 3, ratio, fp64=False, law=DRAG_DI_FELICE)
+    xyz = rng.random((n, 3))
+    vel3 = rng.normal(0.0, 0.05, (n, 3))
+    cx, cy, cz = fine_centres(desc["origin"], desc["extent"], desc["fine_n"])
+    u = np.empty((3, edge, edge, edge), dtype=np.float32)
+    u[0] = (0.1 * np.sin(cx)[None, None, :] * np.cos(cy)[None, :, None] * np.cos(cz)[:, None, None])
+    u[1] = (-0.1 * np.cos(cx)[None, None, :] * np.sin(cy)[None, :, None] * np.cos(cz)[:, None, None])
+    u[2] = 0.0
+    return Workload(f"batch_{k}", desc, _pack(xyz, d, np.float32), _pack(vel3, 0.0, np.float32), u)
+
+
+def uneven_batch(seed: int = 0, count: int = 64, edges=(32, 64, 96, 128), ratios=(2, 4, 8),
+                 n_range=(10_000, 2_000_000), d_range=(0.002, 0.01)) -> list:
+    """Independent instances of uneven sizes: per instance a fine edge from
+    ``edges``, a ratio from ``ratios``, a particle count log-uniform in
+    ``n_range`` and a diameter uniform in ``d_range`` (all from the seed)."""
+    rng = rng_for(seed, 99)
+    out = []
+    for k in range(count):
+        edge = int(rng.choice(edges))
+        ratio = int(rng.choice(ratios))
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        d = float(rng.uniform(*d_range))
+        out.append(batch_instance(seed, k, edge, ratio, n, d))
+    return out
+
+
 def evolved_field(w: Workload, seed: int = 0, amp: float = 0.05) -> np.ndarray:
     """A later fine velocity field for the stale / fresh closure cases:
     the workload's field plus a smooth large-scale swirl of amplitude

@@ -32,6 +32,22 @@ def assert_close(name, got, ref, tol, vec=False, mask=None):
     return mx
 
 
+def assert_close_interp(name, got, ref, ref_abs, tol):
+    """Interpolated vector field ([3][m]): the error of each cell within tol
+    of max(|ref|, |interpolant of the absolute corner values| (ref_abs),
+    1e-3 max|ref|), Euclidean norms per cell.  An FP32 lerp between values
+    of opposite sign rounds relative to the corner magnitudes, not to the
+    (possibly near-zero) result."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    num = np.sqrt(((got - ref) ** 2).sum(axis=0))
+    den = np.maximum(np.sqrt((ref ** 2).sum(axis=0)), np.sqrt((np.asarray(ref_abs, np.float64) ** 2).sum(axis=0)))
+    den = np.maximum(den, 1e-3 * den.max())
+    r = num / den
+    assert r.max() <= tol, f"{name}: max rel err {r.max():.3e} > {tol:.1e}"
+    return float(r.max())
+
+
 def to_dev(a, dev="cuda:0"):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)

@@ -52,6 +52,31 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(cg.GridDesc) == 6 * 8 + 8 * 4 + 5 * 8 + 3 * 8
     assert ctypes.sizeof(cg.StepOut) == 11 * 8
     assert ctypes.sizeof(cg.Particles) == 24
+    # cg_batch_item: desc, particles, u_fine pointer, step outputs; cg_batch_config: 5 int32
+    assert ctypes.sizeof(cg.BatchItem) == ctypes.sizeof(cg.GridDesc) + 24 + 8 + 11 * 8
+    assert ctypes.sizeof(cg.BatchConfig) == 5 * 4
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """sizeof / offsetof of the ABI structs as gcc lays them out from cg.h."""
+    import shutil
+    import subprocess
+    import paper_1807_11834_gb300 as cg
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cg.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cg_grid_desc), '
+                   'sizeof(cg_particles), sizeof(cg_step_out), sizeof(cg_batch_item), '
+                   'offsetof(cg_batch_item, u_fine), offsetof(cg_batch_item, out), sizeof(cg_batch_config));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(cg.GridDesc), ctypes.sizeof(cg.Particles), ctypes.sizeof(cg.StepOut),
+            ctypes.sizeof(cg.BatchItem), cg.BatchItem.u_fine.offset, cg.BatchItem.out.offset,
+            ctypes.sizeof(cg.BatchConfig)]
+    assert got == want
 
 
 def test_invalid_arguments_rejected_before_any_gpu_work(libcg):

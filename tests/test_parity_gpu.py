@@ -162,6 +162,22 @@ def test_small_clustered_bed_fp32_with_euler(cuda_lib):
     got = run_step(cuda_lib, w, dt=w.dt)
     compare_step(w, got, ref, TOL_FP32)
     compare_sums(got, ref, 5 * TOL_FP32)
+    _euler_checks(w, got, ref)
+
+
+def test_packed_bed_full_size_fp32(cuda_lib):
+    """The benchmark's workload (4M particles, fine 256x256x512) at full size,
+    in the launch configuration the benchmark times."""
+    w = synth.packed_bed(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+    got = run_step(cuda_lib, w)
+    mask = switch_mask(w, ref)
+    errs = compare_step(w, got, ref, TOL_FP32, mask=mask)
+    print("packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()},
+          "excluded at switch:", int((~mask).sum()))
+
+
+def _euler_checks(w, got, ref):
     # u_new = u + dt (F/m + g): drag and gravity cancel for some particles, so
     # the bound is relative to the magnitude of the terms, not of the result
     d = w.pos_d[:, 3].astype(np.float64)
@@ -175,16 +191,46 @@ def test_small_clustered_bed_fp32_with_euler(cuda_lib):
     assert np.array_equal(got["pos_d"][:, 3], w.pos_d[:, 3])
 
 
-def test_packed_bed_full_size_fp32(cuda_lib):
-    """The benchmark's workload (4M particles, fine 256x256x512) at full size,
-    in the launch configuration the benchmark times."""
-    w = synth.packed_bed(seed=0)
-    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
-    got = run_step(cuda_lib, w)
-    mask = switch_mask(w, ref)
-    errs = compare_step(w, got, ref, TOL_FP32, mask=mask)
-    print("packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()},
-          "excluded at switch:", int((~mask).sum()))
+def test_clustered_bed_full_size_fp32_with_euler(cuda_lib):
+    """The 32M-particle clustered bed (fine 512x512x256, ratio 4, Di Felice,
+    gravity, dt 1e-4) at full size: one step with the Euler advance from
+    the shared initial state, every field and particle against the oracle."""
+    w = synth.clustered_bed(seed=0)
+    ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, dt=w.dt, want_eps_fine=True)
+    got = run_step(cuda_lib, w, dt=w.dt)
+    errs = compare_step(w, got, ref, TOL_FP32)
+    compare_sums(got, ref, 5 * TOL_FP32)
+    _euler_checks(w, got, ref)
+    print("clustered_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()},
+          "clamped porosities:", got["counts"][2])
+
+
+def test_clustered_bed_100_steps_conservation_drift(cuda_lib):
+    """100 coupled steps of the clustered bed (fluid frozen, particles
+    advanced).  After every step the device's FP64 conservation sums must
+    close: sum F_p + sum S_B V_B = 0, sum S_B V_B = sum S_f V_f and
+    sum V_p = sum (1 - eps_B) V_B, each to FP32 round-off of the summed
+    terms; the per-step residuals are printed (the drift report)."""
+    import torch
+    w = synth.clustered_bed(seed=0)
+    g = cuda_lib.Grids(w.desc)
+    pos, vel, uf = inputs(w)
+    out = g.alloc_outputs(w.n, eps_fine=True)
+    res = []
+    for _ in range(w.steps):
+        g.cg_step(pos, vel, uf, out, dt=w.dt)
+        s = out["sums"].cpu().numpy()
+        res.append((np.abs(s[2:5] + s[5:8]).max() / s[11], np.abs(s[5:8] - s[8:11]).max() / s[11],
+                    abs(s[0] - s[1]) / s[0]))
+    rc, flags, counts = g.cg_sync_status()
+    g.close()
+    res = np.array(res)
+    print("per-step residuals (action-reaction, projection, volume): max", res.max(axis=0),
+          "last", res[-1], "first", res[0])
+    assert rc == 0 and counts[0] == 0 and counts[1] == 0
+    assert np.all(res[:, 0] <= 10 * TOL_FP32) and np.all(res[:, 1] <= 10 * TOL_FP32)
+    assert np.all(res[:, 2] <= TOL_FP32)
+    assert torch.isfinite(pos).all()
 
 
 def test_repeat_is_bit_identical(cuda_lib):
