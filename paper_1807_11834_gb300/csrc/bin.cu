@@ -36,9 +36,6 @@ __device__ __forceinline__ void add_status(unsigned long long* st, int outside, 
 // ----------------------------------------------------------------------
 // Key kernel: cell per particle, per-cell counts, tile histogram of digit 0
 // ----------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T pi6_b();
-template <> __device__ __forceinline__ float pi6_b<float>() { return 0.52359877559829887f; }
-template <> __device__ __forceinline__ double pi6_b<double>() { return 0.52359877559829887308; }
 
 template <typename T>
 __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long long n, const GridDev& g,
@@ -71,7 +68,7 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
             c = cell_of(v, g, outside);
             n_out += outside;
             key[p] = c;
-            vol[p] = pi6_b<T>() * v.w * v.w * v.w;
+            vol[p] = v.w;   // the diameter: the porosity forms the volume as an exact pair
         }
         // counts: one integer atomic per run of equal cells in the warp
         // (spatially ordered input has runs of several particles)

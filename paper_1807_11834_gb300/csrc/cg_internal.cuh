@@ -101,8 +101,8 @@ struct cg_grids {
     int32_t* perm = nullptr;       // [cap] particle ids in cell order
     int32_t* key_sorted = nullptr; // [cap] cell of each slot of the sorted order
     int32_t* inv_perm = nullptr;   // [cap] sorted slot of each particle
-    void* vol = nullptr;           // [cap] T particle volume, caller order
-    void* vol_sorted = nullptr;    // [cap] T particle volume, sorted order
+    void* vol = nullptr;           // [cap] T particle diameter, caller order (for the volume deposit)
+    void* vol_sorted = nullptr;    // [cap] T particle diameter, sorted order
     void* Fs = nullptr;            // [cap] T4 drag force, sorted order
     bool vol_valid = false;        // vol_sorted matches the binned positions
     int32_t* hist = nullptr;       // [2^digit * ntiles]
@@ -111,7 +111,7 @@ struct cg_grids {
 
     // bulk-sized buffers
     int32_t* cell_start = nullptr; // [nbulk + 1]
-    void* bulk4 = nullptr;         // [nbulk] T4: phi, u_x, u_y, u_z
+    void* bulk4 = nullptr;         // [nbulk] T4: eps, u_x, u_y, u_z
     void* eps_t = nullptr;         // [nbulk] T: porosity in the path precision
     void* partials = nullptr;      // conservation-sum block partials: (s, c) pairs of T
     long long part_off[cg::PS_NREG] = {0, 0, 0, 0};
@@ -508,6 +508,76 @@ __device__ __forceinline__ void seg_rounds(long long s, long long t, const int32
             carry_key = k31;
         }
     }
+}
+
+// Segmented sum of one compensated value per slot, compensated at every
+// addition (TwoSum in the lane scan too): load(i, hi, lo) gives slot i as an
+// unevaluated pair, emit(key, tot) receives each segment's pair.  Used for
+// the solid volume, where eps = 1 - phi must stay accurate as phi -> 1.
+template <typename T, typename Load, typename Emit>
+__device__ __forceinline__ void seg_rounds_cs(long long s, long long t, const int32_t* __restrict__ key_sorted,
+                                              Load load, Emit emit) {
+    const int lane = threadIdx.x & 31;
+    CSum<T> carry;
+    int carry_key = -1;
+    for (long long r0 = s; r0 < t; r0 += 32) {
+        const long long i = r0 + lane;
+        const bool valid = i < t;
+        int kj = -1;
+        CSum<T> v;
+        if (valid) {
+            kj = __ldg(key_sorted + i);
+            load(i, v.s, v.c);
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int ko = __shfl_up_sync(0xffffffffu, kj, off);
+            CSum<T> o;
+            o.s = __shfl_up_sync(0xffffffffu, v.s, off);
+            o.c = __shfl_up_sync(0xffffffffu, v.c, off);
+            if (lane >= off && ko == kj) {
+                // keep the lower slots first, as a sequential walk would
+                o.merge(v);
+                v = o;
+            }
+        }
+        int next = __shfl_down_sync(0xffffffffu, kj, 1);
+        const int nxt = (lane == 0 && r0 + 32 < t) ? __ldg(key_sorted + r0 + 32) : -1;
+        const int next31 = __shfl_sync(0xffffffffu, nxt, 0);
+        if (lane == 31) next = next31;
+        if (valid && next != kj) {
+            CSum<T> tot;
+            if (kj == carry_key) tot = carry;
+            tot.merge(v);
+            emit(kj, tot);
+        }
+        const int k31 = __shfl_sync(0xffffffffu, kj, 31);
+        CSum<T> v31;
+        v31.s = __shfl_sync(0xffffffffu, v.s, 31);
+        v31.c = __shfl_sync(0xffffffffu, v.c, 31);
+        if (k31 != carry_key) carry = CSum<T>();
+        carry.merge(v31);
+        carry_key = k31;
+    }
+}
+
+// Sphere volume pi d^3 / 6 as an unevaluated pair hi + lo: exact products
+// by FMA in FP32 (relative error ~2^-46), the plain product in FP64.
+__device__ __forceinline__ void sphere_volume_pair(float d, float& hi, float& lo) {
+    const float p = d * d;
+    const float pe = fmaf(d, d, -p);             // d^2 = p + pe exactly
+    const float q = p * d;
+    const float qe = fmaf(p, d, -q);             // p d = q + qe exactly
+    const float r = fmaf(pe, d, qe);             // d^3 = q + r (to 2^-48)
+    const float ch = 0.5235987901687622f;        // pi / 6 = ch + cl
+    const float cl = -1.457046305830545e-08f;
+    hi = ch * q;
+    const float he = fmaf(ch, q, -hi);
+    lo = fmaf(ch, r, fmaf(cl, q, he));
+}
+__device__ __forceinline__ void sphere_volume_pair(double d, double& hi, double& lo) {
+    hi = 0.52359877559829887308 * d * d * d;
+    lo = 0.0;
 }
 
 // Walk the segments owned by the chunk at `base`: fn(key, b, e) for each.

@@ -20,9 +20,6 @@
 
 namespace cg {
 
-template <typename T> __device__ __forceinline__ T pi_over_6();
-template <> __device__ __forceinline__ float pi_over_6<float>() { return 0.52359877559829887f; }
-template <> __device__ __forceinline__ double pi_over_6<double>() { return 0.52359877559829887308; }
 
 // ----------------------------------------------------------------------
 // Porosity over the sorted order (see seg_chunk_range): the segmented
@@ -62,7 +59,7 @@ k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restri
             if (valid) {
                 key = __ldg(key_sorted + i);
                 const T d = __ldg(pos + 4 * (long long)__ldg(perm + i) + 3);
-                v[0].s = pi_over_6<T>() * d * d * d;
+                sphere_volume_pair(d, v[0].s, v[0].c);
             }
             if (lane == 0 && key == carry_key) {
                 CSum<T> c0 = carry;
@@ -84,10 +81,12 @@ k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restri
     if (do_sums) block_sums<T, 1>(tot, part, pstride, blockIdx.x);
 }
 
-// Porosity from the volumes already in sorted order (written by the final
-// binning pass): rounds of 32 slots, no gather.
+// Porosity from the diameters already in sorted order (written by the final
+// binning pass): each volume as an exact pair, compensated at every
+// addition, so eps = 1 - phi keeps its accuracy in near-packed cells
+// (phi -> 1) on the FP32 path.
 template <typename T>
-__device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__ vs, long long n,
+__device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__ dsorted, long long n,
                                                            const int32_t* __restrict__ key_sorted,
                                                            const int32_t* __restrict__ cs, const GridDev& g,
                                                            double* __restrict__ eps, T* __restrict__ part,
@@ -98,11 +97,11 @@ __device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
         seg_chunk_range(base, n, key_sorted, cs, s, t);
-        seg_rounds<T, 1>(
-            s, t, key_sorted, [&](long long i, T (&v)[1]) { v[0] = __ldg(vs + i); },
-            [&](int key, CSum<T> (&a)[1]) {
-                eps[key] = 1.0 - ((double)a[0].s + (double)a[0].c) * g.invVB;
-                tot[0].merge(a[0]);
+        seg_rounds_cs<T>(
+            s, t, key_sorted, [&](long long i, T& hi, T& lo) { sphere_volume_pair(__ldg(dsorted + i), hi, lo); },
+            [&](int key, const CSum<T>& a) {
+                eps[key] = 1.0 - ((double)a.s + (double)a.c) * g.invVB;
+                tot[0].merge(a);
             });
     }
     if (do_sums) block_sums<T, 1>(tot, part, pstride, b.id);
@@ -110,10 +109,10 @@ __device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_deposit_volume_sorted(const T* __restrict__ vs, long long n, const int32_t* __restrict__ key_sorted,
+k_deposit_volume_sorted(const T* __restrict__ dsorted, long long n, const int32_t* __restrict__ key_sorted,
                         const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
                         long long pstride, int do_sums) {
-    deposit_volume_sorted_body(vs, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk());
+    deposit_volume_sorted_body(dsorted, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk());
 }
 
 // Reaction from the forces the drag wrote in sorted order (T4 per slot);
@@ -225,15 +224,17 @@ k_deposit_momentum(const T* __restrict__ F, long long n, const int32_t* __restri
 }
 
 // ----------------------------------------------------------------------
-// Pack the bulk fields read by the drag gather: (phi, u_x, u_y, u_z) per
-// cell in the path precision, phi = 1 - eps formed in double.
+// Pack the bulk fields read by the drag gather: (eps, u_x, u_y, u_z) per
+// cell in the path precision.  Interpolating eps itself (not 1 - eps) keeps
+// the porosity at the particle accurate to a few roundings of eps also in
+// near-packed cells, where the drag is most sensitive to it.
 // ----------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void pack_body(const double* __restrict__ eps, const T* __restrict__ u, const GridDev& g,
                                           T* __restrict__ bulk4, T* __restrict__ eps_t, Blk b) {
     for (long long c = b.id * blockDim.x + threadIdx.x; c < g.nbulk; c += b.n * blockDim.x) {
         const double e = __ldg(eps + c);
-        st4(bulk4, c, (T)(1.0 - e), __ldg(u + c), __ldg(u + g.nbulk + c), __ldg(u + 2 * g.nbulk + c));
+        st4(bulk4, c, (T)e, __ldg(u + c), __ldg(u + g.nbulk + c), __ldg(u + 2 * g.nbulk + c));
         if (eps_t) eps_t[c] = (T)e;
     }
 }
@@ -382,7 +383,7 @@ cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, dou
     }
     if (n == 0) return CG_OK;
     if (pos_d == nullptr) {
-        // volumes already in sorted order from the binning of these positions
+        // diameters already in sorted order from the binning of these positions
         if (g->fp64)
             CG_LAUNCH(g, "deposit_volume", k_deposit_volume_sorted<double>, nblk, 256, 0,
                       (const double*)g->vol_sorted, n, g->key_sorted, g->cell_start, g->gd, eps, (double*)part,

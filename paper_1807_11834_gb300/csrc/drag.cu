@@ -8,7 +8,7 @@
 // One thread per particle in the caller's order: the particle record is
 // read once (two 16-byte loads) and the force written once (three
 // coalesced stores).  The bulk fields are gathered from a packed array of
-// (phi, u_x, u_y, u_z) per cell, eight 16-byte loads that stay in L2.  For
+// (eps, u_x, u_y, u_z) per cell, eight 16-byte loads that stay in L2.  For
 // the fused reaction deposit the force is also written, as a 16-byte
 // record, to its slot in bin order, so the following segmented sum reads
 // it contiguously.
@@ -57,8 +57,8 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
         const V4<T> x = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
         const V4<T> v = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
         const V4<T> b = gather(bulk4, x.x, x.y, x.z, g);
-        T phi = b.x;
-        T eps = T(1) - phi;
+        T eps = b.x;
+        T phi = T(1) - eps;
         int cl = 0;
         if (eps < P.eps_min) {
             eps = P.eps_min;

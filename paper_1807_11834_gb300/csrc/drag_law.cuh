@@ -76,7 +76,7 @@ __device__ __forceinline__ V4<T> lerp4(const V4<T>& a, const V4<T>& b, T t) {
     return {lerp_(a.x, b.x, t), lerp_(a.y, b.y, t), lerp_(a.z, b.z, t), lerp_(a.w, b.w, t)};
 }
 
-// Gather (phi, u) at a point.
+// Gather (eps, u) at a point.
 template <typename T>
 __device__ __forceinline__ V4<T> gather(const T* __restrict__ bulk4, T x, T y, T z, const GridDev& g) {
     if (g.interp == CG_INTERP_CELL) {
@@ -131,13 +131,13 @@ __device__ __forceinline__ T drag_beta(int law, T eps, T phi, T d, T smag, const
     return T(0.75) * cds * eps * P.rho * M<T>::pow_(eps, T(-2.65)) / d * vp;
 }
 
-// Bulk record and its trilinear gradient at a point: phi, u (value) and
-// d phi / dx_a (zero along an axis where the point is in the outer half
+// Bulk record and its trilinear gradient at a point: eps, u (value) and
+// d eps / dx_a (zero along an axis where the point is in the outer half
 // cell, or in cell-value mode), plus an interpolated scalar field.
 template <typename T>
 struct Probe {
-    T phi, ux, uy, uz, sc;
-    T gphi[3];
+    T eps, ux, uy, uz, sc;
+    T geps[3];
 };
 
 __device__ __forceinline__ bool axis_weight_cl(float x, const GridDev& g, int a, int& i0, float& t);
@@ -151,9 +151,9 @@ __device__ __forceinline__ Probe<T> probe(const T* __restrict__ bulk4, const T* 
         const int c = sizeof(T) == 4 ? cell_of_f((float)x, (float)y, (float)z, g)
                                      : cell_of_d((double)x, (double)y, (double)z, g);
         const V4<T> b = ld4(bulk4, c);
-        r.phi = b.x; r.ux = b.y; r.uy = b.z; r.uz = b.w;
+        r.eps = b.x; r.ux = b.y; r.uy = b.z; r.uz = b.w;
         r.sc = scal ? __ldg(scal + c) : T(0);
-        r.gphi[0] = r.gphi[1] = r.gphi[2] = T(0);
+        r.geps[0] = r.geps[1] = r.geps[2] = T(0);
         return r;
     }
     int i0, j0, k0;
@@ -175,17 +175,17 @@ __device__ __forceinline__ Probe<T> probe(const T* __restrict__ bulk4, const T* 
     const V4<T> a00 = lerp4(v[0], v[1], tx), a10 = lerp4(v[2], v[3], tx);
     const V4<T> a01 = lerp4(v[4], v[5], tx), a11 = lerp4(v[6], v[7], tx);
     const V4<T> val = lerp4(lerp4(a00, a10, ty), lerp4(a01, a11, ty), tz);
-    r.phi = val.x; r.ux = val.y; r.uy = val.z; r.uz = val.w;
+    r.eps = val.x; r.ux = val.y; r.uy = val.z; r.uz = val.w;
     const T s00 = lerp_(s[0], s[1], tx), s10 = lerp_(s[2], s[3], tx);
     const T s01 = lerp_(s[4], s[5], tx), s11 = lerp_(s[6], s[7], tx);
     r.sc = lerp_(lerp_(s00, s10, ty), lerp_(s01, s11, ty), tz);
-    // gradient of phi: difference along the axis, weights of the other two
+    // gradient of eps: difference along the axis, weights of the other two
     const T dx = lerp_(lerp_(v[1].x - v[0].x, v[3].x - v[2].x, ty), lerp_(v[5].x - v[4].x, v[7].x - v[6].x, ty), tz);
     const T dy = lerp_(lerp_(v[2].x - v[0].x, v[3].x - v[1].x, tx), lerp_(v[6].x - v[4].x, v[7].x - v[5].x, tx), tz);
     const T dz = lerp_(lerp_(v[4].x - v[0].x, v[5].x - v[1].x, tx), lerp_(v[6].x - v[2].x, v[7].x - v[3].x, tx), ty);
-    r.gphi[0] = cx ? T(0) : dx * (T)g.invH[0];
-    r.gphi[1] = cy ? T(0) : dy * (T)g.invH[1];
-    r.gphi[2] = cz ? T(0) : dz * (T)g.invH[2];
+    r.geps[0] = cx ? T(0) : dx * (T)g.invH[0];
+    r.geps[1] = cy ? T(0) : dy * (T)g.invH[1];
+    r.geps[2] = cz ? T(0) : dz * (T)g.invH[2];
     return r;
 }
 

@@ -511,9 +511,9 @@ template <typename T>
 __device__ __forceinline__ void closure_features(const Probe<T>& st, const V4<T>& x, const V4<T>& v,
                                                  const GridDev& g, const Phys<T>& P, float (&f)[FEAT_STRIDE],
                                                  T& epsc, T& phic, T (&s)[3], T& smag) {
-    T eps = T(1) - st.phi;
+    const T eps = st.eps;
     epsc = eps;
-    phic = st.phi;
+    phic = T(1) - eps;
     if (eps < P.eps_min) {
         epsc = P.eps_min;
         phic = T(1) - P.eps_min;
@@ -526,9 +526,9 @@ __device__ __forceinline__ void closure_features(const Probe<T>& st, const V4<T>
     f[0] = (float)epsc;
     f[1] = (float)(sizeof(T) == 4 ? log10f((float)(T(1) + Re)) : log10((double)(T(1) + Re)));
     f[2] = (float)smag;
-    f[3] = (float)(-st.gphi[0]);
-    f[4] = (float)(-st.gphi[1]);
-    f[5] = (float)(-st.gphi[2]);
+    f[3] = (float)st.geps[0];
+    f[4] = (float)st.geps[1];
+    f[5] = (float)st.geps[2];
     f[6] = (float)st.sc;
     f[7] = 0.f;
 }
@@ -640,7 +640,7 @@ k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, co
             const Probe<float> st = probe(bulk_stale, var_stale, x.x, x.y, x.z, g);
             float sv[3], smag;
             closure_features(st, x, v, g, P, f, epsc, phic, sv, smag);
-            clamped += (1.f - st.phi) < P.eps_min;
+            clamped += st.eps < P.eps_min;
             const float b = drag_beta(g.law, epsc, phic, x.w, smag, P);
             Fst[0] = b * sv[0];
             Fst[1] = b * sv[1];

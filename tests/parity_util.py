@@ -33,15 +33,16 @@ def assert_close(name, got, ref, tol, vec=False, mask=None):
 
 
 def assert_close_interp(name, got, ref, ref_abs, tol):
-    """Interpolated vector field ([3][m]): the error of each cell within tol
+    """Interpolated field ([3][m] or [m]): the error of each cell within tol
     of max(|ref|, |interpolant of the absolute corner values| (ref_abs),
     1e-3 max|ref|), Euclidean norms per cell.  An FP32 lerp between values
     of opposite sign rounds relative to the corner magnitudes, not to the
     (possibly near-zero) result."""
-    got = np.asarray(got, np.float64)
-    ref = np.asarray(ref, np.float64)
+    got = np.atleast_2d(np.asarray(got, np.float64))
+    ref = np.atleast_2d(np.asarray(ref, np.float64))
+    ref_abs = np.atleast_2d(np.asarray(ref_abs, np.float64))
     num = np.sqrt(((got - ref) ** 2).sum(axis=0))
-    den = np.maximum(np.sqrt((ref ** 2).sum(axis=0)), np.sqrt((np.asarray(ref_abs, np.float64) ** 2).sum(axis=0)))
+    den = np.maximum(np.sqrt((ref ** 2).sum(axis=0)), np.sqrt((ref_abs ** 2).sum(axis=0)))
     den = np.maximum(den, 1e-3 * den.max())
     r = num / den
     assert r.max() <= tol, f"{name}: max rel err {r.max():.3e} > {tol:.1e}"

@@ -74,13 +74,12 @@ def test_features_fp32_grids(cuda_lib):
     fo, to, _ = oracle.mlp_features(w.desc, w.pos_d, w.vel, ref["eps_bulk"], ref["u_bulk"], ref["var_bulk"], ub1)
     for k in (0, 1, 2, 6):
         assert_close(f"feature {k}", f[:, k], fo[:, k], TOL_FP32)
-    # the gradient is a difference of bulk solid fractions phi = 1 - eps,
-    # each rounded to FP32 (2^-24 |phi|), divided by H, then interpolated:
-    # absolute error within 8 roundings of max phi over H, plus the path
-    # tolerance of the value itself
-    phi_max = float((1.0 - ref["eps_bulk"]).max())
+    # the gradient is a difference of bulk porosities, each rounded to FP32
+    # (2^-24 |eps|), divided by H, then interpolated: absolute error within
+    # 8 roundings of max |eps| over H, plus the path tolerance of the value
+    eps_max = float(np.abs(ref["eps_bulk"]).max())
     H = min(w.desc["extent"][a] / w.desc["fine_n"][a] * w.desc["ratio"] for a in range(3))
-    bound = 8 * 2.0 ** -24 * phi_max / H + TOL_FP32 * np.abs(fo[:, 3:6])
+    bound = 8 * 2.0 ** -24 * eps_max / H + TOL_FP32 * np.abs(fo[:, 3:6])
     err = np.abs(f[:, 3:6] - fo[:, 3:6])
     print("grad eps max err / bound", (err / bound).max())
     assert np.all(err <= bound)
