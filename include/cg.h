@@ -173,7 +173,7 @@ cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n, const voi
  * summed in the stable order of the last cg_bin_particles.
  *   CG_DEP_VOLUME:   per_particle = pos_d [n] T4 (diameter used);
  *                    bulk_out = eps double [n_b], eps = 1 - sum(pi d^3/6) / V_B
- *                    (Table 1 porosity field; Sec. 2.3 porosity definition).
+ *                    (Table 1 porosity field; Sec. 2.4 porosity definition).
  *   CG_DEP_MOMENTUM: per_particle = force [3][n] T;
  *                    bulk_out = S [3][n_b] T, S = -(1/V_B) sum F
  *                    (Eq. UFP: F_fpi is the counterpart of F_drag).

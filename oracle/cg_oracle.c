@@ -14,7 +14,7 @@
  *    carries the fluid.  Particle fields go bulk -> fine, the fluid solution
  *    fine -> bulk.
  *  - Table 1: porosity field from sum_i V_pi / V_cell over the n_pc particles
- *    of a cell; Sec. 2.3 defines porosity as fluid volume over cell volume.
+ *    of a cell; Sec. 2.4 defines porosity as fluid volume over cell volume.
  *    Reading: solid fraction phi = sum V_p / V_B, porosity eps = 1 - phi,
  *    deposit at the particle centre's cell.
  *  - Eq. (DragLaw): F_drag = beta (u_f - u_p), beta depending on slip,
@@ -123,7 +123,7 @@ int64_t or_bin(const or_grid* G, int64_t n, const double* pos_d,
     return outside;
 }
 
-/* Porosity (Table 1 and Sec. 2.3): phi_B = sum V_p / V_B, eps = 1 - phi. */
+/* Porosity (Table 1 and Sec. 2.4): phi_B = sum V_p / V_B, eps = 1 - phi. */
 void or_deposit_volume(const or_grid* G, int64_t n, const double* pos_d,
                        const int32_t* cell_start, const int32_t* perm,
                        double* eps, double* phi)

@@ -3,7 +3,7 @@
 // sums.
 //
 // Porosity (Table 1 of arXiv 1807.11834: porosity field from the particle
-// volumes of a cell; Sec. 2.3: porosity = fluid volume / cell volume):
+// volumes of a cell; Sec. 2.4, beside Eq. DragLaw: porosity = fluid volume / cell volume):
 // phi_B = sum_{p in B} V_p / V_B, eps_B = 1 - phi_B.
 // Reaction (Eq. UFP: F_fpi is the counterpart of F_drag):
 // S_B = -(1/V_B) sum_{p in B} F_p.

@@ -118,7 +118,7 @@ def test_bin_is_stable_sort():
 
 
 # --------------------------------------------------------------------------
-# D0: porosity (Table 1: sum V_p / V_cell; Sec. 2.3: eps = fluid / cell volume)
+# D0: porosity (Table 1: sum V_p / V_cell; Sec. 2.4: eps = fluid / cell volume)
 # --------------------------------------------------------------------------
 def test_porosity_conserves_volume_and_empty_cells():
     w = synth.tiny(seed=1, n=3000)
