@@ -450,8 +450,8 @@ static cg_status on_aux(cg_grids* g, Fn f) {
 }
 
 // One coupling step.  Fork / join on the auxiliary stream:
-//   main: bin -> porosity --(avg)--> pack -> drag -> reaction -> project S --(eps_f)--> sums
-//   aux :  average fine -> bulk      \-> project eps
+//   main: bin -> porosity --(avg)--> drag -> reaction -> project S --(eps_f)--> sums
+//   aux :  average fine -> bulk  \-(porosity)-> project eps
 // The averaging reads only the fine field and the porosity projection only
 // the packed porosity, so both overlap the latency-bound particle kernels.
 //
@@ -466,13 +466,25 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     cudaStream_t side = g->prof ? g->stream : g->aux;
     CG_CUDA(cudaEventRecord(g->ev_fork, g->stream));
     CG_CUDA(cudaStreamWaitEvent(side, g->ev_fork, 0));
-    if (!mlp) CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk); }));
+    // the drag's packed record (eps, u) is written by the kernels that form its
+    // parts: the average (u, on the side stream), the binning (eps = 1 in every
+    // cell) and the porosity deposit (eps of occupied cells); with a closure
+    // or no particles it is packed from the outputs instead
+    const bool fused = !mlp && n > 0;
+    void* eps_t = o->eps_fine ? g->eps_t : nullptr;
+    if (!mlp)
+        CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk, fused ? g->bulk4 : nullptr); }));
     CG_CUDA(cudaEventRecord(g->ev_avg, side));
-    CG_TRY(launch_bin(g, n, p->pos_d));
+    if (fused) CG_TRY(launch_bin(g, n, p->pos_d, o->eps_bulk, g->bulk4, eps_t));
+    else CG_TRY(launch_bin(g, n, p->pos_d, o->eps_bulk));
     CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
-    CG_TRY(launch_deposit_volume(g, n, nullptr, o->eps_bulk, true));   // sorted volumes of this binning
-    CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_avg, 0));
-    CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
+    // sorted diameters of this binning
+    if (fused) CG_TRY(launch_deposit_volume(g, n, nullptr, o->eps_bulk, true, true, g->bulk4, eps_t));
+    else CG_TRY(launch_deposit_volume(g, n, nullptr, o->eps_bulk, true, true));
+    if (!fused) {
+        CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_avg, 0));
+        CG_TRY(launch_pack(g, o->eps_bulk, o->u_bulk, o->eps_fine != nullptr));
+    }
     if (o->eps_fine) {
         CG_CUDA(cudaEventRecord(g->ev_pack, g->stream));
         CG_CUDA(cudaStreamWaitEvent(side, g->ev_pack, 0));
@@ -480,6 +492,7 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
         void* eout[4] = {o->eps_fine, nullptr, nullptr, nullptr};
         CG_TRY(on_aux(g, [&] { return launch_project(g, 1, ein, eout, false); }));
     }
+    if (fused) CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_avg, 0));
     CG_CUDA(cudaEventRecord(g->ev_epsf, side));
     if (mlp)
         CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, age, o->force, o->S_bulk,

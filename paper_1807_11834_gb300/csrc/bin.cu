@@ -41,7 +41,9 @@ template <typename T>
 __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long long n, const GridDev& g,
                                              int32_t* __restrict__ key, int32_t* __restrict__ count,
                                              int32_t* __restrict__ hist, int ntiles, int bits0, T* __restrict__ vol,
-                                             unsigned long long* __restrict__ status, int* sh, Blk blk) {
+                                             unsigned long long* __restrict__ status, int* sh, Blk blk,
+                                             double* __restrict__ eps_fill = nullptr, T* __restrict__ rec_fill = nullptr,
+                                             T* __restrict__ eps_t_fill = nullptr) {
     __shared__ int s_cnt[2];
     const int R = 1 << bits0;
     for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
@@ -83,15 +85,26 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
     __syncthreads();
     for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
     if (threadIdx.x == 0) add_status(status, s_cnt[0], s_cnt[1]);
+    // the porosity of cells without particles is 1: set every cell here (and
+    // the porosity of the drag record and of its path-precision copy), the
+    // deposit overwrites the occupied ones (saves launches in the step)
+    if (eps_fill)
+        for (long long c = blk.id * blockDim.x + threadIdx.x; c < g.nbulk; c += blk.n * blockDim.x) {
+            eps_fill[c] = 1.0;
+            if (rec_fill) rec_fill[4 * c] = T(1);
+            if (eps_t_fill) eps_t_fill[c] = T(1);
+        }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
           int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
-          T* __restrict__ vol, unsigned long long* __restrict__ status) {
+          T* __restrict__ vol, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
+          T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
     extern __shared__ int sh[];
-    bin_key_body(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk());
+    bin_key_body(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill, rec_fill,
+                 eps_t_fill);
 }
 
 // Tile histogram of a digit of already-computed keys (second pass).
@@ -357,11 +370,12 @@ static cg_status set_attrs() {
 }
 
 template <typename T>
-static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, long long m0) {
+static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, long long m0, double* eps_fill,
+                            T* rec_fill, T* eps_t_fill) {
     const long long nbulk = g->gd.nbulk;
     const int b0 = g->pass_bits[0], b1 = g->pass_bits[1];
     CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
-              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status);
+              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
     const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
     if (g->npasses == 1) {
@@ -475,7 +489,8 @@ int batch_bin_occupancy(int phase, size_t smem) {
     return occ > 0 ? occ : 1;
 }
 
-cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
+cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fill, void* rec_fill,
+                     void* eps_t_fill) {
     CG_TRY(set_attrs());
     const long long nbulk = g->gd.nbulk;
     // count[] lives in cell_start; the exclusive scan turns it into starts
@@ -493,8 +508,12 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d) {
     const long long m0 = (long long)ntiles << b0;
     if (m0 > g->hist_cap || (two && ((long long)ntiles << b1) > g->hist_cap)) return CG_ERR_OUT_OF_RANGE;
 
-    if (g->fp64) CG_TRY(bin_passes<double>(g, n, (const double*)pos_d, ntiles, m0));
-    else CG_TRY(bin_passes<float>(g, n, (const float*)pos_d, ntiles, m0));
+    if (g->fp64)
+        CG_TRY(bin_passes<double>(g, n, (const double*)pos_d, ntiles, m0, eps_fill, (double*)rec_fill,
+                                  (double*)eps_t_fill));
+    else
+        CG_TRY(bin_passes<float>(g, n, (const float*)pos_d, ntiles, m0, eps_fill, (float*)rec_fill,
+                                 (float*)eps_t_fill));
     g->n_binned = n;
     g->vol_valid = true;
     return CG_OK;

@@ -198,11 +198,19 @@ struct SumsMap {
 cg_status ensure_particle_capacity(cg_grids* g, long long n);
 cg_status ensure_partials(cg_grids* g, long long n);
 
-cg_status launch_bin(cg_grids* g, long long n, const void* pos_d);
-cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums);
+// eps_fill (nullable): also set this [n_b] porosity to 1 (when n > 0), and
+// likewise the porosity of the drag record rec_fill and of eps_t_fill (T).
+cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fill = nullptr,
+                     void* rec_fill = nullptr, void* eps_t_fill = nullptr);
+// prefilled: eps already holds 1 for every cell (the binning set it);
+// rec / eps_t (nullable, sorted-diameter path only): also write the porosity
+// of occupied cells into the drag record and its T copy.
+cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
+                                bool prefilled = false, void* rec = nullptr, void* eps_t = nullptr);
 cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
 cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk);
-cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk);
+// rec (nullable): also write the mean velocity into the drag record's u part.
+cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk, void* rec = nullptr);
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
                       bool sums, double dt);
@@ -510,54 +518,127 @@ __device__ __forceinline__ void seg_rounds(long long s, long long t, const int32
     }
 }
 
-// Segmented sum of one compensated value per slot, compensated at every
-// addition (TwoSum in the lane scan too): load(i, hi, lo) gives slot i as an
-// unevaluated pair, emit(key, tot) receives each segment's pair.  Used for
-// the solid volume, where eps = 1 - phi must stay accurate as phi -> 1.
-template <typename T, typename Load, typename Emit>
-__device__ __forceinline__ void seg_rounds_cs(long long s, long long t, const int32_t* __restrict__ key_sorted,
-                                              Load load, Emit emit) {
+// Segmented sums over the slots [s, t) of one chunk, 256 slots per round.
+// Lane l walks its own 8 consecutive slots r0 + 8l .. r0 + 8l + 7 in order
+// with compensated sums: runs that start and end inside the lane are
+// emitted at once; the open first and last runs of the lanes are joined by
+// one segmented scan over the lanes (compensated merges, lower slots
+// first), and the round's last run is carried into the next round.  With
+// EXACT every addition is compensated; otherwise a lane adds its own (at
+// most 8) slots plainly and only the joins are compensated.  load(i, v)
+// fills slot i's K compensated values; emit(key, tot) receives each
+// segment's total (on one lane, once).  The summation order depends only on
+// the chunk's slots, not on the launch.
+template <typename T, int K, bool EXACT, typename Load, typename Emit>
+__device__ __forceinline__ void seg_seq(long long s, long long t, const int32_t* __restrict__ key_sorted,
+                                        Load load, Emit emit) {
+    constexpr int P = 8;
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    CSum<T> carry;
+    CSum<T> carry[K];
     int carry_key = -1;
-    for (long long r0 = s; r0 < t; r0 += 32) {
-        const long long i = r0 + lane;
-        const bool valid = i < t;
-        int kj = -1;
-        CSum<T> v;
-        if (valid) {
-            kj = __ldg(key_sorted + i);
-            load(i, v.s, v.c);
-        }
+    for (long long r0 = s; r0 < t; r0 += 32 * P) {
+        const long long b0 = r0 + (long long)P * lane;
+        int key[P];
+        CSum<T> v[P][K];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int ko = __shfl_up_sync(0xffffffffu, kj, off);
-            CSum<T> o;
-            o.s = __shfl_up_sync(0xffffffffu, v.s, off);
-            o.c = __shfl_up_sync(0xffffffffu, v.c, off);
-            if (lane >= off && ko == kj) {
-                // keep the lower slots first, as a sequential walk would
-                o.merge(v);
-                v = o;
+        for (int j = 0; j < P; ++j) {
+            key[j] = -1;
+            if (b0 + j < t) {
+                key[j] = __ldg(key_sorted + b0 + j);
+                load(b0 + j, v[j]);
             }
         }
-        int next = __shfl_down_sync(0xffffffffu, kj, 1);
-        const int nxt = (lane == 0 && r0 + 32 < t) ? __ldg(key_sorted + r0 + 32) : -1;
-        const int next31 = __shfl_sync(0xffffffffu, nxt, 0);
-        if (lane == 31) next = next31;
-        if (valid && next != kj) {
-            CSum<T> tot;
-            if (kj == carry_key) tot = carry;
-            tot.merge(v);
-            emit(kj, tot);
+        const int nk = (r0 + 32 * P < t) ? __ldg(key_sorted + r0 + 32 * P) : -1;   // first key after the round
+        // the lane's own slots: head run, complete middle runs, open tail run
+        const int head_key = key[0];
+        int cur = key[0];
+        int nruns = key[0] >= 0 ? 1 : 0;
+        CSum<T> acc[K], head[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = v[0][k];
+#pragma unroll
+        for (int j = 1; j < P; ++j) {
+            if (key[j] < 0) break;
+            if (key[j] != cur) {
+                if (nruns == 1) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) head[k] = acc[k];
+                } else {
+                    emit(cur, acc);
+                }
+                ++nruns;
+                cur = key[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc[k] = v[j][k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (EXACT) acc[k].merge(v[j][k]);
+                    else acc[k].s += v[j][k].s;
+                }
+            }
         }
-        const int k31 = __shfl_sync(0xffffffffu, kj, 31);
-        CSum<T> v31;
-        v31.s = __shfl_sync(0xffffffffu, v.s, 31);
-        v31.c = __shfl_sync(0xffffffffu, v.c, 31);
-        if (k31 != carry_key) carry = CSum<T>();
-        carry.merge(v31);
-        carry_key = k31;
+        const int tail_key = nruns ? cur : -2;
+        // lane 0 continues the run carried from the previous round
+        if (lane == 0 && nruns == 1 && head_key == carry_key)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                CSum<T> c0 = carry[k];
+                c0.merge(acc[k]);
+                acc[k] = c0;
+            }
+        // segmented inclusive scan of the tail runs over the lanes: a lane
+        // holding one run of the previous lane's tail key continues it
+        const int prev_tail = __shfl_up_sync(full, tail_key, 1);
+        bool fl = lane == 0 || nruns != 1 || head_key != prev_tail;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const bool ofl = __shfl_up_sync(full, fl, off);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                CSum<T> o;
+                o.s = __shfl_up_sync(full, acc[k].s, off);
+                o.c = __shfl_up_sync(full, acc[k].c, off);
+                if (lane >= off && !fl) {
+                    o.merge(acc[k]);
+                    acc[k] = o;
+                }
+            }
+            if (lane >= off && !fl) fl = ofl;
+        }
+        // head runs that end inside a lane take the chain before them
+        CSum<T> before[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            before[k].s = __shfl_up_sync(full, acc[k].s, 1);
+            before[k].c = __shfl_up_sync(full, acc[k].c, 1);
+        }
+        if (nruns > 1) {
+            CSum<T> tot[K];
+            const bool cont = lane == 0 ? head_key == carry_key : head_key == prev_tail;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                tot[k] = cont ? (lane == 0 ? carry[k] : before[k]) : CSum<T>();
+                tot[k].merge(head[k]);
+            }
+            emit(head_key, tot);
+        }
+        // tail runs that end at the lane's end
+        int next = __shfl_down_sync(full, head_key, 1);
+        if (lane == 31) next = nk;
+        const int last = (int)min((long long)31, (t - r0 - 1) / P);   // last lane holding slots
+        if (lane == last) next = nk;
+        if (nruns > 0 && next != tail_key) emit(tail_key, acc);
+        // carry the round's last run into the next round
+        const int lk = __shfl_sync(full, tail_key, last);
+        const bool goes_on = nk >= 0 && nk == lk;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            carry[k].s = __shfl_sync(full, acc[k].s, last);
+            carry[k].c = __shfl_sync(full, acc[k].c, last);
+        }
+        carry_key = goes_on ? lk : -1;
     }
 }
 

@@ -90,18 +90,23 @@ __device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__
                                                            const int32_t* __restrict__ key_sorted,
                                                            const int32_t* __restrict__ cs, const GridDev& g,
                                                            double* __restrict__ eps, T* __restrict__ part,
-                                                           long long pstride, int do_sums, Blk b) {
+                                                           long long pstride, int do_sums, Blk b,
+                                                           T* __restrict__ rec = nullptr, T* __restrict__ eps_t = nullptr) {
     const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = b.n * (blockDim.x >> 5);
     CSum<T> tot[1];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
         seg_chunk_range(base, n, key_sorted, cs, s, t);
-        seg_rounds_cs<T>(
-            s, t, key_sorted, [&](long long i, T& hi, T& lo) { sphere_volume_pair(__ldg(dsorted + i), hi, lo); },
-            [&](int key, const CSum<T>& a) {
-                eps[key] = 1.0 - ((double)a.s + (double)a.c) * g.invVB;
-                tot[0].merge(a);
+        seg_seq<T, 1, true>(
+            s, t, key_sorted,
+            [&](long long i, CSum<T> (&v)[1]) { sphere_volume_pair(__ldg(dsorted + i), v[0].s, v[0].c); },
+            [&](int key, const CSum<T> (&a)[1]) {
+                const double e = 1.0 - ((double)a[0].s + (double)a[0].c) * g.invVB;
+                eps[key] = e;
+                if (rec) rec[4 * (long long)key] = (T)e;   // the drag record's porosity
+                if (eps_t) eps_t[key] = (T)e;
+                tot[0].merge(a[0]);
             });
     }
     if (do_sums) block_sums<T, 1>(tot, part, pstride, b.id);
@@ -111,8 +116,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_deposit_volume_sorted(const T* __restrict__ dsorted, long long n, const int32_t* __restrict__ key_sorted,
                         const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
-                        long long pstride, int do_sums) {
-    deposit_volume_sorted_body(dsorted, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk());
+                        long long pstride, int do_sums, T* __restrict__ rec, T* __restrict__ eps_t) {
+    deposit_volume_sorted_body(dsorted, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk(), rec, eps_t);
 }
 
 // Reaction from the forces the drag wrote in sorted order (T4 per slot);
@@ -369,9 +374,10 @@ static unsigned seg_blocks(cg_grids* g, long long n) {
     return (unsigned)std::max(1LL, std::min((chunks + 7) / 8, (long long)g->num_sms * 8));
 }
 
-cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums) {
+cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
+                                bool prefilled, void* rec, void* eps_t) {
     const unsigned fblk = (unsigned)std::min((g->gd.nbulk + 255) / 256, (long long)g->num_sms * 8);
-    CG_LAUNCH(g, "deposit_volume", k_fill<double>, fblk, 256, 0, eps, g->gd.nbulk, 1.0);
+    if (!prefilled || n == 0) CG_LAUNCH(g, "deposit_volume", k_fill<double>, fblk, 256, 0, eps, g->gd.nbulk, 1.0);
     const unsigned nblk = seg_blocks(g, n);
     void* part = part_ptr(g, PS_VOL);
     g->part_blocks[PS_VOL] = sums ? (long long)nblk : -1;
@@ -387,11 +393,11 @@ cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, dou
         if (g->fp64)
             CG_LAUNCH(g, "deposit_volume", k_deposit_volume_sorted<double>, nblk, 256, 0,
                       (const double*)g->vol_sorted, n, g->key_sorted, g->cell_start, g->gd, eps, (double*)part,
-                      (long long)nblk, (int)sums);
+                      (long long)nblk, (int)sums, (double*)rec, (double*)eps_t);
         else
             CG_LAUNCH(g, "deposit_volume", k_deposit_volume_sorted<float>, nblk, 256, 0,
                       (const float*)g->vol_sorted, n, g->key_sorted, g->cell_start, g->gd, eps, (float*)part,
-                      (long long)nblk, (int)sums);
+                      (long long)nblk, (int)sums, (float*)rec, (float*)eps_t);
         return CG_OK;
     }
     if (g->fp64)

@@ -69,32 +69,117 @@ __device__ __forceinline__ void bulk_ijk(long long cb, const GridDev& g, int& I,
 }
 
 // ----------------------------------------------------------------------
-// (a2) mean and variance of the r^3 fine cells of a bulk cell.
+// (a2) mean and variance of the r^3 fine cells of a bulk cell, r = 2, 4, 8.
+// The values are first shifted by the cell's first value (the subtraction
+// is exact for values within a factor two of it), so that nothing below
+// carries the mean's magnitude.  Pairwise over the rows of r values: each
+// row gives its sum S and squared deviations M = sum (d - S/r)^2, and two
+// sets of k values each merge as (S_a + S_b, M_a + M_b + (S_b - S_a)^2 / (2k))
+// (the pairwise update of Chan, Golub & LeVeque), in a fixed binary tree
+// over the r^2 rows; every division is by a power of two.
+// ----------------------------------------------------------------------
+template <typename T, int RC>
+__device__ __forceinline__ void average_cell_pairwise(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
+                                                      T* __restrict__ var, long long cb, T* __restrict__ rec) {
+    constexpr int NR = RC * RC;                                  // rows of a bulk cell
+    constexpr int LV = RC == 2 ? 2 : RC == 4 ? 4 : 6;            // log2(NR)
+    int I, J, K;
+    bulk_ijk(cb, g, I, J, K);
+    const long long nx = g.nf[0], nxy = (long long)g.nf[0] * g.nf[1];
+    const long long f0 = (long long)I * RC + nx * ((long long)J * RC) + nxy * ((long long)K * RC);
+    T stS[3][LV + 1], stM[3][LV + 1], ref[3];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const long long f = f0 + nx * (r % RC) + nxy * (r / RC);
+        T v[3][RC];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Row<T, RC>::load(u + c * g.nfine + f, v[c]);
+        if (r == 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ref[c] = v[c][0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int i = 0; i < RC; ++i) v[c][i] -= ref[c];
+            // the row: pairwise sum, then squared deviations from its mean
+            T w[RC];
+#pragma unroll
+            for (int i = 0; i < RC; ++i) w[i] = v[c][i];
+#pragma unroll
+            for (int h = RC / 2; h >= 1; h /= 2)
+#pragma unroll
+                for (int i = 0; i < h; ++i) w[i] = w[2 * i] + w[2 * i + 1];
+            T S = w[0];
+            const T mean = S * (T(1) / T(RC));
+            T M = T(0);
+#pragma unroll
+            for (int i = 0; i < RC; ++i) {
+                const T d = v[c][i] - mean;
+                M = fma(d, d, M);
+            }
+            // merge up the tree while the row index has trailing ones
+            T k = T(RC);
+#pragma unroll
+            for (int L = 0; L < LV; ++L) {
+                if (((r >> L) & 1) == 0) {
+                    stS[c][L] = S;
+                    stM[c][L] = M;
+                    break;
+                }
+                const T d = S - stS[c][L];
+                M = stM[c][L] + M + d * d * (T(0.5) / k);
+                S = stS[c][L] + S;
+                k *= T(2);
+                if (L == LV - 1) {
+                    stS[c][LV] = S;
+                    stM[c][LV] = M;
+                }
+            }
+        }
+    }
+    constexpr T invn = T(1) / T(RC * RC * RC);
+    T m2 = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T mean = ref[c] + stS[c][LV] * invn;
+        ub[c * g.nbulk + cb] = mean;
+        if (rec) rec[4 * cb + 1 + c] = mean;
+        m2 += stM[c][LV];
+    }
+    if (var) var[cb] = m2 * invn;
+}
+
+// ----------------------------------------------------------------------
+// (a2) mean and variance of the r^3 fine cells of a bulk cell, any r.
 // The variance uses a shift by the first fine value of the cell:
 // var = (Q - sum_c D_c^2 / n) / n with Q = sum (u - ref)^2 and
 // D_c = sum_f u_c - n ref_c, both compensated, which equals the two-pass
 // population variance without a second read of the fine data.
 // ----------------------------------------------------------------------
+// rec (nullable): the drag's packed record (eps, u_x, u_y, u_z) per cell;
+// the mean velocity is also written to its u part.
 template <typename T, int RC>
 __device__ __forceinline__ void average_cell(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
-                                             T* __restrict__ var, long long cb);
+                                             T* __restrict__ var, long long cb, T* __restrict__ rec);
 
 template <typename T, int RC>
 __device__ __forceinline__ void average_body(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
-                                             T* __restrict__ var, Blk b) {
-    for (long long cb = b.id * blockDim.x + threadIdx.x; cb < g.nbulk; cb += b.n * blockDim.x)
-        average_cell<T, RC>(u, g, ub, var, cb);
+                                             T* __restrict__ var, Blk b, T* __restrict__ rec = nullptr) {
+    for (long long cb = b.id * blockDim.x + threadIdx.x; cb < g.nbulk; cb += b.n * blockDim.x) {
+        if constexpr (RC > 0) average_cell_pairwise<T, RC>(u, g, ub, var, cb, rec);
+        else average_cell<T, RC>(u, g, ub, var, cb, rec);
+    }
 }
 
 template <typename T, int RC>
 __global__ void __launch_bounds__(256)
-k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var) {
-    average_body<T, RC>(u, g, ub, var, launch_blk());
+k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var, T* __restrict__ rec) {
+    average_body<T, RC>(u, g, ub, var, launch_blk(), rec);
 }
 
 template <typename T, int RC>
 __device__ __forceinline__ void average_cell(const T* __restrict__ u, const GridDev& g, T* __restrict__ ub,
-                                             T* __restrict__ var, long long cb) {
+                                             T* __restrict__ var, long long cb, T* __restrict__ rec) {
     int I, J, K;
     bulk_ijk(cb, g, I, J, K);
     const int r = RC ? RC : g.r;
@@ -139,9 +224,11 @@ __device__ __forceinline__ void average_cell(const T* __restrict__ u, const Grid
     const T n = (T)r * (T)r * (T)r;
     const T invn = (T)1 / n;
     T corr = 0;
+    T mean[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        ub[c * g.nbulk + cb] = s[c].get() * invn;
+        mean[c] = s[c].get() * invn;
+        ub[c * g.nbulk + cb] = mean[c];
         if (var) {
             // D_c = (s_hi - n ref) + s_lo, the n ref product split exactly
             T p = n * ref[c];
@@ -158,6 +245,9 @@ __device__ __forceinline__ void average_cell(const T* __restrict__ u, const Grid
         T v = (a + (e + q.c)) * invn;
         var[cb] = v > T(0) ? v : T(0);
     }
+    if (rec)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rec[4 * cb + 1 + c] = mean[c];
 }
 
 // ----------------------------------------------------------------------
@@ -402,14 +492,14 @@ int batch_fine_occupancy(int phase) {
 
 static inline unsigned blocks_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
-cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk) {
+cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk, void* rec) {
     // grid-stride over two blocks per SM: each thread keeps r^2 x 3 row loads
     // in flight, enough to stream at HBM speed while leaving most warp slots
     // to the particle kernels running beside it
     const unsigned nblk = (unsigned)std::min((long long)blocks_of(g->gd.nbulk, 256), (long long)g->num_sms * 2);
 #define CG_AVG(T, RC)                                                                                   \
     CG_LAUNCH(g, "average", (k_average<T, RC>), nblk, 256, 0, (const T*)u_fine, g->gd, (T*)u_bulk, \
-              (T*)var_bulk)
+              (T*)var_bulk, (T*)rec)
     if (g->fp64) {
         switch (g->gd.r) {
             case 2: CG_AVG(double, 2); break;
