@@ -152,6 +152,51 @@ __device__ __forceinline__ float gelu(float x) {
     const float q = 0.5f * t * p * __expf(-z * z);
     return x >= 0.f ? x - x * q : x * q;
 }
+// Two activations at once: the same formula with the FP32 arithmetic in
+// packed f32x2 instructions (two lanes per instruction) and the reciprocal
+// and the exponential on the special-function unit (rcp / ex2 approx).
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void gelu2(float a, float b, float& ga, float& gb) {
+    const unsigned long long z = mul2(pk2(fabsf(a), fabsf(b)), pk2(0.70710678118654752f, 0.70710678118654752f));
+    const unsigned long long den = fma2(pk2(0.3275911f, 0.3275911f), z, pk2(1.0f, 1.0f));
+    const unsigned long long t = pk2(rcp_approx(lo2(den)), rcp_approx(hi2(den)));
+    unsigned long long p = fma2(t, pk2(1.061405429f, 1.061405429f), pk2(-1.453152027f, -1.453152027f));
+    p = fma2(t, p, pk2(1.421413741f, 1.421413741f));
+    p = fma2(t, p, pk2(-0.284496736f, -0.284496736f));
+    p = fma2(t, p, pk2(0.254829592f, 0.254829592f));
+    // exp(-z^2) = 2^(-z^2 log2 e)
+    const unsigned long long zz = mul2(mul2(z, z), pk2(-1.4426950408889634f, -1.4426950408889634f));
+    const unsigned long long e = pk2(ex2_approx(lo2(zz)), ex2_approx(hi2(zz)));
+    const unsigned long long q = mul2(mul2(mul2(t, pk2(0.5f, 0.5f)), p), e);
+    const unsigned long long xq = mul2(pk2(a, b), q);
+    ga = a >= 0.f ? a - lo2(xq) : lo2(xq);
+    gb = b >= 0.f ? b - hi2(xq) : hi2(xq);
+}
+
 // Its derivative Phi(x) + x phi(x) (training only), from CUDA's erff / expf.
 __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
@@ -310,7 +355,7 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
         tmem_ld16(lane_addr(s, 16 * q), z);
         float a[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) a[i] = gelu(z[i] + s.b1[16 * q + i]);
+        for (int i = 0; i < 16; i += 2) gelu2(z[i] + s.b1[16 * q + i], z[i + 1] + s.b1[16 * q + i + 1], a[i], a[i + 1]);
         st_row8(s.A1, row, 16 * q, H, a);
         st_row8(s.A1, row, 16 * q + 8, H, a + 8);
     }
@@ -321,7 +366,12 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
         float z[16];
         tmem_ld16(lane_addr(s, z2col + 16 * q), z);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc = fmaf(gelu(z[i] + s.b2[16 * q + i]), s.w3[16 * q + i], acc);
+        for (int i = 0; i < 16; i += 2) {
+            float g0, g1;
+            gelu2(z[i] + s.b2[16 * q + i], z[i + 1] + s.b2[16 * q + i + 1], g0, g1);
+            acc = fmaf(g0, s.w3[16 * q + i], acc);
+            acc = fmaf(g1, s.w3[16 * q + i + 1], acc);
+        }
     }
     c = acc;
     return true;
