@@ -38,7 +38,11 @@ UNIT = "particle-steps/s"
 # DRAM traffic per launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
 # source file is byte-identical to the one profiled (sha256 prefix).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # packed bed, one eager step: k_bin_scatter first pass 21.37 MB, final
+    # pass 90.35 / 86.21 MB (two captures); per launch, the mean of the passes
+    "bin_scatter": {"file": "bin.cu", "sha": "91edeebe374095c2", "bytes": 54.8e6},
+}
 
 
 def parse():
@@ -401,8 +405,9 @@ def run_reference(args):
 
 def run_learned(args):
     """Learned closure against the plain path on one workload family:
-    train on seeds 0 and 1 (stale records refreshed every 2, 5, 10 steps,
-    fluid relaxed by the coupling source), judge the drag error on seed 2
+    train on seeds 0 and 1 (56-step runs, stale records refreshed every 2,
+    5, 10, 20 and 50 steps, fluid relaxed by the coupling source), judge the
+    drag error on seed 2
     at several refresh intervals K, then time the plain step and the
     learned stale step (CUDA graphs) and report the amortised throughput of
     one refresh plus K - 1 learned steps at the largest K whose learned
@@ -421,7 +426,8 @@ def run_learned(args):
     make = getattr(synth, args.workload)
     dt = 1e-4                      # the clustered bed's step; the packed bed is advanced with the same
     t0 = time.time()
-    F, T = closure.generate_pairs(make, seeds=(0, 1), refreshes=(2, 5, 10), steps=12,
+    # runs long enough to cover every refresh interval judged below
+    F, T = closure.generate_pairs(make, seeds=(0, 1), refreshes=(2, 5, 10, 20, 50), steps=56,
                                   n_pairs=2_000_000, dt=dt)
     t_gen = time.time() - t0
     m, hist = closure.train(F, T, epochs=20, batch=65536, lr=2e-3)
@@ -434,14 +440,21 @@ def run_learned(args):
     ok = [K for K in Ks if evals[K]["err_learned"] <= 0.01]
     K_star = max(ok) if ok else None
 
-    g = cg.Grids(w.desc)
+    # the timed state: the held-out run advanced past a refresh, so that the
+    # stale record is `age` steps old and the fluid has evolved as in training
+    age = 2
+    K_t = K_star or 5
+    traj = closure.Trajectory.start(w, K_t, dt=dt)
+    for _ in range(K_t + age):
+        traj.advance()
+    g = traj.grids
     n = w.n
-    pos = torch.from_numpy(w.pos_d).cuda()
-    vel = torch.from_numpy(w.vel).cuda()
-    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).cuda()
-    out = g.alloc_outputs(n, var=True, eps_fine=True)
-    g.cg_step(pos, vel, uf, out)            # the refresh that makes the stale record
+    pos, vel, uf, out = traj.pos, traj.vel, traj.u_fine, traj.out
+    out["u_bulk"].copy_(traj.u_stale)
+    out["var_bulk"].copy_(traj.var_stale)
+    stale_u, stale_var = traj.u_stale.clone(), traj.var_stale.clone()
     torch.cuda.synchronize()
+    g.cg_sync_status()
 
     def graph_of(fn):
         cs = torch.cuda.Stream()
@@ -457,9 +470,13 @@ def run_learned(args):
         torch.cuda.synchronize()
         return gr
 
+    # the plain step overwrites out's bulk record: the learned step is timed
+    # on its own output set holding the stale record
+    out_l = {k: (v.clone() if v is not None else None) for k, v in out.items()}
+    out_l["u_bulk"].copy_(stale_u)
+    out_l["var_bulk"].copy_(stale_var)
     plain = graph_of(lambda: g.cg_step(pos, vel, uf, out))
-    age = 3
-    learned = graph_of(lambda: g.cg_step_learned(pos, vel, uf, out, m, age))
+    learned = graph_of(lambda: g.cg_step_learned(pos, vel, uf, out_l, m, age))
 
     def time_graph(gr, steps):
         for _ in range(max(3, args.warmup)):
@@ -479,6 +496,7 @@ def run_learned(args):
     time.sleep(0.3)
     ta = time.time()
     ms_plain = time_graph(plain, steps)
+    g.cg_sync_status()
     ms_learned = time_graph(learned, steps)
     tb = time.time()
     time.sleep(0.2)
@@ -486,12 +504,13 @@ def run_learned(args):
     rc, flags, counts = g.cg_sync_status()
     if rc != 0:
         raise RuntimeError(f"timed status {rc}")
+    fallback_timed = counts[4] / (n * (steps + max(3, args.warmup)))
 
     # per-kernel times of the learned step (serialised events)
     g.cg_profile_reset()
     g.cg_profile_enable(True)
     for _ in range(20):
-        g.cg_step_learned(pos, vel, uf, out, m, age)
+        g.cg_step_learned(pos, vel, uf, out_l, m, age)
     prof = g.cg_profile_read()
     g.cg_profile_enable(False)
     kern = {k: {"ms_per_launch": round(v[1] / v[0], 5)} for k, v in prof.items() if v[0]}
@@ -523,14 +542,15 @@ def run_learned(args):
             "refresh_K": K_star,
             "plain": {"ms_per_step": round(ms_plain, 5), "value": n / (ms_plain * 1e-3)},
             "learned_step": {"ms_per_step": round(ms_learned, 5), "value": n / (ms_learned * 1e-3),
-                             "age": age},
+                             "age": age, "fallback_share": fallback_timed,
+                             "state": f"held-out run after {K_t + age} steps, record refreshed {age} steps before"},
             "drag_error": {str(K): evals[K] for K in Ks},
             "loss_standardised": [round(h, 5) for h in (hist[0], hist[-1])],
             "kernels_learned_step": kern, "roofline_closure": roof,
             "clocks": sampler.summary(ta, tb)}
     print(json.dumps(line))
     m.close()
-    g.close()
+    traj.close()
 
 
 def run_batch(args):
