@@ -244,6 +244,16 @@ cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine
 cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine,
                        const cg_step_out* out, double dt);
 
+/* cg_step_host without the final wait: the call enqueues the copies in, the
+ * step and the copies out, and returns.  Two staging sets are used in turn,
+ * so the input copies of one call overlap the output copies of the
+ * previous one.  Until cg_step_host_wait returns, the host inputs of a call
+ * must stay unchanged and its host outputs are not yet valid. */
+cg_status cg_step_host_async(cg_grids* g, const cg_particles* p, const void* u_fine,
+                             const cg_step_out* out, double dt);
+/* Wait for every host-buffer step enqueued on the handle. */
+cg_status cg_step_host_wait(cg_grids* g);
+
 /* ------------------------------------------------------------------------
  * Learned drag closure (not in the paper; the paper's drag law is the plain
  * correlation of Eq. DragLaw).  A multilayer perceptron c = f(features),

@@ -93,6 +93,9 @@ _SIGS = {
     "cg_project_bulk_to_fine": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "cg_step": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
     "cg_step_host": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
+    "cg_step_host_async": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut),
+                                     C.c_double]),
+    "cg_step_host_wait": (C.c_int, [C.c_void_p]),
     "cg_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_int64)]),
     "cg_launch_count": (C.c_int64, [C.c_void_p]),
     "cg_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -345,6 +348,21 @@ class Grids:
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step_host(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step_host")
+
+    def cg_step_host_async(self, pos_d, vel, u_fine, out, dt=0.0):
+        """cg_step_host without the final wait (call cg_step_host_wait before
+        reading the outputs or changing the inputs)."""
+        n = pos_d.shape[0]
+        for t in [pos_d, vel, u_fine] + [v for v in out.values() if v is not None]:
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("cg_step_host_async needs contiguous host tensors")
+        p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
+        so = self._out_struct(out)
+        _check(lib().cg_step_host_async(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)),
+               "cg_step_host_async")
+
+    def cg_step_host_wait(self):
+        _check(lib().cg_step_host_wait(self.h), "cg_step_host_wait")
 
     def cg_sync_status(self):
         """(return code, flags, [outside, nonfinite, clamped, timeouts, fallbacks])."""

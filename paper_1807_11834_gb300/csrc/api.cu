@@ -211,13 +211,24 @@ static void free_all(cg_grids* g) {
     dfree(g->partials);
     dfree(g->sums_scratch);
     dfree(g->status);
-    DevBuf* st[] = {&g->st_pos, &g->st_vel, &g->st_ufine, &g->st_eps, &g->st_ub, &g->st_var, &g->st_Sb,
-                    &g->st_F,   &g->st_Sf,  &g->st_epsf,  &g->st_sums, &g->st_cell, &g->st_perm, &g->st_cs,
-                    &g->fresh4};
-    for (DevBuf* b : st) {
-        dfree(b->p);
-        b->bytes = 0;
+    for (HostStage& S : g->hs) {
+        DevBuf* st[] = {&S.pos, &S.vel, &S.ufine, &S.eps, &S.ub, &S.var, &S.Sb,
+                        &S.F,   &S.Sf,  &S.epsf,  &S.sums, &S.cell, &S.perm, &S.cs};
+        for (DevBuf* b : st) {
+            dfree(b->p);
+            b->bytes = 0;
+        }
+        cudaEvent_t evs[] = {S.in_done, S.comp_done, S.out_done};
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+        S.in_done = S.comp_done = S.out_done = nullptr;
+        S.used = false;
     }
+    dfree(g->fresh4.p);
+    g->fresh4.bytes = 0;
+    if (g->h2d) cudaStreamDestroy(g->h2d);
+    if (g->d2h) cudaStreamDestroy(g->d2h);
+    g->h2d = g->d2h = nullptr;
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     g->ev_pool.clear();
     cudaEvent_t evs[] = {g->ev_fork, g->ev_avg, g->ev_pack, g->ev_epsf};
@@ -537,48 +548,75 @@ cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine
     return step_impl(g, p, u_fine, out, dt, age == 0 ? nullptr : mlp, age);
 }
 
-cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
-                       double dt) {
-    CG_TRY(check_handle(g));
-    CG_TRY(check_step_args(p, u_fine, out, dt, false));
+// Host-buffer steps.  Each call takes the next of two staging sets: its
+// inputs go in on the h2d stream (after the set's previous outputs have
+// left), the step runs on the handle's stream, and the outputs go out on the
+// d2h stream; so the copies of consecutive steps overlap each other and the
+// compute (one direction each way at a time).
+static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
+                                   double dt) {
     const long long n = p->n;
     const size_t ts = g->tsize, nb = (size_t)g->gd.nbulk, nf = (size_t)g->gd.nfine;
     const size_t pbytes = 4 * ts * (size_t)std::max(1LL, n);
-    CG_TRY(ensure_buf(g->st_pos, pbytes));
-    CG_TRY(ensure_buf(g->st_vel, pbytes));
-    CG_TRY(ensure_buf(g->st_ufine, 3 * ts * nf));
-    CG_TRY(ensure_buf(g->st_eps, sizeof(double) * nb));
-    CG_TRY(ensure_buf(g->st_ub, 3 * ts * nb));
-    CG_TRY(ensure_buf(g->st_Sb, 3 * ts * nb));
-    CG_TRY(ensure_buf(g->st_F, 3 * ts * (size_t)std::max(1LL, n)));
-    CG_TRY(ensure_buf(g->st_Sf, 3 * ts * nf));
-    if (out->var_bulk) CG_TRY(ensure_buf(g->st_var, ts * nb));
-    if (out->eps_fine) CG_TRY(ensure_buf(g->st_epsf, ts * nf));
-    if (out->sums) CG_TRY(ensure_buf(g->st_sums, sizeof(double) * CG_NSUMS));
-    if (out->cell) CG_TRY(ensure_buf(g->st_cell, sizeof(int32_t) * (size_t)std::max(1LL, n)));
-    if (out->perm) CG_TRY(ensure_buf(g->st_perm, sizeof(int32_t) * (size_t)std::max(1LL, n)));
-    if (out->cell_start) CG_TRY(ensure_buf(g->st_cs, sizeof(int32_t) * (nb + 1)));
-
-    cudaStream_t s = g->stream;
-    if (n > 0) {
-        CG_CUDA(cudaMemcpyAsync(g->st_pos.p, p->pos_d, 4 * ts * n, cudaMemcpyHostToDevice, s));
-        CG_CUDA(cudaMemcpyAsync(g->st_vel.p, p->vel, 4 * ts * n, cudaMemcpyHostToDevice, s));
+    HostStage& S = g->hs[g->hs_next];
+    if (!g->h2d) {
+        CG_CUDA(cudaStreamCreateWithFlags(&g->h2d, cudaStreamNonBlocking));
+        CG_CUDA(cudaStreamCreateWithFlags(&g->d2h, cudaStreamNonBlocking));
     }
-    CG_CUDA(cudaMemcpyAsync(g->st_ufine.p, u_fine, 3 * ts * nf, cudaMemcpyHostToDevice, s));
-    cg_particles dp = {n, g->st_pos.p, g->st_vel.p};
+    if (!S.in_done) {
+        CG_CUDA(cudaEventCreateWithFlags(&S.in_done, cudaEventDisableTiming));
+        CG_CUDA(cudaEventCreateWithFlags(&S.comp_done, cudaEventDisableTiming));
+        CG_CUDA(cudaEventCreateWithFlags(&S.out_done, cudaEventDisableTiming));
+    }
+    // the set's buffers may only be regrown once nothing uses them
+    if (S.used) CG_CUDA(cudaEventSynchronize(S.out_done));
+    CG_TRY(ensure_buf(S.pos, pbytes));
+    CG_TRY(ensure_buf(S.vel, pbytes));
+    CG_TRY(ensure_buf(S.ufine, 3 * ts * nf));
+    CG_TRY(ensure_buf(S.eps, sizeof(double) * nb));
+    CG_TRY(ensure_buf(S.ub, 3 * ts * nb));
+    CG_TRY(ensure_buf(S.Sb, 3 * ts * nb));
+    CG_TRY(ensure_buf(S.F, 3 * ts * (size_t)std::max(1LL, n)));
+    CG_TRY(ensure_buf(S.Sf, 3 * ts * nf));
+    if (out->var_bulk) CG_TRY(ensure_buf(S.var, ts * nb));
+    if (out->eps_fine) CG_TRY(ensure_buf(S.epsf, ts * nf));
+    if (out->sums) CG_TRY(ensure_buf(S.sums, sizeof(double) * CG_NSUMS));
+    if (out->cell) CG_TRY(ensure_buf(S.cell, sizeof(int32_t) * (size_t)std::max(1LL, n)));
+    if (out->perm) CG_TRY(ensure_buf(S.perm, sizeof(int32_t) * (size_t)std::max(1LL, n)));
+    if (out->cell_start) CG_TRY(ensure_buf(S.cs, sizeof(int32_t) * (nb + 1)));
+    g->hs_next ^= 1;
+
+    // inputs in
+    if (S.used) CG_CUDA(cudaStreamWaitEvent(g->h2d, S.out_done, 0));
+    if (n > 0) {
+        CG_CUDA(cudaMemcpyAsync(S.pos.p, p->pos_d, 4 * ts * n, cudaMemcpyHostToDevice, g->h2d));
+        CG_CUDA(cudaMemcpyAsync(S.vel.p, p->vel, 4 * ts * n, cudaMemcpyHostToDevice, g->h2d));
+    }
+    CG_CUDA(cudaMemcpyAsync(S.ufine.p, u_fine, 3 * ts * nf, cudaMemcpyHostToDevice, g->h2d));
+    CG_CUDA(cudaEventRecord(S.in_done, g->h2d));
+    S.used = true;
+
+    // the step
+    CG_CUDA(cudaStreamWaitEvent(g->stream, S.in_done, 0));
+    cg_particles dp = {n, S.pos.p, S.vel.p};
     cg_step_out d;
-    d.eps_bulk = (double*)g->st_eps.p;
-    d.u_bulk = g->st_ub.p;
-    d.var_bulk = out->var_bulk ? g->st_var.p : nullptr;
-    d.S_bulk = g->st_Sb.p;
-    d.force = g->st_F.p;
-    d.S_fine = g->st_Sf.p;
-    d.eps_fine = out->eps_fine ? g->st_epsf.p : nullptr;
-    d.sums = out->sums ? (double*)g->st_sums.p : nullptr;
-    d.cell = out->cell ? (int32_t*)g->st_cell.p : nullptr;
-    d.perm = out->perm ? (int32_t*)g->st_perm.p : nullptr;
-    d.cell_start = out->cell_start ? (int32_t*)g->st_cs.p : nullptr;
-    CG_TRY(step_impl(g, &dp, g->st_ufine.p, &d, dt));
+    d.eps_bulk = (double*)S.eps.p;
+    d.u_bulk = S.ub.p;
+    d.var_bulk = out->var_bulk ? S.var.p : nullptr;
+    d.S_bulk = S.Sb.p;
+    d.force = S.F.p;
+    d.S_fine = S.Sf.p;
+    d.eps_fine = out->eps_fine ? S.epsf.p : nullptr;
+    d.sums = out->sums ? (double*)S.sums.p : nullptr;
+    d.cell = out->cell ? (int32_t*)S.cell.p : nullptr;
+    d.perm = out->perm ? (int32_t*)S.perm.p : nullptr;
+    d.cell_start = out->cell_start ? (int32_t*)S.cs.p : nullptr;
+    CG_TRY(step_impl(g, &dp, S.ufine.p, &d, dt));
+    CG_CUDA(cudaEventRecord(S.comp_done, g->stream));
+
+    // outputs out
+    cudaStream_t s = g->d2h;
+    CG_CUDA(cudaStreamWaitEvent(s, S.comp_done, 0));
     auto d2h = [&](void* dst, const void* src, size_t bytes) -> cg_status {
         if (dst && bytes) CG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
         return CG_OK;
@@ -595,11 +633,37 @@ cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, c
     CG_TRY(d2h(out->perm, d.perm, sizeof(int32_t) * n));
     CG_TRY(d2h(out->cell_start, d.cell_start, sizeof(int32_t) * (nb + 1)));
     if (dt > 0.0 && n > 0) {
-        CG_TRY(d2h(p->pos_d, g->st_pos.p, 4 * ts * n));
-        CG_TRY(d2h(p->vel, g->st_vel.p, 4 * ts * n));
+        CG_TRY(d2h(p->pos_d, S.pos.p, 4 * ts * n));
+        CG_TRY(d2h(p->vel, S.vel.p, 4 * ts * n));
     }
-    CG_CUDA(cudaStreamSynchronize(s));
+    CG_CUDA(cudaEventRecord(S.out_done, s));
     return CG_OK;
+}
+
+static cg_status step_host_wait(cg_grids* g) {
+    if (g->d2h && cudaStreamSynchronize(g->d2h) != cudaSuccess) return CG_ERR_CUDA;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return CG_ERR_CUDA;
+    return CG_OK;
+}
+
+cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
+                       double dt) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, false));
+    CG_TRY(step_host_enqueue(g, p, u_fine, out, dt));
+    return step_host_wait(g);
+}
+
+cg_status cg_step_host_async(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
+                             double dt) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, false));
+    return step_host_enqueue(g, p, u_fine, out, dt);
+}
+
+cg_status cg_step_host_wait(cg_grids* g) {
+    CG_TRY(check_handle(g));
+    return step_host_wait(g);
 }
 
 cg_status cg_sync_status(cg_grids* g, uint32_t* flags, int64_t* counts) {

@@ -78,6 +78,14 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Device staging of one host-buffer step: inputs, outputs, and the events
+// that order its copies and compute against the next use of the same set.
+struct HostStage {
+    DevBuf pos, vel, ufine, eps, ub, var, Sb, F, Sf, epsf, sums, cell, perm, cs;
+    cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
+    bool used = false;
+};
+
 }  // namespace cg
 
 struct cg_grids {
@@ -120,9 +128,11 @@ struct cg_grids {
     double* sums_scratch = nullptr;   // [CG_NSUMS] when the caller gives none
     unsigned long long* status = nullptr;   // [kNumSlots]
 
-    // host-buffer entry: device staging
-    cg::DevBuf st_pos, st_vel, st_ufine, st_eps, st_ub, st_var, st_Sb, st_F, st_Sf, st_epsf,
-        st_sums, st_cell, st_perm, st_cs;
+    // host-buffer entries: two staging sets used in turn, and the copy
+    // streams (inputs in, outputs out) that overlap consecutive steps
+    cg::HostStage hs[2];
+    int hs_next = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
     cg::DevBuf fresh4;   // [nbulk] T4: (phi, u) of the fresh field of cg_mlp_features
 
     // second stream of the step: fine-grid work that does not depend on the
