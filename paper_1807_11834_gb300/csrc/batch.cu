@@ -102,7 +102,7 @@ cg_status plan(cg_batch* b) {
     free_owned(b);
     b->hi.assign(ni, BInst());
     std::vector<long long> blocks((size_t)BP_COUNT * ni, 0);
-    size_t smem_key = 0, smem_s0 = 0, smem_s1 = 0;
+    size_t smem_key = 0, smem_s0 = 0, smem_s1 = 0, smem_hist1 = 0;
     for (int i = 0; i < ni; ++i) {
         cg_grids* g = b->h[i];
         const cg_batch_item& it = b->items[i];
@@ -199,8 +199,9 @@ cg_status plan(cg_batch* b) {
         CG_TRY(dev_alloc(b, (void**)&I.part, sizeof(float) * 2 * pairs));
         I.smap = sums_map(I.part_off, I.part_blocks);
         smem_key = std::max(smem_key, sizeof(int) << I.b0);
-        smem_s0 = std::max(smem_s0, (size_t)kSortWarps * sizeof(int) << I.b0);
-        if (I.npasses == 2) smem_s1 = std::max(smem_s1, (size_t)kSortWarps * sizeof(int) << I.b1);
+        smem_s0 = std::max(smem_s0, scatter_smem_bytes(I.b0, sizeof(float)));
+        if (I.npasses == 2) smem_s1 = std::max(smem_s1, scatter_smem_bytes(I.b1, sizeof(float)));
+        if (I.npasses == 2) smem_hist1 = std::max(smem_hist1, sizeof(int) << I.b1);
     }
     // prefixes and persistent grids
     b->start.assign((size_t)BP_COUNT * (ni + 1), 0);
@@ -214,7 +215,7 @@ cg_status plan(cg_batch* b) {
         b->total[ph] = acc;
     }
     b->smem[BP_KEY] = smem_key;
-    b->smem[BP_HIST1] = smem_s1 / kSortWarps;
+    b->smem[BP_HIST1] = smem_hist1;
     b->smem[BP_SCAT0] = smem_s0;
     b->smem[BP_SCAT1] = smem_s1;
     for (int ph = 0; ph < BP_COUNT; ++ph) {

@@ -131,97 +131,7 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
     bin_hist_body(keys, n, ntiles, shift, bits, hist, sh, launch_blk());
 }
 
-// Stable scatter of one digit pass.  offs = exclusive scan of the tile
-// histograms, digit-major ([digit][tile]).
-template <bool FIRST, bool FINAL, typename T>
-__device__ __forceinline__ void bin_scatter_body(const int32_t* __restrict__ keys_in,
-                                                 const int32_t* __restrict__ vals_in, long long n, int ntiles,
-                                                 int shift, int bits, const int32_t* __restrict__ offs,
-                                                 int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
-                                                 int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
-                                                 int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
-                                                 T* __restrict__ vol_sorted, int* cnt /* [kSortWarps][R] */,
-                                                 Blk blk) {
-    const int R = 1 << bits;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    int* wc = cnt + warp * R;
-    const unsigned lt = lanemask_lt();
-    const long long base = blk.id * kSortTile + (long long)warp * (kSortTile / kSortWarps);
-    int kv[kSortItems], vv[kSortItems], rk[kSortItems];
-    T vol_k[kSortItems];
-    // all loads of the slice first, so they are in flight together
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        long long p = base + k * 32 + lane;
-        bool valid = p < n;
-        kv[k] = valid ? __ldg(keys_in + p) : 0;
-        vv[k] = valid ? (FIRST ? (int)p : __ldg(vals_in + p)) : 0;
-    }
-    if (FINAL)
-#pragma unroll
-        for (int k = 0; k < kSortItems; ++k)
-            if (base + k * 32 + lane < n) vol_k[k] = __ldg(vol + vv[k]);
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        long long p = base + k * 32 + lane;
-        bool valid = p < n;
-        int kk = kv[k];
-        int d = valid ? ((kk >> shift) & (R - 1)) : -1;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int before = __popc(peers & lt);
-        int c0 = valid ? wc[d] : 0;
-        __syncwarp();
-        if (valid && before == 0) wc[d] = c0 + __popc(peers);
-        __syncwarp();
-        rk[k] = c0 + before;
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < R; d += blockDim.x) {
-        int run = __ldg(offs + (long long)d * ntiles + blk.id);
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            int t = cnt[w * R + d];
-            cnt[w * R + d] = run;
-            run += t;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        long long p = base + k * 32 + lane;
-        if (p < n) {
-            int d = (kv[k] >> shift) & (R - 1);
-            int dst = wc[d] + rk[k];
-            if (FINAL) {
-                perm[dst] = vv[k];
-                key_sorted[dst] = kv[k];
-                inv_perm[vv[k]] = dst;
-                vol_sorted[dst] = vol_k[k];
-            } else {
-                keys_out[dst] = kv[k];
-                vals_out[dst] = vv[k];
-            }
-        }
-    }
-}
-
-template <bool FIRST, bool FINAL, typename T>
-__global__ void __launch_bounds__(kSortThreads, 2)
-k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
-              int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
-              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
-              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
-              T* __restrict__ vol_sorted) {
-    extern __shared__ int cnt[];
-    bin_scatter_body<FIRST, FINAL, T>(keys_in, vals_in, n, ntiles, shift, bits, offs, keys_out, vals_out, perm,
-                                      key_sorted, inv_perm, vol, vol_sorted, cnt, launch_blk());
-}
-
-// ----------------------------------------------------------------------
-// Exclusive scan of int32 (totals fit in int32: at most 2^31 - 1 particles)
-// ----------------------------------------------------------------------
+// Block-wide exclusive scan of one int per thread (total in `total`).
 __device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = v;
@@ -247,6 +157,161 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& to
     __syncthreads();
     return wbase + x - v;
 }
+
+// Stable scatter of one digit pass.  offs = exclusive scan of the tile
+// histograms, digit-major ([digit][tile]).  The tile is first ranked (each
+// warp walks its 512-element slice in order with match_any and per-warp
+// digit counters), then reordered by digit in shared memory, and finally
+// written out slot by slot: consecutive threads write consecutive addresses
+// of each digit's run, so the stores coalesce even for keys in random order.
+// Shared memory (ints): a region holding first the per-warp counters
+// [kSortWarps][R], then the staged tile (keys, ids, diameters); then the
+// tile-local digit starts [R] and the global shifts [R].
+
+template <bool FIRST, bool FINAL, typename T>
+__device__ __forceinline__ void bin_scatter_body(const int32_t* __restrict__ keys_in,
+                                                 const int32_t* __restrict__ vals_in, long long n, int ntiles,
+                                                 int shift, int bits, const int32_t* __restrict__ offs,
+                                                 int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
+                                                 int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
+                                                 int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+                                                 T* __restrict__ vol_sorted, int* smem, Blk blk) {
+    __shared__ int shw[32];
+    const int R = 1 << bits;
+    const size_t region = ((size_t)kSortWarps << bits) > (size_t)kSortTile * (8 + sizeof(T)) / sizeof(int)
+                              ? ((size_t)kSortWarps << bits)
+                              : (size_t)kSortTile * (8 + sizeof(T)) / sizeof(int);
+    int* cnt = smem;                       // [kSortWarps][R], then the staged tile
+    int* lbase = smem + region;            // [R] tile-local start of each digit
+    int* shiftg = lbase + R;               // [R] global start - local start
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    int* wc = cnt + warp * R;
+    const unsigned lt = lanemask_lt();
+    const long long tile0 = blk.id * kSortTile;
+    const long long base = tile0 + (long long)warp * (kSortTile / kSortWarps);
+    const int tile_n = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+    int kv[kSortItems], vv[kSortItems], rk[kSortItems];
+    T vol_k[kSortItems];
+    // all loads of the slice first, so they are in flight together
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        bool valid = p < n;
+        kv[k] = valid ? __ldg(keys_in + p) : 0;
+        vv[k] = valid ? (FIRST ? (int)p : __ldg(vals_in + p)) : 0;
+    }
+    if (FINAL)
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k)
+            if (base + k * 32 + lane < n) vol_k[k] = __ldg(vol + vv[k]);
+    // rank within the warp's slice, in index order
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        bool valid = p < n;
+        int kk = kv[k];
+        int d = valid ? ((kk >> shift) & (R - 1)) : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & lt);
+        int c0 = valid ? wc[d] : 0;
+        __syncwarp();
+        if (valid && before == 0) wc[d] = c0 + __popc(peers);
+        __syncwarp();
+        rk[k] = c0 + before;
+    }
+    __syncthreads();
+    // per digit: the warps' exclusive offsets within the tile's digit run,
+    // and the digit's count; then the tile-local digit starts (a block scan
+    // over the digits, consecutive digits per thread)
+    constexpr int kMaxPer = (1 << kMaxDigitBits) / kSortThreads;   // digits per thread at most
+    const int per = (R + (int)blockDim.x - 1) / (int)blockDim.x;
+    int tot[kMaxPer > 0 ? kMaxPer : 1];
+    int mysum = 0;
+#pragma unroll
+    for (int j = 0; j < (kMaxPer > 0 ? kMaxPer : 1); ++j) {
+        tot[j] = 0;
+        const int d = threadIdx.x * per + j;
+        if (j < per && d < R) {
+            int run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const int t = cnt[w * R + d];
+                cnt[w * R + d] = run;
+                run += t;
+            }
+            tot[j] = run;
+            mysum += run;
+        }
+    }
+    int all;
+    int ex = block_exclusive_scan(mysum, shw, all);
+#pragma unroll
+    for (int j = 0; j < (kMaxPer > 0 ? kMaxPer : 1); ++j) {
+        const int d = threadIdx.x * per + j;
+        if (j < per && d < R) {
+            lbase[d] = ex;
+            shiftg[d] = __ldg(offs + (long long)d * ntiles + blk.id) - ex;
+            ex += tot[j];
+        }
+    }
+    __syncthreads();
+    // local slot of every element
+    int lp[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        long long p = base + k * 32 + lane;
+        lp[k] = -1;
+        if (p < n) {
+            const int d = (kv[k] >> shift) & (R - 1);
+            lp[k] = lbase[d] + wc[d] + rk[k];
+        }
+    }
+    __syncthreads();   // every counter read: the region now takes the staged tile
+    int* sk = cnt;
+    int* sv = cnt + kSortTile;
+    T* svol = reinterpret_cast<T*>(cnt + 2 * kSortTile);
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (lp[k] >= 0) {
+            sk[lp[k]] = kv[k];
+            sv[lp[k]] = vv[k];
+            if (FINAL) svol[lp[k]] = vol_k[k];
+        }
+    __syncthreads();
+    // write out in slot order: each digit's run is contiguous in memory
+    for (int i = threadIdx.x; i < tile_n; i += blockDim.x) {
+        const int key = sk[i];
+        const int val = sv[i];
+        const int dst = i + shiftg[(key >> shift) & (R - 1)];
+        if (FINAL) {
+            perm[dst] = val;
+            key_sorted[dst] = key;
+            inv_perm[val] = dst;
+            vol_sorted[dst] = svol[i];
+        } else {
+            keys_out[dst] = key;
+            vals_out[dst] = val;
+        }
+    }
+}
+
+template <bool FIRST, bool FINAL, typename T>
+__global__ void __launch_bounds__(kSortThreads, 2)
+k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, long long n,
+              int ntiles, int shift, int bits, const int32_t* __restrict__ offs,
+              int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
+              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+              T* __restrict__ vol_sorted) {
+    extern __shared__ int cnt[];
+    bin_scatter_body<FIRST, FINAL, T>(keys_in, vals_in, n, ntiles, shift, bits, offs, keys_out, vals_out, perm,
+                                      key_sorted, inv_perm, vol, vol_sorted, cnt, launch_blk());
+}
+
+// ----------------------------------------------------------------------
+// Exclusive scan of int32 (totals fit in int32: at most 2^31 - 1 particles)
+// ----------------------------------------------------------------------
 
 // Load the 16 consecutive elements of a thread (zero past m).
 __device__ __forceinline__ void load16(const int32_t* __restrict__ in, long long start, long long m, int v[16]) {
@@ -355,7 +420,7 @@ static bool g_attr_done = false;
 
 static cg_status set_attrs() {
     if (g_attr_done) return CG_OK;
-    const int smem = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);   // 128 KB at 16 warps x 2^11
+    const int smem = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(double));   // 144 KB at 2^11 digits
 #define CG_ATTR(F, L, T) \
     CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<F, L, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
     CG_ATTR(true, true, float);
@@ -377,7 +442,7 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
     CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
               g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
-    const size_t smem0 = (size_t)kSortWarps * sizeof(int) << b0;
+    const size_t smem0 = scatter_smem_bytes(b0, sizeof(T));
     if (g->npasses == 1) {
         CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true, T>), ntiles, kSortThreads, smem0, g->key, nullptr,
                   n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
@@ -390,7 +455,7 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
         CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1, g->key1, n, ntiles, b0, b1,
                   g->hist);
         CG_TRY(scan_exclusive2(g, g->hist, g->hist, m1, nullptr, nullptr, 0));
-        const size_t smem1 = (size_t)kSortWarps * sizeof(int) << b1;
+        const size_t smem1 = scatter_smem_bytes(b1, sizeof(T));
         CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true, T>), ntiles, kSortThreads, smem1, g->key1, g->val1,
                   n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
                   (const T*)g->vol, (T*)g->vol_sorted);
@@ -441,7 +506,7 @@ static bool g_batch_attr = false;
 
 static cg_status batch_bin_attrs() {
     if (g_batch_attr) return CG_OK;
-    const int mx = kSortWarps * (1 << kMaxDigitBits) * (int)sizeof(int);
+    const int mx = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(float));
     CG_CUDA(cudaFuncSetAttribute(kb_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     CG_CUDA(cudaFuncSetAttribute(kb_bin_key, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (1 << kMaxDigitBits) * (int)sizeof(int)));

@@ -23,6 +23,14 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxDigitBits = 11;                   // radix digit of one pass
 constexpr int kMaxBulkBits = 2 * kMaxDigitBits;     // two passes -> 2^22 cells
 constexpr int kScanItems = 4096;                    // elements per scan block
+// Dynamic shared memory of a sort scatter pass with 2^bits digits: the
+// per-warp counters, or the staged tile (key, id, diameter of T), whichever
+// is larger, plus two [2^bits] int arrays.
+__host__ __device__ constexpr size_t scatter_smem_bytes(int bits, size_t tsize) {
+    return ((size_t)kSortWarps * sizeof(int) << bits) > (size_t)kSortTile * (8 + tsize)
+               ? (((size_t)kSortWarps * sizeof(int) << bits) + (2 * sizeof(int) << bits))
+               : ((size_t)kSortTile * (8 + tsize) + (2 * sizeof(int) << bits));
+}
 constexpr int kNumSlots = 16;                       // status counters
 
 // Status word slots (unsigned long long each).
