@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", default="packed_bed",
-                    choices=["packed_bed", "small_packed_bed", "clustered_bed", "small_clustered_bed"])
+                    choices=["packed_bed", "small_packed_bed", "clustered_bed", "medium_clustered_bed",
+                             "small_clustered_bed"])
     ap.add_argument("--batch", action="store_true",
                     help="64 uneven instances: batched persistent launches vs one by one")
     ap.add_argument("--learned", action="store_true",

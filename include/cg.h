@@ -81,6 +81,9 @@ enum {
  * mu_f and porosity), Eq. (DEM_EQUATIONS) (gravity).
  *   eps_switch  Ergun -> Wen-Yu switch porosity (eps >= eps_switch is Wen-Yu), in (0, 1]
  *   eps_min     porosity seen by the drag law is max(eps, eps_min), in [0, 1)
+ *   sort_digits widest radix digit of the binning sort's passes, 6..11, or 0 for
+ *               the default (digits of up to 10 bits below 2^20 bulk cells, up to
+ *               8 from 2^20 on); any value gives the same bins
  * Limits: fine_n[a] % ratio == 0, bulk cells >= 2 per axis, at most 2^22
  * bulk cells and 2^31 - 1 fine cells. */
 typedef struct {
@@ -91,7 +94,7 @@ typedef struct {
     int32_t prec;        /* cg_precision */
     int32_t law;         /* cg_drag_law  */
     int32_t interp;      /* cg_interp    */
-    int32_t reserved0;
+    int32_t sort_digits; /* 0 = default */
     double rho_f, mu_f, rho_p;
     double eps_switch;
     double eps_min;
@@ -159,7 +162,7 @@ cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
  * Same cell rule, stable order and outputs as cg_bin_particles, but without
  * a handle: the grid comes from desc (the physics fields are not used) and
  * all scratch lives in one fixed device array inside the library (about
- * 10 MB per GPU that loads it, held until exit).
+ * 12 MB per GPU that loads it, held until exit).
  *   n <= 262,144 particles (else CG_ERR_OUT_OF_RANGE), at most 2^22 cells.
  *   pos_d [n] T4 (16-byte aligned); perm_out [n] and cell_start_out
  *   [n_b + 1] required; cell_out [n] nullable.  Enqueued on cuda_stream.

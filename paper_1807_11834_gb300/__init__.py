@@ -46,7 +46,7 @@ class CgError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("extent", C.c_double * 3), ("fine_n", C.c_int32 * 3),
                 ("ratio", C.c_int32), ("prec", C.c_int32), ("law", C.c_int32), ("interp", C.c_int32),
-                ("reserved0", C.c_int32), ("rho_f", C.c_double), ("mu_f", C.c_double),
+                ("sort_digits", C.c_int32), ("rho_f", C.c_double), ("mu_f", C.c_double),
                 ("rho_p", C.c_double), ("eps_switch", C.c_double), ("eps_min", C.c_double),
                 ("gravity", C.c_double * 3)]
 
@@ -178,6 +178,7 @@ def make_desc(d: dict) -> GridDesc:
     g.interp = d.get("interp", CG_INTERP_TRILINEAR)
     g.rho_f, g.mu_f, g.rho_p = d["rho_f"], d["mu_f"], d["rho_p"]
     g.eps_switch, g.eps_min = d["eps_switch"], d["eps_min"]
+    g.sort_digits = int(d.get("sort_digits", 0))
     g.gravity[:] = d.get("gravity", (0.0, 0.0, 0.0))
     return g
 

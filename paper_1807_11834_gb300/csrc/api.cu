@@ -143,6 +143,8 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     dfree(g->key);
     dfree(g->key1);
     dfree(g->val1);
+    dfree(g->key2);
+    dfree(g->val2);
     dfree(g->perm);
     dfree(g->key_sorted);
     dfree(g->inv_perm);
@@ -156,6 +158,8 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     CG_TRY(dalloc(&g->key, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->key1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->val1, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->key2, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->val2, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->perm, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->key_sorted, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->inv_perm, sizeof(int32_t) * cap));
@@ -163,7 +167,7 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     CG_TRY(dalloc(&g->vol_sorted, g->tsize * cap));
     CG_TRY(dalloc(&g->Fs, 4 * g->tsize * cap));
     const long long ntiles = cap / kSortTile;
-    const int maxbits = std::max(g->pass_bits[0], g->pass_bits[1]);
+    const int maxbits = std::max(g->pass_bits[0], std::max(g->pass_bits[1], g->pass_bits[2]));
     g->hist_cap = ntiles << maxbits;
     CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
     g->scan_cap = (g->hist_cap + kScanItems - 1) / kScanItems + (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
@@ -197,6 +201,8 @@ static void free_all(cg_grids* g) {
     dfree(g->key);
     dfree(g->key1);
     dfree(g->val1);
+    dfree(g->key2);
+    dfree(g->val2);
     dfree(g->perm);
     dfree(g->key_sorted);
     dfree(g->inv_perm);
@@ -257,6 +263,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     if (d.prec != CG_FP32 && d.prec != CG_FP64) return CG_ERR_INVALID_ARG;
     if (d.law != CG_DRAG_DI_FELICE && d.law != CG_DRAG_ERGUN_WEN_YU) return CG_ERR_INVALID_ARG;
     if (d.interp != CG_INTERP_TRILINEAR && d.interp != CG_INTERP_CELL) return CG_ERR_INVALID_ARG;
+    if (d.sort_digits != 0 && (d.sort_digits < 6 || d.sort_digits > kMaxDigitBits)) return CG_ERR_INVALID_ARG;
     if (!(d.rho_f > 0.0) || !(d.mu_f > 0.0) || !(d.rho_p > 0.0) || !isfinite(d.rho_f) || !isfinite(d.mu_f) ||
         !isfinite(d.rho_p))
         return CG_ERR_INVALID_ARG;
@@ -315,15 +322,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     for (int a = 0; a < 3; ++a) gd.g[a] = d.gravity[a];
 
     g->bulk_bits = std::max(1, ceil_log2(nbulk));
-    if (g->bulk_bits <= kMaxDigitBits) {
-        g->npasses = 1;
-        g->pass_bits[0] = g->bulk_bits;
-        g->pass_bits[1] = 0;
-    } else {
-        g->npasses = 2;
-        g->pass_bits[0] = (g->bulk_bits + 1) / 2;
-        g->pass_bits[1] = g->bulk_bits - g->pass_bits[0];
-    }
+    g->npasses = split_passes(g->bulk_bits, g->pass_bits, d.sort_digits);
 
     cg_status st = CG_OK;
     if (st == CG_OK) st = dalloc(&g->cell_start, sizeof(int32_t) * (nbulk + 1));

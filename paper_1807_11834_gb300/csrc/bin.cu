@@ -426,9 +426,11 @@ static cg_status set_attrs() {
     CG_ATTR(true, true, float);
     CG_ATTR(true, false, float);
     CG_ATTR(false, true, float);
+    CG_ATTR(false, false, float);
     CG_ATTR(true, true, double);
     CG_ATTR(true, false, double);
     CG_ATTR(false, true, double);
+    CG_ATTR(false, false, double);
 #undef CG_ATTR
     g_attr_done = true;
     return CG_OK;
@@ -438,27 +440,43 @@ template <typename T>
 static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, long long m0, double* eps_fill,
                             T* rec_fill, T* eps_t_fill) {
     const long long nbulk = g->gd.nbulk;
-    const int b0 = g->pass_bits[0], b1 = g->pass_bits[1];
+    const int np = g->npasses;
+    const int b0 = g->pass_bits[0];
     CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
               g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
-    const size_t smem0 = scatter_smem_bytes(b0, sizeof(T));
-    if (g->npasses == 1) {
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true, T>), ntiles, kSortThreads, smem0, g->key, nullptr,
-                  n, ntiles, 0, b0, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
-                  (const T*)g->vol, (T*)g->vol_sorted);
-    } else {
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false, T>), ntiles, kSortThreads, smem0, g->key, nullptr,
-                  n, ntiles, 0, b0, g->hist, g->key1, g->val1, nullptr, nullptr, nullptr, (const T*)nullptr,
-                  (T*)nullptr);
-        const long long m1 = (long long)ntiles << b1;
-        CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << b1, g->key1, n, ntiles, b0, b1,
-                  g->hist);
-        CG_TRY(scan_exclusive2(g, g->hist, g->hist, m1, nullptr, nullptr, 0));
-        const size_t smem1 = scatter_smem_bytes(b1, sizeof(T));
-        CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true, T>), ntiles, kSortThreads, smem1, g->key1, g->val1,
-                  n, ntiles, b0, b1, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
-                  (const T*)g->vol, (T*)g->vol_sorted);
+    // pass p reads (keys, ids) from in[p] and writes them to in[p + 1]; the
+    // last pass writes the final order
+    int32_t* ks[kMaxPasses + 1] = {g->key, g->key1, g->key2, nullptr};
+    int32_t* vs[kMaxPasses + 1] = {nullptr, g->val1, g->val2, nullptr};
+    int shift = 0;
+    for (int p = 0; p < np; ++p) {
+        const int bits = g->pass_bits[p];
+        if (p > 0) {
+            const long long m = (long long)ntiles << bits;
+            CG_LAUNCH(g, "bin_hist", k_bin_hist, ntiles, kSortThreads, sizeof(int) << bits, ks[p], n, ntiles, shift,
+                      bits, g->hist);
+            CG_TRY(scan_exclusive2(g, g->hist, g->hist, m, nullptr, nullptr, 0));
+        }
+        const size_t smem = scatter_smem_bytes(bits, sizeof(T));
+        const bool first = p == 0, last = p == np - 1;
+        if (first && last)
+            CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, true, T>), ntiles, kSortThreads, smem, ks[0], nullptr,
+                      n, ntiles, shift, bits, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
+                      (const T*)g->vol, (T*)g->vol_sorted);
+        else if (first)
+            CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<true, false, T>), ntiles, kSortThreads, smem, ks[0], nullptr,
+                      n, ntiles, shift, bits, g->hist, ks[1], vs[1], nullptr, nullptr, nullptr, (const T*)nullptr,
+                      (T*)nullptr);
+        else if (last)
+            CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, true, T>), ntiles, kSortThreads, smem, ks[p], vs[p],
+                      n, ntiles, shift, bits, g->hist, nullptr, nullptr, g->perm, g->key_sorted, g->inv_perm,
+                      (const T*)g->vol, (T*)g->vol_sorted);
+        else
+            CG_LAUNCH(g, "bin_scatter", (k_bin_scatter<false, false, T>), ntiles, kSortThreads, smem, ks[p], vs[p],
+                      n, ntiles, shift, bits, g->hist, ks[p + 1], vs[p + 1], nullptr, nullptr, nullptr,
+                      (const T*)nullptr, (T*)nullptr);
+        shift += bits;
     }
     return CG_OK;
 }
@@ -568,10 +586,9 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
         return CG_OK;
     }
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
-    const int b0 = g->pass_bits[0], b1 = g->pass_bits[1];
-    const bool two = g->npasses == 2;
-    const long long m0 = (long long)ntiles << b0;
-    if (m0 > g->hist_cap || (two && ((long long)ntiles << b1) > g->hist_cap)) return CG_ERR_OUT_OF_RANGE;
+    const long long m0 = (long long)ntiles << g->pass_bits[0];
+    for (int p = 0; p < g->npasses; ++p)
+        if (((long long)ntiles << g->pass_bits[p]) > g->hist_cap) return CG_ERR_OUT_OF_RANGE;
 
     if (g->fp64)
         CG_TRY(bin_passes<double>(g, n, (const double*)pos_d, ntiles, m0, eps_fill, (double*)rec_fill,

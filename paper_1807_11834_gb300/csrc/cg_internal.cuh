@@ -20,9 +20,25 @@ constexpr int kSortThreads = 512;                   // threads of a sort tile
 constexpr int kSortItems = 8;                       // items per thread
 constexpr int kSortTile = kSortThreads * kSortItems; // 4096 particles per tile
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kMaxDigitBits = 11;                   // radix digit of one pass
+constexpr int kMaxDigitBits = 11;                   // widest radix digit of one pass
+constexpr int kMaxPasses = 3;
 constexpr int kMaxBulkBits = 2 * kMaxDigitBits;     // two passes -> 2^22 cells
 constexpr int kScanItems = 4096;                    // elements per scan block
+// Split of a key of `bits` bits into the fewest passes of at most `digits`
+// bits (at most kMaxPasses; wider only when the key needs it), the low
+// digits first.  digits 0 takes the default: narrow digits (8) for grids of
+// 2^20 cells and more, whose particles are usually far from cell order and
+// whose scatters then profit from long digit runs (three passes measured
+// faster on the 32M-particle clustered bed), wide ones (10) below (two
+// passes measured faster on the 4M-particle packed bed).  Returns the passes.
+inline int split_passes(int bits, int (&pb)[kMaxPasses], int digits = 0) {
+    const int D = digits > 0 ? digits : (bits >= 20 ? 8 : 10);
+    int np = (bits + D - 1) / D;
+    np = np < 1 ? 1 : (np > kMaxPasses ? kMaxPasses : np);
+    for (int i = 0; i < kMaxPasses; ++i) pb[i] = i < np ? bits / np + (i < bits % np ? 1 : 0) : 0;
+    return np;
+}
+
 // Dynamic shared memory of a sort scatter pass with 2^bits digits: the
 // per-warp counters, or the staged tile (key, id, diameter of T), whichever
 // is larger, plus two [2^bits] int arrays.
@@ -104,7 +120,7 @@ struct cg_grids {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 148;
-    int bulk_bits = 0, pass_bits[2] = {0, 0}, npasses = 1;
+    int bulk_bits = 0, pass_bits[cg::kMaxPasses] = {0, 0, 0}, npasses = 1;
 
     // binning state
     long long n_binned = -1;
@@ -114,6 +130,8 @@ struct cg_grids {
     int32_t* key = nullptr;        // [cap] cell per particle (caller order)
     int32_t* key1 = nullptr;       // [cap] keys after pass 1
     int32_t* val1 = nullptr;       // [cap] particle ids after pass 1
+    int32_t* key2 = nullptr;       // [cap] keys after pass 2 of three
+    int32_t* val2 = nullptr;       // [cap] particle ids after pass 2 of three
     int32_t* perm = nullptr;       // [cap] particle ids in cell order
     int32_t* key_sorted = nullptr; // [cap] cell of each slot of the sorted order
     int32_t* inv_perm = nullptr;   // [cap] sorted slot of each particle

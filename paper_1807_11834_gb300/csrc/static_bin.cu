@@ -11,7 +11,7 @@
 // nothing.
 //
 // The array below is part of the library's device image: every GPU that
-// loads the library holds it (about 10 MB) until the process exits.  Host
+// loads the library holds it (about 12 MB) until the process exits.  Host
 // code cannot use the array's name as a device address; the address is
 // looked up once per device with cudaGetSymbolAddress on the first call
 // made with that device current.  Make that first call before any stream
@@ -41,7 +41,9 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kOffKey = 0;
 constexpr size_t kOffKey1 = kOffKey + align256(4 * kStaticMaxParticles);
 constexpr size_t kOffVal1 = kOffKey1 + align256(4 * kStaticMaxParticles);
-constexpr size_t kOffKeySorted = kOffVal1 + align256(4 * kStaticMaxParticles);
+constexpr size_t kOffKey2 = kOffVal1 + align256(4 * kStaticMaxParticles);
+constexpr size_t kOffVal2 = kOffKey2 + align256(4 * kStaticMaxParticles);
+constexpr size_t kOffKeySorted = kOffVal2 + align256(4 * kStaticMaxParticles);
 constexpr size_t kOffInvPerm = kOffKeySorted + align256(4 * kStaticMaxParticles);
 constexpr size_t kOffVol = kOffInvPerm + align256(4 * kStaticMaxParticles);
 constexpr size_t kOffVolSorted = kOffVol + align256(8 * kStaticMaxParticles);
@@ -101,6 +103,7 @@ extern "C" cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n
         if (nb[a] < 2) return CG_ERR_INVALID_ARG;
         nbulk *= nb[a];
     }
+    if (d.sort_digits != 0 && (d.sort_digits < 6 || d.sort_digits > cg::kMaxDigitBits)) return CG_ERR_INVALID_ARG;
     if (nbulk > (1LL << cg::kMaxBulkBits)) return CG_ERR_OUT_OF_RANGE;
 
     void* base = nullptr;
@@ -133,18 +136,12 @@ extern "C" cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n
     int bits = 0;
     while ((1LL << bits) < nbulk) ++bits;
     bits = std::max(bits, 1);
-    if (bits <= cg::kMaxDigitBits) {
-        g.npasses = 1;
-        g.pass_bits[0] = bits;
-        g.pass_bits[1] = 0;
-    } else {
-        g.npasses = 2;
-        g.pass_bits[0] = (bits + 1) / 2;
-        g.pass_bits[1] = bits - g.pass_bits[0];
-    }
+    g.npasses = cg::split_passes(bits, g.pass_bits, d.sort_digits);
     g.key = (int32_t*)(s + kOffKey);
     g.key1 = (int32_t*)(s + kOffKey1);
     g.val1 = (int32_t*)(s + kOffVal1);
+    g.key2 = (int32_t*)(s + kOffKey2);
+    g.val2 = (int32_t*)(s + kOffVal2);
     g.key_sorted = (int32_t*)(s + kOffKeySorted);
     g.inv_perm = (int32_t*)(s + kOffInvPerm);
     g.vol = s + kOffVol;

@@ -196,6 +196,12 @@ def clustered_bed(seed: int = 0, fine_n=(512, 512, 256), ratio: int = 4,
                     dt=dt, steps=steps)
 
 
+def medium_clustered_bed(seed: int = 0, fp64: bool = False) -> Workload:
+    """Clustered bed at 1/8 scale: fine 256x256x128, ratio 4, 4,000,000
+    spheres, 200 clusters (same particles per bulk cell as the full bed)."""
+    return clustered_bed(seed, fine_n=(256, 256, 128), ratio=4, n=4_000_000, fp64=fp64)
+
+
 def small_packed_bed(seed: int = 0, fp64: bool = False) -> Workload:
     """Packed bed at 1/64 of the volume count: fine 64x64x128, ratio 4,
     62,500 spheres of d = 0.016 (same porosity ~0.4, same bed height)."""
@@ -264,4 +270,5 @@ WORKLOADS = {
     "clustered_bed": clustered_bed,
     "small_packed_bed": small_packed_bed,
     "small_clustered_bed": small_clustered_bed,
+    "medium_clustered_bed": medium_clustered_bed,
 }
