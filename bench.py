@@ -39,9 +39,9 @@ UNIT = "particle-steps/s"
 # dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
 # source file is byte-identical to the one profiled (sha256 prefix).
 NCU_TRAFFIC = {
-    # packed bed, one eager step: k_bin_scatter first pass 21.37 MB, final
-    # pass 90.35 / 86.21 MB (two captures); per launch, the mean of the passes
-    "bin_scatter": {"file": "bin.cu", "sha": "91edeebe374095c2", "bytes": 54.8e6},
+    # packed bed, one eager step: k_bin_scatter first pass 20.53 MB, final
+    # pass 62.48 / 60.02 MB (two captures); per launch, the mean of the passes
+    "bin_scatter": {"file": "bin.cu", "sha": "88c48787c50ba765", "bytes": 40.9e6},
 }
 
 
@@ -148,6 +148,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(inside),
                 "power_w_max": max((num(p[2]) or 0.0) for _, p in inside)}
+
+
+def workload_name(name, w):
+    """The workload with its sizes, as the JSON line's config names it."""
+    d = w.desc
+    box = "x".join(f"{e:g}" for e in d["extent"])
+    law = "Di Felice" if d["law"] == 0 else "Ergun/Wen-Yu"
+    prec = "FP64" if d.get("fp64") else "FP32"
+    return (f"{name}: {box} box, fine {'x'.join(map(str, d['fine_n']))}, ratio {d['ratio']}, "
+            f"{w.n} spheres, {law}, {prec}")
 
 
 def algorithmic_bytes(g, n, eps_fine=True):
@@ -362,8 +372,7 @@ def run_gb300(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: 1x1x2 box, fine {'x'.join(map(str, w.desc['fine_n']))}, "
-                                   f"ratio {w.desc['ratio']}, {n} spheres, Ergun/Wen-Yu, FP32",
+            "config": {"workload": workload_name(args.workload, w),
                        "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs {input_bytes / 1e6:.0f} MB > L2 (126 MB) per step, no flush",
@@ -409,8 +418,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": ks, "warmup": wu, "ms_per_step": 1e3 * tc / ks, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: 1x1x2 box, fine {'x'.join(map(str, w.desc['fine_n']))}, "
-                                   f"ratio {w.desc['ratio']}, {n} spheres, Ergun/Wen-Yu",
+            "config": {"workload": workload_name(args.workload, w),
                        "particles": n},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
