@@ -72,6 +72,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over all ranks (x itself on one rank): the
+    job's time is the slowest replica's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, steps, seconds):
+    """Units all replicas processed over the slowest replica's time."""
+    return world * units_per_rank * steps / seconds
+
+
 def file_sha(path):
     with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -268,10 +285,7 @@ def run_gb300(args):
     launches = launches_per_step * args.steps
     time.sleep(0.25)
     sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     rc, flags, counts = g.cg_sync_status()
     if rc != 0:
         raise RuntimeError(f"timed status {rc}")
@@ -310,7 +324,7 @@ def run_gb300(args):
                     "timing": "serialized per-kernel CUDA events over a profiled pass of the same steps"}
     ms_step = ms / args.steps
     step_gbs = step_bytes / (ms_step * 1e-3) / 1e9
-    value = world * n * args.steps / (ms * 1e-3)
+    value = job_throughput(world, n, args.steps, ms * 1e-3)
     clocks = sampler.summary(t0, t1)
 
     # end-to-end: host buffers through the host entries (H2D of the inputs and
@@ -339,17 +353,12 @@ def run_gb300(args):
                     g.cg_step_host(hpos, hvel, huf, hout)
             if pipelined:
                 g.cg_step_host_wait()
-            te = time.perf_counter() - ta
-            if world > 1:
-                t = torch.tensor([te], device=dev, dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                te = float(t.item())
-            return te
+            return max_over_ranks(time.perf_counter() - ta, world, dev)
 
         te_sync = host_run(False)
         te = host_run(True)
         d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None)
-        e2e = {"value": world * n * ke / te, "unit": UNIT, "h2d_bytes_per_step": int(input_bytes),
+        e2e = {"value": job_throughput(world, n, ke, te), "unit": UNIT, "h2d_bytes_per_step": int(input_bytes),
                "d2h_bytes_per_step": int(d2h), "steps": ke, "ms_per_step": 1e3 * te / ke,
                "entry": "cg_step_host_async per step + cg_step_host_wait (pinned host buffers)",
                "blocking_entry_ms_per_step": 1e3 * te_sync / ke}
