@@ -70,6 +70,11 @@ enum {
     CG_FLAG_TIMEOUT = 8u       /* a bounded device wait gave up              */
 };
 
+/* Binning sort choices (cg_grid_desc.sort_digits). */
+#define CG_SORT_AUTO 0
+#define CG_SORT_CELLS 1
+#define CG_SORT_CELLS_AUTO_MAX 8388608   /* 2^23 particles */
+
 /* Number of counters returned by cg_sync_status. */
 #define CG_NCOUNTS 5
 
@@ -81,9 +86,18 @@ enum {
  * mu_f and porosity), Eq. (DEM_EQUATIONS) (gravity).
  *   eps_switch  Ergun -> Wen-Yu switch porosity (eps >= eps_switch is Wen-Yu), in (0, 1]
  *   eps_min     porosity seen by the drag law is max(eps, eps_min), in [0, 1)
- *   sort_digits widest radix digit of the binning sort's passes, 6..11, or 0 for
- *               the default (digits of up to 10 bits below 2^20 bulk cells, up to
- *               8 from 2^20 on); any value gives the same bins
+ *   sort_digits the binning sort (every choice gives the same bins, and so
+ *               the same results):
+ *               CG_SORT_CELLS (1): per-cell sort (counts, arrival ranks,
+ *                 placement, then each cell's ids sorted); fastest when its
+ *                 particle-sized arrays fit in L2 or the particle order keeps
+ *                 neighbours close;
+ *               6..11: least-significant-digit sort with digits of at most
+ *                 that many bits (two or three passes); fastest for large
+ *                 particle sets in random order;
+ *               CG_SORT_AUTO (0): per-cell sort up to CG_SORT_CELLS_AUTO_MAX
+ *                 particles per call, above it the digit sort with digits of
+ *                 up to 10 bits below 2^20 bulk cells, up to 8 from 2^20 on
  * Limits: fine_n[a] % ratio == 0, bulk cells >= 2 per axis, at most 2^22
  * bulk cells and 2^31 - 1 fine cells. */
 typedef struct {
@@ -94,7 +108,7 @@ typedef struct {
     int32_t prec;        /* cg_precision */
     int32_t law;         /* cg_drag_law  */
     int32_t interp;      /* cg_interp    */
-    int32_t sort_digits; /* 0 = default */
+    int32_t sort_digits; /* CG_SORT_AUTO, CG_SORT_CELLS or 6..11 */
     double rho_f, mu_f, rho_p;
     double eps_switch;
     double eps_min;

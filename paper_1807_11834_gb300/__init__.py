@@ -33,6 +33,11 @@ CG_DEP_VOLUME, CG_DEP_MOMENTUM = 0, 1
 CG_FLAG_OUTSIDE, CG_FLAG_NONFINITE, CG_FLAG_EPS_CLAMPED, CG_FLAG_TIMEOUT = 1, 2, 4, 8
 CG_NSUMS = 16
 CG_NCOUNTS = 5
+# binning sort choices (descriptor key "sort_digits"): automatic, per-cell
+# sort, or 6..11 for the digit sort with digits of that many bits at most
+CG_SORT_AUTO = 0
+CG_SORT_CELLS = 1
+CG_SORT_CELLS_AUTO_MAX = 1 << 23
 SUM_NAMES = ["vol_particles", "vol_deposited", "F_x", "F_y", "F_z", "SbVb_x", "SbVb_y", "SbVb_z",
              "SfVf_x", "SfVf_y", "SfVf_z", "F_abs", "mom_x", "mom_y", "mom_z", "n_clamped"]
 

@@ -168,7 +168,9 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     CG_TRY(dalloc(&g->Fs, 4 * g->tsize * cap));
     const long long ntiles = cap / kSortTile;
     const int maxbits = std::max(g->pass_bits[0], std::max(g->pass_bits[1], g->pass_bits[2]));
-    g->hist_cap = ntiles << maxbits;
+    // digit histograms of the digit sort, or the large-cell list of the
+    // default sort (at most cap / 257 cells after a count)
+    g->hist_cap = std::max<long long>(ntiles << maxbits, cap / 256 + 2);
     CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
     g->scan_cap = (g->hist_cap + kScanItems - 1) / kScanItems + (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
     CG_TRY(dalloc(&g->scan_part, sizeof(int32_t) * g->scan_cap));
@@ -263,7 +265,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     if (d.prec != CG_FP32 && d.prec != CG_FP64) return CG_ERR_INVALID_ARG;
     if (d.law != CG_DRAG_DI_FELICE && d.law != CG_DRAG_ERGUN_WEN_YU) return CG_ERR_INVALID_ARG;
     if (d.interp != CG_INTERP_TRILINEAR && d.interp != CG_INTERP_CELL) return CG_ERR_INVALID_ARG;
-    if (d.sort_digits != 0 && (d.sort_digits < 6 || d.sort_digits > kMaxDigitBits)) return CG_ERR_INVALID_ARG;
+    if (!sort_choice_valid(d.sort_digits)) return CG_ERR_INVALID_ARG;
     if (!(d.rho_f > 0.0) || !(d.mu_f > 0.0) || !(d.rho_p > 0.0) || !isfinite(d.rho_f) || !isfinite(d.mu_f) ||
         !isfinite(d.rho_p))
         return CG_ERR_INVALID_ARG;
@@ -322,7 +324,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     for (int a = 0; a < 3; ++a) gd.g[a] = d.gravity[a];
 
     g->bulk_bits = std::max(1, ceil_log2(nbulk));
-    g->npasses = split_passes(g->bulk_bits, g->pass_bits, d.sort_digits);
+    g->npasses = split_passes(g->bulk_bits, g->pass_bits, d.sort_digits >= 6 ? d.sort_digits : 0);
 
     cg_status st = CG_OK;
     if (st == CG_OK) st = dalloc(&g->cell_start, sizeof(int32_t) * (nbulk + 1));

@@ -8,14 +8,25 @@
 // lies within that bound of an integer, so the cell is bit-identical to the
 // double rule at FP32 cost.
 //
-// Sort: least-significant-digit counting sort, one or two passes of at most
-// 11 bits.  Each 4096-particle tile ranks its keys stably with warp-level
-// match: warp w owns a contiguous 512-particle slice, walks it 32 at a time
-// in index order and keeps per-digit counters in shared memory, so the
-// rank of a particle within its digit group follows its index.  Tile
-// histograms are scanned digit-major across tiles, which makes the whole
-// pass stable and fully deterministic (no atomics decide any position).
-// Per-cell counts use integer atomics (order-independent), then a scan.
+// The result is the stable order (ids ascending within each cell), built by
+// one of two sorts that give identical bins:
+//
+// Per-cell sort (default up to 2^23 particles): the count atomics hand out
+// arrival ranks, the scan of the counts gives the cell starts, each
+// particle is placed at start + rank, and each cell's ids are then sorted
+// (details below, before the kernels).
+//
+// Digit sort: least-significant-digit counting sort, one to three passes of
+// at most 11 bits.  Each 4096-particle tile ranks its keys stably with
+// warp-level match: warp w owns a contiguous 512-particle slice, walks it
+// 32 at a time in index order and keeps per-digit counters in shared
+// memory, so the rank of a particle within its digit group follows its
+// index.  Tile histograms are scanned digit-major across tiles, which makes
+// the whole pass stable and fully deterministic (no atomics decide any
+// position).  Per-cell counts use integer atomics (order-independent), then
+// a scan.
+#include <algorithm>
+
 #include "cg_internal.cuh"
 #include "batch.cuh"
 
@@ -37,16 +48,22 @@ __device__ __forceinline__ void add_status(unsigned long long* st, int outside, 
 // Key kernel: cell per particle, per-cell counts, tile histogram of digit 0
 // ----------------------------------------------------------------------
 
-template <typename T>
+// RANK (the default sort): no digit histogram; instead every particle keeps
+// its arrival rank within its cell (the value the count atomic returned).
+// The thread's count atomics are issued together, after all its cells are
+// known, so their round trips overlap.
+template <typename T, bool RANK = false>
 __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long long n, const GridDev& g,
                                              int32_t* __restrict__ key, int32_t* __restrict__ count,
                                              int32_t* __restrict__ hist, int ntiles, int bits0, T* __restrict__ vol,
                                              unsigned long long* __restrict__ status, int* sh, Blk blk,
                                              double* __restrict__ eps_fill = nullptr, T* __restrict__ rec_fill = nullptr,
-                                             T* __restrict__ eps_t_fill = nullptr) {
+                                             T* __restrict__ eps_t_fill = nullptr,
+                                             int32_t* __restrict__ arrival = nullptr) {
     __shared__ int s_cnt[2];
     const int R = 1 << bits0;
-    for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
+    if (!RANK)
+        for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     int n_out = 0, n_nf = 0;
@@ -58,6 +75,7 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
         if (p < n) pv[k] = ld4(pos, p);
     }
+    int ck[kSortItems], lk[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
@@ -75,15 +93,34 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         // counts: one integer atomic per run of equal cells in the warp
         // (spatially ordered input has runs of several particles)
         const int len = run_head_length(c, valid);
-        if (len) {
+        ck[k] = c;
+        lk[k] = len;
+        if (!RANK && len) {
             atomicAdd(&count[c], len);
             atomicAdd(&sh[c & (R - 1)], len);
+        }
+    }
+    if (RANK) {
+        int old[kSortItems];
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) old[k] = lk[k] ? atomicAdd(&count[ck[k]], lk[k]) : 0;
+        // the run's head took len slots of the cell's arrival order; every
+        // member finds its head (the last head at or below it)
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            const long long p = base + (long long)k * kSortThreads + threadIdx.x;
+            const unsigned heads = __ballot_sync(0xffffffffu, lk[k] != 0);
+            const int head = 31 - __clz(heads & ((2u << lane) - 1u));
+            const int o = __shfl_sync(0xffffffffu, old[k], head < 0 ? 0 : head);
+            if (p < n) arrival[p] = o + lane - head;
         }
     }
     if (n_out) atomicAdd(&s_cnt[0], n_out);
     if (n_nf) atomicAdd(&s_cnt[1], n_nf);
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
+    if (!RANK)
+        for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
     if (threadIdx.x == 0) add_status(status, s_cnt[0], s_cnt[1]);
     // the porosity of cells without particles is 1: set every cell here (and
     // the porosity of the drag record and of its path-precision copy), the
@@ -96,15 +133,15 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         }
 }
 
-template <typename T>
+template <typename T, bool RANK>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
           int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
           T* __restrict__ vol, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
-          T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
+          T* __restrict__ rec_fill, T* __restrict__ eps_t_fill, int32_t* __restrict__ arrival) {
     extern __shared__ int sh[];
-    bin_key_body(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill, rec_fill,
-                 eps_t_fill);
+    bin_key_body<T, RANK>(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill,
+                          rec_fill, eps_t_fill, arrival);
 }
 
 // Tile histogram of a digit of already-computed keys (second pass).
@@ -416,6 +453,344 @@ static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA,
     return CG_OK;
 }
 
+
+// ----------------------------------------------------------------------
+// Default sort: arrival rank, placement, and a sort of every cell's ids.
+//
+// The key kernel's count atomics hand each particle its arrival rank within
+// its cell; after the scan of the counts, slot = start(cell) + rank places
+// every particle in its cell's segment, in an order the atomics decided.
+// Sorting each segment by particle id then gives exactly the stable order
+// (ids ascending within a cell), independent of that arrival order.  Cells
+// of up to 256 particles are sorted by one warp in registers (bitonic
+// network); larger ones by a whole CTA, in least-significant-digit passes
+// over the ids.  Placement and the per-cell sort touch memory at random
+// where the caller's particle order is random, so this sort suits orders
+// that keep neighbours close (as DEM codes keep theirs); the digit sort
+// above moves whole digit runs and suits random orders.
+// ----------------------------------------------------------------------
+constexpr int kSegWarpMax = 256;   // largest cell a warp sorts in registers
+
+__device__ __forceinline__ void place_body(const int32_t* __restrict__ key, const int32_t* __restrict__ arrival,
+                                           const int32_t* __restrict__ cell_start, long long n,
+                                           int32_t* __restrict__ tmp, Blk blk) {
+    const long long stride = blk.n * (long long)blockDim.x;
+    for (long long p = blk.id * blockDim.x + threadIdx.x; p < n; p += stride)
+        tmp[__ldg(cell_start + __ldg(key + p)) + __ldg(arrival + p)] = (int)p;
+}
+
+__global__ void __launch_bounds__(512) k_bin_place(const int32_t* __restrict__ key,
+                                                   const int32_t* __restrict__ arrival,
+                                                   const int32_t* __restrict__ cell_start, long long n,
+                                                   int32_t* __restrict__ tmp) {
+    place_body(key, arrival, cell_start, n, tmp, launch_blk());
+}
+
+// Ascending bitonic sort of the warp's 32*K values, blocked layout: lane l
+// holds elements l*K .. l*K + K - 1.  Partners closer than K are in the
+// same thread; farther ones are exchanged by shuffles.
+template <int K>
+__device__ __forceinline__ void warp_bitonic(int (&v)[K]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * K; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int q = r ^ j;
+                    if (q > r) {
+                        const bool asc = ((lane * K + r) & k) == 0;
+                        const int a = v[r], b = v[q];
+                        v[r] = asc ? min(a, b) : max(a, b);
+                        v[q] = asc ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+                const int lj = j / K;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const bool asc = ((lane * K + r) & k) == 0;
+                    const int o = __shfl_xor_sync(0xffffffffu, v[r], lj);
+                    v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
+                }
+            }
+        }
+    }
+}
+
+// Outputs of one sorted slot: the id, its cell, its inverse, its diameter.
+template <typename T>
+__device__ __forceinline__ void emit_slot(long long slot, int id, int cell, int32_t* __restrict__ perm,
+                                          int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+                                          const T* __restrict__ vol, T* __restrict__ vol_sorted) {
+    perm[slot] = id;
+    key_sorted[slot] = cell;
+    inv_perm[id] = (int)slot;
+    vol_sorted[slot] = __ldg(vol + id);
+}
+
+// Sort the c (<= 32 K) ids at src (shared memory when staged, else global)
+// with one warp; staged: write them back sorted and write their cells,
+// else write all outputs of the slots s_out .. s_out + c - 1.
+template <int K, typename T>
+__device__ __forceinline__ void warp_sort_cell(int32_t* src, bool staged, long long s_out, int c, int cell,
+                                               int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
+                                               int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+                                               T* __restrict__ vol_sorted) {
+    const int lane = threadIdx.x & 31;
+    int v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = lane * K + r;
+        v[r] = e < c ? src[e] : 0x7fffffff;
+    }
+    if (c > 1) warp_bitonic<K>(v);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = lane * K + r;
+        if (e < c) {
+            if (staged) {
+                src[e] = v[r];
+                key_sorted[s_out + e] = cell;
+            } else {
+                emit_slot<T>(s_out + e, v[r], cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+            }
+        }
+    }
+}
+
+// One CTA sorts the ids of one large cell: passes of 8-bit digits of
+// (id - min id), each a histogram, a scan, and a stable scatter of chunks of
+// NW * 256 ids in order (warp w ranks its 256 ids of the chunk in index order
+// with match_any, as the tile sort does).  Ids move between buf0 and buf1
+// (the same slots of two arrays); the result is read from whichever holds
+// the last pass.  Static shared memory: NW KB + 1.2 KB.
+template <int NW, typename T>
+__device__ __noinline__ void big_sort_cell(int cell, long long s, int c, int32_t* buf0, int32_t* buf1,
+                                           int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
+                                           int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
+                                           T* __restrict__ vol_sorted) {
+    constexpr int kR = 256;
+    constexpr int kPerWarp = 256;
+    constexpr int kChunk = NW * kPerWarp;
+    __shared__ int wc[NW][kR];
+    __shared__ int run[kR];
+    __shared__ int shw[32];
+    __shared__ int s_min, s_max;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // id range of the cell
+    int lo = 0x7fffffff, hi = 0;
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        const int v = buf0[s + i];
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (threadIdx.x == 0) {
+        s_min = 0x7fffffff;
+        s_max = 0;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        atomicMin(&s_min, lo);
+        atomicMax(&s_max, hi);
+    }
+    __syncthreads();
+    const int vmin = s_min;
+    const unsigned span = (unsigned)(s_max - vmin);
+    int passes = 0;
+    while (passes < 4 && (span >> (8 * passes)) != 0u) ++passes;
+    int32_t* in = buf0;
+    int32_t* out = buf1;
+    const unsigned lt = lanemask_lt();
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = 8 * ps;
+        for (int i = threadIdx.x; i < kR; i += blockDim.x) run[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < c; i += blockDim.x)
+            atomicAdd(&run[((unsigned)(in[s + i] - vmin) >> shift) & (kR - 1)], 1);
+        __syncthreads();
+        {
+            int tot;
+            const int v = threadIdx.x < kR ? run[threadIdx.x] : 0;
+            const int ex = block_exclusive_scan(v, shw, tot);
+            if (threadIdx.x < kR) run[threadIdx.x] = ex;
+        }
+        __syncthreads();
+        for (int base = 0; base < c; base += kChunk) {
+            for (int i = threadIdx.x; i < NW * kR; i += blockDim.x) (&wc[0][0])[i] = 0;
+            __syncthreads();
+            int dv[kPerWarp / 32], vv[kPerWarp / 32], rk[kPerWarp / 32];
+#pragma unroll
+            for (int k = 0; k < kPerWarp / 32; ++k) {
+                const int e = base + warp * kPerWarp + k * 32 + lane;
+                const bool valid = e < c;
+                vv[k] = valid ? in[s + e] : 0;
+                const int d = valid ? (int)(((unsigned)(vv[k] - vmin) >> shift) & (kR - 1)) : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int before = __popc(peers & lt);
+                const int c0 = valid ? wc[warp][d] : 0;
+                __syncwarp();
+                if (valid && before == 0) wc[warp][d] = c0 + __popc(peers);
+                __syncwarp();
+                rk[k] = c0 + before;
+                dv[k] = d;
+            }
+            __syncthreads();
+            // per digit: the warps' offsets, from the digit's running start
+            for (int d = threadIdx.x; d < kR; d += blockDim.x) {
+                int r0 = run[d];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int t = wc[w][d];
+                    wc[w][d] = r0;
+                    r0 += t;
+                }
+                run[d] = r0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPerWarp / 32; ++k)
+                if (dv[k] >= 0) out[s + wc[warp][dv[k]] + rk[k]] = vv[k];
+            __syncthreads();
+        }
+        int32_t* t = in;
+        in = out;
+        out = t;
+    }
+    for (int i = threadIdx.x; i < c; i += blockDim.x)
+        emit_slot<T>(s + i, in[s + i], cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+    __syncthreads();   // the shared state is reused by the CTA's next cell
+}
+
+constexpr int kSegSortWarps = 8;     // warps of a segment-sort CTA
+constexpr int kGroupCells = 32;      // consecutive cells a CTA takes at a time
+constexpr int kStageIds = 8192;      // ids of a group staged in shared memory
+
+// The sort goes through groups of kGroupCells consecutive cells; CTA b takes
+// groups b, b + B, b + 2B, ... (B CTAs), so occupied groups spread over every
+// CTA even where the particles fill a small part of the grid.  Warp 0 first
+// checks 32 of the CTA's groups at once for particles, so empty groups cost
+// one lookup per 32.  A group of at most kStageIds ids is read into shared
+// memory with coalesced loads; each warp sorts cells of the group there
+// (one cell after another, in registers) and writes the sorted ids back;
+// then the whole CTA writes the group's outputs slot by slot (coalesced,
+// with the diameter gathers of all slots in flight together).  A larger
+// group's cells are sorted straight from global memory.  Cells of more than
+// kSegWarpMax particles are sorted by the whole CTA after the group.
+template <typename T>
+__device__ __forceinline__ void seg_sort_body(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp,
+                                              int32_t* alt, int32_t* __restrict__ perm,
+                                              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+                                              const T* __restrict__ vol, T* __restrict__ vol_sorted, Blk blk) {
+    __shared__ int s_ids[kStageIds];
+    __shared__ int s_cs[kGroupCells + 1];
+    __shared__ int s_big[kGroupCells];
+    __shared__ int s_nbig;
+    __shared__ unsigned s_mask;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ngroups = (nbulk + kGroupCells - 1) / kGroupCells;
+    for (long long gsup = blk.id; gsup < ngroups; gsup += 32 * blk.n) {
+        if (warp == 0) {
+            const long long gi = gsup + lane * blk.n;
+            bool ne = false;
+            if (gi < ngroups) {
+                const long long c0 = gi * kGroupCells;
+                const long long c1 = c0 + kGroupCells < nbulk ? c0 + kGroupCells : nbulk;
+                ne = __ldg(cell_start + c1) != __ldg(cell_start + c0);
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, ne);
+            if (lane == 0) s_mask = msk;
+        }
+        __syncthreads();
+        unsigned todo = s_mask;
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long c0 = (gsup + k * blk.n) * kGroupCells;
+            const int nc = (int)(c0 + kGroupCells < nbulk ? kGroupCells : nbulk - c0);
+            if (threadIdx.x <= nc) s_cs[threadIdx.x] = __ldg(cell_start + c0 + threadIdx.x);
+            if (threadIdx.x == 0) s_nbig = 0;
+            __syncthreads();
+            const long long s0 = s_cs[0];
+            const int m = s_cs[nc] - (int)s0;
+            const bool staged = m <= kStageIds;
+            if (staged) {
+                for (int i = threadIdx.x; i < m; i += blockDim.x) s_ids[i] = tmp[s0 + i];
+                __syncthreads();
+            }
+            for (int j = warp; j < nc; j += kSegSortWarps) {
+                const int a = s_cs[j] - (int)s0;
+                const int c = s_cs[j + 1] - s_cs[j];
+                const int cell = (int)(c0 + j);
+                int32_t* src = staged ? s_ids + a : tmp + s0 + a;
+                if (c == 0) continue;
+                if (c > kSegWarpMax) {
+                    if (lane == 0) s_big[atomicAdd(&s_nbig, 1)] = cell;
+                    if (staged)   // its slots are written by the CTA sort
+                        for (int e = lane; e < c; e += 32) src[e] = -1;
+                } else if (c <= 32) {
+                    warp_sort_cell<1, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+                } else if (c <= 64) {
+                    warp_sort_cell<2, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+                } else if (c <= 128) {
+                    warp_sort_cell<4, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+                } else {
+                    warp_sort_cell<8, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+                }
+            }
+            __syncthreads();
+            if (staged) {
+                constexpr int U = 4;
+                for (int i0 = threadIdx.x; i0 < m; i0 += U * blockDim.x) {
+                    int id[U];
+                    T d[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * blockDim.x;
+                        id[u] = i < m ? s_ids[i] : -1;
+                        if (id[u] >= 0) d[u] = __ldg(vol + id[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const long long slot = s0 + i0 + u * blockDim.x;
+                        if (id[u] >= 0) {
+                            perm[slot] = id[u];
+                            inv_perm[id[u]] = (int)slot;
+                            vol_sorted[slot] = d[u];
+                        }
+                    }
+                }
+            }
+            const int nbig = s_nbig;
+            for (int i = 0; i < nbig; ++i) {
+                const int cell = s_big[i];
+                const long long s = s0 + (s_cs[cell - c0] - s_cs[0]);
+                big_sort_cell<kSegSortWarps, T>(cell, s, s_cs[cell - c0 + 1] - s_cs[cell - c0], tmp, alt, perm,
+                                                key_sorted, inv_perm, vol, vol_sorted);
+            }
+            __syncthreads();   // the group's shared state is reused by the next one
+        }
+        __syncthreads();   // s_mask
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSegSortWarps * 32, 4)
+k_seg_sort(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp, int32_t* alt,
+           int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+           const T* __restrict__ vol, T* __restrict__ vol_sorted) {
+    seg_sort_body<T>(cell_start, nbulk, tmp, alt, perm, key_sorted, inv_perm, vol, vol_sorted, launch_blk());
+}
+
 static bool g_attr_done = false;
 
 static cg_status set_attrs() {
@@ -442,8 +817,8 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
     const long long nbulk = g->gd.nbulk;
     const int np = g->npasses;
     const int b0 = g->pass_bits[0];
-    CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
-              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill);
+    CG_LAUNCH(g, "bin_key", (k_bin_key<T, false>), ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
+              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, nullptr);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
     // pass p reads (keys, ids) from in[p] and writes them to in[p + 1]; the
     // last pass writes the final order
@@ -478,6 +853,23 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
                       (const T*)nullptr, (T*)nullptr);
         shift += bits;
     }
+    return CG_OK;
+}
+
+// Default sort: key + arrival rank, scan of the counts (two launches),
+// placement, per-cell sort.
+template <typename T>
+static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, double* eps_fill, T* rec_fill,
+                          T* eps_t_fill) {
+    const long long nbulk = g->gd.nbulk;
+    CG_LAUNCH(g, "bin_key", (k_bin_key<T, true>), ntiles, kSortThreads, 0, pos, n, g->gd, g->key, g->cell_start,
+              g->hist, ntiles, 0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, g->key2);
+    CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, nullptr, nullptr, 0));
+    const long long pb = std::min<long long>((n + 511) / 512, (long long)g->num_sms * 8);
+    CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, g->cell_start, n, g->val1);
+    const long long sb = std::min<long long>((nbulk + kGroupCells - 1) / kGroupCells, (long long)g->num_sms * 4);
+    CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<T>, (unsigned)sb, kSegSortWarps * 32, 0, g->cell_start, nbulk, g->val1,
+              g->key1, g->perm, g->key_sorted, g->inv_perm, (const T*)g->vol, (T*)g->vol_sorted);
     return CG_OK;
 }
 
@@ -587,6 +979,17 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     }
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
     const long long m0 = (long long)ntiles << g->pass_bits[0];
+    if (use_cell_sort(g->desc.sort_digits, n)) {
+        if (g->fp64)
+            CG_TRY(bin_rank<double>(g, n, (const double*)pos_d, ntiles, eps_fill, (double*)rec_fill,
+                                    (double*)eps_t_fill));
+        else
+            CG_TRY(bin_rank<float>(g, n, (const float*)pos_d, ntiles, eps_fill, (float*)rec_fill,
+                                   (float*)eps_t_fill));
+        g->n_binned = n;
+        g->vol_valid = true;
+        return CG_OK;
+    }
     for (int p = 0; p < g->npasses; ++p)
         if (((long long)ntiles << g->pass_bits[p]) > g->hist_cap) return CG_ERR_OUT_OF_RANGE;
 

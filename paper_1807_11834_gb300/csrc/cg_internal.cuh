@@ -39,6 +39,13 @@ inline int split_passes(int bits, int (&pb)[kMaxPasses], int digits = 0) {
     return np;
 }
 
+// cg_grid_desc.sort_digits: automatic, per-cell sort, or a digit width.
+inline bool sort_choice_valid(int v) { return v == CG_SORT_AUTO || v == CG_SORT_CELLS || (v >= 6 && v <= kMaxDigitBits); }
+// The per-cell sort serves a call of n particles.
+inline bool use_cell_sort(int v, long long n) {
+    return v == CG_SORT_CELLS || (v == CG_SORT_AUTO && n <= CG_SORT_CELLS_AUTO_MAX);
+}
+
 // Dynamic shared memory of a sort scatter pass with 2^bits digits: the
 // per-warp counters, or the staged tile (key, id, diameter of T), whichever
 // is larger, plus two [2^bits] int arrays.

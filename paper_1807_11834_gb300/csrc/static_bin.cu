@@ -103,7 +103,7 @@ extern "C" cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n
         if (nb[a] < 2) return CG_ERR_INVALID_ARG;
         nbulk *= nb[a];
     }
-    if (d.sort_digits != 0 && (d.sort_digits < 6 || d.sort_digits > cg::kMaxDigitBits)) return CG_ERR_INVALID_ARG;
+    if (!cg::sort_choice_valid(d.sort_digits)) return CG_ERR_INVALID_ARG;
     if (nbulk > (1LL << cg::kMaxBulkBits)) return CG_ERR_OUT_OF_RANGE;
 
     void* base = nullptr;
@@ -136,7 +136,7 @@ extern "C" cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n
     int bits = 0;
     while ((1LL << bits) < nbulk) ++bits;
     bits = std::max(bits, 1);
-    g.npasses = cg::split_passes(bits, g.pass_bits, d.sort_digits);
+    g.npasses = cg::split_passes(bits, g.pass_bits, d.sort_digits >= 6 ? d.sort_digits : 0);
     g.key = (int32_t*)(s + kOffKey);
     g.key1 = (int32_t*)(s + kOffKey1);
     g.val1 = (int32_t*)(s + kOffVal1);

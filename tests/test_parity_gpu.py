@@ -239,10 +239,10 @@ def test_clustered_bed_100_steps_conservation_drift(cuda_lib):
     assert torch.isfinite(pos).all()
 
 
-@pytest.mark.parametrize("digits", [6, 7, 9, 11])
+@pytest.mark.parametrize("digits", [1, 6, 7, 9, 11])
 def test_sort_digit_width_does_not_change_bins(cuda_lib, digits):
-    """One, two or three passes of any digit width give the same stable
-    order (and so the same fields) as the oracle."""
+    """The per-cell sort (1) and one, two or three passes of any digit width
+    give the same stable order (and so the same fields) as the oracle."""
     import torch
     w = synth.small_clustered_bed(seed=6)
     ref_cell, ref_perm, ref_cs, _ = oracle.bin(w.desc, w.pos_d)
@@ -258,6 +258,77 @@ def test_sort_digit_width_does_not_change_bins(cuda_lib, digits):
     assert np.array_equal(to_np(perm), ref_perm)
     assert np.array_equal(to_np(cs), ref_cs)
     g.close()
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_cells_of_every_sort_size_class(cuda_lib, fp64):
+    """Cells holding 1 to 9,000 particles in shuffled order: every size class
+    of the default per-cell sort (one element, the warp sorts of 32, 64, 128
+    and 256, the CTA sort of larger cells with one to three 4096-id chunks)
+    and both sides of each boundary give the oracle's stable order, as does
+    the digit sort."""
+    import torch
+    w = synth.tiny(seed=4, n=1, fine=64, ratio=4, fp64=fp64)
+    rng = np.random.default_rng(11)
+    sizes = [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 1000, 4095, 4096, 4097, 9000]
+    cells = rng.choice(16 ** 3, size=len(sizes), replace=False)
+    H = 1.0 / 16
+    parts = []
+    for c, m in zip(cells, sizes):
+        ijk = np.array([c % 16, (c // 16) % 16, c // 256], dtype=np.float64)
+        parts.append((ijk + 0.05 + 0.9 * rng.random((m, 3))) * H)
+    parts.append(rng.random((5000, 3)))
+    xyz = np.concatenate(parts)[rng.permutation(sum(sizes) + 5000)]
+    pos = np.empty((len(xyz), 4), dtype=w.pos_d.dtype)
+    pos[:, :3] = xyz
+    pos[:, 3] = 0.002
+    ref_cell, ref_perm, ref_cs, _ = oracle.bin(w.desc, pos)
+    counts = np.diff(ref_cs)
+    assert all(counts[c] >= m for c, m in zip(cells, sizes))
+    for digits in (cuda_lib.CG_SORT_CELLS, 8):
+        d = dict(w.desc)
+        d["sort_digits"] = digits
+        g = cuda_lib.Grids(d)
+        p = to_dev(pos)
+        cell = torch.empty(len(pos), dtype=torch.int32, device="cuda")
+        perm = torch.empty(len(pos), dtype=torch.int32, device="cuda")
+        cs = torch.empty(g.n_bulk + 1, dtype=torch.int32, device="cuda")
+        g.cg_bin_particles(p, cell, perm, cs)
+        assert np.array_equal(to_np(cell), ref_cell), digits
+        assert np.array_equal(to_np(cs), ref_cs), digits
+        assert np.array_equal(to_np(perm), ref_perm), digits
+        g.close()
+
+
+def test_both_sorts_agree_at_full_clustered_size(cuda_lib):
+    """32M particles in random order: the per-cell sort (beyond the size it
+    is picked for automatically) gives the digit sort's bins, and the
+    automatic choice the same again."""
+    import torch
+    w = synth.clustered_bed(seed=1)
+    pos = to_dev(w.pos_d)
+    got = []
+    for digits in (cuda_lib.CG_SORT_CELLS, 8, cuda_lib.CG_SORT_AUTO):
+        d = dict(w.desc)
+        d["sort_digits"] = digits
+        g = cuda_lib.Grids(d)
+        cell = torch.empty(w.n, dtype=torch.int32, device="cuda")
+        perm = torch.empty(w.n, dtype=torch.int32, device="cuda")
+        cs = torch.empty(g.n_bulk + 1, dtype=torch.int32, device="cuda")
+        g.cg_bin_particles(pos, cell, perm, cs)
+        torch.cuda.synchronize()
+        got.append((cell, perm, cs))
+        g.close()
+    for other in got[1:]:
+        for a, b in zip(got[0], other):
+            assert torch.equal(a, b)
+    # the order is a permutation sorted by cell, ids ascending within a cell
+    cell, perm, cs = got[0]
+    ks = cell[perm.long()]
+    assert bool((ks[1:] >= ks[:-1]).all())
+    same = ks[1:] == ks[:-1]
+    assert bool((perm[1:][same] > perm[:-1][same]).all())
+    assert int(cs[-1]) == w.n
 
 
 def test_repeat_is_bit_identical(cuda_lib):
@@ -393,3 +464,9 @@ def test_not_binned_and_bad_args(cuda_lib):
     # misaligned particle array
     assert L.cg_bin_particles(g.h, 10, pos.data_ptr() + 4, None, None, None) == 1
     g.close()
+    # sort choices other than automatic, per-cell and digit widths 6..11
+    for bad in (-1, 2, 5, 12):
+        d = dict(w.desc)
+        d["sort_digits"] = bad
+        with pytest.raises(cuda_lib.CgError):
+            cuda_lib.Grids(d)
