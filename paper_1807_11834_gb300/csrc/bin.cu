@@ -48,22 +48,16 @@ __device__ __forceinline__ void add_status(unsigned long long* st, int outside, 
 // Key kernel: cell per particle, per-cell counts, tile histogram of digit 0
 // ----------------------------------------------------------------------
 
-// RANK (the default sort): no digit histogram; instead every particle keeps
-// its arrival rank within its cell (the value the count atomic returned).
-// The thread's count atomics are issued together, after all its cells are
-// known, so their round trips overlap.
-template <typename T, bool RANK = false>
+template <typename T>
 __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long long n, const GridDev& g,
                                              int32_t* __restrict__ key, int32_t* __restrict__ count,
                                              int32_t* __restrict__ hist, int ntiles, int bits0, T* __restrict__ vol,
                                              unsigned long long* __restrict__ status, int* sh, Blk blk,
                                              double* __restrict__ eps_fill = nullptr, T* __restrict__ rec_fill = nullptr,
-                                             T* __restrict__ eps_t_fill = nullptr,
-                                             int32_t* __restrict__ arrival = nullptr) {
+                                             T* __restrict__ eps_t_fill = nullptr) {
     __shared__ int s_cnt[2];
     const int R = 1 << bits0;
-    if (!RANK)
-        for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) sh[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     int n_out = 0, n_nf = 0;
@@ -75,7 +69,6 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
         if (p < n) pv[k] = ld4(pos, p);
     }
-    int ck[kSortItems], lk[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         long long p = base + (long long)k * kSortThreads + threadIdx.x;
@@ -93,34 +86,15 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         // counts: one integer atomic per run of equal cells in the warp
         // (spatially ordered input has runs of several particles)
         const int len = run_head_length(c, valid);
-        ck[k] = c;
-        lk[k] = len;
-        if (!RANK && len) {
+        if (len) {
             atomicAdd(&count[c], len);
             atomicAdd(&sh[c & (R - 1)], len);
-        }
-    }
-    if (RANK) {
-        int old[kSortItems];
-#pragma unroll
-        for (int k = 0; k < kSortItems; ++k) old[k] = lk[k] ? atomicAdd(&count[ck[k]], lk[k]) : 0;
-        // the run's head took len slots of the cell's arrival order; every
-        // member finds its head (the last head at or below it)
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int k = 0; k < kSortItems; ++k) {
-            const long long p = base + (long long)k * kSortThreads + threadIdx.x;
-            const unsigned heads = __ballot_sync(0xffffffffu, lk[k] != 0);
-            const int head = 31 - __clz(heads & ((2u << lane) - 1u));
-            const int o = __shfl_sync(0xffffffffu, old[k], head < 0 ? 0 : head);
-            if (p < n) arrival[p] = o + lane - head;
         }
     }
     if (n_out) atomicAdd(&s_cnt[0], n_out);
     if (n_nf) atomicAdd(&s_cnt[1], n_nf);
     __syncthreads();
-    if (!RANK)
-        for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) hist[(long long)i * ntiles + blk.id] = sh[i];
     if (threadIdx.x == 0) add_status(status, s_cnt[0], s_cnt[1]);
     // the porosity of cells without particles is 1: set every cell here (and
     // the porosity of the drag record and of its path-precision copy), the
@@ -133,15 +107,84 @@ __device__ __forceinline__ void bin_key_body(const T* __restrict__ pos, long lon
         }
 }
 
-template <typename T, bool RANK>
+template <typename T>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
           int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
           T* __restrict__ vol, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
-          T* __restrict__ rec_fill, T* __restrict__ eps_t_fill, int32_t* __restrict__ arrival) {
+          T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
     extern __shared__ int sh[];
-    bin_key_body<T, RANK>(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill,
-                          rec_fill, eps_t_fill, arrival);
+    bin_key_body<T>(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill, rec_fill,
+                    eps_t_fill);
+}
+
+// Key kernel of the per-cell sort: cell, diameter and arrival rank of every
+// particle, per-cell counts, porosity fill.  No shared memory and no block
+// barrier; four particles per thread, consecutive lanes on consecutive
+// particles (so runs of equal cells share one count atomic), and the
+// thread's count atomics issued together so their round trips overlap.
+constexpr int kKeyThreads = 256;
+constexpr int kKeyItems = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kKeyThreads, 5)
+k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
+               int32_t* __restrict__ count, T* __restrict__ vol, unsigned long long* __restrict__ status,
+               double* __restrict__ eps_fill, T* __restrict__ rec_fill, T* __restrict__ eps_t_fill,
+               int32_t* __restrict__ arrival) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long base = (long long)blockIdx.x * (kKeyThreads * kKeyItems);
+    V4<T> pv[kKeyItems];
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) {
+        const long long p = base + k * kKeyThreads + threadIdx.x;
+        if (p < n) pv[k] = ld4(pos, p);
+    }
+    int n_out = 0, n_nf = 0;
+    int ck[kKeyItems], lk[kKeyItems], old[kKeyItems];
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) {
+        const long long p = base + k * kKeyThreads + threadIdx.x;
+        const bool valid = p < n;
+        int c = -1;
+        if (valid) {
+            const V4<T>& v = pv[k];
+            int outside = 0;
+            if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
+            c = cell_of(v, g, outside);
+            n_out += outside;
+            key[p] = c;
+            vol[p] = v.w;   // the diameter: the porosity forms the volume as an exact pair
+        }
+        ck[k] = c;
+        lk[k] = run_head_length(c, valid);
+    }
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) old[k] = lk[k] ? atomicAdd(&count[ck[k]], lk[k]) : 0;
+    // the run's head took len slots of the cell's arrival order; every
+    // member finds its head (the last head at or below it)
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) {
+        const long long p = base + k * kKeyThreads + threadIdx.x;
+        const unsigned heads = __ballot_sync(full, lk[k] != 0);
+        const int head = 31 - __clz(heads & ((2u << lane) - 1u));
+        const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
+        if (p < n) arrival[p] = o + lane - head;
+    }
+    n_out = __reduce_add_sync(full, n_out);
+    n_nf = __reduce_add_sync(full, n_nf);
+    if (lane == 0 && (n_out | n_nf)) add_status(status, n_out, n_nf);
+    // the porosity of cells without particles is 1: set every cell here (and
+    // the porosity of the drag record and of its path-precision copy), the
+    // deposit overwrites the occupied ones
+    if (eps_fill)
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.nbulk;
+             c += (long long)gridDim.x * blockDim.x) {
+            eps_fill[c] = 1.0;
+            if (rec_fill) rec_fill[4 * c] = T(1);
+            if (eps_t_fill) eps_t_fill[c] = T(1);
+        }
 }
 
 // Tile histogram of a digit of already-computed keys (second pass).
@@ -471,12 +514,30 @@ static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA,
 // ----------------------------------------------------------------------
 constexpr int kSegWarpMax = 256;   // largest cell a warp sorts in registers
 
+// Four particles per thread, consecutive lanes on consecutive particles
+// (so runs of one cell's arrivals store to consecutive slots), with the
+// thread's four loads, gathers and stores each in flight together.
 __device__ __forceinline__ void place_body(const int32_t* __restrict__ key, const int32_t* __restrict__ arrival,
                                            const int32_t* __restrict__ cell_start, long long n,
                                            int32_t* __restrict__ tmp, Blk blk) {
-    const long long stride = blk.n * (long long)blockDim.x;
-    for (long long p = blk.id * blockDim.x + threadIdx.x; p < n; p += stride)
-        tmp[__ldg(cell_start + __ldg(key + p)) + __ldg(arrival + p)] = (int)p;
+    constexpr int U = 4;
+    const long long span = (long long)blockDim.x * U;
+    for (long long b0 = blk.id * span; b0 < n; b0 += blk.n * span) {
+        int kk[U], aa[U], st[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const long long p = b0 + j * blockDim.x + threadIdx.x;
+            kk[j] = p < n ? __ldg(key + p) : 0;
+            aa[j] = p < n ? __ldg(arrival + p) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) st[j] = __ldg(cell_start + kk[j]);
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const long long p = b0 + j * blockDim.x + threadIdx.x;
+            if (p < n) tmp[st[j] + aa[j]] = (int)p;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(512) k_bin_place(const int32_t* __restrict__ key,
@@ -563,49 +624,32 @@ __device__ __forceinline__ void warp_sort_cell(int32_t* src, bool staged, long l
     }
 }
 
-// One CTA sorts the ids of one large cell: passes of 8-bit digits of
-// (id - min id), each a histogram, a scan, and a stable scatter of chunks of
-// NW * 256 ids in order (warp w ranks its 256 ids of the chunk in index order
-// with match_any, as the tile sort does).  Ids move between buf0 and buf1
-// (the same slots of two arrays); the result is read from whichever holds
-// the last pass.  Static shared memory: NW KB + 1.2 KB.
-template <int NW, typename T>
-__device__ __noinline__ void big_sort_cell(int cell, long long s, int c, int32_t* buf0, int32_t* buf1,
+// One warp sorts the ids of a cell larger than kSegWarpMax: passes of 8-bit
+// digits of (id - min id), each a histogram, a scan of the 256 digit counts,
+// and a stable scatter that walks the ids 32 at a time in index order (rank
+// within a digit by match_any, running digit starts in shared memory).  Ids
+// move between buf0 and buf1 (the same slots of two arrays); the outputs
+// are written from whichever holds the last pass.  sm: 256 ints of the
+// warp's shared memory.
+template <typename T>
+__device__ __noinline__ void warp_big_sort(int cell, long long s, int c, int32_t* buf0, int32_t* buf1, int* sm,
                                            int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
                                            int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
                                            T* __restrict__ vol_sorted) {
-    constexpr int kR = 256;
-    constexpr int kPerWarp = 256;
-    constexpr int kChunk = NW * kPerWarp;
-    __shared__ int wc[NW][kR];
-    __shared__ int run[kR];
-    __shared__ int shw[32];
-    __shared__ int s_min, s_max;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // id range of the cell
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     int lo = 0x7fffffff, hi = 0;
-    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    for (int i = lane; i < c; i += 32) {
         const int v = buf0[s + i];
         lo = min(lo, v);
         hi = max(hi, v);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        lo = min(lo, __shfl_xor_sync(full, lo, off));
+        hi = max(hi, __shfl_xor_sync(full, hi, off));
     }
-    if (threadIdx.x == 0) {
-        s_min = 0x7fffffff;
-        s_max = 0;
-    }
-    __syncthreads();
-    if (lane == 0) {
-        atomicMin(&s_min, lo);
-        atomicMax(&s_max, hi);
-    }
-    __syncthreads();
-    const int vmin = s_min;
-    const unsigned span = (unsigned)(s_max - vmin);
+    const unsigned span = (unsigned)(hi - lo);
     int passes = 0;
     while (passes < 4 && (span >> (8 * passes)) != 0u) ++passes;
     int32_t* in = buf0;
@@ -613,129 +657,115 @@ __device__ __noinline__ void big_sort_cell(int cell, long long s, int c, int32_t
     const unsigned lt = lanemask_lt();
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
-        for (int i = threadIdx.x; i < kR; i += blockDim.x) run[i] = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < c; i += blockDim.x)
-            atomicAdd(&run[((unsigned)(in[s + i] - vmin) >> shift) & (kR - 1)], 1);
-        __syncthreads();
-        {
-            int tot;
-            const int v = threadIdx.x < kR ? run[threadIdx.x] : 0;
-            const int ex = block_exclusive_scan(v, shw, tot);
-            if (threadIdx.x < kR) run[threadIdx.x] = ex;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sm[lane * 8 + j] = 0;
+        __syncwarp();
+        for (int i = lane; i < c; i += 32) atomicAdd(&sm[((unsigned)(in[s + i] - lo) >> shift) & 255u], 1);
+        __syncwarp();
+        // exclusive scan of the 256 counts: 8 consecutive digits per lane
+        int cnt[8], tot = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            cnt[j] = sm[lane * 8 + j];
+            tot += cnt[j];
         }
-        __syncthreads();
-        for (int base = 0; base < c; base += kChunk) {
-            for (int i = threadIdx.x; i < NW * kR; i += blockDim.x) (&wc[0][0])[i] = 0;
-            __syncthreads();
-            int dv[kPerWarp / 32], vv[kPerWarp / 32], rk[kPerWarp / 32];
+        int x = tot;
 #pragma unroll
-            for (int k = 0; k < kPerWarp / 32; ++k) {
-                const int e = base + warp * kPerWarp + k * 32 + lane;
-                const bool valid = e < c;
-                vv[k] = valid ? in[s + e] : 0;
-                const int d = valid ? (int)(((unsigned)(vv[k] - vmin) >> shift) & (kR - 1)) : -1;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const int before = __popc(peers & lt);
-                const int c0 = valid ? wc[warp][d] : 0;
-                __syncwarp();
-                if (valid && before == 0) wc[warp][d] = c0 + __popc(peers);
-                __syncwarp();
-                rk[k] = c0 + before;
-                dv[k] = d;
-            }
-            __syncthreads();
-            // per digit: the warps' offsets, from the digit's running start
-            for (int d = threadIdx.x; d < kR; d += blockDim.x) {
-                int r0 = run[d];
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const int t = wc[w][d];
-                    wc[w][d] = r0;
-                    r0 += t;
-                }
-                run[d] = r0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < kPerWarp / 32; ++k)
-                if (dv[k] >= 0) out[s + wc[warp][dv[k]] + rk[k]] = vv[k];
-            __syncthreads();
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(full, x, off);
+            if (lane >= off) x += y;
         }
+        int run = x - tot;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sm[lane * 8 + j] = run;
+            run += cnt[j];
+        }
+        __syncwarp();
+        for (int base = 0; base < c; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < c;
+            const int v = valid ? in[s + e] : 0;
+            const int d = valid ? (int)(((unsigned)(v - lo) >> shift) & 255u) : -1;
+            const unsigned peers = __match_any_sync(full, d);
+            const int before = __popc(peers & lt);
+            const int start = valid ? sm[d] : 0;
+            __syncwarp();
+            if (valid && before == 0) sm[d] = start + __popc(peers);
+            __syncwarp();
+            if (valid) out[s + start + before] = v;
+        }
+        __syncwarp();
         int32_t* t = in;
         in = out;
         out = t;
     }
-    for (int i = threadIdx.x; i < c; i += blockDim.x)
-        emit_slot<T>(s + i, in[s + i], cell, perm, key_sorted, inv_perm, vol, vol_sorted);
-    __syncthreads();   // the shared state is reused by the CTA's next cell
+    for (int i = lane; i < c; i += 32) emit_slot<T>(s + i, in[s + i], cell, perm, key_sorted, inv_perm, vol, vol_sorted);
+    __syncwarp();
 }
 
 constexpr int kSegSortWarps = 8;     // warps of a segment-sort CTA
-constexpr int kGroupCells = 32;      // consecutive cells a CTA takes at a time
-constexpr int kStageIds = 8192;      // ids of a group staged in shared memory
+constexpr int kGroupCells = 8;       // consecutive cells a warp takes at a time
+constexpr int kWarpStage = 1024;     // ids of a group staged in the warp's shared memory
 
-// The sort goes through groups of kGroupCells consecutive cells; CTA b takes
-// groups b, b + B, b + 2B, ... (B CTAs), so occupied groups spread over every
-// CTA even where the particles fill a small part of the grid.  Warp 0 first
-// checks 32 of the CTA's groups at once for particles, so empty groups cost
-// one lookup per 32.  A group of at most kStageIds ids is read into shared
-// memory with coalesced loads; each warp sorts cells of the group there
-// (one cell after another, in registers) and writes the sorted ids back;
-// then the whole CTA writes the group's outputs slot by slot (coalesced,
-// with the diameter gathers of all slots in flight together).  A larger
-// group's cells are sorted straight from global memory.  Cells of more than
-// kSegWarpMax particles are sorted by the whole CTA after the group.
+// Each warp goes through groups of kGroupCells consecutive cells on its
+// own (no CTA-wide barrier): warp w of nw takes groups w, w + nw, w + 2nw,
+// ..., so occupied groups spread over every warp even where the particles
+// fill a small part of the grid; lane l first checks group w + l nw (of the
+// next 32) for particles, so empty groups cost one lookup per 32.  A group
+// of at most kWarpStage ids is read into the warp's shared memory with
+// coalesced loads; the warp sorts its cells there one after another (in
+// registers) and writes them back, then writes the group's outputs slot by
+// slot (coalesced, with the diameter gathers of the lane's slots in flight
+// together).  A larger group's cells are sorted straight from global
+// memory.  Cells of more than kSegWarpMax particles are sorted by
+// warp_big_sort after the group's other cells are written.
 template <typename T>
 __device__ __forceinline__ void seg_sort_body(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp,
                                               int32_t* alt, int32_t* __restrict__ perm,
                                               int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
                                               const T* __restrict__ vol, T* __restrict__ vol_sorted, Blk blk) {
-    __shared__ int s_ids[kStageIds];
-    __shared__ int s_cs[kGroupCells + 1];
-    __shared__ int s_big[kGroupCells];
-    __shared__ int s_nbig;
-    __shared__ unsigned s_mask;
+    __shared__ int s_stage[kSegSortWarps][kWarpStage];
+    const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* stage = s_stage[warp];
+    const long long nw = blk.n * kSegSortWarps;
+    const long long w = blk.id * kSegSortWarps + warp;
     const long long ngroups = (nbulk + kGroupCells - 1) / kGroupCells;
-    for (long long gsup = blk.id; gsup < ngroups; gsup += 32 * blk.n) {
-        if (warp == 0) {
-            const long long gi = gsup + lane * blk.n;
-            bool ne = false;
+    for (long long gsup = w; gsup < ngroups; gsup += 32 * nw) {
+        bool ne = false;
+        {
+            const long long gi = gsup + lane * nw;
             if (gi < ngroups) {
                 const long long c0 = gi * kGroupCells;
                 const long long c1 = c0 + kGroupCells < nbulk ? c0 + kGroupCells : nbulk;
                 ne = __ldg(cell_start + c1) != __ldg(cell_start + c0);
             }
-            const unsigned msk = __ballot_sync(0xffffffffu, ne);
-            if (lane == 0) s_mask = msk;
         }
-        __syncthreads();
-        unsigned todo = s_mask;
+        unsigned todo = __ballot_sync(full, ne);
         while (todo) {
             const int k = __ffs(todo) - 1;
             todo &= todo - 1;
-            const long long c0 = (gsup + k * blk.n) * kGroupCells;
+            const long long c0 = (gsup + k * nw) * kGroupCells;
             const int nc = (int)(c0 + kGroupCells < nbulk ? kGroupCells : nbulk - c0);
-            if (threadIdx.x <= nc) s_cs[threadIdx.x] = __ldg(cell_start + c0 + threadIdx.x);
-            if (threadIdx.x == 0) s_nbig = 0;
-            __syncthreads();
-            const long long s0 = s_cs[0];
-            const int m = s_cs[nc] - (int)s0;
-            const bool staged = m <= kStageIds;
+            const int csl = lane <= nc ? __ldg(cell_start + c0 + lane) : 0;   // lane j: start of cell j
+            const int s0 = __shfl_sync(full, csl, 0);
+            const int m = __shfl_sync(full, csl, nc) - s0;
+            const bool staged = m <= kWarpStage;
             if (staged) {
-                for (int i = threadIdx.x; i < m; i += blockDim.x) s_ids[i] = tmp[s0 + i];
-                __syncthreads();
+                for (int i = lane; i < m; i += 32) stage[i] = tmp[(long long)s0 + i];
+                __syncwarp();
             }
-            for (int j = warp; j < nc; j += kSegSortWarps) {
-                const int a = s_cs[j] - (int)s0;
-                const int c = s_cs[j + 1] - s_cs[j];
+            unsigned bigs = 0;
+            for (int j = 0; j < nc; ++j) {
+                const int a = __shfl_sync(full, csl, j) - s0;
+                const int c = __shfl_sync(full, csl, j + 1) - s0 - a;
                 const int cell = (int)(c0 + j);
-                int32_t* src = staged ? s_ids + a : tmp + s0 + a;
+                int32_t* src = staged ? stage + a : tmp + s0 + a;
                 if (c == 0) continue;
                 if (c > kSegWarpMax) {
-                    if (lane == 0) s_big[atomicAdd(&s_nbig, 1)] = cell;
-                    if (staged)   // its slots are written by the CTA sort
+                    bigs |= 1u << j;
+                    if (staged)   // its slots are written by warp_big_sort
                         for (int e = lane; e < c; e += 32) src[e] = -1;
                 } else if (c <= 32) {
                     warp_sort_cell<1, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
@@ -747,21 +777,21 @@ __device__ __forceinline__ void seg_sort_body(const int32_t* __restrict__ cell_s
                     warp_sort_cell<8, T>(src, staged, s0 + a, c, cell, perm, key_sorted, inv_perm, vol, vol_sorted);
                 }
             }
-            __syncthreads();
+            __syncwarp();
             if (staged) {
                 constexpr int U = 4;
-                for (int i0 = threadIdx.x; i0 < m; i0 += U * blockDim.x) {
+                for (int i0 = lane; i0 < m; i0 += U * 32) {
                     int id[U];
                     T d[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int i = i0 + u * blockDim.x;
-                        id[u] = i < m ? s_ids[i] : -1;
+                        const int i = i0 + u * 32;
+                        id[u] = i < m ? stage[i] : -1;
                         if (id[u] >= 0) d[u] = __ldg(vol + id[u]);
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const long long slot = s0 + i0 + u * blockDim.x;
+                        const long long slot = (long long)s0 + i0 + u * 32;
                         if (id[u] >= 0) {
                             perm[slot] = id[u];
                             inv_perm[id[u]] = (int)slot;
@@ -769,17 +799,16 @@ __device__ __forceinline__ void seg_sort_body(const int32_t* __restrict__ cell_s
                         }
                     }
                 }
+                __syncwarp();
             }
-            const int nbig = s_nbig;
-            for (int i = 0; i < nbig; ++i) {
-                const int cell = s_big[i];
-                const long long s = s0 + (s_cs[cell - c0] - s_cs[0]);
-                big_sort_cell<kSegSortWarps, T>(cell, s, s_cs[cell - c0 + 1] - s_cs[cell - c0], tmp, alt, perm,
-                                                key_sorted, inv_perm, vol, vol_sorted);
+            while (bigs) {
+                const int j = __ffs(bigs) - 1;
+                bigs &= bigs - 1;
+                const int a = __shfl_sync(full, csl, j);
+                const int c = __shfl_sync(full, csl, j + 1) - a;
+                warp_big_sort<T>((int)(c0 + j), a, c, tmp, alt, stage, perm, key_sorted, inv_perm, vol, vol_sorted);
             }
-            __syncthreads();   // the group's shared state is reused by the next one
         }
-        __syncthreads();   // s_mask
     }
 }
 
@@ -817,8 +846,8 @@ static cg_status bin_passes(cg_grids* g, long long n, const T* pos, int ntiles, 
     const long long nbulk = g->gd.nbulk;
     const int np = g->npasses;
     const int b0 = g->pass_bits[0];
-    CG_LAUNCH(g, "bin_key", (k_bin_key<T, false>), ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
-              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, nullptr);
+    CG_LAUNCH(g, "bin_key", k_bin_key<T>, ntiles, kSortThreads, sizeof(int) << b0, pos, n, g->gd, g->key,
+              g->cell_start, g->hist, ntiles, b0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, g->hist, g->hist, m0));
     // pass p reads (keys, ids) from in[p] and writes them to in[p + 1]; the
     // last pass writes the final order
@@ -862,12 +891,14 @@ template <typename T>
 static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, double* eps_fill, T* rec_fill,
                           T* eps_t_fill) {
     const long long nbulk = g->gd.nbulk;
-    CG_LAUNCH(g, "bin_key", (k_bin_key<T, true>), ntiles, kSortThreads, 0, pos, n, g->gd, g->key, g->cell_start,
-              g->hist, ntiles, 0, (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, g->key2);
+    const long long kb = (n + kKeyThreads * kKeyItems - 1) / (kKeyThreads * kKeyItems);
+    CG_LAUNCH(g, "bin_key", k_bin_key_rank<T>, (unsigned)kb, kKeyThreads, 0, pos, n, g->gd, g->key, g->cell_start,
+              (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, g->key2);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, nullptr, nullptr, 0));
-    const long long pb = std::min<long long>((n + 511) / 512, (long long)g->num_sms * 8);
+    const long long pb = std::min<long long>((n + 2047) / 2048, (long long)g->num_sms * 4);
     CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, g->cell_start, n, g->val1);
-    const long long sb = std::min<long long>((nbulk + kGroupCells - 1) / kGroupCells, (long long)g->num_sms * 4);
+    const long long sb = std::min<long long>((nbulk + kGroupCells * kSegSortWarps - 1) / (kGroupCells * kSegSortWarps),
+                                             (long long)g->num_sms * 4);
     CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<T>, (unsigned)sb, kSegSortWarps * 32, 0, g->cell_start, nbulk, g->val1,
               g->key1, g->perm, g->key_sorted, g->inv_perm, (const T*)g->vol, (T*)g->vol_sorted);
     return CG_OK;
