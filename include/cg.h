@@ -74,6 +74,7 @@ enum {
 #define CG_SORT_AUTO 0
 #define CG_SORT_CELLS 1
 #define CG_SORT_CELLS_AUTO_MAX 8388608   /* 2^23 particles */
+#define CG_SORT_CELLS_AUTO_DENSITY 32   /* particles per bulk cell */
 
 /* Number of counters returned by cg_sync_status. */
 #define CG_NCOUNTS 5
@@ -91,13 +92,18 @@ enum {
  *               CG_SORT_CELLS (1): per-cell sort (counts, arrival ranks,
  *                 placement, then each cell's ids sorted); fastest when its
  *                 particle-sized arrays fit in L2 or the particle order keeps
- *                 neighbours close;
+ *                 neighbours close, and cells hold at most a few hundred
+ *                 particles (one warp sorts each larger cell);
  *               6..11: least-significant-digit sort with digits of at most
- *                 that many bits (two or three passes); fastest for large
- *                 particle sets in random order;
- *               CG_SORT_AUTO (0): per-cell sort up to CG_SORT_CELLS_AUTO_MAX
- *                 particles per call, above it the digit sort with digits of
- *                 up to 10 bits below 2^20 bulk cells, up to 8 from 2^20 on
+ *                 that many bits (one to three passes); fastest for large
+ *                 particle sets in random order and for crowded cells;
+ *               CG_SORT_AUTO (0): the per-cell sort for calls of at most
+ *                 CG_SORT_CELLS_AUTO_MAX particles and at most
+ *                 CG_SORT_CELLS_AUTO_DENSITY particles per bulk cell on
+ *                 average, else the digit sort with digits of up to 10 bits
+ *                 below 2^20 bulk cells, up to 8 from 2^20 on; an instance of
+ *                 a batch (cg_batch_create) takes the digit sort unless its
+ *                 descriptor asks for CG_SORT_CELLS
  * Limits: fine_n[a] % ratio == 0, bulk cells >= 2 per axis, at most 2^22
  * bulk cells and 2^31 - 1 fine cells. */
 typedef struct {

@@ -38,6 +38,7 @@ CG_NCOUNTS = 5
 CG_SORT_AUTO = 0
 CG_SORT_CELLS = 1
 CG_SORT_CELLS_AUTO_MAX = 1 << 23
+CG_SORT_CELLS_AUTO_DENSITY = 32
 SUM_NAMES = ["vol_particles", "vol_deposited", "F_x", "F_y", "F_z", "SbVb_x", "SbVb_y", "SbVb_z",
              "SfVf_x", "SfVf_y", "SfVf_z", "F_abs", "mom_x", "mom_y", "mom_z", "n_clamped"]
 

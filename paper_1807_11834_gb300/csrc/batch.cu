@@ -112,11 +112,16 @@ cg_status plan(cg_batch* b) {
         I.P = phys_of<float>(g->gd);
         I.n = n;
         I.ntiles = (int)cdiv(n, kSortTile);
+        // batched instances take the per-cell sort only when the descriptor
+        // asks for it: over a batch of instances in random order the digit
+        // sort measured faster (the per-cell sort's scattered placement and
+        // per-cell work add up across instances)
+        I.cellsort = g->desc.sort_digits == CG_SORT_CELLS ? 1 : 0;
         const int bits = std::max(1, ceil_log2_ll(nb));
-        if (bits > 2 * c.digit_bits) return CG_ERR_OUT_OF_RANGE;
-        I.npasses = bits <= c.digit_bits ? 1 : 2;
-        I.b0 = I.npasses == 1 ? bits : (bits + 1) / 2;
-        I.b1 = I.npasses == 1 ? 0 : bits - I.b0;
+        if (!I.cellsort && bits > 2 * c.digit_bits) return CG_ERR_OUT_OF_RANGE;
+        I.npasses = I.cellsort ? 0 : bits <= c.digit_bits ? 1 : 2;
+        I.b0 = I.cellsort ? 0 : I.npasses == 1 ? bits : (bits + 1) / 2;
+        I.b1 = I.npasses == 2 ? bits - I.b0 : 0;
         I.pos = (float*)it.particles.pos_d;
         I.vel = (float*)it.particles.vel;
         I.u_fine = (const float*)it.u_fine;
@@ -132,6 +137,7 @@ cg_status plan(cg_batch* b) {
         I.count = g->cell_start;
         I.key1 = g->key1;
         I.val1 = g->val1;
+        I.arrival = g->key2;
         I.perm = g->perm;
         I.key_sorted = g->key_sorted;
         I.inv_perm = g->inv_perm;
@@ -142,7 +148,8 @@ cg_status plan(cg_batch* b) {
         I.eps_t = (float*)g->eps_t;
         I.status = g->status;
         // batch-owned scratch: digit histograms, scan partials, sum partials
-        const long long m0 = (long long)I.ntiles << I.b0, m1 = (long long)I.ntiles << I.b1;
+        const long long m0 = I.cellsort ? 0 : (long long)I.ntiles << I.b0;
+        const long long m1 = (long long)I.ntiles << I.b1;
         const long long hist_m = std::max(m0, I.npasses == 2 ? m1 : 0LL);
         CG_TRY(dev_alloc(b, (void**)&I.hist, sizeof(int32_t) * hist_m));
         I.scan0.in[0] = I.count;
@@ -170,14 +177,16 @@ cg_status plan(cg_batch* b) {
         const long long seg = std::max(1LL, cdiv(chunks, 8LL * c.seg_chunks));
         const long long cellb = cdiv(nb, 256);
         set(BP_ZERO, cdiv(3 * nb, 1024));
-        set(BP_KEY, I.ntiles);
+        set(BP_KEY, I.cellsort ? cdiv(n, (long long)kSortThreads * kKeyItems) : I.ntiles);
         set(BP_SCAN0_R, I.scan0.nblk[0] + I.scan0.nblk[1]);
         set(BP_SCAN0_D, I.scan0.nblk[0] + I.scan0.nblk[1]);
-        set(BP_SCAT0, I.ntiles);
+        set(BP_SCAT0, I.cellsort ? 0 : I.ntiles);
         set(BP_HIST1, I.npasses == 2 ? I.ntiles : 0);
         set(BP_SCAN1_R, I.scan1.nblk[0]);
         set(BP_SCAN1_D, I.scan1.nblk[0]);
         set(BP_SCAT1, I.npasses == 2 ? I.ntiles : 0);
+        set(BP_PLACE, I.cellsort ? cdiv(n, 512LL * kPlaceItems) : 0);
+        set(BP_SEGSORT, I.cellsort ? cdiv(nb, (long long)kGroupCells * kSegSortWarps) : 0);
         set(BP_DEPV, seg);
         set(BP_AVG, std::max(1LL, cdiv(nb, 256LL * c.avg_items)));
         set(BP_PACK, cellb);
@@ -198,8 +207,10 @@ cg_status plan(cg_batch* b) {
         const long long pairs = I.part_off[PS_DRAG] + (long long)kDragSums * I.part_blocks[PS_DRAG];
         CG_TRY(dev_alloc(b, (void**)&I.part, sizeof(float) * 2 * pairs));
         I.smap = sums_map(I.part_off, I.part_blocks);
-        smem_key = std::max(smem_key, sizeof(int) << I.b0);
-        smem_s0 = std::max(smem_s0, scatter_smem_bytes(I.b0, sizeof(float)));
+        if (!I.cellsort) {
+            smem_key = std::max(smem_key, sizeof(int) << I.b0);
+            smem_s0 = std::max(smem_s0, scatter_smem_bytes(I.b0, sizeof(float)));
+        }
         if (I.npasses == 2) smem_s1 = std::max(smem_s1, scatter_smem_bytes(I.b1, sizeof(float)));
         if (I.npasses == 2) smem_hist1 = std::max(smem_hist1, sizeof(int) << I.b1);
     }
@@ -222,7 +233,7 @@ cg_status plan(cg_batch* b) {
         int occ = 1;
         switch (ph) {
             case BP_KEY: case BP_SCAN0_R: case BP_SCAN0_D: case BP_SCAT0:
-            case BP_HIST1: case BP_SCAN1_R: case BP_SCAN1_D: case BP_SCAT1:
+            case BP_HIST1: case BP_SCAN1_R: case BP_SCAN1_D: case BP_SCAT1: case BP_PLACE: case BP_SEGSORT:
                 occ = batch_bin_occupancy(ph, b->smem[ph]);
                 break;
             case BP_AVG: case BP_PROJ: case BP_PROJE: occ = batch_fine_occupancy(ph); break;

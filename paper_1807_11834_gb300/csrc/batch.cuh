@@ -23,6 +23,7 @@ struct BInst {
     Phys<float> P;
     long long n;
     int ntiles, b0, b1, npasses;
+    int cellsort;          // per-cell sort (else the digit sort)
     float* pos;
     float* vel;
     const float* u_fine;
@@ -39,8 +40,9 @@ struct BInst {
     int32_t* key;
     int32_t* count;        // cell counts, then cell_start after the scan
     int32_t* hist;
-    int32_t* key1;
-    int32_t* val1;
+    int32_t* key1;         // digit sort: keys after pass 1; per-cell sort: second id buffer
+    int32_t* val1;         // digit sort: ids after pass 1; per-cell sort: placed ids
+    int32_t* arrival;      // per-cell sort: arrival rank in the cell
     int32_t* perm;
     int32_t* key_sorted;
     int32_t* inv_perm;
@@ -61,7 +63,7 @@ struct BInst {
 // Phases of a batched step, in launch order.
 enum BPhase {
     BP_ZERO = 0, BP_KEY, BP_SCAN0_R, BP_SCAN0_D, BP_SCAT0, BP_HIST1, BP_SCAN1_R, BP_SCAN1_D, BP_SCAT1,
-    BP_DEPV, BP_AVG, BP_PACK, BP_DRAG, BP_DEPM, BP_PROJ, BP_PROJE, BP_SUMS, BP_COUNT
+    BP_PLACE, BP_SEGSORT, BP_DEPV, BP_AVG, BP_PACK, BP_DRAG, BP_DEPM, BP_PROJ, BP_PROJE, BP_SUMS, BP_COUNT
 };
 
 // One batched launch: virtual-block prefix over the instances (device).

@@ -120,32 +120,31 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
 
 // Key kernel of the per-cell sort: cell, diameter and arrival rank of every
 // particle, per-cell counts, porosity fill.  No shared memory and no block
-// barrier; four particles per thread, consecutive lanes on consecutive
-// particles (so runs of equal cells share one count atomic), and the
-// thread's count atomics issued together so their round trips overlap.
-constexpr int kKeyThreads = 256;
-constexpr int kKeyItems = 4;
+// barrier; a block takes 4 x (its threads) particles, four per thread,
+// consecutive lanes on consecutive particles (so runs of equal cells share
+// one count atomic), and the thread's count atomics are issued together so
+// their round trips overlap.
 
 template <typename T>
-__global__ void __launch_bounds__(kKeyThreads, 5)
-k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
-               int32_t* __restrict__ count, T* __restrict__ vol, unsigned long long* __restrict__ status,
-               double* __restrict__ eps_fill, T* __restrict__ rec_fill, T* __restrict__ eps_t_fill,
-               int32_t* __restrict__ arrival) {
+__device__ __forceinline__ void bin_key_rank_body(const T* __restrict__ pos, long long n, const GridDev& g,
+                                                  int32_t* __restrict__ key, int32_t* __restrict__ count,
+                                                  T* __restrict__ vol, unsigned long long* __restrict__ status,
+                                                  double* __restrict__ eps_fill, T* __restrict__ rec_fill,
+                                                  T* __restrict__ eps_t_fill, int32_t* __restrict__ arrival, Blk blk) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const long long base = (long long)blockIdx.x * (kKeyThreads * kKeyItems);
+    const long long base = blk.id * (long long)(blockDim.x * kKeyItems);
     V4<T> pv[kKeyItems];
 #pragma unroll
     for (int k = 0; k < kKeyItems; ++k) {
-        const long long p = base + k * kKeyThreads + threadIdx.x;
+        const long long p = base + k * blockDim.x + threadIdx.x;
         if (p < n) pv[k] = ld4(pos, p);
     }
     int n_out = 0, n_nf = 0;
     int ck[kKeyItems], lk[kKeyItems], old[kKeyItems];
 #pragma unroll
     for (int k = 0; k < kKeyItems; ++k) {
-        const long long p = base + k * kKeyThreads + threadIdx.x;
+        const long long p = base + k * blockDim.x + threadIdx.x;
         const bool valid = p < n;
         int c = -1;
         if (valid) {
@@ -166,7 +165,7 @@ k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __res
     // member finds its head (the last head at or below it)
 #pragma unroll
     for (int k = 0; k < kKeyItems; ++k) {
-        const long long p = base + k * kKeyThreads + threadIdx.x;
+        const long long p = base + k * blockDim.x + threadIdx.x;
         const unsigned heads = __ballot_sync(full, lk[k] != 0);
         const int head = 31 - __clz(heads & ((2u << lane) - 1u));
         const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
@@ -179,12 +178,20 @@ k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __res
     // the porosity of the drag record and of its path-precision copy), the
     // deposit overwrites the occupied ones
     if (eps_fill)
-        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.nbulk;
-             c += (long long)gridDim.x * blockDim.x) {
+        for (long long c = blk.id * blockDim.x + threadIdx.x; c < g.nbulk; c += blk.n * blockDim.x) {
             eps_fill[c] = 1.0;
             if (rec_fill) rec_fill[4 * c] = T(1);
             if (eps_t_fill) eps_t_fill[c] = T(1);
         }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kKeyThreads, 5)
+k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key,
+               int32_t* __restrict__ count, T* __restrict__ vol, unsigned long long* __restrict__ status,
+               double* __restrict__ eps_fill, T* __restrict__ rec_fill, T* __restrict__ eps_t_fill,
+               int32_t* __restrict__ arrival) {
+    bin_key_rank_body<T>(pos, n, g, key, count, vol, status, eps_fill, rec_fill, eps_t_fill, arrival, launch_blk());
 }
 
 // Tile histogram of a digit of already-computed keys (second pass).
@@ -512,7 +519,6 @@ static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA,
 // that keep neighbours close (as DEM codes keep theirs); the digit sort
 // above moves whole digit runs and suits random orders.
 // ----------------------------------------------------------------------
-constexpr int kSegWarpMax = 256;   // largest cell a warp sorts in registers
 
 // Four particles per thread, consecutive lanes on consecutive particles
 // (so runs of one cell's arrivals store to consecutive slots), with the
@@ -520,7 +526,7 @@ constexpr int kSegWarpMax = 256;   // largest cell a warp sorts in registers
 __device__ __forceinline__ void place_body(const int32_t* __restrict__ key, const int32_t* __restrict__ arrival,
                                            const int32_t* __restrict__ cell_start, long long n,
                                            int32_t* __restrict__ tmp, Blk blk) {
-    constexpr int U = 4;
+    constexpr int U = kPlaceItems;
     const long long span = (long long)blockDim.x * U;
     for (long long b0 = blk.id * span; b0 < n; b0 += blk.n * span) {
         int kk[U], aa[U], st[U];
@@ -704,9 +710,6 @@ __device__ __noinline__ void warp_big_sort(int cell, long long s, int c, int32_t
     __syncwarp();
 }
 
-constexpr int kSegSortWarps = 8;     // warps of a segment-sort CTA
-constexpr int kGroupCells = 8;       // consecutive cells a warp takes at a time
-constexpr int kWarpStage = 1024;     // ids of a group staged in the warp's shared memory
 
 // Each warp goes through groups of kGroupCells consecutive cells on its
 // own (no CTA-wide barrier): warp w of nw takes groups w, w + nw, w + 2nw,
@@ -895,7 +898,7 @@ static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, do
     CG_LAUNCH(g, "bin_key", k_bin_key_rank<T>, (unsigned)kb, kKeyThreads, 0, pos, n, g->gd, g->key, g->cell_start,
               (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, g->key2);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, nullptr, nullptr, 0));
-    const long long pb = std::min<long long>((n + 2047) / 2048, (long long)g->num_sms * 4);
+    const long long pb = std::min<long long>((n + 512 * kPlaceItems - 1) / (512 * kPlaceItems), (long long)g->num_sms * 4);
     CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, g->cell_start, n, g->val1);
     const long long sb = std::min<long long>((nbulk + kGroupCells * kSegSortWarps - 1) / (kGroupCells * kSegSortWarps),
                                              (long long)g->num_sms * 4);
@@ -910,7 +913,22 @@ static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, do
 __global__ void __launch_bounds__(kSortThreads) kb_bin_key(BLaunch L) {
     extern __shared__ int sh[];
     batch_loop(L, [&](const BInst& I, Blk b) {
-        bin_key_body<float>(I.pos, I.n, I.gd, I.key, I.count, I.hist, I.ntiles, I.b0, I.vol, I.status, sh, b);
+        if (I.cellsort)
+            bin_key_rank_body<float>(I.pos, I.n, I.gd, I.key, I.count, I.vol, I.status, nullptr, nullptr, nullptr,
+                                     I.arrival, b);
+        else
+            bin_key_body<float>(I.pos, I.n, I.gd, I.key, I.count, I.hist, I.ntiles, I.b0, I.vol, I.status, sh, b);
+    });
+}
+
+__global__ void __launch_bounds__(512) kb_bin_place(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) { place_body(I.key, I.arrival, I.count, I.n, I.val1, b); });
+}
+
+__global__ void __launch_bounds__(kSegSortWarps * 32, 4) kb_seg_sort(BLaunch L) {
+    batch_loop(L, [&](const BInst& I, Blk b) {
+        seg_sort_body<float>(I.count, I.gd.nbulk, I.val1, I.key1, I.perm, I.key_sorted, I.inv_perm, I.vol,
+                             I.vol_sorted, b);
     });
 }
 
@@ -969,6 +987,8 @@ cg_status launch_batch_bin(int phase, const BLaunch& L, unsigned grid, size_t sm
         case BP_SCAN1_R: kb_scan_reduce<<<grid, 256, 0, s>>>(L, 1); break;
         case BP_SCAN1_D: kb_scan_down<<<grid, 256, 0, s>>>(L, 1); break;
         case BP_SCAT1: kb_bin_scatter<<<grid, kSortThreads, smem, s>>>(L, 1); break;
+        case BP_PLACE: kb_bin_place<<<grid, 512, 0, s>>>(L); break;
+        case BP_SEGSORT: kb_seg_sort<<<grid, kSegSortWarps * 32, 0, s>>>(L); break;
         default: return CG_ERR_INVALID_ARG;
     }
     CG_CUDA(cudaGetLastError());
@@ -986,6 +1006,10 @@ int batch_bin_occupancy(int phase, size_t smem) {
         case BP_SCAT1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_bin_scatter, kSortThreads, smem); break;
         case BP_SCAN0_R:
         case BP_SCAN1_R: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_scan_reduce, 256, 0); break;
+        case BP_PLACE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_bin_place, 512, 0); break;
+        case BP_SEGSORT:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_seg_sort, kSegSortWarps * 32, 0);
+            break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_scan_down, 256, 0); break;
     }
     if (e != cudaSuccess) {
@@ -1010,7 +1034,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     }
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
     const long long m0 = (long long)ntiles << g->pass_bits[0];
-    if (use_cell_sort(g->desc.sort_digits, n)) {
+    if (use_cell_sort(g->desc.sort_digits, n, nbulk)) {
         if (g->fp64)
             CG_TRY(bin_rank<double>(g, n, (const double*)pos_d, ntiles, eps_fill, (double*)rec_fill,
                                     (double*)eps_t_fill));

@@ -24,6 +24,14 @@ constexpr int kMaxDigitBits = 11;                   // widest radix digit of one
 constexpr int kMaxPasses = 3;
 constexpr int kMaxBulkBits = 2 * kMaxDigitBits;     // two passes -> 2^22 cells
 constexpr int kScanItems = 4096;                    // elements per scan block
+// per-cell sort
+constexpr int kKeyThreads = 256;                    // threads of its key kernel
+constexpr int kKeyItems = 4;                        // particles per thread of the key kernel
+constexpr int kPlaceItems = 4;                      // particles per thread of the placement
+constexpr int kSegSortWarps = 8;                    // warps of a per-cell sort CTA
+constexpr int kGroupCells = 8;                      // consecutive cells a warp takes at a time
+constexpr int kWarpStage = 1024;                    // ids of a group staged in the warp's shared memory
+constexpr int kSegWarpMax = 256;                    // largest cell a warp sorts in registers
 // Split of a key of `bits` bits into the fewest passes of at most `digits`
 // bits (at most kMaxPasses; wider only when the key needs it), the low
 // digits first.  digits 0 takes the default: narrow digits (8) for grids of
@@ -41,9 +49,10 @@ inline int split_passes(int bits, int (&pb)[kMaxPasses], int digits = 0) {
 
 // cg_grid_desc.sort_digits: automatic, per-cell sort, or a digit width.
 inline bool sort_choice_valid(int v) { return v == CG_SORT_AUTO || v == CG_SORT_CELLS || (v >= 6 && v <= kMaxDigitBits); }
-// The per-cell sort serves a call of n particles.
-inline bool use_cell_sort(int v, long long n) {
-    return v == CG_SORT_CELLS || (v == CG_SORT_AUTO && n <= CG_SORT_CELLS_AUTO_MAX);
+// The per-cell sort serves a call of n particles over nbulk cells.
+inline bool use_cell_sort(int v, long long n, long long nbulk) {
+    return v == CG_SORT_CELLS ||
+           (v == CG_SORT_AUTO && n <= CG_SORT_CELLS_AUTO_MAX && n <= (long long)CG_SORT_CELLS_AUTO_DENSITY * nbulk);
 }
 
 // Dynamic shared memory of a sort scatter pass with 2^bits digits: the

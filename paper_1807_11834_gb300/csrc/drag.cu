@@ -42,7 +42,7 @@ __device__ __forceinline__ V4<T> ld4_plain(const T* p, long long i) {
 // With EULER the particle is advanced in place after its force is known:
 // u += dt (F/m + g), x += dt u, specular reflection at the domain faces.
 // ----------------------------------------------------------------------
-template <typename T, bool EULER>
+template <typename T, bool EULER, bool PREFETCH = true>
 __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
                                           const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
                                           const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part,
@@ -53,9 +53,30 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
     for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
     int clamped_total = 0;
     const long long stride = b.n * blockDim.x;
-    for (long long p = b.id * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const V4<T> x = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
-        const V4<T> v = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
+    // PREFETCH: the next particle's record is loaded while this one's
+    // stencil is gathered and its force computed (its DRAM latency overlaps
+    // them); the batched kernel, short of registers, loads it in turn
+    V4<T> xn, vn;
+    int slot_n = 0;
+    long long p = b.id * blockDim.x + threadIdx.x;
+    if (p < n) {
+        xn = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
+        vn = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
+        if (Fs) slot_n = __ldg(inv_perm + p);
+    }
+    for (; p < n; p += stride) {
+        if (!PREFETCH && p != b.id * blockDim.x + threadIdx.x) {
+            xn = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
+            vn = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
+            if (Fs) slot_n = __ldg(inv_perm + p);
+        }
+        const V4<T> x = xn, v = vn;
+        const int slot = slot_n;
+        if (PREFETCH && p + stride < n) {
+            xn = EULER ? ld4_plain(pos, p + stride) : ld4((const T*)pos, p + stride);
+            vn = EULER ? ld4_plain(vel, p + stride) : ld4((const T*)vel, p + stride);
+            if (Fs) slot_n = __ldg(inv_perm + p + stride);
+        }
         const V4<T> b = gather(bulk4, x.x, x.y, x.z, g);
         T eps = b.x;
         T phi = T(1) - eps;
@@ -74,7 +95,7 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
         F[p] = fx;
         F[n + p] = fy;
         F[2 * n + p] = fz;
-        if (Fs) st4(Fs, __ldg(inv_perm + p), fx, fy, fz, T(0));
+        if (Fs) st4(Fs, slot, fx, fy, fz, T(0));
         T ux = v.x, uy = v.y, uz = v.z;
         const T vp = M<T>::pi6() * d * d * d;
         const T m = P.rho_p * vp;
@@ -121,7 +142,7 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
 }
 
 template <typename T, bool EULER>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
        T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
        T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
@@ -133,7 +154,7 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
 template <bool EULER>
 __global__ void __launch_bounds__(256) kb_drag(BLaunch L, float dt) {
     batch_loop(L, [&](const BInst& I, Blk b) {
-        drag_body<float, EULER>(I.pos, I.vel, I.n, I.gd, I.P, I.bulk4, I.force, I.Fs, I.inv_perm, dt,
+        drag_body<float, EULER, false>(I.pos, I.vel, I.n, I.gd, I.P, I.bulk4, I.force, I.Fs, I.inv_perm, dt,
                                 I.part + 2 * I.part_off[PS_DRAG], I.part_blocks[PS_DRAG], 1, I.status, b);
     });
 }

@@ -24,10 +24,15 @@ FIELDS = ("eps_bulk", "u_bulk", "var_bulk", "S_bulk", "force", "S_fine", "eps_fi
 
 def small_batch():
     """Seven instances: fine edges 16..48, ratios 2/4/8, 1 to ~60,000
-    particles (one tile, ragged tiles, one- and two-pass binning)."""
+    particles (one tile, ragged tiles); five take the digit sort (one and
+    two passes), two the per-cell sort, in one batch (one by one, cg_step
+    picks the sort by its own rule: the fields must agree either way)."""
     specs = [(16, 2, 1, 0.01), (32, 4, 5000, 0.01), (48, 8, 61_000, 0.004), (32, 2, 40_000, 0.006),
              (16, 4, 4097, 0.02), (48, 4, 12_345, 0.003), (40, 8, 30_000, 0.005)]
-    return [synth.batch_instance(5, k, e, r, n, d) for k, (e, r, n, d) in enumerate(specs)]
+    ws = [synth.batch_instance(5, k, e, r, n, d) for k, (e, r, n, d) in enumerate(specs)]
+    for k in (3, 5):
+        ws[k].desc["sort_digits"] = 1   # CG_SORT_CELLS
+    return ws
 
 
 def make_batch(cg, ws, eps_fine=(True,), var=(True,)):
@@ -91,7 +96,9 @@ def test_batched_equals_one_by_one_and_oracle(cuda_lib):
     assert_close_interp("S_fine", got[3]["S_fine"], ref["S_fine"], ref_abs, TOL_FP32)
     # the single-particle instance: its cell alone holds the particle
     assert np.count_nonzero(got[0]["eps_bulk"] < 1.0) == 1
-    assert b.launches_per_step() <= 17
+    # both sorts in one batch: the digit sort's 5 launches beside the per-cell
+    # sort's 2 (key and scan shared), 19 in all
+    assert b.launches_per_step() <= 19
     b.close()
 
 
