@@ -39,7 +39,9 @@ UNIT = "particle-steps/s"
 # dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
 # source file is byte-identical to the one profiled (sha256 prefix).
 NCU_TRAFFIC = {
-    # packed bed, one eager step: k_bin_scatter first pass 20.53 MB, final
+    # packed bed, one eager step: k_average<float,4> 404.95 MB read + 5.19 MB written
+    "average": {"file": "fine.cu", "sha": "97fcd2cb0c9162d5", "bytes": 410.14e6},
+    # packed bed with the digit sort: k_bin_scatter first pass 20.53 MB, final
     # pass 62.48 / 60.02 MB (two captures); per launch, the mean of the passes
     "bin_scatter": {"file": "bin.cu", "sha": "88c48787c50ba765", "bytes": 40.9e6},
 }
@@ -186,12 +188,18 @@ def algorithmic_bytes(g, n, eps_fine=True):
     Step: particles read x, y, z, d (16) and u_p (12), write F (12), plus
     the bin key and permutation written and read once (8); fine cells read
     u_f (12) and write S_f (12) and eps_f (4); bulk cells ~40 B."""
+    import paper_1807_11834_gb300 as cg
     nf, nb = g.n_fine, g.n_bulk
     nbx = nb  # bulk cells
+    choice = int(g.desc.get("sort_digits", 0))
+    cell_sort = choice == cg.CG_SORT_CELLS or (
+        choice == cg.CG_SORT_AUTO and n <= cg.CG_SORT_CELLS_AUTO_MAX and n <= cg.CG_SORT_CELLS_AUTO_DENSITY * nb)
     per = {
-        "bin_key": n * (16 + 4 + 4),                      # pos read; key, volume written
+        "bin_key": n * (16 + 4 + 4 + (4 if cell_sort else 0)),   # pos read; key, volume (, arrival rank) written
         "bin_scatter": n * (12 + 28) // 2,                # pass 1: 4 r + 8 w; pass 2: 12 r + 16 w (mean)
         "bin_hist": n * 4,
+        "bin_place": n * (4 + 4 + 4),                     # key, rank read; id written at its slot
+        "bin_seg_sort": n * (4 + 4 + 16),                 # placed id, diameter read; perm, key, inverse, diameter written
         "deposit_volume": (nbx * 8 + n * 8 + nbx * 8) // 2,   # fill eps; read sorted volume + key; write eps
         "pack": nbx * (8 + 12 + 16 + 4),
         "drag": n * (16 + 16 + 4 + 12 + 16),              # pos, vel, slot read; F and sorted F written
