@@ -88,12 +88,23 @@ __device__ __forceinline__ void average_cell_pairwise(const T* __restrict__ u, c
     const long long nx = g.nf[0], nxy = (long long)g.nf[0] * g.nf[1];
     const long long f0 = (long long)I * RC + nx * ((long long)J * RC) + nxy * ((long long)K * RC);
     T stS[3][LV + 1], stM[3][LV + 1], ref[3];
+    // rows are loaded AHEAD at a time (all their loads in flight together),
+    // then merged one by one in the same order
+    constexpr int AHEAD = (sizeof(T) == 4 && RC <= 4) ? (NR < 8 ? NR : 8) : (NR < 4 ? NR : 4);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
+    for (int r0 = 0; r0 < NR; r0 += AHEAD) {
+    T vr[AHEAD][3][RC];
+#pragma unroll
+    for (int rr = 0; rr < AHEAD; ++rr) {
+        const int r = r0 + rr;
         const long long f = f0 + nx * (r % RC) + nxy * (r / RC);
-        T v[3][RC];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Row<T, RC>::load(u + c * g.nfine + f, v[c]);
+        for (int c = 0; c < 3; ++c) Row<T, RC>::load(u + c * g.nfine + f, vr[rr][c]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < AHEAD; ++rr) {
+        const int r = r0 + rr;
+        T (&v)[3][RC] = vr[rr];
         if (r == 0)
 #pragma unroll
             for (int c = 0; c < 3; ++c) ref[c] = v[c][0];
@@ -137,6 +148,7 @@ __device__ __forceinline__ void average_cell_pairwise(const T* __restrict__ u, c
             }
         }
     }
+    }
     constexpr T invn = T(1) / T(RC * RC * RC);
     T m2 = T(0);
 #pragma unroll
@@ -172,7 +184,7 @@ __device__ __forceinline__ void average_body(const T* __restrict__ u, const Grid
 }
 
 template <typename T, int RC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var, T* __restrict__ rec) {
     average_body<T, RC>(u, g, ub, var, launch_blk(), rec);
 }
@@ -436,7 +448,7 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
 // ----------------------------------------------------------------------
 // Batched fine-grid phases (FP32 instances, ratio 2, 4 or 8)
 // ----------------------------------------------------------------------
-__global__ void __launch_bounds__(256) kb_average(BLaunch L) {
+__global__ void __launch_bounds__(256, 2) kb_average(BLaunch L) {
     batch_loop(L, [&](const BInst& I, Blk b) {
         switch (I.gd.r) {
             case 2: average_body<float, 2>(I.u_fine, I.gd, I.u_bulk, I.var, b); break;
@@ -493,10 +505,12 @@ int batch_fine_occupancy(int phase) {
 static inline unsigned blocks_of(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk, void* rec) {
-    // grid-stride over two blocks per SM: each thread keeps r^2 x 3 row loads
-    // in flight, enough to stream at HBM speed while leaving most warp slots
-    // to the particle kernels running beside it
-    const unsigned nblk = (unsigned)std::min((long long)blocks_of(g->gd.nbulk, 256), (long long)g->num_sms * 2);
+    // grid-stride over one block per SM: each thread keeps 8 rows x 3
+    // components of loads in flight (about 100 registers), enough to stream
+    // near HBM speed while leaving most warp slots and registers to the
+    // particle kernels running beside it (two blocks per SM ran the average
+    // alone as fast but slowed the step by 12 us)
+    const unsigned nblk = (unsigned)std::min((long long)blocks_of(g->gd.nbulk, 256), (long long)g->num_sms * 1);
 #define CG_AVG(T, RC)                                                                                   \
     CG_LAUNCH(g, "average", (k_average<T, RC>), nblk, 256, 0, (const T*)u_fine, g->gd, (T*)u_bulk, \
               (T*)var_bulk, (T*)rec)
