@@ -113,6 +113,7 @@ k_bin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict
           int32_t* __restrict__ count, int32_t* __restrict__ hist, int ntiles, int bits0,
           T* __restrict__ vol, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
           T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
+    pdl_wait();
     extern __shared__ int sh[];
     bin_key_body<T>(pos, n, g, key, count, hist, ntiles, bits0, vol, status, sh, launch_blk(), eps_fill, rec_fill,
                     eps_t_fill);
@@ -191,6 +192,7 @@ k_bin_key_rank(const T* __restrict__ pos, long long n, GridDev g, int32_t* __res
                int32_t* __restrict__ count, T* __restrict__ vol, unsigned long long* __restrict__ status,
                double* __restrict__ eps_fill, T* __restrict__ rec_fill, T* __restrict__ eps_t_fill,
                int32_t* __restrict__ arrival) {
+    pdl_wait();
     bin_key_rank_body<T>(pos, n, g, key, count, vol, status, eps_fill, rec_fill, eps_t_fill, arrival, launch_blk());
 }
 
@@ -214,6 +216,7 @@ __device__ __forceinline__ void bin_hist_body(const int32_t* __restrict__ keys, 
 __global__ void __launch_bounds__(kSortThreads)
 k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift, int bits,
            int32_t* __restrict__ hist) {
+    pdl_wait();
     extern __shared__ int sh[];
     bin_hist_body(keys, n, ntiles, shift, bits, hist, sh, launch_blk());
 }
@@ -391,6 +394,7 @@ k_bin_scatter(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ v
               int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int32_t* __restrict__ perm,
               int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, const T* __restrict__ vol,
               T* __restrict__ vol_sorted) {
+    pdl_wait();
     extern __shared__ int cnt[];
     bin_scatter_body<FIRST, FINAL, T>(keys_in, vals_in, n, ntiles, shift, bits, offs, keys_out, vals_out, perm,
                                       key_sorted, inv_perm, vol, vol_sorted, cnt, launch_blk());
@@ -443,6 +447,7 @@ __device__ __forceinline__ void scan_reduce_body(const ScanJob& j, int32_t* __re
 }
 
 __global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restrict__ part) {
+    pdl_wait();
     scan_reduce_body(j, part, launch_blk());
 }
 
@@ -480,6 +485,7 @@ __device__ __forceinline__ void scan_down_body(const ScanJob& j, const int32_t* 
 }
 
 __global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __restrict__ part) {
+    pdl_wait();
     scan_down_body(j, part, launch_blk());
 }
 
@@ -550,6 +556,7 @@ __global__ void __launch_bounds__(512) k_bin_place(const int32_t* __restrict__ k
                                                    const int32_t* __restrict__ arrival,
                                                    const int32_t* __restrict__ cell_start, long long n,
                                                    int32_t* __restrict__ tmp) {
+    pdl_wait();
     place_body(key, arrival, cell_start, n, tmp, launch_blk());
 }
 
@@ -820,6 +827,7 @@ __global__ void __launch_bounds__(kSegSortWarps * 32, 4)
 k_seg_sort(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp, int32_t* alt,
            int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
            const T* __restrict__ vol, T* __restrict__ vol_sorted) {
+    pdl_wait();
     seg_sort_body<T>(cell_start, nbulk, tmp, alt, perm, key_sorted, inv_perm, vol, vol_sorted, launch_blk());
 }
 

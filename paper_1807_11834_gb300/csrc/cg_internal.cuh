@@ -202,6 +202,11 @@ void prof_end(cg_grids* g, int slot, int ev);
 
 // Launch a kernel on the handle's stream, count it, time it when profiling,
 // and turn a launch error into CG_ERR_CUDA.
+// Launches are programmatic dependent launches: the next kernel on the
+// stream may be scheduled while this one drains, and every kernel launched
+// here starts with pdl_wait(), which returns once the kernels it depends on
+// have completed and their memory is visible (so each kernel still sees all
+// earlier work; only the launch latency overlaps).
 #define CG_LAUNCH(g, name, kernel, grid, block, smem, ...)                        \
     do {                                                                         \
         int slot_ = -1, ev_ = -1;                                                \
@@ -209,9 +214,19 @@ void prof_end(cg_grids* g, int slot, int ev);
             slot_ = cg::prof_slot((g), (name));                                  \
             cg::prof_begin((g), slot_, &ev_);                                    \
         }                                                                        \
-        kernel<<<(grid), (block), (smem), (g)->stream>>>(__VA_ARGS__);           \
+        cudaLaunchAttribute a_[1];                                               \
+        a_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;           \
+        a_[0].val.programmaticStreamSerializationAllowed = 1;                    \
+        cudaLaunchConfig_t c_ = {};                                              \
+        c_.gridDim = dim3((unsigned)(grid));                                     \
+        c_.blockDim = dim3((unsigned)(block));                                   \
+        c_.dynamicSmemBytes = (size_t)(smem);                                    \
+        c_.stream = (g)->stream;                                                 \
+        c_.attrs = a_;                                                           \
+        c_.numAttrs = 1;                                                         \
+        cudaError_t e_ = cudaLaunchKernelEx(&c_, kernel, __VA_ARGS__);           \
         (g)->launches++;                                                         \
-        cudaError_t e_ = cudaGetLastError();                                     \
+        if (e_ == cudaSuccess) e_ = cudaGetLastError();                          \
         if ((g)->prof) cg::prof_end((g), slot_, ev_);                            \
         if (e_ != cudaSuccess) return CG_ERR_CUDA;                               \
     } while (0)
@@ -407,6 +422,12 @@ __device__ __forceinline__ int run_head_length(int v, bool valid) {
     const int next = lane == 31 ? 32 : (later ? __ffs(later) - 1 : 32);
     return next - lane;
 }
+
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and flushed their memory (returns at once for a kernel not
+// launched as a dependent).  First statement of every kernel launched
+// through CG_LAUNCH.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;

@@ -34,6 +34,7 @@ __device__ __forceinline__ void fill_body(T* __restrict__ a, long long m, T v, B
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fill(T* __restrict__ a, long long m, T v) {
+    pdl_wait();
     fill_body(a, m, v, launch_blk());
 }
 
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(256)
 k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ key_sorted, const int32_t* __restrict__ cs, GridDev g,
                  double* __restrict__ eps, T* __restrict__ part, long long pstride, int do_sums) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256)
 k_deposit_volume_sorted(const T* __restrict__ dsorted, long long n, const int32_t* __restrict__ key_sorted,
                         const int32_t* __restrict__ cs, GridDev g, double* __restrict__ eps, T* __restrict__ part,
                         long long pstride, int do_sums, T* __restrict__ rec, T* __restrict__ eps_t) {
+    pdl_wait();
     deposit_volume_sorted_body(dsorted, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk(), rec, eps_t);
 }
 
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(256)
 k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
                        const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
                        long long pstride, int do_sums) {
+    pdl_wait();
     deposit_sorted_force_body(Fs, n, key_sorted, cs, g, S, part, pstride, do_sums, launch_blk());
 }
 
@@ -182,6 +186,7 @@ __global__ void __launch_bounds__(256)
 k_deposit_momentum(const T* __restrict__ F, long long n, const int32_t* __restrict__ perm,
                    const int32_t* __restrict__ key_sorted, const int32_t* __restrict__ cs, GridDev g,
                    T* __restrict__ S) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -248,6 +253,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_pack(const double* __restrict__ eps, const T* __restrict__ u, GridDev g, T* __restrict__ bulk4,
        T* __restrict__ eps_t) {
+    pdl_wait();
     pack_body(eps, u, g, bulk4, eps_t, launch_blk());
 }
 
@@ -293,6 +299,7 @@ __device__ __forceinline__ void sums_body(const T* __restrict__ part, const Sums
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sums(const T* __restrict__ part, SumsMap map, double* __restrict__ sums) {
+    pdl_wait();
     sums_body(part, map, sums, launch_blk());
 }
 

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
        T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
        T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
+    pdl_wait();
     drag_body<T, EULER>(pos, vel, n, g, P, bulk4, F, Fs, inv_perm, dt, part, pstride, do_sums, status,
                         launch_blk());
 }

@@ -186,6 +186,7 @@ __device__ __forceinline__ void average_body(const T* __restrict__ u, const Grid
 template <typename T, int RC>
 __global__ void __launch_bounds__(256, 2)
 k_average(const T* __restrict__ u, GridDev g, T* __restrict__ ub, T* __restrict__ var, T* __restrict__ rec) {
+    pdl_wait();
     average_body<T, RC>(u, g, ub, var, launch_blk(), rec);
 }
 
@@ -391,6 +392,7 @@ k_project(const T* __restrict__ in0, const T* __restrict__ in1, const T* __restr
           const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0, T* __restrict__ out1,
           T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part, long long pstride,
           int do_sums) {
+    pdl_wait();
     project_body<T, RC>(in0, in1, in2, in3, ncomp, g, out0, out1, out2, out3, part, pstride, do_sums,
                         launch_blk());
 }

@@ -588,6 +588,7 @@ __global__ void __launch_bounds__(256)
 k_mlp_features(const T* __restrict__ pos, const T* __restrict__ vel, long long n, GridDev g, Phys<T> P,
                const T* __restrict__ bulk_stale, const T* __restrict__ var_stale, const T* __restrict__ bulk_fresh,
                float* __restrict__ feat, float* __restrict__ target) {
+    pdl_wait();
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const V4<T> x = ld4(pos, p), v = ld4(vel, p);
         const Probe<T> st = probe(bulk_stale, var_stale, x.x, x.y, x.z, g);
@@ -669,6 +670,7 @@ k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, co
                const float* __restrict__ var_stale, const float* __restrict__ u_fine, const float* __restrict__ Pm,
                const float* __restrict__ scale, float* __restrict__ F, float* __restrict__ Fs,
                const int32_t* __restrict__ inv_perm, float dt, float age, unsigned long long* __restrict__ status) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& s = smem_as<Smem>(smem_raw);
     load_weights(s, Pm, scale);
