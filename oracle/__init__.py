@@ -86,6 +86,7 @@ def _load():
                 "or_drag_beta": (d, [pg, d, d, pd, P(C.c_int)]),
                 "or_drag": (i64, [pg, i64, pd, pd, pd, pd, pd]),
                 "or_deposit_momentum": (None, [pg, i64, pd, pi, pi, pd]),
+                "or_implicit": (None, [pg, i64, pd, pd, pd, pd, pi, pi, pd]),
                 "or_particle_state": (None, [pg, i64, pd, pd, pd, pd, pd, pd]),
                 "or_mlp_features": (None, [pg, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd]),
                 "or_project": (None, [pg, C.c_int, pd, pd]),
@@ -224,6 +225,24 @@ def drag(desc, pos_d, vel, eps_bulk, u_bulk):
     u = _f64(u_bulk)
     ncl = lib.or_drag(C.byref(g), n, _pd(pos), _pd(v), _pd(e), _pd(u), _pd(F))
     return F, int(ncl)
+
+
+def implicit(desc, pos_d, vel, eps_bulk, u_bulk, cell_start, perm):
+    """Semi-implicit exchange coefficients (A[nb], b[3, nb]) with
+    A = sum beta_p / V_B and b = sum beta_p u_p / V_B per cell (Eq. UFP's
+    F_fpi treated semi-implicitly: F_fpi = -A u_f + b)."""
+    lib = _load()
+    g = grid(desc)
+    pos = _f64(pos_d).reshape(-1, 4)
+    v = _f64(vel).reshape(-1, 4)
+    n = pos.shape[0]
+    nf, nb = dims(desc)
+    nbulk = nb[0] * nb[1] * nb[2]
+    coef = np.zeros((4, nbulk))
+    lib.or_implicit(C.byref(g), n, _pd(pos), _pd(v), _pd(_f64(eps_bulk)), _pd(_f64(u_bulk)),
+                    _pi(np.ascontiguousarray(cell_start, np.int32)), _pi(np.ascontiguousarray(perm, np.int32)),
+                    _pd(coef))
+    return coef[0], coef[1:]
 
 
 def particle_state(desc, pos_d, vel, eps_bulk, u_bulk):

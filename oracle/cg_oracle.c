@@ -396,6 +396,32 @@ void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
     }
 }
 
+/* Semi-implicit exchange coefficients: the drag factor beta_p of each
+ * particle (the same gather and correlation as or_drag), summed per cell in
+ * the stable order and divided by the cell volume. */
+void or_implicit(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                 const double* eps_bulk, const double* u_bulk, const int32_t* cell_start,
+                 const int32_t* perm, double* coef)
+{
+    geom g = geometry(G);
+    for (int64_t c = 0; c < g.nbulk; ++c) {
+        ksum k[4];
+        memset(k, 0, sizeof k);
+        for (int32_t i = cell_start[c]; i < cell_start[c + 1]; ++i) {
+            const int64_t p = perm[i];
+            const double* x = &pos_d[4 * p];
+            double eps_p, uf[3], s[3];
+            or_gather(G, eps_bulk, 1, x, &eps_p);
+            or_gather(G, u_bulk, 3, x, uf);
+            for (int a = 0; a < 3; ++a) s[a] = uf[a] - vel[4 * p + a];
+            const double beta = or_drag_beta(G, eps_p, x[3], s, NULL);
+            ks_add(&k[0], beta);
+            for (int a = 0; a < 3; ++a) ks_add(&k[1 + a], beta * vel[4 * p + a]);
+        }
+        for (int comp = 0; comp < 4; ++comp) coef[comp * g.nbulk + c] = ks_get(&k[comp]) / g.VB;
+    }
+}
+
 /* Bulk -> fine transfer of particle fields (Fig. 1): the bulk field is
  * interpolated at each fine cell centre with the particle stencil. */
 void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine)

@@ -99,6 +99,17 @@ void or_mlp_features(const or_grid* G, int64_t n, const double* pos_d, const dou
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk);
 
+/* Semi-implicit exchange coefficients (Eq. UFP: F_fpi, the counterpart of
+ * F_drag, is treated semi-implicitly).  With F_p = beta_p (u_f(x_p) - u_p):
+ *   A_B = (1/V_B) sum_{p in B} beta_p,   b_B = (1/V_B) sum_{p in B} beta_p u_p,
+ * so that the fluid solver takes F_fpi = -A u_f + b with A in its matrix.
+ * coef[4][n_b] = (A, b_x, b_y, b_z); sums over each cell in the stable order.
+ * PARITY: pinned by tests (uniform field: S_B = -(A u_f - b); sum A V_B =
+ * sum beta_p; one particle; zero particle velocity). */
+void or_implicit(const or_grid* G, int64_t n, const double* pos_d, const double* vel,
+                 const double* eps_bulk, const double* u_bulk, const int32_t* cell_start,
+                 const int32_t* perm, double* coef);
+
 /* Interpolate ncomp bulk fields at every fine cell centre. */
 void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine);
 
