@@ -142,6 +142,8 @@ typedef struct {
     int32_t* cell;         /* [n] bulk cell per particle                nullable */
     int32_t* perm;         /* [n] particles in cell order               nullable */
     int32_t* cell_start;   /* [n_b + 1] segment starts                  nullable */
+    void* implicit_bulk;   /* [4][n_b] T semi-implicit coefficients     nullable */
+    void* implicit_fine;   /* [4][n_f] T their projection (needs the bulk ones) nullable */
 } cg_step_out;
 
 /* Human-readable name of a status code (static storage). */
@@ -241,7 +243,16 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
  * u_fine: [3][n_f] T.  sums (CG_NSUMS doubles): 0 sum V_p,
  * 1 sum (1 - eps_B) V_B, 2..4 sum F_p, 5..7 sum S_B V_B, 8..10 sum S_f V_f,
  * 11 sum |F_p|, 12..14 sum m_p u_p after the advance, 15 particles whose
- * porosity was clamped. */
+ * porosity was clamped.
+ * Semi-implicit exchange (Eq. UFP: F_fpi, the counterpart of F_drag, is
+ * treated semi-implicitly): when out->implicit_bulk is set, it receives
+ * A = (1/V_B) sum_p beta_p and b = (1/V_B) sum_p beta_p u_p per bulk cell
+ * ([4][n_b] T: A, b_x, b_y, b_z; u_p before the advance), with which the
+ * fluid solver takes F_fpi = -A u_f + b (A into its matrix); when
+ * out->implicit_fine is also set, the four fields are projected onto the
+ * fine grid like the source.  Device entries only: cg_step_learned, the
+ * host-buffer entries and batched instances reject these fields
+ * (CG_ERR_INVALID_ARG). */
 cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
                   const cg_step_out* out, double dt);
 

@@ -65,7 +65,8 @@ class StepOut(C.Structure):
     _fields_ = [("eps_bulk", C.c_void_p), ("u_bulk", C.c_void_p), ("var_bulk", C.c_void_p),
                 ("S_bulk", C.c_void_p), ("force", C.c_void_p), ("S_fine", C.c_void_p),
                 ("eps_fine", C.c_void_p), ("sums", C.c_void_p), ("cell", C.c_void_p),
-                ("perm", C.c_void_p), ("cell_start", C.c_void_p)]
+                ("perm", C.c_void_p), ("cell_start", C.c_void_p), ("implicit_bulk", C.c_void_p),
+                ("implicit_fine", C.c_void_p)]
 
 
 class BatchItem(C.Structure):
@@ -282,8 +283,11 @@ class Grids:
         _check(lib().cg_project_bulk_to_fine(self.h, ncomp, _ptr(bulk), _ptr(fine_out)),
                "cg_project_bulk_to_fine")
 
-    def alloc_outputs(self, n, var=True, eps_fine=False, bins=False, device="cuda"):
-        """Output tensors of one step (device), by cg_step_out field name."""
+    def alloc_outputs(self, n, var=True, eps_fine=False, bins=False, implicit=False, implicit_fine=False,
+                      device="cuda"):
+        """Output tensors of one step (device), by cg_step_out field name;
+        implicit: the semi-implicit coefficients [4][n_b] (A, b), and with
+        implicit_fine their projection [4][n_f]."""
         import torch
         kw = dict(device=device, dtype=self.dtype)
         o = dict(eps_bulk=torch.empty(self.n_bulk, device=device, dtype=torch.float64),
@@ -294,6 +298,10 @@ class Grids:
                  S_fine=torch.empty(3, self.n_fine, **kw),
                  eps_fine=torch.empty(self.n_fine, **kw) if eps_fine else None,
                  sums=torch.empty(CG_NSUMS, device=device, dtype=torch.float64))
+        if implicit or implicit_fine:
+            o["implicit_bulk"] = torch.empty(4, self.n_bulk, **kw)
+        if implicit_fine:
+            o["implicit_fine"] = torch.empty(4, self.n_fine, **kw)
         if bins:
             o["cell"] = torch.empty(n, device=device, dtype=torch.int32)
             o["perm"] = torch.empty(n, device=device, dtype=torch.int32)

@@ -474,6 +474,8 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
                            double dt, const cg_mlp* mlp = nullptr, int32_t age = 0) {
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
+    if (o->implicit_bulk && mlp) return CG_ERR_INVALID_ARG;   // no drag factor in the learned form
+    if (o->implicit_bulk && n > 0) CG_TRY(grow_buf(g->Bs, 4 * g->tsize * (size_t)g->cap));
     for (int r = 0; r < PS_NREG; ++r) g->part_blocks[r] = -1;
     cudaStream_t side = g->prof ? g->stream : g->aux;
     CG_CUDA(cudaEventRecord(g->ev_fork, g->stream));
@@ -510,11 +512,20 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
         CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, age, o->force, o->S_bulk,
                                    dt));
     else
-        CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt));
+        CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt, o->implicit_bulk));
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
     const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, nullptr};
     void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, nullptr};
     CG_TRY(launch_project(g, 3, in, out, true));
+    if (o->implicit_fine) {
+        const void* ci[4];
+        void* co[4];
+        for (int c = 0; c < 4; ++c) {
+            ci[c] = (const char*)o->implicit_bulk + c * bs;
+            co[c] = (char*)o->implicit_fine + c * fs;
+        }
+        CG_TRY(launch_project(g, 4, ci, co, false));
+    }
     CG_CUDA(cudaStreamWaitEvent(g->stream, g->ev_epsf, 0));
     CG_TRY(launch_sums(g, o->sums ? o->sums : g->sums_scratch));
     return CG_OK;
@@ -527,6 +538,8 @@ static cg_status check_step_args(const cg_particles* p, const void* u_fine, cons
     if (!(dt >= 0.0) || !isfinite(dt)) return CG_ERR_INVALID_ARG;
     if (p->n > 0 && (!p->pos_d || !p->vel || !o->force)) return CG_ERR_INVALID_ARG;
     if (!o->eps_bulk || !o->u_bulk || !o->S_bulk || !o->S_fine) return CG_ERR_INVALID_ARG;
+    if (o->implicit_fine && !o->implicit_bulk) return CG_ERR_INVALID_ARG;
+    if (!device && (o->implicit_bulk || o->implicit_fine)) return CG_ERR_INVALID_ARG;   // device entries only
     if (device) {
         if (p->n > 0 && (!aligned16(p->pos_d) || !aligned16(p->vel))) return CG_ERR_INVALID_ARG;
         if (!aligned16(u_fine) || !aligned16(o->S_fine) || (o->eps_fine && !aligned16(o->eps_fine)))
@@ -546,6 +559,7 @@ cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine
     CG_TRY(check_handle(g));
     CG_TRY(check_step_args(p, u_fine, out, dt, true));
     if (!mlp || g->fp64 || !out->var_bulk || age < 0) return CG_ERR_INVALID_ARG;
+    if (out->implicit_bulk || out->implicit_fine) return CG_ERR_INVALID_ARG;   // no drag factor in the learned form
     return step_impl(g, p, u_fine, out, dt, age == 0 ? nullptr : mlp, age);
 }
 
@@ -600,7 +614,7 @@ static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const voi
     // the step
     CG_CUDA(cudaStreamWaitEvent(g->stream, S.in_done, 0));
     cg_particles dp = {n, S.pos.p, S.vel.p};
-    cg_step_out d;
+    cg_step_out d = {};   // every field the host call does not map stays null
     d.eps_bulk = (double*)S.eps.p;
     d.u_bulk = S.ub.p;
     d.var_bulk = out->var_bulk ? S.var.p : nullptr;

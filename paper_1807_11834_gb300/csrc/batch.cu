@@ -363,7 +363,7 @@ cg_status cg_batch_create(const cg_batch_item* items, int32_t count, void* cuda_
         if ((((uintptr_t)it.particles.pos_d) | ((uintptr_t)it.particles.vel)) & 15u) return CG_ERR_INVALID_ARG;
         const cg_step_out& o = it.out;
         if (!it.u_fine || !o.eps_bulk || !o.u_bulk || !o.S_bulk || !o.force || !o.S_fine) return CG_ERR_INVALID_ARG;
-        if (o.cell || o.perm || o.cell_start) return CG_ERR_INVALID_ARG;
+        if (o.cell || o.perm || o.cell_start || o.implicit_bulk || o.implicit_fine) return CG_ERR_INVALID_ARG;
         if ((((uintptr_t)it.u_fine) | ((uintptr_t)o.S_fine) | ((uintptr_t)o.eps_fine)) & 15u)
             return CG_ERR_INVALID_ARG;
     }

@@ -176,6 +176,7 @@ struct cg_grids {
     int hs_next = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cg::DevBuf fresh4;   // [nbulk] T4: (phi, u) of the fresh field of cg_mlp_features
+    cg::DevBuf Bs;       // [cap] T4: (beta, beta u) in sorted order, for the semi-implicit coefficients
 
     // second stream of the step: fine-grid work that does not depend on the
     // particle path runs beside it (fork / join through events)
@@ -275,12 +276,14 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
                                 bool prefilled = false, void* rec = nullptr, void* eps_t = nullptr);
 cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
+// Semi-implicit coefficients [4][n_b] (A, b) from the drag's sorted (beta, beta u) records.
+cg_status launch_deposit_implicit(cg_grids* g, long long n, void* coef_bulk);
 cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk);
 // rec (nullable): also write the mean velocity into the drag record's u part.
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk, void* rec = nullptr);
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
-                      bool sums, double dt);
+                      bool sums, double dt, void* coef_bulk = nullptr);
 // Learned drag (FP32 only): bulk4 must hold (phi of this step, stale u).
 cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
                               const void* var_stale, const void* u_fine, int32_t age, void* force, void* S_bulk,
@@ -425,8 +428,8 @@ __device__ __forceinline__ int run_head_length(int v, bool valid) {
 
 // Programmatic dependent launch: wait until the grids this one depends on
 // have completed and flushed their memory (returns at once for a kernel not
-// launched as a dependent).  First statement of every kernel launched
-// through CG_LAUNCH.
+// launched as a dependent).  First statement of every kernel of the
+// library (required of those launched through CG_LAUNCH).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -167,6 +167,44 @@ __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ 
     if (do_sums) block_sums<T, 3>(sv, part, pstride, b.id);
 }
 
+// Semi-implicit coefficients (Eq. UFP): per cell A = (1/V_B) sum beta and
+// b = (1/V_B) sum beta u_p from the drag's sorted (beta, beta u) records,
+// with the reaction's segmented sums.
+template <typename T>
+__device__ __forceinline__ void deposit_implicit_body(const T* __restrict__ Bs, long long n,
+                                                      const int32_t* __restrict__ key_sorted,
+                                                      const int32_t* __restrict__ cs, const GridDev& g,
+                                                      T* __restrict__ coef, Blk b) {
+    const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = b.n * (blockDim.x >> 5);
+    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
+        long long s, t;
+        seg_chunk_range(base, n, key_sorted, cs, s, t);
+        seg_rounds<T, 4>(
+            s, t, key_sorted,
+            [&](long long i, T (&v)[4]) {
+                const V4<T> r = ld4(Bs, i);
+                v[0] = r.x;
+                v[1] = r.y;
+                v[2] = r.z;
+                v[3] = r.w;
+            },
+            [&](int key, CSum<T> (&a)[4]) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    coef[k * g.nbulk + key] = sizeof(T) == 4 ? a[k].get() * (T)g.invVBf : a[k].get() * (T)g.invVB;
+            });
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit_implicit(const T* __restrict__ Bs, long long n, const int32_t* __restrict__ key_sorted,
+                   const int32_t* __restrict__ cs, GridDev g, T* __restrict__ coef) {
+    pdl_wait();
+    deposit_implicit_body<T>(Bs, n, key_sorted, cs, g, coef, launch_blk());
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
@@ -432,6 +470,19 @@ cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bo
     else
         CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<float>, nblk, 256, 0, (const float*)g->Fs, n,
                   g->key_sorted, g->cell_start, g->gd, (float*)S_bulk, (float*)part, (long long)nblk, (int)sums);
+    return CG_OK;
+}
+
+cg_status launch_deposit_implicit(cg_grids* g, long long n, void* coef_bulk) {
+    CG_CUDA(cudaMemsetAsync(coef_bulk, 0, 4 * g->tsize * (size_t)g->gd.nbulk, g->stream));
+    if (n == 0) return CG_OK;
+    const unsigned nblk = seg_blocks(g, n);
+    if (g->fp64)
+        CG_LAUNCH(g, "deposit_implicit", k_deposit_implicit<double>, nblk, 256, 0, (const double*)g->Bs.p, n,
+                  g->key_sorted, g->cell_start, g->gd, (double*)coef_bulk);
+    else
+        CG_LAUNCH(g, "deposit_implicit", k_deposit_implicit<float>, nblk, 256, 0, (const float*)g->Bs.p, n,
+                  g->key_sorted, g->cell_start, g->gd, (float*)coef_bulk);
     return CG_OK;
 }
 

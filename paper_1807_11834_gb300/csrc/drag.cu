@@ -42,12 +42,14 @@ __device__ __forceinline__ V4<T> ld4_plain(const T* p, long long i) {
 // With EULER the particle is advanced in place after its force is known:
 // u += dt (F/m + g), x += dt u, specular reflection at the domain faces.
 // ----------------------------------------------------------------------
+// Bs (nullable): the semi-implicit record (beta, beta u_p) of each particle,
+// written to its sorted slot beside the force record.
 template <typename T, bool EULER, bool PREFETCH = true>
 __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
                                           const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
                                           const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part,
                                           long long pstride, int do_sums, unsigned long long* __restrict__ status,
-                                          Blk b) {
+                                          Blk b, T* __restrict__ Bs = nullptr) {
     T lane_sums[kDragSums];
 #pragma unroll
     for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
@@ -96,6 +98,7 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
         F[n + p] = fy;
         F[2 * n + p] = fz;
         if (Fs) st4(Fs, slot, fx, fy, fz, T(0));
+        if (Bs) st4(Bs, slot, beta, beta * v.x, beta * v.y, beta * v.z);
         T ux = v.x, uy = v.y, uz = v.z;
         const T vp = M<T>::pi6() * d * d * d;
         const T m = P.rho_p * vp;
@@ -145,10 +148,11 @@ template <typename T, bool EULER>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
        T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
-       T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status) {
+       T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status,
+       T* __restrict__ Bs) {
     pdl_wait();
     drag_body<T, EULER>(pos, vel, n, g, P, bulk4, F, Fs, inv_perm, dt, part, pstride, do_sums, status,
-                        launch_blk());
+                        launch_blk(), Bs);
 }
 
 // Batched drag with the fused sorted-order force record (FP32 instances).
@@ -178,17 +182,23 @@ int batch_drag_occupancy() {
 }
 
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
-                      bool sums, double dt) {
+                      bool sums, double dt, void* coef_bulk) {
     const bool euler = dt > 0.0;
     void* part = part_ptr(g, PS_DRAG);
     const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * 8));
     g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
     void* Fs = S_bulk ? g->Fs : nullptr;
+    void* Bs = nullptr;
+    if (coef_bulk && n > 0) {
+        // sized by the step before its first launch
+        if (g->Bs.bytes < 4 * g->tsize * (size_t)n) return CG_ERR_INVALID_ARG;
+        Bs = g->Bs.p;
+    }
     if (n > 0 || sums) {
 #define CG_DRAGP(T, E)                                                                                      \
     CG_LAUNCH(g, "drag", (k_drag<T, E>), nblk, 256, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd),          \
               (const T*)g->bulk4, (T*)force, (T*)Fs, g->inv_perm, (T)dt, (T*)part, (long long)nblk, (int)sums,   \
-              g->status)
+              g->status, (T*)Bs)
         if (g->fp64) {
             if (euler) CG_DRAGP(double, true);
             else CG_DRAGP(double, false);
@@ -199,6 +209,7 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
 #undef CG_DRAGP
     }
     if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, sums));
+    if (coef_bulk) CG_TRY(launch_deposit_implicit(g, n, coef_bulk));
     return CG_OK;
 }
 

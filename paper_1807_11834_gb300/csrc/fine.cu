@@ -405,6 +405,7 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
                   const T* __restrict__ in3, int ncomp, GridDev g, T* __restrict__ out0,
                   T* __restrict__ out1, T* __restrict__ out2, T* __restrict__ out3,
                   T* __restrict__ part, long long pstride, int do_sums) {
+    pdl_wait();
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     CSum<T> sacc[3];
     if (f < g.nfine) {
@@ -540,7 +541,10 @@ cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* co
     const int r = g->gd.r;
     const bool fast = (r == 2 || r == 4 || r == 8);
     const unsigned nblk = fast ? blocks_of(g->gd.nbulk, 256) : blocks_of(g->gd.nfine, 256);
-    g->part_blocks[PS_PROJ] = sums ? (long long)nblk : -1;
+    // only the projection that forms the sums claims their partials (a later
+    // projection without sums, of the porosity or the semi-implicit
+    // coefficients, leaves them to it)
+    if (sums) g->part_blocks[PS_PROJ] = (long long)nblk;
 #define CG_PRJ(T, KER)                                                                                   \
     CG_LAUNCH(g, ncomp == 1 ? "project_eps" : "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2], \
               (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], (T*)part,   \

@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(TILE, 4)
 k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
               long long n, float* __restrict__ c_out, int32_t* __restrict__ in_range,
               unsigned long long* __restrict__ status) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& s = smem_as<Smem>(smem_raw);
     load_weights(s, P, scale);
@@ -421,6 +422,7 @@ __global__ void __launch_bounds__(TILE, 1)
 k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
            const float* __restrict__ target, long long n, float* __restrict__ part,
            unsigned long long* __restrict__ status) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     SmemTrain& st = smem_as<SmemTrain>(smem_raw);
     Smem& s = st.s;
@@ -531,6 +533,7 @@ __global__ void __launch_bounds__(256)
 k_mlp_reduce_adam(const float* __restrict__ part, int nparts, float* __restrict__ grads, float* __restrict__ P,
                   float* __restrict__ m, float* __restrict__ v, int t, float lr, int do_update,
                   float* __restrict__ loss_out, long long n) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > NPARAM) return;
     float g = 0.f;

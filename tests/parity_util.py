@@ -43,7 +43,7 @@ def assert_close_interp(name, got, ref, ref_abs, tol):
     ref_abs = np.atleast_2d(np.asarray(ref_abs, np.float64))
     num = np.sqrt(((got - ref) ** 2).sum(axis=0))
     den = np.maximum(np.sqrt((ref ** 2).sum(axis=0)), np.sqrt((ref_abs ** 2).sum(axis=0)))
-    den = np.maximum(den, 1e-3 * den.max())
+    den = np.maximum(den, max(1e-3 * den.max(), 1e-300))
     r = num / den
     assert r.max() <= tol, f"{name}: max rel err {r.max():.3e} > {tol:.1e}"
     return float(r.max())

@@ -50,10 +50,10 @@ def test_struct_layout_matches_header():
     import paper_1807_11834_gb300 as cg
     # cg_grid_desc: 6 doubles, 3+1+4 int32 + reserved, 5 doubles, 3 doubles
     assert ctypes.sizeof(cg.GridDesc) == 6 * 8 + 8 * 4 + 5 * 8 + 3 * 8
-    assert ctypes.sizeof(cg.StepOut) == 11 * 8
+    assert ctypes.sizeof(cg.StepOut) == 13 * 8
     assert ctypes.sizeof(cg.Particles) == 24
     # cg_batch_item: desc, particles, u_fine pointer, step outputs; cg_batch_config: 5 int32
-    assert ctypes.sizeof(cg.BatchItem) == ctypes.sizeof(cg.GridDesc) + 24 + 8 + 11 * 8
+    assert ctypes.sizeof(cg.BatchItem) == ctypes.sizeof(cg.GridDesc) + 24 + 8 + 13 * 8
     assert ctypes.sizeof(cg.BatchConfig) == 5 * 4
 
 

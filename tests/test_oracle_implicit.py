@@ -49,7 +49,7 @@ def test_uniform_field_source_equals_implicit_split():
 
 
 def test_volume_weighted_sum_equals_particle_factors():
-    d, pos, vel, eps, cs, perm, nbulk = setup(law=1)
+    d, pos, vel, eps, cs, perm, nbulk = setup(law=1, n=600)
     u = uniform_u(nbulk, (0.1, 0.0, 0.4))
     A, b = oracle.implicit(d, pos, vel, eps, u, cs, perm)
     VB = np.prod(np.asarray(d["extent"]) / (np.asarray(d["fine_n"]) // d["ratio"]))
