@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
     ap.add_argument("--no-graph", action="store_true", help="time eager cg_step calls instead of a CUDA graph")
+    ap.add_argument("--implicit", action="store_true",
+                    help="also form the semi-implicit exchange coefficients (bulk and fine) in every step "
+                         "(device entry only: no e2e line)")
     return ap.parse_args()
 
 
@@ -180,7 +183,7 @@ def workload_name(name, w):
             f"{w.n} spheres, {law}, {prec}")
 
 
-def algorithmic_bytes(g, n, eps_fine=True):
+def algorithmic_bytes(g, n, eps_fine=True, implicit=False):
     """Algorithmic bytes of one step (the minimal traffic of the path) and,
     per launch, of each kernel of this implementation (bytes it must move
     to do its part, FP32; L2-resident gathers of the bulk fields and
@@ -208,8 +211,13 @@ def algorithmic_bytes(g, n, eps_fine=True):
         "project": nf * 12 + nbx * 12,                    # S_f written, S_B read
         "project_eps": nf * 4 + nbx * 4,                  # eps_f written, eps_B read
         "average": nf * 12 + nbx * 16,                    # u_f read, u_B and var written
+        "deposit_implicit": n * (16 + 4) + nbx * 16,      # sorted (beta, beta u) + key read; A, b written
+        "project_implicit": nf * 16 + nbx * 16,           # A_f, b_f written, A, b read
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
+    if implicit:
+        per["drag"] += n * 16                             # the sorted (beta, beta u) record
+        step += n * 16 + nf * 16 + nb * 16                # beta, beta u per particle; A, b on both grids
     return step, per
 
 
@@ -233,7 +241,10 @@ def run_gb300(args):
     pos = torch.from_numpy(w.pos_d).to(dev)
     vel = torch.from_numpy(w.vel).to(dev)
     uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).to(dev)
-    out = g.alloc_outputs(n, var=True, eps_fine=True, device=dev)
+    out = g.alloc_outputs(n, var=True, eps_fine=True, implicit=args.implicit, implicit_fine=args.implicit,
+                          device=dev)
+    if args.implicit:
+        args.no_e2e = True   # the host-buffer entries do not form the semi-implicit fields
     input_bytes = pos.numel() * 4 + vel.numel() * 4 + uf.numel() * 4
 
     def barrier():
@@ -311,7 +322,7 @@ def run_gb300(args):
     prof = g.cg_profile_read()
     g.cg_profile_enable(False)
 
-    step_bytes, kern_bytes = algorithmic_bytes(g, n)
+    step_bytes, kern_bytes = algorithmic_bytes(g, n, implicit=args.implicit)
     peak, peak_src = load_peaks()
     kern_ms = {k: v[1] / v[0] for k, v in prof.items() if v[0]}
     kern_total = {k: v[1] for k, v in prof.items()}
@@ -399,7 +410,8 @@ def run_gb300(args):
                        "eager_ms_per_step": round(eager_ms_step, 5),
                        "launches_per_step": launches_per_step,
                        "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
-                       "step_frac_of_hbm": round(step_gbs / peak, 4)},
+                       "step_frac_of_hbm": round(step_gbs / peak, 4),
+                       "semi_implicit": bool(args.implicit)},
             "roofline": roofline,
             "kernels": {k: {"ms_per_launch": round(kern_ms[k], 5), "share": round(kern_total[k] / tot, 4),
                             "launches_per_step": kern_launches[k]} for k in sorted(kern_total)},

@@ -546,7 +546,7 @@ cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* co
     // coefficients, leaves them to it)
     if (sums) g->part_blocks[PS_PROJ] = (long long)nblk;
 #define CG_PRJ(T, KER)                                                                                   \
-    CG_LAUNCH(g, ncomp == 1 ? "project_eps" : "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2], \
+    CG_LAUNCH(g, ncomp == 1 ? "project_eps" : ncomp == 4 ? "project_implicit" : "project", KER, nblk, 256, 0, (const T*)in[0], (const T*)in[1], (const T*)in[2], \
               (const T*)in[3], ncomp, g->gd, (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], (T*)part,   \
               (long long)nblk, (int)sums)
     if (g->fp64) {
