@@ -66,6 +66,18 @@ def grid(desc: dict) -> Grid:
     return g
 
 
+class BoxGrid(C.Structure):
+    _fields_ = [("x0", C.c_double * 3), ("L", C.c_double * 3), ("n", C.c_int32 * 3)]
+
+
+def box_grid(origin, extent, n) -> BoxGrid:
+    g = BoxGrid()
+    g.x0[:] = origin
+    g.L[:] = extent
+    g.n[:] = n
+    return g
+
+
 def _load():
     global _lib
     with _lock:
@@ -87,6 +99,8 @@ def _load():
                 "or_drag": (i64, [pg, i64, pd, pd, pd, pd, pd]),
                 "or_deposit_momentum": (None, [pg, i64, pd, pi, pi, pd]),
                 "or_implicit": (None, [pg, i64, pd, pd, pd, pd, pi, pi, pd]),
+                "or_map_average": (None, [P(BoxGrid), P(BoxGrid), C.c_int, pd, pd]),
+                "or_map_project": (None, [P(BoxGrid), P(BoxGrid), C.c_int, pd, pd]),
                 "or_particle_state": (None, [pg, i64, pd, pd, pd, pd, pd, pd]),
                 "or_mlp_features": (None, [pg, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd]),
                 "or_project": (None, [pg, C.c_int, pd, pd]),
@@ -243,6 +257,33 @@ def implicit(desc, pos_d, vel, eps_bulk, u_bulk, cell_start, perm):
                     _pi(np.ascontiguousarray(cell_start, np.int32)), _pi(np.ascontiguousarray(perm, np.int32)),
                     _pd(coef))
     return coef[0], coef[1:]
+
+
+def map_average(bulk, fine, u_fine):
+    """Volume-weighted fine -> bulk map between non-nested box grids.
+    bulk, fine: (origin, extent, n) triples; u_fine [ncomp][n_f] or [n_f]."""
+    lib = _load()
+    gb, gf = box_grid(*bulk), box_grid(*fine)
+    u = _f64(u_fine)
+    one = u.ndim == 1
+    u = u.reshape(1 if one else u.shape[0], -1)
+    nb = int(np.prod(bulk[2]))
+    out = np.zeros((u.shape[0], nb))
+    lib.or_map_average(C.byref(gb), C.byref(gf), u.shape[0], _pd(u), _pd(out))
+    return out[0] if one else out
+
+
+def map_project(bulk, fine, s_bulk):
+    """Conservative bulk -> fine map between non-nested box grids."""
+    lib = _load()
+    gb, gf = box_grid(*bulk), box_grid(*fine)
+    sb = _f64(s_bulk)
+    one = sb.ndim == 1
+    sb = sb.reshape(1 if one else sb.shape[0], -1)
+    nf = int(np.prod(fine[2]))
+    out = np.zeros((sb.shape[0], nf))
+    lib.or_map_project(C.byref(gb), C.byref(gf), sb.shape[0], _pd(sb), _pd(out))
+    return out[0] if one else out
 
 
 def particle_state(desc, pos_d, vel, eps_bulk, u_bulk):

@@ -422,6 +422,96 @@ void or_implicit(const or_grid* G, int64_t n, const double* pos_d, const double*
     }
 }
 
+/* ---------------------------------------------------------------- */
+/* Non-nested grid maps                                               */
+/* ---------------------------------------------------------------- */
+static double box_lo(const or_box_grid* G, int a, int64_t i) { return G->x0[a] + (double)i * (G->L[a] / G->n[a]); }
+
+/* Length of the overlap of [a0, a1) and [b0, b1). */
+static double overlap(double a0, double a1, double b0, double b1)
+{
+    const double lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+    return hi > lo ? hi - lo : 0.0;
+}
+
+/* Cells of grid G along axis a that may overlap [lo, hi): [*i0, *i1]. */
+static void index_range(const or_box_grid* G, int a, double lo, double hi, int64_t* i0, int64_t* i1)
+{
+    const double h = G->L[a] / G->n[a];
+    int64_t a0 = (int64_t)floor((lo - G->x0[a]) / h) - 1, a1 = (int64_t)floor((hi - G->x0[a]) / h) + 1;
+    if (a0 < 0) a0 = 0;
+    if (a1 > G->n[a] - 1) a1 = G->n[a] - 1;
+    *i0 = a0;
+    *i1 = a1;
+}
+
+/* Intersection volume of cell (i, j, k) of A with cell (p, q, r) of B. */
+static double cell_overlap(const or_box_grid* A, const int64_t ia[3], const or_box_grid* B, const int64_t ib[3])
+{
+    double v = 1.0;
+    for (int a = 0; a < 3; ++a)
+        v *= overlap(box_lo(A, a, ia[a]), box_lo(A, a, ia[a] + 1), box_lo(B, a, ib[a]), box_lo(B, a, ib[a] + 1));
+    return v;
+}
+
+void or_map_average(const or_box_grid* bulk, const or_box_grid* fine, int ncomp, const double* u_fine,
+                    double* u_bulk)
+{
+    const int64_t nbk = (int64_t)bulk->n[0] * bulk->n[1] * bulk->n[2];
+    const int64_t nfn = (int64_t)fine->n[0] * fine->n[1] * fine->n[2];
+    int64_t B[3];
+    for (B[2] = 0; B[2] < bulk->n[2]; ++B[2])
+    for (B[1] = 0; B[1] < bulk->n[1]; ++B[1])
+    for (B[0] = 0; B[0] < bulk->n[0]; ++B[0]) {
+        const int64_t cb = B[0] + (int64_t)bulk->n[0] * (B[1] + (int64_t)bulk->n[1] * B[2]);
+        int64_t r0[3], r1[3];
+        for (int a = 0; a < 3; ++a) index_range(fine, a, box_lo(bulk, a, B[a]), box_lo(bulk, a, B[a] + 1), &r0[a], &r1[a]);
+        ksum w = {0.0, 0.0};
+        ksum acc[8];
+        memset(acc, 0, sizeof acc);
+        int64_t f[3];
+        for (f[2] = r0[2]; f[2] <= r1[2]; ++f[2])
+        for (f[1] = r0[1]; f[1] <= r1[1]; ++f[1])
+        for (f[0] = r0[0]; f[0] <= r1[0]; ++f[0]) {
+            const double v = cell_overlap(bulk, B, fine, f);
+            if (v == 0.0) continue;
+            const int64_t cf = f[0] + (int64_t)fine->n[0] * (f[1] + (int64_t)fine->n[1] * f[2]);
+            ks_add(&w, v);
+            for (int c = 0; c < ncomp; ++c) ks_add(&acc[c], v * u_fine[c * nfn + cf]);
+        }
+        const double W = ks_get(&w);
+        for (int c = 0; c < ncomp; ++c) u_bulk[c * nbk + cb] = W > 0.0 ? ks_get(&acc[c]) / W : 0.0;
+    }
+}
+
+void or_map_project(const or_box_grid* bulk, const or_box_grid* fine, int ncomp, const double* s_bulk,
+                    double* s_fine)
+{
+    const int64_t nbk = (int64_t)bulk->n[0] * bulk->n[1] * bulk->n[2];
+    const int64_t nfn = (int64_t)fine->n[0] * fine->n[1] * fine->n[2];
+    const double Vf = (fine->L[0] / fine->n[0]) * (fine->L[1] / fine->n[1]) * (fine->L[2] / fine->n[2]);
+    int64_t f[3];
+    for (f[2] = 0; f[2] < fine->n[2]; ++f[2])
+    for (f[1] = 0; f[1] < fine->n[1]; ++f[1])
+    for (f[0] = 0; f[0] < fine->n[0]; ++f[0]) {
+        const int64_t cf = f[0] + (int64_t)fine->n[0] * (f[1] + (int64_t)fine->n[1] * f[2]);
+        int64_t r0[3], r1[3];
+        for (int a = 0; a < 3; ++a) index_range(bulk, a, box_lo(fine, a, f[a]), box_lo(fine, a, f[a] + 1), &r0[a], &r1[a]);
+        ksum acc[8];
+        memset(acc, 0, sizeof acc);
+        int64_t B[3];
+        for (B[2] = r0[2]; B[2] <= r1[2]; ++B[2])
+        for (B[1] = r0[1]; B[1] <= r1[1]; ++B[1])
+        for (B[0] = r0[0]; B[0] <= r1[0]; ++B[0]) {
+            const double v = cell_overlap(bulk, B, fine, f);
+            if (v == 0.0) continue;
+            const int64_t cb = B[0] + (int64_t)bulk->n[0] * (B[1] + (int64_t)bulk->n[1] * B[2]);
+            for (int c = 0; c < ncomp; ++c) ks_add(&acc[c], v * s_bulk[c * nbk + cb]);
+        }
+        for (int c = 0; c < ncomp; ++c) s_fine[c * nfn + cf] = ks_get(&acc[c]) / Vf;
+    }
+}
+
 /* Bulk -> fine transfer of particle fields (Fig. 1): the bulk field is
  * interpolated at each fine cell centre with the particle stencil. */
 void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine)

@@ -110,6 +110,30 @@ void or_implicit(const or_grid* G, int64_t n, const double* pos_d, const double*
                  const double* eps_bulk, const double* u_bulk, const int32_t* cell_start,
                  const int32_t* perm, double* coef);
 
+/* Non-nested grids (the grid-to-grid maps computed once per simulation,
+ * Sec. 2.3): two uniform box grids, bulk and fine, in any relative
+ * position and with any spacings.  V(B & f) is the volume of the
+ * intersection of bulk cell B and fine cell f.
+ *   average (fine -> bulk):  u_B = sum_f V(B & f) u_f / sum_f V(B & f)
+ *                            (0 where no fine cell overlaps B);
+ *   project (bulk -> fine):  S_f = sum_B V(B & f) S_B / V_f
+ *                            (conservative: sum S_f V_f = sum S_B V_B
+ *                            where the fine grid covers the bulk one).
+ * Fields are [ncomp][cells], x fastest.
+ * PARITY: pinned by tests (exact rational weights on tiny grids, nested
+ * grids reduce to the plain mean and to cell injection, conservation,
+ * the adjoint identity between the two maps). */
+typedef struct {
+    double x0[3];        /* origin        */
+    double L[3];         /* extent        */
+    int32_t n[3];        /* cells per axis */
+} or_box_grid;
+
+void or_map_average(const or_box_grid* bulk, const or_box_grid* fine, int ncomp, const double* u_fine,
+                    double* u_bulk);
+void or_map_project(const or_box_grid* bulk, const or_box_grid* fine, int ncomp, const double* s_bulk,
+                    double* s_fine);
+
 /* Interpolate ncomp bulk fields at every fine cell centre. */
 void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine);
 
