@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
     ap.add_argument("--no-graph", action="store_true", help="time eager cg_step calls instead of a CUDA graph")
+    ap.add_argument("--map", action="store_true",
+                    help="time the maps between non-nested grids (bulk 64x64x128, fine 250x250x500 offset)")
     ap.add_argument("--implicit", action="store_true",
                     help="also form the semi-implicit exchange coefficients (bulk and fine) in every step "
                          "(device entry only: no e2e line)")
@@ -605,6 +607,58 @@ def run_learned(args):
     traj.close()
 
 
+def run_map(args):
+    """Maps between non-nested grids on the packed bed's bulk grid and a fine
+    grid of 250 x 250 x 500 cells (3.9 fine cells per bulk cell per axis,
+    offset so it covers the bulk grid): the volume-weighted average of three
+    components and the conservative projection of three, each timed with
+    CUDA events over repeated launches (inputs > L2)."""
+    import numpy as np
+    import torch
+    import paper_1807_11834_gb300 as cg
+
+    bulk = ((0.0, 0.0, 0.0), (1.0, 1.0, 2.0), (64, 64, 128))
+    fine = ((-0.004, -0.004, -0.008), (1.008, 1.008, 2.016), (250, 250, 500))
+    m = cg.Map(bulk, fine)
+    nb_, nf_ = m.n_bulk, m.n_fine
+    g = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.rand(3, nf_, device="cuda", generator=g)
+    ub = torch.empty(3, nb_, device="cuda")
+    sb = torch.rand(3, nb_, device="cuda", generator=g)
+    sf = torch.empty(3, nf_, device="cuda")
+    reps = max(5, min(args.steps, 200))
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_avg = timed(lambda: m.average(u, ub))
+    t_prj = timed(lambda: m.project(sb, sf))
+    peak, src = load_peaks()
+    b_avg = 3 * 4 * nf_ + 3 * 4 * nb_
+    b_prj = 3 * 4 * nf_ + 3 * 4 * nb_
+    line = {"metric": "non-nested map bytes/s", "unit": "GB/s",
+            "config": {"bulk": bulk, "fine": fine, "components": 3, "repetitions": reps,
+                       "l2": f"fine fields {3 * 4 * nf_ / 1e6:.0f} MB > L2"},
+            "average": {"ms": round(t_avg, 5), "algorithmic_bytes": b_avg,
+                        "gbs": round(b_avg / (t_avg * 1e-3) / 1e9, 1),
+                        "frac": round(b_avg / (t_avg * 1e-3) / 1e9 / peak, 4)},
+            "project": {"ms": round(t_prj, 5), "algorithmic_bytes": b_prj,
+                        "gbs": round(b_prj / (t_prj * 1e-3) / 1e9, 1),
+                        "frac": round(b_prj / (t_prj * 1e-3) / 1e9 / peak, 4)},
+            "peak": peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    m.close()
+    print(json.dumps(line))
+
+
 def run_batch(args):
     """64 independent uneven instances (fine edge 32..128, ratio 2/4/8, 10^4
     to 2 10^6 particles each, Taylor-Green fluid, Di Felice, FP32): one by
@@ -689,6 +743,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.map:
+        run_map(args)
     elif args.batch:
         run_batch(args)
     elif args.learned:

@@ -146,6 +146,33 @@ typedef struct {
     void* implicit_fine;   /* [4][n_f] T their projection (needs the bulk ones) nullable */
 } cg_step_out;
 
+/* Maps between two uniform grids that are not nested (any relative position
+ * and spacings): the grid-to-grid transfers of Fig. 1 through a static
+ * structure computed once (Sec. 2.3).  With V(B & f) the volume of the
+ * intersection of bulk cell B and fine cell f:
+ *   cg_map_average (fine -> bulk): u_B = sum_f V(B & f) u_f / sum_f V(B & f)
+ *                                  (0 where no fine cell overlaps B);
+ *   cg_map_project (bulk -> fine): S_f = sum_B V(B & f) S_B / V_f, which
+ *                                  conserves sum S V where the fine grid
+ *                                  covers the bulk one.
+ * Fields are [ncomp][cells] T (x fastest), 1 <= ncomp <= 8, device memory
+ * aligned to T; both grids take the same precision.  The map holds per-axis
+ * compressed-row overlap tables on the device (a few arrays of the axis
+ * sizes); calls are enqueued on its stream. */
+typedef struct {
+    double origin[3];
+    double extent[3];
+    int32_t n[3];        /* cells per axis, product < 2^31 */
+    int32_t prec;        /* cg_precision */
+} cg_box_grid;
+
+typedef struct cg_map cg_map;
+
+cg_status cg_map_create(const cg_box_grid* bulk, const cg_box_grid* fine, void* cuda_stream, cg_map** out);
+cg_status cg_map_destroy(cg_map* m);   /* synchronises its stream; NULL is OK */
+cg_status cg_map_average(cg_map* m, int32_t ncomp, const void* fine_in, void* bulk_out);
+cg_status cg_map_project(cg_map* m, int32_t ncomp, const void* bulk_in, void* fine_out);
+
 /* Human-readable name of a status code (static storage). */
 const char* cg_status_string(cg_status s);
 

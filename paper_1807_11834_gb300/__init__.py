@@ -69,6 +69,11 @@ class StepOut(C.Structure):
                 ("implicit_fine", C.c_void_p)]
 
 
+class BoxGrid(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("extent", C.c_double * 3), ("n", C.c_int32 * 3),
+                ("prec", C.c_int32)]
+
+
 class BatchItem(C.Structure):
     _fields_ = [("desc", GridDesc), ("particles", Particles), ("u_fine", C.c_void_p), ("out", StepOut)]
 
@@ -125,6 +130,10 @@ _SIGS = {
     "cg_batch_default_config": (C.c_int, [C.POINTER(BatchConfig)]),
     "cg_batch_create": (C.c_int, [C.POINTER(BatchItem), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "cg_batch_destroy": (C.c_int, [C.c_void_p]),
+    "cg_map_create": (C.c_int, [C.POINTER(BoxGrid), C.POINTER(BoxGrid), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cg_map_destroy": (C.c_int, [C.c_void_p]),
+    "cg_map_average": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "cg_map_project": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "cg_batch_set_config": (C.c_int, [C.c_void_p, C.POINTER(BatchConfig)]),
     "cg_batch_get_config": (C.c_int, [C.c_void_p, C.POINTER(BatchConfig)]),
     "cg_batch_use_graph": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -592,3 +601,52 @@ def mlp_unpack(flat, hidden=64, k0=16):
 
 def status_string(code: int) -> str:
     return lib().cg_status_string(code).decode()
+
+
+class Map:
+    """Owner of a ``cg_map``: the volume-weighted maps between a bulk and a
+    fine uniform grid that are not nested.  bulk, fine: (origin, extent, n);
+    fields are [ncomp][cells] tensors on the device."""
+
+    def __init__(self, bulk, fine, fp64=False, stream=None):
+        import torch
+        self.dtype = torch.float64 if fp64 else torch.float32
+        self.n_bulk = int(bulk[2][0]) * int(bulk[2][1]) * int(bulk[2][2])
+        self.n_fine = int(fine[2][0]) * int(fine[2][1]) * int(fine[2][2])
+        gb, gf = BoxGrid(), BoxGrid()
+        for g, (o, e, n) in ((gb, bulk), (gf, fine)):
+            g.origin[:] = [float(v) for v in o]
+            g.extent[:] = [float(v) for v in e]
+            g.n[:] = [int(v) for v in n]
+            g.prec = CG_FP64 if fp64 else CG_FP32
+        h = C.c_void_p()
+        _check(lib().cg_map_create(C.byref(gb), C.byref(gf), _stream_handle(stream), C.byref(h)), "cg_map_create")
+        self.h = h
+
+    def _fields(self, t, cells, name):
+        if t.dtype != self.dtype or not t.is_contiguous() or t.numel() % cells != 0:
+            raise ValueError(f"{name}: contiguous {self.dtype} tensor of [ncomp][{cells}] expected")
+        return t.numel() // cells
+
+    def average(self, fine_in, bulk_out):
+        nc = self._fields(fine_in, self.n_fine, "fine_in")
+        if self._fields(bulk_out, self.n_bulk, "bulk_out") != nc:
+            raise ValueError("component counts differ")
+        _check(lib().cg_map_average(self.h, nc, _ptr(fine_in), _ptr(bulk_out)), "cg_map_average")
+
+    def project(self, bulk_in, fine_out):
+        nc = self._fields(bulk_in, self.n_bulk, "bulk_in")
+        if self._fields(fine_out, self.n_fine, "fine_out") != nc:
+            raise ValueError("component counts differ")
+        _check(lib().cg_map_project(self.h, nc, _ptr(bulk_in), _ptr(fine_out)), "cg_map_project")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cg_map_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

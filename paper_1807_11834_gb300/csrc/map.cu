@@ -1,0 +1,317 @@
+// map.cu -- maps between two uniform grids in any relative position and
+// with any spacings: the grid-to-grid transfer of arXiv 1807.11834
+// (Fig. 1 arrows; Sec. 2.3: the mapping structure is static and computed
+// once per simulation) for grids that are not nested.
+//
+// With V(B & f) the volume of the intersection of bulk cell B and fine
+// cell f:
+//   average (fine -> bulk):  u_B = sum_f V(B & f) u_f / sum_f V(B & f)
+//   project (bulk -> fine):  S_f = sum_B V(B & f) S_B / V_f   (conserves sum S V
+//                            where the fine grid covers the bulk one)
+// Both grids are boxes, so V(B & f) is the product of the overlaps of the
+// cells' intervals on the three axes.  The static structure is one
+// compressed-row table per axis and direction (bulk index -> overlapping
+// fine indices and overlap lengths, and fine -> bulk), built once on the
+// host in double and kept on the device; the 3-D weight of a pair is the
+// product of its three axis entries.  Average: one thread per bulk cell
+// walks its fine box (consecutive threads read consecutive fine runs);
+// projection: one thread per fine cell over its (usually 1-2 per axis)
+// bulk cells.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "cg_internal.cuh"
+
+struct cg_map {
+    cg_box_grid bulk, fine;
+    int fp64 = 0;
+    size_t tsize = 4;
+    cudaStream_t stream = nullptr;
+    long long nbulk = 0, nfine = 0;
+    // per axis: [ptr (n+1) int32][idx int32][w T], average (bulk rows) and projection (fine rows)
+    void* dev = nullptr;
+    long long off_bptr[3], off_bidx[3], off_bw[3], off_fptr[3], off_fidx[3], off_fw[3], off_cov[3];
+    double Vf = 0.0;
+};
+
+namespace cg {
+namespace {
+
+// Cell bounds along an axis: x0 + i L / n (the same expression for the upper
+// bound of cell i and the lower bound of cell i + 1).
+inline double bound(const cg_box_grid& G, int a, long long i) { return G.origin[a] + (double)i * (G.extent[a] / G.n[a]); }
+
+inline double overlap_len(double a0, double a1, double b0, double b1) {
+    const double lo = std::max(a0, b0), hi = std::min(a1, b1);
+    return hi > lo ? hi - lo : 0.0;
+}
+
+// Compressed rows of grid R's cells along axis a: for each row cell, the
+// cells of grid C along a that overlap it, and the overlap lengths.
+void axis_rows(const cg_box_grid& R, const cg_box_grid& Cg, int a, std::vector<int>& ptr, std::vector<int>& idx,
+               std::vector<double>& w) {
+    const int nr = R.n[a], nc = Cg.n[a];
+    const double hc = Cg.extent[a] / nc;
+    ptr.assign(nr + 1, 0);
+    idx.clear();
+    w.clear();
+    for (int i = 0; i < nr; ++i) {
+        const double lo = bound(R, a, i), hi = bound(R, a, i + 1);
+        long long j0 = (long long)floor((lo - Cg.origin[a]) / hc) - 1, j1 = (long long)floor((hi - Cg.origin[a]) / hc) + 1;
+        j0 = std::max(j0, 0LL);
+        j1 = std::min(j1, (long long)nc - 1);
+        for (long long j = j0; j <= j1; ++j) {
+            const double v = overlap_len(lo, hi, bound(Cg, a, j), bound(Cg, a, j + 1));
+            if (v > 0.0) {
+                idx.push_back((int)j);
+                w.push_back(v);
+            }
+        }
+        ptr[i + 1] = (int)idx.size();
+    }
+}
+
+template <typename T>
+struct MapDev {
+    const int* bptr[3];
+    const int* bidx[3];
+    const T* bw[3];
+    const int* fptr[3];
+    const int* fidx[3];
+    const T* fw[3];
+    const T* cov[3];   // per bulk index: covered length along the axis
+    int nb[3], nf[3];
+    T inv_Vf;
+};
+
+template <typename T>
+MapDev<T> dev_view(const cg_map* m) {
+    MapDev<T> d;
+    const char* base = (const char*)m->dev;
+    for (int a = 0; a < 3; ++a) {
+        d.bptr[a] = (const int*)(base + m->off_bptr[a]);
+        d.bidx[a] = (const int*)(base + m->off_bidx[a]);
+        d.bw[a] = (const T*)(base + m->off_bw[a]);
+        d.fptr[a] = (const int*)(base + m->off_fptr[a]);
+        d.fidx[a] = (const int*)(base + m->off_fidx[a]);
+        d.fw[a] = (const T*)(base + m->off_fw[a]);
+        d.cov[a] = (const T*)(base + m->off_cov[a]);
+        d.nb[a] = m->bulk.n[a];
+        d.nf[a] = m->fine.n[a];
+    }
+    d.inv_Vf = (T)(1.0 / m->Vf);
+    return d;
+}
+
+constexpr int kMapMaxComp = 8;
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_map_average(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
+    pdl_wait();
+    const long long nbk = (long long)d.nb[0] * d.nb[1] * d.nb[2];
+    const long long nfn = (long long)d.nf[0] * d.nf[1] * d.nf[2];
+    for (long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x; cb < nbk;
+         cb += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(cb % d.nb[0]);
+        const int J = (int)((cb / d.nb[0]) % d.nb[1]);
+        const int K = (int)(cb / ((long long)d.nb[0] * d.nb[1]));
+        CSum<T> acc[NC];
+        for (int kz = __ldg(d.bptr[2] + K); kz < __ldg(d.bptr[2] + K + 1); ++kz) {
+            const long long fz = __ldg(d.bidx[2] + kz);
+            const T wz = __ldg(d.bw[2] + kz);
+            for (int ky = __ldg(d.bptr[1] + J); ky < __ldg(d.bptr[1] + J + 1); ++ky) {
+                const long long fy = __ldg(d.bidx[1] + ky);
+                const T wyz = __ldg(d.bw[1] + ky) * wz;
+                const long long row = d.nf[0] * (fy + (long long)d.nf[1] * fz);
+                for (int kx = __ldg(d.bptr[0] + I); kx < __ldg(d.bptr[0] + I + 1); ++kx) {
+                    const long long f = row + __ldg(d.bidx[0] + kx);
+                    const T w = __ldg(d.bw[0] + kx) * wyz;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[c].add(w * __ldg(in + c * nfn + f));
+                }
+            }
+        }
+        const T W = __ldg(d.cov[0] + I) * __ldg(d.cov[1] + J) * __ldg(d.cov[2] + K);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c * nbk + cb] = W > T(0) ? acc[c].get() / W : T(0);
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_map_project(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
+    pdl_wait();
+    const long long nbk = (long long)d.nb[0] * d.nb[1] * d.nb[2];
+    const long long nfn = (long long)d.nf[0] * d.nf[1] * d.nf[2];
+    for (long long cf = (long long)blockIdx.x * blockDim.x + threadIdx.x; cf < nfn;
+         cf += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(cf % d.nf[0]);
+        const int j = (int)((cf / d.nf[0]) % d.nf[1]);
+        const int k = (int)(cf / ((long long)d.nf[0] * d.nf[1]));
+        T acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = T(0);
+        for (int kz = __ldg(d.fptr[2] + k); kz < __ldg(d.fptr[2] + k + 1); ++kz) {
+            const long long bz = __ldg(d.fidx[2] + kz);
+            const T wz = __ldg(d.fw[2] + kz);
+            for (int ky = __ldg(d.fptr[1] + j); ky < __ldg(d.fptr[1] + j + 1); ++ky) {
+                const long long by = __ldg(d.fidx[1] + ky);
+                const T wyz = __ldg(d.fw[1] + ky) * wz;
+                const long long row = d.nb[0] * (by + (long long)d.nb[1] * bz);
+                for (int kx = __ldg(d.fptr[0] + i); kx < __ldg(d.fptr[0] + i + 1); ++kx) {
+                    const long long b = row + __ldg(d.fidx[0] + kx);
+                    const T w = __ldg(d.fw[0] + kx) * wyz;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[c] = fma(w, __ldg(in + c * nbk + b), acc[c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c * nfn + cf] = acc[c] * d.inv_Vf;
+    }
+}
+
+bool finite3(const double* v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+bool valid_box(const cg_box_grid& G) {
+    if (!finite3(G.origin) || !finite3(G.extent)) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(G.extent[a] > 0.0) || G.n[a] < 1) return false;
+    const long long n = (long long)G.n[0] * G.n[1] * G.n[2];
+    return n <= 2147483647LL && (G.prec == CG_FP32 || G.prec == CG_FP64);
+}
+
+unsigned grid_for(long long m) { return (unsigned)std::max(1LL, std::min((m + 255) / 256, 1LL << 20)); }
+
+}  // namespace
+}  // namespace cg
+
+using namespace cg;
+
+extern "C" cg_status cg_map_create(const cg_box_grid* bulk, const cg_box_grid* fine, void* cuda_stream,
+                                   cg_map** out) {
+    if (!out) return CG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!bulk || !fine || !valid_box(*bulk) || !valid_box(*fine) || bulk->prec != fine->prec) return CG_ERR_INVALID_ARG;
+    cg_map* m = new (std::nothrow) cg_map();
+    if (!m) return CG_ERR_OOM;
+    m->bulk = *bulk;
+    m->fine = *fine;
+    m->fp64 = bulk->prec == CG_FP64;
+    m->tsize = m->fp64 ? 8 : 4;
+    m->stream = (cudaStream_t)cuda_stream;
+    m->nbulk = (long long)bulk->n[0] * bulk->n[1] * bulk->n[2];
+    m->nfine = (long long)fine->n[0] * fine->n[1] * fine->n[2];
+    m->Vf = (fine->extent[0] / fine->n[0]) * (fine->extent[1] / fine->n[1]) * (fine->extent[2] / fine->n[2]);
+    // host tables, then one device block: per axis, bulk rows, fine rows, covered lengths
+    std::vector<int> bp[3], bi[3], fp[3], fi[3];
+    std::vector<double> bw[3], fw[3], cov[3];
+    for (int a = 0; a < 3; ++a) {
+        axis_rows(*bulk, *fine, a, bp[a], bi[a], bw[a]);
+        axis_rows(*fine, *bulk, a, fp[a], fi[a], fw[a]);
+        cov[a].assign(bulk->n[a], 0.0);
+        for (int i = 0; i < bulk->n[a]; ++i)
+            for (int k = bp[a][i]; k < bp[a][i + 1]; ++k) cov[a][i] += bw[a][k];
+    }
+    std::vector<unsigned char> host;
+    auto put = [&](const void* p, size_t bytes) {
+        const long long off = (long long)((host.size() + 255) & ~(size_t)255);
+        host.resize((size_t)off + bytes);
+        if (bytes) memcpy(host.data() + off, p, bytes);
+        return off;
+    };
+    auto put_t = [&](const std::vector<double>& v) {
+        if (m->fp64) return put(v.data(), v.size() * sizeof(double));
+        std::vector<float> f(v.begin(), v.end());
+        return put(f.data(), f.size() * sizeof(float));
+    };
+    for (int a = 0; a < 3; ++a) {
+        m->off_bptr[a] = put(bp[a].data(), bp[a].size() * sizeof(int));
+        m->off_bidx[a] = put(bi[a].data(), bi[a].size() * sizeof(int));
+        m->off_bw[a] = put_t(bw[a]);
+        m->off_fptr[a] = put(fp[a].data(), fp[a].size() * sizeof(int));
+        m->off_fidx[a] = put(fi[a].data(), fi[a].size() * sizeof(int));
+        m->off_fw[a] = put_t(fw[a]);
+        m->off_cov[a] = put_t(cov[a]);
+    }
+    if (cudaMalloc(&m->dev, std::max<size_t>(host.size(), 16)) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return CG_ERR_OOM;
+    }
+    if (cudaMemcpy(m->dev, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(m->dev);
+        delete m;
+        return CG_ERR_CUDA;
+    }
+    *out = m;
+    return CG_OK;
+}
+
+extern "C" cg_status cg_map_destroy(cg_map* m) {
+    if (!m) return CG_OK;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(m->dev);
+    delete m;
+    return CG_OK;
+}
+
+// The map's launches go through CG_LAUNCH's counterpart without a handle:
+// a programmatic dependent launch on the map's stream.
+template <typename K, typename... Args>
+static cg_status map_launch(cg_map* m, K kernel, long long work, Args... args) {
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(grid_for(work));
+    c.blockDim = dim3(256);
+    c.stream = m->stream;
+    c.attrs = a;
+    c.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&c, kernel, args...);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+template <typename T, int NC>
+static cg_status map_apply(cg_map* m, bool avg, const void* in, void* out) {
+    if (avg) return map_launch(m, k_map_average<T, NC>, m->nbulk, dev_view<T>(m), (const T*)in, (T*)out);
+    return map_launch(m, k_map_project<T, NC>, m->nfine, dev_view<T>(m), (const T*)in, (T*)out);
+}
+
+template <typename T>
+static cg_status map_dispatch(cg_map* m, bool avg, int ncomp, const void* in, void* out) {
+    switch (ncomp) {
+        case 1: return map_apply<T, 1>(m, avg, in, out);
+        case 2: return map_apply<T, 2>(m, avg, in, out);
+        case 3: return map_apply<T, 3>(m, avg, in, out);
+        case 4: return map_apply<T, 4>(m, avg, in, out);
+        case 5: return map_apply<T, 5>(m, avg, in, out);
+        case 6: return map_apply<T, 6>(m, avg, in, out);
+        case 7: return map_apply<T, 7>(m, avg, in, out);
+        case 8: return map_apply<T, 8>(m, avg, in, out);
+    }
+    return CG_ERR_INVALID_ARG;
+}
+
+static bool aligned_for(const cg_map* m, const void* p) { return ((uintptr_t)p & (m->tsize - 1)) == 0; }
+
+extern "C" cg_status cg_map_average(cg_map* m, int32_t ncomp, const void* fine_in, void* bulk_out) {
+    if (!m || ncomp < 1 || ncomp > kMapMaxComp || !fine_in || !bulk_out) return CG_ERR_INVALID_ARG;
+    if (!aligned_for(m, fine_in) || !aligned_for(m, bulk_out)) return CG_ERR_INVALID_ARG;
+    return m->fp64 ? map_dispatch<double>(m, true, ncomp, fine_in, bulk_out)
+                   : map_dispatch<float>(m, true, ncomp, fine_in, bulk_out);
+}
+
+extern "C" cg_status cg_map_project(cg_map* m, int32_t ncomp, const void* bulk_in, void* fine_out) {
+    if (!m || ncomp < 1 || ncomp > kMapMaxComp || !bulk_in || !fine_out) return CG_ERR_INVALID_ARG;
+    if (!aligned_for(m, bulk_in) || !aligned_for(m, fine_out)) return CG_ERR_INVALID_ARG;
+    return m->fp64 ? map_dispatch<double>(m, false, ncomp, bulk_in, fine_out)
+                   : map_dispatch<float>(m, false, ncomp, bulk_in, fine_out);
+}

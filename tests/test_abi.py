@@ -69,13 +69,14 @@ def test_struct_layout_matches_the_c_compiler(tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cg_grid_desc), '
                    'sizeof(cg_particles), sizeof(cg_step_out), sizeof(cg_batch_item), '
                    'offsetof(cg_batch_item, u_fine), offsetof(cg_batch_item, out), sizeof(cg_batch_config));'
+                   'printf("%zu %zu\\n", sizeof(cg_box_grid), offsetof(cg_box_grid, prec));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(cg.GridDesc), ctypes.sizeof(cg.Particles), ctypes.sizeof(cg.StepOut),
             ctypes.sizeof(cg.BatchItem), cg.BatchItem.u_fine.offset, cg.BatchItem.out.offset,
-            ctypes.sizeof(cg.BatchConfig)]
+            ctypes.sizeof(cg.BatchConfig), ctypes.sizeof(cg.BoxGrid), cg.BoxGrid.prec.offset]
     assert got == want
 
 
