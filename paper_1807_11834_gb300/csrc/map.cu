@@ -15,8 +15,11 @@
 // host in double and kept on the device; the 3-D weight of a pair is the
 // product of its three axis entries.  Average: one thread per bulk cell
 // walks its fine box (consecutive threads read consecutive fine runs);
-// projection: one thread per fine cell over its (usually 1-2 per axis)
-// bulk cells.
+// projection: when no fine cell overlaps more than two bulk cells along an
+// axis (fine cells no larger than bulk cells) a fixed 2 x 2 x 2 stencil,
+// one CTA per fine row with the bulk rows it reaches collapsed over y and z
+// in shared memory first; else one thread per fine cell through the
+// compressed rows.
 #include <math.h>
 #include <string.h>
 
@@ -35,6 +38,10 @@ struct cg_map {
     // per axis: [ptr (n+1) int32][idx int32][w T], average (bulk rows) and projection (fine rows)
     void* dev = nullptr;
     long long off_bptr[3], off_bidx[3], off_bw[3], off_fptr[3], off_fidx[3], off_fw[3], off_cov[3];
+    // when no fine cell overlaps more than two bulk cells along any axis:
+    // per axis and fine index, the first bulk index and the two overlaps
+    bool two = false;
+    long long off_f2b[3], off_f2w0[3], off_f2w1[3];
     double Vf = 0.0;
 };
 
@@ -84,6 +91,9 @@ struct MapDev {
     const int* fidx[3];
     const T* fw[3];
     const T* cov[3];   // per bulk index: covered length along the axis
+    const int* f2b[3];
+    const T* f2w0[3];
+    const T* f2w1[3];
     int nb[3], nf[3];
     T inv_Vf;
 };
@@ -100,6 +110,9 @@ MapDev<T> dev_view(const cg_map* m) {
         d.fidx[a] = (const int*)(base + m->off_fidx[a]);
         d.fw[a] = (const T*)(base + m->off_fw[a]);
         d.cov[a] = (const T*)(base + m->off_cov[a]);
+        d.f2b[a] = m->two ? (const int*)(base + m->off_f2b[a]) : nullptr;
+        d.f2w0[a] = m->two ? (const T*)(base + m->off_f2w0[a]) : nullptr;
+        d.f2w1[a] = m->two ? (const T*)(base + m->off_f2w1[a]) : nullptr;
         d.nb[a] = m->bulk.n[a];
         d.nf[a] = m->fine.n[a];
     }
@@ -109,26 +122,34 @@ MapDev<T> dev_view(const cg_map* m) {
 
 constexpr int kMapMaxComp = 8;
 
+// Both kernels take cells in x-fastest order with 32-bit index arithmetic
+// (grids hold fewer than 2^31 cells): one division per cell splits the index
+// into the x index and the row (y, z), whose two axis ranges are looked up
+// once per cell.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_map_average(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
     pdl_wait();
-    const long long nbk = (long long)d.nb[0] * d.nb[1] * d.nb[2];
-    const long long nfn = (long long)d.nf[0] * d.nf[1] * d.nf[2];
-    for (long long cb = (long long)blockIdx.x * blockDim.x + threadIdx.x; cb < nbk;
-         cb += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(cb % d.nb[0]);
-        const int J = (int)((cb / d.nb[0]) % d.nb[1]);
-        const int K = (int)(cb / ((long long)d.nb[0] * d.nb[1]));
+    const unsigned nbx = (unsigned)d.nb[0], nby = (unsigned)d.nb[1];
+    const unsigned nbk = nbx * nby * (unsigned)d.nb[2];
+    const unsigned nfx = (unsigned)d.nf[0], nfy = (unsigned)d.nf[1];
+    const size_t nfn = (size_t)nfx * nfy * (unsigned)d.nf[2];
+    for (unsigned cb = blockIdx.x * blockDim.x + threadIdx.x; cb < nbk; cb += gridDim.x * blockDim.x) {
+        const unsigned row = cb / nbx;
+        const unsigned I = cb - row * nbx;
+        const unsigned J = row % nby, K = row / nby;
+        const int x0 = __ldg(d.bptr[0] + I), x1 = __ldg(d.bptr[0] + I + 1);
+        const int y0 = __ldg(d.bptr[1] + J), y1 = __ldg(d.bptr[1] + J + 1);
+        const int z0 = __ldg(d.bptr[2] + K), z1 = __ldg(d.bptr[2] + K + 1);
         CSum<T> acc[NC];
-        for (int kz = __ldg(d.bptr[2] + K); kz < __ldg(d.bptr[2] + K + 1); ++kz) {
-            const long long fz = __ldg(d.bidx[2] + kz);
+        for (int kz = z0; kz < z1; ++kz) {
+            const unsigned fz = (unsigned)__ldg(d.bidx[2] + kz);
             const T wz = __ldg(d.bw[2] + kz);
-            for (int ky = __ldg(d.bptr[1] + J); ky < __ldg(d.bptr[1] + J + 1); ++ky) {
-                const long long fy = __ldg(d.bidx[1] + ky);
+            for (int ky = y0; ky < y1; ++ky) {
+                const unsigned fy = (unsigned)__ldg(d.bidx[1] + ky);
                 const T wyz = __ldg(d.bw[1] + ky) * wz;
-                const long long row = d.nf[0] * (fy + (long long)d.nf[1] * fz);
-                for (int kx = __ldg(d.bptr[0] + I); kx < __ldg(d.bptr[0] + I + 1); ++kx) {
-                    const long long f = row + __ldg(d.bidx[0] + kx);
+                const size_t frow = (size_t)nfx * (fy + nfy * fz);
+                for (int kx = x0; kx < x1; ++kx) {
+                    const size_t f = frow + (unsigned)__ldg(d.bidx[0] + kx);
                     const T w = __ldg(d.bw[0] + kx) * wyz;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[c].add(w * __ldg(in + c * nfn + f));
@@ -137,32 +158,36 @@ __global__ void __launch_bounds__(256) k_map_average(MapDev<T> d, const T* __res
         }
         const T W = __ldg(d.cov[0] + I) * __ldg(d.cov[1] + J) * __ldg(d.cov[2] + K);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) out[c * nbk + cb] = W > T(0) ? acc[c].get() / W : T(0);
+        for (int c = 0; c < NC; ++c) out[(size_t)c * nbk + cb] = W > T(0) ? acc[c].get() / W : T(0);
     }
 }
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_map_project(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
     pdl_wait();
-    const long long nbk = (long long)d.nb[0] * d.nb[1] * d.nb[2];
-    const long long nfn = (long long)d.nf[0] * d.nf[1] * d.nf[2];
-    for (long long cf = (long long)blockIdx.x * blockDim.x + threadIdx.x; cf < nfn;
-         cf += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(cf % d.nf[0]);
-        const int j = (int)((cf / d.nf[0]) % d.nf[1]);
-        const int k = (int)(cf / ((long long)d.nf[0] * d.nf[1]));
+    const unsigned nbx = (unsigned)d.nb[0], nby = (unsigned)d.nb[1];
+    const size_t nbk = (size_t)nbx * nby * (unsigned)d.nb[2];
+    const unsigned nfx = (unsigned)d.nf[0], nfy = (unsigned)d.nf[1];
+    const unsigned nfn = nfx * nfy * (unsigned)d.nf[2];
+    for (unsigned cf = blockIdx.x * blockDim.x + threadIdx.x; cf < nfn; cf += gridDim.x * blockDim.x) {
+        const unsigned row = cf / nfx;
+        const unsigned i = cf - row * nfx;
+        const unsigned j = row % nfy, k = row / nfy;
+        const int x0 = __ldg(d.fptr[0] + i), x1 = __ldg(d.fptr[0] + i + 1);
+        const int y0 = __ldg(d.fptr[1] + j), y1 = __ldg(d.fptr[1] + j + 1);
+        const int z0 = __ldg(d.fptr[2] + k), z1 = __ldg(d.fptr[2] + k + 1);
         T acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = T(0);
-        for (int kz = __ldg(d.fptr[2] + k); kz < __ldg(d.fptr[2] + k + 1); ++kz) {
-            const long long bz = __ldg(d.fidx[2] + kz);
+        for (int kz = z0; kz < z1; ++kz) {
+            const unsigned bz = (unsigned)__ldg(d.fidx[2] + kz);
             const T wz = __ldg(d.fw[2] + kz);
-            for (int ky = __ldg(d.fptr[1] + j); ky < __ldg(d.fptr[1] + j + 1); ++ky) {
-                const long long by = __ldg(d.fidx[1] + ky);
+            for (int ky = y0; ky < y1; ++ky) {
+                const unsigned by = (unsigned)__ldg(d.fidx[1] + ky);
                 const T wyz = __ldg(d.fw[1] + ky) * wz;
-                const long long row = d.nb[0] * (by + (long long)d.nb[1] * bz);
-                for (int kx = __ldg(d.fptr[0] + i); kx < __ldg(d.fptr[0] + i + 1); ++kx) {
-                    const long long b = row + __ldg(d.fidx[0] + kx);
+                const size_t brow = (size_t)nbx * (by + nby * bz);
+                for (int kx = x0; kx < x1; ++kx) {
+                    const size_t b = brow + (unsigned)__ldg(d.fidx[0] + kx);
                     const T w = __ldg(d.fw[0] + kx) * wyz;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[c] = fma(w, __ldg(in + c * nbk + b), acc[c]);
@@ -170,7 +195,89 @@ __global__ void __launch_bounds__(256) k_map_project(MapDev<T> d, const T* __res
             }
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) out[c * nfn + cf] = acc[c] * d.inv_Vf;
+        for (int c = 0; c < NC; ++c) out[(size_t)c * nfn + cf] = acc[c] * d.inv_Vf;
+    }
+}
+
+// Projection when every fine cell overlaps at most two bulk cells per axis:
+// a fixed 2 x 2 x 2 stencil (the second weight 0 where there is one), all
+// loads independent, as in the trilinear projection of nested grids.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_map_project2(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
+    pdl_wait();
+    const unsigned nbx = (unsigned)d.nb[0], nby = (unsigned)d.nb[1], nbz = (unsigned)d.nb[2];
+    const size_t nbk = (size_t)nbx * nby * nbz;
+    const unsigned nfx = (unsigned)d.nf[0], nfy = (unsigned)d.nf[1];
+    const unsigned nfn = nfx * nfy * (unsigned)d.nf[2];
+    for (unsigned cf = blockIdx.x * blockDim.x + threadIdx.x; cf < nfn; cf += gridDim.x * blockDim.x) {
+        const unsigned row = cf / nfx;
+        const unsigned i = cf - row * nfx;
+        const unsigned j = row % nfy, k = row / nfy;
+        const unsigned bx = (unsigned)__ldg(d.f2b[0] + i), by = (unsigned)__ldg(d.f2b[1] + j);
+        const unsigned bz = (unsigned)__ldg(d.f2b[2] + k);
+        const T wx[2] = {__ldg(d.f2w0[0] + i), __ldg(d.f2w1[0] + i)};
+        const T wy[2] = {__ldg(d.f2w0[1] + j), __ldg(d.f2w1[1] + j)};
+        const T wz[2] = {__ldg(d.f2w0[2] + k), __ldg(d.f2w1[2] + k)};
+        // the second neighbour stays inside the grid (its weight is 0 at the edge)
+        const unsigned dx = bx + 1 < nbx ? 1u : 0u, dy = by + 1 < nby ? nbx : 0u;
+        const size_t dz = bz + 1 < nbz ? (size_t)nbx * nby : 0;
+        const size_t b0 = bx + (size_t)nbx * (by + (size_t)nby * bz);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const T* s = in + c * nbk + b0;
+            const T v000 = __ldg(s), v001 = __ldg(s + dx), v010 = __ldg(s + dy), v011 = __ldg(s + dy + dx);
+            const T v100 = __ldg(s + dz), v101 = __ldg(s + dz + dx), v110 = __ldg(s + dz + dy);
+            const T v111 = __ldg(s + dz + dy + dx);
+            const T y0 = wy[0] * fma(wx[1], v001, wx[0] * v000) + wy[1] * fma(wx[1], v011, wx[0] * v010);
+            const T y1 = wy[0] * fma(wx[1], v101, wx[0] * v100) + wy[1] * fma(wx[1], v111, wx[0] * v110);
+            out[(size_t)c * nfn + cf] = (wz[0] * y0 + wz[1] * y1) * d.inv_Vf;
+        }
+    }
+}
+
+// Row-tiled projection (the default for the two-point stencil when its
+// shared memory, NC x (bulk cells per x row) values, fits).  (A row-tiled
+// average that collapsed the fine rows of each bulk row first read the fine
+// field about 1.6 times over, and ran slower than the cell kernel above.)
+// Projection with the two-point stencil: the CTA takes fine row (j, k); it
+// first collapses the (at most 2 x 2) bulk rows over y and z for every bulk
+// x index the row reaches, into shared memory, then thread i combines the
+// two x neighbours of its fine cell.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_map_project2_rows(MapDev<T> d, const T* __restrict__ in, T* __restrict__ out) {
+    pdl_wait();
+    extern __shared__ unsigned char smem_raw[];
+    T* v = reinterpret_cast<T*>(smem_raw);   // [NC][nbx]
+    const unsigned nbx = (unsigned)d.nb[0], nby = (unsigned)d.nb[1], nbz = (unsigned)d.nb[2];
+    const size_t nbk = (size_t)nbx * nby * nbz;
+    const unsigned nfx = (unsigned)d.nf[0], nfy = (unsigned)d.nf[1];
+    const unsigned nfn = nfx * nfy * (unsigned)d.nf[2];
+    const unsigned rows = nfy * (unsigned)d.nf[2];
+    for (unsigned r = blockIdx.x; r < rows; r += gridDim.x) {
+        const unsigned j = r % nfy, k = r / nfy;
+        const unsigned by = (unsigned)__ldg(d.f2b[1] + j), bz = (unsigned)__ldg(d.f2b[2] + k);
+        const T wy0 = __ldg(d.f2w0[1] + j), wy1 = __ldg(d.f2w1[1] + j);
+        const T wz0 = __ldg(d.f2w0[2] + k), wz1 = __ldg(d.f2w1[2] + k);
+        const size_t dy = by + 1 < nby ? nbx : 0, dz = bz + 1 < nbz ? (size_t)nbx * nby : 0;
+        const size_t b0 = (size_t)nbx * (by + (size_t)nby * bz);
+        for (unsigned X = threadIdx.x; X < nbx; X += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T* s = in + c * nbk + b0 + X;
+                v[c * nbx + X] = wz0 * fma(wy1, __ldg(s + dy), wy0 * __ldg(s)) +
+                                 wz1 * fma(wy1, __ldg(s + dz + dy), wy0 * __ldg(s + dz));
+            }
+        }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < nfx; i += blockDim.x) {
+            const unsigned bx = (unsigned)__ldg(d.f2b[0] + i);
+            const unsigned bx1 = bx + 1 < nbx ? bx + 1 : bx;
+            const T wx0 = __ldg(d.f2w0[0] + i), wx1 = __ldg(d.f2w1[0] + i);
+            const unsigned cf = i + nfx * r;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out[(size_t)c * nfn + cf] = fma(wx1, v[c * nbx + bx1], wx0 * v[c * nbx + bx]) * d.inv_Vf;
+        }
+        __syncthreads();
     }
 }
 
@@ -184,7 +291,7 @@ bool valid_box(const cg_box_grid& G) {
     return n <= 2147483647LL && (G.prec == CG_FP32 || G.prec == CG_FP64);
 }
 
-unsigned grid_for(long long m) { return (unsigned)std::max(1LL, std::min((m + 255) / 256, 1LL << 20)); }
+unsigned grid_for(long long m) { return (unsigned)std::max(1LL, std::min((m + 255) / 256, 1LL << 16)); }
 
 }  // namespace
 }  // namespace cg
@@ -228,6 +335,24 @@ extern "C" cg_status cg_map_create(const cg_box_grid* bulk, const cg_box_grid* f
         std::vector<float> f(v.begin(), v.end());
         return put(f.data(), f.size() * sizeof(float));
     };
+    m->two = true;
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < fine->n[a]; ++i) m->two = m->two && fp[a][i + 1] - fp[a][i] <= 2;
+    for (int a = 0; a < 3 && m->two; ++a) {
+        std::vector<int> b0(fine->n[a], 0);
+        std::vector<double> w0(fine->n[a], 0.0), w1(fine->n[a], 0.0);
+        for (int i = 0; i < fine->n[a]; ++i) {
+            const int k0 = fp[a][i], k1 = fp[a][i + 1];
+            if (k1 > k0) {
+                b0[i] = fi[a][k0];
+                w0[i] = fw[a][k0];
+                if (k1 - k0 == 2) w1[i] = fw[a][k0 + 1];
+            }
+        }
+        m->off_f2b[a] = put(b0.data(), b0.size() * sizeof(int));
+        m->off_f2w0[a] = put_t(w0);
+        m->off_f2w1[a] = put_t(w1);
+    }
     for (int a = 0; a < 3; ++a) {
         m->off_bptr[a] = put(bp[a].data(), bp[a].size() * sizeof(int));
         m->off_bidx[a] = put(bi[a].data(), bi[a].size() * sizeof(int));
@@ -279,9 +404,48 @@ static cg_status map_launch(cg_map* m, K kernel, long long work, Args... args) {
     return e == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
+constexpr size_t kMapRowSmem = 96 * 1024;   // shared memory of a row-tiled CTA at most
+
+template <typename K>
+static cg_status row_attr(K kernel, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMapRowSmem) != cudaSuccess) {
+        cudaGetLastError();
+        return CG_ERR_CUDA;
+    }
+    return CG_OK;
+}
+
+// One CTA per row (grid-stride over the rows), with dynamic shared memory.
+template <typename K, typename... Args>
+static cg_status map_launch_rows(cg_map* m, K kernel, long long rows, size_t smem, Args... args) {
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3((unsigned)std::max(1LL, std::min(rows, 65535LL)));
+    c.blockDim = dim3(256);
+    c.dynamicSmemBytes = smem;
+    c.stream = m->stream;
+    c.attrs = a;
+    c.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&c, kernel, args...);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
 template <typename T, int NC>
 static cg_status map_apply(cg_map* m, bool avg, const void* in, void* out) {
     if (avg) return map_launch(m, k_map_average<T, NC>, m->nbulk, dev_view<T>(m), (const T*)in, (T*)out);
+    if (m->two) {
+        const size_t smem = (size_t)NC * m->bulk.n[0] * sizeof(T);
+        if (smem <= kMapRowSmem) {
+            CG_TRY(row_attr(k_map_project2_rows<T, NC>, smem));
+            return map_launch_rows(m, k_map_project2_rows<T, NC>, (long long)m->fine.n[1] * m->fine.n[2], smem,
+                                   dev_view<T>(m), (const T*)in, (T*)out);
+        }
+        return map_launch(m, k_map_project2<T, NC>, m->nfine, dev_view<T>(m), (const T*)in, (T*)out);
+    }
     return map_launch(m, k_map_project<T, NC>, m->nfine, dev_view<T>(m), (const T*)in, (T*)out);
 }
 
