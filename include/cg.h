@@ -228,7 +228,7 @@ cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n, const voi
  *                    (Table 1 porosity field; Sec. 2.4 porosity definition).
  *   CG_DEP_MOMENTUM: per_particle = force [3][n] T;
  *                    bulk_out = S [3][n_b] T, S = -(1/V_B) sum F
- *                    (Eq. UFP: F_fpi is the counterpart of F_drag).
+ *                    (Eq. UFP: F_fpi is the fluid-side reaction to F_drag).
  * Returns CG_ERR_NOT_BINNED without a binning of this n. */
 cg_status cg_deposit(cg_grids* g, int32_t kind, int64_t n, const void* per_particle, void* bulk_out);
 
@@ -271,7 +271,7 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
  * 1 sum (1 - eps_B) V_B, 2..4 sum F_p, 5..7 sum S_B V_B, 8..10 sum S_f V_f,
  * 11 sum |F_p|, 12..14 sum m_p u_p after the advance, 15 particles whose
  * porosity was clamped.
- * Semi-implicit exchange (Eq. UFP: F_fpi, the counterpart of F_drag, is
+ * Semi-implicit exchange (Eq. UFP: F_fpi, the fluid-side reaction to F_drag, is
  * treated semi-implicitly): when out->implicit_bulk is set, it receives
  * A = (1/V_B) sum_p beta_p and b = (1/V_B) sum_p beta_p u_p per bulk cell
  * ([4][n_b] T: A, b_x, b_y, b_z; u_p before the advance), with which the

@@ -21,10 +21,10 @@
  *    densities, diameter, area, viscosity and porosity.  The correlation
  *    itself is not printed; the readings are Di Felice and Ergun / Wen-Yu
  *    (Gidaspow), see or_drag_beta.
- *  - Sec. 1: the coupling uses "cell values or locally interpolated values";
+ *  - Sec. 1: the coupling takes the cell value or a value interpolated locally;
  *    reading: trilinear interpolation from bulk-cell centres with constant
  *    extrapolation in the outer half cell (or the cell value).
- *  - Eq. (UFP): F_fpi is the counterpart of F_drag; reading: the bulk source
+ *  - Eq. (UFP): F_fpi is the fluid-side reaction to F_drag; reading: the bulk source
  *    is S_B = -(1/V_B) sum_{p in B} F_p.
  *  - Eq. (DEM_EQUATIONS): m x'' = F_coll + F_drag + F_g; contacts are out of
  *    scope, the integrator is a reading (velocity first, then position).

@@ -99,7 +99,7 @@ void or_mlp_features(const or_grid* G, int64_t n, const double* pos_d, const dou
 void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk);
 
-/* Semi-implicit exchange coefficients (Eq. UFP: F_fpi, the counterpart of
+/* Semi-implicit exchange coefficients (Eq. UFP: F_fpi, the fluid-side reaction to
  * F_drag, is treated semi-implicitly).  With F_p = beta_p (u_f(x_p) - u_p):
  *   A_B = (1/V_B) sum_{p in B} beta_p,   b_B = (1/V_B) sum_{p in B} beta_p u_p,
  * so that the fluid solver takes F_fpi = -A u_f + b with A in its matrix.

@@ -5,7 +5,7 @@
 // Porosity (Table 1 of arXiv 1807.11834: porosity field from the particle
 // volumes of a cell; Sec. 2.4, beside Eq. DragLaw: porosity = fluid volume / cell volume):
 // phi_B = sum_{p in B} V_p / V_B, eps_B = 1 - phi_B.
-// Reaction (Eq. UFP: F_fpi is the counterpart of F_drag):
+// Reaction (Eq. UFP: F_fpi is the fluid-side reaction to F_drag):
 // S_B = -(1/V_B) sum_{p in B} F_p.
 //
 // Both are segmented sums over the stable bin order: one thread per bulk

@@ -1,6 +1,6 @@
 // drag.cu -- (a3) drag on every particle, Eq. (DragLaw) of arXiv 1807.11834:
 // F = beta (u_f - u_p), with the porosity and the fluid velocity taken at the
-// particle from the bulk grid ("cell values or locally interpolated values",
+// particle from the bulk grid (the cell value or a local interpolant,
 // Sec. 1), and beta from a correlation of slip, densities, diameter,
 // viscosity and porosity.  Optionally (a5) the semi-implicit Euler advance
 // of Eq. (DEM_EQUATIONS) without contacts.

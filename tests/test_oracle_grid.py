@@ -169,7 +169,7 @@ def test_porosity_hand_worked_golden():
 
 
 # --------------------------------------------------------------------------
-# A: fine -> bulk averaging (Fig. 1 "Fluid Solution")
+# A: fine -> bulk averaging (Fig. 1, fine-to-coarse arrow)
 # --------------------------------------------------------------------------
 def test_average_brute_force_reshape_mean():
     desc = desc_small()
@@ -229,7 +229,7 @@ def test_average_conserves_volume_integral():
 
 
 # --------------------------------------------------------------------------
-# I: interpolation ("cell values or locally interpolated values", Sec. 1)
+# I: interpolation (cell value or local interpolant, Sec. 1)
 # --------------------------------------------------------------------------
 def hat_interp(desc, bulk, x):
     """Independent formulation: clamp the lattice coordinate to the hull of
@@ -320,7 +320,7 @@ def test_cell_interp_is_cell_value():
 
 
 # --------------------------------------------------------------------------
-# P: bulk -> fine projection (Fig. 1 "Particle related fields")
+# P: bulk -> fine projection (Fig. 1, coarse-to-fine arrow)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("r", [2, 3, 4, 8])
 def test_projection_brute_force_and_conservation(r):

@@ -1,5 +1,5 @@
 """Pins of the oracle's semi-implicit exchange coefficients (Eq. UFP: the
-fluid-particle force F_fpi, counterpart of F_drag, is treated
+fluid-particle force F_fpi, the fluid-side reaction to F_drag, is treated
 semi-implicitly): A_B = sum beta_p / V_B and b_B = sum beta_p u_p / V_B, so
 the fluid solver takes F_fpi = -A u_f + b.
 
