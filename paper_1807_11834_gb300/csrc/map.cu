@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(256) k_map_average(MapDev<T> d, const T* __res
         const int x0 = __ldg(d.bptr[0] + I), x1 = __ldg(d.bptr[0] + I + 1);
         const int y0 = __ldg(d.bptr[1] + J), y1 = __ldg(d.bptr[1] + J + 1);
         const int z0 = __ldg(d.bptr[2] + K), z1 = __ldg(d.bptr[2] + K + 1);
+        // each fine row's few x terms in plain FMAs, the row sums (weighted
+        // by y and z) into compensated sums
         CSum<T> acc[NC];
         for (int kz = z0; kz < z1; ++kz) {
             const unsigned fz = (unsigned)__ldg(d.bidx[2] + kz);
@@ -147,13 +149,18 @@ __global__ void __launch_bounds__(256) k_map_average(MapDev<T> d, const T* __res
             for (int ky = y0; ky < y1; ++ky) {
                 const unsigned fy = (unsigned)__ldg(d.bidx[1] + ky);
                 const T wyz = __ldg(d.bw[1] + ky) * wz;
-                const size_t frow = (size_t)nfx * (fy + nfy * fz);
-                for (int kx = x0; kx < x1; ++kx) {
-                    const size_t f = frow + (unsigned)__ldg(d.bidx[0] + kx);
-                    const T w = __ldg(d.bw[0] + kx) * wyz;
+                const T* rowp = in + (size_t)nfx * (fy + nfy * fz);
+                T rs[NC];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[c].add(w * __ldg(in + c * nfn + f));
+                for (int c = 0; c < NC; ++c) rs[c] = T(0);
+                for (int kx = x0; kx < x1; ++kx) {
+                    const unsigned fx = (unsigned)__ldg(d.bidx[0] + kx);
+                    const T wx = __ldg(d.bw[0] + kx);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) rs[c] = fma(wx, __ldg(rowp + c * nfn + fx), rs[c]);
                 }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[c].add(wyz * rs[c]);
             }
         }
         const T W = __ldg(d.cov[0] + I) * __ldg(d.cov[1] + J) * __ldg(d.cov[2] + K);
