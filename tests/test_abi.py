@@ -96,3 +96,40 @@ def test_invalid_arguments_rejected_before_any_gpu_work(libcg):
     assert L.cg_create_grids(ctypes.byref(d), None, ctypes.byref(h)) == 1
     assert L.cg_create_grids(None, None, ctypes.byref(h)) == 1
     assert L.cg_bin_particles(None, 0, None, None, None, None) == 1
+
+
+def test_argument_checks_answer_before_any_device_work():
+    """Descriptors and grids the ABI rejects come back CG_ERR_INVALID_ARG
+    (1) synchronously, before the library touches a device, so these run
+    without a GPU: unknown sort choices, non-nested ratios, a bulk axis of
+    one cell, and degenerate or mixed-precision map grids."""
+    import paper_1807_11834_gb300 as cg
+    import synth
+    L = cg.lib()
+    base = synth.tiny(seed=0, n=1).desc
+    for bad in (dict(sort_digits=2), dict(sort_digits=12), dict(sort_digits=-1), dict(ratio=3),
+                dict(fine_n=(8, 8, 4), ratio=4), dict(extent=(1.0, 0.0, 1.0))):
+        d = dict(base)
+        d.update(bad)
+        h = ctypes.c_void_p()
+        assert L.cg_create_grids(ctypes.byref(cg.make_desc(d)), None, ctypes.byref(h)) == 1, bad
+        assert not h.value
+    ok = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (4, 4, 4))
+
+    def box(o, e, n, prec=0):
+        g = cg.BoxGrid()
+        g.origin[:] = o
+        g.extent[:] = e
+        g.n[:] = n
+        g.prec = prec
+        return g
+    for b, f in ((box(*ok), box((0, 0, 0), (1, 1, 1), (4, 0, 4))),
+                 (box((0, 0, 0), (1, -1, 1), (4, 4, 4)), box(*ok)),
+                 (box(*ok, prec=1), box(*ok, prec=0)),
+                 (box(*ok, prec=3), box(*ok, prec=3)),
+                 (box((0, 0, float("nan")), (1, 1, 1), (4, 4, 4)), box(*ok))):
+        h = ctypes.c_void_p()
+        assert L.cg_map_create(ctypes.byref(b), ctypes.byref(f), None, ctypes.byref(h)) == 1
+        assert not h.value
+    assert L.cg_map_average(None, 1, None, None) == 1
+    assert L.cg_destroy_grids(None) == 0 and L.cg_map_destroy(None) == 0
