@@ -204,6 +204,19 @@ cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, in
 cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
                            int32_t* cell_out, int32_t* perm_out, int32_t* cell_start_out);
 
+/* (a0, optional) Physical reorder of the particles into the binned order:
+ * pos_out[s] = pos_d[perm[s]] and vel_out[s] = vel[perm[s]] (vel and
+ * vel_out nullable together), for the binning of these n particles (made
+ * by cg_bin_particles or cg_step with the same n; CG_ERR_NOT_BINNED
+ * otherwise).  The output arrays are the caller's, [n] T4, 16-byte aligned,
+ * and must not overlap the inputs.  Particles kept in cell order make the
+ * later steps' memory access follow the grids: the per-cell sort
+ * (CG_SORT_CELLS) then places and sorts in order, and the deposits and the
+ * drag read neighbours together.  Rebinning the reordered positions gives
+ * the identity permutation. */
+cg_status cg_reorder_particles(cg_grids* g, int64_t n, const void* pos_d, const void* vel, void* pos_out,
+                               void* vel_out);
+
 /* Binning that allocates nothing, for callers that must not allocate
  * device memory (for example code running while another component
  * captures a CUDA graph, or plug-ins restricted to the memory their host

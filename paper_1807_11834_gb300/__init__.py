@@ -130,6 +130,7 @@ _SIGS = {
     "cg_batch_default_config": (C.c_int, [C.POINTER(BatchConfig)]),
     "cg_batch_create": (C.c_int, [C.POINTER(BatchItem), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "cg_batch_destroy": (C.c_int, [C.c_void_p]),
+    "cg_reorder_particles": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_map_create": (C.c_int, [C.POINTER(BoxGrid), C.POINTER(BoxGrid), C.c_void_p, C.POINTER(C.c_void_p)]),
     "cg_map_destroy": (C.c_int, [C.c_void_p]),
     "cg_map_average": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -324,6 +325,18 @@ class Grids:
             t = out.get(name)
             setattr(so, name, None if t is None else t.data_ptr())
         return so
+
+    def cg_reorder_particles(self, pos_d, vel, pos_out, vel_out):
+        """Gather the particle records into the order of the last binning
+        of these n particles (vel / vel_out may both be None)."""
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(pos_out, 4 * n, name="pos_out")
+        if vel is not None:
+            self._t(vel, 4 * n, name="vel")
+            self._t(vel_out, 4 * n, name="vel_out")
+        _check(lib().cg_reorder_particles(self.h, n, _ptr(pos_d), _ptr(vel), _ptr(pos_out), _ptr(vel_out)),
+               "cg_reorder_particles")
 
     def cg_step(self, pos_d, vel, u_fine, out, dt=0.0):
         n = pos_d.shape[0]

@@ -395,6 +395,25 @@ cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d, int32_t* c
     return copy_bins(g, n, cell_out, perm_out, cell_start_out);
 }
 
+cg_status cg_reorder_particles(cg_grids* g, int64_t n, const void* pos_d, const void* vel, void* pos_out,
+                               void* vel_out) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_n(n));
+    if ((vel == nullptr) != (vel_out == nullptr)) return CG_ERR_INVALID_ARG;
+    if (n == 0) return CG_OK;
+    if (!pos_d || !pos_out || !aligned16(pos_d) || !aligned16(pos_out)) return CG_ERR_INVALID_ARG;
+    if (vel && (!aligned16(vel) || !aligned16(vel_out))) return CG_ERR_INVALID_ARG;
+    const size_t bytes = 4 * g->tsize * (size_t)n;
+    auto overlap = [&](const void* a, const void* b) {
+        const char *x = (const char*)a, *y = (const char*)b;
+        return x < y + bytes && y < x + bytes;
+    };
+    if (overlap(pos_d, pos_out) || (vel && (overlap(vel, vel_out) || overlap(pos_d, vel_out) || overlap(vel, pos_out))))
+        return CG_ERR_INVALID_ARG;
+    if (g->n_binned != n) return CG_ERR_NOT_BINNED;
+    return launch_reorder(g, n, pos_d, vel, pos_out, vel_out);
+}
+
 cg_status cg_deposit(cg_grids* g, int32_t kind, int64_t n, const void* per_particle, void* bulk_out) {
     CG_TRY(check_handle(g));
     CG_TRY(check_n(n));

@@ -916,6 +916,38 @@ static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, do
 }
 
 // ----------------------------------------------------------------------
+// Physical reorder into the binned order: slot s takes the records of
+// particle perm[s] (16 or 32 bytes each; consecutive threads write
+// consecutive slots).
+// ----------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_reorder(const int32_t* __restrict__ perm, long long n,
+                                                 const T* __restrict__ pos, const T* __restrict__ vel,
+                                                 T* __restrict__ pos_out, T* __restrict__ vel_out) {
+    pdl_wait();
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int p = __ldg(perm + s);
+        const V4<T> a = ld4(pos, p);
+        st4(pos_out, s, a.x, a.y, a.z, a.w);
+        if (vel) {
+            const V4<T> b = ld4(vel, p);
+            st4(vel_out, s, b.x, b.y, b.z, b.w);
+        }
+    }
+}
+
+cg_status launch_reorder(cg_grids* g, long long n, const void* pos_d, const void* vel, void* pos_out, void* vel_out) {
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)g->num_sms * 16);
+    if (g->fp64)
+        CG_LAUNCH(g, "reorder", k_reorder<double>, grid, 256, 0, g->perm, n, (const double*)pos_d,
+                  (const double*)vel, (double*)pos_out, (double*)vel_out);
+    else
+        CG_LAUNCH(g, "reorder", k_reorder<float>, grid, 256, 0, g->perm, n, (const float*)pos_d, (const float*)vel,
+                  (float*)pos_out, (float*)vel_out);
+    return CG_OK;
+}
+
+// ----------------------------------------------------------------------
 // Batched binning phases (FP32 instances)
 // ----------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) kb_bin_key(BLaunch L) {

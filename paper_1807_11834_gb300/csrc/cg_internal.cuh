@@ -276,6 +276,8 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
                                 bool prefilled = false, void* rec = nullptr, void* eps_t = nullptr);
 cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
+// Gather the particle records into the binned order (cg_reorder_particles).
+cg_status launch_reorder(cg_grids* g, long long n, const void* pos_d, const void* vel, void* pos_out, void* vel_out);
 // Semi-implicit coefficients [4][n_b] (A, b) from the drag's sorted (beta, beta u) records.
 cg_status launch_deposit_implicit(cg_grids* g, long long n, void* coef_bulk);
 cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_soa, void* S_bulk);

@@ -470,3 +470,40 @@ def test_not_binned_and_bad_args(cuda_lib):
         d["sort_digits"] = bad
         with pytest.raises(cuda_lib.CgError):
             cuda_lib.Grids(d)
+
+
+def test_reorder_particles_into_cell_order(cuda_lib):
+    """cg_reorder_particles gathers the records into the binned order;
+    rebinning them gives the identity permutation, and a step on the
+    reordered particles gives bit-identical bulk and fine fields (each cell
+    sums the same particles in the same order) and the same forces,
+    permuted."""
+    import torch
+    cg = cuda_lib
+    w = synth.small_clustered_bed(seed=8)
+    d = dict(w.desc)
+    d["sort_digits"] = cg.CG_SORT_CELLS
+    g = cg.Grids(d)
+    pos, vel, uf = inputs(w)
+    out = g.alloc_outputs(w.n, eps_fine=True, bins=True)
+    g.cg_step(pos, vel, uf, out)
+    pos2, vel2 = torch.empty_like(pos), torch.empty_like(vel)
+    g.cg_reorder_particles(pos, vel, pos2, vel2)
+    perm = out["perm"].long()
+    torch.cuda.synchronize()
+    assert torch.equal(pos2, pos[perm]) and torch.equal(vel2, vel[perm])
+    out2 = g.alloc_outputs(w.n, eps_fine=True, bins=True)
+    g.cg_step(pos2, vel2, uf, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out2["perm"], torch.arange(w.n, device="cuda", dtype=torch.int32))
+    assert torch.equal(out2["cell_start"], out["cell_start"])
+    for k in ("eps_bulk", "u_bulk", "var_bulk", "S_bulk", "S_fine", "eps_fine"):
+        assert torch.equal(out2[k], out[k]), k
+    assert torch.equal(out2["force"], out["force"][:, perm])
+    # a different particle count has no binning; overlapping outputs are refused
+    with pytest.raises(cg.CgError) as e:
+        g.cg_reorder_particles(pos[:-1], None, pos2[:-1], None)
+    assert e.value.code == 4
+    with pytest.raises(cg.CgError):
+        g.cg_reorder_particles(pos2, None, pos2, None)
+    g.close()
