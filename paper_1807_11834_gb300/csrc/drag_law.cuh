@@ -71,6 +71,17 @@ __device__ __forceinline__ void axis_weight(double x, const GridDev& g, int a, i
 template <typename T>
 __device__ __forceinline__ T lerp_(T a, T b, T t) { return fma(t, b - a, a); }
 
+// Read-only load of one packed record at p.
+__device__ __forceinline__ V4<float> ldv4(const V4<float>* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ldv4(const V4<double>* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
 template <typename T>
 __device__ __forceinline__ V4<T> lerp4(const V4<T>& a, const V4<T>& b, T t) {
     return {lerp_(a.x, b.x, t), lerp_(a.y, b.y, t), lerp_(a.z, b.z, t), lerp_(a.w, b.w, t)};
@@ -89,12 +100,13 @@ __device__ __forceinline__ V4<T> gather(const T* __restrict__ bulk4, T x, T y, T
     axis_weight(x, g, 0, i0, tx);
     axis_weight(y, g, 1, j0, ty);
     axis_weight(z, g, 2, k0, tz);
-    const long long sx = 1, sy = g.nb[0], sz = (long long)g.nb[0] * g.nb[1];
-    const long long c = i0 + sy * j0 + sz * k0;
-    V4<T> a00 = lerp4(ld4(bulk4, c), ld4(bulk4, c + sx), tx);
-    V4<T> a10 = lerp4(ld4(bulk4, c + sy), ld4(bulk4, c + sy + sx), tx);
-    V4<T> a01 = lerp4(ld4(bulk4, c + sz), ld4(bulk4, c + sz + sx), tx);
-    V4<T> a11 = lerp4(ld4(bulk4, c + sz + sy), ld4(bulk4, c + sz + sy + sx), tx);
+    // cell indices fit in int (fewer than 2^31 bulk cells)
+    const int sy = g.nb[0], sz = g.nb[0] * g.nb[1];
+    const V4<T>* b = reinterpret_cast<const V4<T>*>(bulk4) + (i0 + sy * j0 + sz * k0);
+    V4<T> a00 = lerp4(ldv4(b), ldv4(b + 1), tx);
+    V4<T> a10 = lerp4(ldv4(b + sy), ldv4(b + sy + 1), tx);
+    V4<T> a01 = lerp4(ldv4(b + sz), ldv4(b + sz + 1), tx);
+    V4<T> a11 = lerp4(ldv4(b + sz + sy), ldv4(b + sz + sy + 1), tx);
     return lerp4(lerp4(a00, a10, ty), lerp4(a01, a11, ty), tz);
 }
 
@@ -123,7 +135,9 @@ __device__ __forceinline__ T drag_beta(int law, T eps, T phi, T d, T smag, const
         return M<T>::pi8() * P.rho * d * d * cds * M<T>::pow_(eps, T(2) - chi);
     }
     const T vp = M<T>::pi6() * d * d * d;
-    if (eps < P.eps_switch) return (T(150) * phi * P.mu / (eps * d * d) + T(1.75) * P.rho * smag / d) * vp;
+    // Ergun (150 phi mu / (eps d^2) + 1.75 rho |s| / d) V_p with V_p = pi d^3 / 6,
+    // rearranged to one division: pi/6 d (150 phi mu / eps + 1.75 rho |s| d)
+    if (eps < P.eps_switch) return M<T>::pi6() * d * (T(150) * phi * P.mu / eps + T(1.75) * P.rho * smag * d);
     const T eRe = eps * P.rho_mu * d * smag;
     T cds;
     if (eRe < T(1000)) cds = T(24) * P.mu / (eps * P.rho * d) * (T(1) + T(0.15) * M<T>::pow_(eRe, T(0.687)));
