@@ -472,7 +472,8 @@ def test_not_binned_and_bad_args(cuda_lib):
             cuda_lib.Grids(d)
 
 
-def test_reorder_particles_into_cell_order(cuda_lib):
+@pytest.mark.parametrize("fp64", [False, True])
+def test_reorder_particles_into_cell_order(cuda_lib, fp64):
     """cg_reorder_particles gathers the records into the binned order;
     rebinning them gives the identity permutation, and a step on the
     reordered particles gives bit-identical bulk and fine fields (each cell
@@ -480,7 +481,7 @@ def test_reorder_particles_into_cell_order(cuda_lib):
     permuted."""
     import torch
     cg = cuda_lib
-    w = synth.small_clustered_bed(seed=8)
+    w = synth.tiny(seed=8, n=20_000) if fp64 else synth.small_clustered_bed(seed=8)
     d = dict(w.desc)
     d["sort_digits"] = cg.CG_SORT_CELLS
     g = cg.Grids(d)
