@@ -475,7 +475,7 @@ def run_reference(args):
 def run_learned(args):
     """Learned closure against the plain path on one workload family:
     train on seeds 0 and 1 (56-step runs, stale records refreshed every 2,
-    5, 10, 20 and 50 steps, fluid relaxed by the coupling source), judge the
+    5, 10, 20 and 50 steps, fluid relaxed by the coupling source), score the
     drag error on seed 2
     at several refresh intervals K, then time the plain step and the
     learned stale step (CUDA graphs) and report the amortised throughput of
@@ -495,7 +495,7 @@ def run_learned(args):
     make = getattr(synth, args.workload)
     dt = 1e-4                      # the clustered bed's step; the packed bed is advanced with the same
     t0 = time.time()
-    # runs long enough to cover every refresh interval judged below
+    # runs long enough to cover every refresh interval scored below
     F, T = closure.generate_pairs(make, seeds=(0, 1), refreshes=(2, 5, 10, 20, 50), steps=56,
                                   n_pairs=2_000_000, dt=dt)
     t_gen = time.time() - t0

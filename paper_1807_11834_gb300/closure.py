@@ -218,7 +218,7 @@ def evaluate(m: Mlp, make, seed, refresh=5, steps=30, device="cuda", dt=None):
     F_le = torch.empty_like(t.out["force"])
     acc = dict(num_st=0.0, num_le=0.0, den=0.0, fall=0, rows=0)
 
-    def judge(fresh):
+    def score(fresh):
         if fresh:
             return
         g = t.grids
@@ -236,7 +236,7 @@ def evaluate(m: Mlp, make, seed, refresh=5, steps=30, device="cuda", dt=None):
         acc["rows"] += w.n
 
     for _ in range(steps):
-        t.advance(judge)
+        t.advance(score)
     m.bind(None, None)
     t.close()
     return {"err_stale": (acc["num_st"] / acc["den"]) ** 0.5, "err_learned": (acc["num_le"] / acc["den"]) ** 0.5,

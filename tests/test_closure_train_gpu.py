@@ -5,7 +5,7 @@ ratio 4, 500,000 log-normal spheres in 200 clusters, Di Felice, gravity,
 dt 1e-4) with the fluid relaxed by the coupling source each step.  The
 closure is trained on the GPU (cg_mlp_features, cg_mlp_train_step) from
 seeds 0 and 1 with the bulk record refreshed every 2, 5 and 10 steps, and
-judged on held-out seed 2 against the plain path with a fresh average on
+scored on held-out seed 2 against the plain path with a fresh average on
 every step: the relative L2 drag error of the learned drag must be well
 below that of the stale drag (c = 1) at every refresh interval, with few
 rows falling back.
