@@ -395,11 +395,15 @@ def test_edge_empty_particle_set(cuda_lib):
     assert got["sums"][0] == 0.0 and got["sums"][2] == 0.0
 
 
-def test_edge_faces_outside_and_one_crowded_cell(cuda_lib):
+@pytest.mark.parametrize("sort", [0, 1])
+def test_edge_faces_outside_and_one_crowded_cell(cuda_lib, sort):
     """Particles exactly on bulk faces and on the upper domain faces, some
     outside (clamped and counted), and 30,000 in a single cell (one long
-    segment across many sort tiles)."""
+    segment across many sort tiles), with the automatic sort (the digit sort
+    at this density) and with the per-cell sort (the cell goes to its
+    large-cell digit passes)."""
     w = synth.tiny(seed=9, n=40_000, fine=32, ratio=4, fp64=False)
+    w.desc["sort_digits"] = sort
     rng = np.random.default_rng(0)
     pos = w.pos_d
     H = 1.0 / 8
