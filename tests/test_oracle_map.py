@@ -10,6 +10,7 @@ from fractions import Fraction as Fr
 import itertools
 
 import numpy as np
+import pytest
 
 import oracle
 
@@ -98,3 +99,35 @@ def test_constants_stay_constant_and_uncovered_cells_are_zero():
     fine = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (3, 3, 3))
     got = oracle.map_average(bulk, fine, np.ones(27))
     assert np.allclose(got[:2], 1.0) and np.all(got[2:] == 0.0)
+
+
+def test_random_geometries_conserve_and_stay_adjoint():
+    """Any pair of box grids where the fine one covers the bulk one:
+    conservation of sum S V, the adjoint identity, constants kept."""
+    hypothesis = pytest.importorskip("hypothesis")
+    st = hypothesis.strategies
+
+    @hypothesis.settings(max_examples=40, deadline=None)
+    @hypothesis.given(st.lists(st.integers(1, 6), min_size=3, max_size=3),
+                      st.lists(st.integers(1, 9), min_size=3, max_size=3),
+                      st.lists(st.floats(0.0, 0.3), min_size=6, max_size=6),
+                      st.integers(0, 2 ** 31 - 1))
+    def check(nb, nf, pad, seed):
+        L = np.array([1.0, 0.7, 1.3])
+        bulk = ((0.0, 0.0, 0.0), tuple(L), tuple(nb))
+        lo = -np.array(pad[:3]) * L
+        hi = L * (1.0 + np.array(pad[3:]))
+        fine = (tuple(lo), tuple(hi - lo), tuple(nf))
+        rng = np.random.default_rng(seed)
+        S = rng.normal(size=int(np.prod(nb)))
+        u = rng.normal(size=int(np.prod(nf)))
+        Sf = oracle.map_project(bulk, fine, S)
+        ub = oracle.map_average(bulk, fine, u)
+        VB = np.prod(L / np.array(nb))
+        Vf = np.prod((hi - lo) / np.array(nf))
+        scale = np.abs(S).sum() * VB + 1e-300
+        assert abs(Sf.sum() * Vf - S.sum() * VB) <= 1e-12 * scale
+        assert abs((Vf * u * Sf).sum() - (VB * ub * S).sum()) <= 1e-11 * (np.abs(u).max() * scale)
+        assert np.allclose(oracle.map_average(bulk, fine, np.full(u.size, 2.5)), 2.5, rtol=0, atol=1e-14)
+
+    check()
