@@ -414,9 +414,12 @@ int batch_deposit_occupancy(int phase) {
 // ----------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// Grid of the segmented deposits: at most one chunk per warp, and no more
+// CTAs than are resident at once (4 per SM at their 64 registers), so the
+// grid-stride loop runs without a second, partial wave.
 static unsigned seg_blocks(cg_grids* g, long long n) {
     const long long chunks = (n + kSegChunk - 1) / kSegChunk;
-    return (unsigned)std::max(1LL, std::min((chunks + 7) / 8, (long long)g->num_sms * 8));
+    return (unsigned)std::max(1LL, std::min((chunks + 7) / 8, (long long)g->num_sms * 4));
 }
 
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,

@@ -185,7 +185,10 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
                       bool sums, double dt, void* coef_bulk) {
     const bool euler = dt > 0.0;
     void* part = part_ptr(g, PS_DRAG);
-    const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * 8));
+    // exactly the resident CTAs (the launch bounds' minimum per SM): a grid-stride
+    // loop with no second, partial wave of blocks
+    const long long per_sm = g->fp64 ? 2 : 4;
+    const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * per_sm));
     g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
     void* Fs = S_bulk ? g->Fs : nullptr;
     void* Bs = nullptr;
