@@ -11,7 +11,8 @@
 // The result is the stable order (ids ascending within each cell), built by
 // one of two sorts that give identical bins:
 //
-// Per-cell sort (default up to 2^23 particles): the count atomics hand out
+// Per-cell sort (the default up to 2^23 particles and 32 per bulk cell on
+// average; batched instances take it on request): the count atomics hand out
 // arrival ranks, the scan of the counts gives the cell starts, each
 // particle is placed at start + rank, and each cell's ids are then sorted
 // (details below, before the kernels).

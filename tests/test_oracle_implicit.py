@@ -96,3 +96,27 @@ def test_b_is_linear_in_particle_velocity_in_the_viscous_regime():
     A2, b2 = oracle.implicit(d, pos, v2, eps, u, cs, perm)
     assert np.allclose(A2, A1, rtol=1e-6)
     assert np.allclose(b2, 2.0 * b1, rtol=1e-6, atol=1e-6 * np.abs(b1).max())
+
+
+def test_uniform_field_identity_over_random_cases():
+    """The uniform-field identity for random particle sets, laws, fluid
+    velocities and particle speeds (property-based)."""
+    import pytest
+    hypothesis = pytest.importorskip("hypothesis")
+    st = hypothesis.strategies
+
+    @hypothesis.settings(max_examples=25, deadline=None)
+    @hypothesis.given(st.integers(0, 2), st.integers(1, 800), st.sampled_from([0, 1]),
+                      st.floats(1e-6, 2.0), st.lists(st.floats(-1.0, 1.0), min_size=3, max_size=3))
+    def check(seed, n, law, vscale, uf):
+        d, pos, vel, eps, cs, perm, nbulk = setup(law=law, n=n, seed=seed, vel_scale=vscale)
+        u = uniform_u(nbulk, uf)
+        A, b = oracle.implicit(d, pos, vel, eps, u, cs, perm)
+        F, _ = oracle.drag(d, pos, vel, eps, u)
+        S = oracle.deposit_momentum(d, F, cs, perm)
+        split = -(A[None, :] * u - b)
+        scale = np.max(np.abs(S)) + np.max(np.abs(b)) + 1e-300
+        assert np.max(np.abs(S - split)) <= 1e-11 * scale
+        assert np.all(A >= 0.0)
+
+    check()
