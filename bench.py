@@ -461,7 +461,7 @@ def run_reference(args):
         oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
     tc = time.perf_counter() - ta
     value = n * ks / tc
-    sample = f"{ks} full oracle steps (warm-up {wu}) of the packed bed, FP64 C, single thread"
+    sample = f"{ks} full oracle steps (warm-up {wu}) of the {args.workload.replace('_', ' ')}, FP64 C, single thread"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": ks, "warmup": wu, "ms_per_step": 1e3 * tc / ks, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
