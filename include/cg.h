@@ -389,8 +389,18 @@ cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void*
 cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int32_t age);
 
 /* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
- * kernels expired (flags: CG_FLAG_*). */
+ * kernels expired (flags: CG_FLAG_*).  Reading the status clears it. */
 cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags);
+
+/* Check of the failure path of the bounded device waits (no GPU fault, no
+ * hang): enqueues on the closure's stream one warp that waits, with the
+ * tensor-core kernels' bounded mbarrier wait, on a barrier that nothing
+ * arrives at, for at most `polls` polls (1 .. 2^22), and records the expiry
+ * in the closure's status word as a stalled tensor-core kernel would.  The
+ * next cg_mlp_sync_status returns CG_ERR_TIMEOUT with CG_FLAG_TIMEOUT set;
+ * the context and the handle stay usable.  CG_ERR_INVALID_ARG for a NULL
+ * handle or polls outside the range. */
+cg_status cg_mlp_wait_selftest(cg_mlp* m, uint32_t polls);
 
 /* ------------------------------------------------------------------------
  * Batched coupling (not in the paper): many independent FP32 instances of

@@ -122,6 +122,7 @@ _SIGS = {
     "cg_mlp_grads": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p]),
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "cg_mlp_wait_selftest": (C.c_int, [C.c_void_p, C.c_uint32]),
     "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -496,6 +497,11 @@ class Mlp:
         flags = C.c_uint32()
         rc = lib().cg_mlp_sync_status(self.h, C.byref(flags))
         return rc, flags.value
+
+    def wait_selftest(self, polls):
+        """Enqueue the bounded-wait check (cg_mlp_wait_selftest): the next
+        sync_status reports CG_ERR_TIMEOUT."""
+        _check(lib().cg_mlp_wait_selftest(self.h, int(polls)), "cg_mlp_wait_selftest")
 
     def bind(self, var_stale, u_fine, age=1):
         """Stale variance field, fine velocity and record age used by

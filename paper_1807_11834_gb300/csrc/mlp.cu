@@ -65,10 +65,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Bounded wait for the given phase parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the given phase parity (at most `limit` polls); returns
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
     uint32_t done = 0;
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    for (uint32_t it = 0; it < limit && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
@@ -333,6 +334,22 @@ __device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const u
     }
     fence_after();
     return !failed;
+}
+
+// The failure path of the bounded waits, without a stalled tensor core: one
+// warp waits, with the same bounded wait, on an mbarrier that nothing
+// arrives at (phase 0 never completes), and records the expiry in the
+// status word exactly as run_gemm does.
+__global__ void __launch_bounds__(32) k_wait_selftest(uint32_t polls, unsigned long long* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool mine = mbar_wait(&bar, 0, polls);
+    const bool failed = __syncthreads_or(!mine) != 0;
+    if (failed && threadIdx.x == 0) {
+        atomicAdd(&status[ST_TIMEOUT], 1ull);
+        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_TIMEOUT);
+    }
 }
 
 // TMEM address of this thread's lane at a column.
@@ -980,6 +997,13 @@ cg_status cg_mlp_train_step(cg_mlp* m, int64_t n, const float* features, const f
                             float* loss_out) {
     if (!(lr > 0.f) || !isfinite(lr)) return CG_ERR_INVALID_ARG;
     return grad_impl(m, n, features, targets, lr, 1, loss_out);
+}
+
+cg_status cg_mlp_wait_selftest(cg_mlp* m, uint32_t polls) {
+    if (!m || polls == 0 || polls > kSpinLimit) return CG_ERR_INVALID_ARG;
+    k_wait_selftest<<<1, 32, 0, m->stream>>>(polls, m->status);
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
 }
 
 cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags) {

@@ -121,3 +121,33 @@ def test_training_fits_a_smooth_target(cuda_lib):
     print("loss", l0, "->", loss.item())
     assert loss.item() < 0.02 * l0
     m.close()
+
+
+def test_bounded_wait_expires_into_a_timeout_status(cuda_lib):
+    """A bounded mbarrier wait that nothing completes (no GPU fault, no
+    hang) ends in CG_ERR_TIMEOUT with CG_FLAG_TIMEOUT; reading the status
+    clears it, and the same handle then runs the forward pass bit for bit
+    as before, with a clean status."""
+    import time
+    import torch
+    cg = cuda_lib
+    m, _ = make(cg, 0)
+    feat = torch.from_numpy(random_features(300, 7)).cuda()
+    c0 = torch.empty(300, device="cuda")
+    m.forward(feat, c0)
+    assert m.sync_status() == (0, 0)
+    for bad in (0, (1 << 22) + 1):
+        with pytest.raises(cg.CgError):
+            m.wait_selftest(bad)
+    t0 = time.perf_counter()
+    m.wait_selftest(4096)
+    rc, flags = m.sync_status()
+    waited = time.perf_counter() - t0
+    assert rc == 6 and flags & cg.CG_FLAG_TIMEOUT, (rc, flags)
+    assert waited < 30.0
+    assert m.sync_status() == (0, 0)
+    c1 = torch.empty(300, device="cuda")
+    m.forward(feat, c1)
+    assert m.sync_status() == (0, 0)
+    assert torch.equal(c0, c1)
+    m.close()
