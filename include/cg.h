@@ -185,6 +185,17 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
 /* Free the handle and everything it owns (synchronises its stream). NULL is OK. */
 cg_status cg_destroy_grids(cg_grids* g);
 
+/* Host-side fault injection for the allocation failure paths (process-wide,
+ * no device fault): the next k device allocations a coupling handle makes
+ * for itself (its bulk buffers, particle scratch and host-entry staging)
+ * succeed and the one after fails as if the device were out of memory, so
+ * the call that made it returns CG_ERR_OOM; the injection then switches
+ * itself off.  k = -1 switches it off at once; k < -1 is CG_ERR_INVALID_ARG.
+ * A failed cg_create_grids frees everything and returns no handle; any
+ * other call that fails this way enqueues no work, and its handle stays
+ * valid and allocates again on its next call. */
+cg_status cg_debug_fail_alloc_after(int64_t k);
+
 /* Change the stream later calls are enqueued on. */
 cg_status cg_set_stream(cg_grids* g, void* cuda_stream);
 

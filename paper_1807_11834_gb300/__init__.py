@@ -123,6 +123,7 @@ _SIGS = {
     "cg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p]),
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "cg_mlp_wait_selftest": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "cg_debug_fail_alloc_after": (C.c_int, [C.c_int64]),
     "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),

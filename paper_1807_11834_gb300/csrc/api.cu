@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 #include "cg_internal.cuh"
@@ -16,10 +17,22 @@ bool finite3(const double* v) { return isfinite(v[0]) && isfinite(v[1]) && isfin
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Host-side fault injection (cg_debug_fail_alloc_after): the number of
+// handle-owned allocations still allowed before one fails; -1 = none fails.
+std::atomic<long long> g_alloc_fail_after{-1};
+
+bool injected_alloc_failure() {
+    long long k = g_alloc_fail_after.load();
+    while (k >= 0)
+        if (g_alloc_fail_after.compare_exchange_weak(k, k - 1)) return k == 0;   // after the failure: -1
+    return false;
+}
+
 template <typename P>
 cg_status dalloc(P** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (injected_alloc_failure()) return CG_ERR_OOM;
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
@@ -126,6 +139,7 @@ cg_status ensure_partials(cg_grids* g, long long n) {
     const long long need = part_blk * (1 + kDragCellSums + 3) + proj_blk * 3;
     if (need > g->part_cap) {
         dfree(g->partials);
+        g->part_cap = 0;
         CG_TRY(dalloc(&g->partials, 2 * g->tsize * need));
         g->part_cap = need;
     }
@@ -345,6 +359,12 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
         return st;
     }
     *out = g;
+    return CG_OK;
+}
+
+cg_status cg_debug_fail_alloc_after(int64_t k) {
+    if (k < -1) return CG_ERR_INVALID_ARG;
+    g_alloc_fail_after.store(k);
     return CG_OK;
 }
 
@@ -618,6 +638,8 @@ static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const voi
     if (out->cell) CG_TRY(ensure_buf(S.cell, sizeof(int32_t) * (size_t)std::max(1LL, n)));
     if (out->perm) CG_TRY(ensure_buf(S.perm, sizeof(int32_t) * (size_t)std::max(1LL, n)));
     if (out->cell_start) CG_TRY(ensure_buf(S.cs, sizeof(int32_t) * (nb + 1)));
+    // the particle scratch too, so that a failed allocation enqueues nothing
+    CG_TRY(ensure_particle_capacity(g, n));
     g->hs_next ^= 1;
 
     // inputs in

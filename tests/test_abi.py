@@ -133,3 +133,6 @@ def test_argument_checks_answer_before_any_device_work():
         assert not h.value
     assert L.cg_map_average(None, 1, None, None) == 1
     assert L.cg_destroy_grids(None) == 0 and L.cg_map_destroy(None) == 0
+    # the allocation fault injection is host-side: set, switched off, refused below -1
+    assert L.cg_debug_fail_alloc_after(-2) == 1
+    assert L.cg_debug_fail_alloc_after(3) == 0 and L.cg_debug_fail_alloc_after(-1) == 0

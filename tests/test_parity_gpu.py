@@ -512,3 +512,65 @@ def test_reorder_particles_into_cell_order(cuda_lib, fp64):
     with pytest.raises(cg.CgError):
         g.cg_reorder_particles(pos2, None, pos2, None)
     g.close()
+
+
+def test_allocation_failures_are_reported_and_recovered(cuda_lib):
+    """Host-side fault injection (no device fault): each allocation of
+    cg_create_grids fails in turn with CG_ERR_OOM and leaves no handle; a
+    device step and a host-buffer step whose buffers cannot be allocated
+    fail with CG_ERR_OOM, and the same handle then steps exactly as a
+    fresh one."""
+    import ctypes as C
+    import torch
+    cg = cuda_lib
+    L = cg.lib()
+    w = synth.tiny(seed=4)          # 10,000 particles: more than a new handle's particle scratch
+    ref = run_step(cg, w, eps_fine=False)
+    keys = ("cell", "perm", "cell_start", "eps_bulk", "u_bulk", "var_bulk", "force", "S_bulk", "S_fine", "sums")
+    try:
+        k = 0
+        while True:
+            assert L.cg_debug_fail_alloc_after(k) == 0
+            h = C.c_void_p()
+            rc = L.cg_create_grids(C.byref(cg.make_desc(w.desc)), None, C.byref(h))
+            if rc == 0:                 # k allocations were all it needed: the injection is still armed
+                assert L.cg_debug_fail_alloc_after(-1) == 0
+                L.cg_destroy_grids(h)
+                break
+            assert rc == 3 and not h.value, (k, rc)
+            k += 1
+            assert k < 100
+        assert k >= 6               # the bulk buffers and the particle scratch
+        # device entry: the particle scratch grows for 10,000 particles and fails
+        g = cg.Grids(w.desc)
+        pos, vel, uf = inputs(w)
+        out = g.alloc_outputs(w.n, bins=True)
+        assert L.cg_debug_fail_alloc_after(0) == 0
+        with pytest.raises(cg.CgError) as e:
+            g.cg_step(pos, vel, uf, out)
+        assert e.value.code == 3
+        g.cg_step(pos, vel, uf, out)   # the injection switched itself off
+        assert g.cg_sync_status()[0] == 0
+        torch.cuda.synchronize()
+        for key in keys:
+            assert np.array_equal(to_np(out[key]), ref[key]), key
+        g.close()
+        # host entry: its first staging buffer fails, then (after the 13
+        # staging buffers these outputs need) its particle scratch
+        g = cg.Grids(w.desc)
+        hout = {key: (v.cpu().pin_memory() if v is not None else None)
+                for key, v in g.alloc_outputs(w.n, bins=True).items()}
+        hpos = torch.from_numpy(w.pos_d.copy()).pin_memory()
+        hvel = torch.from_numpy(w.vel.copy()).pin_memory()
+        huf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).pin_memory()
+        for fail_at in (0, 13):
+            assert L.cg_debug_fail_alloc_after(fail_at) == 0
+            with pytest.raises(cg.CgError) as e:
+                g.cg_step_host(hpos, hvel, huf, hout)
+            assert e.value.code == 3, fail_at
+        g.cg_step_host(hpos, hvel, huf, hout)
+        for key in keys:
+            assert np.array_equal(hout[key].numpy(), ref[key]), key
+        g.close()
+    finally:
+        L.cg_debug_fail_alloc_after(-1)
