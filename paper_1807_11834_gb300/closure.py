@@ -28,11 +28,14 @@ without crossing it.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Grids, Mlp, mlp_pack, MLP_NFEAT
+from . import Grids, Mlp, mlp_pack, MLP_NFEAT, MLP_NPARAM
 
 HIDDEN = 64
 K0 = 16
@@ -241,6 +244,61 @@ def evaluate(m: Mlp, make, seed, refresh=5, steps=30, device="cuda", dt=None):
     t.close()
     return {"err_stale": (acc["num_st"] / acc["den"]) ** 0.5, "err_learned": (acc["num_le"] / acc["den"]) ** 0.5,
             "fallback_share": acc["fall"] / max(acc["rows"], 1), "stale_steps": acc["rows"] // max(w.n, 1)}
+
+
+CHECKPOINT_FORMAT = "dual-grid drag closure"
+CHECKPOINT_VERSION = 1
+
+
+def save_checkpoint(path: str, params, feat_lo, feat_hi, **meta) -> None:
+    """Write a trained closure as two files: ``path + ".f32"`` holds the
+    MLP_NPARAM parameters as little-endian float32 in the ABI order of
+    mlp_pack (W1, b1, W2, b2, w3, b3), and ``path + ".json"`` the sizes, the
+    feature box (min / max of each of the MLP_NFEAT features over the
+    training set), the SHA-256 of the parameter file and any extra JSON
+    values given as keywords (the refresh interval, the target mean and
+    spread, ...).  The parameters are written exactly as given (float32)."""
+    p = np.ascontiguousarray(params, dtype="<f4").reshape(-1)
+    lo = np.asarray(feat_lo, np.float32).reshape(-1)
+    hi = np.asarray(feat_hi, np.float32).reshape(-1)
+    if p.size != MLP_NPARAM or lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
+        raise ValueError("closure checkpoint: bad parameter or feature-box sizes")
+    if not (np.all(np.isfinite(p)) and np.all(np.isfinite(lo)) and np.all(np.isfinite(hi)) and np.all(hi > lo)):
+        raise ValueError("closure checkpoint: non-finite parameters or an empty feature box")
+    raw = p.tobytes()
+    head = {"format": CHECKPOINT_FORMAT, "version": CHECKPOINT_VERSION, "nparam": MLP_NPARAM,
+            "nfeat": MLP_NFEAT, "hidden": HIDDEN, "k0": K0,
+            "params_file": os.path.basename(path) + ".f32", "params_sha256": hashlib.sha256(raw).hexdigest(),
+            # float32 values written as the doubles they are, so they read back exactly
+            "feature_lo": [float(v) for v in lo], "feature_hi": [float(v) for v in hi], "meta": meta}
+    with open(path + ".f32", "wb") as f:
+        f.write(raw)
+    with open(path + ".json", "w") as f:
+        json.dump(head, f, indent=1)
+
+
+def load_checkpoint(path: str):
+    """Read a closure written by save_checkpoint: (params float32
+    [MLP_NPARAM], feat_lo float32 [MLP_NFEAT], feat_hi, meta dict).  Raises
+    ValueError when the format, a size or the checksum does not match.
+    ``Mlp(params, feat_lo, feat_hi)`` makes the closure handle."""
+    with open(path + ".json") as f:
+        head = json.load(f)
+    if head.get("format") != CHECKPOINT_FORMAT or head.get("version") != CHECKPOINT_VERSION:
+        raise ValueError("closure checkpoint: unknown format or version")
+    if (head.get("nparam"), head.get("nfeat"), head.get("hidden"), head.get("k0")) != (MLP_NPARAM, MLP_NFEAT,
+                                                                                        HIDDEN, K0):
+        raise ValueError("closure checkpoint: network sizes differ from this library's")
+    with open(os.path.join(os.path.dirname(path), head["params_file"]), "rb") as f:
+        raw = f.read()
+    if len(raw) != 4 * MLP_NPARAM or hashlib.sha256(raw).hexdigest() != head.get("params_sha256"):
+        raise ValueError("closure checkpoint: parameter file size or checksum mismatch")
+    params = np.frombuffer(raw, dtype="<f4").astype(np.float32)
+    lo = np.asarray(head["feature_lo"], np.float32)
+    hi = np.asarray(head["feature_hi"], np.float32)
+    if lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
+        raise ValueError("closure checkpoint: bad feature box")
+    return params, lo, hi, dict(head.get("meta") or {})
 
 
 def drag_demo(seed: int = 2, launches: int = 23):
