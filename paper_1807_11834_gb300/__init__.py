@@ -180,6 +180,43 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def check_tensor(t, numel, dtype, on_device, name="tensor"):
+    """The binding's check of a tensor before its pointer crosses the ABI:
+    device memory for the device entries (host memory for the host-buffer
+    ones), contiguous, and the dtype and element count the entry reads or
+    writes.  A host pointer handed to a device entry would be dereferenced by
+    a kernel; this stops it on the host."""
+    if t.is_cuda != on_device or not t.is_contiguous() or t.dtype != dtype:
+        where = "CUDA" if on_device else "host"
+        raise ValueError(f"{name}: need a contiguous {where} {dtype} tensor")
+    if numel is not None and t.numel() != int(numel):
+        raise ValueError(f"{name}: need {numel} elements, got {t.numel()}")
+    return t
+
+
+# Components, cell set and dtype of each cg_step_out field ("T": the grids'
+# precision); the counts the ABI documents for each pointer.
+STEP_OUT_LAYOUT = {
+    "eps_bulk": (1, "bulk", "f64"), "u_bulk": (3, "bulk", "T"), "var_bulk": (1, "bulk", "T"),
+    "S_bulk": (3, "bulk", "T"), "force": (3, "particles", "T"), "S_fine": (3, "fine", "T"),
+    "eps_fine": (1, "fine", "T"), "sums": (CG_NSUMS, "one", "f64"), "cell": (1, "particles", "i32"),
+    "perm": (1, "particles", "i32"), "cell_start": (1, "bulk+1", "i32"), "implicit_bulk": (4, "bulk", "T"),
+    "implicit_fine": (4, "fine", "T"),
+}
+
+
+def check_step_outputs(out, n, n_bulk, n_fine, dtype, on_device):
+    """check_tensor for every output of one step that is not None (which
+    combinations may be None is the library's to check)."""
+    import torch
+    count = {"bulk": n_bulk, "fine": n_fine, "particles": n, "bulk+1": n_bulk + 1, "one": 1}
+    kinds = {"T": dtype, "f64": torch.float64, "i32": torch.int32}
+    for name, (comps, cells, kind) in STEP_OUT_LAYOUT.items():
+        t = out.get(name)
+        if t is not None:
+            check_tensor(t, comps * count[cells], kinds[kind], on_device, name)
+
+
 def _stream_handle(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -238,12 +275,7 @@ class Grids:
     def _t(self, t, shape, dtype=None, name="tensor"):
         if t is None:
             return None
-        dtype = dtype or self.dtype
-        if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
-            raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor")
-        if shape is not None and t.numel() != int(shape):
-            raise ValueError(f"{name}: need {shape} elements, got {t.numel()}")
-        return t
+        return check_tensor(t, shape, dtype or self.dtype, True, name)
 
     def set_stream(self, stream=None):
         _check(lib().cg_set_stream(self.h, _stream_handle(stream)), "cg_set_stream")
@@ -345,6 +377,7 @@ class Grids:
         self._t(pos_d, 4 * n, name="pos_d")
         self._t(vel, 4 * n, name="vel")
         self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        check_step_outputs(out, n, self.n_bulk, self.n_fine, self.dtype, True)
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step")
@@ -357,6 +390,7 @@ class Grids:
         self._t(pos_d, 4 * n, name="pos_d")
         self._t(vel, 4 * n, name="vel")
         self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        check_step_outputs(out, n, self.n_bulk, self.n_fine, self.dtype, True)
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step_learned(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt), mlp.h,
@@ -378,12 +412,17 @@ class Grids:
                                      _ptr(var_stale), _ptr(u_fresh), _ptr(features), _ptr(target)),
                "cg_mlp_features")
 
+    def _host_step_args(self, pos_d, vel, u_fine, out):
+        n = pos_d.shape[0]
+        check_tensor(pos_d, 4 * n, self.dtype, False, "pos_d")
+        check_tensor(vel, 4 * n, self.dtype, False, "vel")
+        check_tensor(u_fine, 3 * self.n_fine, self.dtype, False, "u_fine")
+        check_step_outputs(out, n, self.n_bulk, self.n_fine, self.dtype, False)
+
     def cg_step_host(self, pos_d, vel, u_fine, out, dt=0.0):
         """Same as cg_step on host (CPU, ideally pinned) tensors; blocks."""
         n = pos_d.shape[0]
-        for t in [pos_d, vel, u_fine] + [v for v in out.values() if v is not None]:
-            if t.is_cuda or not t.is_contiguous():
-                raise ValueError("cg_step_host needs contiguous host tensors")
+        self._host_step_args(pos_d, vel, u_fine, out)
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step_host(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step_host")
@@ -392,9 +431,7 @@ class Grids:
         """cg_step_host without the final wait (call cg_step_host_wait before
         reading the outputs or changing the inputs)."""
         n = pos_d.shape[0]
-        for t in [pos_d, vel, u_fine] + [v for v in out.values() if v is not None]:
-            if t.is_cuda or not t.is_contiguous():
-                raise ValueError("cg_step_host_async needs contiguous host tensors")
+        self._host_step_args(pos_d, vel, u_fine, out)
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step_host_async(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)),
