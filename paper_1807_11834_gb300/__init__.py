@@ -560,6 +560,11 @@ class Batch:
         items = (BatchItem * len(instances))()
         self._keep = []
         for k, (desc, pos, vel, uf, out) in enumerate(instances):
+            # device memory only (a host pointer would reach a kernel); sizes,
+            # precision and descriptors are the library's to check
+            for t in [pos, vel, uf] + [v for v in out.values() if v is not None]:
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError(f"batch instance {k}: contiguous CUDA tensors expected")
             it = items[k]
             it.desc = make_desc(desc)
             it.particles = Particles(pos.shape[0], pos.data_ptr(), vel.data_ptr())
@@ -681,8 +686,8 @@ class Map:
         self.h = h
 
     def _fields(self, t, cells, name):
-        if t.dtype != self.dtype or not t.is_contiguous() or t.numel() % cells != 0:
-            raise ValueError(f"{name}: contiguous {self.dtype} tensor of [ncomp][{cells}] expected")
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() % cells != 0:
+            raise ValueError(f"{name}: contiguous CUDA {self.dtype} tensor of [ncomp][{cells}] expected")
         return t.numel() // cells
 
     def average(self, fine_in, bulk_out):

@@ -63,3 +63,13 @@ def test_check_tensor():
         cg.check_tensor(t.t(), 12, torch.float32, False, "t")
     with pytest.raises(ValueError):
         cg.check_tensor(t, 11, torch.float32, False, "t")
+
+
+def test_batch_refuses_host_tensors_before_any_library_call():
+    import synth
+    w = synth.batch_instance(0, 0, 16, 4, 100, 0.01)
+    out, _ = _outputs(torch.float32, n=w.n, nb=(16 // 4) ** 3, nf=16 ** 3)
+    pos, vel = torch.from_numpy(w.pos_d), torch.from_numpy(w.vel)
+    uf = torch.from_numpy(w.u_fine.reshape(3, -1).copy())
+    with pytest.raises(ValueError, match="CUDA"):
+        cg.Batch([(w.desc, pos, vel, uf, out)])
