@@ -519,17 +519,35 @@ class Mlp:
         p = np.ascontiguousarray(params, dtype=np.float32)
         _check(lib().cg_mlp_set_params(self.h, p.ctypes.data), "cg_mlp_set_params")
 
-    def forward(self, features, c_out, in_range=None):
+    @staticmethod
+    def _batch(features, targets=None, loss=None):
+        """Rows of a feature batch ([n][8] float32 on the device) after the
+        checks of its companions (targets [n], loss [1], both float32)."""
+        import torch
         n = features.shape[0]
+        check_tensor(features, 8 * n, torch.float32, True, "features")
+        if targets is not None:
+            check_tensor(targets, n, torch.float32, True, "targets")
+        if loss is not None:
+            check_tensor(loss, 1, torch.float32, True, "loss")
+        return n
+
+    def forward(self, features, c_out, in_range=None):
+        import torch
+        n = Mlp._batch(features)
+        check_tensor(c_out, n, torch.float32, True, "c_out")
+        if in_range is not None:
+            check_tensor(in_range, n, torch.int32, True, "in_range")
         _check(lib().cg_mlp_forward(self.h, n, _ptr(features), _ptr(c_out), _ptr(in_range)), "cg_mlp_forward")
 
     def grads(self, features, targets, loss=None):
-        _check(lib().cg_mlp_grads(self.h, features.shape[0], _ptr(features), _ptr(targets), _ptr(loss)),
-               "cg_mlp_grads")
+        n = Mlp._batch(features, targets, loss)
+        _check(lib().cg_mlp_grads(self.h, n, _ptr(features), _ptr(targets), _ptr(loss)), "cg_mlp_grads")
 
     def train_step(self, features, targets, lr, loss=None):
-        _check(lib().cg_mlp_train_step(self.h, features.shape[0], _ptr(features), _ptr(targets), float(lr),
-                                       _ptr(loss)), "cg_mlp_train_step")
+        n = Mlp._batch(features, targets, loss)
+        _check(lib().cg_mlp_train_step(self.h, n, _ptr(features), _ptr(targets), float(lr), _ptr(loss)),
+               "cg_mlp_train_step")
 
     def sync_status(self):
         flags = C.c_uint32()
@@ -545,6 +563,10 @@ class Mlp:
         """Stale variance field, fine velocity and record age used by
         Grids.cg_drag(mlp=self) (float32 device tensors, kept alive by this
         object)."""
+        import torch
+        for name, t in (("var_stale", var_stale), ("u_fine", u_fine)):
+            if t is not None:
+                check_tensor(t, None, torch.float32, True, name)
         self._bound = (var_stale, u_fine)
         _check(lib().cg_mlp_bind(self.h, _ptr(var_stale), _ptr(u_fine), int(age)), "cg_mlp_bind")
 

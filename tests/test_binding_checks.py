@@ -73,3 +73,14 @@ def test_batch_refuses_host_tensors_before_any_library_call():
     uf = torch.from_numpy(w.u_fine.reshape(3, -1).copy())
     with pytest.raises(ValueError, match="CUDA"):
         cg.Batch([(w.desc, pos, vel, uf, out)])
+
+
+def test_closure_entries_check_their_tensors_first():
+    fake = types.SimpleNamespace(h=None)
+    feats = torch.zeros(10, 8)
+    with pytest.raises(ValueError, match="features"):
+        cg.Mlp.forward(fake, feats, torch.zeros(10))                 # host memory
+    with pytest.raises(ValueError, match="features"):
+        cg.Mlp.train_step(fake, torch.zeros(10, 7), torch.zeros(10), 1e-3)
+    with pytest.raises(ValueError, match="var_stale"):
+        cg.Mlp.bind(fake, torch.zeros(5, dtype=torch.float64), None)
