@@ -280,3 +280,48 @@ def test_step_conservation_invariants(make):
     assert np.all(np.abs(s[5:8] - s[8:11]) <= 1e-12 * scale)
     assert o["outside"] == 0
     assert np.all(o["eps_fine"] <= 1.0 + 1e-15)
+
+
+def test_one_particle_sweep_is_continuous_across_bulk_faces():
+    """Continuity across cell boundaries (the paper's one-particle check,
+    Sec. 4.1, made a sweep): a particle moved along a line through fixed bulk
+    fields crosses interior bulk faces and the outer half cells; the
+    interpolated porosity and fluid velocity, and with them the Di Felice
+    drag, change continuously.  Halving the step halves the largest change
+    between neighbouring positions; a jump at a face would not shrink.  The
+    particle's own deposit moves wholly from one cell to the next at each
+    face (NGP), and its total stays V_p."""
+    desc = synth.make_desc((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (8, 8, 8), 2, fp64=True, law=0)
+    rng = np.random.default_rng(5)
+    bg = np.zeros((400, 4))
+    bg[:, :3] = rng.random((400, 3))
+    bg[:, 3] = 0.04
+    _, perm, cs, _ = oracle.bin(desc, bg)
+    eps, _ = oracle.deposit_volume(desc, bg, cs, perm)
+    u_fine = rng.normal(0.0, 0.2, (3, 8, 8, 8))
+    u_bulk, _ = oracle.average(desc, u_fine)
+
+    def largest_change(m, d):
+        pos = np.zeros((m, 4))
+        pos[:, 0], pos[:, 1], pos[:, 2], pos[:, 3] = np.linspace(0.01, 0.99, m), 0.37, 0.61, 0.01
+        vel = np.zeros((m, 4))
+        vel[:, :3] = [0.05, -0.02, 0.01]
+        F, _ = oracle.drag(d, pos, vel, eps, u_bulk)
+        return np.max(np.linalg.norm(np.diff(F, axis=1), axis=0))
+
+    j1, j2 = largest_change(1001, desc), largest_change(2001, desc)
+    assert j1 > 0 and j2 <= 0.6 * j1, (j1, j2)
+    # the criterion sees a jump: the cell-value gather (Sec. 1's other option)
+    # is discontinuous at the faces, and there halving the step changes nothing
+    cell = dict(desc, interp=1)
+    assert largest_change(2001, cell) >= 0.9 * largest_change(1001, cell)
+    # the moving particle's own deposit: one cell at a time, all of V_p
+    vp = math.pi * 0.01 ** 3 / 6.0
+    H = 0.25
+    for x in (0.2499999, 0.25, 0.2500001, 0.7499999, 0.75):
+        p = np.array([[x, 0.37, 0.61, 0.01]])
+        _, pm, c, _ = oracle.bin(desc, p)
+        e, _ = oracle.deposit_volume(desc, p, c, pm)
+        phi = 1.0 - e
+        assert np.count_nonzero(phi) == 1 and phi.sum() * H ** 3 == pytest.approx(vp, rel=1e-12)
+        assert int(np.argmax(phi)) % 4 == int(math.floor(x / H))
