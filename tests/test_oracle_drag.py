@@ -284,7 +284,7 @@ def test_step_conservation_invariants(make):
 
 def test_one_particle_sweep_is_continuous_across_bulk_faces():
     """Continuity across cell boundaries (the paper's one-particle check,
-    Sec. 4.1, made a sweep): a particle moved along a line through fixed bulk
+    Sec. 3.1, made a sweep): a particle moved along a line through fixed bulk
     fields crosses interior bulk faces and the outer half cells; the
     interpolated porosity and fluid velocity, and with them the Di Felice
     drag, change continuously.  Halving the step halves the largest change
