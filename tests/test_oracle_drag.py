@@ -325,3 +325,28 @@ def test_one_particle_sweep_is_continuous_across_bulk_faces():
         phi = 1.0 - e
         assert np.count_nonzero(phi) == 1 and phi.sum() * H ** 3 == pytest.approx(vp, rel=1e-12)
         assert int(np.argmax(phi)) % 4 == int(math.floor(x / H))
+
+
+def test_step_is_invariant_under_particle_renumbering():
+    """The paper finds the coupled results identical whatever the
+    decomposition (Sec. 3.1); here, whatever the particle numbering: a step
+    on the particles in another order gives each particle the same cell and
+    force, each cell the same particles, and the same fields, to the
+    rounding of the compensated per-cell sums taken in another order."""
+    w = synth.small_packed_bed(seed=3, fp64=True)
+    a = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, dt=1e-4, want_eps_fine=True)
+    p = np.random.default_rng(11).permutation(w.n)
+    b = oracle.step(w.desc, w.pos_d[p], w.vel[p], w.u_fine, dt=1e-4, want_eps_fine=True)
+    assert np.array_equal(b["cell"], a["cell"][p])
+    assert np.array_equal(b["cell_start"], a["cell_start"])
+    for c in np.random.default_rng(12).choice(len(a["cell_start"]) - 1, 200, replace=False):
+        s0, s1 = a["cell_start"][c], a["cell_start"][c + 1]
+        assert sorted(a["perm"][s0:s1]) == sorted(p[b["perm"][s0:s1]]), c
+    assert np.all(np.diff(b["perm"][b["cell_start"][5]:b["cell_start"][6]]) > 0)   # still stable
+    for k in ("eps_bulk", "u_bulk", "var_bulk", "S_bulk", "S_fine", "eps_fine"):
+        x, y = a[k], b[k]
+        assert np.allclose(y, x, rtol=1e-13, atol=1e-13 * np.max(np.abs(x))), k
+    F = a["force"]
+    assert np.allclose(b["force"], F[:, p], rtol=1e-12, atol=1e-13 * np.max(np.abs(F)))
+    assert np.allclose(b["pos_d"], a["pos_d"][p], rtol=0, atol=1e-15)
+    assert np.allclose(b["vel"], a["vel"][p], rtol=1e-12, atol=1e-15)
