@@ -136,3 +136,31 @@ def test_argument_checks_answer_before_any_device_work():
     # the allocation fault injection is host-side: set, switched off, refused below -1
     assert L.cg_debug_fail_alloc_after(-2) == 1
     assert L.cg_debug_fail_alloc_after(3) == 0 and L.cg_debug_fail_alloc_after(-1) == 0
+
+
+def test_constants_match_the_header(tmp_path):
+    """Every constant the binding hard-codes equals the header's, as the C
+    compiler sees it."""
+    import shutil
+    import subprocess
+    import paper_1807_11834_gb300 as cg
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    names = ["CG_OK", "CG_ERR_INVALID_ARG", "CG_ERR_CUDA", "CG_ERR_OOM", "CG_ERR_NOT_BINNED", "CG_ERR_OUT_OF_RANGE",
+             "CG_ERR_TIMEOUT", "CG_ERR_NONFINITE", "CG_FP32", "CG_FP64", "CG_DRAG_DI_FELICE", "CG_DRAG_ERGUN_WEN_YU",
+             "CG_INTERP_TRILINEAR", "CG_INTERP_CELL", "CG_DEP_VOLUME", "CG_DEP_MOMENTUM", "CG_FLAG_OUTSIDE",
+             "CG_FLAG_NONFINITE", "CG_FLAG_EPS_CLAMPED", "CG_FLAG_TIMEOUT", "CG_SORT_AUTO", "CG_SORT_CELLS",
+             "CG_SORT_CELLS_AUTO_MAX", "CG_SORT_CELLS_AUTO_DENSITY", "CG_NCOUNTS", "CG_NSUMS", "CG_MLP_NPARAM",
+             "CG_MLP_NFEAT"]
+    src = tmp_path / "k.c"
+    src.write_text('#include <stdio.h>\n#include "cg.h"\nint main(void){\n'
+                   + "".join(f'printf("%lld\\n", (long long)({n}));\n' for n in names) + "return 0;}\n")
+    exe = tmp_path / "k"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    py = {n: getattr(cg, n) for n in names if hasattr(cg, n)}
+    py["CG_MLP_NPARAM"], py["CG_MLP_NFEAT"] = cg.MLP_NPARAM, cg.MLP_NFEAT
+    for k in ("CG_ERR_INVALID_ARG", "CG_ERR_CUDA", "CG_ERR_OOM", "CG_ERR_NOT_BINNED", "CG_ERR_OUT_OF_RANGE",
+              "CG_ERR_TIMEOUT", "CG_ERR_NONFINITE"):
+        py[k] = {v: c for c, v in cg.STATUS_NAMES.items()}[k]
+    assert {n: v for n, v in zip(names, got)} == {n: py[n] for n in names}
