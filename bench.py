@@ -407,7 +407,8 @@ def run_gb300(args):
             oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
         tc = time.perf_counter() - ta
         cpu = {"value": n * ks / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ks} full oracle steps of the same packed bed (FP64 C, single thread), {tc:.1f} s"}
+               "sample": f"{ks} full oracle steps of the same {args.workload.replace('_', ' ')} (FP64 C, single thread), "
+                         f"{tc:.1f} s"}
 
     if world > 1:
         dist.barrier()
@@ -415,7 +416,8 @@ def run_gb300(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.desc.get("fp64") else "f32",
+            "data": "synthetic",
             "config": {"workload": workload_name(args.workload, w),
                        "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
                        "parallelism": f"replicas x{world}",
