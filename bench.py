@@ -421,7 +421,8 @@ def run_gb300(args):
             "config": {"workload": workload_name(args.workload, w),
                        "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs {input_bytes / 1e6:.0f} MB > L2 (126 MB) per step, no flush",
+                       "l2": (f"inputs {input_bytes / 1e6:.0f} MB {'>' if input_bytes > 126e6 else '<'} L2 (126 MB) "
+                              "per step, no flush"),
                        "timing": ("CUDA graph of one cg_step, replayed K times" if graph is not None
                                   else "eager cg_step calls"),
                        "eager_ms_per_step": round(eager_ms_step, 5),
