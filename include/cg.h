@@ -25,8 +25,10 @@
  *     vel[n] = (u, v, w, unused).  Field arrays are SoA: [ncomp][cells].
  *     Per-particle outputs are in the caller's particle order.
  *   - Every pointer passed to a compute call is DEVICE memory owned by the
- *     caller (cg_step_host excepted), 16-byte aligned for T = float and
- *     32-byte aligned for T = double.  The library never frees them.
+ *     caller (cg_step_host excepted), 16-byte aligned for either T (the
+ *     kernels read particle records as 16-byte vectors: one float4, or two
+ *     double2); misaligned particle and fine-field pointers are refused
+ *     with CG_ERR_INVALID_ARG.  The library never frees them.
  *   - Every compute call is enqueued on the handle's CUDA stream and
  *     returns without synchronising.  Argument errors are reported
  *     synchronously by the return code and nothing is enqueued.

@@ -471,9 +471,23 @@ class Grids:
 
 def cg_bin_particles_static(desc: dict, pos_d, perm, cell_start, cell=None, stream=None):
     """Binning without any device allocation (fixed scratch inside the
-    library, at most 262,144 particles); same outputs as cg_bin_particles."""
+    library, at most 262,144 particles); same outputs as cg_bin_particles.
+    Every tensor is checked as the handle entries check theirs: CUDA memory,
+    contiguous, the descriptor's precision for pos_d ([n][4]) and int32
+    perm / cell ([n]) and cell_start ([n_b + 1])."""
+    import torch
     d = make_desc(desc)
     n = pos_d.shape[0]
+    dtype = torch.float64 if desc.get("fp64", False) else torch.float32
+    ratio = int(desc["ratio"])
+    n_bulk = 1
+    for f in desc["fine_n"]:
+        n_bulk *= int(f) // ratio if ratio > 0 else 0
+    check_tensor(pos_d, 4 * n, dtype, True, "pos_d")
+    check_tensor(perm, n, torch.int32, True, "perm")
+    check_tensor(cell_start, n_bulk + 1, torch.int32, True, "cell_start")
+    if cell is not None:
+        check_tensor(cell, n, torch.int32, True, "cell")
     _check(lib().cg_bin_particles_static(C.byref(d), n, _ptr(pos_d), _ptr(cell), _ptr(perm), _ptr(cell_start),
                                          _stream_handle(stream)), "cg_bin_particles_static")
 

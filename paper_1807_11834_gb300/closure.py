@@ -299,43 +299,3 @@ def load_checkpoint(path: str):
     if lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
         raise ValueError("closure checkpoint: bad feature box")
     return params, lo, hi, dict(head.get("meta") or {})
-
-
-def drag_demo(seed: int = 2, launches: int = 23):
-    """One plain step of the small clustered bed, then the learned drag with
-    a random closure whose feature box covers every row (no fallback),
-    `launches` times; prints the mean time of the last 20 (CUDA events).
-    A fixed case for profiling the learned drag kernel."""
-    import torch
-    from synth import small_clustered_bed
-    w = small_clustered_bed(seed=seed)
-    g = Grids(w.desc)
-    pos = torch.from_numpy(w.pos_d).cuda()
-    vel = torch.from_numpy(w.vel).cuda()
-    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).cuda()
-    out = g.alloc_outputs(w.n, var=True, eps_fine=True)
-    g.cg_step(pos, vel, uf, out)
-    feat = torch.empty(w.n, 8, device="cuda")
-    tg = torch.empty(w.n, device="cuda")
-    g.cg_mlp_features(pos, vel, out["eps_bulk"], out["u_bulk"], out["var_bulk"], out["u_bulk"], feat, tg)
-    lo, hi = feature_box(feat)
-    m = Mlp(mlp_pack(init_params(0)), lo - 1, hi + 1)
-    m.bind(out["var_bulk"], uf, 2)
-    F = torch.empty(3, w.n, device="cuda")
-    for _ in range(max(0, launches - 20)):
-        g.cg_drag(pos, vel, out["eps_bulk"], out["u_bulk"], F, mlp=m)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(min(20, launches)):
-        g.cg_drag(pos, vel, out["eps_bulk"], out["u_bulk"], F, mlp=m)
-    e1.record()
-    e1.synchronize()
-    rc = g.cg_sync_status()
-    print(f"learned drag: {e0.elapsed_time(e1) / min(20, launches):.4f} ms per launch, {w.n} rows, status {rc}")
-    m.close()
-    g.close()
-
-
-if __name__ == "__main__":
-    drag_demo()

@@ -273,8 +273,11 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
         if (!(d.extent[a] > 0.0) || d.fine_n[a] < 1 || d.fine_n[a] % d.ratio != 0) return CG_ERR_INVALID_ARG;
         nb[a] = d.fine_n[a] / d.ratio;
         if (nb[a] < 2) return CG_ERR_INVALID_ARG;
+        // the fine count is at most 2^31 - 1, so each factor is too and the
+        // running products (checked as they grow) cannot overflow 64 bits
         nbulk *= nb[a];
         nfine *= d.fine_n[a];
+        if (nbulk > (1LL << kMaxBulkBits) || nfine > 2147483647LL) return CG_ERR_OUT_OF_RANGE;
     }
     if (d.prec != CG_FP32 && d.prec != CG_FP64) return CG_ERR_INVALID_ARG;
     if (d.law != CG_DRAG_DI_FELICE && d.law != CG_DRAG_ERGUN_WEN_YU) return CG_ERR_INVALID_ARG;

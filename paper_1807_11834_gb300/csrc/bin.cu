@@ -832,24 +832,24 @@ k_seg_sort(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp
     seg_sort_body<T>(cell_start, nbulk, tmp, alt, perm, key_sorted, inv_perm, vol, vol_sorted, launch_blk());
 }
 
-static bool g_attr_done = false;
+static PerDeviceOnce g_attr_once;
 
 static cg_status set_attrs() {
-    if (g_attr_done) return CG_OK;
-    const int smem = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(double));   // 144 KB at 2^11 digits
+    return once_per_device(g_attr_once, [] {
+        const int smem = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(double));   // 144 KB at 2^11 digits
 #define CG_ATTR(F, L, T) \
     CG_CUDA(cudaFuncSetAttribute(k_bin_scatter<F, L, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
-    CG_ATTR(true, true, float);
-    CG_ATTR(true, false, float);
-    CG_ATTR(false, true, float);
-    CG_ATTR(false, false, float);
-    CG_ATTR(true, true, double);
-    CG_ATTR(true, false, double);
-    CG_ATTR(false, true, double);
-    CG_ATTR(false, false, double);
+        CG_ATTR(true, true, float);
+        CG_ATTR(true, false, float);
+        CG_ATTR(false, true, float);
+        CG_ATTR(false, false, float);
+        CG_ATTR(true, true, double);
+        CG_ATTR(true, false, double);
+        CG_ATTR(false, true, double);
+        CG_ATTR(false, false, double);
 #undef CG_ATTR
-    g_attr_done = true;
-    return CG_OK;
+        return CG_OK;
+    });
 }
 
 template <typename T>
@@ -1002,18 +1002,18 @@ __global__ void __launch_bounds__(256) kb_scan_down(BLaunch L, int pass) {
     batch_loop(L, [&](const BInst& I, Blk b) { scan_down_body(pass ? I.scan1 : I.scan0, I.scan_part, b); });
 }
 
-static bool g_batch_attr = false;
+static PerDeviceOnce g_batch_attr_once;
 
 static cg_status batch_bin_attrs() {
-    if (g_batch_attr) return CG_OK;
-    const int mx = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(float));
-    CG_CUDA(cudaFuncSetAttribute(kb_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    CG_CUDA(cudaFuncSetAttribute(kb_bin_key, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (1 << kMaxDigitBits) * (int)sizeof(int)));
-    CG_CUDA(cudaFuncSetAttribute(kb_bin_hist1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (1 << kMaxDigitBits) * (int)sizeof(int)));
-    g_batch_attr = true;
-    return CG_OK;
+    return once_per_device(g_batch_attr_once, [] {
+        const int mx = (int)scatter_smem_bytes(kMaxDigitBits, sizeof(float));
+        CG_CUDA(cudaFuncSetAttribute(kb_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        CG_CUDA(cudaFuncSetAttribute(kb_bin_key, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (1 << kMaxDigitBits) * (int)sizeof(int)));
+        CG_CUDA(cudaFuncSetAttribute(kb_bin_hist1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (1 << kMaxDigitBits) * (int)sizeof(int)));
+        return CG_OK;
+    });
 }
 
 cg_status launch_batch_bin(int phase, const BLaunch& L, unsigned grid, size_t smem, cudaStream_t s) {

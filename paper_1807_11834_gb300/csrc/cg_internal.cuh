@@ -6,12 +6,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/cg.h"
 
 namespace cg {
+
+// One-time settings that the CUDA runtime keeps per device (kernel
+// attributes such as the dynamic shared-memory limit): f runs once on each
+// device, the first time a call is made with that device current, under a
+// lock; a failure is returned and retried on the next call.
+struct PerDeviceOnce {
+    std::mutex mu;
+    bool done[64] = {};
+};
+
+template <typename F>
+inline cg_status once_per_device(PerDeviceOnce& o, F f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return CG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(o.mu);
+    if (o.done[dev]) return CG_OK;
+    const cg_status s = f();
+    if (s == CG_OK) o.done[dev] = true;
+    return s;
+}
 
 // ----------------------------------------------------------------------
 // Sizes

@@ -804,15 +804,17 @@ using namespace cg::mlp;
 size_t smem_forward() { return std::max<size_t>(sizeof(Smem) + 1024, 28 * 1024); }
 size_t smem_learned() { return smem_forward(); }
 size_t smem_train() { return sizeof(SmemTrain) + 1024; }
-bool g_mlp_attr = false;
+cg::PerDeviceOnce g_mlp_attr_once;
 
 cg_status mlp_attrs() {
-    if (g_mlp_attr) return CG_OK;
-    CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forward()));
-    CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
-    CG_CUDA(cudaFuncSetAttribute(k_drag_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_learned()));
-    g_mlp_attr = true;
-    return CG_OK;
+    return cg::once_per_device(g_mlp_attr_once, [] {
+        CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_forward()));
+        CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
+        CG_CUDA(cudaFuncSetAttribute(k_drag_learned, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_learned()));
+        return CG_OK;
+    });
 }
 
 void host_scale(const float* lo, const float* hi, float out[16]) {

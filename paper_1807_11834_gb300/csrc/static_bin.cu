@@ -101,7 +101,11 @@ extern "C" cg_status cg_bin_particles_static(const cg_grid_desc* desc, int64_t n
         if (!(d.extent[a] > 0.0) || d.fine_n[a] < 1 || d.fine_n[a] % d.ratio != 0) return CG_ERR_INVALID_ARG;
         nb[a] = d.fine_n[a] / d.ratio;
         if (nb[a] < 2) return CG_ERR_INVALID_ARG;
+        // refuse before the product can overflow: each factor is at most
+        // 2^22, so the running product stays below 2^63
+        if (nb[a] > (1 << cg::kMaxBulkBits)) return CG_ERR_OUT_OF_RANGE;
         nbulk *= nb[a];
+        if (nbulk > (1LL << cg::kMaxBulkBits)) return CG_ERR_OUT_OF_RANGE;
     }
     if (!cg::sort_choice_valid(d.sort_digits)) return CG_ERR_INVALID_ARG;
     if (nbulk > (1LL << cg::kMaxBulkBits)) return CG_ERR_OUT_OF_RANGE;

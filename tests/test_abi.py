@@ -164,3 +164,24 @@ def test_constants_match_the_header(tmp_path):
               "CG_ERR_TIMEOUT", "CG_ERR_NONFINITE"):
         py[k] = {v: c for c, v in cg.STATUS_NAMES.items()}[k]
     assert {n: v for n, v in zip(names, got)} == {n: py[n] for n in names}
+
+
+def test_grid_sizes_whose_product_overflows_are_refused():
+    """Cell counts are checked while their product grows: fine_n of
+    2^21 x 2^21 x 2^22 (ratio 1) would wrap a 64-bit product to 0; both the
+    handle and the allocation-free binning refuse it (CG_ERR_OUT_OF_RANGE)
+    before any device work, as they refuse a grid just over 2^22 bulk
+    cells."""
+    import paper_1807_11834_gb300 as cg
+    import synth
+    L = cg.lib()
+    base = synth.tiny(seed=0, n=1).desc
+    for fine_n, ratio in (((1 << 21, 1 << 21, 1 << 22), 1), ((1 << 30, 1 << 30, 4), 2),
+                          ((4096, 2050, 4), 2)):
+        d = dict(base, fine_n=fine_n, ratio=ratio)
+        h = ctypes.c_void_p()
+        assert L.cg_create_grids(ctypes.byref(cg.make_desc(d)), None, ctypes.byref(h)) == 5, fine_n
+        assert not h.value
+        buf = ctypes.c_int32 * 4
+        perm, cs = buf(), buf()
+        assert L.cg_bin_particles_static(ctypes.byref(cg.make_desc(d)), 0, None, None, perm, cs, None) == 5, fine_n

@@ -84,3 +84,23 @@ def test_closure_entries_check_their_tensors_first():
         cg.Mlp.train_step(fake, torch.zeros(10, 7), torch.zeros(10), 1e-3)
     with pytest.raises(ValueError, match="var_stale"):
         cg.Mlp.bind(fake, torch.zeros(5, dtype=torch.float64), None)
+
+
+def test_static_binning_checks_its_tensors_first():
+    """cg_bin_particles_static's wrapper refuses a host tensor, a particle
+    array of the other precision and a short cell_start before its pointers
+    reach the library (a kernel would otherwise read or write out of
+    bounds)."""
+    import synth
+    w = synth.tiny(seed=0, n=64, fp64=False)
+    nb = (w.desc["fine_n"][0] // w.desc["ratio"]) ** 3
+    pos = torch.from_numpy(w.pos_d)
+    perm = torch.empty(w.n, dtype=torch.int32)
+    cs = torch.empty(nb + 1, dtype=torch.int32)
+    with pytest.raises(ValueError, match="pos_d"):
+        cg.cg_bin_particles_static(w.desc, pos, perm, cs)                      # host memory
+    with pytest.raises(ValueError, match="pos_d"):
+        cg.cg_bin_particles_static(w.desc, pos.double(), perm, cs)             # FP64 under an FP32 descriptor
+    d64 = dict(w.desc, fp64=True)
+    with pytest.raises(ValueError, match="pos_d"):
+        cg.cg_bin_particles_static(d64, pos, perm, cs)                         # FP32 under an FP64 descriptor
