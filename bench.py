@@ -1,12 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the particle <-> dual-grid coupling step on GB300.
 
-Workload: the packed bed (1 x 1 x 2 m, fine 256 x 256 x 512, ratio 4 ->
-bulk 64 x 64 x 128, 4,000,000 spheres d = 4 mm, Ergun / Wen-Yu drag,
-FP32), seeded synthetic inputs resident in HBM.  One step is one call of
-cg_step: bin, porosity, fluid average, drag with the fused reaction
-deposit, projection of the source and of the porosity onto the fine grid,
-and the conservation sums.
+Workload (default): the clustered bed, the largest single-GPU
+configuration (1 x 1 x 0.5 m, fine 512 x 512 x 256, ratio 4 -> bulk
+128 x 128 x 64, 32,000,000 log-normal spheres in 200 Gaussian clusters,
+Di Felice drag, gravity, FP32), seeded synthetic inputs resident in HBM.
+One step is one call of cg_step with dt = 1e-4: bin, porosity, fluid
+average, drag with the fused reaction deposit and the semi-implicit Euler
+advance of the particles, projection of the source and of the porosity
+onto the fine grid, and the conservation sums.  The particles move from
+step to step, so every timed step rebins a new state.  --workload
+packed_bed times the 4M-particle packed bed (no advance) instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -54,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", default="packed_bed",
+    ap.add_argument("--workload", default="clustered_bed",
                     choices=["packed_bed", "small_packed_bed", "clustered_bed", "medium_clustered_bed",
                              "small_clustered_bed"])
     ap.add_argument("--batch", action="store_true",
@@ -63,7 +67,8 @@ def parse():
                     help="train the drag closure on the workload family, then compare learned and plain steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=2, help="full oracle steps in the CPU baseline")
+    ap.add_argument("--cpu-steps", type=int, default=0,
+                    help="full oracle steps in the CPU baseline (0: one above 8M particles, else two)")
     ap.add_argument("--no-graph", action="store_true", help="time eager cg_step calls instead of a CUDA graph")
     ap.add_argument("--map", action="store_true",
                     help="time the maps between non-nested grids (bulk 64x64x128, fine 250x250x500 offset)")
@@ -188,7 +193,7 @@ def workload_name(name, w):
             f"{w.n} spheres, {law}, {prec}")
 
 
-def algorithmic_bytes(g, n, eps_fine=True, implicit=False):
+def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False):
     """Algorithmic bytes of one step (the minimal traffic of the path) and,
     per launch, of each kernel of this implementation (bytes it must move
     to do its part, FP32; L2-resident gathers of the bulk fields and
@@ -196,7 +201,8 @@ def algorithmic_bytes(g, n, eps_fine=True, implicit=False):
 
     Step: particles read x, y, z, d (16) and u_p (12), write F (12), plus
     the bin key and permutation written and read once (8); fine cells read
-    u_f (12) and write S_f (12) and eps_f (4); bulk cells ~40 B."""
+    u_f (12) and write S_f (12) and eps_f (4); bulk cells ~40 B.  With the
+    Euler advance, particles also write x and u_p back (24)."""
     import paper_1807_11834_gb300 as cg
     nf, nb = g.n_fine, g.n_bulk
     nbx = nb  # bulk cells
@@ -220,6 +226,9 @@ def algorithmic_bytes(g, n, eps_fine=True, implicit=False):
         "project_implicit": nf * 16 + nbx * 16,           # A_f, b_f written, A, b read
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
+    if euler:
+        per["drag"] += n * 24                             # x and u_p written back
+        step += n * 24
     if implicit:
         per["drag"] += n * 16                             # the sorted (beta, beta u) record
         step += n * 16 + nf * 16 + nb * 16                # beta, beta u per particle; A, b on both grids
@@ -240,6 +249,7 @@ def run_gb300(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = getattr(synth, args.workload)(seed=rank)
+    dt = float(w.dt)                # 1e-4 for the clustered bed (advanced every step), 0 for the packed bed
     if args.reorder:
         w.desc["sort_digits"] = cg.CG_SORT_CELLS
     g = cg.Grids(w.desc)
@@ -267,14 +277,14 @@ def run_gb300(args):
         torch.cuda.synchronize()
 
     for _ in range(max(3, args.warmup)):
-        g.cg_step(pos, vel, uf, out)
+        g.cg_step(pos, vel, uf, out, dt=dt)
     rc, flags, counts = g.cg_sync_status()
     if rc != 0:
         raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
 
     # launches of one step (counted eagerly; graph replays run the same kernels)
     l0 = g.cg_launch_count()
-    g.cg_step(pos, vel, uf, out)
+    g.cg_step(pos, vel, uf, out, dt=dt)
     launches_per_step = g.cg_launch_count() - l0
     torch.cuda.synchronize()
 
@@ -291,20 +301,20 @@ def run_gb300(args):
         barrier()
         return e0.elapsed_time(e1), t0, t1
 
-    eager_ms, _, _ = timed(lambda: g.cg_step(pos, vel, uf, out), min(args.steps, 200))
+    eager_ms, _, _ = timed(lambda: g.cg_step(pos, vel, uf, out, dt=dt), min(args.steps, 200))
     eager_ms_step = eager_ms / min(args.steps, 200)
-    step_fn = lambda: g.cg_step(pos, vel, uf, out)
+    step_fn = lambda: g.cg_step(pos, vel, uf, out, dt=dt)
     graph = None
     if not args.no_graph:
         cs = torch.cuda.Stream()
         cs.wait_stream(torch.cuda.current_stream())
         g.set_stream(cs)
         with torch.cuda.stream(cs):
-            g.cg_step(pos, vel, uf, out)
+            g.cg_step(pos, vel, uf, out, dt=dt)
         cs.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=cs):
-            g.cg_step(pos, vel, uf, out)
+            g.cg_step(pos, vel, uf, out, dt=dt)
         g.set_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
         step_fn = graph.replay
@@ -332,11 +342,11 @@ def run_gb300(args):
     g.cg_profile_reset()
     g.cg_profile_enable(True)
     for _ in range(prof_steps):
-        g.cg_step(pos, vel, uf, out)
+        g.cg_step(pos, vel, uf, out, dt=dt)
     prof = g.cg_profile_read()
     g.cg_profile_enable(False)
 
-    step_bytes, kern_bytes = algorithmic_bytes(g, n, implicit=args.implicit)
+    step_bytes, kern_bytes = algorithmic_bytes(g, n, implicit=args.implicit, euler=dt > 0)
     peak, peak_src = load_peaks()
     kern_ms = {k: v[1] / v[0] for k, v in prof.items() if v[0]}
     kern_total = {k: v[1] for k, v in prof.items()}
@@ -375,7 +385,7 @@ def run_gb300(args):
         hout = {k: (torch.empty(v.shape, dtype=v.dtype).pin_memory() if v is not None else None)
                 for k, v in out.items()}
         for _ in range(2):
-            g.cg_step_host(hpos, hvel, huf, hout)
+            g.cg_step_host(hpos, hvel, huf, hout, dt=dt)
         ke = max(3, min(args.steps, 30))
 
         def host_run(pipelined):
@@ -383,9 +393,9 @@ def run_gb300(args):
             ta = time.perf_counter()
             for _ in range(ke):
                 if pipelined:
-                    g.cg_step_host_async(hpos, hvel, huf, hout)
+                    g.cg_step_host_async(hpos, hvel, huf, hout, dt=dt)
                 else:
-                    g.cg_step_host(hpos, hvel, huf, hout)
+                    g.cg_step_host(hpos, hvel, huf, hout, dt=dt)
             if pipelined:
                 g.cg_step_host_wait()
             return max_over_ranks(time.perf_counter() - ta, world, dev)
@@ -401,13 +411,16 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        ks = max(1, args.cpu_steps)
+        ks = args.cpu_steps if args.cpu_steps > 0 else (1 if n > 8_000_000 else 2)
+        cpos, cvel = w.pos_d, w.vel
         ta = time.perf_counter()
         for _ in range(ks):
-            oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+            r = oracle.step(w.desc, cpos, cvel, w.u_fine, dt=dt, want_eps_fine=True)
+            cpos, cvel = r["pos_d"], r["vel"]
         tc = time.perf_counter() - ta
         cpu = {"value": n * ks / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ks} full oracle steps of the same {args.workload.replace('_', ' ')} (FP64 C, single thread), "
+               "sample": f"{ks} full oracle step{'s' if ks > 1 else ''} (dt {dt:g}) of the same "
+                         f"{args.workload.replace('_', ' ')} from its initial state (FP64 C, single thread), "
                          f"{tc:.1f} s"}
 
     if world > 1:
@@ -430,8 +443,9 @@ def run_gb300(args):
                        "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
                        "step_frac_of_hbm": round(step_gbs / peak, 4),
                        "semi_implicit": bool(args.implicit),
+                       "dt": dt, "euler_advance": dt > 0,
                        "particle_order": ("reordered into cell order once before timing, per-cell sort"
-                                          if args.reorder else "as generated")},
+                                          if args.reorder else w.notes.get("order", "as generated"))},
             "roofline": roofline,
             "kernels": {k: {"ms_per_launch": round(kern_ms[k], 5), "share": round(kern_total[k] / tot, 4),
                             "launches_per_step": kern_launches[k]} for k in sorted(kern_total)},
@@ -455,16 +469,22 @@ def run_reference(args):
     oracle.build()
     w = getattr(synth, args.workload)(seed=0)
     n = w.n
+    dt = float(w.dt)
+    # a bounded sample: whole steps of the workload, as many as fit a few minutes
     wu = min(max(0, args.warmup), 1)
-    ks = max(1, min(args.steps, 8))
+    ks = max(1, min(args.steps, 3 if n > 8_000_000 else 8))
+    pos, vel = w.pos_d, w.vel
     for _ in range(wu):
-        oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True)
+        pos, vel = r["pos_d"], r["vel"]
     ta = time.perf_counter()
     for _ in range(ks):
-        oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
+        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True)
+        pos, vel = r["pos_d"], r["vel"]
     tc = time.perf_counter() - ta
     value = n * ks / tc
-    sample = f"{ks} full oracle steps (warm-up {wu}) of the {args.workload.replace('_', ' ')}, FP64 C, single thread"
+    sample = (f"{ks} full oracle steps (warm-up {wu}, dt {dt:g}, each from the state the last one advanced) of the "
+              f"{args.workload.replace('_', ' ')}, FP64 C, single thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": ks, "warmup": wu, "ms_per_step": 1e3 * tc / ks, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -157,7 +157,8 @@ def packed_bed(seed: int = 0, fine_n=(256, 256, 512), ratio: int = 4,
     layers = int(math.ceil(n / (nlx * nly)))
     return Workload("packed_bed", desc, _pack(xyz, d, dtype), vel, u.astype(dtype, copy=False),
                     notes=dict(lattice_spacing=tuple(sp), layers=layers,
-                               bed_height=layers * sp[2]))
+                               bed_height=layers * sp[2],
+                               order="lattice order, layer by layer (close to cell order)"))
 
 
 def clustered_bed(seed: int = 0, fine_n=(512, 512, 256), ratio: int = 4,
@@ -193,7 +194,9 @@ def clustered_bed(seed: int = 0, fine_n=(512, 512, 256), ratio: int = 4,
     pos = _pack(xyz, dd, dtype)
     # positions exactly at the upper face after rounding to the path dtype stay inside
     return Workload("clustered_bed", desc, pos, vel, u.astype(dtype, copy=False),
-                    dt=dt, steps=steps)
+                    dt=dt, steps=steps,
+                    notes=dict(order="draw order: each particle in a uniformly drawn cluster "
+                                     "(no spatial order)"))
 
 
 def medium_clustered_bed(seed: int = 0, fp64: bool = False) -> Workload:

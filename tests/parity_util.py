@@ -32,21 +32,44 @@ def assert_close(name, got, ref, tol, vec=False, mask=None):
     return mx
 
 
-def assert_close_interp(name, got, ref, ref_abs, tol):
+def interp_errors(got, ref, ref_abs, mask=None):
+    """Per-cell errors of an interpolated field ([3][m] or [m]) under the two
+    denominators: (plain, widened).  plain is the metric of rel_err
+    (max(|ref|, 1e-3 max|ref|)); widened also takes |interpolant of the
+    absolute corner values| (ref_abs).  Euclidean norms per cell; mask
+    (nullable, [m] bool) keeps the cells compared."""
+    got = np.atleast_2d(np.asarray(got, np.float64))
+    ref = np.atleast_2d(np.asarray(ref, np.float64))
+    ref_abs = np.atleast_2d(np.asarray(ref_abs, np.float64))
+    if mask is not None:
+        got, ref, ref_abs = got[:, mask], ref[:, mask], ref_abs[:, mask]
+    if ref.shape[1] == 0:
+        return np.zeros(0), np.zeros(0)
+    num = np.sqrt(((got - ref) ** 2).sum(axis=0))
+    den_ref = np.sqrt((ref ** 2).sum(axis=0))
+    den_w = np.maximum(den_ref, np.sqrt((ref_abs ** 2).sum(axis=0)))
+    plain = num / np.maximum(den_ref, max(1e-3 * den_ref.max(), 1e-300))
+    widened = num / np.maximum(den_w, max(1e-3 * den_w.max(), 1e-300))
+    return plain, widened
+
+
+def assert_close_interp(name, got, ref, ref_abs, tol, mask=None, report=None):
     """Interpolated field ([3][m] or [m]): the error of each cell within tol
     of max(|ref|, |interpolant of the absolute corner values| (ref_abs),
     1e-3 max|ref|), Euclidean norms per cell.  An FP32 lerp between values
     of opposite sign rounds relative to the corner magnitudes, not to the
-    (possibly near-zero) result."""
-    got = np.atleast_2d(np.asarray(got, np.float64))
-    ref = np.atleast_2d(np.asarray(ref, np.float64))
-    ref_abs = np.atleast_2d(np.asarray(ref_abs, np.float64))
-    num = np.sqrt(((got - ref) ** 2).sum(axis=0))
-    den = np.maximum(np.sqrt((ref ** 2).sum(axis=0)), np.sqrt((ref_abs ** 2).sum(axis=0)))
-    den = np.maximum(den, max(1e-3 * den.max(), 1e-300))
-    r = num / den
-    assert r.max() <= tol, f"{name}: max rel err {r.max():.3e} > {tol:.1e}"
-    return float(r.max())
+    (possibly near-zero) result.  report (nullable dict) receives both
+    metrics' maxima and the number of cells that pass only under the
+    widened denominator, so that the widening is seen not to hide error."""
+    plain, widened = interp_errors(got, ref, ref_abs, mask)
+    if plain.size == 0:
+        return 0.0
+    if report is not None:
+        report[name] = {"max_widened": float(widened.max()), "max_plain": float(plain.max()),
+                        "cells_only_widened": int(((plain > tol) & (widened <= tol)).sum()),
+                        "cells": int(plain.size)}
+    assert widened.max() <= tol, f"{name}: max rel err {widened.max():.3e} > {tol:.1e}"
+    return float(widened.max())
 
 
 def to_dev(a, dev="cuda:0"):
@@ -61,6 +84,20 @@ def to_np(t):
 def inputs(w, dev="cuda:0"):
     """pos_d, vel, u_fine (flattened [3][n_f]) as device tensors."""
     return to_dev(w.pos_d, dev), to_dev(w.vel, dev), to_dev(w.u_fine.reshape(3, -1), dev)
+
+
+def switch_exclusions(w, ref, mask):
+    """The cells whose values depend on a particle excluded by mask (near a
+    correlation switch): bulk cells holding one (their reaction sums its
+    force) and fine cells whose projection stencil reads such a bulk cell
+    (the oracle's projection of the cells' indicator is non-zero there).
+    Returns (bulk cells kept, fine cells kept) as bool arrays."""
+    import oracle
+    nb = np.asarray(ref["eps_bulk"]).shape[0]
+    bad = np.zeros(nb, bool)
+    bad[np.asarray(ref["cell"])[~mask]] = True
+    fine_bad = oracle.project(w.desc, bad.astype(np.float64)) > 0
+    return ~bad, ~fine_bad
 
 
 def switch_mask(w, ref):

@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from parity_util import (TOL_FP32, TOL_FP64, assert_close, assert_close_interp, inputs, to_dev, to_np,
-                         switch_mask)
+                         switch_exclusions, switch_mask)
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,14 @@ def run_step(cg, w, dt=0.0, eps_fine=True):
     return host
 
 
-def compare_step(w, got, ref, tol, mask=None):
+def compare_step(w, got, ref, tol, mask=None, report=None):
+    """Bins bit for bit, then every field within tol.  mask ([n] bool,
+    nullable) drops the particles within rounding of a correlation switch
+    (FP32 and FP64 may take different branches there): their forces, the
+    reaction of the bulk cells holding them and the fine cells whose
+    stencil reads those bulk cells; everything else is compared.  report
+    (nullable dict) receives the number of excluded particles and cells and
+    the widened-denominator statistics of the interpolated fields."""
     assert np.array_equal(got["cell"], ref["cell"]), "cells differ"
     assert np.array_equal(got["cell_start"], ref["cell_start"]), "cell starts differ"
     assert np.array_equal(got["perm"], ref["perm"]), "permutation differs"
@@ -40,21 +47,58 @@ def compare_step(w, got, ref, tol, mask=None):
     errs["u_bulk"] = assert_close("u_bulk", got["u_bulk"], ref["u_bulk"], tol, vec=True)
     errs["var_bulk"] = assert_close("var_bulk", got["var_bulk"], ref["var_bulk"], tol)
     errs["force"] = assert_close("force", got["force"], ref["force"], tol, vec=True, mask=mask)
+    bulk_ok = fine_ok = None
+    if mask is not None and not mask.all():
+        bulk_ok, fine_ok = switch_exclusions(w, ref, mask)
+    if report is not None:
+        report["excluded"] = {"particles": 0 if mask is None else int((~mask).sum()),
+                              "bulk_cells": 0 if bulk_ok is None else int((~bulk_ok).sum()),
+                              "fine_cells": 0 if fine_ok is None else int((~fine_ok).sum())}
     # the projections interpolate bulk values of either sign (sources; the
     # porosity, negative where spheres overlap): their rounding is relative
     # to the interpolant of the absolute bulk values, projected by the oracle
-    if mask is None or mask.all():
-        errs["S_bulk"] = assert_close("S_bulk", got["S_bulk"], ref["S_bulk"], tol, vec=True)
-        S_abs = oracle.project(w.desc, np.abs(ref["S_bulk"]))
-        errs["S_fine"] = assert_close_interp("S_fine", got["S_fine"], ref["S_fine"], S_abs, tol)
+    errs["S_bulk"] = assert_close("S_bulk", got["S_bulk"], ref["S_bulk"], tol, vec=True, mask=bulk_ok)
+    S_abs = oracle.project(w.desc, np.abs(ref["S_bulk"]))
+    errs["S_fine"] = assert_close_interp("S_fine", got["S_fine"], ref["S_fine"], S_abs, tol, mask=fine_ok,
+                                         report=report)
     if got.get("eps_fine") is not None and ref.get("eps_fine") is not None:
         e_abs = oracle.project(w.desc, np.abs(ref["eps_bulk"]))
-        errs["eps_fine"] = assert_close_interp("eps_fine", got["eps_fine"], ref["eps_fine"], e_abs, tol)
+        errs["eps_fine"] = assert_close_interp("eps_fine", got["eps_fine"], ref["eps_fine"], e_abs, tol,
+                                               report=report)
     return errs
 
 
-def compare_sums(got, ref, tol):
-    s, r = got["sums"], ref["sums"]
+def _without_particles(sums, force, keep, mass_u=None):
+    """The step's sums with the drag of the particles outside keep taken
+    out: sum F loses their forces, sum S_B V_B and sum S_f V_f (each equal to
+    -sum F by action-reaction and conservative projection) lose their
+    reactions, sum |F| loses their magnitudes, and the momentum after the
+    advance loses their m u (mass_u, [3][n], when given)."""
+    s = np.array(sums, np.float64)
+    if keep is None or keep.all():
+        return s
+    F = np.asarray(force, np.float64)[:, ~keep]
+    fx = F.sum(axis=1)
+    s[2:5] -= fx
+    s[5:8] += fx
+    s[8:11] += fx
+    s[11] -= np.sqrt((F ** 2).sum(axis=0)).sum()
+    if mass_u is not None:
+        s[12:15] -= np.asarray(mass_u, np.float64)[:, ~keep].sum(axis=1)
+    return s
+
+
+def compare_sums(got, ref, tol, mask=None, w=None):
+    """The device's FP64 conservation sums against the oracle's (with the
+    particles outside mask taken out of both, see _without_particles)."""
+    mu_got = mu_ref = None
+    if mask is not None and not mask.all() and w is not None and "vel" in got:
+        d = w.pos_d[:, 3].astype(np.float64)
+        m = w.desc["rho_p"] * np.pi * d ** 3 / 6.0
+        mu_got = m * np.asarray(got["vel"], np.float64)[:, :3].T
+        mu_ref = m * np.asarray(ref["vel"], np.float64)[:, :3].T
+    s = _without_particles(got["sums"], got["force"], mask, mu_got)
+    r = _without_particles(ref["sums"], ref["force"], mask, mu_ref)
     vol = abs(r[0])
     fs = r[11]
     assert abs(s[0] - r[0]) <= tol * vol and abs(s[1] - r[1]) <= tol * vol
@@ -150,13 +194,18 @@ def test_tiny_fp32_step(cuda_lib):
 
 
 def test_small_packed_bed_fp32(cuda_lib):
+    """The packed-bed recipe at 1/64 of its cells (Ergun / Wen-Yu): every
+    field and the sums, with only the particles at the correlation switch
+    and the cells that depend on them left out."""
     w = synth.small_packed_bed(seed=0)
     ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
     got = run_step(cuda_lib, w)
     mask = switch_mask(w, ref)
-    compare_step(w, got, ref, TOL_FP32, mask=mask)
-    if mask.all():
-        compare_sums(got, ref, TOL_FP32)
+    report = {}
+    errs = compare_step(w, got, ref, TOL_FP32, mask=mask, report=report)
+    compare_sums(got, ref, TOL_FP32, mask=mask, w=w)
+    assert {"S_bulk", "S_fine", "eps_fine"} <= set(errs)
+    print("small_packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()}, report)
 
 
 def test_small_clustered_bed_fp32_with_euler(cuda_lib):
@@ -178,9 +227,14 @@ def test_packed_bed_full_size_fp32(cuda_lib):
     ref = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, want_eps_fine=True)
     got = run_step(cuda_lib, w)
     mask = switch_mask(w, ref)
-    errs = compare_step(w, got, ref, TOL_FP32, mask=mask)
-    print("packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()},
-          "excluded at switch:", int((~mask).sum()))
+    report = {}
+    errs = compare_step(w, got, ref, TOL_FP32, mask=mask, report=report)
+    compare_sums(got, ref, TOL_FP32, mask=mask, w=w)
+    assert {"S_bulk", "S_fine", "eps_fine"} <= set(errs)
+    # the exclusion stays local: a few particles, their cells and stencils
+    ex = report["excluded"]
+    assert ex["particles"] < 1e-4 * w.n and ex["fine_cells"] <= 64 * ex["bulk_cells"] * 8
+    print("packed_bed max rel errors:", {k: f"{v:.2e}" for k, v in errs.items()}, report)
 
 
 def _euler_checks(w, got, ref):
