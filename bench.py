@@ -45,10 +45,7 @@ UNIT = "particle-steps/s"
 NCU_TRAFFIC = {
     # packed bed, two eager steps: k_average<float,4> 404.15 + 6.02 and
     # 404.79 + 5.02 MB (read + written); per launch, the mean
-    "average": {"file": "fine.cu", "sha": "a4d41dcdd302d93f", "bytes": 410.0e6},
-    # packed bed with the digit sort: k_bin_scatter first pass 20.53 MB, final
-    # pass 62.48 / 60.02 MB (two captures); per launch, the mean of the passes
-    "bin_scatter": {"file": "bin.cu", "sha": "88c48787c50ba765", "bytes": 40.9e6},
+    ("packed_bed", "average"): {"file": "fine.cu", "sha": "a4d41dcdd302d93f", "bytes": 410.0e6},
 }
 
 
@@ -75,6 +72,9 @@ def parse():
     ap.add_argument("--reorder", action="store_true",
                     help="reorder the particles into cell order once before timing (cg_reorder_particles) and "
                          "bin with the per-cell sort")
+    ap.add_argument("--step", choices=["auto", "sorted", "caller"], default="auto",
+                    help="the step timed: cg_step_sorted (particles left in cell order every step; the default "
+                         "for an advancing workload) or cg_step (the caller's particle order kept)")
     ap.add_argument("--implicit", action="store_true",
                     help="also form the semi-implicit exchange coefficients (bulk and fine) in every step "
                          "(device entry only: no e2e line)")
@@ -193,7 +193,7 @@ def workload_name(name, w):
             f"{w.n} spheres, {law}, {prec}")
 
 
-def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False):
+def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False, sorted_step=False):
     """Algorithmic bytes of one step (the minimal traffic of the path) and,
     per launch, of each kernel of this implementation (bytes it must move
     to do its part, FP32; L2-resident gathers of the bulk fields and
@@ -224,6 +224,13 @@ def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False):
         "average": nf * 12 + nbx * 16,                    # u_f read, u_B and var written
         "deposit_implicit": n * (16 + 4) + nbx * 16,      # sorted (beta, beta u) + key read; A, b written
         "project_implicit": nf * 16 + nbx * 16,           # A_f, b_f written, A, b read
+        # incremental rebinning (movers' own kernels and the idle fallback not counted)
+        "rebin_key": n * (16 + 4 + 4),                    # pos read; key, diameter written
+        "rebin_mark": n * ((16 + 4 + 4 + 4 + 8) if sorted_step else (4 + 4 + 4 + 8)),
+        # sorted input: pos, old cell read; key, diameter, record written;
+        # else old id, old cell, new cell (gathered) read, record written
+        "rebin_cells": nbx * 16,                          # old starts, departures, arrivals read; counts written
+        "rebin_stay": n * (8 + 4 + 16),                   # record, diameter read; perm, cell, inverse, diameter written
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
     if euler:
@@ -250,6 +257,10 @@ def run_gb300(args):
 
     w = getattr(synth, args.workload)(seed=rank)
     dt = float(w.dt)                # 1e-4 for the clustered bed (advanced every step), 0 for the packed bed
+    # the advancing workload steps with cg_step_sorted, which leaves the
+    # particles in cell order (as a DEM code keeps them); --step caller times
+    # cg_step, which keeps the caller's particle order
+    sorted_step = args.step == "sorted" or (args.step == "auto" and dt > 0)
     if args.reorder:
         w.desc["sort_digits"] = cg.CG_SORT_CELLS
     g = cg.Grids(w.desc)
@@ -270,54 +281,106 @@ def run_gb300(args):
     if args.implicit:
         args.no_e2e = True   # the host-buffer entries do not form the semi-implicit fields
     input_bytes = pos.numel() * 4 + vel.numel() * 4 + uf.numel() * 4
+    # an advanced workload is a run of w.steps steps from its initial state
+    # (the clustered bed: 100; explicit Euler at dt = 1e-4 is not stable for
+    # the smallest spheres in the clamped cluster cores over much longer
+    # runs): timed steps come in such runs, each from a copy of the initial
+    # state made outside the timed region
+    run_len = int(w.steps) if dt > 0 else 0
+    pos0, vel0 = pos.clone(), vel.clone()
+    # the sorted step reads one pair of particle arrays and writes the other
+    bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))] if sorted_step else [(pos, vel)]
+    par = [0]
+
+    def reset():
+        if run_len:
+            pos.copy_(pos0)
+            vel.copy_(vel0)
+            par[0] = 0
+
+    def step_sorted():
+        src, dst = bufs[par[0]], bufs[par[0] ^ 1]
+        g.cg_step_sorted(src[0], src[1], dst[0], dst[1], uf, out, dt=dt)
+        par[0] ^= 1
+
+    def step_caller():
+        g.cg_step(pos, vel, uf, out, dt=dt)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        g.cg_step(pos, vel, uf, out, dt=dt)
-    rc, flags, counts = g.cg_sync_status()
-    if rc != 0:
-        raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
-
-    # launches of one step (counted eagerly; graph replays run the same kernels)
-    l0 = g.cg_launch_count()
-    g.cg_step(pos, vel, uf, out, dt=dt)
-    launches_per_step = g.cg_launch_count() - l0
-    torch.cuda.synchronize()
-
     def timed(fn, steps):
+        """Device time of `steps` calls of fn (CUDA events on the launching
+        stream), in runs of run_len steps each from the initial state when
+        the workload advances; the resets stay outside the events."""
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total, left = 0.0, steps
         barrier()
         t0 = time.time()
-        e0.record()
-        for _ in range(steps):
-            fn()
-        e1.record()
-        e1.synchronize()
+        while left > 0:
+            k = min(run_len, left) if run_len else left
+            reset()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(k):
+                fn()
+            e1.record()
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            left -= k
         t1 = time.time()
         barrier()
-        return e0.elapsed_time(e1), t0, t1
+        return total, t0, t1
 
-    eager_ms, _, _ = timed(lambda: g.cg_step(pos, vel, uf, out, dt=dt), min(args.steps, 200))
-    eager_ms_step = eager_ms / min(args.steps, 200)
-    step_fn = lambda: g.cg_step(pos, vel, uf, out, dt=dt)
-    graph = None
-    if not args.no_graph:
+    def graphed(eager_fn, variants):
+        """CUDA graphs of the step, one per particle buffer the step can start
+        from, replayed in turn; captured on a side stream after the handle has
+        stepped through every variant once (so that each capture sees the
+        handle state its replays will meet)."""
         cs = torch.cuda.Stream()
         cs.wait_stream(torch.cuda.current_stream())
         g.set_stream(cs)
         with torch.cuda.stream(cs):
-            g.cg_step(pos, vel, uf, out, dt=dt)
+            for _ in range(2 * variants):
+                eager_fn()
         cs.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=cs):
-            g.cg_step(pos, vel, uf, out, dt=dt)
+        graphs = []
+        for _ in range(variants):
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=cs):
+                eager_fn()
+            graphs.append(gr)
         g.set_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
-        step_fn = graph.replay
+
+        def replay():
+            graphs[par[0]].replay()
+            par[0] = (par[0] + 1) % variants
+        return replay
+
+    eager_fn = step_sorted if sorted_step else step_caller
+    for _ in range(max(3, args.warmup)):
+        eager_fn()
+    rc, flags, counts = g.cg_sync_status()
+    if rc != 0:
+        raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
+    reset()
+
+    # launches of one step (counted eagerly; graph replays run the same kernels)
+    l0 = g.cg_launch_count()
+    eager_fn()
+    launches_per_step = g.cg_launch_count() - l0
+    torch.cuda.synchronize()
+
+    eager_ms, _, _ = timed(eager_fn, min(args.steps, 200))
+    eager_ms_step = eager_ms / min(args.steps, 200)
+    step_fn = eager_fn
+    if not args.no_graph:
+        reset()
+        step_fn = graphed(eager_fn, 2 if sorted_step else 1)
+        reset()
         for _ in range(max(3, args.warmup)):
             step_fn()
         torch.cuda.synchronize()
@@ -334,6 +397,21 @@ def run_gb300(args):
     if rc != 0:
         raise RuntimeError(f"timed status {rc}")
 
+    # the other step of an advancing workload, timed the same way: cg_step
+    # keeps the caller's (generated, random) particle order
+    caller = None
+    if sorted_step and not args.no_graph:
+        reset()
+        for _ in range(max(3, args.warmup)):
+            step_caller()
+        reset()
+        caller_fn = graphed(step_caller, 1)
+        ms_c, _, _ = timed(caller_fn, min(args.steps, 400))
+        ms_c /= min(args.steps, 400)
+        caller = {"ms_per_step": round(ms_c, 5), "value": n / (ms_c * 1e-3),
+                  "entry": "cg_step (particles kept in the caller's order, incremental rebinning from the last step)"}
+        par[0] = 0
+
     # per-kernel device time: a second pass of the same steps with the
     # library's CUDA events around every launch (kept out of the timed pass;
     # the library runs the step on one stream while timing kernels, so each
@@ -341,12 +419,14 @@ def run_gb300(args):
     prof_steps = min(args.steps, 200)
     g.cg_profile_reset()
     g.cg_profile_enable(True)
-    for _ in range(prof_steps):
-        g.cg_step(pos, vel, uf, out, dt=dt)
+    for k in range(prof_steps):
+        if k == 0 or (run_len and k % run_len == 0):
+            reset()
+        eager_fn()
     prof = g.cg_profile_read()
     g.cg_profile_enable(False)
 
-    step_bytes, kern_bytes = algorithmic_bytes(g, n, implicit=args.implicit, euler=dt > 0)
+    step_bytes, kern_bytes = algorithmic_bytes(g, n, implicit=args.implicit, euler=dt > 0, sorted_step=sorted_step)
     peak, peak_src = load_peaks()
     kern_ms = {k: v[1] / v[0] for k, v in prof.items() if v[0]}
     kern_total = {k: v[1] for k, v in prof.items()}
@@ -357,7 +437,7 @@ def run_gb300(args):
     roofline = None
     if dom_bytes is not None:
         ach = dom_bytes / (kern_ms[dominant] * 1e-3) / 1e9
-        tr = NCU_TRAFFIC.get(dominant)
+        tr = NCU_TRAFFIC.get((args.workload, dominant))
         traffic = None
         if tr and tr["sha"] == file_sha(os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", tr["file"])):
             traffic = tr["bytes"]
@@ -375,18 +455,17 @@ def run_gb300(args):
     # D2H of every output inside the timed region, every step).  The
     # pipelined entry enqueues each step (copies in, step, copies out) and the
     # timed region ends after the wait for the last one; the blocking entry
-    # is timed too.
+    # is timed too.  The host entries keep the caller's particle order.
     e2e = None
     if not args.no_e2e:
-        # the same particle order as the device-timed steps
-        hpos = pos.cpu().pin_memory()
-        hvel = vel.cpu().pin_memory()
+        hpos = pos0.cpu().pin_memory()
+        hvel = vel0.cpu().pin_memory()
         huf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).pin_memory()
         hout = {k: (torch.empty(v.shape, dtype=v.dtype).pin_memory() if v is not None else None)
                 for k, v in out.items()}
         for _ in range(2):
             g.cg_step_host(hpos, hvel, huf, hout, dt=dt)
-        ke = max(3, min(args.steps, 30))
+        ke = max(3, min(args.steps, 30))    # within one run of an advanced workload
 
         def host_run(pipelined):
             barrier()
@@ -403,6 +482,8 @@ def run_gb300(args):
         te_sync = host_run(False)
         te = host_run(True)
         d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None)
+        if dt > 0:
+            d2h += hpos.numel() * 4 + hvel.numel() * 4     # the advanced particles come back too
         e2e = {"value": job_throughput(world, n, ke, te), "unit": UNIT, "h2d_bytes_per_step": int(input_bytes),
                "d2h_bytes_per_step": int(d2h), "steps": ke, "ms_per_step": 1e3 * te / ke,
                "entry": "cg_step_host_async per step + cg_step_host_wait (pinned host buffers)",
@@ -426,6 +507,13 @@ def run_gb300(args):
     if world > 1:
         dist.barrier()
     if rank == 0:
+        if args.reorder:
+            order = "reordered into cell order once before timing, per-cell sort"
+        elif sorted_step:
+            order = (w.notes.get("order", "as generated") + " at the start of each run; every step writes the "
+                     "advanced particles in its own cell order (cg_step_sorted, two particle buffers)")
+        else:
+            order = w.notes.get("order", "as generated")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
@@ -436,16 +524,20 @@ def run_gb300(args):
                        "parallelism": f"replicas x{world}",
                        "l2": (f"inputs {input_bytes / 1e6:.0f} MB {'>' if input_bytes > 126e6 else '<'} L2 (126 MB) "
                               "per step, no flush"),
-                       "timing": ("CUDA graph of one cg_step, replayed K times" if graph is not None
-                                  else "eager cg_step calls"),
+                       "step": "cg_step_sorted" if sorted_step else "cg_step",
+                       "timing": ("CUDA graph of one step, replayed K times" if not args.no_graph
+                                  else "eager step calls") + (" (one graph per particle buffer, in turn)"
+                                                              if sorted_step and not args.no_graph else ""),
                        "eager_ms_per_step": round(eager_ms_step, 5),
                        "launches_per_step": launches_per_step,
                        "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
                        "step_frac_of_hbm": round(step_gbs / peak, 4),
                        "semi_implicit": bool(args.implicit),
                        "dt": dt, "euler_advance": dt > 0,
-                       "particle_order": ("reordered into cell order once before timing, per-cell sort"
-                                          if args.reorder else w.notes.get("order", "as generated"))},
+                       "run_length": (f"timed in runs of {run_len} steps, each from the initial state "
+                                      "(reset outside the timed region)") if run_len else "one run",
+                       "particle_order": order},
+            "caller_order_step": caller,
             "roofline": roofline,
             "kernels": {k: {"ms_per_launch": round(kern_ms[k], 5), "share": round(kern_total[k] / tot, 4),
                             "launches_per_step": kern_launches[k]} for k in sorted(kern_total)},

@@ -213,7 +213,17 @@ cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, in
  * at perm[cell_start[c] .. cell_start[c+1]) in increasing index order.
  * pos_d: [n] T4.  Outputs (all nullable): cell_out[n], perm_out[n],
  * cell_start_out[n_b + 1].  The handle keeps the binning for later
- * cg_deposit / cg_drag calls with the same n. */
+ * cg_deposit / cg_drag calls with the same n.
+ * Incremental rebinning: when the handle holds a binning of the same n (from
+ * the last call of cg_bin_particles or of a step) and sort_digits is
+ * CG_SORT_AUTO or CG_SORT_CELLS, the binning starts from it: only the
+ * particles whose cell changed are re-sorted, with particle i taken to be
+ * the particle i of that binning (or, for the sorted output of
+ * cg_step_sorted, the particle at its slot i).  The result is the same
+ * stable order whatever the particles did; when more than a quarter of them
+ * changed cell, or a cell received more than 256, the device falls back to
+ * the per-cell sort.  A descriptor with a digit width (6..11) always sorts
+ * from scratch. */
 cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
                            int32_t* cell_out, int32_t* perm_out, int32_t* cell_start_out);
 
@@ -308,6 +318,25 @@ cg_status cg_project_bulk_to_fine(cg_grids* g, int32_t ncomp, const void* bulk, 
  * (CG_ERR_INVALID_ARG). */
 cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine,
                   const cg_step_out* out, double dt);
+
+/* One coupling step, as cg_step, that also leaves the particles in the order
+ * of this step's binning (cell order): p_out->pos_d[s] and p_out->vel[s] are
+ * the records of particle perm[s] of p, advanced when dt > 0 (unchanged when
+ * dt == 0), and p's arrays are not written.  Per-particle outputs
+ * (out->force, out->cell) are in p's order; out->perm (nullable) is the map
+ * from p_out's slots to p's indices.  vel[.].w is carried unchanged, so a
+ * particle id kept there travels with its particle.  p_out: the caller's
+ * [n] T4 arrays, p_out->n == p->n, 16-byte aligned, overlapping neither
+ * each other nor p's arrays (else CG_ERR_INVALID_ARG).
+ * A DEM code keeps its particles in cell order this way (double-buffered
+ * arrays, swapped every step): the next step's binning then starts from
+ * this one with its particle i at slot i, and only the particles that
+ * changed cell are re-sorted (the per-step connectivity rebuild of
+ * Sec. 2.2); its memory accesses follow the grids.  The fields and forces
+ * are those of cg_step on the same particles, each cell summing the same
+ * particles in the same order. */
+cg_status cg_step_sorted(cg_grids* g, const cg_particles* p, const cg_particles* p_out, const void* u_fine,
+                         const cg_step_out* out, double dt);
 
 /* Learned coupling step (closure below; not in the paper).  age == 0: a
  * refresh, exactly cg_step, which also writes the fresh u_bulk and var_bulk

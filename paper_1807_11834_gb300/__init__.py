@@ -105,6 +105,8 @@ _SIGS = {
     "cg_project_bulk_to_fine": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "cg_step": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
     "cg_step_host": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut), C.c_double]),
+    "cg_step_sorted": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles), C.c_void_p,
+                                 C.POINTER(StepOut), C.c_double]),
     "cg_step_host_async": (C.c_int, [C.c_void_p, C.POINTER(Particles), C.c_void_p, C.POINTER(StepOut),
                                      C.c_double]),
     "cg_step_host_wait": (C.c_int, [C.c_void_p]),
@@ -381,6 +383,25 @@ class Grids:
         p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
         so = self._out_struct(out)
         _check(lib().cg_step(self.h, C.byref(p), _ptr(u_fine), C.byref(so), float(dt)), "cg_step")
+
+    def cg_step_sorted(self, pos_d, vel, pos_out, vel_out, u_fine, out, dt=0.0):
+        """cg_step that writes the (advanced) particles to pos_out / vel_out in
+        this step's cell order (pos_out[s] = particle out["perm"][s]); pos_d
+        and vel are not written.  Keep the particles this way from step to
+        step (swap the two pairs of arrays) and each binning starts from the
+        last one."""
+        n = pos_d.shape[0]
+        self._t(pos_d, 4 * n, name="pos_d")
+        self._t(vel, 4 * n, name="vel")
+        self._t(pos_out, 4 * n, name="pos_out")
+        self._t(vel_out, 4 * n, name="vel_out")
+        self._t(u_fine, 3 * self.n_fine, name="u_fine")
+        check_step_outputs(out, n, self.n_bulk, self.n_fine, self.dtype, True)
+        p = Particles(n, pos_d.data_ptr() if n else None, vel.data_ptr() if n else None)
+        po = Particles(n, pos_out.data_ptr() if n else None, vel_out.data_ptr() if n else None)
+        so = self._out_struct(out)
+        _check(lib().cg_step_sorted(self.h, C.byref(p), C.byref(po), _ptr(u_fine), C.byref(so), float(dt)),
+               "cg_step_sorted")
 
     def cg_step_learned(self, pos_d, vel, u_fine, out, mlp, age, dt=0.0):
         """cg_step with the learned closure: age 0 refreshes (cg_step);

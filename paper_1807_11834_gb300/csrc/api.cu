@@ -167,8 +167,14 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
+    dfree(g->rb_rec);
+    dfree(g->rb_mov);
+    dfree(g->rb_arr);
+    dfree(g->rb_small);
     g->cap = -1;
     g->n_binned = -1;
+    g->hint_n = -1;
+    g->hint_ident = nullptr;
     CG_TRY(dalloc(&g->key, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->key1, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->val1, sizeof(int32_t) * cap));
@@ -186,7 +192,18 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     // default sort (at most cap / 257 cells after a count)
     g->hist_cap = std::max<long long>(ntiles << maxbits, cap / 256 + 2);
     CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
-    g->scan_cap = (g->hist_cap + kScanItems - 1) / kScanItems + (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
+    // incremental rebinning: a record per old slot, movers up to a quarter of
+    // the particles (more fall back to the full sort), per-cell and per-block
+    // counts
+    g->rb_nblk = (cap + kRebinTile - 1) / kRebinTile;
+    g->rb_mov_cap = std::max<long long>(4096, cap / 4);
+    CG_TRY(dalloc(&g->rb_rec, sizeof(int2) * cap));
+    CG_TRY(dalloc(&g->rb_mov, sizeof(int4) * g->rb_mov_cap));
+    CG_TRY(dalloc(&g->rb_arr, sizeof(int32_t) * g->rb_mov_cap));
+    CG_TRY(dalloc(&g->rb_small, sizeof(int32_t) * rebin_small_ints(g->gd.nbulk, g->rb_nblk)));
+    const long long cells_blk = (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
+    g->scan_cap = std::max((g->hist_cap + kScanItems - 1) / kScanItems + cells_blk,
+                           2 * cells_blk + (g->rb_nblk + 1 + kScanItems - 1) / kScanItems);
     CG_TRY(dalloc(&g->scan_part, sizeof(int32_t) * g->scan_cap));
     g->cap = cap;
     return CG_OK;
@@ -227,6 +244,10 @@ static void free_all(cg_grids* g) {
     dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
+    dfree(g->rb_rec);
+    dfree(g->rb_mov);
+    dfree(g->rb_arr);
+    dfree(g->rb_small);
     dfree(g->cell_start);
     dfree(g->bulk4);
     dfree(g->eps_t);
@@ -512,8 +533,11 @@ static cg_status on_aux(cg_grids* g, Fn f) {
 // With a learned closure and no refresh the averaging is skipped: u_bulk and
 // var_bulk are inputs (the record of the last refresh) and the drag is the
 // learned kernel, which reads the fine field only for its fallback rows.
+// sorted_out (nullable): the particles leave in this binning's order in
+// these arrays (cg_step_sorted), and the next binning of them starts from it.
 static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* o,
-                           double dt, const cg_mlp* mlp = nullptr, int32_t age = 0) {
+                           double dt, const cg_mlp* mlp = nullptr, int32_t age = 0,
+                           const cg_particles* sorted_out = nullptr) {
     const long long n = p->n;
     CG_TRY(ensure_particle_capacity(g, n));
     if (o->implicit_bulk && mlp) return CG_ERR_INVALID_ARG;   // no drag factor in the learned form
@@ -554,7 +578,10 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
         CG_TRY(launch_drag_learned(g, mlp, n, p->pos_d, p->vel, o->var_bulk, u_fine, age, o->force, o->S_bulk,
                                    dt));
     else
-        CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt, o->implicit_bulk));
+        CG_TRY(launch_drag(g, n, p->pos_d, p->vel, o->force, o->S_bulk, true, dt, o->implicit_bulk,
+                           sorted_out ? sorted_out->pos_d : nullptr, sorted_out ? sorted_out->vel : nullptr));
+    // the binning above lists the sorted output's particle i at slot i
+    if (sorted_out && g->n_binned == n) g->hint_ident = sorted_out->pos_d;
     const size_t bs = (size_t)g->gd.nbulk * g->tsize, fs = (size_t)g->gd.nfine * g->tsize;
     const void* in[4] = {o->S_bulk, (const char*)o->S_bulk + bs, (const char*)o->S_bulk + 2 * bs, nullptr};
     void* out[4] = {o->S_fine, (char*)o->S_fine + fs, (char*)o->S_fine + 2 * fs, nullptr};
@@ -594,6 +621,30 @@ cg_status cg_step(cg_grids* g, const cg_particles* p, const void* u_fine, const 
     CG_TRY(check_handle(g));
     CG_TRY(check_step_args(p, u_fine, out, dt, true));
     return step_impl(g, p, u_fine, out, dt);
+}
+
+cg_status cg_step_sorted(cg_grids* g, const cg_particles* p, const cg_particles* p_out, const void* u_fine,
+                         const cg_step_out* out, double dt) {
+    CG_TRY(check_handle(g));
+    CG_TRY(check_step_args(p, u_fine, out, dt, true));
+    if (!p_out || p_out->n != p->n) return CG_ERR_INVALID_ARG;
+    const long long n = p->n;
+    if (n > 0) {
+        if (!p_out->pos_d || !p_out->vel || !aligned16(p_out->pos_d) || !aligned16(p_out->vel))
+            return CG_ERR_INVALID_ARG;
+        const size_t bytes = 4 * g->tsize * (size_t)n;
+        auto overlap = [&](const void* a, const void* b) {
+            const char *x = (const char*)a, *y = (const char*)b;
+            return x < y + bytes && y < x + bytes;
+        };
+        const void* ins[2] = {p->pos_d, p->vel};
+        const void* outs[2] = {p_out->pos_d, p_out->vel};
+        if (overlap(outs[0], outs[1])) return CG_ERR_INVALID_ARG;
+        for (const void* a : outs)
+            for (const void* b : ins)
+                if (overlap(a, b)) return CG_ERR_INVALID_ARG;
+    }
+    return step_impl(g, p, u_fine, out, dt, nullptr, 0, p_out);
 }
 
 cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out, double dt,

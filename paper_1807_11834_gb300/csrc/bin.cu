@@ -222,33 +222,6 @@ k_bin_hist(const int32_t* __restrict__ keys, long long n, int ntiles, int shift,
     bin_hist_body(keys, n, ntiles, shift, bits, hist, sh, launch_blk());
 }
 
-// Block-wide exclusive scan of one int per thread (total in `total`).
-__device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) sh_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < (int)(blockDim.x >> 5) ? sh_warp[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += y;
-        }
-        sh_warp[lane] = w;   // inclusive warp totals
-    }
-    __syncthreads();
-    int wbase = warp ? sh_warp[warp - 1] : 0;
-    total = sh_warp[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return wbase + x - v;
-}
-
 // Stable scatter of one digit pass.  offs = exclusive scan of the tile
 // histograms, digit-major ([digit][tile]).  The tile is first ranked (each
 // warp walks its 512-element slice in order with match_any and per-warp
@@ -420,22 +393,27 @@ __device__ __forceinline__ void load16(const int32_t* __restrict__ in, long long
     }
 }
 
-__device__ __forceinline__ void scan_locate(const ScanJob& j, long long id, int& which, long long& blk) {
+// Block `id` of a job is block `blk` of array `which`; `first` is the job's
+// index of that array's first block.
+__device__ __forceinline__ void scan_locate(const ScanJob& j, long long id, int& which, long long& blk,
+                                            long long& first) {
     blk = id;
     which = 0;
-    if (blk >= j.nblk[0]) {
-        blk -= j.nblk[0];
-        which = 1;
+    first = 0;
+    while (which < kScanArrays - 1 && blk >= j.nblk[which]) {
+        blk -= j.nblk[which];
+        first += j.nblk[which];
+        ++which;
     }
 }
 
-// Blocks of a job: [0, nblk[0]) over array A, then nblk[1] over array B;
-// part holds one total per block of the job.
+// Blocks of a job: [0, nblk[0]) over array 0, then nblk[1] over array 1,
+// then nblk[2] over array 2; part holds one total per block of the job.
 __device__ __forceinline__ void scan_reduce_body(const ScanJob& j, int32_t* __restrict__ part, Blk b) {
     __shared__ int shw[32];
     int which;
-    long long blk;
-    scan_locate(j, b.id, which, blk);
+    long long blk, first;
+    scan_locate(j, b.id, which, blk, first);
     long long start = blk * kScanItems + threadIdx.x * 16;
     int v[16];
     load16(j.in[which], start, j.m[which], v);
@@ -458,9 +436,8 @@ __device__ __forceinline__ void scan_down_body(const ScanJob& j, const int32_t* 
     __shared__ int shw[32];
     __shared__ int s_base;
     int which;
-    long long blk;
-    scan_locate(j, b.id, which, blk);
-    const long long first = which ? j.nblk[0] : 0;
+    long long blk, first;
+    scan_locate(j, b.id, which, blk, first);
     int acc = 0;
     for (long long i = threadIdx.x; i < blk; i += blockDim.x) acc += part[first + i];
     int tot;
@@ -490,24 +467,32 @@ __global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __r
     scan_down_body(j, part, launch_blk());
 }
 
-// Exclusive scans of one or two arrays (out may alias in).
-static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA, long long mA,
-                                 const int32_t* inB, int32_t* outB, long long mB) {
+// Exclusive scans of up to three arrays by one pair of launches (out may
+// alias in; an array with in == nullptr is skipped).
+cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m) {
     ScanJob j;
-    j.in[0] = inA;
-    j.out[0] = outA;
-    j.m[0] = mA;
-    j.in[1] = inB;
-    j.out[1] = outB;
-    j.m[1] = inB ? mB : 0;
-    j.nblk[0] = (mA + kScanItems - 1) / kScanItems;
-    j.nblk[1] = (j.m[1] + kScanItems - 1) / kScanItems;
-    const long long nblk = j.nblk[0] + j.nblk[1];
+    long long nblk = 0;
+    for (int a = 0; a < kScanArrays; ++a) {
+        const bool use = a < count && in[a];
+        j.in[a] = use ? in[a] : nullptr;
+        j.out[a] = use ? out[a] : nullptr;
+        j.m[a] = use ? m[a] : 0;
+        j.nblk[a] = (j.m[a] + kScanItems - 1) / kScanItems;
+        nblk += j.nblk[a];
+    }
     if (nblk == 0) return CG_OK;
     if (nblk > g->scan_cap) return CG_ERR_OUT_OF_RANGE;
     CG_LAUNCH(g, "bin_scan", k_scan_reduce, (unsigned)nblk, 256, 0, j, g->scan_part);
     CG_LAUNCH(g, "bin_scan", k_scan_down, (unsigned)nblk, 256, 0, j, g->scan_part);
     return CG_OK;
+}
+
+static cg_status scan_exclusive2(cg_grids* g, const int32_t* inA, int32_t* outA, long long mA,
+                                 const int32_t* inB, int32_t* outB, long long mB) {
+    const int32_t* in[2] = {inA, inB};
+    int32_t* out[2] = {outA, outB};
+    const long long m[2] = {mA, mB};
+    return scan_exclusive(g, 2, in, out, m);
 }
 
 
@@ -553,11 +538,14 @@ __device__ __forceinline__ void place_body(const int32_t* __restrict__ key, cons
     }
 }
 
+// run_if (nullable): the kernel does nothing unless *run_if is non-zero
+// (the fallback of the incremental rebinning, decided on the device).
 __global__ void __launch_bounds__(512) k_bin_place(const int32_t* __restrict__ key,
                                                    const int32_t* __restrict__ arrival,
                                                    const int32_t* __restrict__ cell_start, long long n,
-                                                   int32_t* __restrict__ tmp) {
+                                                   int32_t* __restrict__ tmp, const int32_t* __restrict__ run_if) {
     pdl_wait();
+    if (run_if && *run_if == 0) return;
     place_body(key, arrival, cell_start, n, tmp, launch_blk());
 }
 
@@ -827,8 +815,9 @@ template <typename T>
 __global__ void __launch_bounds__(kSegSortWarps * 32, 4)
 k_seg_sort(const int32_t* __restrict__ cell_start, long long nbulk, int32_t* tmp, int32_t* alt,
            int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
-           const T* __restrict__ vol, T* __restrict__ vol_sorted) {
+           const T* __restrict__ vol, T* __restrict__ vol_sorted, const int32_t* __restrict__ run_if) {
     pdl_wait();
+    if (run_if && *run_if == 0) return;
     seg_sort_body<T>(cell_start, nbulk, tmp, alt, perm, key_sorted, inv_perm, vol, vol_sorted, launch_blk());
 }
 
@@ -907,12 +896,23 @@ static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, do
     CG_LAUNCH(g, "bin_key", k_bin_key_rank<T>, (unsigned)kb, kKeyThreads, 0, pos, n, g->gd, g->key, g->cell_start,
               (T*)g->vol, g->status, eps_fill, rec_fill, eps_t_fill, g->key2);
     CG_TRY(scan_exclusive2(g, g->cell_start, g->cell_start, nbulk + 1, nullptr, nullptr, 0));
+    return launch_cellsort_tail(g, n, g->cell_start, nullptr);
+}
+
+// Placement and per-cell sort of the per-cell sort, from the cell starts cs
+// and the arrival ranks in key2 (the keys in key, the diameters in vol).
+cg_status launch_cellsort_tail(cg_grids* g, long long n, const int32_t* cs, const int32_t* run_if) {
+    const long long nbulk = g->gd.nbulk;
     const long long pb = std::min<long long>((n + 512 * kPlaceItems - 1) / (512 * kPlaceItems), (long long)g->num_sms * 4);
-    CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, g->cell_start, n, g->val1);
+    CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, cs, n, g->val1, run_if);
     const long long sb = std::min<long long>((nbulk + kGroupCells * kSegSortWarps - 1) / (kGroupCells * kSegSortWarps),
                                              (long long)g->num_sms * 4);
-    CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<T>, (unsigned)sb, kSegSortWarps * 32, 0, g->cell_start, nbulk, g->val1,
-              g->key1, g->perm, g->key_sorted, g->inv_perm, (const T*)g->vol, (T*)g->vol_sorted);
+    if (g->fp64)
+        CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<double>, (unsigned)sb, kSegSortWarps * 32, 0, cs, nbulk, g->val1,
+                  g->key1, g->perm, g->key_sorted, g->inv_perm, (const double*)g->vol, (double*)g->vol_sorted, run_if);
+    else
+        CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<float>, (unsigned)sb, kSegSortWarps * 32, 0, cs, nbulk, g->val1,
+                  g->key1, g->perm, g->key_sorted, g->inv_perm, (const float*)g->vol, (float*)g->vol_sorted, run_if);
     return CG_OK;
 }
 
@@ -1064,10 +1064,24 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
                      void* eps_t_fill) {
     CG_TRY(set_attrs());
     const long long nbulk = g->gd.nbulk;
-    // count[] lives in cell_start; the exclusive scan turns it into starts
-    CG_CUDA(cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (nbulk + 1), g->stream));
+    // a binning of the same count held by the handle is the starting point
+    // (rebin.cu), unless the descriptor asks for a digit sort
+    const bool rebin = n > 0 && g->rb_rec && g->hint_n == n && n <= g->cap &&
+                       (g->desc.sort_digits == CG_SORT_AUTO || g->desc.sort_digits == CG_SORT_CELLS);
+    const bool ident = rebin && pos_d == g->hint_ident;
+    g->hint_n = -1;
+    g->hint_ident = nullptr;
     g->n_binned = -1;
     g->vol_valid = false;
+    if (rebin) {
+        CG_TRY(launch_rebin(g, n, pos_d, ident, eps_fill, rec_fill, eps_t_fill));
+        g->n_binned = n;
+        g->vol_valid = true;
+        g->hint_n = n;
+        return CG_OK;
+    }
+    // count[] lives in cell_start; the exclusive scan turns it into starts
+    CG_CUDA(cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (nbulk + 1), g->stream));
     if (n == 0) {
         g->n_binned = 0;
         g->vol_valid = true;
@@ -1084,6 +1098,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
                                    (float*)eps_t_fill));
         g->n_binned = n;
         g->vol_valid = true;
+        g->hint_n = n;
         return CG_OK;
     }
     for (int p = 0; p < g->npasses; ++p)
@@ -1097,6 +1112,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
                                  (float*)eps_t_fill));
     g->n_binned = n;
     g->vol_valid = true;
+    g->hint_n = n;
     return CG_OK;
 }
 

@@ -179,6 +179,17 @@ struct cg_grids {
     void* vol_sorted = nullptr;    // [cap] T particle diameter, sorted order
     void* Fs = nullptr;            // [cap] T4 drag force, sorted order
     bool vol_valid = false;        // vol_sorted matches the binned positions
+    // incremental rebinning (rebin.cu): a binning of hint_n particles held in
+    // perm / key_sorted / cell_start is where the next binning of the same
+    // count starts; hint_ident is the particle array the last sorted step
+    // wrote in that binning's order (so its particle i sat at old slot i)
+    long long hint_n = -1;
+    const void* hint_ident = nullptr;
+    int2* rb_rec = nullptr;        // [cap] per old slot: (id, new cell; its complement for a mover)
+    int4* rb_mov = nullptr;        // [rb_mov_cap] movers: (id, new cell, arrival rank, unused)
+    int32_t* rb_arr = nullptr;     // [rb_mov_cap] arrivals, grouped by cell
+    int32_t* rb_small = nullptr;   // new counts / starts, arrivals, departures per cell; block departures; counters
+    long long rb_mov_cap = 0, rb_nblk = 0;
     int32_t* hist = nullptr;       // [2^digit * ntiles]
     int32_t* scan_part = nullptr;  // scan block partials
     long long hist_cap = 0, scan_cap = 0;
@@ -271,13 +282,14 @@ void prof_end(cg_grids* g, int slot, int ev);
 // ----------------------------------------------------------------------
 // Step launchers (one .cu each)
 // ----------------------------------------------------------------------
-// Up to two independent arrays are scanned by one pair of launches: blocks
-// [0, nA) cover array A, blocks [nA, nA + nB) array B.
+// Up to three independent arrays are scanned by one pair of launches: blocks
+// [0, n0) cover array 0, blocks [n0, n0 + n1) array 1, and so on.
+constexpr int kScanArrays = 3;
 struct ScanJob {
-    const int32_t* in[2];
-    int32_t* out[2];
-    long long m[2];
-    long long nblk[2];
+    const int32_t* in[kScanArrays] = {};
+    int32_t* out[kScanArrays] = {};
+    long long m[kScanArrays] = {};
+    long long nblk[kScanArrays] = {};
 };
 
 // Column map of the conservation-sum reduction: sum k merges cnt[k]
@@ -288,6 +300,22 @@ struct SumsMap {
 };
 
 cg_status ensure_particle_capacity(cg_grids* g, long long n);
+// Exclusive scans of up to kScanArrays int32 arrays (in[a] nullable: skipped).
+cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m);
+// Placement and per-cell sort of the per-cell binning sort from the cell
+// starts cs; with run_if set they do nothing unless *run_if != 0.
+cg_status launch_cellsort_tail(cg_grids* g, long long n, const int32_t* cs, const int32_t* run_if);
+// Incremental rebinning (rebin.cu).
+constexpr int kRebinThreads = 256;
+constexpr int kRebinItems = 4;
+constexpr int kRebinTile = kRebinThreads * kRebinItems;   // old slots per block
+constexpr int kRebinMaxArrivals = 256;                     // arrivals per cell before the fallback
+constexpr int kRebinCounters = 8;
+inline long long rebin_small_ints(long long nbulk, long long nblk) { return 3 * (nbulk + 1) + (nblk + 1) + kRebinCounters; }
+// The binning of n particles from the handle's last binning of n; ident:
+// the particles are that binning's sorted output (particle i at old slot i).
+cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,
+                       void* eps_t_fill);
 cg_status ensure_partials(cg_grids* g, long long n);
 
 // eps_fill (nullable): also set this [n_b] porosity to 1 (when n > 0), and
@@ -308,8 +336,11 @@ cg_status launch_deposit_momentum(cg_grids* g, long long n, const void* force_so
 // rec (nullable): also write the mean velocity into the drag record's u part.
 cg_status launch_average(cg_grids* g, const void* u_fine, void* u_bulk, void* var_bulk, void* rec = nullptr);
 cg_status launch_pack(cg_grids* g, const double* eps, const void* u_bulk, bool want_eps_t);
+// pos_out, vel_out (nullable, needs S_bulk): the particles, advanced when
+// dt > 0, are written to these arrays in the order of the binning.
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
-                      bool sums, double dt, void* coef_bulk = nullptr);
+                      bool sums, double dt, void* coef_bulk = nullptr, void* pos_out = nullptr,
+                      void* vel_out = nullptr);
 // Learned drag (FP32 only): bulk4 must hold (phi of this step, stale u).
 cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* pos_d, void* vel,
                               const void* var_stale, const void* u_fine, int32_t age, void* force, void* S_bulk,
@@ -437,6 +468,34 @@ __device__ __forceinline__ void block_sums(CSum<T> (&v)[K], T* __restrict__ part
         dst[0] = a.s;
         dst[1] = a.c;
     }
+}
+
+// Block-wide exclusive scan of one int per thread (total in `total`); every
+// thread of the block must call it.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) sh_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        sh_warp[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    int wbase = warp ? sh_warp[warp - 1] : 0;
+    total = sh_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return wbase + x - v;
 }
 
 // Length of the run of equal values starting at this lane, or 0 if the lane

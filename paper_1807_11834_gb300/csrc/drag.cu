@@ -44,12 +44,16 @@ __device__ __forceinline__ V4<T> ld4_plain(const T* p, long long i) {
 // ----------------------------------------------------------------------
 // Bs (nullable): the semi-implicit record (beta, beta u_p) of each particle,
 // written to its sorted slot beside the force record.
+// pos_out, vel_out (nullable, with Fs): the particle records, advanced when
+// EULER, are written to their sorted slot of these arrays instead of in
+// place (the sorted step: the particles leave in this binning's order).
 template <typename T, bool EULER, bool PREFETCH = true>
 __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
                                           const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
                                           const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part,
                                           long long pstride, int do_sums, unsigned long long* __restrict__ status,
-                                          Blk b, T* __restrict__ Bs = nullptr) {
+                                          Blk b, T* __restrict__ Bs = nullptr, T* __restrict__ pos_out = nullptr,
+                                          T* __restrict__ vel_out = nullptr) {
     T lane_sums[kDragSums];
 #pragma unroll
     for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
@@ -113,11 +117,19 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
                 else if (xa > hi) { xa = T(2) * hi - xa; un[a] = -un[a]; }
                 xn[a] = xa;
             }
-            st4(pos, p, xn[0], xn[1], xn[2], d);
-            st4(vel, p, un[0], un[1], un[2], v.w);
+            if (pos_out) {
+                st4(pos_out, slot, xn[0], xn[1], xn[2], d);
+                st4(vel_out, slot, un[0], un[1], un[2], v.w);
+            } else {
+                st4(pos, p, xn[0], xn[1], xn[2], d);
+                st4(vel, p, un[0], un[1], un[2], v.w);
+            }
             ux = un[0];
             uy = un[1];
             uz = un[2];
+        } else if (pos_out) {
+            st4(pos_out, slot, x.x, x.y, x.z, x.w);
+            st4(vel_out, slot, v.x, v.y, v.z, v.w);
         }
         lane_sums[0] += vp;
         lane_sums[1] += fx;
@@ -149,10 +161,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
        T* __restrict__ F, T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt,
        T* __restrict__ part, long long pstride, int do_sums, unsigned long long* __restrict__ status,
-       T* __restrict__ Bs) {
+       T* __restrict__ Bs, T* __restrict__ pos_out, T* __restrict__ vel_out) {
     pdl_wait();
     drag_body<T, EULER>(pos, vel, n, g, P, bulk4, F, Fs, inv_perm, dt, part, pstride, do_sums, status,
-                        launch_blk(), Bs);
+                        launch_blk(), Bs, pos_out, vel_out);
 }
 
 // Batched drag with the fused sorted-order force record (FP32 instances).
@@ -182,7 +194,7 @@ int batch_drag_occupancy() {
 }
 
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
-                      bool sums, double dt, void* coef_bulk) {
+                      bool sums, double dt, void* coef_bulk, void* pos_out, void* vel_out) {
     const bool euler = dt > 0.0;
     void* part = part_ptr(g, PS_DRAG);
     // exactly the resident CTAs (the launch bounds' minimum per SM): a grid-stride
@@ -191,6 +203,7 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
     const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * per_sm));
     g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
     void* Fs = S_bulk ? g->Fs : nullptr;
+    if (pos_out && !Fs) return CG_ERR_INVALID_ARG;   // the sorted slots come with the fused reaction
     void* Bs = nullptr;
     if (coef_bulk && n > 0) {
         // sized by the step before its first launch
@@ -201,7 +214,7 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
 #define CG_DRAGP(T, E)                                                                                      \
     CG_LAUNCH(g, "drag", (k_drag<T, E>), nblk, 256, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd),          \
               (const T*)g->bulk4, (T*)force, (T*)Fs, g->inv_perm, (T)dt, (T*)part, (long long)nblk, (int)sums,   \
-              g->status, (T*)Bs)
+              g->status, (T*)Bs, (T*)pos_out, (T*)vel_out)
         if (g->fp64) {
             if (euler) CG_DRAGP(double, true);
             else CG_DRAGP(double, false);

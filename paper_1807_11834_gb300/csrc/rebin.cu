@@ -1,0 +1,399 @@
+// rebin.cu -- incremental rebinning: the per-step particle-to-cell
+// connectivity rebuild of Sec. 2.2 of arXiv 1807.11834, started from the
+// binning of the previous step.
+//
+// From one coupling step to the next a particle moves a small fraction of a
+// bulk cell, so most particles keep their cell.  The handle's last binning
+// of the same particle count (perm_old, key_sorted_old, cell_start_old: the
+// stable order, ids ascending within each cell) is therefore nearly the
+// new one.  Call a particle whose cell is unchanged a stayer and one whose
+// cell changed a mover.  Stayers keep their relative order (their old order
+// is sorted by (cell, id) and their cells did not change), so with
+//   D(s)   = movers at old slots before s (departures),
+//   A(c)   = movers arriving in cells before c,
+//   a_c(i) = movers arriving in c with an id below i,
+// the new slot of the stayer at old slot s, of cell c and id i, is
+//   s - D(s) + A(c) + a_c(i),
+// and the new slot of a mover i arriving in c is
+//   start_new(c) + (stayers of c with an id below i) + a_c(i),
+// where start_new is the exclusive scan of the new counts
+// count_old(c) - departures(c) + arrivals(c).  This holds for any new
+// positions and any valid binning of the same count: the old order only
+// decides how many particles are movers, never the result, which is the
+// stable order of the new cells exactly as a full sort gives it.
+//
+// Old slot s holds particle perm_old[s] when the caller kept its particle
+// order, or particle s when the particles are the sorted output of the last
+// step (cg_step_sorted; the identity hint).  When more than a quarter of the
+// particles moved, or a cell receives more than kRebinMaxArrivals movers,
+// the device falls back to the per-cell sort: both paths are launched and
+// each kernel checks a device flag, so a captured CUDA graph takes the
+// right path on every replay.
+#include <algorithm>
+
+#include "cg_internal.cuh"
+
+namespace cg {
+
+namespace {
+
+enum { RB_NMOV = 0, RB_FALLBACK = 1 };
+
+struct RebinPtrs {
+    int32_t* cnt;       // [n_b + 1] new counts, then (scanned in place) new starts
+    int32_t* arr;       // [n_b + 1] arrivals per cell, then their starts
+    int32_t* dep;       // [n_b + 1] departures per cell
+    int32_t* blk;       // [nblk + 1] departures per block of old slots, then their starts
+    int32_t* ctr;       // [kRebinCounters] movers, fallback flag
+};
+
+RebinPtrs rebin_ptrs(cg_grids* g) {
+    const long long nb1 = g->gd.nbulk + 1;
+    RebinPtrs r;
+    r.cnt = g->rb_small;
+    r.arr = r.cnt + nb1;
+    r.dep = r.arr + nb1;
+    r.blk = r.dep + nb1;
+    r.ctr = r.blk + g->rb_nblk + 1;
+    return r;
+}
+
+// Set every cell's porosity to 1 (and that of the drag record and of its
+// path-precision copy); the porosity deposit overwrites the occupied cells.
+template <typename T>
+__device__ __forceinline__ void eps_fill_cells(long long nbulk, double* __restrict__ eps_fill,
+                                               T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
+    if (!eps_fill) return;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nbulk;
+         c += (long long)gridDim.x * blockDim.x) {
+        eps_fill[c] = 1.0;
+        if (rec_fill) rec_fill[4 * c] = T(1);
+        if (eps_t_fill) eps_t_fill[c] = T(1);
+    }
+}
+
+__device__ __forceinline__ void add_status_counts(unsigned long long* st, int outside, int nonfin) {
+    if (outside) {
+        atomicAdd(&st[ST_OUTSIDE], (unsigned long long)outside);
+        atomicOr(&st[ST_FLAGS], (unsigned long long)CG_FLAG_OUTSIDE);
+    }
+    if (nonfin) {
+        atomicAdd(&st[ST_NONFINITE], (unsigned long long)nonfin);
+        atomicOr(&st[ST_FLAGS], (unsigned long long)CG_FLAG_NONFINITE);
+    }
+}
+
+// Cell and diameter of particle p (caller order), with the status counts.
+template <typename T>
+__device__ __forceinline__ int key_of(const T* __restrict__ pos, long long p, const GridDev& g,
+                                      int32_t* __restrict__ key, T* __restrict__ vol, int& n_out, int& n_nf) {
+    const V4<T> v = ld4(pos, p);
+    int outside = 0;
+    if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
+    const int c = cell_of(v, g, outside);
+    n_out += outside;
+    key[p] = c;
+    vol[p] = v.w;   // the diameter: the porosity forms the volume as an exact pair
+    return c;
+}
+
+__device__ __forceinline__ void flush_status(unsigned long long* st, int n_out, int n_nf) {
+    n_out = __reduce_add_sync(0xffffffffu, n_out);
+    n_nf = __reduce_add_sync(0xffffffffu, n_nf);
+    if ((threadIdx.x & 31) == 0 && (n_out | n_nf)) add_status_counts(st, n_out, n_nf);
+}
+
+}  // namespace
+
+// Cells and diameters in the caller's order (the particles kept their order:
+// old slot s holds perm_old[s]).
+template <typename T>
+__global__ void __launch_bounds__(kRebinThreads)
+k_rebin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key, T* __restrict__ vol,
+            unsigned long long* __restrict__ status, double* __restrict__ eps_fill, T* __restrict__ rec_fill,
+            T* __restrict__ eps_t_fill) {
+    pdl_wait();
+    int n_out = 0, n_nf = 0;
+    const long long base = (long long)blockIdx.x * kRebinTile;
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long p = base + k * kRebinThreads + threadIdx.x;
+        if (p < n) key_of(pos, p, g, key, vol, n_out, n_nf);
+    }
+    flush_status(status, n_out, n_nf);
+    eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
+}
+
+// Mark the movers, over the old slots: the record (id, new cell) of every
+// old slot, with the new cell complemented for a mover; per mover one
+// departure from its old cell, one arrival (and its rank) in its new cell
+// and an entry of the mover list; the departures of each block of old slots.
+// IDENT: old slot s holds particle s, whose cell is formed here.
+template <typename T, bool IDENT>
+__global__ void __launch_bounds__(kRebinThreads)
+k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* __restrict__ perm_old,
+             const int32_t* __restrict__ ks_old, int32_t* __restrict__ key, T* __restrict__ vol,
+             int2* __restrict__ rec, int32_t* __restrict__ arr, int32_t* __restrict__ dep, int4* __restrict__ mov,
+             long long mov_cap, int32_t* __restrict__ blk_dep, int32_t* __restrict__ ctr,
+             unsigned long long* __restrict__ status, double* __restrict__ eps_fill, T* __restrict__ rec_fill,
+             T* __restrict__ eps_t_fill) {
+    pdl_wait();
+    __shared__ int s_dep[kRebinThreads / 32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kRebinTile;
+    int n_out = 0, n_nf = 0, ndep = 0;
+    int idk[kRebinItems], cnk[kRebinItems], cok[kRebinItems];
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        idk[k] = -1;
+        cnk[k] = cok[k] = 0;
+        if (s < n) {
+            idk[k] = IDENT ? (int)s : __ldg(perm_old + s);
+            cok[k] = __ldg(ks_old + s);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        if (s < n) cnk[k] = IDENT ? key_of(pos, s, g, key, vol, n_out, n_nf) : __ldg(key + idk[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        const bool valid = s < n;
+        const bool moved = valid && cnk[k] != cok[k];
+        const unsigned mb = __ballot_sync(full, moved);
+        if (mb) {
+            int first = 0;
+            if (lane == __ffs(mb) - 1) first = atomicAdd(&ctr[RB_NMOV], __popc(mb));
+            first = __shfl_sync(full, first, __ffs(mb) - 1);
+            if (moved) {
+                const long long idx = (long long)first + __popc(mb & lanemask_lt());
+                atomicAdd(&dep[cok[k]], 1);
+                const int r = atomicAdd(&arr[cnk[k]], 1);
+                if (idx < mov_cap && r < kRebinMaxArrivals) mov[idx] = make_int4(idk[k], cnk[k], r, 0);
+                else ctr[RB_FALLBACK] = 1;
+            }
+        }
+        if (valid) rec[s] = make_int2(idk[k], moved ? ~cnk[k] : cnk[k]);
+        ndep += moved;
+    }
+    ndep = __reduce_add_sync(full, ndep);
+    if (lane == 0) s_dep[warp] = ndep;
+    if (IDENT) flush_status(status, n_out, n_nf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kRebinThreads / 32; ++w) t += s_dep[w];
+        blk_dep[blockIdx.x] = t;
+    }
+    if (IDENT) eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
+}
+
+// New count of every cell (the fallback counts into cnt itself).
+__global__ void __launch_bounds__(256)
+k_rebin_cells(const int32_t* __restrict__ cs_old, long long nbulk, const int32_t* __restrict__ dep,
+              const int32_t* __restrict__ arr, int32_t* __restrict__ cnt, const int32_t* __restrict__ ctr) {
+    pdl_wait();
+    if (ctr[RB_FALLBACK]) return;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nbulk;
+         c += (long long)gridDim.x * blockDim.x)
+        cnt[c] = __ldg(cs_old + c + 1) - __ldg(cs_old + c) - __ldg(dep + c) + __ldg(arr + c);
+}
+
+// Fallback: per-cell counts and arrival ranks of the per-cell sort, from the
+// cells already formed (consecutive lanes on consecutive particles, one
+// atomic per run of equal cells).
+__global__ void __launch_bounds__(kRebinThreads)
+k_rebin_rank(const int32_t* __restrict__ key, long long n, int32_t* __restrict__ cnt,
+             int32_t* __restrict__ arrival, const int32_t* __restrict__ ctr) {
+    pdl_wait();
+    if (!ctr[RB_FALLBACK]) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long base = (long long)blockIdx.x * kRebinTile;
+    int ck[kRebinItems], lk[kRebinItems], old[kRebinItems];
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long p = base + k * kRebinThreads + threadIdx.x;
+        const bool valid = p < n;
+        ck[k] = valid ? __ldg(key + p) : -1;
+        lk[k] = run_head_length(ck[k], valid);
+    }
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) old[k] = lk[k] ? atomicAdd(&cnt[ck[k]], lk[k]) : 0;
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long p = base + k * kRebinThreads + threadIdx.x;
+        const unsigned heads = __ballot_sync(full, lk[k] != 0);
+        const int head = 31 - __clz(heads & ((2u << lane) - 1u));
+        const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
+        if (p < n) arrival[p] = o + lane - head;
+    }
+}
+
+// Each mover into the arrival list of its new cell, at its arrival rank.
+__global__ void __launch_bounds__(256)
+k_rebin_place(const int4* __restrict__ mov, const int32_t* __restrict__ arr_start, int32_t* __restrict__ arr_list,
+              const int32_t* __restrict__ ctr) {
+    pdl_wait();
+    if (ctr[RB_FALLBACK]) return;
+    const long long nm = ctr[RB_NMOV];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
+        const int4 m = mov[i];
+        arr_list[__ldg(arr_start + m.y) + m.z] = m.x;
+    }
+}
+
+// Arrivals in the list [a0, a1) with an id below i.
+__device__ __forceinline__ int arrivals_below(const int32_t* __restrict__ arr_list, int a0, int a1, int i) {
+    int a = 0;
+    for (int q = a0; q < a1; ++q) a += __ldg(arr_list + q) < i;
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void emit(long long n, long long ns, int i, int c, int32_t* __restrict__ perm,
+                                     int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+                                     const T* __restrict__ vol, T* __restrict__ vol_sorted) {
+    if ((unsigned long long)ns >= (unsigned long long)n) return;   // never for a valid binning
+    perm[ns] = i;
+    key_sorted[ns] = c;
+    inv_perm[i] = (int)ns;
+    vol_sorted[ns] = __ldg(vol + i);
+}
+
+// Stayers: four consecutive old slots per thread, the block's departures
+// before each slot by a block scan, the blocks' departure starts from the
+// scan of the block totals.
+template <typename T>
+__global__ void __launch_bounds__(kRebinThreads)
+k_rebin_stay(const int2* __restrict__ rec, long long n, const int32_t* __restrict__ blk_start,
+             const int32_t* __restrict__ arr_start, const int32_t* __restrict__ arr_list, const T* __restrict__ vol,
+             int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+             T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
+    pdl_wait();
+    if (ctr[RB_FALLBACK]) return;
+    __shared__ int shw[32];
+    const long long s0 = (long long)blockIdx.x * kRebinTile + threadIdx.x * kRebinItems;
+    int2 r[kRebinItems];
+    if (s0 + kRebinItems <= n) {
+        const int4* q = reinterpret_cast<const int4*>(rec + s0);   // s0 is a multiple of 4: 32-byte aligned
+        const int4 a = __ldg(q), b = __ldg(q + 1);
+        r[0] = make_int2(a.x, a.y);
+        r[1] = make_int2(a.z, a.w);
+        r[2] = make_int2(b.x, b.y);
+        r[3] = make_int2(b.z, b.w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRebinItems; ++k) r[k] = s0 + k < n ? rec[s0 + k] : make_int2(0, -1);
+    }
+    int nd = 0;
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) nd += (s0 + k < n && r[k].y < 0);
+    int total;
+    int D = block_exclusive_scan(nd, shw, total) + __ldg(blk_start + blockIdx.x);
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = s0 + k;
+        if (s >= n) break;
+        if (r[k].y < 0) {
+            ++D;
+            continue;
+        }
+        const int c = r[k].y, i = r[k].x;
+        const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
+        const long long ns = s - D + a0 + (a1 > a0 ? arrivals_below(arr_list, a0, a1, i) : 0);
+        emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
+    }
+}
+
+// Movers: the stayers of the new cell with an id below the mover's (a binary
+// search over the old segment, whose ids ascend, then a count of the
+// stayers before that point) and the arrivals with an id below it.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rebin_movers(const int4* __restrict__ mov, const int2* __restrict__ rec, long long n,
+               const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
+               const int32_t* __restrict__ arr_start, const int32_t* __restrict__ arr_list, const T* __restrict__ vol,
+               int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+               T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
+    pdl_wait();
+    if (ctr[RB_FALLBACK]) return;
+    const long long nm = ctr[RB_NMOV];
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += (long long)gridDim.x * blockDim.x) {
+        const int4 m = mov[j];
+        const int i = m.x, c = m.y;
+        const int o0 = __ldg(cs_old + c), o1 = __ldg(cs_old + c + 1);
+        int lo = o0, hi = o1;
+        while (lo < hi) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if (__ldg(&rec[mid].x) < i) lo = mid + 1;
+            else hi = mid;
+        }
+        int stay = 0;
+        for (int q = o0; q < lo; ++q) stay += __ldg(&rec[q].y) >= 0;
+        const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
+        const long long ns = (long long)__ldg(cs_new + c) + stay + arrivals_below(arr_list, a0, a1, i);
+        emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
+    }
+}
+
+template <typename T>
+static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, double* eps_fill, T* rec_fill,
+                            T* eps_t_fill) {
+    const long long nbulk = g->gd.nbulk;
+    const RebinPtrs R = rebin_ptrs(g);
+    const long long nblk = (n + kRebinTile - 1) / kRebinTile;
+    if (nblk > g->rb_nblk) return CG_ERR_OUT_OF_RANGE;
+    CG_CUDA(cudaMemsetAsync(g->rb_small, 0, sizeof(int32_t) * rebin_small_ints(nbulk, g->rb_nblk), g->stream));
+    if (!ident)
+        CG_LAUNCH(g, "rebin_key", k_rebin_key<T>, (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd, g->key, (T*)g->vol,
+                  g->status, eps_fill, rec_fill, eps_t_fill);
+    if (ident)
+        CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, true>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
+                  (const int32_t*)nullptr, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rec, R.arr, R.dep,
+                  g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, eps_fill, rec_fill, eps_t_fill);
+    else
+        CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, false>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
+                  (const int32_t*)g->perm, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rec, R.arr, R.dep,
+                  g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr, (T*)nullptr);
+    const unsigned cgrid = (unsigned)std::min<long long>((nbulk + 255) / 256, (long long)g->num_sms * 8);
+    CG_LAUNCH(g, "rebin_cells", k_rebin_cells, cgrid, 256, 0, (const int32_t*)g->cell_start, nbulk,
+              (const int32_t*)R.dep, (const int32_t*)R.arr, R.cnt, (const int32_t*)R.ctr);
+    CG_LAUNCH(g, "rebin_rank", k_rebin_rank, (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->key, n, R.cnt,
+              g->key2, (const int32_t*)R.ctr);
+    {
+        const int32_t* in[3] = {R.cnt, R.arr, R.blk};
+        int32_t* out[3] = {R.cnt, R.arr, R.blk};
+        const long long m[3] = {nbulk + 1, nbulk + 1, nblk + 1};
+        CG_TRY(scan_exclusive(g, 3, in, out, m));
+    }
+    const unsigned mgrid = (unsigned)std::max<long long>(1, std::min<long long>((g->rb_mov_cap + 255) / 256,
+                                                                              (long long)g->num_sms * 8));
+    CG_LAUNCH(g, "rebin_place", k_rebin_place, mgrid, 256, 0, (const int4*)g->rb_mov, (const int32_t*)R.arr,
+              g->rb_arr, (const int32_t*)R.ctr);
+    CG_LAUNCH(g, "rebin_stay", k_rebin_stay<T>, (unsigned)nblk, kRebinThreads, 0, (const int2*)g->rb_rec, n,
+              (const int32_t*)R.blk, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm,
+              g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);
+    CG_LAUNCH(g, "rebin_movers", k_rebin_movers<T>, mgrid, 256, 0, (const int4*)g->rb_mov, (const int2*)g->rb_rec,
+              n, (const int32_t*)g->cell_start, (const int32_t*)R.cnt, (const int32_t*)R.arr,
+              (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted,
+              (const int32_t*)R.ctr);
+    // fallback: placement and per-cell sort from the scanned counts
+    CG_TRY(launch_cellsort_tail(g, n, R.cnt, R.ctr + RB_FALLBACK));
+    CG_CUDA(cudaMemcpyAsync(g->cell_start, R.cnt, sizeof(int32_t) * (nbulk + 1), cudaMemcpyDeviceToDevice, g->stream));
+    return CG_OK;
+}
+
+cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,
+                       void* eps_t_fill) {
+    if (g->fp64) return rebin_impl<double>(g, n, (const double*)pos_d, ident, eps_fill, (double*)rec_fill,
+                                           (double*)eps_t_fill);
+    return rebin_impl<float>(g, n, (const float*)pos_d, ident, eps_fill, (float*)rec_fill, (float*)eps_t_fill);
+}
+
+}  // namespace cg
