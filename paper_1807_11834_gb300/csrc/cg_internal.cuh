@@ -311,7 +311,12 @@ constexpr int kRebinItems = 4;
 constexpr int kRebinTile = kRebinThreads * kRebinItems;   // old slots per block
 constexpr int kRebinMaxArrivals = 256;                     // arrivals per cell before the fallback
 constexpr int kRebinCounters = 8;
-inline long long rebin_small_ints(long long nbulk, long long nblk) { return 3 * (nbulk + 1) + (nblk + 1) + kRebinCounters; }
+// The small rebinning arrays (three of n_b + 1 ints, one of nblk + 1, the
+// counters) each start on a 256-byte boundary: the scan reads them as int4.
+inline long long rebin_pad(long long ints) { return (ints + 63) / 64 * 64; }
+inline long long rebin_small_ints(long long nbulk, long long nblk) {
+    return 3 * rebin_pad(nbulk + 1) + rebin_pad(nblk + 1) + kRebinCounters;
+}
 // The binning of n particles from the handle's last binning of n; ident:
 // the particles are that binning's sorted output (particle i at old slot i).
 cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,

@@ -48,13 +48,13 @@ struct RebinPtrs {
 };
 
 RebinPtrs rebin_ptrs(cg_grids* g) {
-    const long long nb1 = g->gd.nbulk + 1;
+    const long long nb1 = rebin_pad(g->gd.nbulk + 1);
     RebinPtrs r;
     r.cnt = g->rb_small;
     r.arr = r.cnt + nb1;
     r.dep = r.arr + nb1;
     r.blk = r.dep + nb1;
-    r.ctr = r.blk + g->rb_nblk + 1;
+    r.ctr = r.blk + rebin_pad(g->rb_nblk + 1);
     return r;
 }
 
