@@ -72,6 +72,31 @@ def assert_close_interp(name, got, ref, ref_abs, tol, mask=None, report=None):
     return float(widened.max())
 
 
+def assert_close_slip(name, got, ref, slip, u_p, tol, report=None):
+    """Drag forces ([3][n]) of particles that move: F = beta s with the slip
+    s = u_f - u_p, and where u_p is close to u_f the subtraction cancels, so
+    an FP32 rounding of the interpolated u_f is relative to |u_f| + |u_p|,
+    not to |s|.  The error of each particle is taken within tol of
+    max(|F|, |F| (|s| + 2 |u_p|) / |s|, 1e-3 max|F|) (|s| + 2 |u_p| bounds
+    |u_f| + |u_p|); report (nullable dict) gets the maxima of this metric and
+    of the plain one, and the particles that pass only under this one."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    num = np.sqrt(((got - ref) ** 2).sum(axis=0))
+    fm = np.sqrt((ref ** 2).sum(axis=0))
+    slip = np.asarray(slip, np.float64)
+    up = np.sqrt((np.asarray(u_p, np.float64) ** 2).sum(axis=1))
+    amp = np.where(slip > 0, (slip + 2 * up) / np.maximum(slip, 1e-300), 1.0)
+    floor = max(1e-3 * fm.max(), 1e-300)
+    plain = num / np.maximum(fm, floor)
+    terms = num / np.maximum(fm * amp, floor)
+    if report is not None:
+        report[name] = {"max_terms": float(terms.max()), "max_plain": float(plain.max()),
+                        "particles_only_terms": int(((plain > tol) & (terms <= tol)).sum())}
+    assert terms.max() <= tol, f"{name}: max rel err {terms.max():.3e} > {tol:.1e}"
+    return float(terms.max())
+
+
 def to_dev(a, dev="cuda:0"):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)

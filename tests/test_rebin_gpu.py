@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import TOL_FP32, assert_close, inputs, to_dev, to_np
+from parity_util import TOL_FP32, assert_close, assert_close_slip, inputs, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -200,9 +200,15 @@ def test_full_clustered_bed_sorted_steps_bit_exact(cuda_lib):
         _assert_bins_equal(out, _scratch_bins(cg, w.desc, pi), f"step {step}")
         if step in (0, 1, 11):
             _assert_oracle_bins(w, pi, out, f"step {step}")
-    ref = oracle.step(w.desc, to_np(state[0]), to_np(state[1]), w.u_fine, dt=w.dt)
-    assert_close("force", to_np(out["force"]), ref["force"], TOL_FP32, vec=True)
+    p11, v11 = to_np(state[0]), to_np(state[1])
+    ref = oracle.step(w.desc, p11, v11, w.u_fine, dt=w.dt)
+    # after 11 steps the particles move with the fluid: the force is judged
+    # against the terms of its slip (FP32 rounding of u_f cancels in u_f - u_p)
+    _, slip = oracle.particle_state(w.desc, p11, v11, ref["eps_bulk"], ref["u_bulk"])
+    report = {}
+    assert_close_slip("force", to_np(out["force"]), ref["force"], slip, v11[:, :3], TOL_FP32, report)
     assert_close("S_bulk", to_np(out["S_bulk"]), ref["S_bulk"], TOL_FP32, vec=True)
+    print("clustered bed after 11 sorted steps:", report)
     perm = to_np(out["perm"])
     got_pos = to_np(bufs[0][0]).astype(np.float64)
     assert np.max(np.abs(got_pos[:, :3] - ref["pos_d"][perm, :3])) <= 2e-6
