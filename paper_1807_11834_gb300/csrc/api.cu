@@ -167,7 +167,8 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
-    dfree(g->rb_rec);
+    dfree(g->rb_rid);
+    dfree(g->rb_rkn);
     dfree(g->rb_mov);
     dfree(g->rb_arr);
     dfree(g->rb_small);
@@ -197,7 +198,8 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     // counts
     g->rb_nblk = (cap + kRebinTile - 1) / kRebinTile;
     g->rb_mov_cap = std::max<long long>(4096, cap / 4);
-    CG_TRY(dalloc(&g->rb_rec, sizeof(int2) * cap));
+    CG_TRY(dalloc(&g->rb_rid, sizeof(int32_t) * cap));
+    CG_TRY(dalloc(&g->rb_rkn, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->rb_mov, sizeof(int4) * g->rb_mov_cap));
     CG_TRY(dalloc(&g->rb_arr, sizeof(int32_t) * g->rb_mov_cap));
     CG_TRY(dalloc(&g->rb_small, sizeof(int32_t) * rebin_small_ints(g->gd.nbulk, g->rb_nblk)));
@@ -244,7 +246,8 @@ static void free_all(cg_grids* g) {
     dfree(g->Fs);
     dfree(g->hist);
     dfree(g->scan_part);
-    dfree(g->rb_rec);
+    dfree(g->rb_rid);
+    dfree(g->rb_rkn);
     dfree(g->rb_mov);
     dfree(g->rb_arr);
     dfree(g->rb_small);

@@ -1066,7 +1066,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     const long long nbulk = g->gd.nbulk;
     // a binning of the same count held by the handle is the starting point
     // (rebin.cu), unless the descriptor asks for a digit sort
-    const bool rebin = n > 0 && g->rb_rec && g->hint_n == n && n <= g->cap &&
+    const bool rebin = n > 0 && g->rb_rkn && g->hint_n == n && n <= g->cap &&
                        (g->desc.sort_digits == CG_SORT_AUTO || g->desc.sort_digits == CG_SORT_CELLS);
     const bool ident = rebin && pos_d == g->hint_ident;
     g->hint_n = -1;

@@ -185,7 +185,8 @@ struct cg_grids {
     // wrote in that binning's order (so its particle i sat at old slot i)
     long long hint_n = -1;
     const void* hint_ident = nullptr;
-    int2* rb_rec = nullptr;        // [cap] per old slot: (id, new cell; its complement for a mover)
+    int32_t* rb_rid = nullptr;     // [cap] per old slot: its particle id (the caller's order kept)
+    int32_t* rb_rkn = nullptr;     // [cap] per old slot: the new cell, complemented for a mover
     int4* rb_mov = nullptr;        // [rb_mov_cap] movers: (id, new cell, arrival rank, unused)
     int32_t* rb_arr = nullptr;     // [rb_mov_cap] arrivals, grouped by cell
     int32_t* rb_small = nullptr;   // new counts / starts, arrivals, departures per cell; block departures; counters

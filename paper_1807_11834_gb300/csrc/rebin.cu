@@ -124,25 +124,30 @@ k_rebin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restri
     eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
 }
 
-// Mark the movers, over the old slots: the record (id, new cell) of every
-// old slot, with the new cell complemented for a mover; per mover one
-// departure from its old cell, one arrival (and its rank) in its new cell
-// and an entry of the mover list; the departures of each block of old slots.
-// IDENT: old slot s holds particle s, whose cell is formed here.
+// Mark the movers, over the old slots (slot base + k * threads + t of
+// thread t, so every load and store of a row is coalesced): the new cell of
+// every old slot, complemented for a mover (rkn), and the old id (rid, only
+// when the particles kept the caller's order); per mover one departure
+// from its old cell, one arrival (with its rank) in its new cell and an
+// entry of the mover list, whose slots the block takes with one atomic; the
+// departures of each block of old slots.  IDENT: old slot s holds particle
+// s, whose cell and diameter are formed here.
 template <typename T, bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
 k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* __restrict__ perm_old,
              const int32_t* __restrict__ ks_old, int32_t* __restrict__ key, T* __restrict__ vol,
-             int2* __restrict__ rec, int32_t* __restrict__ arr, int32_t* __restrict__ dep, int4* __restrict__ mov,
-             long long mov_cap, int32_t* __restrict__ blk_dep, int32_t* __restrict__ ctr,
-             unsigned long long* __restrict__ status, double* __restrict__ eps_fill, T* __restrict__ rec_fill,
-             T* __restrict__ eps_t_fill) {
+             int32_t* __restrict__ rid, int32_t* __restrict__ rkn, int32_t* __restrict__ arr,
+             int32_t* __restrict__ dep, int4* __restrict__ mov, long long mov_cap, int32_t* __restrict__ blk_dep,
+             int32_t* __restrict__ ctr, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
+             T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
     pdl_wait();
-    __shared__ int s_dep[kRebinThreads / 32];
+    constexpr int W = kRebinThreads / 32;
+    __shared__ int s_cnt[W];
+    __shared__ int s_base[W];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)blockIdx.x * kRebinTile;
-    int n_out = 0, n_nf = 0, ndep = 0;
+    int n_out = 0, n_nf = 0;
     int idk[kRebinItems], cnk[kRebinItems], cok[kRebinItems];
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
@@ -159,36 +164,49 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
         const long long s = base + k * kRebinThreads + threadIdx.x;
         if (s < n) cnk[k] = IDENT ? key_of(pos, s, g, key, vol, n_out, n_nf) : __ldg(key + idk[k]);
     }
+    unsigned mb[kRebinItems];
+    int wc = 0;
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
         const bool valid = s < n;
         const bool moved = valid && cnk[k] != cok[k];
-        const unsigned mb = __ballot_sync(full, moved);
-        if (mb) {
-            int first = 0;
-            if (lane == __ffs(mb) - 1) first = atomicAdd(&ctr[RB_NMOV], __popc(mb));
-            first = __shfl_sync(full, first, __ffs(mb) - 1);
-            if (moved) {
-                const long long idx = (long long)first + __popc(mb & lanemask_lt());
-                atomicAdd(&dep[cok[k]], 1);
-                const int r = atomicAdd(&arr[cnk[k]], 1);
-                if (idx < mov_cap && r < kRebinMaxArrivals) mov[idx] = make_int4(idk[k], cnk[k], r, 0);
-                else ctr[RB_FALLBACK] = 1;
-            }
+        mb[k] = __ballot_sync(full, moved);
+        wc += __popc(mb[k]);
+        if (valid) {
+            rkn[s] = moved ? ~cnk[k] : cnk[k];
+            if (!IDENT) rid[s] = idk[k];
         }
-        if (valid) rec[s] = make_int2(idk[k], moved ? ~cnk[k] : cnk[k]);
-        ndep += moved;
     }
-    ndep = __reduce_add_sync(full, ndep);
-    if (lane == 0) s_dep[warp] = ndep;
+    if (lane == 0) s_cnt[warp] = wc;
     if (IDENT) flush_status(status, n_out, n_nf);
     __syncthreads();
     if (threadIdx.x == 0) {
         int t = 0;
 #pragma unroll
-        for (int w = 0; w < kRebinThreads / 32; ++w) t += s_dep[w];
+        for (int w = 0; w < W; ++w) {
+            s_base[w] = t;
+            t += s_cnt[w];
+        }
         blk_dep[blockIdx.x] = t;
+        const int b0 = t ? atomicAdd(&ctr[RB_NMOV], t) : 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_base[w] += b0;
+    }
+    __syncthreads();
+    if (wc) {
+        long long idx = s_base[warp];
+#pragma unroll
+        for (int k = 0; k < kRebinItems; ++k) {
+            if (mb[k] >> lane & 1u) {
+                const long long j = idx + __popc(mb[k] & lanemask_lt());
+                atomicAdd(&dep[cok[k]], 1);
+                const int r = atomicAdd(&arr[cnk[k]], 1);
+                if (j < mov_cap && r < kRebinMaxArrivals) mov[j] = make_int4(idk[k], cnk[k], r, 0);
+                else ctr[RB_FALLBACK] = 1;
+            }
+            idx += __popc(mb[k]);
+        }
     }
     if (IDENT) eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
 }
@@ -214,24 +232,25 @@ k_rebin_rank(const int32_t* __restrict__ key, long long n, int32_t* __restrict__
     if (!ctr[RB_FALLBACK]) return;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const long long base = (long long)blockIdx.x * kRebinTile;
-    int ck[kRebinItems], lk[kRebinItems], old[kRebinItems];
+    for (long long base = (long long)blockIdx.x * kRebinTile; base < n; base += (long long)gridDim.x * kRebinTile) {
+        int ck[kRebinItems], lk[kRebinItems], old[kRebinItems];
 #pragma unroll
-    for (int k = 0; k < kRebinItems; ++k) {
-        const long long p = base + k * kRebinThreads + threadIdx.x;
-        const bool valid = p < n;
-        ck[k] = valid ? __ldg(key + p) : -1;
-        lk[k] = run_head_length(ck[k], valid);
-    }
+        for (int k = 0; k < kRebinItems; ++k) {
+            const long long p = base + k * kRebinThreads + threadIdx.x;
+            const bool valid = p < n;
+            ck[k] = valid ? __ldg(key + p) : -1;
+            lk[k] = run_head_length(ck[k], valid);
+        }
 #pragma unroll
-    for (int k = 0; k < kRebinItems; ++k) old[k] = lk[k] ? atomicAdd(&cnt[ck[k]], lk[k]) : 0;
+        for (int k = 0; k < kRebinItems; ++k) old[k] = lk[k] ? atomicAdd(&cnt[ck[k]], lk[k]) : 0;
 #pragma unroll
-    for (int k = 0; k < kRebinItems; ++k) {
-        const long long p = base + k * kRebinThreads + threadIdx.x;
-        const unsigned heads = __ballot_sync(full, lk[k] != 0);
-        const int head = 31 - __clz(heads & ((2u << lane) - 1u));
-        const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
-        if (p < n) arrival[p] = o + lane - head;
+        for (int k = 0; k < kRebinItems; ++k) {
+            const long long p = base + k * kRebinThreads + threadIdx.x;
+            const unsigned heads = __ballot_sync(full, lk[k] != 0);
+            const int head = 31 - __clz(heads & ((2u << lane) - 1u));
+            const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
+            if (p < n) arrival[p] = o + lane - head;
+        }
     }
 }
 
@@ -266,45 +285,51 @@ __device__ __forceinline__ void emit(long long n, long long ns, int i, int c, in
     vol_sorted[ns] = __ldg(vol + i);
 }
 
-// Stayers: four consecutive old slots per thread, the block's departures
-// before each slot by a block scan, the blocks' departure starts from the
-// scan of the block totals.
-template <typename T>
+// Stayers, over the old slots in the layout of the mark kernel (coalesced
+// rows).  Departures before a slot: the block's start (scan of the block
+// totals), the rows and warps before it in the block (a table of warp
+// counts), and the lanes before it (ballot).
+template <typename T, bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
-k_rebin_stay(const int2* __restrict__ rec, long long n, const int32_t* __restrict__ blk_start,
-             const int32_t* __restrict__ arr_start, const int32_t* __restrict__ arr_list, const T* __restrict__ vol,
-             int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
-             T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
+k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
+             const int32_t* __restrict__ blk_start, const int32_t* __restrict__ arr_start,
+             const int32_t* __restrict__ arr_list, const T* __restrict__ vol, int32_t* __restrict__ perm,
+             int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, T* __restrict__ vol_sorted,
+             const int32_t* __restrict__ ctr) {
     pdl_wait();
     if (ctr[RB_FALLBACK]) return;
-    __shared__ int shw[32];
-    const long long s0 = (long long)blockIdx.x * kRebinTile + threadIdx.x * kRebinItems;
-    int2 r[kRebinItems];
-    if (s0 + kRebinItems <= n) {
-        const int4* q = reinterpret_cast<const int4*>(rec + s0);   // s0 is a multiple of 4: 32-byte aligned
-        const int4 a = __ldg(q), b = __ldg(q + 1);
-        r[0] = make_int2(a.x, a.y);
-        r[1] = make_int2(a.z, a.w);
-        r[2] = make_int2(b.x, b.y);
-        r[3] = make_int2(b.z, b.w);
-    } else {
-#pragma unroll
-        for (int k = 0; k < kRebinItems; ++k) r[k] = s0 + k < n ? rec[s0 + k] : make_int2(0, -1);
-    }
-    int nd = 0;
-#pragma unroll
-    for (int k = 0; k < kRebinItems; ++k) nd += (s0 + k < n && r[k].y < 0);
-    int total;
-    int D = block_exclusive_scan(nd, shw, total) + __ldg(blk_start + blockIdx.x);
+    constexpr int W = kRebinThreads / 32;
+    __shared__ int s_tab[kRebinItems * W];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kRebinTile;
+    int kn[kRebinItems], id[kRebinItems];
+    unsigned db[kRebinItems];
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
-        const long long s = s0 + k;
-        if (s >= n) break;
-        if (r[k].y < 0) {
-            ++D;
-            continue;
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        kn[k] = s < n ? __ldg(rkn + s) : -1;
+        id[k] = IDENT ? (int)s : (s < n ? __ldg(rid + s) : 0);
+        db[k] = __ballot_sync(full, s < n && kn[k] < 0);
+        if (lane == 0) s_tab[k * W + warp] = __popc(db[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // exclusive prefix over (row, warp) in slot order
+        int t = __ldg(blk_start + blockIdx.x);
+#pragma unroll
+        for (int j = 0; j < kRebinItems * W; ++j) {
+            const int c = s_tab[j];
+            s_tab[j] = t;
+            t += c;
         }
-        const int c = r[k].y, i = r[k].x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        if (s >= n || kn[k] < 0) continue;
+        const int D = s_tab[k * W + warp] + __popc(db[k] & lanemask_lt());
+        const int c = kn[k], i = id[k];
         const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
         const long long ns = s - D + a0 + (a1 > a0 ? arrivals_below(arr_list, a0, a1, i) : 0);
         emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
@@ -314,10 +339,10 @@ k_rebin_stay(const int2* __restrict__ rec, long long n, const int32_t* __restric
 // Movers: the stayers of the new cell with an id below the mover's (a binary
 // search over the old segment, whose ids ascend, then a count of the
 // stayers before that point) and the arrivals with an id below it.
-template <typename T>
+template <typename T, bool IDENT>
 __global__ void __launch_bounds__(256)
-k_rebin_movers(const int4* __restrict__ mov, const int2* __restrict__ rec, long long n,
-               const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
+k_rebin_movers(const int4* __restrict__ mov, const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn,
+               long long n, const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
                const int32_t* __restrict__ arr_start, const int32_t* __restrict__ arr_list, const T* __restrict__ vol,
                int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
                T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
@@ -329,13 +354,17 @@ k_rebin_movers(const int4* __restrict__ mov, const int2* __restrict__ rec, long 
         const int i = m.x, c = m.y;
         const int o0 = __ldg(cs_old + c), o1 = __ldg(cs_old + c + 1);
         int lo = o0, hi = o1;
-        while (lo < hi) {
-            const int mid = lo + ((hi - lo) >> 1);
-            if (__ldg(&rec[mid].x) < i) lo = mid + 1;
-            else hi = mid;
+        if (IDENT) {
+            lo = i < o0 ? o0 : (i > o1 ? o1 : i);   // the old ids of the segment are its slots
+        } else {
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (__ldg(rid + mid) < i) lo = mid + 1;
+                else hi = mid;
+            }
         }
         int stay = 0;
-        for (int q = o0; q < lo; ++q) stay += __ldg(&rec[q].y) >= 0;
+        for (int q = o0; q < lo; ++q) stay += __ldg(rkn + q) >= 0;
         const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
         const long long ns = (long long)__ldg(cs_new + c) + stay + arrivals_below(arr_list, a0, a1, i);
         emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
@@ -355,17 +384,19 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
                   g->status, eps_fill, rec_fill, eps_t_fill);
     if (ident)
         CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, true>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
-                  (const int32_t*)nullptr, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rec, R.arr, R.dep,
-                  g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, eps_fill, rec_fill, eps_t_fill);
+                  (const int32_t*)nullptr, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rid, g->rb_rkn,
+                  R.arr, R.dep, g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, eps_fill, rec_fill, eps_t_fill);
     else
         CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, false>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
-                  (const int32_t*)g->perm, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rec, R.arr, R.dep,
-                  g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr, (T*)nullptr);
+                  (const int32_t*)g->perm, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rid, g->rb_rkn,
+                  R.arr, R.dep, g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr,
+                  (T*)nullptr);
     const unsigned cgrid = (unsigned)std::min<long long>((nbulk + 255) / 256, (long long)g->num_sms * 8);
     CG_LAUNCH(g, "rebin_cells", k_rebin_cells, cgrid, 256, 0, (const int32_t*)g->cell_start, nbulk,
               (const int32_t*)R.dep, (const int32_t*)R.arr, R.cnt, (const int32_t*)R.ctr);
-    CG_LAUNCH(g, "rebin_rank", k_rebin_rank, (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->key, n, R.cnt,
-              g->key2, (const int32_t*)R.ctr);
+    const unsigned rgrid = (unsigned)std::min<long long>(nblk, (long long)g->num_sms * 4);
+    CG_LAUNCH(g, "rebin_rank", k_rebin_rank, rgrid, kRebinThreads, 0, (const int32_t*)g->key, n, R.cnt, g->key2,
+              (const int32_t*)R.ctr);
     {
         const int32_t* in[3] = {R.cnt, R.arr, R.blk};
         int32_t* out[3] = {R.cnt, R.arr, R.blk};
@@ -376,13 +407,20 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
                                                                               (long long)g->num_sms * 8));
     CG_LAUNCH(g, "rebin_place", k_rebin_place, mgrid, 256, 0, (const int4*)g->rb_mov, (const int32_t*)R.arr,
               g->rb_arr, (const int32_t*)R.ctr);
-    CG_LAUNCH(g, "rebin_stay", k_rebin_stay<T>, (unsigned)nblk, kRebinThreads, 0, (const int2*)g->rb_rec, n,
-              (const int32_t*)R.blk, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm,
-              g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);
-    CG_LAUNCH(g, "rebin_movers", k_rebin_movers<T>, mgrid, 256, 0, (const int4*)g->rb_mov, (const int2*)g->rb_rec,
-              n, (const int32_t*)g->cell_start, (const int32_t*)R.cnt, (const int32_t*)R.arr,
-              (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted,
-              (const int32_t*)R.ctr);
+#define CG_REBIN_TAIL(ID)                                                                                        \
+    CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->rb_rid,   \
+              (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, \
+              (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);      \
+    CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int4*)g->rb_mov,                   \
+              (const int32_t*)g->rb_rid, (const int32_t*)g->rb_rkn, n, (const int32_t*)g->cell_start,              \
+              (const int32_t*)R.cnt, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm,   \
+              g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr)
+    if (ident) {
+        CG_REBIN_TAIL(true);
+    } else {
+        CG_REBIN_TAIL(false);
+    }
+#undef CG_REBIN_TAIL
     // fallback: placement and per-cell sort from the scanned counts
     CG_TRY(launch_cellsort_tail(g, n, R.cnt, R.ctr + RB_FALLBACK));
     CG_CUDA(cudaMemcpyAsync(g->cell_start, R.cnt, sizeof(int32_t) * (nbulk + 1), cudaMemcpyDeviceToDevice, g->stream));
