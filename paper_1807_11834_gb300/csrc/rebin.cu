@@ -149,6 +149,8 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
     const long long base = (long long)blockIdx.x * kRebinTile;
     int n_out = 0, n_nf = 0;
     int idk[kRebinItems], cnk[kRebinItems], cok[kRebinItems];
+    V4<T> pv[kRebinItems];
+    // every load of the thread first, so that they are in flight together
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
@@ -157,12 +159,24 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
         if (s < n) {
             idk[k] = IDENT ? (int)s : __ldg(perm_old + s);
             cok[k] = __ldg(ks_old + s);
+            if (IDENT) pv[k] = ld4(pos, s);
         }
     }
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
-        if (s < n) cnk[k] = IDENT ? key_of(pos, s, g, key, vol, n_out, n_nf) : __ldg(key + idk[k]);
+        if (s >= n) continue;
+        if (IDENT) {
+            int outside = 0;
+            const V4<T>& v = pv[k];
+            if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
+            cnk[k] = cell_of(v, g, outside);
+            n_out += outside;
+            key[s] = cnk[k];
+            vol[s] = v.w;   // the diameter: the porosity forms the volume as an exact pair
+        } else {
+            cnk[k] = __ldg(key + idk[k]);
+        }
     }
     unsigned mb[kRebinItems];
     int wc = 0;
@@ -303,13 +317,26 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)blockIdx.x * kRebinTile;
-    int kn[kRebinItems], id[kRebinItems];
+    int kn[kRebinItems], id[kRebinItems], a0[kRebinItems], a1[kRebinItems];
+    T d[kRebinItems];
     unsigned db[kRebinItems];
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
         kn[k] = s < n ? __ldg(rkn + s) : -1;
         id[k] = IDENT ? (int)s : (s < n ? __ldg(rid + s) : 0);
+    }
+    // the gathers of each stayer (its cell's arrivals, its diameter) go out
+    // before the block waits for the departure table
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long s = base + k * kRebinThreads + threadIdx.x;
+        a0[k] = a1[k] = 0;
+        if (s < n && kn[k] >= 0) {
+            a0[k] = __ldg(arr_start + kn[k]);
+            a1[k] = __ldg(arr_start + kn[k] + 1);
+            d[k] = __ldg(vol + id[k]);
+        }
         db[k] = __ballot_sync(full, s < n && kn[k] < 0);
         if (lane == 0) s_tab[k * W + warp] = __popc(db[k]);
     }
@@ -330,9 +357,12 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
         if (s >= n || kn[k] < 0) continue;
         const int D = s_tab[k * W + warp] + __popc(db[k] & lanemask_lt());
         const int c = kn[k], i = id[k];
-        const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
-        const long long ns = s - D + a0 + (a1 > a0 ? arrivals_below(arr_list, a0, a1, i) : 0);
-        emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
+        const long long ns = s - D + a0[k] + (a1[k] > a0[k] ? arrivals_below(arr_list, a0[k], a1[k], i) : 0);
+        if ((unsigned long long)ns >= (unsigned long long)n) continue;   // never for a valid binning
+        perm[ns] = i;
+        key_sorted[ns] = c;
+        inv_perm[i] = (int)ns;
+        vol_sorted[ns] = d[k];
     }
 }
 
