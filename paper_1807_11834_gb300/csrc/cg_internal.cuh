@@ -614,10 +614,9 @@ __device__ __forceinline__ void seg_chunk_range(long long base, long long n, con
 // segment's total.  load(i, v) fills the K values of slot i; emit(key, tot)
 // receives each segment's compensated total on the lane of its last slot.
 // The next round's slots are loaded before the current one is reduced.
-template <typename T, int K, typename Load, typename Emit>
+template <typename T, int K, typename Load, typename Emit, int B = 4>   // B: rounds loaded ahead of the reduction
 __device__ __forceinline__ void seg_rounds(long long s, long long t, const int32_t* __restrict__ key_sorted,
                                            Load load, Emit emit) {
-    constexpr int B = 4;   // rounds loaded ahead of the reduction
     const int lane = threadIdx.x & 31;
     CSum<T> carry[K];
     int carry_key = -1;
@@ -806,6 +805,31 @@ __device__ __forceinline__ void seg_seq(long long s, long long t, const int32_t*
             carry[k].c = __shfl_sync(full, acc[k].c, last);
         }
         carry_key = goes_on ? lk : -1;
+    }
+}
+
+// Reaction of one cell from its compensated force sum a: S_B = -(1/V_B) sum F
+// (Eq. UFP: F_fpi is the fluid-side reaction to F_drag), written to S
+// ([3][n_b]), and S_B V_B added to the diagnostics sv (an exact
+// float-float product on the FP32 path).
+template <typename T>
+__device__ __forceinline__ void reaction_emit(const GridDev& g, T* __restrict__ S, int key, CSum<T> (&a)[3],
+                                              CSum<T> (&sv)[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T s_;
+        if (sizeof(T) == 4) s_ = -(a[k].get()) * (T)g.invVBf;
+        else s_ = -(a[k].get()) * (T)g.invVB;
+        S[k * g.nbulk + key] = s_;
+        if (sizeof(T) == 4) {
+            T hi = s_ * (T)g.VBh;
+            T lo = fma(s_, (T)g.VBh, -hi);
+            lo = fma(s_, (T)g.VBl, lo);
+            sv[k].add(hi);
+            sv[k].c += lo;
+        } else {
+            sv[k].add(s_ * (T)g.VB);
+        }
     }
 }
 

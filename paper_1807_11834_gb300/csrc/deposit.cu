@@ -145,24 +145,7 @@ __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ 
                 v[1] = f.y;
                 v[2] = f.z;
             },
-            [&](int key, CSum<T> (&a)[3]) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    T s_;
-                    if (sizeof(T) == 4) s_ = -(a[k].get()) * (T)g.invVBf;
-                    else s_ = -(a[k].get()) * (T)g.invVB;
-                    S[k * g.nbulk + key] = s_;
-                    if (sizeof(T) == 4) {
-                        T hi = s_ * (T)g.VBh;
-                        T lo = fma(s_, (T)g.VBh, -hi);
-                        lo = fma(s_, (T)g.VBl, lo);
-                        sv[k].add(hi);
-                        sv[k].c += lo;
-                    } else {
-                        sv[k].add(s_ * (T)g.VB);
-                    }
-                }
-            });
+            [&](int key, CSum<T> (&a)[3]) { reaction_emit<T>(g, S, key, a, sv); });
     }
     if (do_sums) block_sums<T, 3>(sv, part, pstride, b.id);
 }
