@@ -130,11 +130,10 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
     for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
     int clamped_total = 0;
     const long long stride = b.n * blockDim.x;
-    // particle and slot of loop index q (the particle index of a slot loop
-    // comes from pp, loaded one iteration ahead of the record)
-    auto at = [&](long long q, int pp, long long& p, int& slot) {
+    // particle and slot of loop index q
+    auto at = [&](long long q, long long& p, int& slot) {
         if (SLOT) {
-            p = pp;
+            p = __ldg(idx + q);
             slot = (int)q;
         } else {
             p = q;
@@ -145,20 +144,17 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
     // stencil is gathered and its force computed (its DRAM latency overlaps
     // them); the batched kernel, short of registers, loads it in turn
     V4<T> xn, vn;
-    int slot_n = 0, pp = 0;
+    int slot_n = 0;
     long long p_n = 0;
     long long q = b.id * blockDim.x + threadIdx.x;
     if (q < n) {
-        if (SLOT) pp = __ldg(idx + q);
-        at(q, pp, p_n, slot_n);
+        at(q, p_n, slot_n);
         xn = EULER ? ld4_plain(pos, p_n) : ld4((const T*)pos, p_n);
         vn = EULER ? ld4_plain(vel, p_n) : ld4((const T*)vel, p_n);
-        if (SLOT && PREFETCH && q + stride < n) pp = __ldg(idx + q + stride);
     }
     for (; q < n; q += stride) {
         if (!PREFETCH && q != b.id * blockDim.x + threadIdx.x) {
-            if (SLOT) pp = __ldg(idx + q);
-            at(q, pp, p_n, slot_n);
+            at(q, p_n, slot_n);
             xn = EULER ? ld4_plain(pos, p_n) : ld4((const T*)pos, p_n);
             vn = EULER ? ld4_plain(vel, p_n) : ld4((const T*)vel, p_n);
         }
@@ -166,10 +162,9 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
         const int slot = slot_n;
         const long long p = p_n;
         if (PREFETCH && q + stride < n) {
-            at(q + stride, pp, p_n, slot_n);
+            at(q + stride, p_n, slot_n);
             xn = EULER ? ld4_plain(pos, p_n) : ld4((const T*)pos, p_n);
             vn = EULER ? ld4_plain(vel, p_n) : ld4((const T*)vel, p_n);
-            if (SLOT && q + 2 * stride < n) pp = __ldg(idx + q + 2 * stride);
         }
         const DragOne<T> r = drag_one<T, EULER>(x, v, g, P, bulk4, dt);
         clamped_total += r.cl;
