@@ -558,7 +558,7 @@ static cg_status step_impl(cg_grids* g, const cg_particles* p, const void* u_fin
     if (!mlp)
         CG_TRY(on_aux(g, [&] { return launch_average(g, u_fine, o->u_bulk, o->var_bulk, fused ? g->bulk4 : nullptr); }));
     CG_CUDA(cudaEventRecord(g->ev_avg, side));
-    if (fused) CG_TRY(launch_bin(g, n, p->pos_d, o->eps_bulk, g->bulk4, eps_t, sorted_out == nullptr));
+    if (fused) CG_TRY(launch_bin(g, n, p->pos_d, o->eps_bulk, g->bulk4, eps_t));
     else CG_TRY(launch_bin(g, n, p->pos_d, o->eps_bulk));
     CG_TRY(copy_bins(g, n, o->cell, o->perm, o->cell_start));
     // sorted diameters of this binning

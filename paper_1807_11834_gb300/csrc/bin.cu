@@ -1061,7 +1061,7 @@ int batch_bin_occupancy(int phase, size_t smem) {
 }
 
 cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fill, void* rec_fill,
-                     void* eps_t_fill, bool need_inv) {
+                     void* eps_t_fill) {
     CG_TRY(set_attrs());
     const long long nbulk = g->gd.nbulk;
     // a binning of the same count held by the handle is the starting point
@@ -1073,12 +1073,10 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     g->hint_ident = nullptr;
     g->n_binned = -1;
     g->vol_valid = false;
-    g->inv_valid = false;
     if (rebin) {
-        CG_TRY(launch_rebin(g, n, pos_d, ident, need_inv, eps_fill, rec_fill, eps_t_fill));
+        CG_TRY(launch_rebin(g, n, pos_d, ident, eps_fill, rec_fill, eps_t_fill));
         g->n_binned = n;
         g->vol_valid = true;
-        g->inv_valid = need_inv;
         g->hint_n = n;
         return CG_OK;
     }
@@ -1087,7 +1085,6 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     if (n == 0) {
         g->n_binned = 0;
         g->vol_valid = true;
-        g->inv_valid = true;
         return CG_OK;
     }
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
@@ -1101,7 +1098,6 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
                                    (float*)eps_t_fill));
         g->n_binned = n;
         g->vol_valid = true;
-        g->inv_valid = true;
         g->hint_n = n;
         return CG_OK;
     }
@@ -1116,7 +1112,6 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
                                  (float*)eps_t_fill));
     g->n_binned = n;
     g->vol_valid = true;
-    g->inv_valid = true;
     g->hint_n = n;
     return CG_OK;
 }

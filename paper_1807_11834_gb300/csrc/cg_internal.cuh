@@ -179,7 +179,6 @@ struct cg_grids {
     void* vol_sorted = nullptr;    // [cap] T particle diameter, sorted order
     void* Fs = nullptr;            // [cap] T4 drag force, sorted order
     bool vol_valid = false;        // vol_sorted matches the binned positions
-    bool inv_valid = false;        // inv_perm is the inverse of perm
     // incremental rebinning (rebin.cu): a binning of hint_n particles held in
     // perm / key_sorted / cell_start is where the next binning of the same
     // count starts; hint_ident is the particle array the last sorted step
@@ -321,19 +320,14 @@ inline long long rebin_small_ints(long long nbulk, long long nblk) {
 }
 // The binning of n particles from the handle's last binning of n; ident:
 // the particles are that binning's sorted output (particle i at old slot i).
-// need_inv false: the incremental path leaves inv_perm out (inv_valid false).
-cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, bool need_inv, double* eps_fill,
-                       void* rec_fill, void* eps_t_fill);
-// inv_perm of the current binning (rebuilt from perm when a binning left it out).
-cg_status ensure_inv_perm(cg_grids* g, long long n);
+cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,
+                       void* eps_t_fill);
 cg_status ensure_partials(cg_grids* g, long long n);
 
 // eps_fill (nullable): also set this [n_b] porosity to 1 (when n > 0), and
 // likewise the porosity of the drag record rec_fill and of eps_t_fill (T).
-// need_inv false: the caller does not need inv_perm (an incremental binning
-// may then leave it out; ensure_inv_perm rebuilds it on demand).
 cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fill = nullptr,
-                     void* rec_fill = nullptr, void* eps_t_fill = nullptr, bool need_inv = true);
+                     void* rec_fill = nullptr, void* eps_t_fill = nullptr);
 // prefilled: eps already holds 1 for every cell (the binning set it);
 // rec / eps_t (nullable, sorted-diameter path only): also write the porosity
 // of occupied cells into the drag record and its T copy.
@@ -620,10 +614,9 @@ __device__ __forceinline__ void seg_chunk_range(long long base, long long n, con
 // segment's total.  load(i, v) fills the K values of slot i; emit(key, tot)
 // receives each segment's compensated total on the lane of its last slot.
 // The next round's slots are loaded before the current one is reduced.
-template <typename T, int K, typename Load, typename Emit>
+template <typename T, int K, typename Load, typename Emit, int B = 4>   // B: rounds loaded ahead of the reduction
 __device__ __forceinline__ void seg_rounds(long long s, long long t, const int32_t* __restrict__ key_sorted,
                                            Load load, Emit emit) {
-    constexpr int B = 4;   // rounds loaded ahead of the reduction
     const int lane = threadIdx.x & 31;
     CSum<T> carry[K];
     int carry_key = -1;

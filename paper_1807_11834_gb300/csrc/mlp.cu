@@ -845,7 +845,6 @@ cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* p
     CG_TRY(mlp_attrs());
     g->part_blocks[PS_DRAG] = -1;   // the drag diagnostics are not formed on this path
     void* Fs = S_bulk ? g->Fs : nullptr;
-    if (Fs) CG_TRY(ensure_inv_perm(g, n));
     if (n > 0) {
         const long long ntiles = (n + TILE - 1) / TILE;
         const unsigned grid = (unsigned)std::min(ntiles, (long long)4 * g->num_sms);

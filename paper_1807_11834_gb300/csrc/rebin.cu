@@ -295,7 +295,7 @@ __device__ __forceinline__ void emit(long long n, long long ns, int i, int c, in
     if ((unsigned long long)ns >= (unsigned long long)n) return;   // never for a valid binning
     perm[ns] = i;
     key_sorted[ns] = c;
-    if (inv_perm) inv_perm[i] = (int)ns;
+    inv_perm[i] = (int)ns;
     vol_sorted[ns] = __ldg(vol + i);
 }
 
@@ -361,7 +361,7 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
         if ((unsigned long long)ns >= (unsigned long long)n) continue;   // never for a valid binning
         perm[ns] = i;
         key_sorted[ns] = c;
-        if (inv_perm) inv_perm[i] = (int)ns;
+        inv_perm[i] = (int)ns;
         vol_sorted[ns] = d[k];
     }
 }
@@ -402,9 +402,8 @@ k_rebin_movers(const int4* __restrict__ mov, const int32_t* __restrict__ rid, co
 }
 
 template <typename T>
-static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, bool need_inv, double* eps_fill,
-                            T* rec_fill, T* eps_t_fill) {
-    int32_t* inv = need_inv ? g->inv_perm : nullptr;   // the sorted step's drag runs over the slots
+static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, double* eps_fill, T* rec_fill,
+                            T* eps_t_fill) {
     const long long nbulk = g->gd.nbulk;
     const RebinPtrs R = rebin_ptrs(g);
     const long long nblk = (n + kRebinTile - 1) / kRebinTile;
@@ -441,11 +440,11 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
 #define CG_REBIN_TAIL(ID)                                                                                        \
     CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->rb_rid,   \
               (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, \
-              (const T*)g->vol, g->perm, g->key_sorted, inv, (T*)g->vol_sorted, (const int32_t*)R.ctr);              \
+              (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);      \
     CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int4*)g->rb_mov,                   \
               (const int32_t*)g->rb_rid, (const int32_t*)g->rb_rkn, n, (const int32_t*)g->cell_start,              \
               (const int32_t*)R.cnt, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm,   \
-              g->key_sorted, inv, (T*)g->vol_sorted, (const int32_t*)R.ctr)
+              g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr)
     if (ident) {
         CG_REBIN_TAIL(true);
     } else {
@@ -458,28 +457,11 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
     return CG_OK;
 }
 
-cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, bool need_inv, double* eps_fill,
-                       void* rec_fill, void* eps_t_fill) {
-    if (g->fp64) return rebin_impl<double>(g, n, (const double*)pos_d, ident, need_inv, eps_fill, (double*)rec_fill,
+cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,
+                       void* eps_t_fill) {
+    if (g->fp64) return rebin_impl<double>(g, n, (const double*)pos_d, ident, eps_fill, (double*)rec_fill,
                                            (double*)eps_t_fill);
-    return rebin_impl<float>(g, n, (const float*)pos_d, ident, need_inv, eps_fill, (float*)rec_fill,
-                             (float*)eps_t_fill);
-}
-
-// Inverse of the binning's permutation, for a binning that left it out.
-__global__ void __launch_bounds__(256) k_inv_perm(const int32_t* __restrict__ perm, long long n,
-                                                  int32_t* __restrict__ inv) {
-    pdl_wait();
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x)
-        inv[__ldg(perm + s)] = (int)s;
-}
-
-cg_status ensure_inv_perm(cg_grids* g, long long n) {
-    if (g->inv_valid || n <= 0) return CG_OK;
-    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)g->num_sms * 8);
-    CG_LAUNCH(g, "inv_perm", k_inv_perm, grid, 256, 0, (const int32_t*)g->perm, n, g->inv_perm);
-    g->inv_valid = true;
-    return CG_OK;
+    return rebin_impl<float>(g, n, (const float*)pos_d, ident, eps_fill, (float*)rec_fill, (float*)eps_t_fill);
 }
 
 }  // namespace cg
