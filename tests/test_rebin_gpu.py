@@ -118,6 +118,14 @@ def test_sorted_steps_keep_cell_order_and_match_cg_step(cuda_lib):
             assert breaks < 0.2, (step, breaks)
     ids = bufs[0][1][:, 3].view(torch.int32)
     assert torch.equal(torch.sort(ids.long())[0], torch.arange(w.n, device="cuda"))
+    # the entry points on the sorted step's binning: a drag in the caller's
+    # order gives the step's forces and reaction again
+    pi, vi = bufs[1]     # the last step's input
+    F2 = torch.empty_like(out["force"])
+    S2 = torch.empty_like(out["S_bulk"])
+    g.cg_drag(pi, vi, out["eps_bulk"], out["u_bulk"], F2, S2)
+    torch.cuda.synchronize()
+    assert torch.equal(F2, out["force"]) and torch.equal(S2, out["S_bulk"])
     assert g.cg_sync_status()[0] == 0
     g.close()
     f.close()
