@@ -76,9 +76,10 @@ __device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, c
     r.u[1] = v.y;
     r.u[2] = v.z;
     if (EULER) {
+        const T inv_m = T(1) / r.m;   // one division for the three components
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            T ua = r.u[a] + dt * (r.f[a] / r.m + P.g[a]);
+            T ua = r.u[a] + dt * (r.f[a] * inv_m + P.g[a]);
             T xa = r.x[a] + dt * ua;
             const T lo = (T)g.x0[a], hi = (T)g.xhi[a];
             if (xa < lo) { xa = T(2) * lo - xa; ua = -ua; }
