@@ -430,6 +430,33 @@ cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void*
  * are kept, not copied. */
 cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int32_t age);
 
+/* Checkpoints of a trained closure (the same files closure.save_checkpoint
+ * and closure.load_checkpoint of the Python binding read and write), two
+ * files beside each other:
+ *   <path>.f32   the CG_MLP_NPARAM parameters, little-endian float32, in the
+ *                order above;
+ *   <path>.json  a JSON object with "format": "dual-grid drag closure",
+ *                "version": 1, "nparam", "nfeat", "hidden" (64), "k0" (16),
+ *                "params_file" (the .f32 file's name, no directory),
+ *                "params_sha256" (SHA-256 of that file, FIPS 180-4, lower-case
+ *                hex), "feature_lo" / "feature_hi" (the feature box) and
+ *                "meta" (a JSON object the caller chooses).
+ * cg_mlp_save writes the closure's current parameters and feature box
+ * (waits for its stream); meta_json is a JSON object text or NULL ({}).
+ * cg_mlp_load reads a checkpoint and creates a closure from it on the
+ * current device, as cg_mlp_create.  The host-only pair underneath works
+ * on host arrays (no device needed): cg_mlp_checkpoint_write(params [NPARAM],
+ * feat_lo / feat_hi [NFEAT]) and cg_mlp_checkpoint_read (outputs nullable).
+ * CG_ERR_INVALID_ARG: a file cannot be written or read, or does not hold a
+ * checkpoint of this network (format, version or sizes differ, the
+ * checksum does not match, a value is not finite, the feature box is
+ * empty), or meta_json is not a JSON object; nothing is created then. */
+cg_status cg_mlp_save(cg_mlp* m, const char* path, const char* meta_json);
+cg_status cg_mlp_load(const char* path, void* cuda_stream, cg_mlp** out);
+cg_status cg_mlp_checkpoint_write(const char* path, const float* params, const float* feat_lo, const float* feat_hi,
+                                  const char* meta_json);
+cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo, float* feat_hi);
+
 /* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
  * kernels expired (flags: CG_FLAG_*).  Reading the status clears it. */
 cg_status cg_mlp_sync_status(cg_mlp* m, uint32_t* flags);

@@ -124,6 +124,10 @@ _SIGS = {
     "cg_mlp_grads": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p]),
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "cg_mlp_save": (C.c_int, [C.c_void_p, C.c_char_p, C.c_char_p]),
+    "cg_mlp_load": (C.c_int, [C.c_char_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cg_mlp_checkpoint_write": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_char_p]),
+    "cg_mlp_checkpoint_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cg_mlp_wait_selftest": (C.c_int, [C.c_void_p, C.c_uint32]),
     "cg_debug_fail_alloc_after": (C.c_int, [C.c_int64]),
     "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -513,6 +517,30 @@ def cg_bin_particles_static(desc: dict, pos_d, perm, cell_start, cell=None, stre
                                          _stream_handle(stream)), "cg_bin_particles_static")
 
 
+def checkpoint_write(path, params, feat_lo, feat_hi, meta=None):
+    """cg_mlp_checkpoint_write: a closure checkpoint from host arrays (no device)."""
+    import json
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    lo = np.ascontiguousarray(feat_lo, dtype=np.float32)
+    hi = np.ascontiguousarray(feat_hi, dtype=np.float32)
+    if p.size != MLP_NPARAM or lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
+        raise ValueError("bad closure parameter or feature-box sizes")
+    _check(lib().cg_mlp_checkpoint_write(os.fsencode(path), p.ctypes.data, lo.ctypes.data, hi.ctypes.data,
+                                         json.dumps(meta or {}).encode()), "cg_mlp_checkpoint_write")
+
+
+def checkpoint_read(path):
+    """cg_mlp_checkpoint_read: (params, feat_lo, feat_hi) float32 arrays of a checkpoint."""
+    import numpy as np
+    p = np.zeros(MLP_NPARAM, np.float32)
+    lo = np.zeros(MLP_NFEAT, np.float32)
+    hi = np.zeros(MLP_NFEAT, np.float32)
+    _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), p.ctypes.data, lo.ctypes.data, hi.ctypes.data),
+           "cg_mlp_checkpoint_read")
+    return p, lo, hi
+
+
 class Mlp:
     """Owner of a ``cg_mlp`` closure handle (learned drag correction).
     Parameters are a flat float32 array of MLP_NPARAM (W1, b1, W2, b2, w3, b3)."""
@@ -529,6 +557,26 @@ class Mlp:
                                    C.byref(h)), "cg_mlp_create")
         self.h = h
         self.lo, self.hi = lo, hi
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """The closure of a checkpoint (cg_mlp_load)."""
+        import numpy as np
+        m = cls.__new__(cls)
+        h = C.c_void_p()
+        _check(lib().cg_mlp_load(os.fsencode(path), _stream_handle(stream), C.byref(h)), "cg_mlp_load")
+        m.h = h
+        m.lo = np.zeros(MLP_NFEAT, np.float32)
+        m.hi = np.zeros(MLP_NFEAT, np.float32)
+        _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), None, m.lo.ctypes.data, m.hi.ctypes.data),
+               "cg_mlp_checkpoint_read")
+        return m
+
+    def save(self, path, meta=None):
+        """Checkpoint of the current parameters and feature box (cg_mlp_save);
+        meta: a JSON-serialisable dict kept in the head."""
+        import json
+        _check(lib().cg_mlp_save(self.h, os.fsencode(path), json.dumps(meta or {}).encode()), "cg_mlp_save")
 
     def close(self):
         if getattr(self, "h", None):

@@ -352,6 +352,8 @@ cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* p
                               const void* var_stale, const void* u_fine, int32_t age, void* force, void* S_bulk,
                               double dt);
 cg_status grow_buf(DevBuf& b, size_t bytes);
+// The closure's feature box (CG_MLP_NFEAT values each).
+cg_status mlp_feature_box(const cg_mlp* m, float* lo, float* hi);
 // The stale variance field, fine velocity and record age bound to a closure by cg_mlp_bind.
 cg_status mlp_bound_inputs(const cg_mlp* m, const void** var_stale, const void** u_fine, int32_t* age);
 cg_status launch_project(cg_grids* g, int ncomp, const void* const* in, void* const* out, bool sums);

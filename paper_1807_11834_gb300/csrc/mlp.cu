@@ -859,6 +859,17 @@ cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* p
 
 }  // namespace cg
 
+namespace cg {
+cg_status mlp_feature_box(const cg_mlp* m, float* lo, float* hi) {
+    if (!m) return CG_ERR_INVALID_ARG;
+    for (int k = 0; k < NFEAT; ++k) {
+        lo[k] = m->lo[k];
+        hi[k] = m->hi[k];
+    }
+    return CG_OK;
+}
+}  // namespace cg
+
 extern "C" {
 
 cg_status cg_mlp_features(cg_grids* g, int64_t n, const void* pos_d, const void* vel, const double* eps_bulk,
@@ -949,6 +960,7 @@ cg_status cg_mlp_destroy(cg_mlp* m) {
     delete m;
     return CG_OK;
 }
+
 
 cg_status cg_mlp_get_params(cg_mlp* m, float* params, float* grads) {
     if (!m) return CG_ERR_INVALID_ARG;

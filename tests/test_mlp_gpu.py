@@ -151,3 +151,31 @@ def test_bounded_wait_expires_into_a_timeout_status(cuda_lib):
     assert m.sync_status() == (0, 0)
     assert torch.equal(c0, c1)
     m.close()
+
+
+def test_checkpoint_round_trip_through_the_c_abi(cuda_lib, tmp_path):
+    """cg_mlp_save of a trained-in-place closure, then cg_mlp_load: the
+    loaded closure holds the same parameters and feature box bit for bit
+    and computes the same c on the same rows; the Python reader reads the
+    same files."""
+    import torch
+    from paper_1807_11834_gb300 import closure
+    m, _ = make(cuda_lib, 3)
+    feat = random_features(700, 4)
+    f_d = torch.from_numpy(feat).cuda()
+    tg = torch.rand(700, device="cuda")
+    m.train_step(f_d, tg, 1e-3)                  # parameters moved on the device
+    base = str(tmp_path / "trained")
+    m.save(base, meta={"steps": 1})
+    m2 = cuda_lib.Mlp.load(base)
+    assert m2.params().tobytes() == m.params().tobytes()
+    assert m2.lo.tobytes() == m.lo.tobytes() and m2.hi.tobytes() == m.hi.tobytes()
+    c1, c2 = torch.empty(700, device="cuda"), torch.empty(700, device="cuda")
+    m.forward(f_d, c1)
+    m2.forward(f_d, c2)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2)
+    q, lo, hi, meta = closure.load_checkpoint(base)
+    assert q.tobytes() == m.params().tobytes() and meta == {"steps": 1}
+    m.close()
+    m2.close()
