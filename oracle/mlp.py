@@ -67,8 +67,14 @@ def init_params(hidden: int = 64, seed: int = 0) -> dict:
                 w3=u((hidden,), hidden) * 0.1, b3=np.array([1.0]))
 
 
+def _exact(a):
+    """float64, or complex128 for complex values (so that the forward pass
+    can be differentiated by a complex step)."""
+    return np.asarray(a, dtype=np.result_type(a, np.float64))
+
+
 def forward(p: dict, X: np.ndarray, bf16_inputs: bool = False):
-    q = (lambda a: bf16(a)) if bf16_inputs else (lambda a: np.asarray(a, np.float64))
+    q = (lambda a: bf16(a)) if bf16_inputs else _exact
     Z1 = q(X) @ q(p["W1"]) + p["b1"]
     A1 = gelu(Z1)
     Z2 = q(A1) @ q(p["W2"]) + p["b2"]

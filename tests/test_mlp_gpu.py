@@ -6,8 +6,10 @@ float64.  The remaining differences are FP32 accumulation and FP32 GELU in
 the kernels, plus rare one-ulp differences in re-rounding a hidden
 activation to bfloat16 when it sits on a rounding boundary (each moves c by
 at most ~2^-8 of one term).  Tolerances below are set from that: c within
-5e-3 absolute (c ~ 1), gradients within 1e-2 relative per parameter block
-(norm-wise), Adam within 1e-5 of the oracle's update of the same gradient.
+1e-4 absolute on 99.9% of the rows (c ~ 1; measured ~1e-5 at the maximum)
+and within 5e-3 on the rare boundary rows; gradients within 1e-3 relative
+per parameter block (norm-wise; measured ~1.5e-5), Adam within 1e-5 of the
+oracle's update of the same gradient.
 """
 import numpy as np
 import pytest
@@ -58,8 +60,12 @@ def test_forward_matches_oracle(cuda_lib):
     want, _ = om.forward(p, scaled(feat), bf16_inputs=True)
     got = c.cpu().numpy()
     err = np.abs(got - want)
-    print("forward max abs err", err.max(), "median", np.median(err))
-    assert err.max() < 5e-3 and np.median(err) < 1e-4
+    print("forward max abs err", err.max(), "median", np.median(err), "p99.9", np.quantile(err, 0.999))
+    # the bulk agrees to FP32 accumulation; a hidden activation sitting on a
+    # bf16 rounding boundary may round the other way, which moves c by at
+    # most ~2^-8 of one term: such rows stay within 5e-3 and are rare
+    assert np.quantile(err, 0.999) < 1e-4 and np.median(err) < 1e-6
+    assert err.max() < 5e-3 and (err > 1e-4).sum() <= 0.001 * n
     assert ok.cpu().numpy().all()
     feat[5, 0] = HI[0] * 1.5      # out of the training box
     m.forward(torch.from_numpy(feat).cuda(), c, ok)
@@ -79,12 +85,12 @@ def test_gradients_match_oracle(cuda_lib):
     _, g_flat = m.params(grads=True)
     g = cuda_lib.mlp_unpack(g_flat)
     want_loss, want = om.loss_and_grads(p, scaled(feat), target.astype(np.float64), bf16_inputs=True)
-    assert loss.item() == pytest.approx(want_loss, rel=1e-3)
+    assert loss.item() == pytest.approx(want_loss, rel=1e-4)
     for k in want:
         num = np.linalg.norm(g[k] - want[k])
         den = np.linalg.norm(want[k])
         print(k, num / den)
-        assert num <= 1e-2 * den, (k, num / den)
+        assert num <= 1e-3 * den, (k, num / den)
     m.close()
 
 
