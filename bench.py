@@ -490,19 +490,7 @@ def run_gb300(args):
                "blocking_entry_ms_per_step": 1e3 * te_sync / ke}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        ks = args.cpu_steps if args.cpu_steps > 0 else (1 if n > 8_000_000 else 2)
-        cpos, cvel = w.pos_d, w.vel
-        ta = time.perf_counter()
-        for _ in range(ks):
-            r = oracle.step(w.desc, cpos, cvel, w.u_fine, dt=dt, want_eps_fine=True)
-            cpos, cvel = r["pos_d"], r["vel"]
-        tc = time.perf_counter() - ta
-        cpu = {"value": n * ks / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ks} full oracle step{'s' if ks > 1 else ''} (dt {dt:g}) of the same "
-                         f"{args.workload.replace('_', ' ')} from its initial state (FP64 C, single thread), "
-                         f"{tc:.1f} s"}
+        cpu = oracle_baseline(args, w, dt)
 
     if world > 1:
         dist.barrier()
@@ -552,37 +540,84 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def oracle_rate(w, dt, steps, threads):
+    """(particle-steps/s, seconds) of `steps` whole oracle steps of w from its
+    initial state, each from the state the last one advanced."""
+    import oracle
+    oracle.build(threads=threads)
+    pos, vel = w.pos_d, w.vel
+    ta = time.perf_counter()
+    for _ in range(steps):
+        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True, threads=threads)
+        pos, vel = r["pos_d"], r["vel"]
+    tc = time.perf_counter() - ta
+    return w.n * steps / tc, tc
+
+
+def oracle_baseline(args, w, dt):
+    """The FP64 oracle on the host cores: the OpenMP build on every core (the
+    headline baseline) and the single-thread build, each on a bounded
+    sample of whole steps of the same workload."""
+    cores = os.cpu_count() or 1
+    name = args.workload.replace("_", " ")
+    big = w.n > 8_000_000
+    k1 = args.cpu_steps if args.cpu_steps > 0 else (1 if big else 2)
+    v1, t1 = oracle_rate(w, dt, k1, threads=False)
+    single = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{k1} full oracle step{'s' if k1 > 1 else ''} (dt {dt:g}) of the same {name} from its "
+                        f"initial state (FP64 C, single thread), {t1:.1f} s"}
+    try:
+        kn = max(k1, 2 if big else 4)
+        vn, tn = oracle_rate(w, dt, kn, threads=True)
+    except Exception as e:   # no OpenMP on this host: the single-thread figure stands alone
+        single["all_cores_unavailable"] = str(e)[:200]
+        return single
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{kn} full oracle steps (dt {dt:g}) of the same {name} from its initial state (FP64 C, "
+                      f"OpenMP build over the independent particle and cell loops, {cores} threads, results "
+                      f"bit-identical to the single-thread build), {tn:.1f} s",
+            "single_thread": single}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
     import synth
     import oracle
-    oracle.build()
     w = getattr(synth, args.workload)(seed=0)
     n = w.n
     dt = float(w.dt)
+    cores = os.cpu_count() or 1
+    threads = True
+    try:
+        oracle.build(threads=True)
+    except Exception:
+        threads, cores = False, 1
+        oracle.build()
     # a bounded sample: whole steps of the workload, as many as fit a few minutes
     wu = min(max(0, args.warmup), 1)
-    ks = max(1, min(args.steps, 3 if n > 8_000_000 else 8))
+    ks = max(1, min(args.steps, 4 if n > 8_000_000 else 8))
     pos, vel = w.pos_d, w.vel
     for _ in range(wu):
-        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True)
+        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True, threads=threads)
         pos, vel = r["pos_d"], r["vel"]
     ta = time.perf_counter()
     for _ in range(ks):
-        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True)
+        r = oracle.step(w.desc, pos, vel, w.u_fine, dt=dt, want_eps_fine=True, threads=threads)
         pos, vel = r["pos_d"], r["vel"]
     tc = time.perf_counter() - ta
     value = n * ks / tc
     sample = (f"{ks} full oracle steps (warm-up {wu}, dt {dt:g}, each from the state the last one advanced) of the "
-              f"{args.workload.replace('_', ' ')}, FP64 C, single thread")
+              f"{args.workload.replace('_', ' ')}, FP64 C, "
+              + (f"OpenMP build on {cores} threads (bit-identical to the single-thread build)" if threads
+                 else "single thread"))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": ks, "warmup": wu, "ms_per_step": 1e3 * tc / ks, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.workload, w),
                        "particles": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

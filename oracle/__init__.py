@@ -26,23 +26,28 @@ _SRC = os.path.join(_HERE, "cg_oracle.c")
 _HDR = os.path.join(_HERE, "cg_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libcg_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libcg_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 NSUMS = 16
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, no FMA contraction)."""
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile the oracle shared library (gcc, no FMA contraction).  With
+    threads the same source is built with -fopenmp: its loops over
+    independent particles and cells run on every host core, with results
+    bit-identical to the single-thread build."""
     os.makedirs(_BUILD, exist_ok=True)
+    out = _LIB_OMP if threads else _LIB
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-        tmp = _LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-ffp-contract=off", "-fno-fast-math"] + (["-fopenmp"] if threads else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class Grid(C.Structure):
@@ -78,11 +83,10 @@ def box_grid(origin, extent, n) -> BoxGrid:
     return g
 
 
-def _load():
-    global _lib
+def _load(threads: bool = False):
     with _lock:
-        if _lib is None:
-            lib = C.CDLL(build())
+        if threads not in _libs:
+            lib = C.CDLL(build(threads=threads))
             P = C.POINTER
             d, i32, i64 = C.c_double, C.c_int32, C.c_int64
             pd, pi = P(d), P(i32)
@@ -111,8 +115,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[threads] = lib
+    return _libs[threads]
 
 
 def _f64(a) -> np.ndarray:
@@ -348,11 +352,12 @@ def euler(desc, pos_d, vel, force, dt):
     return pos, v
 
 
-def step(desc, pos_d, vel, u_fine, dt=0.0, want_var=True, want_eps_fine=False):
+def step(desc, pos_d, vel, u_fine, dt=0.0, want_var=True, want_eps_fine=False, threads=False):
     """One whole coupling step; returns a dict of float64 / int32 arrays.
     Particle arrays are copied; with dt > 0 the returned pos_d / vel are
-    the advanced state."""
-    lib = _load()
+    the advanced state.  threads: run the OpenMP build on every host core
+    (bit-identical results)."""
+    lib = _load(threads)
     g = grid(desc)
     pos = _f64(pos_d).reshape(-1, 4).copy()
     v = _f64(vel).reshape(-1, 4).copy()

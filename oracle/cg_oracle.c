@@ -6,7 +6,11 @@
  * CPU baseline of the benchmark; never by the CUDA library.
  *
  * Compile with -ffp-contract=off: every product and sum below is rounded
- * on its own, as written.
+ * on its own, as written.  The OpenMP pragmas mark loops whose iterations
+ * are independent (one particle, one cell, one fine cell each); a build
+ * with -fopenmp runs them on several threads with bit-identical results,
+ * and a build without it ignores them.  Sorts and global sums stay
+ * sequential.
  *
  * What the paper fixes and what is a reading of it:
  *  - Fig. 1 / Sec. 2.1: a coarse uniform "bulk" grid maps Lagrangian fields
@@ -130,6 +134,7 @@ void or_deposit_volume(const or_grid* G, int64_t n, const double* pos_d,
 {
     (void)n;
     geom g = geometry(G);
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < g.nbulk; ++c) {
         ksum k = {0.0, 0.0};
         for (int32_t i = cell_start[c]; i < cell_start[c + 1]; ++i)
@@ -149,6 +154,7 @@ void or_average(const or_grid* G, const double* u_fine, double* u_bulk, double* 
     const int r = G->r;
     const int64_t nxf = G->nf[0], nyf = G->nf[1];
     const double cnt = (double)r * r * r;
+#pragma omp parallel for schedule(static)
     for (int K = 0; K < g.nb[2]; ++K)
     for (int J = 0; J < g.nb[1]; ++J)
     for (int I = 0; I < g.nb[0]; ++I) {
@@ -310,6 +316,7 @@ int64_t or_drag(const or_grid* G, int64_t n, const double* pos_d, const double* 
                 const double* eps_bulk, const double* u_bulk, double* force)
 {
     int64_t nclamped = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nclamped)
     for (int64_t p = 0; p < n; ++p) {
         const double* x = &pos_d[4 * p];
         double eps_p, uf[3], s[3];
@@ -386,6 +393,7 @@ void or_deposit_momentum(const or_grid* G, int64_t n, const double* force,
                          const int32_t* cell_start, const int32_t* perm, double* S_bulk)
 {
     geom g = geometry(G);
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < g.nbulk; ++c) {
         for (int comp = 0; comp < 3; ++comp) {
             ksum k = {0.0, 0.0};
@@ -517,10 +525,11 @@ void or_map_project(const or_box_grid* bulk, const or_box_grid* fine, int ncomp,
 void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine)
 {
     geom g = geometry(G);
-    double v[8];
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < G->nf[2]; ++k)
     for (int j = 0; j < G->nf[1]; ++j)
     for (int i = 0; i < G->nf[0]; ++i) {
+        double v[8];
         double x[3] = {G->x0[0] + (i + 0.5) * g.h[0],
                        G->x0[1] + (j + 0.5) * g.h[1],
                        G->x0[2] + (k + 0.5) * g.h[2]};
@@ -533,6 +542,7 @@ void or_project(const or_grid* G, int ncomp, const double* bulk, double* fine)
 void or_euler(const or_grid* G, int64_t n, double* pos_d, double* vel,
               const double* force, double dt)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) {
         double m = G->rho_p * sphere_volume(pos_d[4 * p + 3]);
         for (int a = 0; a < 3; ++a) {

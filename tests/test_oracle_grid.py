@@ -364,3 +364,21 @@ def test_projection_constant_and_linear_interior():
                     assert fine[k, j, i] == pytest.approx(1.0 + b @ x, rel=1e-13)
     const = oracle.project(desc, np.full(int(np.prod(nb)), 2.5))
     assert np.all(np.abs(const - 2.5) < 1e-15)
+
+
+def test_threaded_build_is_bit_identical():
+    """The OpenMP build of the oracle (its loops over independent particles,
+    cells and fine cells on every host core) gives the single-thread
+    build's step bit for bit, Euler advance included."""
+    import os
+    import oracle
+    import synth
+    w = synth.small_clustered_bed(seed=2)
+    a = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, dt=w.dt, want_eps_fine=True)
+    b = oracle.step(w.desc, w.pos_d, w.vel, w.u_fine, dt=w.dt, want_eps_fine=True, threads=True)
+    for k, v in a.items():
+        if isinstance(v, np.ndarray):
+            assert np.array_equal(v, b[k]), k
+        else:
+            assert v == b[k], k
+    assert (os.cpu_count() or 1) >= 1
