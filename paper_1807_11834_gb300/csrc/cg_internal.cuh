@@ -616,9 +616,10 @@ __device__ __forceinline__ void seg_chunk_range(long long base, long long n, con
 // segment's total.  load(i, v) fills the K values of slot i; emit(key, tot)
 // receives each segment's compensated total on the lane of its last slot.
 // The next round's slots are loaded before the current one is reduced.
-template <typename T, int K, typename Load, typename Emit, int B = 4>   // B: rounds loaded ahead of the reduction
+template <typename T, int K, typename Load, typename Emit>
 __device__ __forceinline__ void seg_rounds(long long s, long long t, const int32_t* __restrict__ key_sorted,
                                            Load load, Emit emit) {
+    constexpr int B = 4;   // rounds loaded ahead of the reduction
     const int lane = threadIdx.x & 31;
     CSum<T> carry[K];
     int carry_key = -1;

@@ -193,69 +193,6 @@ k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ 
                         launch_blk(), Bs, pos_out, vel_out);
 }
 
-// ----------------------------------------------------------------------
-// Drag over the sorted slots with the reaction deposited in the same pass
-// (the sorted step).  Warps own chunks of slots as the deposits do; slot s
-// takes particle perm[s], whose force goes to its caller-order place in F
-// and, at once, into the segmented sum of its cell's reaction, in exactly
-// the order of the deposit over sorted force records (so S_B has the same
-// bits as the two-pass form).  The particle, advanced when EULER, leaves at
-// slot s of pos_out / vel_out: the particles of this binning in cell order.
-// ----------------------------------------------------------------------
-template <typename T, bool EULER>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
-k_drag_sorted(const T* __restrict__ pos, const T* __restrict__ vel, long long n, GridDev g, Phys<T> P,
-              const T* __restrict__ bulk4, const int32_t* __restrict__ perm, const int32_t* __restrict__ key_sorted,
-              const int32_t* __restrict__ cs, T* __restrict__ F, T* __restrict__ S, T* __restrict__ pos_out,
-              T* __restrict__ vel_out, T dt, T* __restrict__ part_drag, T* __restrict__ part_mom, long long pstride,
-              int do_sums, unsigned long long* __restrict__ status, T* __restrict__ Bs) {
-    pdl_wait();
-    const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    T lane_sums[kDragSums];
-#pragma unroll
-    for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
-    int clamped_total = 0;
-    CSum<T> sv[3];
-    for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
-        long long s, t;
-        seg_chunk_range(base, n, key_sorted, cs, s, t);
-        // two rounds of 32 slots loaded (and their drag formed) ahead of the reduction
-        auto load = [&](long long i, T (&v)[3]) {
-                const int p = __ldg(perm + i);
-                const V4<T> x = ld4(pos, p), u = ld4(vel, p);
-                const DragOne<T> r = drag_one<T, EULER>(x, u, g, P, bulk4, dt);
-                clamped_total += r.cl;
-                F[p] = r.f[0];
-                F[n + p] = r.f[1];
-                F[2 * n + p] = r.f[2];
-                if (Bs) st4(Bs, i, r.beta, r.beta * u.x, r.beta * u.y, r.beta * u.z);
-                st4(pos_out, i, r.x[0], r.x[1], r.x[2], x.w);
-                st4(vel_out, i, r.u[0], r.u[1], r.u[2], u.w);
-                drag_lane_sums(lane_sums, r);
-                v[0] = r.f[0];
-                v[1] = r.f[1];
-                v[2] = r.f[2];
-        };
-        auto emit = [&](int key, CSum<T> (&a)[3]) { reaction_emit<T>(g, S, key, a, sv); };
-        seg_rounds<T, 3, decltype(load), decltype(emit), 2>(s, t, key_sorted, load, emit);
-    }
-    int wsum = clamped_total;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
-    if ((threadIdx.x & 31) == 0 && wsum) {
-        atomicAdd(&status[ST_CLAMPED], (unsigned long long)wsum);
-        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
-    }
-    if (do_sums) {
-        CSum<T> acc[kDragSums];
-#pragma unroll
-        for (int k = 0; k < kDragSums; ++k) acc[k].add(lane_sums[k]);
-        block_sums<T, kDragSums>(acc, part_drag, pstride, blockIdx.x);
-        block_sums<T, 3>(sv, part_mom, pstride, blockIdx.x);
-    }
-}
-
 // Batched drag with the fused sorted-order force record (FP32 instances).
 template <bool EULER>
 __global__ void __launch_bounds__(256) kb_drag(BLaunch L, float dt) {
@@ -282,39 +219,6 @@ int batch_drag_occupancy() {
     return occ > 0 ? occ : 1;
 }
 
-// The sorted step's drag: one pass over the sorted slots with the reaction
-// (and the semi-implicit coefficients' records) formed in it.
-static cg_status launch_drag_sorted(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force,
-                                    void* S_bulk, bool sums, double dt, void* coef_bulk, void* pos_out,
-                                    void* vel_out) {
-    CG_CUDA(cudaMemsetAsync(S_bulk, 0, 3 * g->tsize * (size_t)g->gd.nbulk, g->stream));
-    const long long chunks = (n + kSegChunk - 1) / kSegChunk;
-    const long long per_sm = g->fp64 ? 1 : 3;   // the launch bounds' resident blocks: one wave
-    const unsigned nblk = (unsigned)std::max(1LL, std::min((chunks + 7) / 8, (long long)g->num_sms * per_sm));
-    g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
-    g->part_blocks[PS_MOM] = sums ? (long long)nblk : -1;
-    void* Bs = nullptr;
-    if (coef_bulk) {
-        if (g->Bs.bytes < 4 * g->tsize * (size_t)n) return CG_ERR_INVALID_ARG;   // sized by the step
-        Bs = g->Bs.p;
-    }
-#define CG_DRAGS(T, E)                                                                                        \
-    CG_LAUNCH(g, "drag_sorted", (k_drag_sorted<T, E>), nblk, 256, 0, (const T*)pos_d, (const T*)vel, n, g->gd,    \
-              phys_of<T>(g->gd), (const T*)g->bulk4, (const int32_t*)g->perm, (const int32_t*)g->key_sorted,        \
-              (const int32_t*)g->cell_start, (T*)force, (T*)S_bulk, (T*)pos_out, (T*)vel_out, (T)dt,               \
-              (T*)part_ptr(g, PS_DRAG), (T*)part_ptr(g, PS_MOM), (long long)nblk, (int)sums, g->status, (T*)Bs)
-    if (g->fp64) {
-        if (dt > 0.0) CG_DRAGS(double, true);
-        else CG_DRAGS(double, false);
-    } else {
-        if (dt > 0.0) CG_DRAGS(float, true);
-        else CG_DRAGS(float, false);
-    }
-#undef CG_DRAGS
-    if (coef_bulk) CG_TRY(launch_deposit_implicit(g, n, coef_bulk));
-    return CG_OK;
-}
-
 cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* vel, void* force, void* S_bulk,
                       bool sums, double dt, void* coef_bulk, void* pos_out, void* vel_out) {
     const bool euler = dt > 0.0;
@@ -326,8 +230,6 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
     g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
     void* Fs = S_bulk ? g->Fs : nullptr;
     if (pos_out && !Fs) return CG_ERR_INVALID_ARG;   // the sorted slots come with the fused reaction
-    if (pos_out && n > 0) return launch_drag_sorted(g, n, pos_d, vel, force, S_bulk, sums, dt, coef_bulk, pos_out,
-                                                    vel_out);
     void* Bs = nullptr;
     if (coef_bulk && n > 0) {
         // sized by the step before its first launch
