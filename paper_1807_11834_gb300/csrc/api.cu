@@ -422,6 +422,7 @@ cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, in
 static cg_status check_n(long long n) { return (n < 0 || n > 2147483647LL) ? CG_ERR_OUT_OF_RANGE : CG_OK; }
 
 static cg_status copy_bins(cg_grids* g, long long n, int32_t* cell_out, int32_t* perm_out, int32_t* cs_out) {
+    if (cell_out && n) CG_TRY(ensure_keys(g, n));
     if (cell_out && n)
         CG_CUDA(cudaMemcpyAsync(cell_out, g->key, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, g->stream));
     if (perm_out && n)

@@ -903,10 +903,14 @@ static cg_status bin_rank(cg_grids* g, long long n, const T* pos, int ntiles, do
 // and the arrival ranks in key2 (the keys in key, the diameters in vol).
 cg_status launch_cellsort_tail(cg_grids* g, long long n, const int32_t* cs, const int32_t* run_if) {
     const long long nbulk = g->gd.nbulk;
-    const long long pb = std::min<long long>((n + 512 * kPlaceItems - 1) / (512 * kPlaceItems), (long long)g->num_sms * 4);
+    // as the device's fallback (run_if set) the kernels are usually idle: one
+    // grid-stride CTA per SM keeps an idle launch short
+    const long long per_sm = run_if ? 1 : 4;
+    const long long pb = std::min<long long>((n + 512 * kPlaceItems - 1) / (512 * kPlaceItems),
+                                             (long long)g->num_sms * per_sm);
     CG_LAUNCH(g, "bin_place", k_bin_place, (unsigned)pb, 512, 0, g->key, g->key2, cs, n, g->val1, run_if);
     const long long sb = std::min<long long>((nbulk + kGroupCells * kSegSortWarps - 1) / (kGroupCells * kSegSortWarps),
-                                             (long long)g->num_sms * 4);
+                                             (long long)g->num_sms * per_sm);
     if (g->fp64)
         CG_LAUNCH(g, "bin_seg_sort", k_seg_sort<double>, (unsigned)sb, kSegSortWarps * 32, 0, cs, nbulk, g->val1,
                   g->key1, g->perm, g->key_sorted, g->inv_perm, (const double*)g->vol, (double*)g->vol_sorted, run_if);
@@ -1073,10 +1077,12 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
     g->hint_ident = nullptr;
     g->n_binned = -1;
     g->vol_valid = false;
+    g->key_valid = true;   // written by every path but the identity-hint rebinning
     if (rebin) {
         CG_TRY(launch_rebin(g, n, pos_d, ident, eps_fill, rec_fill, eps_t_fill));
         g->n_binned = n;
         g->vol_valid = true;
+        g->key_valid = !ident;
         g->hint_n = n;
         return CG_OK;
     }

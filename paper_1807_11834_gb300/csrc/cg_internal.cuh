@@ -179,6 +179,7 @@ struct cg_grids {
     void* vol_sorted = nullptr;    // [cap] T particle diameter, sorted order
     void* Fs = nullptr;            // [cap] T4 drag force, sorted order
     bool vol_valid = false;        // vol_sorted matches the binned positions
+    bool key_valid = false;        // key holds the binning's caller-order cells (see ensure_keys)
     // incremental rebinning (rebin.cu): a binning of hint_n particles held in
     // perm / key_sorted / cell_start is where the next binning of the same
     // count starts; hint_ident is the particle array the last sorted step
@@ -322,6 +323,9 @@ inline long long rebin_small_ints(long long nbulk, long long nblk) {
 // the particles are that binning's sorted output (particle i at old slot i).
 cg_status launch_rebin(cg_grids* g, long long n, const void* pos_d, bool ident, double* eps_fill, void* rec_fill,
                        void* eps_t_fill);
+// g->key of the last binning (an identity-hint rebinning leaves it to be
+// formed from its records on demand).
+cg_status ensure_keys(cg_grids* g, long long n);
 cg_status ensure_partials(cg_grids* g, long long n);
 
 // eps_fill (nullable): also set this [n_b] porosity to 1 (when n > 0), and

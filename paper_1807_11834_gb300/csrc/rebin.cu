@@ -167,12 +167,12 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
         const long long s = base + k * kRebinThreads + threadIdx.x;
         if (s >= n) continue;
         if (IDENT) {
+            // the cell itself is kept only in rkn below (key is formed from it on demand)
             int outside = 0;
             const V4<T>& v = pv[k];
             if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
             cnk[k] = cell_of(v, g, outside);
             n_out += outside;
-            key[s] = cnk[k];
             vol[s] = v.w;   // the diameter: the porosity forms the volume as an exact pair
         } else {
             cnk[k] = __ldg(key + idk[k]);
@@ -225,25 +225,23 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
     if (IDENT) eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
 }
 
-// New count of every cell (the fallback counts into cnt itself).
-__global__ void __launch_bounds__(256)
-k_rebin_cells(const int32_t* __restrict__ cs_old, long long nbulk, const int32_t* __restrict__ dep,
-              const int32_t* __restrict__ arr, int32_t* __restrict__ cnt, const int32_t* __restrict__ ctr) {
-    pdl_wait();
-    if (ctr[RB_FALLBACK]) return;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nbulk;
-         c += (long long)gridDim.x * blockDim.x)
-        cnt[c] = __ldg(cs_old + c + 1) - __ldg(cs_old + c) - __ldg(dep + c) + __ldg(arr + c);
-}
-
-// Fallback: per-cell counts and arrival ranks of the per-cell sort, from the
-// cells already formed (consecutive lanes on consecutive particles, one
-// atomic per run of equal cells).
+// The new count of every cell; or, when the device falls back to the
+// per-cell sort, that sort's per-cell counts and arrival ranks (consecutive
+// lanes on consecutive particles, one atomic per run of equal cells), from
+// the cells already formed (IDENT: from rkn, whose cells are written to key
+// here for the sort's placement).
+template <bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
-k_rebin_rank(const int32_t* __restrict__ key, long long n, int32_t* __restrict__ cnt,
-             int32_t* __restrict__ arrival, const int32_t* __restrict__ ctr) {
+k_rebin_cells(const int32_t* __restrict__ cs_old, long long nbulk, const int32_t* __restrict__ dep,
+              const int32_t* __restrict__ arr, int32_t* __restrict__ cnt, const int32_t* __restrict__ ctr,
+              int32_t* __restrict__ key, const int32_t* __restrict__ rkn, long long n, int32_t* __restrict__ arrival) {
     pdl_wait();
-    if (!ctr[RB_FALLBACK]) return;
+    if (!ctr[RB_FALLBACK]) {
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nbulk;
+             c += (long long)gridDim.x * blockDim.x)
+            cnt[c] = __ldg(cs_old + c + 1) - __ldg(cs_old + c) - __ldg(dep + c) + __ldg(arr + c);
+        return;
+    }
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (long long base = (long long)blockIdx.x * kRebinTile; base < n; base += (long long)gridDim.x * kRebinTile) {
@@ -252,7 +250,16 @@ k_rebin_rank(const int32_t* __restrict__ key, long long n, int32_t* __restrict__
         for (int k = 0; k < kRebinItems; ++k) {
             const long long p = base + k * kRebinThreads + threadIdx.x;
             const bool valid = p < n;
-            ck[k] = valid ? __ldg(key + p) : -1;
+            ck[k] = -1;
+            if (valid) {
+                if (IDENT) {
+                    const int r = __ldg(rkn + p);
+                    ck[k] = r >= 0 ? r : ~r;
+                    key[p] = ck[k];
+                } else {
+                    ck[k] = __ldg(key + p);
+                }
+            }
             lk[k] = run_head_length(ck[k], valid);
         }
 #pragma unroll
@@ -265,6 +272,17 @@ k_rebin_rank(const int32_t* __restrict__ key, long long n, int32_t* __restrict__
             const int o = __shfl_sync(full, old[k], head < 0 ? 0 : head);
             if (p < n) arrival[p] = o + lane - head;
         }
+    }
+}
+
+// The caller-order cells of an identity-hint binning, from the records
+// (a caller asks for them, or the handle needs them).
+__global__ void __launch_bounds__(256) k_rebin_keys(const int32_t* __restrict__ rkn, long long n,
+                                                    int32_t* __restrict__ key) {
+    pdl_wait();
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int r = __ldg(rkn + p);
+        key[p] = r >= 0 ? r : ~r;
     }
 }
 
@@ -421,12 +439,16 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
                   (const int32_t*)g->perm, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rid, g->rb_rkn,
                   R.arr, R.dep, g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr,
                   (T*)nullptr);
-    const unsigned cgrid = (unsigned)std::min<long long>((nbulk + 255) / 256, (long long)g->num_sms * 8);
-    CG_LAUNCH(g, "rebin_cells", k_rebin_cells, cgrid, 256, 0, (const int32_t*)g->cell_start, nbulk,
-              (const int32_t*)R.dep, (const int32_t*)R.arr, R.cnt, (const int32_t*)R.ctr);
-    const unsigned rgrid = (unsigned)std::min<long long>(nblk, (long long)g->num_sms * 4);
-    CG_LAUNCH(g, "rebin_rank", k_rebin_rank, rgrid, kRebinThreads, 0, (const int32_t*)g->key, n, R.cnt, g->key2,
-              (const int32_t*)R.ctr);
+    const unsigned cgrid = (unsigned)std::max<long long>(1, std::min<long long>(std::max((nbulk + 255) / 256, nblk),
+                                                                               (long long)g->num_sms * 8));
+    if (ident)
+        CG_LAUNCH(g, "rebin_cells", k_rebin_cells<true>, cgrid, kRebinThreads, 0, (const int32_t*)g->cell_start,
+                  nbulk, (const int32_t*)R.dep, (const int32_t*)R.arr, R.cnt, (const int32_t*)R.ctr, g->key,
+                  (const int32_t*)g->rb_rkn, n, g->key2);
+    else
+        CG_LAUNCH(g, "rebin_cells", k_rebin_cells<false>, cgrid, kRebinThreads, 0, (const int32_t*)g->cell_start,
+                  nbulk, (const int32_t*)R.dep, (const int32_t*)R.arr, R.cnt, (const int32_t*)R.ctr, g->key,
+                  (const int32_t*)g->rb_rkn, n, g->key2);
     {
         const int32_t* in[3] = {R.cnt, R.arr, R.blk};
         int32_t* out[3] = {R.cnt, R.arr, R.blk};
@@ -454,6 +476,16 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
     // fallback: placement and per-cell sort from the scanned counts
     CG_TRY(launch_cellsort_tail(g, n, R.cnt, R.ctr + RB_FALLBACK));
     CG_CUDA(cudaMemcpyAsync(g->cell_start, R.cnt, sizeof(int32_t) * (nbulk + 1), cudaMemcpyDeviceToDevice, g->stream));
+    return CG_OK;
+}
+
+// The caller-order cells of the last binning (g->key), formed from the
+// mover records when an identity-hint binning left them out.
+cg_status ensure_keys(cg_grids* g, long long n) {
+    if (g->key_valid || n <= 0) return CG_OK;
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)g->num_sms * 8);
+    CG_LAUNCH(g, "rebin_keys", k_rebin_keys, grid, 256, 0, (const int32_t*)g->rb_rkn, n, g->key);
+    g->key_valid = true;
     return CG_OK;
 }
 
