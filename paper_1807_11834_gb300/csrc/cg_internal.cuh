@@ -337,10 +337,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
 // of occupied cells into the drag record and its T copy.
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
                                 bool prefilled = false, void* rec = nullptr, void* eps_t = nullptr);
-// F_caller (nullable): the caller-order forces [3][n], read through the
-// permutation instead of the sorted force record.
-cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums,
-                                      const void* F_caller = nullptr);
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
 // Gather the particle records into the binned order (cg_reorder_particles).
 cg_status launch_reorder(cg_grids* g, long long n, const void* pos_d, const void* vel, void* pos_out, void* vel_out);
 // Semi-implicit coefficients [4][n_b] (A, b) from the drag's sorted (beta, beta u) records.

@@ -125,14 +125,12 @@ k_deposit_volume_sorted(const T* __restrict__ dsorted, long long n, const int32_
 
 // Reaction from the forces the drag wrote in sorted order (T4 per slot);
 // S_B V_B accumulated as an exact float-float product for the diagnostics.
-// PERM: slot s takes the caller-order force of particle perm[s] instead (the
-// same values in the same order, so the same bits).
-template <typename T, bool PERM = false>
+template <typename T>
 __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ Fs, long long n,
                                                           const int32_t* __restrict__ key_sorted,
                                                           const int32_t* __restrict__ cs, const GridDev& g,
                                                           T* __restrict__ S, T* __restrict__ part, long long pstride,
-                                                          int do_sums, Blk b, const int32_t* __restrict__ perm = nullptr) {
+                                                          int do_sums, Blk b) {
     const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = b.n * (blockDim.x >> 5);
     CSum<T> sv[3];
@@ -142,17 +140,10 @@ __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ 
         seg_rounds<T, 3>(
             s, t, key_sorted,
             [&](long long i, T (&v)[3]) {
-                if (PERM) {
-                    const long long p = __ldg(perm + i);
-                    v[0] = __ldg(Fs + p);
-                    v[1] = __ldg(Fs + n + p);
-                    v[2] = __ldg(Fs + 2 * n + p);
-                } else {
-                    const V4<T> f = ld4(Fs, i);
-                    v[0] = f.x;
-                    v[1] = f.y;
-                    v[2] = f.z;
-                }
+                const V4<T> f = ld4(Fs, i);
+                v[0] = f.x;
+                v[1] = f.y;
+                v[2] = f.z;
             },
             [&](int key, CSum<T> (&a)[3]) { reaction_emit<T>(g, S, key, a, sv); });
     }
@@ -197,13 +188,13 @@ k_deposit_implicit(const T* __restrict__ Bs, long long n, const int32_t* __restr
     deposit_implicit_body<T>(Bs, n, key_sorted, cs, g, coef, launch_blk());
 }
 
-template <typename T, bool PERM>
+template <typename T>
 __global__ void __launch_bounds__(256)
 k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
                        const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
-                       long long pstride, int do_sums, const int32_t* __restrict__ perm) {
+                       long long pstride, int do_sums) {
     pdl_wait();
-    deposit_sorted_force_body<T, PERM>(Fs, n, key_sorted, cs, g, S, part, pstride, do_sums, launch_blk(), perm);
+    deposit_sorted_force_body(Fs, n, key_sorted, cs, g, S, part, pstride, do_sums, launch_blk());
 }
 
 // ----------------------------------------------------------------------
@@ -449,7 +440,7 @@ cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, dou
     return CG_OK;
 }
 
-cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums, const void* F_caller) {
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums) {
     CG_CUDA(cudaMemsetAsync(S_bulk, 0, 3 * g->tsize * (size_t)g->gd.nbulk, g->stream));
     void* part = part_ptr(g, PS_MOM);
     if (n == 0) {
@@ -459,19 +450,12 @@ cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bo
     }
     const unsigned nblk = seg_blocks(g, n);
     g->part_blocks[PS_MOM] = sums ? (long long)nblk : -1;
-    const bool by_perm = F_caller != nullptr;
-#define CG_DEPF(T, PM)                                                                                          \
-    CG_LAUNCH(g, "deposit_momentum", (k_deposit_sorted_force<T, PM>), nblk, 256, 0,                               \
-              (const T*)(PM ? F_caller : g->Fs), n, g->key_sorted, g->cell_start, g->gd, (T*)S_bulk, (T*)part,     \
-              (long long)nblk, (int)sums, (const int32_t*)g->perm)
-    if (g->fp64) {
-        if (by_perm) CG_DEPF(double, true);
-        else CG_DEPF(double, false);
-    } else {
-        if (by_perm) CG_DEPF(float, true);
-        else CG_DEPF(float, false);
-    }
-#undef CG_DEPF
+    if (g->fp64)
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<double>, nblk, 256, 0, (const double*)g->Fs, n,
+                  g->key_sorted, g->cell_start, g->gd, (double*)S_bulk, (double*)part, (long long)nblk, (int)sums);
+    else
+        CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<float>, nblk, 256, 0, (const float*)g->Fs, n,
+                  g->key_sorted, g->cell_start, g->gd, (float*)S_bulk, (float*)part, (long long)nblk, (int)sums);
     return CG_OK;
 }
 

@@ -112,9 +112,9 @@ __device__ __forceinline__ void drag_lane_sums(T (&ls)[kDragSums], const DragOne
 // ----------------------------------------------------------------------
 // Bs (nullable): the semi-implicit record (beta, beta u_p) of each particle,
 // written to its sorted slot beside the force record.
-// pos_out, vel_out (nullable): the particle records, advanced when EULER,
-// are written to their sorted slot of these arrays instead of in place (the
-// sorted step: the particles leave in this binning's order).
+// pos_out, vel_out (nullable, with Fs): the particle records, advanced when
+// EULER, are written to their sorted slot of these arrays instead of in
+// place (the sorted step: the particles leave in this binning's order).
 template <typename T, bool EULER, bool PREFETCH = true>
 __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
                                           const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
@@ -132,25 +132,24 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
     // them); the batched kernel, short of registers, loads it in turn
     V4<T> xn, vn;
     int slot_n = 0;
-    const bool need_slot = Fs || pos_out;
     long long p = b.id * blockDim.x + threadIdx.x;
     if (p < n) {
         xn = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
         vn = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
-        if (need_slot) slot_n = __ldg(inv_perm + p);
+        if (Fs) slot_n = __ldg(inv_perm + p);
     }
     for (; p < n; p += stride) {
         if (!PREFETCH && p != b.id * blockDim.x + threadIdx.x) {
             xn = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
             vn = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
-            if (need_slot) slot_n = __ldg(inv_perm + p);
+            if (Fs) slot_n = __ldg(inv_perm + p);
         }
         const V4<T> x = xn, v = vn;
         const int slot = slot_n;
         if (PREFETCH && p + stride < n) {
             xn = EULER ? ld4_plain(pos, p + stride) : ld4((const T*)pos, p + stride);
             vn = EULER ? ld4_plain(vel, p + stride) : ld4((const T*)vel, p + stride);
-            if (need_slot) slot_n = __ldg(inv_perm + p + stride);
+            if (Fs) slot_n = __ldg(inv_perm + p + stride);
         }
         const DragOne<T> r = drag_one<T, EULER>(x, v, g, P, bulk4, dt);
         clamped_total += r.cl;
@@ -229,11 +228,8 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
     const long long per_sm = g->fp64 ? 2 : 4;
     const unsigned nblk = (unsigned)std::max(1LL, std::min((n + 255) / 256, (long long)g->num_sms * per_sm));
     g->part_blocks[PS_DRAG] = sums ? (long long)nblk : -1;
-    // the sorted step's particles are nearly in slot order, so its reaction
-    // deposit reads the caller-order forces through the permutation and no
-    // sorted force record is written; otherwise the record goes to each slot
-    void* Fs = (S_bulk && !pos_out) ? g->Fs : nullptr;
-    if (pos_out && !S_bulk) return CG_ERR_INVALID_ARG;   // the sorted slots come with the binning of the step
+    void* Fs = S_bulk ? g->Fs : nullptr;
+    if (pos_out && !Fs) return CG_ERR_INVALID_ARG;   // the sorted slots come with the fused reaction
     void* Bs = nullptr;
     if (coef_bulk && n > 0) {
         // sized by the step before its first launch
@@ -254,7 +250,7 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
         }
 #undef CG_DRAGP
     }
-    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, sums, pos_out ? force : nullptr));
+    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, sums));
     if (coef_bulk) CG_TRY(launch_deposit_implicit(g, n, coef_bulk));
     return CG_OK;
 }
