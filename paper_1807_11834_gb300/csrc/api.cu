@@ -193,15 +193,14 @@ cg_status ensure_particle_capacity(cg_grids* g, long long n) {
     // default sort (at most cap / 257 cells after a count)
     g->hist_cap = std::max<long long>(ntiles << maxbits, cap / 256 + 2);
     CG_TRY(dalloc(&g->hist, sizeof(int32_t) * g->hist_cap));
-    // incremental rebinning: a record per old slot, movers up to a quarter of
-    // the particles (more fall back to the full sort), per-cell and per-block
-    // counts
+    // incremental rebinning: records per old slot, room for every particle to
+    // move (each block of old slots has its own part of the mover list), the
+    // arrival lists, per-cell and per-block counts
     g->rb_nblk = (cap + kRebinTile - 1) / kRebinTile;
-    g->rb_mov_cap = std::max<long long>(4096, cap / 4);
     CG_TRY(dalloc(&g->rb_rid, sizeof(int32_t) * cap));
     CG_TRY(dalloc(&g->rb_rkn, sizeof(int32_t) * cap));
-    CG_TRY(dalloc(&g->rb_mov, sizeof(int4) * g->rb_mov_cap));
-    CG_TRY(dalloc(&g->rb_arr, sizeof(int32_t) * g->rb_mov_cap));
+    CG_TRY(dalloc(&g->rb_mov, sizeof(int2) * g->rb_nblk * kRebinTile));
+    CG_TRY(dalloc(&g->rb_arr, sizeof(int2) * cap));
     CG_TRY(dalloc(&g->rb_small, sizeof(int32_t) * rebin_small_ints(g->gd.nbulk, g->rb_nblk)));
     const long long cells_blk = (g->gd.nbulk + 1 + kScanItems - 1) / kScanItems;
     g->scan_cap = std::max((g->hist_cap + kScanItems - 1) / kScanItems + cells_blk,

@@ -188,10 +188,10 @@ struct cg_grids {
     const void* hint_ident = nullptr;
     int32_t* rb_rid = nullptr;     // [cap] per old slot: its particle id (the caller's order kept)
     int32_t* rb_rkn = nullptr;     // [cap] per old slot: the new cell, complemented for a mover
-    int4* rb_mov = nullptr;        // [rb_mov_cap] movers: (id, new cell, arrival rank, unused)
-    int32_t* rb_arr = nullptr;     // [rb_mov_cap] arrivals, grouped by cell
-    int32_t* rb_small = nullptr;   // new counts / starts, arrivals, departures per cell; block departures; counters
-    long long rb_mov_cap = 0, rb_nblk = 0;
+    int2* rb_mov = nullptr;        // [rb_nblk * kRebinTile] movers, each block of old slots its own part: (id, cell | rank << 22)
+    int2* rb_arr = nullptr;        // [cap] arrivals grouped by cell: (id, cell)
+    int32_t* rb_small = nullptr;   // new counts / starts, arrivals, departures per cell; block movers; counters
+    long long rb_nblk = 0;
     int32_t* hist = nullptr;       // [2^digit * ntiles]
     int32_t* scan_part = nullptr;  // scan block partials
     long long hist_cap = 0, scan_cap = 0;

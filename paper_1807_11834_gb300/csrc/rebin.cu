@@ -24,9 +24,10 @@
 //
 // Old slot s holds particle perm_old[s] when the caller kept its particle
 // order, or particle s when the particles are the sorted output of the last
-// step (cg_step_sorted; the identity hint).  When more than a quarter of the
-// particles moved, or a cell receives more than kRebinMaxArrivals movers,
-// the device falls back to the per-cell sort: both paths are launched and
+// step (cg_step_sorted; the identity hint).  When a cell receives more than
+// kRebinMaxArrivals movers (the movers' searches and counts grow with the
+// arrivals of their cell) the device falls back to the per-cell sort: both
+// paths are launched and
 // each kernel checks a device flag, so a captured CUDA graph takes the
 // right path on every replay.
 #include <algorithm>
@@ -37,7 +38,8 @@ namespace cg {
 
 namespace {
 
-enum { RB_NMOV = 0, RB_FALLBACK = 1 };
+enum { RB_FALLBACK = 0 };
+constexpr int kCellBits = 22;   // a mover entry packs its new cell (< 2^22) and arrival rank (< 2^8)
 
 struct RebinPtrs {
     int32_t* cnt;       // [n_b + 1] new counts, then (scanned in place) new starts
@@ -129,15 +131,15 @@ k_rebin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restri
 // every old slot, complemented for a mover (rkn), and the old id (rid, only
 // when the particles kept the caller's order); per mover one departure
 // from its old cell, one arrival (with its rank) in its new cell and an
-// entry of the mover list, whose slots the block takes with one atomic; the
-// departures of each block of old slots.  IDENT: old slot s holds particle
+// entry in the block's own part of the mover list (kRebinTile entries per
+// block: no atomic decides a position); the movers of each block.  IDENT: old slot s holds particle
 // s, whose cell and diameter are formed here.
 template <typename T, bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
 k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* __restrict__ perm_old,
              const int32_t* __restrict__ ks_old, int32_t* __restrict__ key, T* __restrict__ vol,
              int32_t* __restrict__ rid, int32_t* __restrict__ rkn, int32_t* __restrict__ arr,
-             int32_t* __restrict__ dep, int4* __restrict__ mov, long long mov_cap, int32_t* __restrict__ blk_dep,
+             int32_t* __restrict__ dep, int2* __restrict__ mov, int32_t* __restrict__ blk_dep,
              int32_t* __restrict__ ctr, unsigned long long* __restrict__ status, double* __restrict__ eps_fill,
              T* __restrict__ rec_fill, T* __restrict__ eps_t_fill) {
     pdl_wait();
@@ -203,20 +205,17 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
             t += s_cnt[w];
         }
         blk_dep[blockIdx.x] = t;
-        const int b0 = t ? atomicAdd(&ctr[RB_NMOV], t) : 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) s_base[w] += b0;
     }
     __syncthreads();
     if (wc) {
-        long long idx = s_base[warp];
+        long long idx = base + s_base[warp];
 #pragma unroll
         for (int k = 0; k < kRebinItems; ++k) {
             if (mb[k] >> lane & 1u) {
                 const long long j = idx + __popc(mb[k] & lanemask_lt());
                 atomicAdd(&dep[cok[k]], 1);
                 const int r = atomicAdd(&arr[cnk[k]], 1);
-                if (j < mov_cap && r < kRebinMaxArrivals) mov[j] = make_int4(idk[k], cnk[k], r, 0);
+                if (r < kRebinMaxArrivals) mov[j] = make_int2(idk[k], cnk[k] | (r << kCellBits));
                 else ctr[RB_FALLBACK] = 1;
             }
             idx += __popc(mb[k]);
@@ -286,23 +285,29 @@ __global__ void __launch_bounds__(256) k_rebin_keys(const int32_t* __restrict__ 
     }
 }
 
-// Each mover into the arrival list of its new cell, at its arrival rank.
+// Each mover into the arrival list of its new cell, at its arrival rank:
+// one warp per block of old slots walks that block's movers.
 __global__ void __launch_bounds__(256)
-k_rebin_place(const int4* __restrict__ mov, const int32_t* __restrict__ arr_start, int32_t* __restrict__ arr_list,
-              const int32_t* __restrict__ ctr) {
+k_rebin_place(const int2* __restrict__ mov, const int32_t* __restrict__ blk_start, long long nblk,
+              const int32_t* __restrict__ arr_start, int2* __restrict__ arr_list, const int32_t* __restrict__ ctr) {
     pdl_wait();
     if (ctr[RB_FALLBACK]) return;
-    const long long nm = ctr[RB_NMOV];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
-        const int4 m = mov[i];
-        arr_list[__ldg(arr_start + m.y) + m.z] = m.x;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblk; b += nw) {
+        const int cnt = __ldg(blk_start + b + 1) - __ldg(blk_start + b);
+        for (int j = lane; j < cnt; j += 32) {
+            const int2 m = mov[b * kRebinTile + j];
+            const int c = m.y & ((1 << kCellBits) - 1), r = m.y >> kCellBits;
+            arr_list[__ldg(arr_start + c) + r] = make_int2(m.x, c);
+        }
     }
 }
 
 // Arrivals in the list [a0, a1) with an id below i.
-__device__ __forceinline__ int arrivals_below(const int32_t* __restrict__ arr_list, int a0, int a1, int i) {
+__device__ __forceinline__ int arrivals_below(const int2* __restrict__ arr_list, int a0, int a1, int i) {
     int a = 0;
-    for (int q = a0; q < a1; ++q) a += __ldg(arr_list + q) < i;
+    for (int q = a0; q < a1; ++q) a += __ldg(&arr_list[q].x) < i;
     return a;
 }
 
@@ -325,7 +330,7 @@ template <typename T, bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
 k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
              const int32_t* __restrict__ blk_start, const int32_t* __restrict__ arr_start,
-             const int32_t* __restrict__ arr_list, const T* __restrict__ vol, int32_t* __restrict__ perm,
+             const int2* __restrict__ arr_list, const T* __restrict__ vol, int32_t* __restrict__ perm,
              int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, T* __restrict__ vol_sorted,
              const int32_t* __restrict__ ctr) {
     pdl_wait();
@@ -389,16 +394,16 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
 // stayers before that point) and the arrivals with an id below it.
 template <typename T, bool IDENT>
 __global__ void __launch_bounds__(256)
-k_rebin_movers(const int4* __restrict__ mov, const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn,
-               long long n, const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
-               const int32_t* __restrict__ arr_start, const int32_t* __restrict__ arr_list, const T* __restrict__ vol,
-               int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
-               T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
+k_rebin_movers(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
+               const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
+               const int32_t* __restrict__ arr_start, const int2* __restrict__ arr_list, long long nbulk,
+               const T* __restrict__ vol, int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
+               int32_t* __restrict__ inv_perm, T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
     pdl_wait();
     if (ctr[RB_FALLBACK]) return;
-    const long long nm = ctr[RB_NMOV];
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += (long long)gridDim.x * blockDim.x) {
-        const int4 m = mov[j];
+    const long long nm = __ldg(arr_start + nbulk);   // all arrivals
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nm; q += (long long)gridDim.x * blockDim.x) {
+        const int2 m = arr_list[q];
         const int i = m.x, c = m.y;
         const int o0 = __ldg(cs_old + c), o1 = __ldg(cs_old + c + 1);
         int lo = o0, hi = o1;
@@ -412,7 +417,7 @@ k_rebin_movers(const int4* __restrict__ mov, const int32_t* __restrict__ rid, co
             }
         }
         int stay = 0;
-        for (int q = o0; q < lo; ++q) stay += __ldg(rkn + q) >= 0;
+        for (int p = o0; p < lo; ++p) stay += __ldg(rkn + p) >= 0;
         const int a0 = __ldg(arr_start + c), a1 = __ldg(arr_start + c + 1);
         const long long ns = (long long)__ldg(cs_new + c) + stay + arrivals_below(arr_list, a0, a1, i);
         emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
@@ -433,12 +438,11 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
     if (ident)
         CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, true>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
                   (const int32_t*)nullptr, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rid, g->rb_rkn,
-                  R.arr, R.dep, g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, eps_fill, rec_fill, eps_t_fill);
+                  R.arr, R.dep, g->rb_mov, R.blk, R.ctr, g->status, eps_fill, rec_fill, eps_t_fill);
     else
         CG_LAUNCH(g, "rebin_mark", (k_rebin_mark<T, false>), (unsigned)nblk, kRebinThreads, 0, pos, n, g->gd,
                   (const int32_t*)g->perm, (const int32_t*)g->key_sorted, g->key, (T*)g->vol, g->rb_rid, g->rb_rkn,
-                  R.arr, R.dep, g->rb_mov, g->rb_mov_cap, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr,
-                  (T*)nullptr);
+                  R.arr, R.dep, g->rb_mov, R.blk, R.ctr, g->status, (double*)nullptr, (T*)nullptr, (T*)nullptr);
     const unsigned cgrid = (unsigned)std::max<long long>(1, std::min<long long>(std::max((nbulk + 255) / 256, nblk),
                                                                                (long long)g->num_sms * 8));
     if (ident)
@@ -455,18 +459,18 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
         const long long m[3] = {nbulk + 1, nbulk + 1, nblk + 1};
         CG_TRY(scan_exclusive(g, 3, in, out, m));
     }
-    const unsigned mgrid = (unsigned)std::max<long long>(1, std::min<long long>((g->rb_mov_cap + 255) / 256,
-                                                                              (long long)g->num_sms * 8));
-    CG_LAUNCH(g, "rebin_place", k_rebin_place, mgrid, 256, 0, (const int4*)g->rb_mov, (const int32_t*)R.arr,
-              g->rb_arr, (const int32_t*)R.ctr);
+    const unsigned pgrid = (unsigned)std::max<long long>(1, std::min<long long>((nblk + 7) / 8, (long long)g->num_sms * 8));
+    CG_LAUNCH(g, "rebin_place", k_rebin_place, pgrid, 256, 0, (const int2*)g->rb_mov, (const int32_t*)R.blk, nblk,
+              (const int32_t*)R.arr, g->rb_arr, (const int32_t*)R.ctr);
+    const unsigned mgrid = (unsigned)(g->num_sms * 8);
 #define CG_REBIN_TAIL(ID)                                                                                        \
     CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->rb_rid,   \
-              (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, \
+              (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int2*)g->rb_arr,    \
               (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);      \
-    CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int4*)g->rb_mov,                   \
-              (const int32_t*)g->rb_rid, (const int32_t*)g->rb_rkn, n, (const int32_t*)g->cell_start,              \
-              (const int32_t*)R.cnt, (const int32_t*)R.arr, (const int32_t*)g->rb_arr, (const T*)g->vol, g->perm,   \
-              g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr)
+    CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int32_t*)g->rb_rid,                 \
+              (const int32_t*)g->rb_rkn, n, (const int32_t*)g->cell_start, (const int32_t*)R.cnt,                   \
+              (const int32_t*)R.arr, (const int2*)g->rb_arr, nbulk, (const T*)g->vol, g->perm, g->key_sorted,      \
+              g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr)
     if (ident) {
         CG_REBIN_TAIL(true);
     } else {
