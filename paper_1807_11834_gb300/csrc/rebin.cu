@@ -322,12 +322,10 @@ __device__ __forceinline__ void emit(long long n, long long ns, int i, int c, in
     vol_sorted[ns] = __ldg(vol + i);
 }
 
-// Stayers, over the old slots in rows of the mark kernel's layout
-// (coalesced), two mark blocks (kStayRows rows) per block so that each
-// thread has twice the loads in flight.  Departures before a slot: the
-// block's start (scan of the block totals), the rows and warps before it in
-// the block (a table of warp counts), and the lanes before it (ballot).
-constexpr int kStayRows = 2 * kRebinItems;
+// Stayers, over the old slots in the layout of the mark kernel (coalesced
+// rows).  Departures before a slot: the block's start (scan of the block
+// totals), the rows and warps before it in the block (a table of warp
+// counts), and the lanes before it (ballot).
 template <typename T, bool IDENT>
 __global__ void __launch_bounds__(kRebinThreads)
 k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
@@ -338,15 +336,15 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     pdl_wait();
     if (ctr[RB_FALLBACK]) return;
     constexpr int W = kRebinThreads / 32;
-    __shared__ int s_tab[kStayRows * W];
+    __shared__ int s_tab[kRebinItems * W];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long base = (long long)blockIdx.x * kStayRows * kRebinThreads;
-    int kn[kStayRows], id[kStayRows], a0[kStayRows], a1[kStayRows];
-    T d[kStayRows];
-    unsigned db[kStayRows];
+    const long long base = (long long)blockIdx.x * kRebinTile;
+    int kn[kRebinItems], id[kRebinItems], a0[kRebinItems], a1[kRebinItems];
+    T d[kRebinItems];
+    unsigned db[kRebinItems];
 #pragma unroll
-    for (int k = 0; k < kStayRows; ++k) {
+    for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
         kn[k] = s < n ? __ldg(rkn + s) : -1;
         id[k] = IDENT ? (int)s : (s < n ? __ldg(rid + s) : 0);
@@ -354,7 +352,7 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     // the gathers of each stayer (its cell's arrivals, its diameter) go out
     // before the block waits for the departure table
 #pragma unroll
-    for (int k = 0; k < kStayRows; ++k) {
+    for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
         a0[k] = a1[k] = 0;
         if (s < n && kn[k] >= 0) {
@@ -367,9 +365,9 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     }
     __syncthreads();
     if (threadIdx.x == 0) {   // exclusive prefix over (row, warp) in slot order
-        int t = __ldg(blk_start + 2 * (long long)blockIdx.x);
+        int t = __ldg(blk_start + blockIdx.x);
 #pragma unroll
-        for (int j = 0; j < kStayRows * W; ++j) {
+        for (int j = 0; j < kRebinItems * W; ++j) {
             const int c = s_tab[j];
             s_tab[j] = t;
             t += c;
@@ -377,7 +375,7 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kStayRows; ++k) {
+    for (int k = 0; k < kRebinItems; ++k) {
         const long long s = base + k * kRebinThreads + threadIdx.x;
         if (s >= n || kn[k] < 0) continue;
         const int D = s_tab[k * W + warp] + __popc(db[k] & lanemask_lt());
@@ -466,8 +464,7 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
               (const int32_t*)R.arr, g->rb_arr, (const int32_t*)R.ctr);
     const unsigned mgrid = (unsigned)(g->num_sms * 8);
 #define CG_REBIN_TAIL(ID)                                                                                        \
-    CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)((nblk + 1) / 2), kRebinThreads, 0,                  \
-              (const int32_t*)g->rb_rid,                                                                       \
+    CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->rb_rid,   \
               (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int2*)g->rb_arr,    \
               (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);      \
     CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int32_t*)g->rb_rid,                 \
