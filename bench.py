@@ -43,9 +43,11 @@ UNIT = "particle-steps/s"
 # dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
 # source file is byte-identical to the one profiled (sha256 prefix).
 NCU_TRAFFIC = {
-    # packed bed, two eager steps: k_average<float,4> 404.15 + 6.02 and
-    # 404.79 + 5.02 MB (read + written); per launch, the mean
-    ("packed_bed", "average"): {"file": "fine.cu", "sha": "a4d41dcdd302d93f", "bytes": 410.0e6},
+    # packed bed, one warm launch of k_average<float,4>: 405.5 MB read + 8.1 MB written
+    ("packed_bed", "average"): {"file": "fine.cu", "sha": "a4d41dcdd302d93f", "bytes": 413.6e6},
+    # clustered-bed recipe at 16M particles, a warm sorted step of k_drag<float,1>:
+    # 579.4 MB read + 903.6 MB written, times 2 for the 32M bed (traffic per particle)
+    ("clustered_bed", "drag"): {"file": "drag.cu", "sha": "ae20239f200d9374", "bytes": 2.966e9},
 }
 
 
@@ -72,6 +74,9 @@ def parse():
     ap.add_argument("--reorder", action="store_true",
                     help="reorder the particles into cell order once before timing (cg_reorder_particles) and "
                          "bin with the per-cell sort")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="clustered-bed workloads only: this many particles on the workload's grid (profiling "
+                         "cases of the same recipe)")
     ap.add_argument("--step", choices=["auto", "sorted", "caller"], default="auto",
                     help="the step timed: cg_step_sorted (particles left in cell order every step; the default "
                          "for an advancing workload) or cg_step (the caller's particle order kept)")
@@ -183,6 +188,21 @@ class ClockSampler:
                 "power_w_max": max((num(p[2]) or 0.0) for _, p in inside)}
 
 
+CLUSTERED_GRIDS = {"clustered_bed": (512, 512, 256), "medium_clustered_bed": (256, 256, 128),
+                   "small_clustered_bed": (128, 128, 64)}
+
+
+def make_workload(args, seed):
+    """The named synthetic workload; --particles re-draws a clustered bed
+    with that many particles on the same grid."""
+    import synth
+    if args.particles > 0:
+        if args.workload not in CLUSTERED_GRIDS:
+            raise SystemExit("--particles applies to the clustered-bed workloads")
+        return synth.clustered_bed(seed=seed, fine_n=CLUSTERED_GRIDS[args.workload], n=args.particles)
+    return getattr(synth, args.workload)(seed=seed)
+
+
 def workload_name(name, w):
     """The workload with its sizes, as the JSON line's config names it."""
     d = w.desc
@@ -255,7 +275,7 @@ def run_gb300(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = getattr(synth, args.workload)(seed=rank)
+    w = make_workload(args, rank)
     dt = float(w.dt)                # 1e-4 for the clustered bed (advanced every step), 0 for the packed bed
     # the advancing workload steps with cg_step_sorted, which leaves the
     # particles in cell order (as a DEM code keeps them); --step caller times
@@ -585,7 +605,7 @@ def run_reference(args):
         return
     import synth
     import oracle
-    w = getattr(synth, args.workload)(seed=0)
+    w = make_workload(args, 0)
     n = w.n
     dt = float(w.dt)
     cores = os.cpu_count() or 1
