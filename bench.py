@@ -64,6 +64,11 @@ def parse():
                     help="64 uneven instances: batched persistent launches vs one by one")
     ap.add_argument("--learned", action="store_true",
                     help="train the drag closure on the workload family, then compare learned and plain steps")
+    ap.add_argument("--activation", choices=("gelu", "relu"), default="relu",
+                    help="activation of the closure trained by --learned or timed by --closure-drag")
+    ap.add_argument("--closure-drag", action="store_true",
+                    help="time the learned drag kernel alone on the workload (a random closure whose feature box "
+                         "holds every row): the profiling case of the closure")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=0,
@@ -669,7 +674,7 @@ def run_learned(args):
     F, T = closure.generate_pairs(make, seeds=(0, 1), refreshes=(2, 5, 10, 20, 50), steps=56,
                                   n_pairs=2_000_000, dt=dt)
     t_gen = time.time() - t0
-    m, hist = closure.train(F, T, epochs=20, batch=65536, lr=2e-3)
+    m, hist = closure.train(F, T, epochs=20, batch=65536, lr=2e-3, activation=args.activation)
     t_train = time.time() - t0 - t_gen
     n_pairs = int(F.shape[0])
     del F, T
@@ -776,7 +781,8 @@ def run_learned(args):
             "value": amort, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
             "higher_is_better": True, "dtype": "f32 (closure bf16 x bf16 -> f32)", "data": "synthetic",
             "config": {"workload": args.workload, "particles": n, "fine_cells": g.n_fine, "bulk_cells": g.n_bulk,
-                       "dt": dt, "training_pairs": n_pairs, "train_seeds": [0, 1], "eval_seed": 2,
+                       "dt": dt, "activation": args.activation, "training_pairs": n_pairs, "train_seeds": [0, 1],
+                       "eval_seed": 2,
                        "generate_s": round(t_gen, 1), "train_s": round(t_train, 1)},
             "refresh_K": K_star,
             "plain": {"ms_per_step": round(ms_plain, 5), "value": n / (ms_plain * 1e-3)},
@@ -790,6 +796,60 @@ def run_learned(args):
     print(json.dumps(line))
     m.close()
     traj.close()
+
+
+def run_closure_drag(args):
+    """The learned drag kernel alone, for profiling: one plain step of the
+    workload (its record is the closure's stale record), a random closure
+    (He-style initial weights) whose feature box holds every row, so no row
+    falls back, bound with record age 2; then `warmup` untimed and `steps`
+    timed launches of cg_drag with the closure, timed with CUDA events on
+    the handle's stream (inputs larger than L2).  One JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1807_11834_gb300 as cg
+    from paper_1807_11834_gb300 import closure
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = make_workload(args, 0)
+    g = cg.Grids(w.desc)
+    n = w.n
+    pos = torch.from_numpy(w.pos_d).cuda()
+    vel = torch.from_numpy(w.vel).cuda()
+    uf = torch.from_numpy(np.ascontiguousarray(w.u_fine.reshape(3, -1))).cuda()
+    out = g.alloc_outputs(n, var=True, eps_fine=True)
+    g.cg_step(pos, vel, uf, out)
+    feat = torch.empty(n, 8, device="cuda")
+    tg = torch.empty(n, device="cuda")
+    g.cg_mlp_features(pos, vel, out["eps_bulk"], out["u_bulk"], out["var_bulk"], out["u_bulk"], feat, tg)
+    lo, hi = closure.feature_box(feat)
+    m = cg.Mlp(cg.mlp_pack(closure.init_params(0)), lo - 1, hi + 1, activation=args.activation)
+    m.bind(out["var_bulk"], uf, 2)
+    F = torch.empty(3, n, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        g.cg_drag(pos, vel, out["eps_bulk"], out["u_bulk"], F, mlp=m)
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.cg_drag(pos, vel, out["eps_bulk"], out["u_bulk"], F, mlp=m)
+    e1.record()
+    e1.synchronize()
+    rc, flags, counts = g.cg_sync_status()
+    if rc != 0 or m.sync_status()[0] != 0:
+        raise RuntimeError(f"learned drag status {rc}")
+    ms = e0.elapsed_time(e1) / steps
+    print(json.dumps({"metric": "learned drag launches", "ms_per_launch": round(ms, 5), "rows": n,
+                      "ns_per_1000_rows": round(ms * 1e6 / n * 1000, 2), "activation": args.activation,
+                      "fallbacks": int(counts[4]), "launches": steps + max(3, args.warmup),
+                      "config": {"workload": workload_name(args.workload, w)}}))
+    m.close()
+    g.close()
 
 
 def run_map(args):
@@ -934,6 +994,8 @@ def main():
         run_batch(args)
     elif args.learned:
         run_learned(args)
+    elif args.closure_drag:
+        run_closure_drag(args)
     else:
         run_gb300(args)
 

@@ -373,10 +373,12 @@ cg_status cg_step_host_wait(cg_grids* g);
 /* ------------------------------------------------------------------------
  * Learned drag closure (not in the paper; the paper's drag law is the plain
  * correlation of Eq. DragLaw).  A multilayer perceptron c = f(features),
- * 16 (7 used) -> 64 -> 64 -> 1 with exact-erf GELU, scales the drag computed
- * from stale bulk fields, F = c F_stale, in place of a fresh fine-to-bulk
- * average.  BF16 operands, FP32 accumulation on the tensor cores; FP32
- * master weights; Adam.  Parameters (FP32, CG_MLP_NPARAM floats, in order):
+ * 16 (7 used) -> 64 -> 64 -> 1 with one activation in both hidden layers
+ * (exact-erf GELU, the default, or ReLU), scales the drag computed from
+ * stale bulk fields, F = c F_stale, in place of a fresh fine-to-bulk
+ * average.  BF16 operands, FP32 accumulation on the tensor cores (the
+ * biases b1, b2 enter the products exactly, as three BF16 terms each);
+ * FP32 master weights; Adam.  Parameters (FP32, CG_MLP_NPARAM floats, in order):
  * W1 [16][64] (input, hidden), b1 [64], W2 [64][64] (in, out), b2 [64],
  * w3 [64], b3 [1].  Feature rows are 8 floats: eps, log10(1 + Re), |s|,
  * d eps/dx, d eps/dy, d eps/dz, sigma^2, unused; the network sees
@@ -387,12 +389,20 @@ cg_status cg_step_host_wait(cg_grids* g);
  * ------------------------------------------------------------------------ */
 #define CG_MLP_NPARAM 5313
 #define CG_MLP_NFEAT 7
+#define CG_MLP_GELU 0   /* x Phi(x), Phi the standard normal CDF */
+#define CG_MLP_RELU 1   /* max(x, 0) */
 
 /* Create a closure from host parameters and the feature box [lo, hi]
  * (host, CG_MLP_NFEAT each, hi > lo).  Allocates its device state. */
 cg_status cg_mlp_create(const float* params, const float* feat_lo, const float* feat_hi, void* cuda_stream,
                         cg_mlp** out);
 cg_status cg_mlp_destroy(cg_mlp* m);
+
+/* The activation of both hidden layers (CG_MLP_GELU after create), used by
+ * every later forward, gradient and learned drag of the closure.
+ * CG_ERR_INVALID_ARG for another value. */
+cg_status cg_mlp_set_activation(cg_mlp* m, int32_t activation);
+cg_status cg_mlp_get_activation(const cg_mlp* m, int32_t* activation);
 
 /* Copy the current parameters and / or the last reduced gradient to the
  * host (either nullable; waits for the stream). */
@@ -439,14 +449,18 @@ cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int3
  *                "version": 1, "nparam", "nfeat", "hidden" (64), "k0" (16),
  *                "params_file" (the .f32 file's name, no directory),
  *                "params_sha256" (SHA-256 of that file, FIPS 180-4, lower-case
- *                hex), "feature_lo" / "feature_hi" (the feature box) and
- *                "meta" (a JSON object the caller chooses).
- * cg_mlp_save writes the closure's current parameters and feature box
- * (waits for its stream); meta_json is a JSON object text or NULL ({}).
- * cg_mlp_load reads a checkpoint and creates a closure from it on the
- * current device, as cg_mlp_create.  The host-only pair underneath works
- * on host arrays (no device needed): cg_mlp_checkpoint_write(params [NPARAM],
- * feat_lo / feat_hi [NFEAT]) and cg_mlp_checkpoint_read (outputs nullable).
+ *                hex), "feature_lo" / "feature_hi" (the feature box),
+ *                "activation" ("gelu" or "relu"; a head without it is
+ *                read as "gelu") and "meta" (a JSON object the caller
+ *                chooses).
+ * cg_mlp_save writes the closure's current parameters, feature box and
+ * activation (waits for its stream); meta_json is a JSON object text or
+ * NULL ({}).  cg_mlp_load reads a checkpoint and creates a closure from it
+ * on the current device, as cg_mlp_create followed by
+ * cg_mlp_set_activation.  The host-only pair underneath works on host
+ * arrays (no device needed): cg_mlp_checkpoint_write(params [NPARAM],
+ * feat_lo / feat_hi [NFEAT], activation CG_MLP_*) and
+ * cg_mlp_checkpoint_read (outputs nullable).
  * CG_ERR_INVALID_ARG: a file cannot be written or read, or does not hold a
  * checkpoint of this network (format, version or sizes differ, the
  * checksum does not match, a value is not finite, the feature box is
@@ -454,8 +468,9 @@ cg_status cg_mlp_bind(cg_mlp* m, const void* var_stale, const void* u_fine, int3
 cg_status cg_mlp_save(cg_mlp* m, const char* path, const char* meta_json);
 cg_status cg_mlp_load(const char* path, void* cuda_stream, cg_mlp** out);
 cg_status cg_mlp_checkpoint_write(const char* path, const float* params, const float* feat_lo, const float* feat_hi,
-                                  const char* meta_json);
-cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo, float* feat_hi);
+                                  int32_t activation, const char* meta_json);
+cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo, float* feat_hi,
+                                 int32_t* activation);
 
 /* Wait for the closure's stream; CG_ERR_TIMEOUT if a bounded wait of its
  * kernels expired (flags: CG_FLAG_*).  Reading the status clears it. */

@@ -7,13 +7,14 @@ The closure is a small multilayer perceptron c = f(features) that scales
 the drag computed from stale bulk fields, F = c F_stale, standing in for a
 fresh fine-to-bulk average.  Network (features padded to K0 = 16):
 
-    Z1 = X W1 + b1,   A1 = GELU(Z1)           X: [B, 16], W1: [16, H]
-    Z2 = A1 W2 + b2,  A2 = GELU(Z2)           W2: [H, H]
+    Z1 = X W1 + b1,   A1 = act(Z1)            X: [B, 16], W1: [16, H]
+    Z2 = A1 W2 + b2,  A2 = act(Z2)            W2: [H, H]
     c  = A2 w3 + b3                           w3: [H]
     loss = mean (c - c*)^2
 
-GELU is the exact form x Phi(x) with Phi the standard normal CDF
-(Hendrycks & Gimpel).  Training is Adam (Kingma & Ba) on FP32-style master
+The activation is one of two: GELU, the exact form x Phi(x) with Phi the
+standard normal CDF (Hendrycks & Gimpel), or ReLU, max(x, 0) (its
+derivative taken as 0 at x = 0).  Training is Adam (Kingma & Ba) on FP32-style master
 weights.  With ``bf16=True`` the inputs of the two forward matrix products
 (X, W1, A1, W2) and of the backward product dZ2 W2^T are rounded to
 bfloat16 (round to nearest even) exactly where the tensor-core kernels round
@@ -55,6 +56,20 @@ def gelu_grad(x):
     return cdf + x * pdf
 
 
+def relu(x):
+    """max(x, 0); for complex x (a complex step) the branch follows the real
+    part, so the step differentiates the piece it lies on."""
+    x = np.asarray(x)
+    return np.where(x.real > 0, x, 0.0 * x)
+
+
+def relu_grad(x):
+    return (np.asarray(x).real > 0).astype(np.float64)
+
+
+ACTIVATIONS = {"gelu": (gelu, gelu_grad), "relu": (relu, relu_grad)}
+
+
 def init_params(hidden: int = 64, seed: int = 0) -> dict:
     """He-style uniform init from a Philox stream (the same numbers are
     handed to the GPU; the GPU never draws its own)."""
@@ -73,20 +88,22 @@ def _exact(a):
     return np.asarray(a, dtype=np.result_type(a, np.float64))
 
 
-def forward(p: dict, X: np.ndarray, bf16_inputs: bool = False):
+def forward(p: dict, X: np.ndarray, bf16_inputs: bool = False, act: str = "gelu"):
     q = (lambda a: bf16(a)) if bf16_inputs else _exact
+    f = ACTIVATIONS[act][0]
     Z1 = q(X) @ q(p["W1"]) + p["b1"]
-    A1 = gelu(Z1)
+    A1 = f(Z1)
     Z2 = q(A1) @ q(p["W2"]) + p["b2"]
-    A2 = gelu(Z2)
+    A2 = f(Z2)
     c = A2 @ p["w3"] + p["b3"][0]
     return c, dict(X=X, Z1=Z1, A1=A1, Z2=Z2, A2=A2)
 
 
-def loss_and_grads(p: dict, X: np.ndarray, target: np.ndarray, bf16_inputs: bool = False):
+def loss_and_grads(p: dict, X: np.ndarray, target: np.ndarray, bf16_inputs: bool = False, act: str = "gelu"):
     q = (lambda a: bf16(a)) if bf16_inputs else (lambda a: np.asarray(a, np.float64))
+    dact = ACTIVATIONS[act][1]
     B = X.shape[0]
-    c, s = forward(p, X, bf16_inputs)
+    c, s = forward(p, X, bf16_inputs, act)
     r = c - target
     loss = float(np.mean(r * r))
     dc = 2.0 * r / B
@@ -94,11 +111,11 @@ def loss_and_grads(p: dict, X: np.ndarray, target: np.ndarray, bf16_inputs: bool
     g["w3"] = s["A2"].T @ dc
     g["b3"] = np.array([dc.sum()])
     dA2 = np.outer(dc, p["w3"])
-    dZ2 = dA2 * gelu_grad(s["Z2"])
+    dZ2 = dA2 * dact(s["Z2"])
     g["W2"] = q(s["A1"]).T @ dZ2
     g["b2"] = dZ2.sum(axis=0)
     dA1 = q(dZ2) @ q(p["W2"]).T
-    dZ1 = dA1 * gelu_grad(s["Z1"])
+    dZ1 = dA1 * dact(s["Z1"])
     g["W1"] = q(X).T @ dZ1
     g["b1"] = dZ1.sum(axis=0)
     return loss, g

@@ -126,8 +126,10 @@ _SIGS = {
     "cg_mlp_sync_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "cg_mlp_save": (C.c_int, [C.c_void_p, C.c_char_p, C.c_char_p]),
     "cg_mlp_load": (C.c_int, [C.c_char_p, C.c_void_p, C.POINTER(C.c_void_p)]),
-    "cg_mlp_checkpoint_write": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_char_p]),
-    "cg_mlp_checkpoint_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_checkpoint_write": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_char_p]),
+    "cg_mlp_checkpoint_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cg_mlp_set_activation": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cg_mlp_get_activation": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "cg_mlp_wait_selftest": (C.c_int, [C.c_void_p, C.c_uint32]),
     "cg_debug_fail_alloc_after": (C.c_int, [C.c_int64]),
     "cg_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -158,6 +160,7 @@ _SIGS = {
 
 MLP_NPARAM = 5313
 MLP_NFEAT = 7
+MLP_ACTIVATIONS = {"gelu": 0, "relu": 1}   # CG_MLP_GELU, CG_MLP_RELU
 
 
 def lib():
@@ -517,7 +520,13 @@ def cg_bin_particles_static(desc: dict, pos_d, perm, cell_start, cell=None, stre
                                          _stream_handle(stream)), "cg_bin_particles_static")
 
 
-def checkpoint_write(path, params, feat_lo, feat_hi, meta=None):
+def _activation_code(activation):
+    if activation not in MLP_ACTIVATIONS:
+        raise ValueError(f"activation must be one of {sorted(MLP_ACTIVATIONS)}")
+    return MLP_ACTIVATIONS[activation]
+
+
+def checkpoint_write(path, params, feat_lo, feat_hi, meta=None, activation="gelu"):
     """cg_mlp_checkpoint_write: a closure checkpoint from host arrays (no device)."""
     import json
     import numpy as np
@@ -527,36 +536,48 @@ def checkpoint_write(path, params, feat_lo, feat_hi, meta=None):
     if p.size != MLP_NPARAM or lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
         raise ValueError("bad closure parameter or feature-box sizes")
     _check(lib().cg_mlp_checkpoint_write(os.fsencode(path), p.ctypes.data, lo.ctypes.data, hi.ctypes.data,
-                                         json.dumps(meta or {}).encode()), "cg_mlp_checkpoint_write")
+                                         _activation_code(activation), json.dumps(meta or {}).encode()),
+           "cg_mlp_checkpoint_write")
 
 
 def checkpoint_read(path):
-    """cg_mlp_checkpoint_read: (params, feat_lo, feat_hi) float32 arrays of a checkpoint."""
+    """cg_mlp_checkpoint_read: (params, feat_lo, feat_hi) float32 arrays of a
+    checkpoint and its activation ("gelu" or "relu")."""
     import numpy as np
     p = np.zeros(MLP_NPARAM, np.float32)
     lo = np.zeros(MLP_NFEAT, np.float32)
     hi = np.zeros(MLP_NFEAT, np.float32)
-    _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), p.ctypes.data, lo.ctypes.data, hi.ctypes.data),
-           "cg_mlp_checkpoint_read")
-    return p, lo, hi
+    act = C.c_int32(-1)
+    _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), p.ctypes.data, lo.ctypes.data, hi.ctypes.data,
+                                        C.addressof(act)), "cg_mlp_checkpoint_read")
+    return p, lo, hi, {v: k for k, v in MLP_ACTIVATIONS.items()}[act.value]
 
 
 class Mlp:
     """Owner of a ``cg_mlp`` closure handle (learned drag correction).
     Parameters are a flat float32 array of MLP_NPARAM (W1, b1, W2, b2, w3, b3)."""
 
-    def __init__(self, params, feat_lo, feat_hi, stream=None):
+    def __init__(self, params, feat_lo, feat_hi, stream=None, activation="gelu"):
         import numpy as np
         p = np.ascontiguousarray(params, dtype=np.float32)
         lo = np.ascontiguousarray(feat_lo, dtype=np.float32)
         hi = np.ascontiguousarray(feat_hi, dtype=np.float32)
         if p.size != MLP_NPARAM or lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
             raise ValueError("bad closure parameter or feature-box sizes")
+        code = _activation_code(activation)
         h = C.c_void_p()
         _check(lib().cg_mlp_create(p.ctypes.data, lo.ctypes.data, hi.ctypes.data, _stream_handle(stream),
                                    C.byref(h)), "cg_mlp_create")
         self.h = h
         self.lo, self.hi = lo, hi
+        _check(lib().cg_mlp_set_activation(self.h, code), "cg_mlp_set_activation")
+
+    @property
+    def activation(self):
+        """The closure's activation, "gelu" or "relu" (cg_mlp_get_activation)."""
+        a = C.c_int32(-1)
+        _check(lib().cg_mlp_get_activation(self.h, C.byref(a)), "cg_mlp_get_activation")
+        return {v: k for k, v in MLP_ACTIVATIONS.items()}[a.value]
 
     @classmethod
     def load(cls, path, stream=None):
@@ -568,12 +589,12 @@ class Mlp:
         m.h = h
         m.lo = np.zeros(MLP_NFEAT, np.float32)
         m.hi = np.zeros(MLP_NFEAT, np.float32)
-        _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), None, m.lo.ctypes.data, m.hi.ctypes.data),
+        _check(lib().cg_mlp_checkpoint_read(os.fsencode(path), None, m.lo.ctypes.data, m.hi.ctypes.data, None),
                "cg_mlp_checkpoint_read")
         return m
 
     def save(self, path, meta=None):
-        """Checkpoint of the current parameters and feature box (cg_mlp_save);
+        """Checkpoint of the current parameters, feature box and activation (cg_mlp_save);
         meta: a JSON-serialisable dict kept in the head."""
         import json
         _check(lib().cg_mlp_save(self.h, os.fsencode(path), json.dumps(meta or {}).encode()), "cg_mlp_save")

@@ -35,7 +35,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Grids, Mlp, mlp_pack, MLP_NFEAT, MLP_NPARAM
+from . import Grids, Mlp, mlp_pack, MLP_ACTIVATIONS, MLP_NFEAT, MLP_NPARAM
 
 HIDDEN = 64
 K0 = 16
@@ -170,14 +170,14 @@ def init_params(seed: int = 0):
                 b2=np.zeros(HIDDEN), w3=u((HIDDEN,), HIDDEN) * 0.1, b3=np.array([0.0]))
 
 
-def train(features, targets, epochs=20, batch=65536, lr=1e-3, seed=0, box=None):
+def train(features, targets, epochs=20, batch=65536, lr=1e-3, seed=0, box=None, activation="gelu"):
     """Adam on minibatches (shuffled each epoch) through cg_mlp_train_step
     on the standardised targets; the mean and spread are folded into the
-    output layer at the end.  Returns the closure handle and the mean loss
-    of each epoch (standardised units)."""
+    output layer at the end.  Returns the closure handle (with the given
+    activation) and the mean loss of each epoch (standardised units)."""
     import torch
     lo, hi = box if box is not None else feature_box(features)
-    m = Mlp(mlp_pack(init_params(seed)), lo, hi)
+    m = Mlp(mlp_pack(init_params(seed)), lo, hi, activation=activation)
     mu = float(targets.double().mean())
     sd = float(targets.double().std())
     sd = sd if sd > 0 else 1.0
@@ -250,14 +250,17 @@ CHECKPOINT_FORMAT = "dual-grid drag closure"
 CHECKPOINT_VERSION = 1
 
 
-def save_checkpoint(path: str, params, feat_lo, feat_hi, **meta) -> None:
+def save_checkpoint(path: str, params, feat_lo, feat_hi, activation: str = "gelu", **meta) -> None:
     """Write a trained closure as two files: ``path + ".f32"`` holds the
     MLP_NPARAM parameters as little-endian float32 in the ABI order of
     mlp_pack (W1, b1, W2, b2, w3, b3), and ``path + ".json"`` the sizes, the
     feature box (min / max of each of the MLP_NFEAT features over the
-    training set), the SHA-256 of the parameter file and any extra JSON
-    values given as keywords (the refresh interval, the target mean and
-    spread, ...).  The parameters are written exactly as given (float32)."""
+    training set), the SHA-256 of the parameter file, the activation and
+    any extra JSON values given as keywords (the refresh interval, the
+    target mean and spread, ...).  The parameters are written exactly as
+    given (float32)."""
+    if activation not in MLP_ACTIVATIONS:
+        raise ValueError("closure checkpoint: unknown activation")
     p = np.ascontiguousarray(params, dtype="<f4").reshape(-1)
     lo = np.asarray(feat_lo, np.float32).reshape(-1)
     hi = np.asarray(feat_hi, np.float32).reshape(-1)
@@ -270,7 +273,8 @@ def save_checkpoint(path: str, params, feat_lo, feat_hi, **meta) -> None:
             "nfeat": MLP_NFEAT, "hidden": HIDDEN, "k0": K0,
             "params_file": os.path.basename(path) + ".f32", "params_sha256": hashlib.sha256(raw).hexdigest(),
             # float32 values written as the doubles they are, so they read back exactly
-            "feature_lo": [float(v) for v in lo], "feature_hi": [float(v) for v in hi], "meta": meta}
+            "feature_lo": [float(v) for v in lo], "feature_hi": [float(v) for v in hi], "activation": activation,
+            "meta": meta}
     with open(path + ".f32", "wb") as f:
         f.write(raw)
     with open(path + ".json", "w") as f:
@@ -279,9 +283,11 @@ def save_checkpoint(path: str, params, feat_lo, feat_hi, **meta) -> None:
 
 def load_checkpoint(path: str):
     """Read a closure written by save_checkpoint: (params float32
-    [MLP_NPARAM], feat_lo float32 [MLP_NFEAT], feat_hi, meta dict).  Raises
-    ValueError when the format, a size or the checksum does not match.
-    ``Mlp(params, feat_lo, feat_hi)`` makes the closure handle."""
+    [MLP_NPARAM], feat_lo float32 [MLP_NFEAT], feat_hi, meta dict,
+    activation; "gelu" when the head names none).  Raises ValueError when
+    the format, a size, the activation or the checksum does not match.
+    ``Mlp(params, feat_lo, feat_hi, activation=activation)`` makes the
+    closure handle."""
     with open(path + ".json") as f:
         head = json.load(f)
     if head.get("format") != CHECKPOINT_FORMAT or head.get("version") != CHECKPOINT_VERSION:
@@ -298,4 +304,7 @@ def load_checkpoint(path: str):
     hi = np.asarray(head["feature_hi"], np.float32)
     if lo.size != MLP_NFEAT or hi.size != MLP_NFEAT:
         raise ValueError("closure checkpoint: bad feature box")
-    return params, lo, hi, dict(head.get("meta") or {})
+    activation = head.get("activation", "gelu")
+    if activation not in MLP_ACTIVATIONS:
+        raise ValueError("closure checkpoint: unknown activation")
+    return params, lo, hi, dict(head.get("meta") or {}), activation

@@ -8,7 +8,8 @@
 //                "hidden", "k0"), "params_file" (the .f32 file's name),
 //                "params_sha256" (SHA-256 of the .f32 file, lower-case hex),
 //                "feature_lo" / "feature_hi" (the feature box, floats written
-//                as the doubles they are) and "meta" (any JSON object).
+//                as the doubles they are), "activation" ("gelu" or "relu";
+//                absent: "gelu") and "meta" (any JSON object).
 // Python's closure.save_checkpoint / load_checkpoint read and write the same
 // files.  SHA-256 follows FIPS 180-4; its round constants and initial hash
 // are formed here from their definition (the fractional parts of the cube
@@ -214,7 +215,7 @@ struct Json {
 };
 
 struct Head {
-    std::string format, params_file, sha;
+    std::string format, params_file, sha, activation = "gelu";
     double version = -1, nparam = -1, nfeat = -1, hidden = -1, k0 = -1;
     std::vector<double> lo, hi;
 };
@@ -233,10 +234,11 @@ bool parse_head(const std::string& text, Head& h) {
         if (j.p >= j.e || *j.p != ':') return false;
         ++j.p;
         j.ws();
-        if (key == "format" || key == "params_file" || key == "params_sha256") {
+        if (key == "format" || key == "params_file" || key == "params_sha256" || key == "activation") {
             std::string v;
             if (!j.str(&v)) return false;
-            (key == "format" ? h.format : key == "params_file" ? h.params_file : h.sha) = v;
+            (key == "format" ? h.format : key == "params_file" ? h.params_file
+                                         : key == "activation" ? h.activation : h.sha) = v;
         } else if (key == "version" || key == "nparam" || key == "nfeat" || key == "hidden" || key == "k0") {
             double v;
             if (!j.num(&v)) return false;
@@ -329,8 +331,9 @@ bool finite_box(const float* lo, const float* hi) {
 extern "C" {
 
 cg_status cg_mlp_checkpoint_write(const char* path, const float* params, const float* feat_lo, const float* feat_hi,
-                                  const char* meta_json) {
+                                  int32_t activation, const char* meta_json) {
     if (!path || !*path || !params || !feat_lo || !feat_hi) return CG_ERR_INVALID_ARG;
+    if (activation != CG_MLP_GELU && activation != CG_MLP_RELU) return CG_ERR_INVALID_ARG;
     for (int k = 0; k < CG_MLP_NPARAM; ++k)
         if (!std::isfinite(params[k])) return CG_ERR_INVALID_ARG;
     if (!finite_box(feat_lo, feat_hi)) return CG_ERR_INVALID_ARG;
@@ -364,13 +367,15 @@ cg_status cg_mlp_checkpoint_write(const char* path, const float* params, const f
         }
         return s + "],\n";
     };
-    head += arr("feature_lo", feat_lo) + arr("feature_hi", feat_hi) + " \"meta\": " + meta + "\n}\n";
+    head += arr("feature_lo", feat_lo) + arr("feature_hi", feat_hi) + " \"activation\": \"" +
+            (activation == CG_MLP_RELU ? "relu" : "gelu") + "\",\n \"meta\": " + meta + "\n}\n";
     if (!write_file(p + ".f32", raw.data(), raw.size())) return CG_ERR_INVALID_ARG;
     if (!write_file(p + ".json", head.data(), head.size())) return CG_ERR_INVALID_ARG;
     return CG_OK;
 }
 
-cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo, float* feat_hi) {
+cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo, float* feat_hi,
+                                 int32_t* activation) {
     if (!path || !*path) return CG_ERR_INVALID_ARG;
     const std::string p(path);
     std::string text, raw;
@@ -381,6 +386,7 @@ cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo
         return CG_ERR_INVALID_ARG;
     if (h.params_file.empty() || h.params_file.find('/') != std::string::npos) return CG_ERR_INVALID_ARG;
     if ((int)h.lo.size() != CG_MLP_NFEAT || (int)h.hi.size() != CG_MLP_NFEAT) return CG_ERR_INVALID_ARG;
+    if (h.activation != "gelu" && h.activation != "relu") return CG_ERR_INVALID_ARG;
     if (!read_file(dir_name(p) + h.params_file, raw) || raw.size() != 4 * (size_t)CG_MLP_NPARAM) return CG_ERR_INVALID_ARG;
     if (sha256_hex((const unsigned char*)raw.data(), raw.size()) != h.sha) return CG_ERR_INVALID_ARG;
     float P[CG_MLP_NPARAM], lo[CG_MLP_NFEAT], hi[CG_MLP_NFEAT];
@@ -398,6 +404,7 @@ cg_status cg_mlp_checkpoint_read(const char* path, float* params, float* feat_lo
     if (params) memcpy(params, P, sizeof P);
     if (feat_lo) memcpy(feat_lo, lo, sizeof lo);
     if (feat_hi) memcpy(feat_hi, hi, sizeof hi);
+    if (activation) *activation = h.activation == "relu" ? CG_MLP_RELU : CG_MLP_GELU;
     return CG_OK;
 }
 
@@ -405,16 +412,25 @@ cg_status cg_mlp_save(cg_mlp* m, const char* path, const char* meta_json) {
     if (!m || !path) return CG_ERR_INVALID_ARG;
     float P[CG_MLP_NPARAM], lo[CG_MLP_NFEAT], hi[CG_MLP_NFEAT];
     CG_TRY(cg_mlp_get_params(m, P, nullptr));
+    int32_t act = CG_MLP_GELU;
     CG_TRY(cg::mlp_feature_box(m, lo, hi));
-    return cg_mlp_checkpoint_write(path, P, lo, hi, meta_json);
+    CG_TRY(cg_mlp_get_activation(m, &act));
+    return cg_mlp_checkpoint_write(path, P, lo, hi, act, meta_json);
 }
 
 cg_status cg_mlp_load(const char* path, void* cuda_stream, cg_mlp** out) {
     if (!out) return CG_ERR_INVALID_ARG;
     *out = nullptr;
     float P[CG_MLP_NPARAM], lo[CG_MLP_NFEAT], hi[CG_MLP_NFEAT];
-    CG_TRY(cg_mlp_checkpoint_read(path, P, lo, hi));
-    return cg_mlp_create(P, lo, hi, cuda_stream, out);
+    int32_t act = CG_MLP_GELU;
+    CG_TRY(cg_mlp_checkpoint_read(path, P, lo, hi, &act));
+    CG_TRY(cg_mlp_create(P, lo, hi, cuda_stream, out));
+    const cg_status s = cg_mlp_set_activation(*out, act);
+    if (s != CG_OK) {
+        cg_mlp_destroy(*out);
+        *out = nullptr;
+    }
+    return s;
 }
 
 }  // extern "C"

@@ -3,16 +3,19 @@
 // fields, trained and evaluated by this library's own tensor-core kernels.
 //
 // Network (features padded to 16 inputs, hidden width 64):
-//   Z1 = X W1 + b1, A1 = GELU(Z1); Z2 = A1 W2 + b2, A2 = GELU(Z2); c = A2 w3 + b3
-// GELU is the exact erf form.  Weights are kept as FP32 master copies; the
-// matrix products take BF16 operands with FP32 accumulation on the 5th
-// generation tensor cores: a CTA of 128 threads owns a tile of 128 rows,
-// stages BF16 operands in shared memory in the no-swizzle K-major
-// core-matrix layout, one thread issues tcgen05.mma into tensor memory
-// (TMEM), completion is tracked by an mbarrier (bounded wait), and each
-// thread reads back its row with tcgen05.ld.  The small weight-gradient
-// products (A^T dZ) run in FP32 on the CUDA cores in a fixed order, so
-// training is deterministic.
+//   Z1 = X W1 + b1, A1 = act(Z1); Z2 = A1 W2 + b2, A2 = act(Z2); c = A2 w3 + b3
+// act is GELU (the exact erf form) or ReLU, chosen per closure.  Weights are
+// kept as FP32 master copies; the matrix products take BF16 operands with
+// FP32 accumulation on the 5th generation tensor cores: a CTA of 128
+// threads owns a tile of 128 rows, stages BF16 operands in shared memory in
+// the no-swizzle K-major core-matrix layout, one thread issues tcgen05.mma
+// into tensor memory (TMEM), completion is tracked by an mbarrier (bounded
+// wait), and each thread reads back its row with tcgen05.ld.  The biases
+// b1 and b2 ride in the products: three operand columns of ones meet the
+// bias split into three BF16 terms whose sum is the FP32 bias exactly, so
+// the epilogue between the products is the activation alone.  The small
+// weight-gradient products (A^T dZ) run in FP32 on the CUDA cores in a
+// fixed order, so training is deterministic.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -31,6 +34,9 @@ namespace mlp {
 constexpr int K0 = 16;                 // padded input width
 constexpr int H = 64;                  // hidden width
 constexpr int NFEAT = 7;               // used inputs
+constexpr int KA = H + 16;             // K of the second product: 64 activations, 3 bias columns, zeros
+constexpr int ACT_GELU = CG_MLP_GELU;
+constexpr int ACT_RELU = CG_MLP_RELU;
 constexpr int FEAT_STRIDE = 8;         // floats per feature row in memory
 constexpr int OFF_W1 = 0;              // [K0][H]
 constexpr int OFF_B1 = OFF_W1 + K0 * H;
@@ -130,12 +136,35 @@ __host__ __device__ constexpr uint32_t koff(int row, int k, int K) {
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
+// Two values as a BF16 pair (lo in the low half), rounded to nearest even;
+// the relu form clamps negative results to zero in the same instruction.
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 // Store 8 consecutive K values of one row (one 16-byte core-matrix row).
 __device__ __forceinline__ void st_row8(unsigned char* tile, int row, int k0, int K, const float* v) {
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) w[i] = (uint32_t)bf16_bits(v[2 * i]) | ((uint32_t)bf16_bits(v[2 * i + 1]) << 16);
-    *reinterpret_cast<uint4*>(tile + koff(row, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(tile + koff(row, k0, K)) =
+        make_uint4(bf16x2(v[0], v[1]), bf16x2(v[2], v[3]), bf16x2(v[4], v[5]), bf16x2(v[6], v[7]));
+}
+
+// Term j (0, 1, 2) of the split of an FP32 value into three BF16 values
+// whose sum is the value exactly: h = bf16(b); the remainder b - h is exact
+// in FP32 and holds at most 16 significant bits, m = bf16(b - h), and the
+// last remainder b - h - m (exact again) fits the 8 bits of a BF16.
+__device__ __forceinline__ float bias_term(float b, int j) {
+    const float h = bf16_val(bf16_bits(b));
+    if (j == 0) return h;
+    const float r = b - h;
+    const float m = bf16_val(bf16_bits(r));
+    return j == 1 ? m : r - m;
 }
 
 // GELU x Phi(x) of the forward pass, with the complementary error function
@@ -207,14 +236,20 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // Shared-memory layout of a CTA: the forward part, and the extra operands of
 // the training kernel
 // ---------------------------------------------------------------------------
-struct Smem {
-    alignas(128) unsigned char W1t[H * K0 * 2];    // B of GEMM 1: (n = hidden, k = input)
-    alignas(128) unsigned char W2t[H * H * 2];     // B of GEMM 2: (n = out, k = in)
-    alignas(128) unsigned char X[TILE * K0 * 2];   // A of GEMM 1
-    alignas(128) unsigned char A1[TILE * H * 2];   // A of GEMM 2 (BF16 GELU(Z1))
-    float b1[H], b2[H], w3[H];
+// The network's forward operands as a CTA's shared memory holds them: built
+// by k_mlp_image whenever the parameters change, copied by every CTA.
+struct WeightImage {
+    alignas(128) unsigned char W1t[H * K0 * 2];    // B of GEMM 1: (n = hidden, k = input; k 7..9: b1)
+    alignas(128) unsigned char W2t[H * KA * 2];    // B of GEMM 2: (n = out, k = in; k 64..66: b2)
+    float w3[H];
     float lo[FEAT_STRIDE], inv[FEAT_STRIDE];
     float b3;
+};
+static_assert(sizeof(WeightImage) % 16 == 0, "the image is copied in 16-byte words");
+struct Smem {
+    WeightImage w;
+    alignas(128) unsigned char X[TILE * K0 * 2];   // A of GEMM 1 (columns 7..9: ones)
+    alignas(128) unsigned char A1[TILE * KA * 2];  // A of GEMM 2 (BF16 act(Z1); columns 64..66: ones)
     uint64_t bar;
     uint32_t tmem;
     int fail;
@@ -230,26 +265,41 @@ struct SmemTrain {
     float r2[TILE];
 };
 
-// Load the BF16 operand copies of the weights and the FP32 vectors.
-__device__ void load_weights(Smem& s, const float* __restrict__ P, const float* __restrict__ scale) {
+// The weight image from the FP32 parameters: BF16 operand copies of the
+// weights with the split biases, and the FP32 vectors.  One CTA.
+__global__ void __launch_bounds__(256)
+k_mlp_image(const float* __restrict__ P, const float* __restrict__ scale, WeightImage* __restrict__ img) {
     for (int e = threadIdx.x; e < H * K0; e += blockDim.x) {
-        const int n = e / K0, k = e % K0;   // W1t(n, k) = W1[k][n]
-        *reinterpret_cast<uint16_t*>(s.W1t + koff(n, k, K0)) = bf16_bits(P[OFF_W1 + k * H + n]);
+        const int n = e / K0, k = e % K0;   // W1t(n, k) = W1[k][n]; inputs past NFEAT are zero
+        const float w = k < NFEAT ? P[OFF_W1 + k * H + n] : k < NFEAT + 3 ? bias_term(P[OFF_B1 + n], k - NFEAT) : 0.f;
+        *reinterpret_cast<uint16_t*>(img->W1t + koff(n, k, K0)) = bf16_bits(w);
     }
-    for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
-        const int i = e / H, o = e % H;     // W2[i][o]
-        *reinterpret_cast<uint16_t*>(s.W2t + koff(o, i, H)) = bf16_bits(P[OFF_W2 + i * H + o]);   // (n = out, k = in)
+    for (int e = threadIdx.x; e < H * KA; e += blockDim.x) {
+        const int i = e / H, o = e % H;     // W2[i][o] as (n = out, k = in)
+        const float w = i < H ? P[OFF_W2 + i * H + o] : i < H + 3 ? bias_term(P[OFF_B2 + o], i - H) : 0.f;
+        *reinterpret_cast<uint16_t*>(img->W2t + koff(o, i, KA)) = bf16_bits(w);
     }
-    for (int j = threadIdx.x; j < H; j += blockDim.x) {
-        s.b1[j] = P[OFF_B1 + j];
-        s.b2[j] = P[OFF_B2 + j];
-        s.w3[j] = P[OFF_W3 + j];
-    }
+    for (int j = threadIdx.x; j < H; j += blockDim.x) img->w3[j] = P[OFF_W3 + j];
     if (threadIdx.x < FEAT_STRIDE) {
-        s.lo[threadIdx.x] = scale[threadIdx.x];
-        s.inv[threadIdx.x] = scale[FEAT_STRIDE + threadIdx.x];
+        img->lo[threadIdx.x] = scale[threadIdx.x];
+        img->inv[threadIdx.x] = scale[FEAT_STRIDE + threadIdx.x];
     }
-    if (threadIdx.x == 0) s.b3 = P[OFF_B3];
+    if (threadIdx.x == 0) img->b3 = P[OFF_B3];
+}
+
+// A CTA's copy of the weight image (16-byte words, all in flight at once),
+// and the constant columns of the second product's A tile (ones at
+// 64..66, zeros up to KA), which no tile overwrites.
+__device__ void load_weights(Smem& s, const WeightImage* __restrict__ img) {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(&s.w);
+    constexpr int words = (int)(sizeof(WeightImage) / 16);
+    for (int e = threadIdx.x; e < words; e += blockDim.x) dst[e] = __ldg(src + e);
+    for (int row = threadIdx.x; row < TILE; row += blockDim.x) {
+        const float one[8] = {1.f, 1.f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        st_row8(s.A1, row, H, KA, one);
+        st_row8(s.A1, row, H + 8, KA, zero);
+    }
 }
 
 // W2 as the B operand of dA1 = dZ2 W2^T (training).
@@ -260,14 +310,15 @@ __device__ void load_w2b(SmemTrain& st, const float* __restrict__ P) {
     }
 }
 
-// Scaled network input of one row from raw features; returns in-range.
+// Scaled network input of one row from raw features (and the three ones
+// that meet b1); returns in-range.
 __device__ __forceinline__ bool scale_row(const Smem& s, const float* f, float (&x)[K0]) {
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < K0; ++k) x[k] = 0.f;
+    for (int k = 0; k < K0; ++k) x[k] = k >= NFEAT && k < NFEAT + 3 ? 1.f : 0.f;
 #pragma unroll
     for (int k = 0; k < NFEAT; ++k) {
-        const float v = (f[k] - s.lo[k]) * s.inv[k];
+        const float v = (f[k] - s.w.lo[k]) * s.w.inv[k];
         ok = ok && (v >= 0.f && v <= 1.f);
         x[k] = v;
     }
@@ -286,15 +337,19 @@ __device__ void cta_setup(Smem& s, uint32_t ncols) {
     fence_after();
 }
 
-__device__ void cta_teardown(Smem& s, uint32_t ncols) {
+__device__ void cta_teardown(Smem& s, uint32_t ncols, uint64_t* bar2 = nullptr) {
     fence_before();
     __syncthreads();
     fence_after();
     if (s.fail && threadIdx.x == 0) {
         // a wait expired: give the tensor core one more bounded wait for the
-        // product still in flight before its TMEM columns are released
+        // products still in flight before their TMEM columns are released
         mbar_wait(&s.bar, 0);
         mbar_wait(&s.bar, 1);
+        if (bar2) {
+            mbar_wait(bar2, 0);
+            mbar_wait(bar2, 1);
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) tmem_dealloc(s.tmem, ncols);
@@ -308,11 +363,11 @@ __device__ __forceinline__ S& smem_as(unsigned char* raw) {
 }
 
 // D[128 x 64] (TMEM columns dcol..dcol+63) = A[128 x 16 nk] B^T with A and
-// B K-major core-matrix tiles of K = 16 nk: issued from thread 0 after the
-// CTA's operand stores, then a bounded wait for completion.  Returns false
-// (and marks the CTA failed) if the wait expires; the whole CTA agrees.
-__device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const unsigned char* B, int nk,
-                         uint32_t& phase, unsigned long long* status) {
+// B K-major core-matrix tiles of K = 16 nk, issued from thread 0 after the
+// CTA's operand stores (and its reads of the columns the product
+// overwrites); completion arrives at `bar`.
+__device__ void gemm_issue(Smem& s, uint64_t* bar, uint32_t dcol, const unsigned char* A, const unsigned char* B,
+                           int nk) {
     fence_async_smem();   // make this thread's shared-memory stores visible to the tensor core
     fence_before();
     __syncthreads();
@@ -322,9 +377,15 @@ __device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const u
         for (int kk = 0; kk < nk; ++kk)
             umma(s.tmem + dcol, sdesc(saddr(A) + kk * 256, 128, sbo), sdesc(saddr(B) + kk * 256, 128, sbo),
                  idesc_bf16(TILE, H), kk > 0);
-        umma_commit(&s.bar);
+        umma_commit(bar);
     }
-    const bool mine = mbar_wait(&s.bar, phase);
+}
+
+// Bounded wait for the product committed to `bar` (phase parity `phase`,
+// flipped here).  Returns false (and marks the CTA failed) if the wait
+// expires; the whole CTA agrees.
+__device__ bool gemm_wait(Smem& s, uint64_t* bar, uint32_t& phase, unsigned long long* status) {
+    const bool mine = mbar_wait(bar, phase);
     phase ^= 1u;
     const bool failed = __syncthreads_or(!mine) != 0;
     if (failed && threadIdx.x == 0) {
@@ -334,6 +395,12 @@ __device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const u
     }
     fence_after();
     return !failed;
+}
+
+__device__ bool run_gemm(Smem& s, uint32_t dcol, const unsigned char* A, const unsigned char* B, int nk,
+                         uint32_t& phase, unsigned long long* status) {
+    gemm_issue(s, &s.bar, dcol, A, B, nk);
+    return gemm_wait(s, &s.bar, phase, status);
 }
 
 // The failure path of the bounded waits, without a stalled tensor core: one
@@ -357,40 +424,87 @@ __device__ __forceinline__ uint32_t lane_addr(const Smem& s, int col) {
     return s.tmem + ((uint32_t)((threadIdx.x & ~31) & 127) << 16) + (uint32_t)col;
 }
 
-// Forward of the tile: rows' X already in s.X.  Z1 goes to TMEM columns
-// 0..63 and Z2 (without bias) to z2col..z2col+63 (0 reuses Z1's columns,
-// which are read out before GEMM 2 is issued); returns this thread's c.
-__device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c, uint32_t z2col) {
-    if (!run_gemm(s, 0, s.X, s.W1t, K0 / 16, phase, status)) return false;
-    const int row = threadIdx.x;
-    // the column loops stay rolled: 16 activations per pass give enough
-    // independent work, and the unrolled body would not fit the
-    // instruction cache beside the rest of the fused drag kernel
-#pragma unroll 1
-    for (int q = 0; q < H / 16; ++q) {
-        float z[16];
-        tmem_ld16(lane_addr(s, 16 * q), z);
-        float a[16];
+// Activation of one value on the CUDA cores (the training kernel's FP32
+// path, and the second layer of the ReLU closure) and its derivative.
+template <int ACT>
+__device__ __forceinline__ float act1(float x) {
+    return ACT == ACT_RELU ? fmaxf(x, 0.f) : gelu(x);
+}
+template <int ACT>
+__device__ __forceinline__ float act_grad(float x) {
+    return ACT == ACT_RELU ? (x > 0.f ? 1.f : 0.f) : gelu_grad(x);
+}
+
+// BF16 act(z) of 16 consecutive columns into row `row` of the second
+// product's A tile.  ReLU: the clamp is part of the conversion, one
+// instruction per pair.
+template <int ACT>
+__device__ __forceinline__ void act_store16(unsigned char* A1, int row, int k0, const float (&z)[16]) {
+    uint32_t w[8];
+    if (ACT == ACT_RELU) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) gelu2(z[i] + s.b1[16 * q + i], z[i + 1] + s.b1[16 * q + i + 1], a[i], a[i + 1]);
-        st_row8(s.A1, row, 16 * q, H, a);
-        st_row8(s.A1, row, 16 * q + 8, H, a + 8);
-    }
-    if (!run_gemm(s, z2col, s.A1, s.W2t, H / 16, phase, status)) return false;
-    float acc = s.b3;
-#pragma unroll 1
-    for (int q = 0; q < H / 16; ++q) {
-        float z[16];
-        tmem_ld16(lane_addr(s, z2col + 16 * q), z);
+        for (int i = 0; i < 8; ++i) w[i] = bf16x2_relu(z[2 * i], z[2 * i + 1]);
+    } else {
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-            float g0, g1;
-            gelu2(z[i] + s.b2[16 * q + i], z[i + 1] + s.b2[16 * q + i + 1], g0, g1);
-            acc = fmaf(g0, s.w3[16 * q + i], acc);
-            acc = fmaf(g1, s.w3[16 * q + i + 1], acc);
+        for (int i = 0; i < 8; ++i) {
+            float a, b;
+            gelu2(z[2 * i], z[2 * i + 1], a, b);
+            w[i] = bf16x2(a, b);
         }
     }
-    c = acc;
+    *reinterpret_cast<uint4*>(A1 + koff(row, k0, KA)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(A1 + koff(row, k0 + 8, KA)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// First epilogue: act(Z1) of this thread's row (TMEM columns col0..col0+63)
+// into the second product's A tile.  The column loops stay rolled: 16
+// activations per pass give enough independent work, and the unrolled
+// body would not fit the instruction cache beside the rest of the fused
+// drag kernel.
+template <int ACT>
+__device__ __forceinline__ void layer1_epilogue(Smem& s, uint32_t col0) {
+#pragma unroll 1
+    for (int q = 0; q < H / 16; ++q) {
+        float z[16];
+        tmem_ld16(lane_addr(s, col0 + 16 * q), z);
+        act_store16<ACT>(s.A1, threadIdx.x, 16 * q, z);
+    }
+}
+
+// Second epilogue: c = act(Z2) w3 + b3 of this thread's row (Z2 in TMEM
+// columns col0..col0+63), in FP32.
+template <int ACT>
+__device__ __forceinline__ float layer2_epilogue(const Smem& s, uint32_t col0) {
+    float acc = s.w.b3;
+#pragma unroll 1
+    for (int q = 0; q < H / 16; ++q) {
+        float z[16];
+        tmem_ld16(lane_addr(s, col0 + 16 * q), z);
+        if (ACT == ACT_RELU) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc = fmaf(fmaxf(z[i], 0.f), s.w.w3[16 * q + i], acc);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                float g0, g1;
+                gelu2(z[i], z[i + 1], g0, g1);
+                acc = fmaf(g0, s.w.w3[16 * q + i], acc);
+                acc = fmaf(g1, s.w.w3[16 * q + i + 1], acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// Forward of the tile: rows' X already in s.X.  Z1 (bias included) goes to
+// TMEM columns 0..63 and Z2 to z2col..z2col+63 (0 reuses Z1's columns,
+// which are read out before GEMM 2 is issued); returns this thread's c.
+template <int ACT>
+__device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* status, float& c, uint32_t z2col) {
+    if (!run_gemm(s, 0, s.X, s.w.W1t, K0 / 16, phase, status)) return false;
+    layer1_epilogue<ACT>(s, 0);
+    if (!run_gemm(s, z2col, s.A1, s.w.W2t, KA / 16, phase, status)) return false;
+    c = layer2_epilogue<ACT>(s, z2col);
     return true;
 }
 
@@ -399,14 +513,14 @@ __device__ bool tile_forward(Smem& s, uint32_t& phase, unsigned long long* statu
 // ---------------------------------------------------------------------------
 // c for every feature row (rows outside the training box still get c; the
 // in-range flag tells the caller).
+template <int ACT>
 __global__ void __launch_bounds__(TILE, 4)
-k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
-              long long n, float* __restrict__ c_out, int32_t* __restrict__ in_range,
-              unsigned long long* __restrict__ status) {
+k_mlp_forward(const WeightImage* __restrict__ img, const float* __restrict__ feat, long long n,
+              float* __restrict__ c_out, int32_t* __restrict__ in_range, unsigned long long* __restrict__ status) {
     pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& s = smem_as<Smem>(smem_raw);
-    load_weights(s, P, scale);
+    load_weights(s, img);
     cta_setup(s, kInferCols);
     uint32_t phase = 0;
     const long long ntiles = (n + TILE - 1) / TILE;
@@ -423,7 +537,7 @@ k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, cons
         st_row8(s.X, threadIdx.x, 0, K0, x);
         st_row8(s.X, threadIdx.x, 8, K0, x + 8);
         float c = 0.f;
-        if (!tile_forward(s, phase, status, c, 0)) break;
+        if (!tile_forward<ACT>(s, phase, status, c, 0)) break;
         if (r < n) {
             c_out[r] = c;
             if (in_range) in_range[r] = ok ? 1 : 0;
@@ -435,15 +549,16 @@ k_mlp_forward(const float* __restrict__ P, const float* __restrict__ scale, cons
 // Loss and gradient partials of a batch: each CTA accumulates its tiles'
 // contributions in a fixed order and writes one partial per parameter.
 // Layout of part: [gridDim.x][NPARAM + 1] (the last entry: sum of residual^2).
+template <int ACT>
 __global__ void __launch_bounds__(TILE, 1)
-k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const float* __restrict__ feat,
+k_mlp_grad(const float* __restrict__ P, const WeightImage* __restrict__ img, const float* __restrict__ feat,
            const float* __restrict__ target, long long n, float* __restrict__ part,
            unsigned long long* __restrict__ status) {
     pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     SmemTrain& st = smem_as<SmemTrain>(smem_raw);
     Smem& s = st.s;
-    load_weights(s, P, scale);
+    load_weights(s, img);
     load_w2b(st, P);
     cta_setup(s, kTrainCols);
     uint32_t phase = 0;
@@ -473,12 +588,12 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
         st_row8(s.X, tid, 0, K0, x);
         st_row8(s.X, tid, 8, K0, x + 8);
         float c = 0.f;
-        if (!tile_forward(s, phase, status, c, 64)) break;
+        if (!tile_forward<ACT>(s, phase, status, c, 64)) break;
         const float res = (r < n) ? (c - tg) : 0.f;
         const float dc = 2.0f * res * inv_n;
         st.dc[tid] = dc;
         st.r2[tid] = res * res;
-        // dZ2 = dc w3 * GELU'(Z2); A2 dc for the w3 gradient
+        // dZ2 = dc w3 * act'(Z2); A2 dc for the w3 gradient
 #pragma unroll
         for (int q = 0; q < H / 16; ++q) {
             float z[16], d[16];
@@ -486,10 +601,9 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int j = 16 * q + i;
-                const float zz = z[i] + s.b2[j];
-                d[i] = dc * s.w3[j] * gelu_grad(zz);
+                d[i] = dc * s.w.w3[j] * act_grad<ACT>(z[i]);
                 st.dZ2[tid][j] = d[i];
-                st.A2dc[tid][j] = gelu(zz) * dc;
+                st.A2dc[tid][j] = act1<ACT>(z[i]) * dc;
             }
             st_row8(st.dZ2b, tid, 16 * q, H, d);
             st_row8(st.dZ2b, tid, 16 * q + 8, H, d + 8);
@@ -502,7 +616,7 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
             tmem_ld16(lane_addr(s, 128 + 16 * q), da);
             tmem_ld16(lane_addr(s, 16 * q), z1);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) st.dZ1[tid][16 * q + i] = da[i] * gelu_grad(z1[i] + s.b1[16 * q + i]);
+            for (int i = 0; i < 16; ++i) st.dZ1[tid][16 * q + i] = da[i] * act_grad<ACT>(z1[i]);
         }
         __syncthreads();
         // weight gradients, rows summed in increasing order
@@ -510,12 +624,14 @@ k_mlp_grad(const float* __restrict__ P, const float* __restrict__ scale, const f
         for (int row = 0; row < TILE; ++row) {
             // W2 (in, out): entries tid*32 + e -> in = (tid*32+e) / 64, out = (tid*32+e) % 64
             const int in = (tid * 32) / H, out0 = (tid * 32) % H;
-            const float a1 = bf16_val(*reinterpret_cast<const uint16_t*>(s.A1 + koff(row, in, H)));
+            const float a1 = bf16_val(*reinterpret_cast<const uint16_t*>(s.A1 + koff(row, in, KA)));
 #pragma unroll
             for (int e = 0; e < 32; ++e) gW2[e] = fmaf(a1, st.dZ2[row][out0 + e], gW2[e]);
-            // W1 (k, j): entries tid*8 + e -> k = (tid*8+e) / 64, j = (tid*8+e) % 64
+            // W1 (k, j): entries tid*8 + e -> k = (tid*8+e) / 64, j = (tid*8+e) % 64; the
+            // inputs past NFEAT are zero in the network (the tile's ones there meet b1)
             const int k = (tid * 8) / H, j0 = (tid * 8) % H;
-            const float xk = bf16_val(*reinterpret_cast<const uint16_t*>(s.X + koff(row, k, K0)));
+            const float xk =
+                k < NFEAT ? bf16_val(*reinterpret_cast<const uint16_t*>(s.X + koff(row, k, K0))) : 0.f;
 #pragma unroll
             for (int e = 0; e < 8; ++e) gW1[e] = fmaf(xk, st.dZ1[row][j0 + e], gW1[e]);
             if (tid < H) {
@@ -676,6 +792,18 @@ __device__ V4<float> fresh_velocity(const float* __restrict__ u_fine, float x, f
     return {0.f, u[0], u[1], u[2]};
 }
 
+// Shared memory of the learned drag: the forward part, a second mbarrier
+// (completions of the second product) and, for the tile between its two
+// halves, each row's state in a thread-private stash (two tiles deep).
+struct SmemLearned {
+    Smem s;
+    uint64_t bar2;
+    float4 x[2][TILE], v[2][TILE];   // position and velocity as read
+    float4 F[2][TILE];               // stale drag (fallback rows: the drag itself); w = sorted slot
+    int state[2][TILE];              // 0 no row, 1 learned, 2 fallback
+};
+constexpr uint32_t kLearnCols = 128;    // Z of two tiles in flight: columns 0..63 and 64..127
+
 // Learned drag: per tile of 128 particles (caller order) each thread forms
 // its particle's closure inputs and the drag F_stale from the stale bulk
 // record (porosity of this step, fluid velocity and variance of the last
@@ -685,90 +813,134 @@ __device__ V4<float> fresh_velocity(const float* __restrict__ u_fine, float x, f
 // velocity averaged afresh from the fine grid.  The force is also written
 // to its sorted slot for the fused reaction deposit when Fs is given, and
 // with dt > 0 the particle is advanced as the plain drag kernel does.
+//
+// Software pipeline over a CTA's tiles t (two TMEM buffers, b = tile
+// parity): (A) rows of t: inputs (loaded one tile ahead), features, stale
+// drag; issue the first product of t; load the inputs of the next tile;
+// (B) wait for the second product of t - 1, its output c and the stores of
+// t - 1; (C) wait for the first product of t, the activations, issue the
+// second product of t.  The first product runs under (B), the second
+// under the next (A).
+template <int ACT>
 __global__ void __launch_bounds__(TILE, 4)
 k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, const float* __restrict__ bulk_stale,
-               const float* __restrict__ var_stale, const float* __restrict__ u_fine, const float* __restrict__ Pm,
-               const float* __restrict__ scale, float* __restrict__ F, float* __restrict__ Fs,
+               const float* __restrict__ var_stale, const float* __restrict__ u_fine,
+               const WeightImage* __restrict__ img, float* __restrict__ F, float* __restrict__ Fs,
                const int32_t* __restrict__ inv_perm, float dt, float age, unsigned long long* __restrict__ status) {
     pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem& s = smem_as<Smem>(smem_raw);
-    load_weights(s, Pm, scale);
-    cta_setup(s, kInferCols);
-    uint32_t phase = 0;
+    SmemLearned& L = smem_as<SmemLearned>(smem_raw);
+    Smem& s = L.s;
+    const int tid = threadIdx.x;
+    load_weights(s, img);
+    if (tid == 0) mbar_init(&L.bar2, 1);
+    cta_setup(s, kLearnCols);
+    uint32_t ph1 = 0, ph2 = 0;
     unsigned fallbacks = 0, clamped = 0;
     const long long ntiles = (n + TILE - 1) / TILE;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long p = t * TILE + threadIdx.x;
-        float f[FEAT_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
-        float Fst[3] = {0.f, 0.f, 0.f};
-        V4<float> x = {0, 0, 0, 0}, v = {0, 0, 0, 0};
-        float epsc = 1.f, phic = 0.f;
-        if (p < n) {
-            const float4 xa = reinterpret_cast<const float4*>(pos)[p];
-            const float4 va = reinterpret_cast<const float4*>(vel)[p];
-            x = {xa.x, xa.y, xa.z, xa.w};
-            v = {va.x, va.y, va.z, va.w};
-            const Probe<float> st = probe(bulk_stale, var_stale, x.x, x.y, x.z, g);
-            float sv[3], smag;
-            closure_features(st, x, v, g, P, f, epsc, phic, sv, smag);
-            clamped += st.eps < P.eps_min;
-            const float b = drag_beta(g.law, epsc, phic, x.w, smag, P);
-            Fst[0] = b * sv[0];
-            Fst[1] = b * sv[1];
-            Fst[2] = b * sv[2];
+    // this thread's row of the coming tile, loaded a tile ahead
+    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), va = xa;
+    int slot = 0;
+    auto fetch = [&](long long t) {
+        const long long p = t * TILE + tid;
+        if (t < ntiles && p < n) {
+            xa = reinterpret_cast<const float4*>(pos)[p];
+            va = reinterpret_cast<const float4*>(vel)[p];
+            slot = Fs ? __ldg(inv_perm + p) : 0;
         }
-        float xin[K0];
-        const bool ok = scale_row(s, f, xin);
-        st_row8(s.X, threadIdx.x, 0, K0, xin);
-        st_row8(s.X, threadIdx.x, 8, K0, xin + 8);
-        float c = 0.f;
-        if (!tile_forward(s, phase, status, c, 0)) break;
-        if (p < n) {
-            float Fo[3];
-            if (ok) {
-                const float cc = fmaf(age, c, 1.0f);   // correction after `age` steps
-                Fo[0] = cc * Fst[0];
-                Fo[1] = cc * Fst[1];
-                Fo[2] = cc * Fst[2];
-            } else {
+    };
+    fetch(blockIdx.x);
+    long long prev = -1;
+    int b = 0;
+    for (long long t = blockIdx.x;; t += gridDim.x) {
+        const bool have = t < ntiles;
+        if (have) {
+            // (A) rows of tile t
+            const long long p = t * TILE + tid;
+            float f[FEAT_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float Fo[3] = {0.f, 0.f, 0.f};
+            float epsc = 1.f, phic = 0.f;
+            if (p < n) {
+                const Probe<float> st = probe(bulk_stale, var_stale, xa.x, xa.y, xa.z, g);
+                const V4<float> x = {xa.x, xa.y, xa.z, xa.w}, v = {va.x, va.y, va.z, va.w};
+                float sv[3], smag;
+                closure_features(st, x, v, g, P, f, epsc, phic, sv, smag);
+                clamped += st.eps < P.eps_min;
+                const float be = drag_beta(g.law, epsc, phic, xa.w, smag, P);
+                Fo[0] = be * sv[0];
+                Fo[1] = be * sv[1];
+                Fo[2] = be * sv[2];
+            }
+            float xin[K0];
+            const bool ok = scale_row(s, f, xin);
+            st_row8(s.X, tid, 0, K0, xin);
+            st_row8(s.X, tid, 8, K0, xin + 8);
+            if (p < n && !ok) {
+                // out of the training box: the plain drag with the fluid velocity averaged afresh
                 ++fallbacks;
-                const V4<float> uf = fresh_velocity(u_fine, x.x, x.y, x.z, g);
-                const float sf[3] = {uf.y - v.x, uf.z - v.y, uf.w - v.z};
+                const V4<float> uf = fresh_velocity(u_fine, xa.x, xa.y, xa.z, g);
+                const float sf[3] = {uf.y - va.x, uf.z - va.y, uf.w - va.z};
                 const float sm = sqrtf(sf[0] * sf[0] + sf[1] * sf[1] + sf[2] * sf[2]);
-                const float b = drag_beta(g.law, epsc, phic, x.w, sm, P);
-                Fo[0] = b * sf[0];
-                Fo[1] = b * sf[1];
-                Fo[2] = b * sf[2];
+                const float be = drag_beta(g.law, epsc, phic, xa.w, sm, P);
+                Fo[0] = be * sf[0];
+                Fo[1] = be * sf[1];
+                Fo[2] = be * sf[2];
             }
-            F[p] = Fo[0];
-            F[n + p] = Fo[1];
-            F[2 * n + p] = Fo[2];
-            if (Fs) st4(Fs, __ldg(inv_perm + p), Fo[0], Fo[1], Fo[2], 0.f);
-            if (dt > 0.f) {
-                const float m = P.rho_p * M<float>::pi6() * x.w * x.w * x.w;
-                float xn[3] = {x.x, x.y, x.z};
-                float un[3] = {v.x + dt * (Fo[0] / m + P.g[0]), v.y + dt * (Fo[1] / m + P.g[1]),
-                               v.z + dt * (Fo[2] / m + P.g[2])};
+            L.x[b][tid] = xa;
+            L.v[b][tid] = va;
+            L.F[b][tid] = make_float4(Fo[0], Fo[1], Fo[2], __int_as_float(slot));
+            L.state[b][tid] = p < n ? (ok ? 1 : 2) : 0;
+            gemm_issue(s, &s.bar, (uint32_t)b * 64, s.X, s.w.W1t, K0 / 16);
+            fetch(t + gridDim.x);
+        }
+        if (prev >= 0) {
+            // (B) tile prev: its second product, c, the outputs
+            if (!gemm_wait(s, &L.bar2, ph2, status)) break;
+            const int pb = b ^ 1;
+            const float c = layer2_epilogue<ACT>(s, (uint32_t)pb * 64);
+            const int state = L.state[pb][tid];
+            if (state) {
+                const long long p = prev * TILE + tid;
+                const float4 Fv = L.F[pb][tid];
+                const float cc = state == 1 ? fmaf(age, c, 1.0f) : 1.0f;   // correction after `age` steps
+                const float Fo[3] = {cc * Fv.x, cc * Fv.y, cc * Fv.z};
+                F[p] = Fo[0];
+                F[n + p] = Fo[1];
+                F[2 * n + p] = Fo[2];
+                if (Fs) st4(Fs, __float_as_int(Fv.w), Fo[0], Fo[1], Fo[2], 0.f);
+                if (dt > 0.f) {
+                    const float4 x = L.x[pb][tid], v = L.v[pb][tid];
+                    const float m = P.rho_p * M<float>::pi6() * x.w * x.w * x.w;
+                    float xn[3] = {x.x, x.y, x.z};
+                    float un[3] = {v.x + dt * (Fo[0] / m + P.g[0]), v.y + dt * (Fo[1] / m + P.g[1]),
+                                   v.z + dt * (Fo[2] / m + P.g[2])};
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float xa = xn[a] + dt * un[a];
-                    const float lo = (float)g.x0[a], hi = (float)g.xhi[a];
-                    if (xa < lo) { xa = 2.f * lo - xa; un[a] = -un[a]; }
-                    else if (xa > hi) { xa = 2.f * hi - xa; un[a] = -un[a]; }
-                    xn[a] = xa;
+                    for (int a = 0; a < 3; ++a) {
+                        float xq = xn[a] + dt * un[a];
+                        const float lo = (float)g.x0[a], hi = (float)g.xhi[a];
+                        if (xq < lo) { xq = 2.f * lo - xq; un[a] = -un[a]; }
+                        else if (xq > hi) { xq = 2.f * hi - xq; un[a] = -un[a]; }
+                        xn[a] = xq;
+                    }
+                    st4(pos, p, xn[0], xn[1], xn[2], x.w);
+                    st4(vel, p, un[0], un[1], un[2], v.w);
                 }
-                st4(pos, p, xn[0], xn[1], xn[2], x.w);
-                st4(vel, p, un[0], un[1], un[2], v.w);
             }
         }
+        if (!have) break;
+        // (C) tile t: first product, activations, second product
+        if (!gemm_wait(s, &s.bar, ph1, status)) break;
+        layer1_epilogue<ACT>(s, (uint32_t)b * 64);
+        gemm_issue(s, &L.bar2, (uint32_t)b * 64, s.A1, s.w.W2t, KA / 16);
+        prev = t;
+        b ^= 1;
     }
     if (fallbacks) atomicAdd(&status[ST_FALLBACK], (unsigned long long)fallbacks);
     if (clamped) {
         atomicAdd(&status[ST_CLAMPED], (unsigned long long)clamped);
         atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
     }
-    cta_teardown(s, kInferCols);
+    cta_teardown(s, kLearnCols, &L.bar2);
 }
 
 }  // namespace mlp
@@ -785,6 +957,7 @@ struct cg_mlp {
     float* v = nullptr;        // Adam second moments
     float* grads = nullptr;    // last reduced gradient
     float* scale = nullptr;    // lo[8], 1/(hi - lo)[8]
+    cg::mlp::WeightImage* img = nullptr;   // the forward operands, rebuilt whenever P changes
     float* part = nullptr;     // CTA partials
     unsigned long long* status = nullptr;
     float lo[8] = {0}, hi[8] = {0};
@@ -792,6 +965,7 @@ struct cg_mlp {
     const void* var_bulk = nullptr;   // bound inputs of the fused learned drag
     const void* u_fine = nullptr;
     int32_t age = 1;
+    int32_t act = CG_MLP_GELU;        // activation of both hidden layers
 };
 
 namespace {
@@ -802,19 +976,38 @@ using namespace cg::mlp;
 // SM's 512 (a training CTA, 256 columns and over 150 KB, leaves room for at
 // most two of them beside it).
 size_t smem_forward() { return std::max<size_t>(sizeof(Smem) + 1024, 28 * 1024); }
-size_t smem_learned() { return smem_forward(); }
+// A learned-drag CTA holds 128 TMEM columns: its shared memory (over 46 KB)
+// keeps it to four per SM, whose columns fill the SM's 512 at most.
+size_t smem_learned() { return std::max<size_t>(sizeof(SmemLearned) + 1024, 47 * 1024); }
 size_t smem_train() { return sizeof(SmemTrain) + 1024; }
 cg::PerDeviceOnce g_mlp_attr_once;
 
+template <int ACT>
+cudaError_t mlp_attrs_of() {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_forward());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_grad<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_drag_learned<ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_learned());
+    return e;
+}
+
 cg_status mlp_attrs() {
     return cg::once_per_device(g_mlp_attr_once, [] {
-        CG_CUDA(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_forward()));
-        CG_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_train()));
-        CG_CUDA(cudaFuncSetAttribute(k_drag_learned, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_learned()));
+        CG_CUDA(mlp_attrs_of<ACT_GELU>());
+        CG_CUDA(mlp_attrs_of<ACT_RELU>());
         return CG_OK;
     });
+}
+
+// Rebuild the weight image from P on the closure's stream (after every
+// change of P, in the same stream order).
+cg_status rebuild_image(cg_mlp* m) {
+    k_mlp_image<<<1, 256, 0, m->stream>>>(m->P, m->scale, m->img);
+    CG_CUDA(cudaGetLastError());
+    return CG_OK;
 }
 
 void host_scale(const float* lo, const float* hi, float out[16]) {
@@ -848,10 +1041,11 @@ cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* p
     if (n > 0) {
         const long long ntiles = (n + TILE - 1) / TILE;
         const unsigned grid = (unsigned)std::min(ntiles, (long long)4 * g->num_sms);
-        CG_LAUNCH(g, "drag_learned", k_drag_learned, grid, TILE, smem_learned(), (float*)pos_d, (float*)vel, n,
-                  g->gd, cg::phys_of<float>(g->gd), (const float*)g->bulk4, (const float*)var_stale,
-                  (const float*)u_fine, m->P, m->scale, (float*)force, (float*)Fs, g->inv_perm, (float)dt,
-                  (float)age, g->status);
+        auto kern = m->act == CG_MLP_RELU ? k_drag_learned<ACT_RELU> : k_drag_learned<ACT_GELU>;
+        CG_LAUNCH(g, "drag_learned", kern, grid, TILE, smem_learned(), (float*)pos_d, (float*)vel, n, g->gd,
+                  cg::phys_of<float>(g->gd), (const float*)g->bulk4, (const float*)var_stale, (const float*)u_fine,
+                  (const WeightImage*)m->img, (float*)force, (float*)Fs, g->inv_perm, (float)dt, (float)age,
+                  g->status);
     }
     if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, true));
     return CG_OK;
@@ -935,15 +1129,17 @@ cg_status cg_mlp_create(const float* params, const float* feat_lo, const float* 
     bool ok = cudaMalloc(&m->P, pb) == cudaSuccess && cudaMalloc(&m->m, pb) == cudaSuccess &&
               cudaMalloc(&m->v, pb) == cudaSuccess && cudaMalloc(&m->grads, pb) == cudaSuccess &&
               cudaMalloc(&m->scale, sizeof sc) == cudaSuccess && cudaMalloc(&m->part, partb) == cudaSuccess &&
+              cudaMalloc(&m->img, sizeof(WeightImage)) == cudaSuccess &&
               cudaMalloc(&m->status, sizeof(unsigned long long) * cg::kNumSlots) == cudaSuccess;
     ok = ok && cudaMemcpy(m->P, params, pb, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(m->m, 0, pb) == cudaSuccess && cudaMemset(m->v, 0, pb) == cudaSuccess &&
          cudaMemcpy(m->scale, sc, sizeof sc, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(m->status, 0, sizeof(unsigned long long) * cg::kNumSlots) == cudaSuccess;
-    if (!ok || mlp_attrs() != CG_OK) {
+    ok = ok && mlp_attrs() == CG_OK && rebuild_image(m) == CG_OK && cudaStreamSynchronize(m->stream) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         cudaFree(m->P); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grads); cudaFree(m->scale);
-        cudaFree(m->part); cudaFree(m->status);
+        cudaFree(m->part); cudaFree(m->status); cudaFree(m->img);
         delete m;
         return CG_ERR_OOM;
     }
@@ -955,7 +1151,7 @@ cg_status cg_mlp_destroy(cg_mlp* m) {
     if (!m) return CG_OK;
     cudaStreamSynchronize(m->stream);
     cudaFree(m->P); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grads); cudaFree(m->scale);
-    cudaFree(m->part); cudaFree(m->status);
+    cudaFree(m->part); cudaFree(m->status); cudaFree(m->img);
     cudaGetLastError();
     delete m;
     return CG_OK;
@@ -970,9 +1166,22 @@ cg_status cg_mlp_get_params(cg_mlp* m, float* params, float* grads) {
     return CG_OK;
 }
 
+cg_status cg_mlp_set_activation(cg_mlp* m, int32_t activation) {
+    if (!m || (activation != CG_MLP_GELU && activation != CG_MLP_RELU)) return CG_ERR_INVALID_ARG;
+    m->act = activation;
+    return CG_OK;
+}
+
+cg_status cg_mlp_get_activation(const cg_mlp* m, int32_t* activation) {
+    if (!m || !activation) return CG_ERR_INVALID_ARG;
+    *activation = m->act;
+    return CG_OK;
+}
+
 cg_status cg_mlp_set_params(cg_mlp* m, const float* params) {
     if (!m || !params) return CG_ERR_INVALID_ARG;
     CG_CUDA(cudaMemcpyAsync(m->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, m->stream));
+    CG_TRY(rebuild_image(m));
     CG_CUDA(cudaStreamSynchronize(m->stream));
     return CG_OK;
 }
@@ -983,7 +1192,8 @@ cg_status cg_mlp_forward(cg_mlp* m, int64_t n, const float* features, float* c_o
     CG_TRY(mlp_attrs());
     const long long ntiles = (n + TILE - 1) / TILE;
     const unsigned grid = (unsigned)std::min(ntiles, (long long)4 * m->num_sms);
-    k_mlp_forward<<<grid, TILE, smem_forward(), m->stream>>>(m->P, m->scale, features, n, c_out, in_range_out, m->status);
+    auto kern = m->act == CG_MLP_RELU ? k_mlp_forward<ACT_RELU> : k_mlp_forward<ACT_GELU>;
+    kern<<<grid, TILE, smem_forward(), m->stream>>>(m->img, features, n, c_out, in_range_out, m->status);
     CG_CUDA(cudaGetLastError());
     return CG_OK;
 }
@@ -994,12 +1204,14 @@ static cg_status grad_impl(cg_mlp* m, int64_t n, const float* features, const fl
     CG_TRY(mlp_attrs());
     const long long ntiles = (n + TILE - 1) / TILE;
     const int grid = (int)std::min(ntiles, (long long)m->num_sms);
-    k_mlp_grad<<<grid, TILE, smem_train(), m->stream>>>(m->P, m->scale, features, targets, n, m->part, m->status);
+    auto kern = m->act == CG_MLP_RELU ? k_mlp_grad<ACT_RELU> : k_mlp_grad<ACT_GELU>;
+    kern<<<grid, TILE, smem_train(), m->stream>>>(m->P, m->img, features, targets, n, m->part, m->status);
     CG_CUDA(cudaGetLastError());
     if (do_update) m->t += 1;
     k_mlp_reduce_adam<<<(NPARAM + 1 + 255) / 256, 256, 0, m->stream>>>(m->part, grid, m->grads, m->P, m->m, m->v,
                                                                         m->t, lr, do_update, loss_out, n);
     CG_CUDA(cudaGetLastError());
+    if (do_update) CG_TRY(rebuild_image(m));
     return CG_OK;
 }
 

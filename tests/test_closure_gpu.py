@@ -88,7 +88,7 @@ def test_features_fp32_grids(cuda_lib):
 
 
 # ---------------------------------------------------------------- learned drag
-def _closure(cg, fo, seed=0, q=(0.03, 0.97)):
+def _closure(cg, fo, seed=0, q=(0.03, 0.97), act="gelu"):
     """A random closure with a feature box from quantiles of the oracle's
     features (so that a good share of rows falls outside)."""
     lo = np.quantile(fo[:, :7], q[0], axis=0).astype(np.float32)
@@ -98,11 +98,11 @@ def _closure(cg, fo, seed=0, q=(0.03, 0.97)):
     rng = np.random.default_rng(seed + 1)
     p["b1"] = rng.normal(size=64) * 0.1
     p["b2"] = rng.normal(size=64) * 0.1
-    m = cg.Mlp(cg.mlp_pack(p), lo, hi)
+    m = cg.Mlp(cg.mlp_pack(p), lo, hi, activation=act)
     return m, cg.mlp_unpack(cg.mlp_pack(p)), lo, hi
 
 
-def _expected_learned(w, ref, ub1, p, lo, hi, age=1):
+def _expected_learned(w, ref, ub1, p, lo, hi, age=1, act="gelu"):
     """Oracle learned forces, the in-range decision, and the rows whose
     decision sits within rounding of the box edge."""
     fo, _, Fs = oracle.mlp_features(w.desc, w.pos_d, w.vel, ref["eps_bulk"], ref["u_bulk"], ref["var_bulk"], ub1)
@@ -113,7 +113,7 @@ def _expected_learned(w, ref, ub1, p, lo, hi, age=1):
     edge = np.any((np.abs(xs) < 1e-4) | (np.abs(xs - 1) < 1e-4), axis=1)
     X = np.zeros((w.n, om.K0))
     X[:, :7] = xs
-    r, _ = om.forward(p, X, bf16_inputs=True)
+    r, _ = om.forward(p, X, bf16_inputs=True, act=act)
     F_fresh, _ = oracle.drag(w.desc, w.pos_d, w.vel, ref["eps_bulk"], ub1)
     return (1.0 + age * r) * Fs, F_fresh, inside, edge, Fs
 
@@ -134,15 +134,16 @@ def _learned_drag(cg, w, ref, ub1, u1, m, age):
     return out
 
 
+@pytest.mark.parametrize("act", ["gelu", "relu"])
 @pytest.mark.parametrize("make", [synth.small_clustered_bed, synth.small_packed_bed])
-def test_learned_drag_matches_oracle(cuda_lib, make):
+def test_learned_drag_matches_oracle(cuda_lib, make, act):
     w = make(seed=2)
     ref, u1, ub1 = _records(w)
     fo, _, _ = oracle.mlp_features(w.desc, w.pos_d, w.vel, ref["eps_bulk"], ref["u_bulk"], ref["var_bulk"], ub1)
-    m, p, lo, hi = _closure(cuda_lib, fo)
+    m, p, lo, hi = _closure(cuda_lib, fo, act=act)
     age = 2
     F, counts = _learned_drag(cuda_lib, w, ref, ub1, u1, m, age)
-    F_c, F_fresh, inside, edge, Fs = _expected_learned(w, ref, ub1, p, lo, hi, age)
+    F_c, F_fresh, inside, edge, Fs = _expected_learned(w, ref, ub1, p, lo, hi, age, act)
     sure = ~edge
     print("rows", w.n, "in range", inside.sum(), "edge", edge.sum(), "fallbacks", counts[4])
     assert 0.1 * w.n < (~inside).sum() < 0.9 * w.n

@@ -8,7 +8,7 @@ seeds 0 and 1 with the bulk record refreshed every 2, 5 and 10 steps, and
 scored on held-out seed 2 against the plain path with a fresh average on
 every step: the relative L2 drag error of the learned drag must be well
 below that of the stale drag (c = 1) at every refresh interval, with few
-rows falling back.
+rows falling back, for either activation of the closure.
 """
 import pytest
 
@@ -18,13 +18,21 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def trained(cuda_lib):
+def pairs(cuda_lib):
     from paper_1807_11834_gb300 import closure
     F, T = closure.generate_pairs(synth.small_clustered_bed, seeds=(0, 1), refreshes=(2, 5, 10), steps=12,
                                   n_pairs=400_000)
     assert F.shape[0] >= 390_000 and T.shape == (F.shape[0],)
-    m, hist = closure.train(F, T, epochs=20, batch=16384, lr=2e-3)
-    print("loss (standardised)", hist[0], "->", hist[-1])
+    return F, T
+
+
+@pytest.fixture(scope="module", params=["gelu", "relu"])
+def trained(pairs, request):
+    from paper_1807_11834_gb300 import closure
+    F, T = pairs
+    m, hist = closure.train(F, T, epochs=20, batch=16384, lr=2e-3, activation=request.param)
+    print(request.param, "loss (standardised)", hist[0], "->", hist[-1])
+    assert m.activation == request.param
     assert hist[-1] < 0.2 * hist[0]
     yield closure, m
     m.close()

@@ -2,10 +2,12 @@
 
 The oracle runs in its bf16 mode: the operands of the matrix products are
 rounded to bfloat16 where the kernels round them, and everything else is
-float64.  The remaining differences are FP32 accumulation and FP32 GELU in
-the kernels, plus rare one-ulp differences in re-rounding a hidden
+float64.  The remaining differences are FP32 accumulation (the biases
+included, which enter the products as three exact BF16 terms) and the FP32
+GELU in the kernels, plus rare one-ulp differences in re-rounding a hidden
 activation to bfloat16 when it sits on a rounding boundary (each moves c by
-at most ~2^-8 of one term).  Tolerances below are set from that: c within
+at most ~2^-8 of one term).  Both activations, GELU and ReLU, are held to
+the same bounds.  Tolerances below are set from that: c within
 1e-4 absolute on 99.9% of the rows (c ~ 1; measured ~1e-5 at the maximum)
 and within 5e-3 on the rare boundary rows; gradients within 1e-3 relative
 per parameter block (norm-wise; measured ~1.5e-5), Adam within 1e-5 of the
@@ -38,18 +40,23 @@ def random_features(n, seed):
     return f
 
 
-def make(cg, seed=0):
+def make(cg, seed=0, act="gelu"):
     p = om.init_params(hidden=64, seed=seed)
     rng = np.random.default_rng(seed + 10)
     p["b1"] = rng.normal(size=64) * 0.1
     p["b2"] = rng.normal(size=64) * 0.1
-    m = cg.Mlp(cg.mlp_pack(p), LO, HI)
+    m = cg.Mlp(cg.mlp_pack(p), LO, HI, activation=act)
+    assert m.activation == act
     return m, cg.mlp_unpack(cg.mlp_pack(p))
 
 
-def test_forward_matches_oracle(cuda_lib):
+ACTS = pytest.mark.parametrize("act", ["gelu", "relu"])
+
+
+@ACTS
+def test_forward_matches_oracle(cuda_lib, act):
     import torch
-    m, p = make(cuda_lib, 0)
+    m, p = make(cuda_lib, 0, act)
     n = 1000                      # 8 tiles of 128, ragged tail
     feat = random_features(n, 1)
     f_d = torch.from_numpy(feat).cuda()
@@ -57,7 +64,7 @@ def test_forward_matches_oracle(cuda_lib):
     ok = torch.empty(n, dtype=torch.int32, device="cuda")
     m.forward(f_d, c, ok)
     assert m.sync_status()[0] == 0
-    want, _ = om.forward(p, scaled(feat), bf16_inputs=True)
+    want, _ = om.forward(p, scaled(feat), bf16_inputs=True, act=act)
     got = c.cpu().numpy()
     err = np.abs(got - want)
     print("forward max abs err", err.max(), "median", np.median(err), "p99.9", np.quantile(err, 0.999))
@@ -73,9 +80,10 @@ def test_forward_matches_oracle(cuda_lib):
     m.close()
 
 
-def test_gradients_match_oracle(cuda_lib):
+@ACTS
+def test_gradients_match_oracle(cuda_lib, act):
     import torch
-    m, p = make(cuda_lib, 1)
+    m, p = make(cuda_lib, 1, act)
     n = 777
     feat = random_features(n, 2)
     rng = np.random.default_rng(3)
@@ -84,7 +92,7 @@ def test_gradients_match_oracle(cuda_lib):
     m.grads(torch.from_numpy(feat).cuda(), torch.from_numpy(target).cuda(), loss)
     _, g_flat = m.params(grads=True)
     g = cuda_lib.mlp_unpack(g_flat)
-    want_loss, want = om.loss_and_grads(p, scaled(feat), target.astype(np.float64), bf16_inputs=True)
+    want_loss, want = om.loss_and_grads(p, scaled(feat), target.astype(np.float64), bf16_inputs=True, act=act)
     assert loss.item() == pytest.approx(want_loss, rel=1e-4)
     for k in want:
         num = np.linalg.norm(g[k] - want[k])
@@ -94,9 +102,10 @@ def test_gradients_match_oracle(cuda_lib):
     m.close()
 
 
-def test_adam_step_matches_oracle_update(cuda_lib):
+@ACTS
+def test_adam_step_matches_oracle_update(cuda_lib, act):
     import torch
-    m, p = make(cuda_lib, 2)
+    m, p = make(cuda_lib, 2, act)
     n = 512
     feat = torch.from_numpy(random_features(n, 4)).cuda()
     target = torch.full((n,), 1.2, device="cuda")
@@ -109,9 +118,10 @@ def test_adam_step_matches_oracle_update(cuda_lib):
     m.close()
 
 
-def test_training_fits_a_smooth_target(cuda_lib):
+@ACTS
+def test_training_fits_a_smooth_target(cuda_lib, act):
     import torch
-    m, _ = make(cuda_lib, 3)
+    m, _ = make(cuda_lib, 3, act)
     n = 8192
     feat_np = random_features(n, 5)
     x = scaled(feat_np)
@@ -159,14 +169,15 @@ def test_bounded_wait_expires_into_a_timeout_status(cuda_lib):
     m.close()
 
 
-def test_checkpoint_round_trip_through_the_c_abi(cuda_lib, tmp_path):
+@ACTS
+def test_checkpoint_round_trip_through_the_c_abi(cuda_lib, tmp_path, act):
     """cg_mlp_save of a trained-in-place closure, then cg_mlp_load: the
-    loaded closure holds the same parameters and feature box bit for bit
+    loaded closure holds the same parameters, feature box and activation
     and computes the same c on the same rows; the Python reader reads the
     same files."""
     import torch
     from paper_1807_11834_gb300 import closure
-    m, _ = make(cuda_lib, 3)
+    m, _ = make(cuda_lib, 3, act)
     feat = random_features(700, 4)
     f_d = torch.from_numpy(feat).cuda()
     tg = torch.rand(700, device="cuda")
@@ -176,12 +187,25 @@ def test_checkpoint_round_trip_through_the_c_abi(cuda_lib, tmp_path):
     m2 = cuda_lib.Mlp.load(base)
     assert m2.params().tobytes() == m.params().tobytes()
     assert m2.lo.tobytes() == m.lo.tobytes() and m2.hi.tobytes() == m.hi.tobytes()
+    assert m2.activation == act
     c1, c2 = torch.empty(700, device="cuda"), torch.empty(700, device="cuda")
     m.forward(f_d, c1)
     m2.forward(f_d, c2)
     torch.cuda.synchronize()
     assert torch.equal(c1, c2)
-    q, lo, hi, meta = closure.load_checkpoint(base)
-    assert q.tobytes() == m.params().tobytes() and meta == {"steps": 1}
+    q, lo, hi, meta, act2 = closure.load_checkpoint(base)
+    assert q.tobytes() == m.params().tobytes() and meta == {"steps": 1} and act2 == act
     m.close()
     m2.close()
+
+
+def test_activation_argument_checks(cuda_lib):
+    cg = cuda_lib
+    m, _ = make(cg, 0)
+    assert m.activation == "gelu"
+    assert cg.lib().cg_mlp_set_activation(m.h, 2) == 1
+    assert cg.lib().cg_mlp_set_activation(m.h, -1) == 1
+    assert m.activation == "gelu"
+    with pytest.raises(ValueError):
+        cg.Mlp(m.params(), LO, HI, activation="tanh")
+    m.close()

@@ -2,8 +2,10 @@
 
 The closure is not in the paper; these pins tie the oracle to definitions
 it does not share code with: torch's own bfloat16 conversion, closed-form
-GELU values, central differences of the loss, the closed form of the first
-Adam step, and closed-form closure targets in the Stokes regime.
+GELU values, the linear closed forms and the positive homogeneity of the
+ReLU network, central differences and complex steps of the loss, the closed
+form of the first Adam step, and closed-form closure targets in the Stokes
+regime.
 """
 import math
 
@@ -38,7 +40,44 @@ def test_gelu_closed_forms_and_derivative():
     assert np.allclose(mlp.gelu_grad(x), fd, rtol=1e-7, atol=1e-9)
 
 
-def test_backprop_matches_central_differences():
+def test_relu_network_closed_forms():
+    """With every input, weight and bias of the hidden layers non-negative
+    no unit is cut, and the network is the affine map
+    ((X W1 + b1) W2 + b2) w3 + b3; with b2 far below zero every second-layer
+    unit is cut and c = b3; with zero biases the network is positively
+    homogeneous, c(a X) - b3 = a (c(X) - b3) for a > 0."""
+    rng = np.random.default_rng(6)
+    p = mlp.init_params(hidden=16, seed=2)
+    X = np.zeros((21, mlp.K0))
+    X[:, :mlp.NFEAT] = rng.random((21, mlp.NFEAT))
+    q = dict(p)
+    q["W1"] = np.abs(p["W1"])
+    q["W2"] = np.abs(p["W2"])
+    q["b1"] = rng.random(16)
+    q["b2"] = rng.random(16)
+    c, _ = mlp.forward(q, X, act="relu")
+    affine = ((X @ q["W1"] + q["b1"]) @ q["W2"] + q["b2"]) @ q["w3"] + q["b3"][0]
+    assert np.allclose(c, affine, rtol=1e-13, atol=1e-13)
+    q["b2"] = np.full(16, -1e3)
+    c, _ = mlp.forward(q, X, act="relu")
+    assert np.all(c == q["b3"][0])
+    z = dict(p)
+    z["b1"] = np.zeros(16)
+    z["b2"] = np.zeros(16)
+    z["b3"] = np.array([0.7])
+    c1, _ = mlp.forward(z, X, act="relu")
+    c3, _ = mlp.forward(z, 3.5 * X, act="relu")
+    assert np.allclose(c3 - 0.7, 3.5 * (c1 - 0.7), rtol=1e-12, atol=1e-14)
+    # the GELU network is not homogeneous: the pin would catch a swapped activation
+    g1, _ = mlp.forward(z, X)
+    g3, _ = mlp.forward(z, 3.5 * X)
+    assert not np.allclose(g3 - 0.7, 3.5 * (g1 - 0.7), rtol=1e-3)
+    assert mlp.relu(-2.0) == 0.0 and mlp.relu(3.0) == 3.0
+    assert mlp.relu_grad(-2.0) == 0.0 and mlp.relu_grad(3.0) == 1.0 and mlp.relu_grad(0.0) == 0.0
+
+
+@pytest.mark.parametrize("act", ["gelu", "relu"])
+def test_backprop_matches_central_differences(act):
     rng = np.random.default_rng(1)
     p = mlp.init_params(hidden=8, seed=3)
     p["b1"] = rng.normal(size=8) * 0.1
@@ -46,16 +85,16 @@ def test_backprop_matches_central_differences():
     X = np.zeros((13, mlp.K0))
     X[:, :mlp.NFEAT] = rng.random((13, mlp.NFEAT))
     t = 1.0 + 0.3 * rng.normal(size=13)
-    loss, g = mlp.loss_and_grads(p, X, t)
+    loss, g = mlp.loss_and_grads(p, X, t, act=act)
     h = 1e-6
     for k, v in p.items():
         flat = v.reshape(-1)
         for idx in range(flat.size):
             q = {kk: vv.copy() for kk, vv in p.items()}
             q[k].reshape(-1)[idx] += h
-            lp, _ = mlp.loss_and_grads(q, X, t)
+            lp, _ = mlp.loss_and_grads(q, X, t, act=act)
             q[k].reshape(-1)[idx] -= 2 * h
-            lm, _ = mlp.loss_and_grads(q, X, t)
+            lm, _ = mlp.loss_and_grads(q, X, t, act=act)
             fd = (lp - lm) / (2 * h)
             assert g[k].reshape(-1)[idx] == pytest.approx(fd, rel=1e-5, abs=1e-9), (k, idx)
 
@@ -146,11 +185,13 @@ def test_target_in_stokes_regime_is_velocity_ratio():
     assert np.allclose(Fs[0], 3 * math.pi * 1e-3 * 0.003 * 1e-9 * (1 + 0.15 * re ** 0.687), rtol=1e-12)
 
 
-def test_backprop_matches_complex_step_derivatives():
+@pytest.mark.parametrize("act", ["gelu", "relu"])
+def test_backprop_matches_complex_step_derivatives(act):
     """The FP64 backprop against complex-step derivatives of the oracle's
     own forward pass (Squire & Trapp 1998: f'(x) = Im f(x + ih) / h with no
     subtractive cancellation, so h = 1e-30 gives the derivative to machine
-    precision; the GELU's erf and the matrix products are analytic).  Every
+    precision; the GELU's erf and the matrix products are analytic, and the
+    ReLU is linear on the piece each pre-activation lies on).  Every
     parameter of a small network agrees to 1e-10 relative: the FP64
     reference mode of the closure's gradient."""
     rng = np.random.default_rng(4)
@@ -160,7 +201,7 @@ def test_backprop_matches_complex_step_derivatives():
     X = np.zeros((17, mlp.K0))
     X[:, :mlp.NFEAT] = rng.random((17, mlp.NFEAT))
     t = 1.0 + 0.3 * rng.normal(size=17)
-    _, g = mlp.loss_and_grads(p, X, t)
+    _, g = mlp.loss_and_grads(p, X, t, act=act)
     h = 1e-30
     worst = 0.0
     for k, v in p.items():
@@ -168,7 +209,7 @@ def test_backprop_matches_complex_step_derivatives():
         for idx in range(flat.size):
             q = {kk: vv.astype(np.complex128) for kk, vv in p.items()}
             q[k].reshape(-1)[idx] += 1j * h
-            c, _ = mlp.forward(q, X)
+            c, _ = mlp.forward(q, X, act=act)
             d = np.mean((c - t) ** 2).imag / h
             ref = g[k].reshape(-1)[idx]
             err = abs(ref - d) / max(abs(d), 1e-12)
