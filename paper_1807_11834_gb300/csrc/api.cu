@@ -341,6 +341,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
         h[a] = d.extent[a] / (double)d.fine_n[a];
         gd.invH[a] = 1.0 / gd.H[a];
         gd.x0f[a] = (float)d.origin[a];
+        gd.xhif[a] = (float)gd.xhi[a];
         gd.invHf[a] = (float)gd.invH[a];
         gd.ax0f[a] = (float)fabs(d.origin[a] * gd.invH[a]);
         split_ff(d.origin[a], gd.x0h[a], gd.x0l[a]);
@@ -354,6 +355,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     gd.Vff = (float)gd.Vf;
     split_ff(gd.VB, gd.VBh, gd.VBl);
     split_ff(gd.Vf, gd.Vfh, gd.Vfl);
+    split_ff(gd.invVB, gd.ivBh, gd.ivBl);
     gd.law = d.law;
     gd.interp = d.interp;
     gd.rho_f = d.rho_f;

@@ -112,12 +112,14 @@ struct GridDev {
     double VB, invVB, Vf;
     // float versions for the FP32 path
     float x0f[3];       // (float)x0
+    float xhif[3];      // (float)xhi
     float invHf[3];     // (float)(1/H)
     float ax0f[3];      // |x0 / H| (filter margin term)
     float x0h[3], x0l[3];   // x0 as float-float
     float ihh[3], ihl[3];   // 1/H as float-float
     float invVBf, VBf, Vff;
     float VBh, VBl, Vfh, Vfl;   // V_B, V_f as float-float
+    float ivBh, ivBl;           // 1 / V_B as float-float
     // physics
     int law, interp;
     double rho_f, mu_f, rho_p, eps_switch, eps_min, g[3];
@@ -406,6 +408,46 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
     s = a + b;
     T z = s - a;
     e = (a - (s - z)) + (b - z);
+}
+
+// A float's exact value as a double, assembled from its bits with integer
+// operations (sign, exponent rebiased by 1023 - 127, mantissa shifted to the
+// double's 52 bits), so that no conversion instruction lands on the FP64
+// pipe; subnormal floats (below 2^-126) take the ordinary conversion.
+__device__ __forceinline__ double f32_exact_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u && (u & 0x7fffffu)) return (double)f;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long ex = e == 0u ? 0ull : e == 255u ? 0x7ffull << 52 : (unsigned long long)(e + 896u) << 52;
+    const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sign | ex | man));
+}
+
+// Porosity 1 - V / V_B of a bulk cell from its compensated volume sum
+// V = s + c: as a double (the output) and in the working precision (the
+// drag's record and the porosity projection).  FP32 path: the product with
+// 1 / V_B and the difference in float-float (relative error about 2^-46 of
+// V / V_B, the accuracy of the volume sum itself), then one FP64 addition
+// of the exact pair (GB300 issues FP64 at 1/64 of the FP32 rate, and this
+// runs wherever a lane of the warp closes a cell); FP64 path: plain double
+// arithmetic.
+__device__ __forceinline__ void cell_porosity(float s, float c, const GridDev& g, double& e, float& et) {
+    const float ph = s * g.ivBh;
+    float pl = fmaf(s, g.ivBh, -ph);   // s / V_B = ph + pl to second order
+    pl = fmaf(s, g.ivBl, pl);
+    pl = fmaf(c, g.ivBh, pl);
+    float eh, el;
+    two_sum(1.0f, -ph, eh, el);
+    el -= pl;
+    float hi, lo;
+    two_sum(eh, el, hi, lo);
+    e = f32_exact_f64(hi) + f32_exact_f64(lo);
+    et = hi;
+}
+__device__ __forceinline__ void cell_porosity(double s, double c, const GridDev& g, double& e, double& et) {
+    e = 1.0 - (s + c) * g.invVB;
+    et = e;
 }
 
 // Compensated accumulator (TwoSum cascade, Neumaier-equivalent).

@@ -72,7 +72,10 @@ k_deposit_volume(const T* __restrict__ pos, long long n, const int32_t* __restri
             int next = __shfl_down_sync(0xffffffffu, key, 1);
             if (lane == 31) next = (i + 1 < t) ? __ldg(key_sorted + i + 1) : -1;
             if (valid && next != key) {
-                eps[key] = 1.0 - ((double)v[0].s + (double)v[0].c) * g.invVB;
+                double e;
+                T et;
+                cell_porosity(v[0].s, v[0].c, g, e, et);
+                eps[key] = e;
                 tot[0].merge(v[0]);
             }
             carry.s = __shfl_sync(0xffffffffu, v[0].s, 31);
@@ -104,10 +107,12 @@ __device__ __forceinline__ void deposit_volume_sorted_body(const T* __restrict__
             s, t, key_sorted,
             [&](long long i, CSum<T> (&v)[1]) { sphere_volume_pair(__ldg(dsorted + i), v[0].s, v[0].c); },
             [&](int key, const CSum<T> (&a)[1]) {
-                const double e = 1.0 - ((double)a[0].s + (double)a[0].c) * g.invVB;
+                double e;
+                T et;
+                cell_porosity(a[0].s, a[0].c, g, e, et);
                 eps[key] = e;
-                if (rec) rec[4 * (long long)key] = (T)e;   // the drag record's porosity
-                if (eps_t) eps_t[key] = (T)e;
+                if (rec) rec[4 * (long long)key] = et;   // the drag record's porosity
+                if (eps_t) eps_t[key] = et;
                 tot[0].merge(a[0]);
             });
     }

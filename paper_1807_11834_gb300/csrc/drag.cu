@@ -81,7 +81,9 @@ __device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, c
         for (int a = 0; a < 3; ++a) {
             T ua = r.u[a] + dt * (r.f[a] * inv_m + P.g[a]);
             T xa = r.x[a] + dt * ua;
-            const T lo = (T)g.x0[a], hi = (T)g.xhi[a];
+            // the FP32 path reads the bounds' float copies (no conversion in the loop)
+            const T lo = sizeof(T) == 4 ? (T)g.x0f[a] : (T)g.x0[a];
+            const T hi = sizeof(T) == 4 ? (T)g.xhif[a] : (T)g.xhi[a];
             if (xa < lo) { xa = T(2) * lo - xa; ua = -ua; }
             else if (xa > hi) { xa = T(2) * hi - xa; ua = -ua; }
             r.x[a] = xa;

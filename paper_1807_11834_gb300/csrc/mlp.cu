@@ -917,7 +917,7 @@ k_drag_learned(float* pos, float* vel, long long n, GridDev g, Phys<float> P, co
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         float xq = xn[a] + dt * un[a];
-                        const float lo = (float)g.x0[a], hi = (float)g.xhi[a];
+                        const float lo = g.x0f[a], hi = g.xhif[a];
                         if (xq < lo) { xq = 2.f * lo - xq; un[a] = -un[a]; }
                         else if (xq > hi) { xq = 2.f * hi - xq; un[a] = -un[a]; }
                         xn[a] = xq;
