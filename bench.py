@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--step", choices=["auto", "sorted", "caller"], default="auto",
                     help="the step timed: cg_step_sorted (particles left in cell order every step; the default "
                          "for an advancing workload) or cg_step (the caller's particle order kept)")
+    ap.add_argument("--stencil", choices=("gather", "window"), default="gather",
+                    help="the drag's stencil reads: eight loads per particle from L1/L2, or each warp's stencil "
+                         "window staged in shared memory (sorted step only)")
     ap.add_argument("--implicit", action="store_true",
                     help="also form the semi-implicit exchange coefficients (bulk and fine) in every step "
                          "(device entry only: no e2e line)")
@@ -288,6 +291,7 @@ def run_gb300(args):
     sorted_step = args.step == "sorted" or (args.step == "auto" and dt > 0)
     if args.reorder:
         w.desc["sort_digits"] = cg.CG_SORT_CELLS
+    w.desc["stencil"] = cg.CG_STENCIL_WINDOW if args.stencil == "window" else cg.CG_STENCIL_GATHER
     g = cg.Grids(w.desc)
     n = w.n
     dev = torch.device("cuda", local)
@@ -538,6 +542,7 @@ def run_gb300(args):
                        "l2": (f"inputs {input_bytes / 1e6:.0f} MB {'>' if input_bytes > 126e6 else '<'} L2 (126 MB) "
                               "per step, no flush"),
                        "step": "cg_step_sorted" if sorted_step else "cg_step",
+                       "stencil": args.stencil,
                        "timing": ("CUDA graph of one step, replayed K times" if not args.no_graph
                                   else "eager step calls") + (" (one graph per particle buffer, in turn)"
                                                               if sorted_step and not args.no_graph else ""),

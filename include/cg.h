@@ -78,6 +78,10 @@ enum {
 #define CG_SORT_CELLS_AUTO_MAX 8388608   /* 2^23 particles */
 #define CG_SORT_CELLS_AUTO_DENSITY 32   /* particles per bulk cell */
 
+/* Stencil reads of the drag (cg_grid_desc.stencil). */
+#define CG_STENCIL_GATHER 0   /* the eight records of each particle's stencil from global memory */
+#define CG_STENCIL_WINDOW 1   /* in the sorted step, each warp's stencil window staged in shared memory */
+
 /* Number of counters returned by cg_sync_status. */
 #define CG_NCOUNTS 5
 
@@ -106,6 +110,18 @@ enum {
  *                 below 2^20 bulk cells, up to 8 from 2^20 on; an instance of
  *                 a batch (cg_batch_create) takes the digit sort unless its
  *                 descriptor asks for CG_SORT_CELLS
+ *   stencil     how the drag reads the bulk records of each particle's
+ *               trilinear stencil (both give the same bits):
+ *               CG_STENCIL_GATHER (0): eight 16-byte loads per particle,
+ *                 served by L1 and L2 (the bulk record of a 2^22-cell grid
+ *                 is 64 MB, inside the 129 MB L2); the faster choice;
+ *               CG_STENCIL_WINDOW (1): in cg_step_sorted on the FP32
+ *                 trilinear path, each warp stages the bounding box of its
+ *                 32 particles' stencils (with the +1 halo) in shared memory
+ *                 and reads the corners there; a box of more than 64
+ *                 records takes the global gather (measured slower, see
+ *                 the design notes: the kernel is bound by instruction
+ *                 issue, and the window costs instructions)
  * Limits: fine_n[a] % ratio == 0, bulk cells >= 2 per axis, at most 2^22
  * bulk cells and 2^31 - 1 fine cells. */
 typedef struct {
@@ -117,6 +133,7 @@ typedef struct {
     int32_t law;         /* cg_drag_law  */
     int32_t interp;      /* cg_interp    */
     int32_t sort_digits; /* CG_SORT_AUTO, CG_SORT_CELLS or 6..11 */
+    int32_t stencil;     /* CG_STENCIL_GATHER or CG_STENCIL_WINDOW */
     double rho_f, mu_f, rho_p;
     double eps_switch;
     double eps_min;

@@ -39,6 +39,8 @@ CG_SORT_AUTO = 0
 CG_SORT_CELLS = 1
 CG_SORT_CELLS_AUTO_MAX = 1 << 23
 CG_SORT_CELLS_AUTO_DENSITY = 32
+# the drag's stencil reads (descriptor key "stencil")
+CG_STENCIL_GATHER, CG_STENCIL_WINDOW = 0, 1
 SUM_NAMES = ["vol_particles", "vol_deposited", "F_x", "F_y", "F_z", "SbVb_x", "SbVb_y", "SbVb_z",
              "SfVf_x", "SfVf_y", "SfVf_z", "F_abs", "mom_x", "mom_y", "mom_z", "n_clamped"]
 
@@ -52,7 +54,7 @@ class CgError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("extent", C.c_double * 3), ("fine_n", C.c_int32 * 3),
                 ("ratio", C.c_int32), ("prec", C.c_int32), ("law", C.c_int32), ("interp", C.c_int32),
-                ("sort_digits", C.c_int32), ("rho_f", C.c_double), ("mu_f", C.c_double),
+                ("sort_digits", C.c_int32), ("stencil", C.c_int32), ("rho_f", C.c_double), ("mu_f", C.c_double),
                 ("rho_p", C.c_double), ("eps_switch", C.c_double), ("eps_min", C.c_double),
                 ("gravity", C.c_double * 3)]
 
@@ -244,6 +246,7 @@ def make_desc(d: dict) -> GridDesc:
     g.rho_f, g.mu_f, g.rho_p = d["rho_f"], d["mu_f"], d["rho_p"]
     g.eps_switch, g.eps_min = d["eps_switch"], d["eps_min"]
     g.sort_digits = int(d.get("sort_digits", 0))
+    g.stencil = int(d.get("stencil", CG_STENCIL_GATHER))
     g.gravity[:] = d.get("gravity", (0.0, 0.0, 0.0))
     return g
 

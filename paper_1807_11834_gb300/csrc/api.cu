@@ -306,6 +306,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
     if (d.law != CG_DRAG_DI_FELICE && d.law != CG_DRAG_ERGUN_WEN_YU) return CG_ERR_INVALID_ARG;
     if (d.interp != CG_INTERP_TRILINEAR && d.interp != CG_INTERP_CELL) return CG_ERR_INVALID_ARG;
     if (!sort_choice_valid(d.sort_digits)) return CG_ERR_INVALID_ARG;
+    if (d.stencil != CG_STENCIL_GATHER && d.stencil != CG_STENCIL_WINDOW) return CG_ERR_INVALID_ARG;
     if (!(d.rho_f > 0.0) || !(d.mu_f > 0.0) || !(d.rho_p > 0.0) || !isfinite(d.rho_f) || !isfinite(d.mu_f) ||
         !isfinite(d.rho_p))
         return CG_ERR_INVALID_ARG;

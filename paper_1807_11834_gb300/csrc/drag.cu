@@ -48,27 +48,27 @@ struct DragOne {
 };
 
 template <typename T, bool EULER>
-__device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, const GridDev& g, const Phys<T>& P,
-                                               const T* __restrict__ bulk4, T dt) {
+__device__ __forceinline__ DragOne<T> drag_from(const V4<T>& x, const V4<T>& v, const V4<T>& b, const GridDev& g,
+                                                const Phys<T>& P, T dt) {
+    using X = M<T>;
     DragOne<T> r;
-    const V4<T> b = gather(bulk4, x.x, x.y, x.z, g);
     T eps = b.x;
-    T phi = T(1) - eps;
+    T phi = X::sub(T(1), eps);
     r.cl = 0;
     if (eps < P.eps_min) {
         eps = P.eps_min;
-        phi = T(1) - P.eps_min;
+        phi = X::sub(T(1), P.eps_min);
         r.cl = 1;
     }
-    const T sx = b.y - v.x, sy = b.z - v.y, sz = b.w - v.z;
-    r.smag = M<T>::sqrt_(sx * sx + sy * sy + sz * sz);
+    const T sx = X::sub(b.y, v.x), sy = X::sub(b.z, v.y), sz = X::sub(b.w, v.z);
+    r.smag = X::sqrt_(X::fma_(sx, sx, X::fma_(sy, sy, X::mul(sz, sz))));
     const T d = x.w;
     r.beta = drag_beta(g.law, eps, phi, d, r.smag, P);
-    r.f[0] = r.beta * sx;
-    r.f[1] = r.beta * sy;
-    r.f[2] = r.beta * sz;
-    r.vp = M<T>::pi6() * d * d * d;
-    r.m = P.rho_p * r.vp;
+    r.f[0] = X::mul(r.beta, sx);
+    r.f[1] = X::mul(r.beta, sy);
+    r.f[2] = X::mul(r.beta, sz);
+    r.vp = X::mul(X::mul(X::mul(M<T>::pi6(), d), d), d);
+    r.m = X::mul(P.rho_p, r.vp);
     r.x[0] = x.x;
     r.x[1] = x.y;
     r.x[2] = x.z;
@@ -76,16 +76,16 @@ __device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, c
     r.u[1] = v.y;
     r.u[2] = v.z;
     if (EULER) {
-        const T inv_m = T(1) / r.m;   // one division for the three components
+        const T inv_m = X::div(T(1), r.m);   // one division for the three components
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            T ua = r.u[a] + dt * (r.f[a] * inv_m + P.g[a]);
-            T xa = r.x[a] + dt * ua;
+            T ua = X::fma_(dt, X::fma_(r.f[a], inv_m, P.g[a]), r.u[a]);
+            T xa = X::fma_(dt, ua, r.x[a]);
             // the FP32 path reads the bounds' float copies (no conversion in the loop)
             const T lo = sizeof(T) == 4 ? (T)g.x0f[a] : (T)g.x0[a];
             const T hi = sizeof(T) == 4 ? (T)g.xhif[a] : (T)g.xhi[a];
-            if (xa < lo) { xa = T(2) * lo - xa; ua = -ua; }
-            else if (xa > hi) { xa = T(2) * hi - xa; ua = -ua; }
+            if (xa < lo) { xa = X::sub(X::mul(T(2), lo), xa); ua = -ua; }
+            else if (xa > hi) { xa = X::sub(X::mul(T(2), hi), xa); ua = -ua; }
             r.x[a] = xa;
             r.u[a] = ua;
         }
@@ -93,18 +93,92 @@ __device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, c
     return r;
 }
 
+template <typename T, bool EULER>
+__device__ __forceinline__ DragOne<T> drag_one(const V4<T>& x, const V4<T>& v, const GridDev& g, const Phys<T>& P,
+                                               const T* __restrict__ bulk4, T dt) {
+    return drag_from<T, EULER>(x, v, gather(bulk4, x.x, x.y, x.z, g), g, P, dt);
+}
+
+// Stencil window of a warp (particles in cell order): the bounding box of
+// the 32 particles' stencil base cells, grown by the +1 halo on each axis,
+// staged from the bulk record into the warp's slice of shared memory with
+// one 16-byte load per record (x rows contiguous), and each particle's
+// eight corners read from there.  A box of more than kWinRecs records (the
+// particles far apart: not in cell order) takes the gather from global
+// memory.  Both give the same value (interp8).  All lanes of the warp call
+// it together (valid: the lane holds a particle).
+constexpr int kWinRecs = 64;
+__device__ __forceinline__ void st_win(V4<float>* q, const V4<float>& v) {
+    *reinterpret_cast<float4*>(q) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ void st_win(V4<double>* q, const V4<double>& v) {
+    reinterpret_cast<double2*>(q)[0] = make_double2(v.x, v.y);
+    reinterpret_cast<double2*>(q)[1] = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ V4<float> ld_win(const V4<float>* q) {
+    const float4 v = *reinterpret_cast<const float4*>(q);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld_win(const V4<double>* q) {
+    const double2 a = reinterpret_cast<const double2*>(q)[0], b = reinterpret_cast<const double2*>(q)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+template <typename T>
+__device__ __forceinline__ V4<T> window_gather(const T* __restrict__ bulk4, const V4<T>& x, bool valid,
+                                               const GridDev& g, V4<T>* __restrict__ win) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int i0 = 0, j0 = 0, k0 = 0;
+    T tx = T(0), ty = T(0), tz = T(0);
+    if (valid) {
+        axis_weight(x.x, g, 0, i0, tx);
+        axis_weight(x.y, g, 1, j0, ty);
+        axis_weight(x.z, g, 2, k0, tz);
+    }
+    const int big = 0x7fffffff;
+    const int imin = __reduce_min_sync(full, valid ? i0 : big), imax = __reduce_max_sync(full, valid ? i0 : -1);
+    const int jmin = __reduce_min_sync(full, valid ? j0 : big), jmax = __reduce_max_sync(full, valid ? j0 : -1);
+    const int kmin = __reduce_min_sync(full, valid ? k0 : big), kmax = __reduce_max_sync(full, valid ? k0 : -1);
+    const int nx = imax - imin + 2, ny = jmax - jmin + 2, nz = kmax - kmin + 2;
+    const int sy = g.nb[0], sz = g.nb[0] * g.nb[1];
+    const V4<T>* rec = reinterpret_cast<const V4<T>*>(bulk4);
+    V4<T> out = {T(0), T(0), T(0), T(0)};
+    // the box is small only if every extent is (no product of large extents)
+    if (nx <= kWinRecs && ny <= kWinRecs && nz <= kWinRecs && nx * ny * nz <= kWinRecs) {
+        const int W = nx * ny * nz;
+        // record r = wx + nx (wy + ny wz); (r + 1/2) / n never rounds across an integer for r < 2^11
+        const float inx = 1.0f / (float)nx, iny = 1.0f / (float)ny;
+        for (int r = lane; r < W; r += 32) {
+            const int q = (int)(((float)r + 0.5f) * inx);
+            const int wx = r - q * nx;
+            const int wz = (int)(((float)q + 0.5f) * iny);
+            const int wy = q - wz * ny;
+            st_win(win + r, ldv4(rec + (imin + wx) + sy * (jmin + wy) + sz * (kmin + wz)));
+        }
+        __syncwarp();
+        if (valid)
+            out = interp8<T>(win + (i0 - imin) + nx * ((j0 - jmin) + ny * (k0 - kmin)), nx, nx * ny, tx, ty, tz,
+                             [](const V4<T>* q) { return ld_win(q); });
+        __syncwarp();   // the next call restages the slice
+    } else if (valid) {
+        out = interp8<T>(rec + (i0 + sy * j0 + sz * k0), sy, sz, tx, ty, tz, [](const V4<T>* q) { return ldv4(q); });
+    }
+    return out;
+}
+
 // Per-lane diagnostics: V_p, F (3), |F|, m u (3) after the advance, clamped.
 template <typename T>
 __device__ __forceinline__ void drag_lane_sums(T (&ls)[kDragSums], const DragOne<T>& r) {
-    ls[0] += r.vp;
-    ls[1] += r.f[0];
-    ls[2] += r.f[1];
-    ls[3] += r.f[2];
-    ls[4] += r.beta * r.smag;
-    ls[5] += r.m * r.u[0];
-    ls[6] += r.m * r.u[1];
-    ls[7] += r.m * r.u[2];
-    ls[8] += (T)r.cl;
+    using X = M<T>;
+    ls[0] = X::add(ls[0], r.vp);
+    ls[1] = X::add(ls[1], r.f[0]);
+    ls[2] = X::add(ls[2], r.f[1]);
+    ls[3] = X::add(ls[3], r.f[2]);
+    ls[4] = X::fma_(r.beta, r.smag, ls[4]);
+    ls[5] = X::fma_(r.m, r.u[0], ls[5]);
+    ls[6] = X::fma_(r.m, r.u[1], ls[6]);
+    ls[7] = X::fma_(r.m, r.u[2], ls[7]);
+    ls[8] = X::add(ls[8], (T)r.cl);
 }
 
 // ----------------------------------------------------------------------
@@ -184,6 +258,79 @@ __device__ __forceinline__ void drag_body(T* pos, T* vel, long long n, const Gri
     }
 }
 
+// The drag of particles in cell order (the sorted step) with the stencil
+// window of each warp (window_gather); otherwise as drag_body, whose
+// results it reproduces bit for bit.  The loop runs warp by warp (every
+// lane of a warp takes the same number of turns).
+template <typename T, bool EULER>
+__device__ __forceinline__ void drag_body_win(T* pos, T* vel, long long n, const GridDev& g, const Phys<T>& P,
+                                              const T* __restrict__ bulk4, T* __restrict__ F, T* __restrict__ Fs,
+                                              const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part,
+                                              long long pstride, int do_sums, unsigned long long* __restrict__ status,
+                                              Blk b, T* __restrict__ pos_out, T* __restrict__ vel_out,
+                                              V4<T>* __restrict__ win) {
+    T lane_sums[kDragSums];
+#pragma unroll
+    for (int k = 0; k < kDragSums; ++k) lane_sums[k] = T(0);
+    int clamped_total = 0;
+    const long long stride = b.n * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    V4<T> xn = {T(0), T(0), T(0), T(0)}, vn = xn;
+    int slot_n = 0;
+    long long p = b.id * blockDim.x + threadIdx.x;
+    if (p < n) {
+        xn = EULER ? ld4_plain(pos, p) : ld4((const T*)pos, p);
+        vn = EULER ? ld4_plain(vel, p) : ld4((const T*)vel, p);
+        slot_n = __ldg(inv_perm + p);
+    }
+    for (; p - lane < n; p += stride) {
+        const bool valid = p < n;
+        const V4<T> x = xn, v = vn;
+        const int slot = slot_n;
+        if (p + stride < n) {
+            xn = EULER ? ld4_plain(pos, p + stride) : ld4((const T*)pos, p + stride);
+            vn = EULER ? ld4_plain(vel, p + stride) : ld4((const T*)vel, p + stride);
+            slot_n = __ldg(inv_perm + p + stride);
+        }
+        const V4<T> bv = window_gather(bulk4, x, valid, g, win);
+        if (valid) {
+            const DragOne<T> r = drag_from<T, EULER>(x, v, bv, g, P, dt);
+            clamped_total += r.cl;
+            F[p] = r.f[0];
+            F[n + p] = r.f[1];
+            F[2 * n + p] = r.f[2];
+            st4(Fs, slot, r.f[0], r.f[1], r.f[2], T(0));
+            st4(pos_out, slot, r.x[0], r.x[1], r.x[2], x.w);
+            st4(vel_out, slot, r.u[0], r.u[1], r.u[2], v.w);
+            drag_lane_sums(lane_sums, r);
+        }
+    }
+    int wsum = clamped_total;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+    if ((threadIdx.x & 31) == 0 && wsum) {
+        atomicAdd(&status[ST_CLAMPED], (unsigned long long)wsum);
+        atomicOr(&status[ST_FLAGS], (unsigned long long)CG_FLAG_EPS_CLAMPED);
+    }
+    if (do_sums) {
+        CSum<T> acc[kDragSums];
+#pragma unroll
+        for (int k = 0; k < kDragSums; ++k) acc[k].add(lane_sums[k]);
+        block_sums<T, kDragSums>(acc, part, pstride, b.id);
+    }
+}
+
+template <typename T, bool EULER>
+__global__ void __launch_bounds__(256, 4)
+k_drag_win(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4, T* __restrict__ F,
+           T* __restrict__ Fs, const int32_t* __restrict__ inv_perm, T dt, T* __restrict__ part, long long pstride,
+           int do_sums, unsigned long long* __restrict__ status, T* __restrict__ pos_out, T* __restrict__ vel_out) {
+    __shared__ __align__(16) V4<T> win[256 / 32][kWinRecs];
+    pdl_wait();
+    drag_body_win<T, EULER>(pos, vel, n, g, P, bulk4, F, Fs, inv_perm, dt, part, pstride, do_sums, status,
+                            launch_blk(), pos_out, vel_out, win[threadIdx.x >> 5]);
+}
+
 template <typename T, bool EULER>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_drag(T* pos, T* vel, long long n, GridDev g, Phys<T> P, const T* __restrict__ bulk4,
@@ -243,7 +390,22 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
     CG_LAUNCH(g, "drag", (k_drag<T, E>), nblk, 256, 0, (T*)pos_d, (T*)vel, n, g->gd, phys_of<T>(g->gd),          \
               (const T*)g->bulk4, (T*)force, (T*)Fs, g->inv_perm, (T)dt, (T*)part, (long long)nblk, (int)sums,   \
               g->status, (T*)Bs, (T*)pos_out, (T*)vel_out)
-        if (g->fp64) {
+        // on request, the sorted step (its particles come in nearly in cell
+        // order) stages each warp's stencil window on the FP32 trilinear path
+        const bool win = g->desc.stencil == CG_STENCIL_WINDOW && pos_out && !g->fp64 && !Bs &&
+                         g->gd.interp != CG_INTERP_CELL;
+        if (win) {
+            if (euler)
+                CG_LAUNCH(g, "drag", (k_drag_win<float, true>), nblk, 256, 0, (float*)pos_d, (float*)vel, n, g->gd,
+                          phys_of<float>(g->gd), (const float*)g->bulk4, (float*)force, (float*)Fs, g->inv_perm,
+                          (float)dt, (float*)part, (long long)nblk, (int)sums, g->status, (float*)pos_out,
+                          (float*)vel_out);
+            else
+                CG_LAUNCH(g, "drag", (k_drag_win<float, false>), nblk, 256, 0, (float*)pos_d, (float*)vel, n, g->gd,
+                          phys_of<float>(g->gd), (const float*)g->bulk4, (float*)force, (float*)Fs, g->inv_perm,
+                          (float)dt, (float*)part, (long long)nblk, (int)sums, g->status, (float*)pos_out,
+                          (float*)vel_out);
+        } else if (g->fp64) {
             if (euler) CG_DRAGP(double, true);
             else CG_DRAGP(double, false);
         } else {

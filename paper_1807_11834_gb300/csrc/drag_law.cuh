@@ -8,8 +8,19 @@
 
 namespace cg {
 
+// Math of the drag step.  The arithmetic of the correlations and of the
+// Euler advance is written with explicitly rounded operations (mul, add,
+// sub, div, and fma where a fused product is meant), so the compiler cannot
+// fuse a product into an addition in one kernel and not in another: every
+// kernel built from this code (plain, windowed, batched, learned) gives the
+// same bits for the same particle.
 template <typename T> struct M;
 template <> struct M<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
@@ -18,6 +29,11 @@ template <> struct M<float> {
     static __device__ __forceinline__ float pi8() { return 0.39269908169872415f; }
 };
 template <> struct M<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
@@ -87,6 +103,19 @@ __device__ __forceinline__ V4<T> lerp4(const V4<T>& a, const V4<T>& b, T t) {
     return {lerp_(a.x, b.x, t), lerp_(a.y, b.y, t), lerp_(a.z, b.z, t), lerp_(a.w, b.w, t)};
 }
 
+// Trilinear value from the 8 records of a stencil: c the base corner,
+// oy / oz the record steps along y / z (x is 1), read by ld; x, then y,
+// then z, in this order wherever the records come from (global memory or a
+// staged window), so every path gives the same value bit for bit.
+template <typename T, typename Ld>
+__device__ __forceinline__ V4<T> interp8(const V4<T>* c, int oy, int oz, T tx, T ty, T tz, Ld ld) {
+    V4<T> a00 = lerp4(ld(c), ld(c + 1), tx);
+    V4<T> a10 = lerp4(ld(c + oy), ld(c + oy + 1), tx);
+    V4<T> a01 = lerp4(ld(c + oz), ld(c + oz + 1), tx);
+    V4<T> a11 = lerp4(ld(c + oz + oy), ld(c + oz + oy + 1), tx);
+    return lerp4(lerp4(a00, a10, ty), lerp4(a01, a11, ty), tz);
+}
+
 // Gather (eps, u) at a point.
 template <typename T>
 __device__ __forceinline__ V4<T> gather(const T* __restrict__ bulk4, T x, T y, T z, const GridDev& g) {
@@ -102,12 +131,8 @@ __device__ __forceinline__ V4<T> gather(const T* __restrict__ bulk4, T x, T y, T
     axis_weight(z, g, 2, k0, tz);
     // cell indices fit in int (fewer than 2^31 bulk cells)
     const int sy = g.nb[0], sz = g.nb[0] * g.nb[1];
-    const V4<T>* b = reinterpret_cast<const V4<T>*>(bulk4) + (i0 + sy * j0 + sz * k0);
-    V4<T> a00 = lerp4(ldv4(b), ldv4(b + 1), tx);
-    V4<T> a10 = lerp4(ldv4(b + sy), ldv4(b + sy + 1), tx);
-    V4<T> a01 = lerp4(ldv4(b + sz), ldv4(b + sz + 1), tx);
-    V4<T> a11 = lerp4(ldv4(b + sz + sy), ldv4(b + sz + sy + 1), tx);
-    return lerp4(lerp4(a00, a10, ty), lerp4(a01, a11, ty), tz);
+    return interp8<T>(reinterpret_cast<const V4<T>*>(bulk4) + (i0 + sy * j0 + sz * k0), sy, sz, tx, ty, tz,
+                      [](const V4<T>* q) { return ldv4(q); });
 }
 
 // ----------------------------------------------------------------------
@@ -122,27 +147,35 @@ __device__ __forceinline__ V4<T> gather(const T* __restrict__ bulk4, T x, T y, T
 // ----------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T drag_beta(int law, T eps, T phi, T d, T smag, const Phys<T>& P) {
+    using X = M<T>;
     if (law == CG_DRAG_DI_FELICE) {
-        const T red = P.rho_mu * eps * d;
-        const T Re = red * smag;
-        const T a = T(0.63) * M<T>::sqrt_(smag) + T(4.8) / M<T>::sqrt_(red);
-        const T cds = a * a;
+        const T red = X::mul(X::mul(P.rho_mu, eps), d);
+        const T Re = X::mul(red, smag);
+        const T a = X::fma_(T(0.63), X::sqrt_(smag), X::div(T(4.8), X::sqrt_(red)));
+        const T cds = X::mul(a, a);
         T chi = T(3.7);
         if (Re > T(0)) {
-            const T l = T(1.5) - M<T>::log10_(Re);
-            chi = T(3.7) - T(0.65) * M<T>::exp_(T(-0.5) * l * l);
+            const T l = X::sub(T(1.5), X::log10_(Re));
+            chi = X::fma_(T(-0.65), X::exp_(X::mul(X::mul(T(-0.5), l), l)), T(3.7));
         }
-        return M<T>::pi8() * P.rho * d * d * cds * M<T>::pow_(eps, T(2) - chi);
+        return X::mul(X::mul(X::mul(X::mul(X::mul(X::pi8(), P.rho), d), d), cds), X::pow_(eps, X::sub(T(2), chi)));
     }
-    const T vp = M<T>::pi6() * d * d * d;
+    const T vp = X::mul(X::mul(X::mul(X::pi6(), d), d), d);
     // Ergun (150 phi mu / (eps d^2) + 1.75 rho |s| / d) V_p with V_p = pi d^3 / 6,
     // rearranged to one division: pi/6 d (150 phi mu / eps + 1.75 rho |s| d)
-    if (eps < P.eps_switch) return M<T>::pi6() * d * (T(150) * phi * P.mu / eps + T(1.75) * P.rho * smag * d);
-    const T eRe = eps * P.rho_mu * d * smag;
+    if (eps < P.eps_switch) {
+        const T visc = X::div(X::mul(X::mul(T(150), phi), P.mu), eps);
+        const T inert = X::mul(X::mul(X::mul(T(1.75), P.rho), smag), d);
+        return X::mul(X::mul(X::pi6(), d), X::add(visc, inert));
+    }
+    const T eRe = X::mul(X::mul(X::mul(eps, P.rho_mu), d), smag);
     T cds;
-    if (eRe < T(1000)) cds = T(24) * P.mu / (eps * P.rho * d) * (T(1) + T(0.15) * M<T>::pow_(eRe, T(0.687)));
-    else cds = T(0.44) * smag;
-    return T(0.75) * cds * eps * P.rho * M<T>::pow_(eps, T(-2.65)) / d * vp;
+    if (eRe < T(1000))
+        cds = X::mul(X::div(X::mul(T(24), P.mu), X::mul(X::mul(eps, P.rho), d)),
+                     X::fma_(T(0.15), X::pow_(eRe, T(0.687)), T(1)));
+    else
+        cds = X::mul(T(0.44), smag);
+    return X::mul(X::div(X::mul(X::mul(X::mul(X::mul(T(0.75), cds), eps), P.rho), X::pow_(eps, T(-2.65))), d), vp);
 }
 
 // Bulk record and its trilinear gradient at a point: eps, u (value) and

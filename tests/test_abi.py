@@ -49,7 +49,7 @@ def test_status_strings_without_gpu(libcg):
 def test_struct_layout_matches_header():
     import paper_1807_11834_gb300 as cg
     # cg_grid_desc: 6 doubles, 3+1+4 int32 + reserved, 5 doubles, 3 doubles
-    assert ctypes.sizeof(cg.GridDesc) == 6 * 8 + 8 * 4 + 5 * 8 + 3 * 8
+    assert ctypes.sizeof(cg.GridDesc) == 6 * 8 + 10 * 4 + 5 * 8 + 3 * 8   # 9 int32 and 4 bytes of padding
     assert ctypes.sizeof(cg.StepOut) == 13 * 8
     assert ctypes.sizeof(cg.Particles) == 24
     # cg_batch_item: desc, particles, u_fine pointer, step outputs; cg_batch_config: 5 int32
@@ -101,13 +101,14 @@ def test_invalid_arguments_rejected_before_any_gpu_work(libcg):
 def test_argument_checks_answer_before_any_device_work():
     """Descriptors and grids the ABI rejects come back CG_ERR_INVALID_ARG
     (1) synchronously, before the library touches a device, so these run
-    without a GPU: unknown sort choices, non-nested ratios, a bulk axis of
+    without a GPU: unknown sort and stencil choices, non-nested ratios, a bulk axis of
     one cell, and degenerate or mixed-precision map grids."""
     import paper_1807_11834_gb300 as cg
     import synth
     L = cg.lib()
     base = synth.tiny(seed=0, n=1).desc
-    for bad in (dict(sort_digits=2), dict(sort_digits=12), dict(sort_digits=-1), dict(ratio=3),
+    for bad in (dict(sort_digits=2), dict(sort_digits=12), dict(sort_digits=-1), dict(stencil=2), dict(stencil=-1),
+                dict(ratio=3),
                 dict(fine_n=(8, 8, 4), ratio=4), dict(extent=(1.0, 0.0, 1.0))):
         d = dict(base)
         d.update(bad)

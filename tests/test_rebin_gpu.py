@@ -131,6 +131,38 @@ def test_sorted_steps_keep_cell_order_and_match_cg_step(cuda_lib):
     f.close()
 
 
+def test_stencil_window_gives_the_gather_bits(cuda_lib):
+    """Six sorted steps of the small clustered bed with the drag's stencil
+    windows staged in shared memory (CG_STENCIL_WINDOW) against the global
+    gather: the same bins, fields, forces and advanced particles, bit for
+    bit.  The first step's input is in generation order, so most warps'
+    boxes are too large and take the gather path inside the windowed
+    kernel; the later inputs are in cell order and use the windows."""
+    import torch
+    cg = cuda_lib
+    w = synth.small_clustered_bed(seed=13)
+    runs = []
+    for stencil in (cg.CG_STENCIL_GATHER, cg.CG_STENCIL_WINDOW):
+        d = dict(w.desc)
+        d["stencil"] = stencil
+        g = cg.Grids(d)
+        pos, vel, uf = inputs(w)
+        bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
+        out = g.alloc_outputs(w.n, eps_fine=True, bins=True)
+        steps = []
+        for step in range(6):
+            (pi, vi), (po, vo) = bufs[step % 2], bufs[(step + 1) % 2]
+            g.cg_step_sorted(pi, vi, po, vo, uf, out, dt=w.dt)
+            torch.cuda.synchronize()
+            steps.append({k: v.clone() for k, v in out.items() if v is not None} | {"pos": po.clone(), "vel": vo.clone()})
+        assert g.cg_sync_status()[0] == 0
+        g.close()
+        runs.append(steps)
+    for step, (a, b) in enumerate(zip(*runs)):
+        for k in a:
+            assert torch.equal(a[k], b[k]), (step, k)
+
+
 def test_fallback_when_most_particles_changed(cuda_lib):
     """The same handle bins three unrelated particle sets of one count (every
     particle a mover: the device falls back to the per-cell sort) and then
