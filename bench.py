@@ -41,13 +41,14 @@ UNIT = "particle-steps/s"
 
 # DRAM traffic per launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel, valid only while the kernel's
-# source file is byte-identical to the one profiled (sha256 prefix).
+# source files are byte-identical to the ones profiled (sha256 prefixes).
 NCU_TRAFFIC = {
     # packed bed, one warm launch of k_average<float,4>: 405.5 MB read + 8.1 MB written
-    ("packed_bed", "average"): {"file": "fine.cu", "sha": "a4d41dcdd302d93f", "bytes": 413.6e6},
+    ("packed_bed", "average"): {"files": {"fine.cu": "a4d41dcdd302d93f"}, "bytes": 413.6e6},
     # clustered-bed recipe at 16M particles, a warm sorted step of k_drag<float,1>:
     # 579.5 MB read + 904.2 MB written, times 2 for the 32M bed (traffic per particle)
-    ("clustered_bed", "drag"): {"file": "drag.cu", "sha": "c8c088e2117d96a8", "bytes": 2.967e9},
+    ("clustered_bed", "drag"): {"files": {"drag.cu": "c8c088e2117d96a8", "drag_law.cuh": "pending"},
+                                "bytes": 2.967e9},
 }
 
 
@@ -468,7 +469,9 @@ def run_gb300(args):
         ach = dom_bytes / (kern_ms[dominant] * 1e-3) / 1e9
         tr = NCU_TRAFFIC.get((args.workload, dominant))
         traffic = None
-        if tr and tr["sha"] == file_sha(os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", tr["file"])):
+        # the counters hold only while every source of the kernel is the one they were taken from
+        if tr and all(sha == file_sha(os.path.join(ROOT, "paper_1807_11834_gb300", "csrc", f))
+                      for f, sha in tr["files"].items()):
             traffic = tr["bytes"]
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(ach, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,

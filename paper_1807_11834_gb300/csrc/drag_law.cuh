@@ -21,10 +21,28 @@ template <> struct M<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+    // square root and reciprocal square root on the special-function unit
+    // (sqrt.approx / rsqrt.approx: relative error about 2^-23, a rounding
+    // or two, for normal inputs; 0 gives 0 and +inf)
+    static __device__ __forceinline__ float sqrt_(float x) {
+        float y;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float rsqrt_(float x) {
+        float y;
+        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    // x^y for the correlations' bases, which are never negative (a porosity of
+    // at least eps_min >= 0, or eps Re >= 0): 2^(y log2 x), without powf's
+    // handling of negative bases and integer exponents; log2f (1 ulp) and
+    // exp2f (2 ulp) keep the result within about 5e-7 relative for |y| < 3
+    // and x in (0, 1000]; x = 0 gives 2^(-inf y), the same 0 or inf as powf
+    static __device__ __forceinline__ float pow_(float x, float y) { return exp2f(__fmul_rn(y, log2f(x))); }
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
-    static __device__ __forceinline__ float log10_(float x) { return log10f(x); }
+    // log10 x = log2 x * log10 2 (log2f: 1 ulp)
+    static __device__ __forceinline__ float log10_(float x) { return __fmul_rn(log2f(x), 0.30102999566398120f); }
     static __device__ __forceinline__ float pi6() { return 0.52359877559829887f; }
     static __device__ __forceinline__ float pi8() { return 0.39269908169872415f; }
 };
@@ -35,6 +53,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return __ddiv_rn(1.0, sqrt(x)); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log10_(double x) { return log10(x); }
@@ -151,7 +170,7 @@ __device__ __forceinline__ T drag_beta(int law, T eps, T phi, T d, T smag, const
     if (law == CG_DRAG_DI_FELICE) {
         const T red = X::mul(X::mul(P.rho_mu, eps), d);
         const T Re = X::mul(red, smag);
-        const T a = X::fma_(T(0.63), X::sqrt_(smag), X::div(T(4.8), X::sqrt_(red)));
+        const T a = X::fma_(T(0.63), X::sqrt_(smag), X::mul(T(4.8), X::rsqrt_(red)));
         const T cds = X::mul(a, a);
         T chi = T(3.7);
         if (Re > T(0)) {
