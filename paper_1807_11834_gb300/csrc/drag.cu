@@ -76,7 +76,7 @@ __device__ __forceinline__ DragOne<T> drag_from(const V4<T>& x, const V4<T>& v, 
     r.u[1] = v.y;
     r.u[2] = v.z;
     if (EULER) {
-        const T inv_m = X::div(T(1), r.m);   // one division for the three components
+        const T inv_m = X::rcp_(r.m);   // one reciprocal for the three components
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             T ua = X::fma_(dt, X::fma_(r.f[a], inv_m, P.g[a]), r.u[a]);

@@ -23,15 +23,23 @@ template <> struct M<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     // square root and reciprocal square root on the special-function unit
     // (sqrt.approx / rsqrt.approx: relative error about 2^-23, a rounding
-    // or two, for normal inputs; 0 gives 0 and +inf)
+    // or two; subnormal inputs count as 0, which turns a slip below 1e-19
+    // into none, a drag that is zero to within 1e-19 of its scale anyway)
     static __device__ __forceinline__ float sqrt_(float x) {
         float y;
-        asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
     static __device__ __forceinline__ float rsqrt_(float x) {
         float y;
-        asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    // 1 / x on the special-function unit (rcp.approx: about one rounding; the
+    // masses, porosities and diameters it divides by are normal numbers)
+    static __device__ __forceinline__ float rcp_(float x) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
     // x^y for the correlations' bases, which are never negative (a porosity of
@@ -54,6 +62,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double rsqrt_(double x) { return __ddiv_rn(1.0, sqrt(x)); }
+    static __device__ __forceinline__ double rcp_(double x) { return __ddiv_rn(1.0, x); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log10_(double x) { return log10(x); }
@@ -183,18 +192,20 @@ __device__ __forceinline__ T drag_beta(int law, T eps, T phi, T d, T smag, const
     // Ergun (150 phi mu / (eps d^2) + 1.75 rho |s| / d) V_p with V_p = pi d^3 / 6,
     // rearranged to one division: pi/6 d (150 phi mu / eps + 1.75 rho |s| d)
     if (eps < P.eps_switch) {
-        const T visc = X::div(X::mul(X::mul(T(150), phi), P.mu), eps);
+        const T visc = X::mul(X::mul(X::mul(T(150), phi), P.mu), X::rcp_(eps));
         const T inert = X::mul(X::mul(X::mul(T(1.75), P.rho), smag), d);
         return X::mul(X::mul(X::pi6(), d), X::add(visc, inert));
     }
     const T eRe = X::mul(X::mul(X::mul(eps, P.rho_mu), d), smag);
     T cds;
     if (eRe < T(1000))
-        cds = X::mul(X::div(X::mul(T(24), P.mu), X::mul(X::mul(eps, P.rho), d)),
+        cds = X::mul(X::mul(X::mul(T(24), P.mu), X::rcp_(X::mul(X::mul(eps, P.rho), d))),
                      X::fma_(T(0.15), X::pow_(eRe, T(0.687)), T(1)));
     else
         cds = X::mul(T(0.44), smag);
-    return X::mul(X::div(X::mul(X::mul(X::mul(X::mul(T(0.75), cds), eps), P.rho), X::pow_(eps, T(-2.65))), d), vp);
+    return X::mul(X::mul(X::mul(X::mul(X::mul(X::mul(T(0.75), cds), eps), P.rho), X::pow_(eps, T(-2.65))),
+                          X::rcp_(d)),
+                  vp);
 }
 
 // Bulk record and its trilinear gradient at a point: eps, u (value) and
