@@ -347,6 +347,7 @@ cg_status cg_create_grids(const cg_grid_desc* desc, void* cuda_stream, cg_grids*
         gd.ax0f[a] = (float)fabs(d.origin[a] * gd.invH[a]);
         split_ff(d.origin[a], gd.x0h[a], gd.x0l[a]);
         split_ff(gd.invH[a], gd.ihh[a], gd.ihl[a]);
+        split_ff(-(d.origin[a] / gd.H[a] + 0.5), gd.xbh[a], gd.xbl[a]);
     }
     gd.VB = gd.H[0] * gd.H[1] * gd.H[2];
     gd.invVB = 1.0 / gd.VB;

@@ -117,6 +117,7 @@ struct GridDev {
     float ax0f[3];      // |x0 / H| (filter margin term)
     float x0h[3], x0l[3];   // x0 as float-float
     float ihh[3], ihl[3];   // 1/H as float-float
+    float xbh[3], xbl[3];   // -(x0 / H + 1/2) as float-float: the lattice coordinate is x / H + xb
     float invVBf, VBf, Vff;
     float VBh, VBl, Vfh, Vfl;   // V_B, V_f as float-float
     float ivBh, ivBl;           // 1 / V_B as float-float

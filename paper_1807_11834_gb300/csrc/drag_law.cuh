@@ -80,18 +80,14 @@ struct Phys {
 // xi = (x - x0)/H - 1/2, i0 = clamp(floor xi, 0, nb - 2), t = clamp(xi - i0, 0, 1).
 // ----------------------------------------------------------------------
 __device__ __forceinline__ void axis_weight(float x, const GridDev& g, int a, int& i0, float& t) {
-    float s, e;
-    two_sum(x, -g.x0h[a], s, e);
-    e -= g.x0l[a];
-    const float dh = s + e;
-    const float dl = e - (dh - s);
-    const float qh = dh * g.ihh[a];
-    float ql = fmaf(dh, g.ihh[a], -qh);
-    ql = fmaf(dh, g.ihl[a], ql);
-    ql = fmaf(dl, g.ihh[a], ql);
+    // xi = x / H + xb as float-float: x * (1/H)_hi is exact as p + pe (FMA),
+    // one TwoSum with xb_hi, the small terms added plainly (about 2^-44
+    // relative to xi, as the float-float difference and product it replaces)
+    const float p = __fmul_rn(x, g.ihh[a]);   // never fused into the TwoSum below
+    const float pe = fmaf(x, g.ihh[a], -p);
     float xh, xl;
-    two_sum(qh, -0.5f, xh, xl);
-    xl += ql;
+    two_sum(p, g.xbh[a], xh, xl);
+    xl += pe + fmaf(x, g.ihl[a], g.xbl[a]);
     float fi = floorf(xh);
     if (xh == fi && xl < 0.f) fi -= 1.f;
     const float top = (float)(g.nb[a] - 2);
