@@ -364,14 +364,16 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
         if (lane == 0) s_tab[k * W + warp] = __popc(db[k]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {   // exclusive prefix over (row, warp) in slot order
-        int t = __ldg(blk_start + blockIdx.x);
+    static_assert(kRebinItems * W == 32, "one lane per (row, warp) entry");
+    if (warp == 0) {   // exclusive prefix over (row, warp) in slot order: one shuffle scan
+        const int c = s_tab[lane];
+        int incl = c;
 #pragma unroll
-        for (int j = 0; j < kRebinItems * W; ++j) {
-            const int c = s_tab[j];
-            s_tab[j] = t;
-            t += c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(full, incl, off);
+            if (lane >= off) incl += o;
         }
+        s_tab[lane] = __ldg(blk_start + blockIdx.x) + incl - c;
     }
     __syncthreads();
 #pragma unroll
