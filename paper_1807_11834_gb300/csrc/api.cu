@@ -136,7 +136,7 @@ cg_status ensure_partials(cg_grids* g, long long n) {
     (void)n;
     const long long proj_blk = (g->gd.r == 2 || g->gd.r == 4 || g->gd.r == 8) ? bulk_blk : fine_blk;
     const long long part_blk = std::max(bulk_blk, (long long)g->num_sms * 8);
-    const long long need = part_blk * (1 + kDragCellSums + 3) + proj_blk * 3;
+    const long long need = part_blk * (1 + kDragCellSums) + proj_blk * 6;
     if (need > g->part_cap) {
         dfree(g->partials);
         g->part_cap = 0;
@@ -144,9 +144,8 @@ cg_status ensure_partials(cg_grids* g, long long n) {
         g->part_cap = need;
     }
     g->part_off[PS_VOL] = 0;
-    g->part_off[PS_MOM] = part_blk;
-    g->part_off[PS_PROJ] = part_blk * 4;
-    g->part_off[PS_DRAG] = part_blk * 4 + proj_blk * 3;
+    g->part_off[PS_PROJ] = part_blk;
+    g->part_off[PS_DRAG] = part_blk + proj_blk * 6;
     return CG_OK;
 }
 

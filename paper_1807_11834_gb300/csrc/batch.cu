@@ -195,15 +195,13 @@ cg_status plan(cg_batch* b) {
         set(BP_PROJ, cellb);
         set(BP_PROJE, I.eps_fine ? cellb : 0);
         set(BP_SUMS, CG_NSUMS);
-        // partial regions (pairs): volume 1 column, reaction 3, projection 3, drag 9
+        // partial regions (pairs): volume 1 column, projection 6 (S_f V_f, S_B V_B), drag 9
         I.part_blocks[PS_VOL] = seg;
-        I.part_blocks[PS_MOM] = seg;
         I.part_blocks[PS_PROJ] = cellb;
         I.part_blocks[PS_DRAG] = B[(size_t)BP_DRAG * ni];
         I.part_off[PS_VOL] = 0;
-        I.part_off[PS_MOM] = seg;
-        I.part_off[PS_PROJ] = seg + 3 * seg;
-        I.part_off[PS_DRAG] = seg + 3 * seg + 3 * cellb;
+        I.part_off[PS_PROJ] = seg;
+        I.part_off[PS_DRAG] = seg + 6 * cellb;
         const long long pairs = I.part_off[PS_DRAG] + (long long)kDragSums * I.part_blocks[PS_DRAG];
         CG_TRY(dev_alloc(b, (void**)&I.part, sizeof(float) * 2 * pairs));
         I.smap = sums_map(I.part_off, I.part_blocks);

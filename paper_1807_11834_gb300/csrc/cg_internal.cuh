@@ -93,7 +93,9 @@ constexpr int kNumSlots = 16;                       // status counters
 enum { ST_FLAGS = 0, ST_OUTSIDE = 1, ST_NONFINITE = 2, ST_CLAMPED = 3, ST_TIMEOUT = 4, ST_FALLBACK = 5 };
 
 // Partial-sum regions of the conservation sums.
-enum { PS_VOL = 0, PS_DRAG = 1, PS_MOM = 2, PS_PROJ = 3, PS_NREG = 4 };
+// The projection's region holds six columns: sum S_f V_f (3), then sum S_B
+// V_B (3) of the source it reads.
+enum { PS_VOL = 0, PS_DRAG = 1, PS_PROJ = 2, PS_NREG = 3 };
 constexpr int kDragSums = 9;   // V_p, F(3), |F|, m u (3), clamped count
 constexpr int kDragCellSums = kDragSums + 3;   // + S_B V_B (3) in the cell-order drag
 
@@ -204,8 +206,8 @@ struct cg_grids {
     void* bulk4 = nullptr;         // [nbulk] T4: eps, u_x, u_y, u_z
     void* eps_t = nullptr;         // [nbulk] T: porosity in the path precision
     void* partials = nullptr;      // conservation-sum block partials: (s, c) pairs of T
-    long long part_off[cg::PS_NREG] = {0, 0, 0, 0};
-    long long part_blocks[cg::PS_NREG] = {0, 0, 0, 0};
+    long long part_off[cg::PS_NREG] = {0, 0, 0};
+    long long part_blocks[cg::PS_NREG] = {0, 0, 0};
     long long part_cap = 0;
     double* sums_scratch = nullptr;   // [CG_NSUMS] when the caller gives none
     unsigned long long* status = nullptr;   // [kNumSlots]
@@ -340,7 +342,7 @@ cg_status launch_bin(cg_grids* g, long long n, const void* pos_d, double* eps_fi
 // of occupied cells into the drag record and its T copy.
 cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, double* eps, bool sums,
                                 bool prefilled = false, void* rec = nullptr, void* eps_t = nullptr);
-cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums);
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk);
 // Gather the particle records into the binned order (cg_reorder_particles).
 cg_status launch_reorder(cg_grids* g, long long n, const void* pos_d, const void* vel, void* pos_out, void* vel_out);
 // Semi-implicit coefficients [4][n_b] (A, b) from the drag's sorted (beta, beta u) records.
@@ -860,26 +862,16 @@ __device__ __forceinline__ void seg_seq(long long s, long long t, const int32_t*
 
 // Reaction of one cell from its compensated force sum a: S_B = -(1/V_B) sum F
 // (Eq. UFP: F_fpi is the fluid-side reaction to F_drag), written to S
-// ([3][n_b]), and S_B V_B added to the diagnostics sv (an exact
-// float-float product on the FP32 path).
+// ([3][n_b]).  The conservation sum of S_B V_B is formed by the projection,
+// which reads every S_B.
 template <typename T>
-__device__ __forceinline__ void reaction_emit(const GridDev& g, T* __restrict__ S, int key, CSum<T> (&a)[3],
-                                              CSum<T> (&sv)[3]) {
+__device__ __forceinline__ void reaction_emit(const GridDev& g, T* __restrict__ S, int key, const CSum<T> (&a)[3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         T s_;
         if (sizeof(T) == 4) s_ = -(a[k].get()) * (T)g.invVBf;
         else s_ = -(a[k].get()) * (T)g.invVB;
         S[k * g.nbulk + key] = s_;
-        if (sizeof(T) == 4) {
-            T hi = s_ * (T)g.VBh;
-            T lo = fma(s_, (T)g.VBh, -hi);
-            lo = fma(s_, (T)g.VBl, lo);
-            sv[k].add(hi);
-            sv[k].c += lo;
-        } else {
-            sv[k].add(s_ * (T)g.VB);
-        }
     }
 }
 

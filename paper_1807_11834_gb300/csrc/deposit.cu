@@ -128,17 +128,14 @@ k_deposit_volume_sorted(const T* __restrict__ dsorted, long long n, const int32_
     deposit_volume_sorted_body(dsorted, n, key_sorted, cs, g, eps, part, pstride, do_sums, launch_blk(), rec, eps_t);
 }
 
-// Reaction from the forces the drag wrote in sorted order (T4 per slot);
-// S_B V_B accumulated as an exact float-float product for the diagnostics.
+// Reaction from the forces the drag wrote in sorted order (T4 per slot).
 template <typename T>
 __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ Fs, long long n,
                                                           const int32_t* __restrict__ key_sorted,
                                                           const int32_t* __restrict__ cs, const GridDev& g,
-                                                          T* __restrict__ S, T* __restrict__ part, long long pstride,
-                                                          int do_sums, Blk b) {
+                                                          T* __restrict__ S, Blk b) {
     const long long wg = b.id * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = b.n * (blockDim.x >> 5);
-    CSum<T> sv[3];
     for (long long base = wg * kSegChunk; base < n; base += nw * kSegChunk) {
         long long s, t;
         seg_chunk_range(base, n, key_sorted, cs, s, t);
@@ -150,9 +147,8 @@ __device__ __forceinline__ void deposit_sorted_force_body(const T* __restrict__ 
                 v[1] = f.y;
                 v[2] = f.z;
             },
-            [&](int key, CSum<T> (&a)[3]) { reaction_emit<T>(g, S, key, a, sv); });
+            [&](int key, CSum<T> (&a)[3]) { reaction_emit<T>(g, S, key, a); });
     }
-    if (do_sums) block_sums<T, 3>(sv, part, pstride, b.id);
 }
 
 // Semi-implicit coefficients (Eq. UFP): per cell A = (1/V_B) sum beta and
@@ -196,10 +192,9 @@ k_deposit_implicit(const T* __restrict__ Bs, long long n, const int32_t* __restr
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_deposit_sorted_force(const T* __restrict__ Fs, long long n, const int32_t* __restrict__ key_sorted,
-                       const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S, T* __restrict__ part,
-                       long long pstride, int do_sums) {
+                       const int32_t* __restrict__ cs, GridDev g, T* __restrict__ S) {
     pdl_wait();
-    deposit_sorted_force_body(Fs, n, key_sorted, cs, g, S, part, pstride, do_sums, launch_blk());
+    deposit_sorted_force_body(Fs, n, key_sorted, cs, g, S, launch_blk());
 }
 
 // ----------------------------------------------------------------------
@@ -357,8 +352,7 @@ __global__ void __launch_bounds__(256) kb_pack(BLaunch L) {
 
 __global__ void __launch_bounds__(256) kb_deposit_momentum(BLaunch L) {
     batch_loop(L, [&](const BInst& I, Blk b) {
-        deposit_sorted_force_body<float>(I.Fs, I.n, I.key_sorted, I.count, I.gd, I.S_bulk,
-                                         I.part + 2 * I.part_off[PS_MOM], I.part_blocks[PS_MOM], 1, b);
+        deposit_sorted_force_body<float>(I.Fs, I.n, I.key_sorted, I.count, I.gd, I.S_bulk, b);
     });
 }
 
@@ -445,22 +439,16 @@ cg_status launch_deposit_volume(cg_grids* g, long long n, const void* pos_d, dou
     return CG_OK;
 }
 
-cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk, bool sums) {
+cg_status launch_deposit_sorted_force(cg_grids* g, long long n, void* S_bulk) {
     CG_CUDA(cudaMemsetAsync(S_bulk, 0, 3 * g->tsize * (size_t)g->gd.nbulk, g->stream));
-    void* part = part_ptr(g, PS_MOM);
-    if (n == 0) {
-        g->part_blocks[PS_MOM] = sums ? 1 : -1;
-        if (sums) CG_CUDA(cudaMemsetAsync(part, 0, 2 * g->tsize * 3, g->stream));
-        return CG_OK;
-    }
+    if (n == 0) return CG_OK;
     const unsigned nblk = seg_blocks(g, n);
-    g->part_blocks[PS_MOM] = sums ? (long long)nblk : -1;
     if (g->fp64)
         CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<double>, nblk, 256, 0, (const double*)g->Fs, n,
-                  g->key_sorted, g->cell_start, g->gd, (double*)S_bulk, (double*)part, (long long)nblk, (int)sums);
+                  g->key_sorted, g->cell_start, g->gd, (double*)S_bulk);
     else
         CG_LAUNCH(g, "deposit_momentum", k_deposit_sorted_force<float>, nblk, 256, 0, (const float*)g->Fs, n,
-                  g->key_sorted, g->cell_start, g->gd, (float*)S_bulk, (float*)part, (long long)nblk, (int)sums);
+                  g->key_sorted, g->cell_start, g->gd, (float*)S_bulk);
     return CG_OK;
 }
 
@@ -517,7 +505,7 @@ SumsMap sums_map(const long long* part_off, const long long* part_blocks) {
     col(1, PS_VOL, 0);
     for (int a = 0; a < 3; ++a) {
         col(2 + a, PS_DRAG, 1 + a);
-        col(5 + a, PS_MOM, a);
+        col(5 + a, PS_PROJ, 3 + a);   // S_B V_B: formed by the projection from the S_B it reads
         col(8 + a, PS_PROJ, a);
         col(12 + a, PS_DRAG, 5 + a);
     }

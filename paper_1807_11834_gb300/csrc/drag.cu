@@ -414,7 +414,7 @@ cg_status launch_drag(cg_grids* g, long long n, const void* pos_d, const void* v
         }
 #undef CG_DRAGP
     }
-    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, sums));
+    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk));
     if (coef_bulk) CG_TRY(launch_deposit_implicit(g, n, coef_bulk));
     return CG_OK;
 }

@@ -299,6 +299,19 @@ __device__ __forceinline__ void scale_sum(CSum<double>& a, const GridDev& g) {
     a.c *= g.Vf;
 }
 
+// S_B V_B of one bulk cell into a conservation sum: an exact float-float
+// product on the FP32 path (the reaction deposit's S_B = -(1/V_B) sum F,
+// so the sums of S_B V_B and of the forces cancel to the compensated sums'
+// accuracy).
+__device__ __forceinline__ void add_bulk_term(CSum<float>& a, float sb, const GridDev& g) {
+    const float hi = sb * g.VBh;
+    float lo = fmaf(sb, g.VBh, -hi);
+    lo = fmaf(sb, g.VBl, lo);
+    a.add(hi);
+    a.c += lo;
+}
+__device__ __forceinline__ void add_bulk_term(CSum<double>& a, double sb, const GridDev& g) { a.add(sb * g.VB); }
+
 // One thread per bulk cell (block b covers cells [b.id blockDim, (b.id + 1) blockDim)).
 template <typename T, int RC>
 __device__ __forceinline__ void project_body(const T* __restrict__ in0, const T* __restrict__ in1,
@@ -307,7 +320,7 @@ __device__ __forceinline__ void project_body(const T* __restrict__ in0, const T*
                                              T* __restrict__ out2, T* __restrict__ out3, T* __restrict__ part,
                                              long long pstride, int do_sums, Blk b) {
     const long long cb = b.id * blockDim.x + threadIdx.x;
-    CSum<T> sacc[3];
+    CSum<T> sacc[6];   // sum_f S_f (3), then sum S_B V_B of this thread's bulk cell (3)
     if (cb < g.nbulk) {
         int I, J, K;
         bulk_ijk(cb, g, I, J, K);
@@ -375,14 +388,17 @@ __device__ __forceinline__ void project_body(const T* __restrict__ in0, const T*
                     rowsum.add(rs);
                 }
             }
-            if (c < 3) sacc[c] = rowsum;
+            if (c < 3) {
+                sacc[c] = rowsum;
+                add_bulk_term(sacc[3 + c], f[1][1][1], g);   // the stencil's centre: this cell's S_B
+            }
         }
     }
     if (do_sums) {
         // sum_f S_f V_f = V_f sum_f S_f; V_f applied as a float-float product
 #pragma unroll
         for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
-        block_sums<T, 3>(sacc, part, pstride, b.id);
+        block_sums<T, 6>(sacc, part, pstride, b.id);
     }
 }
 
@@ -407,7 +423,7 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
                   T* __restrict__ part, long long pstride, int do_sums) {
     pdl_wait();
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    CSum<T> sacc[3];
+    CSum<T> sacc[6];   // sum_f S_f (3), then sum S_B V_B (3, from each bulk cell's lower-corner fine cell)
     if (f < g.nfine) {
         const int r = g.r;
         long long t = f;
@@ -438,13 +454,17 @@ k_project_generic(const T* __restrict__ in0, const T* __restrict__ in1, const T*
             }
             const T v = lerp(zv[0], zv[1], w[2]);
             O[f] = v;
-            if (c < 3) sacc[c].add(v);
+            if (c < 3) {
+                sacc[c].add(v);
+                if (fi[0] % r == 0 && fi[1] % r == 0 && fi[2] % r == 0)
+                    add_bulk_term(sacc[3 + c], __ldg(B + (fi[2] / r) * nbxy + (fi[1] / r) * nbx + fi[0] / r), g);
+            }
         }
     }
     if (do_sums) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) scale_sum(sacc[c], g);
-        block_sums<T, 3>(sacc, part, pstride, blockIdx.x);
+        block_sums<T, 6>(sacc, part, pstride, blockIdx.x);
     }
 }
 

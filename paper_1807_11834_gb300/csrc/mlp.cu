@@ -1047,7 +1047,7 @@ cg_status launch_drag_learned(cg_grids* g, const cg_mlp* m, long long n, void* p
                   (const WeightImage*)m->img, (float*)force, (float*)Fs, g->inv_perm, (float)dt, (float)age,
                   g->status);
     }
-    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk, true));
+    if (S_bulk) CG_TRY(launch_deposit_sorted_force(g, n, S_bulk));
     return CG_OK;
 }
 
