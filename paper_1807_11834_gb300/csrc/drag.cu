@@ -14,9 +14,12 @@
 // it contiguously.
 //
 // FP32 path: the lattice coordinate (x - x0)/H - 1/2 is formed in
-// float-float (TwoSum / FMA TwoProduct), so the interpolation weights carry
-// only the final float rounding even at |xi| ~ 100; the correlations run in
-// float with IEEE division and square root.
+// float-float (FMA TwoProduct and one TwoSum), so the interpolation weights
+// carry only the final float rounding even at |xi| ~ 100; the correlations
+// run in float with explicitly rounded operations, their powers, logarithm,
+// roots and reciprocals on the special-function unit (drag_law.cuh).
+// On request (CG_STENCIL_WINDOW) the sorted step stages each warp's stencil
+// window in shared memory instead of gathering from L2 (window_gather).
 #include <algorithm>
 
 #include "cg_internal.cuh"
