@@ -335,6 +335,25 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
              const int32_t* __restrict__ ctr) {
     pdl_wait();
     if (ctr[RB_FALLBACK]) return;
+    const long long base0 = (long long)blockIdx.x * kRebinTile;
+    if (__ldg(blk_start + gridDim.x) == 0) {
+        // no particle changed its cell (the scanned departures sum to zero):
+        // slot s keeps its particle and cell, so key_sorted stands, and in the
+        // caller's order perm and inv_perm stand too; the diameters are read
+        // afresh (a particle may have changed its size)
+#pragma unroll
+        for (int k = 0; k < kRebinItems; ++k) {
+            const long long s = base0 + k * kRebinThreads + threadIdx.x;
+            if (s >= n) continue;
+            const int i = IDENT ? (int)s : __ldg(rid + s);
+            vol_sorted[s] = __ldg(vol + i);
+            if (IDENT) {
+                perm[s] = i;
+                inv_perm[i] = (int)s;
+            }
+        }
+        return;
+    }
     constexpr int W = kRebinThreads / 32;
     __shared__ int s_tab[kRebinItems * W];
     const unsigned full = 0xffffffffu;

@@ -163,6 +163,44 @@ def test_stencil_window_gives_the_gather_bits(cuda_lib):
             assert torch.equal(a[k], b[k]), (step, k)
 
 
+@pytest.mark.parametrize("sorted_step", [False, True])
+def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
+    """Steps whose particles keep their cells (no advance) while their
+    diameters change: the rebinning finds no mover and keeps the bins, and
+    the porosity and forces follow the new diameters; bins, fields and
+    forces equal a fresh handle's on the same input, bit for bit."""
+    import torch
+    cg = cuda_lib
+    w = synth.small_clustered_bed(seed=17)
+    g = cg.Grids(w.desc)
+    pos, vel, uf = inputs(w)
+    out = g.alloc_outputs(w.n, eps_fine=True, bins=True)
+    bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
+    par = 0
+    rng = np.random.default_rng(3)
+    for step in range(4):
+        pi, vi = bufs[par]
+        if step >= 2:   # new diameters, same positions
+            scale = torch.from_numpy(rng.uniform(0.8, 1.2, w.n).astype(np.float32)).cuda()
+            pi[:, 3] *= scale
+        ref_in = (pi.clone(), vi.clone())
+        if sorted_step:
+            po, vo = bufs[par ^ 1]
+            g.cg_step_sorted(pi, vi, po, vo, uf, out, dt=0.0)
+            par ^= 1
+        else:
+            g.cg_step(pi, vi, uf, out, dt=0.0)
+        f = cg.Grids(w.desc)
+        o2 = f.alloc_outputs(w.n, eps_fine=True, bins=True)
+        f.cg_step(ref_in[0], ref_in[1], uf, o2, dt=0.0)
+        torch.cuda.synchronize()
+        for k in ("cell", "perm", "cell_start", "eps_bulk", "u_bulk", "force", "S_bulk", "S_fine", "eps_fine"):
+            assert torch.equal(out[k], o2[k]), (step, k)
+        f.close()
+    assert g.cg_sync_status()[0] == 0
+    g.close()
+
+
 def test_fallback_when_most_particles_changed(cuda_lib):
     """The same handle bins three unrelated particle sets of one count (every
     particle a mover: the device falls back to the per-cell sort) and then
