@@ -237,10 +237,12 @@ cg_status cg_grid_dims(const cg_grids* g, int32_t bulk_n[3], int64_t* n_bulk, in
  * particles whose cell changed are re-sorted, with particle i taken to be
  * the particle i of that binning (or, for the sorted output of
  * cg_step_sorted, the particle at its slot i).  The result is the same
- * stable order whatever the particles did; when more than a quarter of them
- * changed cell, or a cell received more than 256, the device falls back to
- * the per-cell sort.  A descriptor with a digit width (6..11) always sorts
- * from scratch. */
+ * stable order whatever the particles did (moved, resized or permuted);
+ * any share of them may change cell, and when a cell receives more than
+ * 256 in one call the device falls back to the per-cell sort.  When none
+ * changed cell the bins are kept and only the sorted diameters are read
+ * afresh.  A descriptor with a digit width (6..11) always sorts from
+ * scratch. */
 cg_status cg_bin_particles(cg_grids* g, int64_t n, const void* pos_d,
                            int32_t* cell_out, int32_t* perm_out, int32_t* cell_start_out);
 
