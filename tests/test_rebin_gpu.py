@@ -166,9 +166,11 @@ def test_stencil_window_gives_the_gather_bits(cuda_lib):
 @pytest.mark.parametrize("sorted_step", [False, True])
 def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
     """Steps whose particles keep their cells (no advance) while their
-    diameters change: the rebinning finds no mover and keeps the bins, and
-    the porosity and forces follow the new diameters; bins, fields and
-    forces equal a fresh handle's on the same input, bit for bit."""
+    diameters change, then two particles of one cell swap places in the
+    caller's arrays: the rebinning finds no mover and keeps the bins, and
+    the porosity and forces follow the new diameters and the swap; bins,
+    fields and forces equal a fresh handle's on the same input, bit for
+    bit."""
     import torch
     cg = cuda_lib
     w = synth.small_clustered_bed(seed=17)
@@ -178,11 +180,20 @@ def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
     bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
     par = 0
     rng = np.random.default_rng(3)
-    for step in range(4):
+    for step in range(5):
         pi, vi = bufs[par]
-        if step >= 2:   # new diameters, same positions
+        if step in (2, 3):   # new diameters, same positions
             scale = torch.from_numpy(rng.uniform(0.8, 1.2, w.n).astype(np.float32)).cuda()
             pi[:, 3] *= scale
+        if step == 4:   # two particles of one cell swap places in the caller's arrays
+            cs = out["cell_start"].cpu().numpy()
+            s0 = int(cs[np.nonzero(np.diff(cs) >= 2)[0][0]])   # first slot of a cell holding two or more
+            # the input's indices: the last binning's slots (sorted step) or its perm (caller order)
+            a, b = (s0, s0 + 1) if sorted_step else (int(out["perm"][s0]), int(out["perm"][s0 + 1]))
+            for arr in (pi, vi):
+                t = arr[a].clone()
+                arr[a] = arr[b]
+                arr[b] = t
         ref_in = (pi.clone(), vi.clone())
         if sorted_step:
             po, vo = bufs[par ^ 1]
