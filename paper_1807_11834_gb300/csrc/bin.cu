@@ -427,6 +427,7 @@ __device__ __forceinline__ void scan_reduce_body(const ScanJob& j, int32_t* __re
 
 __global__ void __launch_bounds__(256) k_scan_reduce(ScanJob j, int32_t* __restrict__ part) {
     pdl_wait();
+    if (j.skip && __ldg(j.skip) == 0) return;
     scan_reduce_body(j, part, launch_blk());
 }
 
@@ -464,13 +465,18 @@ __device__ __forceinline__ void scan_down_body(const ScanJob& j, const int32_t* 
 
 __global__ void __launch_bounds__(256) k_scan_down(ScanJob j, const int32_t* __restrict__ part) {
     pdl_wait();
+    if (j.skip && __ldg(j.skip) == 0) return;
     scan_down_body(j, part, launch_blk());
 }
 
 // Exclusive scans of up to three arrays by one pair of launches (out may
-// alias in; an array with in == nullptr is skipped).
-cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m) {
+// alias in; an array with in == nullptr is skipped).  skip (device, may be
+// null): when it reads 0 the launches return at once, the caller having
+// left the outputs in their scanned form.
+cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m,
+                         const int32_t* skip) {
     ScanJob j;
+    j.skip = skip;
     long long nblk = 0;
     for (int a = 0; a < kScanArrays; ++a) {
         const bool use = a < count && in[a];

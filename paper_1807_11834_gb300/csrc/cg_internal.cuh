@@ -297,6 +297,7 @@ struct ScanJob {
     int32_t* out[kScanArrays] = {};
     long long m[kScanArrays] = {};
     long long nblk[kScanArrays] = {};
+    const int32_t* skip = nullptr;   // device flag: when 0, the outputs already hold the scans and nothing runs
 };
 
 // Column map of the conservation-sum reduction: sum k merges cnt[k]
@@ -308,7 +309,8 @@ struct SumsMap {
 
 cg_status ensure_particle_capacity(cg_grids* g, long long n);
 // Exclusive scans of up to kScanArrays int32 arrays (in[a] nullable: skipped).
-cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m);
+cg_status scan_exclusive(cg_grids* g, int count, const int32_t* const* in, int32_t* const* out, const long long* m,
+                         const int32_t* skip = nullptr);
 // Placement and per-cell sort of the per-cell binning sort from the cell
 // starts cs; with run_if set they do nothing unless *run_if != 0.
 cg_status launch_cellsort_tail(cg_grids* g, long long n, const int32_t* cs, const int32_t* run_if);

@@ -29,7 +29,9 @@
 // arrivals of their cell) the device falls back to the per-cell sort: both
 // paths are launched and
 // each kernel checks a device flag, so a captured CUDA graph takes the
-// right path on every replay.
+// right path on every replay.  The same holds when no particle changed its
+// cell: the scans return at once on a device count of the movers, and the
+// kernels after them keep the old bins.
 #include <algorithm>
 
 #include "cg_internal.cuh"
@@ -38,7 +40,7 @@ namespace cg {
 
 namespace {
 
-enum { RB_FALLBACK = 0 };
+enum { RB_FALLBACK = 0, RB_MOVERS = 1 };   // counters: fallback flag, movers
 constexpr int kCellBits = 22;   // a mover entry packs its new cell (< 2^22) and arrival rank (< 2^8)
 
 struct RebinPtrs {
@@ -85,11 +87,10 @@ __device__ __forceinline__ void add_status_counts(unsigned long long* st, int ou
     }
 }
 
-// Cell and diameter of particle p (caller order), with the status counts.
+// Cell and diameter of particle p (caller order, record v), with the status counts.
 template <typename T>
-__device__ __forceinline__ int key_of(const T* __restrict__ pos, long long p, const GridDev& g,
-                                      int32_t* __restrict__ key, T* __restrict__ vol, int& n_out, int& n_nf) {
-    const V4<T> v = ld4(pos, p);
+__device__ __forceinline__ int key_of(const V4<T>& v, long long p, const GridDev& g, int32_t* __restrict__ key,
+                                      T* __restrict__ vol, int& n_out, int& n_nf) {
     int outside = 0;
     if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) n_nf++;
     const int c = cell_of(v, g, outside);
@@ -108,19 +109,27 @@ __device__ __forceinline__ void flush_status(unsigned long long* st, int n_out, 
 }  // namespace
 
 // Cells and diameters in the caller's order (the particles kept their order:
-// old slot s holds perm_old[s]).
+// old slot s holds perm_old[s]).  Six CTAs per SM (40 registers): the
+// loads of more warps in flight (measured faster than four).
 template <typename T>
-__global__ void __launch_bounds__(kRebinThreads)
+__global__ void __launch_bounds__(kRebinThreads, 6)
 k_rebin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key, T* __restrict__ vol,
             unsigned long long* __restrict__ status, double* __restrict__ eps_fill, T* __restrict__ rec_fill,
             T* __restrict__ eps_t_fill) {
     pdl_wait();
     int n_out = 0, n_nf = 0;
     const long long base = (long long)blockIdx.x * kRebinTile;
+    V4<T> pv[kRebinItems];
+    // every load of the thread first, so that they are in flight together
 #pragma unroll
     for (int k = 0; k < kRebinItems; ++k) {
         const long long p = base + k * kRebinThreads + threadIdx.x;
-        if (p < n) key_of(pos, p, g, key, vol, n_out, n_nf);
+        if (p < n) pv[k] = ld4(pos, p);
+    }
+#pragma unroll
+    for (int k = 0; k < kRebinItems; ++k) {
+        const long long p = base + k * kRebinThreads + threadIdx.x;
+        if (p < n) key_of(pv[k], p, g, key, vol, n_out, n_nf);
     }
     flush_status(status, n_out, n_nf);
     eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
@@ -205,6 +214,7 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
             t += s_cnt[w];
         }
         blk_dep[blockIdx.x] = t;
+        if (t) atomicAdd(&ctr[RB_MOVERS], t);
     }
     __syncthreads();
     if (wc) {
@@ -224,7 +234,8 @@ k_rebin_mark(const T* __restrict__ pos, long long n, GridDev g, const int32_t* _
     if (IDENT) eps_fill_cells<T>(g.nbulk, eps_fill, rec_fill, eps_t_fill);
 }
 
-// The new count of every cell; or, when the device falls back to the
+// The new count of every cell (the new starts themselves when no particle
+// changed its cell: the scans are then left out); or, when the device falls back to the
 // per-cell sort, that sort's per-cell counts and arrival ranks (consecutive
 // lanes on consecutive particles, one atomic per run of equal cells), from
 // the cells already formed (IDENT: from rkn, whose cells are written to key
@@ -236,6 +247,15 @@ k_rebin_cells(const int32_t* __restrict__ cs_old, long long nbulk, const int32_t
               int32_t* __restrict__ key, const int32_t* __restrict__ rkn, long long n, int32_t* __restrict__ arrival) {
     pdl_wait();
     if (!ctr[RB_FALLBACK]) {
+        if (ctr[RB_MOVERS] == 0) {
+            // no particle changed its cell: the new starts are the old ones,
+            // written in their scanned form (the scans are left out; the
+            // arrivals and departures, all zero, are their own scans)
+            for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c <= nbulk;
+                 c += (long long)gridDim.x * blockDim.x)
+                cnt[c] = __ldg(cs_old + c);
+            return;
+        }
         for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nbulk;
              c += (long long)gridDim.x * blockDim.x)
             cnt[c] = __ldg(cs_old + c + 1) - __ldg(cs_old + c) - __ldg(dep + c) + __ldg(arr + c);
@@ -341,15 +361,26 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
         // slot s keeps its particle and cell, so key_sorted stands, and in the
         // caller's order perm and inv_perm stand too; the diameters are read
         // afresh (a particle may have changed its size)
+        int ik[kRebinItems];
+        T dk[kRebinItems];
+#pragma unroll
+        for (int k = 0; k < kRebinItems; ++k) {
+            const long long s = base0 + k * kRebinThreads + threadIdx.x;
+            ik[k] = IDENT ? (int)s : (s < n ? __ldg(rid + s) : 0);
+        }
+#pragma unroll
+        for (int k = 0; k < kRebinItems; ++k) {
+            const long long s = base0 + k * kRebinThreads + threadIdx.x;
+            if (s < n) dk[k] = __ldg(vol + ik[k]);
+        }
 #pragma unroll
         for (int k = 0; k < kRebinItems; ++k) {
             const long long s = base0 + k * kRebinThreads + threadIdx.x;
             if (s >= n) continue;
-            const int i = IDENT ? (int)s : __ldg(rid + s);
-            vol_sorted[s] = __ldg(vol + i);
+            vol_sorted[s] = dk[k];
             if (IDENT) {
-                perm[s] = i;
-                inv_perm[i] = (int)s;
+                perm[s] = ik[k];
+                inv_perm[ik[k]] = (int)s;
             }
         }
         return;
@@ -478,7 +509,7 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
         const int32_t* in[3] = {R.cnt, R.arr, R.blk};
         int32_t* out[3] = {R.cnt, R.arr, R.blk};
         const long long m[3] = {nbulk + 1, nbulk + 1, nblk + 1};
-        CG_TRY(scan_exclusive(g, 3, in, out, m));
+        CG_TRY(scan_exclusive(g, 3, in, out, m, R.ctr + RB_MOVERS));
     }
     const unsigned pgrid = (unsigned)std::max<long long>(1, std::min<long long>((nblk + 7) / 8, (long long)g->num_sms * 8));
     CG_LAUNCH(g, "rebin_place", k_rebin_place, pgrid, 256, 0, (const int2*)g->rb_mov, (const int32_t*)R.blk, nblk,
