@@ -109,10 +109,10 @@ __device__ __forceinline__ void flush_status(unsigned long long* st, int n_out, 
 }  // namespace
 
 // Cells and diameters in the caller's order (the particles kept their order:
-// old slot s holds perm_old[s]).  Six CTAs per SM (40 registers): the
-// loads of more warps in flight (measured faster than four).
+// old slot s holds perm_old[s]).  FP32: six CTAs per SM (40 registers),
+// the loads of more warps in flight (measured faster than four).
 template <typename T>
-__global__ void __launch_bounds__(kRebinThreads, 6)
+__global__ void __launch_bounds__(kRebinThreads, sizeof(T) == 4 ? 6 : 4)
 k_rebin_key(const T* __restrict__ pos, long long n, GridDev g, int32_t* __restrict__ key, T* __restrict__ vol,
             unsigned long long* __restrict__ status, double* __restrict__ eps_fill, T* __restrict__ rec_fill,
             T* __restrict__ eps_t_fill) {
