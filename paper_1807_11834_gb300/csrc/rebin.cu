@@ -347,16 +347,14 @@ __device__ __forceinline__ void emit(long long n, long long ns, int i, int c, in
 // totals), the rows and warps before it in the block (a table of warp
 // counts), and the lanes before it (ballot).
 template <typename T, bool IDENT>
-__global__ void __launch_bounds__(kRebinThreads)
-k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
-             const int32_t* __restrict__ blk_start, const int32_t* __restrict__ arr_start,
-             const int2* __restrict__ arr_list, const T* __restrict__ vol, int32_t* __restrict__ perm,
-             int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm, T* __restrict__ vol_sorted,
-             const int32_t* __restrict__ ctr) {
-    pdl_wait();
-    if (ctr[RB_FALLBACK]) return;
-    const long long base0 = (long long)blockIdx.x * kRebinTile;
-    if (__ldg(blk_start + gridDim.x) == 0) {
+__device__ __forceinline__ void rebin_stay_body(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn,
+                                                long long n, const int32_t* __restrict__ blk_start,
+                                                const int32_t* __restrict__ arr_start, const int2* __restrict__ arr_list,
+                                                const T* __restrict__ vol, int32_t* __restrict__ perm,
+                                                int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+                                                T* __restrict__ vol_sorted, long long bid, long long nblk) {
+    const long long base0 = bid * kRebinTile;
+    if (__ldg(blk_start + nblk) == 0) {
         // no particle changed its cell (the scanned departures sum to zero):
         // slot s keeps its particle and cell, so key_sorted stands, and in the
         // caller's order perm and inv_perm stand too; the diameters are read
@@ -389,7 +387,7 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
     __shared__ int s_tab[kRebinItems * W];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long base = (long long)blockIdx.x * kRebinTile;
+    const long long base = base0;
     int kn[kRebinItems], id[kRebinItems], a0[kRebinItems], a1[kRebinItems];
     T d[kRebinItems];
     unsigned db[kRebinItems];
@@ -423,7 +421,7 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
             const int o = __shfl_up_sync(full, incl, off);
             if (lane >= off) incl += o;
         }
-        s_tab[lane] = __ldg(blk_start + blockIdx.x) + incl - c;
+        s_tab[lane] = __ldg(blk_start + bid) + incl - c;
     }
     __syncthreads();
 #pragma unroll
@@ -445,16 +443,16 @@ k_rebin_stay(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, l
 // search over the old segment, whose ids ascend, then a count of the
 // stayers before that point) and the arrivals with an id below it.
 template <typename T, bool IDENT>
-__global__ void __launch_bounds__(256)
-k_rebin_movers(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
-               const int32_t* __restrict__ cs_old, const int32_t* __restrict__ cs_new,
-               const int32_t* __restrict__ arr_start, const int2* __restrict__ arr_list, long long nbulk,
-               const T* __restrict__ vol, int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted,
-               int32_t* __restrict__ inv_perm, T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr) {
-    pdl_wait();
-    if (ctr[RB_FALLBACK]) return;
+__device__ __forceinline__ void rebin_movers_body(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn,
+                                                  long long n, const int32_t* __restrict__ cs_old,
+                                                  const int32_t* __restrict__ cs_new,
+                                                  const int32_t* __restrict__ arr_start,
+                                                  const int2* __restrict__ arr_list, long long nbulk,
+                                                  const T* __restrict__ vol, int32_t* __restrict__ perm,
+                                                  int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+                                                  T* __restrict__ vol_sorted, long long bid, long long nb) {
     const long long nm = __ldg(arr_start + nbulk);   // all arrivals
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nm; q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = bid * blockDim.x + threadIdx.x; q < nm; q += nb * blockDim.x) {
         const int2 m = arr_list[q];
         const int i = m.x, c = m.y;
         const int o0 = __ldg(cs_old + c), o1 = __ldg(cs_old + c + 1);
@@ -474,6 +472,27 @@ k_rebin_movers(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn,
         const long long ns = (long long)__ldg(cs_new + c) + stay + arrivals_below(arr_list, a0, a1, i);
         emit<T>(n, ns, i, c, perm, key_sorted, inv_perm, vol, vol_sorted);
     }
+}
+
+// Every particle's new slot in one launch: blocks [0, mgrid) place the
+// movers (first, so that their searches run beside the stayers), blocks
+// [mgrid, mgrid + nblk) the stayers of one block of old slots each.
+template <typename T, bool IDENT>
+__global__ void __launch_bounds__(kRebinThreads)
+k_rebin_slots(const int32_t* __restrict__ rid, const int32_t* __restrict__ rkn, long long n,
+              const int32_t* __restrict__ blk_start, const int32_t* __restrict__ cs_old,
+              const int32_t* __restrict__ cs_new, const int32_t* __restrict__ arr_start,
+              const int2* __restrict__ arr_list, long long nbulk, const T* __restrict__ vol,
+              int32_t* __restrict__ perm, int32_t* __restrict__ key_sorted, int32_t* __restrict__ inv_perm,
+              T* __restrict__ vol_sorted, const int32_t* __restrict__ ctr, long long nblk, long long mgrid) {
+    pdl_wait();
+    if (ctr[RB_FALLBACK]) return;
+    if ((long long)blockIdx.x < mgrid)
+        rebin_movers_body<T, IDENT>(rid, rkn, n, cs_old, cs_new, arr_start, arr_list, nbulk, vol, perm, key_sorted,
+                                    inv_perm, vol_sorted, blockIdx.x, mgrid);
+    else
+        rebin_stay_body<T, IDENT>(rid, rkn, n, blk_start, arr_start, arr_list, vol, perm, key_sorted, inv_perm,
+                                  vol_sorted, blockIdx.x - mgrid, nblk);
 }
 
 template <typename T>
@@ -514,21 +533,19 @@ static cg_status rebin_impl(cg_grids* g, long long n, const T* pos, bool ident, 
     const unsigned pgrid = (unsigned)std::max<long long>(1, std::min<long long>((nblk + 7) / 8, (long long)g->num_sms * 8));
     CG_LAUNCH(g, "rebin_place", k_rebin_place, pgrid, 256, 0, (const int2*)g->rb_mov, (const int32_t*)R.blk, nblk,
               (const int32_t*)R.arr, g->rb_arr, (const int32_t*)R.ctr);
-    const unsigned mgrid = (unsigned)(g->num_sms * 8);
-#define CG_REBIN_TAIL(ID)                                                                                        \
-    CG_LAUNCH(g, "rebin_stay", (k_rebin_stay<T, ID>), (unsigned)nblk, kRebinThreads, 0, (const int32_t*)g->rb_rid,   \
-              (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk, (const int32_t*)R.arr, (const int2*)g->rb_arr,    \
-              (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr);      \
-    CG_LAUNCH(g, "rebin_movers", (k_rebin_movers<T, ID>), mgrid, 256, 0, (const int32_t*)g->rb_rid,                 \
-              (const int32_t*)g->rb_rkn, n, (const int32_t*)g->cell_start, (const int32_t*)R.cnt,                   \
-              (const int32_t*)R.arr, (const int2*)g->rb_arr, nbulk, (const T*)g->vol, g->perm, g->key_sorted,      \
-              g->inv_perm, (T*)g->vol_sorted, (const int32_t*)R.ctr)
+    const long long mgrid = (long long)g->num_sms * 8;
+#define CG_REBIN_SLOTS(ID)                                                                                        \
+    CG_LAUNCH(g, "rebin_slots", (k_rebin_slots<T, ID>), (unsigned)(mgrid + nblk), kRebinThreads, 0,                 \
+              (const int32_t*)g->rb_rid, (const int32_t*)g->rb_rkn, n, (const int32_t*)R.blk,                      \
+              (const int32_t*)g->cell_start, (const int32_t*)R.cnt, (const int32_t*)R.arr, (const int2*)g->rb_arr,   \
+              nbulk, (const T*)g->vol, g->perm, g->key_sorted, g->inv_perm, (T*)g->vol_sorted,                      \
+              (const int32_t*)R.ctr, nblk, mgrid)
     if (ident) {
-        CG_REBIN_TAIL(true);
+        CG_REBIN_SLOTS(true);
     } else {
-        CG_REBIN_TAIL(false);
+        CG_REBIN_SLOTS(false);
     }
-#undef CG_REBIN_TAIL
+#undef CG_REBIN_SLOTS
     // fallback: placement and per-cell sort from the scanned counts
     CG_TRY(launch_cellsort_tail(g, n, R.cnt, R.ctr + RB_FALLBACK));
     CG_CUDA(cudaMemcpyAsync(g->cell_start, R.cnt, sizeof(int32_t) * (nbulk + 1), cudaMemcpyDeviceToDevice, g->stream));
