@@ -329,6 +329,7 @@ def run_gb300(args):
     # the sorted step reads one pair of particle arrays and writes the other
     bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))] if sorted_step else [(pos, vel)]
     par = [0]
+    replayed = [0]   # kernels of the graph replays so far
 
     def reset():
         if run_len:
@@ -384,17 +385,20 @@ def run_gb300(args):
             for _ in range(2 * variants):
                 eager_fn()
         cs.synchronize()
-        graphs = []
+        graphs, counts = [], []
         for _ in range(variants):
             gr = torch.cuda.CUDAGraph()
+            c0 = g.cg_launch_count()
             with torch.cuda.graph(gr, stream=cs):
                 eager_fn()
+            counts.append(g.cg_launch_count() - c0)   # the library's kernels the graph holds
             graphs.append(gr)
         g.set_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
 
         def replay():
             graphs[par[0]].replay()
+            replayed[0] += counts[par[0]]
             par[0] = (par[0] + 1) % variants
         return replay
 
@@ -405,12 +409,6 @@ def run_gb300(args):
     if rc != 0:
         raise RuntimeError(f"warm-up status {rc} flags {flags} counts {counts}")
     reset()
-
-    # launches of one step (counted eagerly; graph replays run the same kernels)
-    l0 = g.cg_launch_count()
-    eager_fn()
-    launches_per_step = g.cg_launch_count() - l0
-    torch.cuda.synchronize()
 
     eager_ms, _, _ = timed(eager_fn, min(args.steps, 200))
     eager_ms_step = eager_ms / min(args.steps, 200)
@@ -426,8 +424,12 @@ def run_gb300(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.35)
+    replayed[0] = 0
+    l0 = g.cg_launch_count()
     ms, t0, t1 = timed(step_fn, args.steps)
-    launches = launches_per_step * args.steps
+    # the library's kernels launched in the timed region: those of the
+    # replayed graphs, or counted as launched by the eager steps
+    launches = replayed[0] if step_fn is not eager_fn else g.cg_launch_count() - l0
     time.sleep(0.25)
     sampler.stop()
     ms = max_over_ranks(ms, world, dev)
@@ -559,7 +561,7 @@ def run_gb300(args):
                                   else "eager step calls") + (" (one graph per particle buffer, in turn)"
                                                               if sorted_step and not args.no_graph else ""),
                        "eager_ms_per_step": round(eager_ms_step, 5),
-                       "launches_per_step": launches_per_step,
+                       "launches_per_step": round(launches / args.steps, 3),
                        "step_algorithmic_bytes": step_bytes, "step_gbs": round(step_gbs, 1),
                        "step_frac_of_hbm": round(step_gbs / peak, 4),
                        "semi_implicit": bool(args.implicit),
