@@ -167,10 +167,12 @@ def test_stencil_window_gives_the_gather_bits(cuda_lib):
 def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
     """Steps whose particles keep their cells (no advance) while their
     diameters change, then two particles of one cell swap places in the
-    caller's arrays: the rebinning finds no mover and keeps the bins, and
-    the porosity and forces follow the new diameters and the swap; bins,
-    fields and forces equal a fresh handle's on the same input, bit for
-    bit."""
+    caller's arrays: the rebinning finds no mover and keeps the bins (its
+    scans left out), and the porosity and forces follow the new diameters
+    and the swap.  Then 64 particles take the positions of others (movers
+    after steps without any: the scans run again) and a last step has no
+    mover again.  Bins, fields and forces equal a fresh handle's on the
+    same input, bit for bit, at every step."""
     import torch
     cg = cuda_lib
     w = synth.small_clustered_bed(seed=17)
@@ -180,7 +182,7 @@ def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
     bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
     par = 0
     rng = np.random.default_rng(3)
-    for step in range(5):
+    for step in range(7):
         pi, vi = bufs[par]
         if step in (2, 3):   # new diameters, same positions
             scale = torch.from_numpy(rng.uniform(0.8, 1.2, w.n).astype(np.float32)).cuda()
@@ -194,6 +196,10 @@ def test_no_movers_with_new_diameters(cuda_lib, sorted_step):
                 t = arr[a].clone()
                 arr[a] = arr[b]
                 arr[b] = t
+        if step == 5:   # 64 particles move onto the positions of others (diameters kept)
+            dst = torch.from_numpy(rng.choice(w.n, 64, replace=False)).cuda()
+            src = torch.from_numpy(rng.choice(w.n, 64, replace=False)).cuda()
+            pi[dst, :3] = pi[src, :3]
         ref_in = (pi.clone(), vi.clone())
         if sorted_step:
             po, vo = bufs[par ^ 1]
