@@ -641,10 +641,12 @@ __device__ __forceinline__ int cell_of_d(double x, double y, double z, const Gri
 // segments (cells) that START in its chunks and runs past a chunk's end to
 // finish its last segment, so every segment is reduced by exactly one warp
 // and the work follows the particles, not the cells (a dense bed occupying
-// a few percent of the cells still spreads over every SM).  The warp walks
-// its segments one by one: lane l accumulates slots b + l, b + l + 32, ...
-// of segment [b, e) in a compensated sum, and a fixed xor tree combines the
-// lanes.  The summation order depends only on the segment's own slots.
+// a few percent of the cells still spreads over every SM).  The warp reduces
+// its range in rounds: 32 slots a round, one per lane, with a segmented
+// shuffle scan (seg_rounds: the reaction), or 256 slots a round, 8
+// consecutive ones per lane (seg_seq: the porosity).  The rounds start at the
+// range's first slot, so the summation order depends only on the chunk's
+// slots, never on the launch shape.
 // ----------------------------------------------------------------------
 constexpr int kSegChunk = 256;
 
@@ -894,20 +896,6 @@ __device__ __forceinline__ void sphere_volume_pair(float d, float& hi, float& lo
 __device__ __forceinline__ void sphere_volume_pair(double d, double& hi, double& lo) {
     hi = 0.52359877559829887308 * d * d * d;
     lo = 0.0;
-}
-
-// Walk the segments owned by the chunk at `base`: fn(key, b, e) for each.
-template <typename Fn>
-__device__ __forceinline__ void seg_walk(long long base, long long n, const int32_t* __restrict__ key_sorted,
-                                         const int32_t* __restrict__ cs, Fn fn) {
-    long long s, t;
-    seg_chunk_range(base, n, key_sorted, cs, s, t);
-    while (s < t) {
-        const int key = __ldg(key_sorted + s);
-        const long long e = __ldg(cs + key + 1);
-        fn(key, s, e);
-        s = e;
-    }
 }
 
 // Inclusive segmented scan of K compensated sums over the lanes, keyed by
