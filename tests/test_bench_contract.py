@@ -43,3 +43,22 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_do_no_work():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_stored_counters_key_on_code_not_comments(tmp_path):
+    """The key under which the benchmark keeps a kernel's measured DRAM
+    traffic ignores the comments and spacing of its source files but changes
+    with their code (a changed kernel reports no traffic until it is
+    captured again)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "a.cu"
+    a.write_text("int f(int x) {  // add one\n  return x + 1; /* the sum */ }\n")
+    b = tmp_path / "b.cu"
+    b.write_text("/* header\n   over two lines */\nint f(int x) {\n    return x + 1;   // plus one\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.file_sha(str(a)) == bench.file_sha(str(b))
+    assert bench.file_sha(str(a)) != bench.file_sha(str(c))
+    for tr in bench.NCU_TRAFFIC.values():
+        assert tr["bytes"] > 0 and all(len(sha) == 16 for sha in tr["files"].values())
