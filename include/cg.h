@@ -383,7 +383,11 @@ cg_status cg_step_host(cg_grids* g, const cg_particles* p, const void* u_fine,
  * step and the copies out, and returns.  Two staging sets are used in turn,
  * so the input copies of one call overlap the output copies of the
  * previous one.  Until cg_step_host_wait returns, the host inputs of a call
- * must stay unchanged and its host outputs are not yet valid. */
+ * must stay unchanged and its host outputs are not yet valid.  One
+ * exception: when a call advances its particles in place (dt > 0), a later
+ * call given the same particle arrays (p->pos_d or p->vel) copies them in
+ * only after the advanced particles have arrived there, so an advancing run
+ * may enqueue its steps back to back on one pair of arrays. */
 cg_status cg_step_host_async(cg_grids* g, const cg_particles* p, const void* u_fine,
                              const cg_step_out* out, double dt);
 /* Wait for every host-buffer step enqueued on the handle. */

@@ -270,6 +270,9 @@ static void free_all(cg_grids* g) {
     }
     dfree(g->fresh4.p);
     g->fresh4.bytes = 0;
+    if (g->part_out) cudaEventDestroy(g->part_out);
+    g->part_out = nullptr;
+    g->part_pos = g->part_vel = nullptr;
     if (g->h2d) cudaStreamDestroy(g->h2d);
     if (g->d2h) cudaStreamDestroy(g->d2h);
     g->h2d = g->d2h = nullptr;
@@ -666,7 +669,11 @@ cg_status cg_step_learned(cg_grids* g, const cg_particles* p, const void* u_fine
 // inputs go in on the h2d stream (after the set's previous outputs have
 // left), the step runs on the handle's stream, and the outputs go out on the
 // d2h stream; so the copies of consecutive steps overlap each other and the
-// compute (one direction each way at a time).
+// compute (one direction each way at a time).  A step that advances its
+// particles (dt > 0) sends them back first; a later call whose particle
+// arrays are those host arrays copies them in only after they have arrived
+// (its fluid field goes in meanwhile), so advancing steps may be enqueued
+// back to back on the same arrays.
 static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const void* u_fine, const cg_step_out* out,
                                    double dt) {
     const long long n = p->n;
@@ -702,13 +709,16 @@ static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const voi
     CG_TRY(ensure_particle_capacity(g, n));
     g->hs_next ^= 1;
 
-    // inputs in
+    // inputs in: the fluid field, then the particles (once a step that
+    // advanced these host arrays has sent them back)
     if (S.used) CG_CUDA(cudaStreamWaitEvent(g->h2d, S.out_done, 0));
+    CG_CUDA(cudaMemcpyAsync(S.ufine.p, u_fine, 3 * ts * nf, cudaMemcpyHostToDevice, g->h2d));
     if (n > 0) {
+        if (g->part_out && (p->pos_d == g->part_pos || p->vel == g->part_vel))
+            CG_CUDA(cudaStreamWaitEvent(g->h2d, g->part_out, 0));
         CG_CUDA(cudaMemcpyAsync(S.pos.p, p->pos_d, 4 * ts * n, cudaMemcpyHostToDevice, g->h2d));
         CG_CUDA(cudaMemcpyAsync(S.vel.p, p->vel, 4 * ts * n, cudaMemcpyHostToDevice, g->h2d));
     }
-    CG_CUDA(cudaMemcpyAsync(S.ufine.p, u_fine, 3 * ts * nf, cudaMemcpyHostToDevice, g->h2d));
     CG_CUDA(cudaEventRecord(S.in_done, g->h2d));
     S.used = true;
 
@@ -737,6 +747,15 @@ static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const voi
         if (dst && bytes) CG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
         return CG_OK;
     };
+    if (dt > 0.0 && n > 0) {
+        // the advanced particles first: the next step on these arrays waits for them
+        if (!g->part_out) CG_CUDA(cudaEventCreateWithFlags(&g->part_out, cudaEventDisableTiming));
+        CG_TRY(d2h(p->pos_d, S.pos.p, 4 * ts * n));
+        CG_TRY(d2h(p->vel, S.vel.p, 4 * ts * n));
+        CG_CUDA(cudaEventRecord(g->part_out, s));
+        g->part_pos = p->pos_d;
+        g->part_vel = p->vel;
+    }
     CG_TRY(d2h(out->eps_bulk, d.eps_bulk, sizeof(double) * nb));
     CG_TRY(d2h(out->u_bulk, d.u_bulk, 3 * ts * nb));
     CG_TRY(d2h(out->var_bulk, d.var_bulk, ts * nb));
@@ -748,10 +767,6 @@ static cg_status step_host_enqueue(cg_grids* g, const cg_particles* p, const voi
     CG_TRY(d2h(out->cell, d.cell, sizeof(int32_t) * n));
     CG_TRY(d2h(out->perm, d.perm, sizeof(int32_t) * n));
     CG_TRY(d2h(out->cell_start, d.cell_start, sizeof(int32_t) * (nb + 1)));
-    if (dt > 0.0 && n > 0) {
-        CG_TRY(d2h(p->pos_d, S.pos.p, 4 * ts * n));
-        CG_TRY(d2h(p->vel, S.vel.p, 4 * ts * n));
-    }
     CG_CUDA(cudaEventRecord(S.out_done, s));
     return CG_OK;
 }

@@ -217,6 +217,12 @@ struct cg_grids {
     cg::HostStage hs[2];
     int hs_next = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr;
+    // the last host step that advanced its particles in place: the event
+    // after their copies back and the host arrays they went to (a later
+    // host step reading those arrays waits for them)
+    cudaEvent_t part_out = nullptr;
+    const void* part_pos = nullptr;
+    const void* part_vel = nullptr;
     cg::DevBuf fresh4;   // [nbulk] T4: (phi, u) of the fresh field of cg_mlp_features
     cg::DevBuf Bs;       // [cap] T4: (beta, beta u) in sorted order, for the semi-implicit coefficients
 
