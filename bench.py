@@ -262,9 +262,9 @@ def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False, sorted_s
         "project_implicit": nf * 16 + nbx * 16,           # A_f, b_f written, A, b read
         # incremental rebinning (the movers' placement and the idle fallback not counted)
         "rebin_key": n * (16 + 4 + 4),                    # pos read; key, diameter written
-        "rebin_mark": n * ((16 + 4 + 4 + 4 + 8) if sorted_step else (4 + 4 + 4 + 8)),
-        # sorted input: pos, old cell read; key, diameter, record written;
-        # else old id, old cell, new cell (gathered) read, record written
+        "rebin_mark": n * ((16 + 4 + 4 + 4) if sorted_step else (4 + 4 + 4 + 8)),
+        # sorted input: pos, old cell read; diameter, record written;
+        # else old id, old cell, new cell (gathered) read; record, old id written
         "rebin_cells": nbx * 16,                          # old starts, departures, arrivals read; counts written
         "rebin_slots": n * (8 + 4 + 16),                  # stayers (the movers beside them not counted): record,
                                                           # diameter read; perm, cell, inverse, diameter written
