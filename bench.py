@@ -266,8 +266,9 @@ def algorithmic_bytes(g, n, eps_fine=True, implicit=False, euler=False, sorted_s
         # sorted input: pos, old cell read; diameter, record written;
         # else old id, old cell, new cell (gathered) read; record, old id written
         "rebin_cells": nbx * 16,                          # old starts, departures, arrivals read; counts written
-        "rebin_slots": n * (8 + 4 + 16),                  # stayers (the movers beside them not counted): record,
-                                                          # diameter read; perm, cell, inverse, diameter written
+        "rebin_slots": n * (4 + 4 + 16 + (0 if sorted_step else 4)),
+        # stayers (the movers beside them not counted): record, diameter (and
+        # in caller order the old id) read; perm, cell, inverse, diameter written
     }
     step = n * 48 + nf * (24 + (4 if eps_fine else 0)) + nb * 40
     if euler:
